@@ -1,0 +1,240 @@
+/*
+ * qcs.h -- C ABI of the GB300 (sm_103a) library for tensor-network quantum
+ * circuit simulation by error-corrected SGEMM emulation on tensor cores with
+ * automatic precision selection (Ootomo, Manabe, Harada, Yokota, 2023).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Matrices are BLAS column-major.  A complex number is qcs_c32 (two
+ *   floats, real then imaginary: layout-compatible with cuComplex and
+ *   torch.complex64).  Element (i, j) of a matrix X with leading dimension
+ *   ldx is X[i + j * ldx].
+ * - op(X): QCS_OP_N uses X as stored, QCS_OP_T its transpose, QCS_OP_C its
+ *   conjugate transpose.
+ * - Pointers marked "device" are CUDA device pointers owned by the caller;
+ *   the library never frees or keeps them beyond the call's stream work.
+ *   Pointers marked "host" are read during the call only.
+ * - Every call is asynchronous on the handle's stream and never waits for
+ *   the GPU (Section 4.2: the statistics never travel to the host).
+ *   Argument errors are found on the host and returned before any launch.
+ *   Errors raised on the device (a bounded wait that ran out) are recorded
+ *   in a device error word and returned by the next qcs_sync().
+ * - Return value: QCS_SUCCESS (0) or a negative QCS_ERR_* code.
+ * - No call takes or returns ownership of memory: the handle owns its
+ *   workspace (allocated with cudaMalloc on first need, grown on demand,
+ *   freed by qcs_destroy).
+ */
+#ifndef QCS_H
+#define QCS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QCS_SUCCESS 0
+#define QCS_ERR_INVALID_ARG (-1) /* bad pointer, size, leading dimension, enum or plan */
+#define QCS_ERR_UNSUPPORTED (-2) /* valid request this build cannot run (e.g. alignment) */
+#define QCS_ERR_ALLOC (-3)       /* cudaMalloc of the workspace failed */
+#define QCS_ERR_CUDA (-4)        /* a CUDA runtime call failed */
+#define QCS_ERR_TIMEOUT (-5)     /* a device-side bounded wait ran out (see qcs_sync) */
+
+typedef struct qcs_handle_s *qcs_handle_t;
+
+/* GEMM computing modes.  Section 2.1 / Table 1 define FP16TCEC and TF32TCEC,
+ * Section 4 adds FP16TCEC with scaling and the automatic choice between them;
+ * FP32 is the plain single-precision SIMT baseline; BF16X3 is a measured
+ * candidate with the same split on bfloat16 parts (not chosen by AUTO). */
+typedef enum {
+    QCS_MODE_AUTO = 0,
+    QCS_MODE_FP16X = 1,
+    QCS_MODE_FP16X_SCALED = 2,
+    QCS_MODE_TF32X = 3,
+    QCS_MODE_FP32 = 4,
+    QCS_MODE_BF16X3 = 5
+} qcs_mode_t;
+
+typedef enum { QCS_OP_N = 0, QCS_OP_T = 1, QCS_OP_C = 2 } qcs_op_t;
+
+typedef struct {
+    float x, y;
+} qcs_c32;
+
+/* Exponent statistics of one matrix (Section 4.1), device-resident.
+ * Every real and every imaginary scalar x counts once.  For x != 0,
+ * e = floor(log2 |x|); hist[e + 127] counts normal binary32 numbers,
+ * hist[0] subnormal ones and hist[255] Inf/NaN.  Zeros enter no bin and are
+ * counted in n_zero.  n is the total number of scalars (2 * rows * cols). */
+typedef struct {
+    int64_t hist[256];
+    int64_t n_zero;
+    int64_t n;
+} qcs_stats_t;
+
+/* Per-GEMM mode descriptor written on the device by the selector (the
+ * "mode flag buffer" of Section 4.2): the chosen qcs_mode_t and the
+ * power-of-two exponents sA, sB applied to op(A), op(B) before the split
+ * (zero unless mode is FP16X_SCALED; the product is multiplied by
+ * 2^-(sA+sB) in the epilogue). */
+typedef struct {
+    int32_t mode;
+    int32_t sA;
+    int32_t sB;
+    int32_t reserved;
+} qcs_gemm_desc_t;
+
+/* Create a handle bound to the current CUDA device and to ``cuda_stream``
+ * (a cudaStream_t; NULL = legacy default stream).  Returns INVALID_ARG if
+ * ``out`` is NULL, CUDA if no device is usable. */
+int qcs_create(qcs_handle_t *out, void *cuda_stream);
+
+/* Destroy a handle: synchronizes its stream, frees its workspace. */
+int qcs_destroy(qcs_handle_t h);
+
+/* Rebind the handle to another stream (subsequent calls only). */
+int qcs_set_stream(qcs_handle_t h, void *cuda_stream);
+
+/* Underflow tolerance t of Section 4.1 (the "underflow admissibility
+ * threshold", AUTO-t of Section 5.2), in [0, 1].  An operand tolerates a
+ * mode when at most t * (number of nonzero finite scalars) of its scalars
+ * fall outside that mode's exponent window.  Default 0 (no underflow). */
+int qcs_set_underflow_tol(qcs_handle_t h, double t);
+
+/* Enable (1, default) or disable (0) the size rule of Section 4.3 for
+ * QCS_MODE_AUTO: min(m,n,k) >= 2048 -> automatic selection; >= 512 ->
+ * TF32X; else FP32.  With the rule disabled AUTO always selects from the
+ * statistics. */
+int qcs_set_size_rule(qcs_handle_t h, int enabled);
+
+/* Exponent statistics (Section 4.1, Stage 1 and Stage 2 in one pass) of the
+ * rows x cols complex matrix X (device, leading dim ldx >= rows), written
+ * to d_stats (device, caller-owned).  rows or cols may be 0. */
+int qcs_exp_stats(qcs_handle_t h, int64_t rows, int64_t cols, const qcs_c32 *X, int64_t ldx,
+                  qcs_stats_t *d_stats);
+
+/* Mode selection rule of Section 4.1 from the statistics of op(A) and
+ * op(B) (both device), with the handle's tolerance.  Writes the descriptor
+ * to d_desc (device).  Either operand out of both FP16 windows -> TF32X;
+ * either out of the unscaled window -> FP16X_SCALED with sA, sB moving each
+ * maximum exponent to 14; otherwise FP16X.  Inf/NaN or a maximum exponent
+ * of 127 -> FP32. */
+int qcs_select(qcs_handle_t h, const qcs_stats_t *d_statsA, const qcs_stats_t *d_statsB,
+               qcs_gemm_desc_t *d_desc);
+
+/* C = alpha * op(A) * op(B) + beta * C (Section 3: the complex product as
+ * four real products, each emulated with Eq. 1 of Section 2.1).
+ *   op(A) is m x k, op(B) is k x n, C is m x n; all device pointers.
+ *   lda >= rows of A as stored (m for OP_N, k otherwise), likewise ldb, and
+ *   ldc >= m.  alpha and beta are host pointers.  m, n, k >= 0.
+ *   mode AUTO runs statistics + selection on the device (Section 4); a forced
+ *   mode skips them.  d_desc_out (device, optional) receives the descriptor
+ *   the GEMM ran with.  C must not overlap A or B.
+ *   The tensor-core modes need A, B, C 8-byte aligned (always true for
+ *   cudaMalloc'd complex64); otherwise UNSUPPORTED. */
+int qcs_cgemm(qcs_handle_t h, qcs_mode_t mode, qcs_op_t transA, qcs_op_t transB, int64_t m,
+              int64_t n, int64_t k, const qcs_c32 *alpha, const qcs_c32 *A, int64_t lda,
+              const qcs_c32 *B, int64_t ldb, const qcs_c32 *beta, qcs_c32 *C, int64_t ldc,
+              qcs_gemm_desc_t *d_desc_out);
+
+/* The split stage of qcs_cgemm alone (Eq. 1 of Section 2.1 after the
+ * scaling of Section 4.2), for inspection: op(X) (R x K for which == 0, i.e.
+ * the A operand; K x R for which == 1, the B operand) is split under the
+ * mode and scale held in d_desc (device) into four planes
+ * hi.re, hi.im, lo.re, lo.im, each R x K row-major (K contiguous) with row
+ * pitch ``pitch`` elements, stored as IEEE binary16 bit patterns (FP16X,
+ * FP16X_SCALED), bfloat16 bit patterns (BF16X3) or binary32 (TF32X).  Planes
+ * are consecutive, ``plane_stride`` elements apart.  Nothing is written for
+ * mode FP32. */
+int qcs_split(qcs_handle_t h, const qcs_gemm_desc_t *d_desc, int which, qcs_op_t op, int64_t R,
+              int64_t K, const qcs_c32 *X, int64_t ldx, void *planes, int64_t pitch,
+              int64_t plane_stride);
+
+/* Tensor permutation with fixed (sliced) indices: the reshaping step of the
+ * TTGT contraction (Section 1, Section 2.2).  out (device, contiguous,
+ * first index fastest) has ``rank`` dims ``dims[0..rank)``; its element
+ * (i_0, ..., i_{r-1}) is in[offset + sum_d i_d * strides[d]] (element
+ * strides of the input, device).  dims/strides are host arrays, rank <= 24.
+ * When d_stats is not NULL, the exponent statistics of the output are also
+ * written there (fused, Section 4.1). */
+int qcs_permute(qcs_handle_t h, int rank, const int64_t *dims, const int64_t *strides,
+                int64_t offset, const qcs_c32 *in, qcs_c32 *out, qcs_stats_t *d_stats);
+
+/* ---- contraction tree (Section 2.2, Section 5.3) ---------------------- */
+
+/* One pairwise contraction step of a plan.  Tensors are numbered: leaves
+ * 0 .. n_leaves-1, then step s produces tensor n_leaves + s.  Every tensor
+ * is stored contiguous, first index fastest.  The step computes
+ *   out(m x n) = op_a(A_mat) * op_b(B_mat)
+ * where A_mat is the m x k matrix gathered from tensor ``a`` (gather: rank,
+ * dims, element strides into the source tensor, and, for leaves, a
+ * per-slice offset table) and likewise B_mat (k x n).  A gather with
+ * rank == -1 means the source tensor is used as it is (already the m x k /
+ * k x n column-major matrix). */
+typedef struct {
+    int32_t rank;
+    int32_t pad_;
+    int64_t dims[24];
+    int64_t strides[24];
+} qcs_gather_t;
+
+typedef struct {
+    int32_t a, b;         /* source tensor ids */
+    int32_t op_a, op_b;   /* qcs_op_t applied after the gather */
+    int64_t m, n, k;
+    qcs_gather_t ga, gb;  /* gathers building A_mat (m x k) and B_mat (k x n) */
+    int32_t mode;         /* qcs_mode_t for this GEMM (AUTO = per-GEMM selection) */
+    int32_t pad_;
+} qcs_step_t;
+
+typedef struct {
+    int32_t n_leaves;
+    int32_t n_steps;
+    int32_t n_slices;        /* >= 1 */
+    int32_t pad_;
+    const int64_t *leaf_size;     /* host, n_leaves: elements of each leaf as sliced */
+    const int64_t *slice_offset;  /* host, n_slices * n_leaves: element offset of each
+                                     sliced leaf into the caller's full leaf tensor */
+    const qcs_step_t *steps;      /* host, n_steps; the last step's output is the result */
+    int64_t out_size;             /* elements of the final tensor (1 for an amplitude) */
+} qcs_tree_t;
+
+typedef struct {
+    double seconds;            /* host wall time of the call (launch side) */
+    int64_t gemm_count;        /* GEMMs issued (all slices) */
+    int64_t mode_count[6];     /* GEMMs per forced/size-rule mode; AUTO ones are counted in [0] */
+    int64_t workspace_bytes;   /* bytes of intermediates + GEMM workspace in use */
+} qcs_run_info_t;
+
+/* Contract the plan for every slice and sum the slices in FP64.
+ *   leaves: host array of n_leaves device pointers (complex64, full tensors).
+ *   d_out: device complex128 (interleaved double re, im), out_size elements,
+ *   overwritten with the sum over slices of the final tensor.
+ *   info: optional host out. */
+int qcs_contract_tree(qcs_handle_t h, const qcs_tree_t *tree, const qcs_c32 *const *leaves,
+                      double *d_out, qcs_run_info_t *info);
+
+/* Adjoint of qcs_contract_tree.  Given d_grad_out (device complex128,
+ * out_size elements: dL/dRe + i dL/dIm of the summed result), accumulates
+ * into d_grad_leaves[i] (host array of device complex64 pointers, each the
+ * size of the caller's full leaf tensor) the gradient of L with respect to
+ * each leaf, in the same convention.  Each GEMM of the forward pass has two
+ * adjoint GEMMs, grad_A = grad_C op(B)^H and grad_B = op(A)^H grad_C, run as
+ * emulated CGEMMs; intermediates are recomputed per slice. */
+int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
+                               const qcs_c32 *const *leaves, const double *d_grad_out,
+                               qcs_c32 *const *d_grad_leaves, qcs_run_info_t *info);
+
+/* Wait for the handle's stream; return TIMEOUT if a device-side bounded
+ * wait gave up since the last qcs_sync (the word is then cleared), CUDA on
+ * a runtime error, else SUCCESS. */
+int qcs_sync(qcs_handle_t h);
+
+/* Static string for a status code. */
+const char *qcs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCS_H */

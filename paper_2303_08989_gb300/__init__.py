@@ -1,0 +1,196 @@
+"""GB300-native emulated-CGEMM tensor-network quantum circuit simulation.
+
+Python face of libqcs (include/qcs.h).  Every numerical step runs in the CUDA
+library; this module only passes device pointers, sizes and the current torch
+stream.  Matrices are column-major: a torch tensor ``X`` of shape (rows, cols)
+with ``X.stride() == (1, ld)`` (``ld >= rows``), complex64, on the GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+from . import _lib
+from ._lib import (MODE_AUTO, MODE_BF16X3, MODE_BY_NAME, MODE_FP16X, MODE_FP16X_SCALED, MODE_FP32,
+                   MODE_NAME, MODE_TF32X, OP_C, OP_N, OP_T, QcsError)
+
+__all__ = [
+    "Handle", "cgemm", "exp_stats", "select", "split", "permute", "fortran_empty", "to_fortran",
+    "MODE_AUTO", "MODE_FP16X", "MODE_FP16X_SCALED", "MODE_TF32X", "MODE_FP32", "MODE_BF16X3",
+    "MODE_BY_NAME", "MODE_NAME", "OP_N", "OP_T", "OP_C", "QcsError",
+]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _mode(mode) -> int:
+    if isinstance(mode, str):
+        return MODE_BY_NAME[mode]
+    return int(mode)
+
+
+def _ld(X, rows: int) -> int:
+    """Leading dimension of a column-major tensor view."""
+    if X.dim() != 2:
+        raise ValueError("expected a 2-D column-major tensor")
+    if X.shape[1] <= 1:
+        return max(rows, X.stride(1) if X.shape[1] == 1 else rows, 1)
+    if X.stride(0) != 1:
+        raise ValueError("tensor is not column-major (stride(0) must be 1)")
+    return X.stride(1)
+
+
+def fortran_empty(rows: int, cols: int, ld: Optional[int] = None, device="cuda"):
+    """Uninitialised column-major complex64 (rows x cols) with leading dim ld."""
+    torch = _torch()
+    ld = rows if ld is None else ld
+    base = torch.empty((cols, ld), dtype=torch.complex64, device=device)
+    return base.t()[:rows]
+
+
+def to_fortran(x, device="cuda"):
+    """Copy a 2-D array/tensor into a column-major complex64 device tensor."""
+    torch = _torch()
+    t = torch.as_tensor(x)
+    if t.dim() == 1:
+        t = t.reshape(-1, 1)
+    out = fortran_empty(t.shape[0], t.shape[1], device=device)
+    out.copy_(t.to(torch.complex64))
+    return out
+
+
+class Handle:
+    """Owns a qcs handle (workspace, tolerance, size rule) bound to a stream."""
+
+    def __init__(self, stream=None, tol: float = 0.0, size_rule: bool = True):
+        torch = _torch()
+        self.lib = _lib.load()
+        self._h = ctypes.c_void_p()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _lib.check(self.lib.qcs_create(ctypes.byref(self._h), ctypes.c_void_p(s.cuda_stream)),
+                   "qcs_create")
+        self.stream = s
+        self.set_tol(tol)
+        self.set_size_rule(size_rule)
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def set_stream(self, stream):
+        _lib.check(self.lib.qcs_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)))
+        self.stream = stream
+
+    def set_tol(self, t: float):
+        _lib.check(self.lib.qcs_set_underflow_tol(self._h, float(t)), "qcs_set_underflow_tol")
+        self.tol = float(t)
+
+    def set_size_rule(self, on: bool):
+        _lib.check(self.lib.qcs_set_size_rule(self._h, 1 if on else 0))
+        self.size_rule = bool(on)
+
+    def sync(self):
+        _lib.check(self.lib.qcs_sync(self._h), "qcs_sync")
+
+    def close(self):
+        if self._h:
+            self.lib.qcs_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cgemm(h: Handle, A, B, C=None, *, m=None, n=None, k=None, alpha=1.0, beta=0.0,
+          opA=OP_N, opB=OP_N, mode="auto", desc_out=None):
+    """C = alpha op(A) op(B) + beta C with qcs_cgemm; returns C.
+
+    A, B, C are column-major complex64 device tensors (see module doc).  If C
+    is None a new m x n tensor is allocated (beta must then be 0).
+    ``desc_out``: optional int32 device tensor with 4 elements receiving the
+    descriptor (mode, sA, sB, 0) the GEMM ran with.
+    """
+    torch = _torch()
+    rA, cA = A.shape
+    rB, cB = B.shape
+    m = (rA if opA == OP_N else cA) if m is None else m
+    k = (cA if opA == OP_N else rA) if k is None else k
+    n = (cB if opB == OP_N else rB) if n is None else n
+    if C is None:
+        if complex(beta) != 0:
+            raise ValueError("beta != 0 needs C")
+        C = fortran_empty(m, n, device=A.device)
+    lda = _ld(A, rA)
+    ldb = _ld(B, rB)
+    ldc = _ld(C, C.shape[0])
+    al = _lib.qcs_c32(complex(alpha).real, complex(alpha).imag)
+    be = _lib.qcs_c32(complex(beta).real, complex(beta).imag)
+    dp = ctypes.c_void_p(desc_out.data_ptr()) if desc_out is not None else None
+    rc = h.lib.qcs_cgemm(h.ptr, _mode(mode), int(opA), int(opB), m, n, k, ctypes.byref(al),
+                         ctypes.c_void_p(A.data_ptr()), lda, ctypes.c_void_p(B.data_ptr()), ldb,
+                         ctypes.byref(be), ctypes.c_void_p(C.data_ptr()), ldc, dp)
+    _lib.check(rc, "qcs_cgemm")
+    del torch
+    return C
+
+
+def exp_stats(h: Handle, X, out=None):
+    """Exponent statistics of a column-major matrix into an int64 device
+    tensor of 258 entries (hist[256], n_zero, n)."""
+    torch = _torch()
+    rows, cols = X.shape
+    if out is None:
+        out = torch.zeros(258, dtype=torch.int64, device=X.device)
+    _lib.check(h.lib.qcs_exp_stats(h.ptr, rows, cols, ctypes.c_void_p(X.data_ptr()), _ld(X, rows),
+                                   ctypes.c_void_p(out.data_ptr())), "qcs_exp_stats")
+    return out
+
+
+def select(h: Handle, statsA, statsB, desc=None):
+    """Mode selection from two statistics tensors; returns an int32 device
+    tensor (mode, sA, sB, 0)."""
+    torch = _torch()
+    if desc is None:
+        desc = torch.zeros(4, dtype=torch.int32, device=statsA.device)
+    _lib.check(h.lib.qcs_select(h.ptr, ctypes.c_void_p(statsA.data_ptr()),
+                                ctypes.c_void_p(statsB.data_ptr()), ctypes.c_void_p(desc.data_ptr())),
+               "qcs_select")
+    return desc
+
+
+def split(h: Handle, desc, which: int, op: int, X, R: int, K: int):
+    """The split stage alone: returns the 4 planes (hi.re, hi.im, lo.re,
+    lo.im) as a (4, R, K) int16 tensor (16-bit modes) or float32 tensor
+    (TF32X)."""
+    torch = _torch()
+    mode = int(desc[0].item())
+    dt = torch.float32 if mode == MODE_TF32X else torch.int16
+    planes = torch.zeros((4, R, K), dtype=dt, device=X.device)
+    rows = (R if op == OP_N else K) if which == 0 else (K if op == OP_N else R)
+    _lib.check(h.lib.qcs_split(h.ptr, ctypes.c_void_p(desc.data_ptr()), which, op, R, K,
+                               ctypes.c_void_p(X.data_ptr()), _ld(X, rows),
+                               ctypes.c_void_p(planes.data_ptr()), K, R * K), "qcs_split")
+    return planes
+
+
+def permute(h: Handle, src, dims, strides, offset: int = 0, out=None):
+    """Strided gather (first index fastest) of a complex64 device tensor."""
+    torch = _torch()
+    total = 1
+    for d in dims:
+        total *= int(d)
+    if out is None:
+        out = torch.empty(total, dtype=torch.complex64, device=src.device)
+    r = len(dims)
+    D = (ctypes.c_int64 * max(r, 1))(*[int(d) for d in dims])
+    S = (ctypes.c_int64 * max(r, 1))(*[int(s) for s in strides])
+    _lib.check(h.lib.qcs_permute(h.ptr, r, D, S, int(offset), ctypes.c_void_p(src.data_ptr()),
+                                 ctypes.c_void_p(out.data_ptr()), None), "qcs_permute")
+    return out

@@ -1,0 +1,134 @@
+"""ctypes binding of libqcs.so (include/qcs.h): argument marshalling only.
+
+The library is built in-tree by ``paper_2303_08989_gb300.build`` into
+``paper_2303_08989_gb300/_build/libqcs.so``.  Loading fails loudly when it is
+missing: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libqcs.so")
+
+QCS_SUCCESS = 0
+QCS_ERR_INVALID_ARG = -1
+QCS_ERR_UNSUPPORTED = -2
+QCS_ERR_ALLOC = -3
+QCS_ERR_CUDA = -4
+QCS_ERR_TIMEOUT = -5
+
+MODE_AUTO, MODE_FP16X, MODE_FP16X_SCALED, MODE_TF32X, MODE_FP32, MODE_BF16X3 = range(6)
+MODE_BY_NAME = {"auto": 0, "fp16x": 1, "fp16x_scaled": 2, "tf32x": 3, "fp32": 4, "bf16x3": 5}
+MODE_NAME = {v: k for k, v in MODE_BY_NAME.items()}
+OP_N, OP_T, OP_C = 0, 1, 2
+
+#: every entry point include/qcs.h declares
+EXPORTED = [
+    "qcs_create", "qcs_destroy", "qcs_set_stream", "qcs_set_underflow_tol", "qcs_set_size_rule",
+    "qcs_exp_stats", "qcs_select", "qcs_cgemm", "qcs_split", "qcs_permute", "qcs_contract_tree",
+    "qcs_contract_tree_backward", "qcs_sync", "qcs_status_string",
+]
+
+
+class QcsError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})" if what else status_string(code))
+
+
+class qcs_c32(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_float), ("y", ctypes.c_float)]
+
+
+class qcs_stats_t(ctypes.Structure):
+    _fields_ = [("hist", ctypes.c_int64 * 256), ("n_zero", ctypes.c_int64), ("n", ctypes.c_int64)]
+
+
+class qcs_gemm_desc_t(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("sA", ctypes.c_int32), ("sB", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class qcs_gather_t(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("dims", ctypes.c_int64 * 24), ("strides", ctypes.c_int64 * 24)]
+
+
+class qcs_step_t(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_int32), ("b", ctypes.c_int32), ("op_a", ctypes.c_int32),
+                ("op_b", ctypes.c_int32), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("k", ctypes.c_int64), ("ga", qcs_gather_t), ("gb", qcs_gather_t),
+                ("mode", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+class qcs_tree_t(ctypes.Structure):
+    _fields_ = [("n_leaves", ctypes.c_int32), ("n_steps", ctypes.c_int32),
+                ("n_slices", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("leaf_size", ctypes.POINTER(ctypes.c_int64)),
+                ("slice_offset", ctypes.POINTER(ctypes.c_int64)),
+                ("steps", ctypes.POINTER(qcs_step_t)), ("out_size", ctypes.c_int64)]
+
+
+class qcs_run_info_t(ctypes.Structure):
+    _fields_ = [("seconds", ctypes.c_double), ("gemm_count", ctypes.c_int64),
+                ("mode_count", ctypes.c_int64 * 6), ("workspace_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libqcs.so and declare every prototype.  Raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    I64 = ctypes.c_int64
+    H = ctypes.c_void_p
+    sig = {
+        "qcs_create": [ctypes.POINTER(ctypes.c_void_p), P],
+        "qcs_destroy": [H],
+        "qcs_set_stream": [H, P],
+        "qcs_set_underflow_tol": [H, ctypes.c_double],
+        "qcs_set_size_rule": [H, I],
+        "qcs_exp_stats": [H, I64, I64, P, I64, P],
+        "qcs_select": [H, P, P, P],
+        "qcs_cgemm": [H, I, I, I, I64, I64, I64, ctypes.POINTER(qcs_c32), P, I64, P, I64,
+                      ctypes.POINTER(qcs_c32), P, I64, P],
+        "qcs_split": [H, P, I, I, I64, I64, P, I64, P, I64, I64],
+        "qcs_permute": [H, I, ctypes.POINTER(I64), ctypes.POINTER(I64), I64, P, P, P],
+        "qcs_contract_tree": [H, ctypes.POINTER(qcs_tree_t), ctypes.POINTER(P), P,
+                              ctypes.POINTER(qcs_run_info_t)],
+        "qcs_contract_tree_backward": [H, ctypes.POINTER(qcs_tree_t), ctypes.POINTER(P), P,
+                                       ctypes.POINTER(P), ctypes.POINTER(qcs_run_info_t)],
+        "qcs_sync": [H],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = I
+    lib.qcs_status_string.argtypes = [I]
+    lib.qcs_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return load().qcs_status_string(code).decode()
+    except ImportError:
+        return f"status {code}"
+
+
+def check(code: int, what: str = ""):
+    if code != QCS_SUCCESS:
+        raise QcsError(code, what)
+    return code

@@ -1,0 +1,384 @@
+// C ABI (include/qcs.h): argument validation, workspace, tensor-map encoding
+// and the launch sequence of one emulated CGEMM:
+//
+//   stats(A) + stats(B)  -- one launch, one HBM pass over each operand
+//   select               -- mode flag / scale descriptor on the device
+//   split(A), split(B)   -- Eq. 1 planes (kernel exits for mode FP32)
+//   tcgen05 FP16 kernel  -- exits unless FP16X / FP16X_SCALED was selected
+//   tcgen05 TF32 kernel  -- exits unless TF32X was selected
+//   SIMT FP32 kernel     -- exits unless FP32 was selected
+//
+// i.e. the host never learns the mode: every candidate is launched and the
+// ones not selected return at once (Section 4.2).
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace qcs;
+
+namespace qcs {
+
+int ensure_workspace(Workspace &w, size_t bytes) {
+    if (bytes <= w.bytes) return QCS_SUCCESS;
+    if (w.ptr) {
+        cudaFree(w.ptr);
+        w.ptr = nullptr;
+        w.bytes = 0;
+    }
+    // grow with some headroom so that a sweep of sizes does not reallocate each call
+    const size_t want = bytes + bytes / 8;
+    if (cudaMalloc(&w.ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        w.ptr = nullptr;
+        return QCS_ERR_ALLOC;
+    }
+    w.bytes = want;
+    return QCS_SUCCESS;
+}
+
+}  // namespace qcs
+
+namespace {
+
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? QCS_SUCCESS : QCS_ERR_CUDA; }
+
+// Number of stats blocks for a matrix of ``nel`` complex values.
+int stats_blocks(int64_t nel, int num_sms) {
+    const int64_t per_block = int64_t(kStatsThreads) * 64;  // complex values per block, minimum
+    int64_t g = (nel + per_block - 1) / per_block;
+    g = std::max<int64_t>(1, std::min<int64_t>(g, num_sms));
+    return static_cast<int>(g);
+}
+
+int encode_planes(qcs_handle_t h, CUtensorMap *map, void *base, int64_t R_pad, int64_t K_pad,
+                  int esz) {
+    const CUtensorMapDataType dt =
+        esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    cuuint64_t gdim[3] = {(cuuint64_t)K_pad, (cuuint64_t)R_pad, (cuuint64_t)kPlanes};
+    cuuint64_t gstride[2] = {(cuuint64_t)(K_pad * esz), (cuuint64_t)(K_pad * R_pad * esz)};
+    cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)kBM, (cuuint32_t)kPlanes};
+    cuuint32_t estride[3] = {1, 1, 1};
+    CUresult r = h->encode(map, dt, 3, base, gdim, gstride, box, estride,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? QCS_SUCCESS : QCS_ERR_CUDA;
+}
+
+bool valid_op(int op) { return op == QCS_OP_N || op == QCS_OP_T || op == QCS_OP_C; }
+bool valid_mode(int m) { return m >= QCS_MODE_AUTO && m <= QCS_MODE_BF16X3; }
+
+// Plane strides of op(X) for the split: element (r, c) of the plane is
+// X[r * sr + c * sc].  For the A operand r = i, c = l (op(A) is m x k);
+// for the B operand r = j, c = l (op(B) is k x n).
+void plane_strides(int which, int op, int64_t ld, int64_t &sr, int64_t &sc) {
+    if (which == 0) {
+        if (op == QCS_OP_N) { sr = 1; sc = ld; } else { sr = ld; sc = 1; }
+    } else {
+        if (op == QCS_OP_N) { sr = ld; sc = 1; } else { sr = 1; sc = ld; }
+    }
+}
+
+}  // namespace
+
+// Effective mode after the size rule (host side, sizes are known on the host).
+static int effective_mode(qcs_handle_t h, int mode, int64_t m, int64_t n, int64_t k) {
+    if (mode != QCS_MODE_AUTO || !h->size_rule) return mode;
+    const int64_t s = std::min(m, std::min(n, k));
+    if (s >= 2048) return QCS_MODE_AUTO;
+    if (s >= 512) return QCS_MODE_TF32X;
+    return QCS_MODE_FP32;
+}
+
+// The whole emulated CGEMM on the handle's stream.  desc_ws/partials/planes
+// come from ``ws`` (a device buffer of at least gemm_workspace_bytes()).
+namespace qcs {
+
+size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms) {
+    size_t bytes = 256;  // descriptor
+    bytes += align256(size_t(2) * num_sms * kPartialStride * sizeof(int64_t));
+    if (eff != QCS_MODE_FP32) {
+        const int esz = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X) ? 4 : 2;
+        const int64_t kp = round_up(k, 32), mp = round_up(m, kBM), np = round_up(n, kBN);
+        bytes += align256(size_t(kPlanes) * mp * kp * esz);
+        bytes += align256(size_t(kPlanes) * np * kp * esz);
+    }
+    return bytes;
+}
+
+int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n, int64_t k,
+              float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta,
+              float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out, const qcs_gemm_desc_t *d_desc_in) {
+    cudaStream_t s = h->stream;
+    uint8_t *p = static_cast<uint8_t *>(ws);
+    qcs_gemm_desc_t *desc = reinterpret_cast<qcs_gemm_desc_t *>(p);
+    p += 256;
+    int64_t *partials = reinterpret_cast<int64_t *>(p);
+    p += align256(size_t(2) * h->num_sms * kPartialStride * sizeof(int64_t));
+    cudaError_t e = cudaSuccess;
+
+    if (d_desc_in) {
+        desc = const_cast<qcs_gemm_desc_t *>(d_desc_in);
+    } else if (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X_SCALED) {
+        // Statistics of both operands as stored (a transpose does not change the multiset).
+        const int64_t ra = (opA == QCS_OP_N) ? m : k, ca = (opA == QCS_OP_N) ? k : m;
+        const int64_t rb = (opB == QCS_OP_N) ? k : n, cb = (opB == QCS_OP_N) ? n : k;
+        const int gA = stats_blocks(ra * ca, h->num_sms), gB = stats_blocks(rb * cb, h->num_sms);
+        e = launch_stats2(A, ra, ca, lda, gA, B, rb, cb, ldb, gB, partials, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+        e = launch_select(partials, gA, gB, 2 * ra * ca, 2 * rb * cb, h->tol, eff, nullptr,
+                          nullptr, desc, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    } else {
+        e = launch_set_desc(desc, eff, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    }
+
+    if (k == 0) {
+        // C = beta C: the SIMT kernel with k = 0 does exactly that (no desc gate).
+        e = launch_cgemm_simt(nullptr, opA, opB, m, n, 0, alpha, A, lda, B, ldb, beta, C, ldc, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    } else if (eff != QCS_MODE_FP32) {
+        const int64_t kp = round_up(k, 32), mp = round_up(m, kBM), np = round_up(n, kBN);
+        const bool need16 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X ||
+                             eff == QCS_MODE_FP16X_SCALED || eff == QCS_MODE_BF16X3);
+        const bool need32 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X);
+        const int esz_max = need32 ? 4 : 2;
+        uint8_t *planesA = p;
+        uint8_t *planesB = p + align256(size_t(kPlanes) * mp * kp * esz_max);
+        int64_t sr, sc;
+        // The split writes with the selected kind's element size; the pitch is
+        // kp elements either way, so both tensor maps below describe it.
+        plane_strides(0, opA, lda, sr, sc);
+        e = launch_split(desc, 0, A, sr, sc, opA == QCS_OP_C, m, k, mp, kp, planesA, kp, mp * kp, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+        plane_strides(1, opB, ldb, sr, sc);
+        e = launch_split(desc, 1, B, sr, sc, opB == QCS_OP_C, n, k, np, kp, planesB, kp, np * kp, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+        if (need16) {
+            CUtensorMap ma, mb;
+            if (encode_planes(h, &ma, planesA, mp, kp, 2) || encode_planes(h, &mb, planesB, np, kp, 2))
+                return QCS_ERR_CUDA;
+            const int kind = (eff == QCS_MODE_BF16X3) ? 2 : 0;
+            e = launch_cgemm_tc(kind, desc, &ma, &mb, m, n, kp, alpha, beta, C, ldc, h->d_err,
+                                h->num_sms, s);
+            if (e != cudaSuccess) return QCS_ERR_CUDA;
+        }
+        if (need32) {
+            CUtensorMap ma, mb;
+            if (encode_planes(h, &ma, planesA, mp, kp, 4) || encode_planes(h, &mb, planesB, np, kp, 4))
+                return QCS_ERR_CUDA;
+            e = launch_cgemm_tc(1, desc, &ma, &mb, m, n, kp, alpha, beta, C, ldc, h->d_err,
+                                h->num_sms, s);
+            if (e != cudaSuccess) return QCS_ERR_CUDA;
+        }
+        if (eff == QCS_MODE_AUTO) {
+            e = launch_cgemm_simt(desc, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+            if (e != cudaSuccess) return QCS_ERR_CUDA;
+        }
+    } else {
+        e = launch_cgemm_simt(nullptr, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    }
+    if (d_desc_out) {
+        e = cudaMemcpyAsync(d_desc_out, desc, sizeof(qcs_gemm_desc_t), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    }
+    return QCS_SUCCESS;
+}
+
+int validate_cgemm(int mode, int opA, int opB, int64_t m, int64_t n, int64_t k, const void *alpha,
+                   const void *A, int64_t lda, const void *B, int64_t ldb, const void *beta,
+                   const void *C, int64_t ldc) {
+    if (!valid_mode(mode) || !valid_op(opA) || !valid_op(opB)) return QCS_ERR_INVALID_ARG;
+    if (m < 0 || n < 0 || k < 0) return QCS_ERR_INVALID_ARG;
+    if (!alpha || !beta) return QCS_ERR_INVALID_ARG;
+    const int64_t rowsA = (opA == QCS_OP_N) ? m : k;
+    const int64_t rowsB = (opB == QCS_OP_N) ? k : n;
+    if (lda < std::max<int64_t>(1, rowsA) || ldb < std::max<int64_t>(1, rowsB) ||
+        ldc < std::max<int64_t>(1, m))
+        return QCS_ERR_INVALID_ARG;
+    if (m == 0 || n == 0) return QCS_SUCCESS;
+    if (!C) return QCS_ERR_INVALID_ARG;
+    if (k > 0 && (!A || !B)) return QCS_ERR_INVALID_ARG;
+    auto mis = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) != 0; };
+    if (mis(A) || mis(B) || mis(C)) return QCS_ERR_UNSUPPORTED;
+    return QCS_SUCCESS;
+}
+
+}  // namespace qcs
+
+extern "C" {
+
+int qcs_create(qcs_handle_t *out, void *cuda_stream) {
+    if (!out) return QCS_ERR_INVALID_ARG;
+    *out = nullptr;
+    qcs_handle_s *h = new (std::nothrow) qcs_handle_s;
+    if (!h) return QCS_ERR_ALLOC;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return QCS_ERR_CUDA;
+    }
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return QCS_ERR_ALLOC;
+    }
+    cudaMemset(h->d_err, 0, sizeof(int));
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        cudaFree(h->d_err);
+        delete h;
+        return QCS_ERR_CUDA;
+    }
+    h->encode = reinterpret_cast<EncodeTiledFn>(fn);
+    if (const char *t = std::getenv("QCS_UNDERFLOW_TOL")) h->tol = std::atof(t);
+    if (const char *r = std::getenv("QCS_SIZE_RULE")) h->size_rule = std::atoi(r) != 0;
+    *out = h;
+    return QCS_SUCCESS;
+}
+
+int qcs_destroy(qcs_handle_t h) {
+    if (!h) return QCS_ERR_INVALID_ARG;
+    cudaStreamSynchronize(h->stream);
+    if (h->ws.ptr) cudaFree(h->ws.ptr);
+    if (h->tree_ws.ptr) cudaFree(h->tree_ws.ptr);
+    if (h->d_err) cudaFree(h->d_err);
+    delete h;
+    return QCS_SUCCESS;
+}
+
+int qcs_set_stream(qcs_handle_t h, void *cuda_stream) {
+    if (!h) return QCS_ERR_INVALID_ARG;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    return QCS_SUCCESS;
+}
+
+int qcs_set_underflow_tol(qcs_handle_t h, double t) {
+    if (!h || !(t >= 0.0 && t <= 1.0)) return QCS_ERR_INVALID_ARG;
+    h->tol = t;
+    return QCS_SUCCESS;
+}
+
+int qcs_set_size_rule(qcs_handle_t h, int enabled) {
+    if (!h) return QCS_ERR_INVALID_ARG;
+    h->size_rule = enabled ? 1 : 0;
+    return QCS_SUCCESS;
+}
+
+int qcs_exp_stats(qcs_handle_t h, int64_t rows, int64_t cols, const qcs_c32 *X, int64_t ldx,
+                  qcs_stats_t *d_stats) {
+    if (!h || !d_stats || rows < 0 || cols < 0 || ldx < std::max<int64_t>(1, rows))
+        return QCS_ERR_INVALID_ARG;
+    if (rows * cols > 0 && !X) return QCS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(X) & 7u) != 0) return QCS_ERR_UNSUPPORTED;
+    const size_t bytes = align256(size_t(2) * h->num_sms * kPartialStride * sizeof(int64_t)) + 256;
+    if (int r = ensure_workspace(h->ws, bytes)) return r;
+    int64_t *partials = reinterpret_cast<int64_t *>(static_cast<uint8_t *>(h->ws.ptr) + 256);
+    const int g = stats_blocks(rows * cols, h->num_sms);
+    cudaError_t e = launch_stats2(reinterpret_cast<const float2 *>(X), rows, cols, ldx, g, nullptr,
+                                  0, 0, 1, 0, partials, h->stream);
+    if (e != cudaSuccess) return QCS_ERR_CUDA;
+    return cuda_status(launch_stats_finalize(partials, g, 2 * rows * cols, d_stats, h->stream));
+}
+
+int qcs_select(qcs_handle_t h, const qcs_stats_t *d_statsA, const qcs_stats_t *d_statsB,
+               qcs_gemm_desc_t *d_desc) {
+    if (!h || !d_statsA || !d_statsB || !d_desc) return QCS_ERR_INVALID_ARG;
+    return cuda_status(launch_select_from_stats(d_statsA, d_statsB, h->tol, d_desc, h->stream));
+}
+
+int qcs_cgemm(qcs_handle_t h, qcs_mode_t mode, qcs_op_t transA, qcs_op_t transB, int64_t m,
+              int64_t n, int64_t k, const qcs_c32 *alpha, const qcs_c32 *A, int64_t lda,
+              const qcs_c32 *B, int64_t ldb, const qcs_c32 *beta, qcs_c32 *C, int64_t ldc,
+              qcs_gemm_desc_t *d_desc_out) {
+    if (!h) return QCS_ERR_INVALID_ARG;
+    if (int r = validate_cgemm(mode, transA, transB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc))
+        return r;
+    if (m == 0 || n == 0) return QCS_SUCCESS;
+    if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) return QCS_ERR_UNSUPPORTED;
+    const int eff = effective_mode(h, mode, m, n, k);
+    if (int r = ensure_workspace(h->ws, gemm_workspace_bytes(eff, m, n, k, h->num_sms))) return r;
+    const float2 al = make_float2(alpha->x, alpha->y), be = make_float2(beta->x, beta->y);
+    return run_cgemm(h, h->ws.ptr, eff, transA, transB, m, n, k, al,
+                     reinterpret_cast<const float2 *>(A), lda, reinterpret_cast<const float2 *>(B),
+                     ldb, be, reinterpret_cast<float2 *>(C), ldc, d_desc_out, nullptr);
+}
+
+int qcs_split(qcs_handle_t h, const qcs_gemm_desc_t *d_desc, int which, qcs_op_t op, int64_t R,
+              int64_t K, const qcs_c32 *X, int64_t ldx, void *planes, int64_t pitch,
+              int64_t plane_stride) {
+    if (!h || !d_desc || !X || !planes || (which != 0 && which != 1) || !valid_op(op))
+        return QCS_ERR_INVALID_ARG;
+    if (R < 0 || K < 0 || pitch < K || plane_stride < R * pitch) return QCS_ERR_INVALID_ARG;
+    const int64_t rows = (which == 0) ? ((op == QCS_OP_N) ? R : K) : ((op == QCS_OP_N) ? K : R);
+    if (ldx < std::max<int64_t>(1, rows)) return QCS_ERR_INVALID_ARG;
+    int64_t sr, sc;
+    plane_strides(which, op, ldx, sr, sc);
+    return cuda_status(launch_split(d_desc, which, reinterpret_cast<const float2 *>(X), sr, sc,
+                                    op == QCS_OP_C, R, K, R, K, planes, pitch, plane_stride,
+                                    h->stream));
+}
+
+int qcs_permute(qcs_handle_t h, int rank, const int64_t *dims, const int64_t *strides,
+                int64_t offset, const qcs_c32 *in, qcs_c32 *out, qcs_stats_t *d_stats) {
+    if (!h || rank < 0 || rank > 24 || (rank > 0 && (!dims || !strides)) || !in || !out)
+        return QCS_ERR_INVALID_ARG;
+    int64_t total = 1;
+    for (int d = 0; d < rank; ++d) {
+        if (dims[d] < 0) return QCS_ERR_INVALID_ARG;
+        total *= dims[d];
+    }
+    cudaError_t e = launch_permute(rank, dims, strides, offset, reinterpret_cast<const float2 *>(in),
+                                   reinterpret_cast<float2 *>(out), nullptr, 0, h->stream);
+    if (e != cudaSuccess) return QCS_ERR_CUDA;
+    if (d_stats) return qcs_exp_stats(h, total, 1, out, std::max<int64_t>(1, total), d_stats);
+    return QCS_SUCCESS;
+}
+
+int qcs_sync(qcs_handle_t h) {
+    if (!h) return QCS_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    int err = 0;
+    if (cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return QCS_ERR_CUDA;
+    if (err != 0) {
+        cudaMemset(h->d_err, 0, sizeof(int));
+        return QCS_ERR_TIMEOUT;
+    }
+    return QCS_SUCCESS;
+}
+
+const char *qcs_status_string(int status) {
+    switch (status) {
+        case QCS_SUCCESS: return "success";
+        case QCS_ERR_INVALID_ARG: return "invalid argument";
+        case QCS_ERR_UNSUPPORTED: return "unsupported";
+        case QCS_ERR_ALLOC: return "workspace allocation failed";
+        case QCS_ERR_CUDA: return "CUDA runtime error";
+        case QCS_ERR_TIMEOUT: return "device-side wait timed out";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

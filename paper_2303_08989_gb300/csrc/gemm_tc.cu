@@ -1,0 +1,407 @@
+// Error-corrected complex GEMM on the fifth-generation tensor cores
+// (tcgen05, sm_103a).
+//
+// Method (Section 2.1, Eq. 1; Section 3): every FP32 operand x is split into
+// hi = toLow(x 2^s) and lo = toLow((x 2^s - hi) 2^11) (done by the split
+// kernel, which writes four planes per operand: hi.re, hi.im, lo.re, lo.im).
+// A complex product is four real products (Re = ArBr - AiBi,
+// Im = ArBi + AiBr); each real product is emulated by three tensor-core
+// products, hi*hi into accumulator 0 and lo*hi + hi*lo into accumulator 1:
+//   C = 2^-(sA+sB) (acc0 + 2^-11 acc1).
+//
+// Rounding.  Section 2.1 adds the hi*hi products outside the tensor core with
+// round-to-nearest because the A100 tensor core truncates inside its
+// accumulation.  The sm_103a tensor core truncates too (measured: 1 + 0.75 ulp
+// accumulates to 1, within one MMA and across MMAs, for FP16 and TF32
+// inputs), which makes the error of a TMEM-resident hi*hi sum grow linearly
+// with k.  So accumulator 0 is drained every pipeline stage (two UMMA K
+// steps): the stage's hi*hi sum is computed fresh in tensor memory and added
+// with round-to-nearest FP32 adds into registers of the epilogue warps.  The
+// correction products (accumulator 1, weight 2^-11) stay in tensor memory for
+// the whole K loop: their truncation error enters the result scaled by 2^-11.
+//
+// Kernel structure (one CTA per SM, persistent over 128 x 128 complex tiles):
+//   warp 0     TMA producer: per stage, one 3-D box of the four A planes and
+//              one of the four B planes (128 rows x 64 bytes each, 64-byte
+//              swizzle) into a 3-stage shared-memory ring.
+//   warp 1     MMA issuer (one thread).  Per stage: the 16 correction MMAs into
+//              acc1 first; then, once the epilogue has drained the previous
+//              stage's acc0, the 8 hi*hi MMAs into a fresh acc0.  The drain thus
+//              overlaps the correction MMAs.  Tensor memory: 512 columns =
+//              acc0.re, acc0.im, acc1.re, acc1.im x 128.  The -Ai*Bi terms use
+//              the instruction descriptor's negate-A bit.
+//   warps 2-9  epilogue, two warps per tensor-memory lane quadrant (each owns
+//              64 columns of its 32 rows): per stage, tcgen05.ld of acc0 and
+//              round-to-nearest adds into 128 registers; at the end of a tile,
+//              + 2^-11 acc1, the alpha/beta epilogue and coalesced stores (32
+//              consecutive complex values of one column per store).
+// The descriptor the selector wrote decides at run time whether this
+// instantiation runs at all (the "launch all candidates, the unselected one
+// exits" scheme of Section 4.2).
+#include <cuda_fp16.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace qcs {
+
+namespace {
+
+constexpr int kGroupM = 8;        // tile rows per raster group (L2 reuse of B panels)
+constexpr int kEpiWarps = 8;
+constexpr int kEpiCols = kBN / 2;  // columns per epilogue warp
+
+struct TcSmem {
+    uint8_t stage[kStages][kStageBytes];
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t acc0_full;
+    uint64_t acc0_empty;
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int &tm, int &tn) {
+    const int per_group = kGroupM * tiles_n;
+    const int g = t / per_group;
+    const int first_m = g * kGroupM;
+    const int gsize = min(tiles_m - first_m, kGroupM);
+    const int r = t - g * per_group;
+    tm = first_m + r % gsize;
+    tn = r / gsize;
+}
+
+__device__ __forceinline__ void raise_abort(TcSmem &S, int *d_err, int code) {
+    *reinterpret_cast<volatile int *>(&S.abort) = 1;
+    atomicCAS(d_err, 0, code);
+}
+
+__device__ __forceinline__ bool kind_runs(int kind, int mode) {
+    if (kind == 0) return mode == QCS_MODE_FP16X || mode == QCS_MODE_FP16X_SCALED;
+    if (kind == 1) return mode == QCS_MODE_TF32X;
+    return mode == QCS_MODE_BF16X3;
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t acc) {
+    if (KIND == 1)
+        mma_tf32(d, a, b, idesc, acc);
+    else
+        mma_f16(d, a, b, idesc, acc);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    cgemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
+                    const __grid_constant__ CUtensorMap mapB,
+                    const qcs_gemm_desc_t *__restrict__ desc, int m, int n, int k_pad,
+                    float2 alpha, float2 beta, float2 *__restrict__ C, int64_t ldc, int *d_err) {
+    const int mode = desc->mode;
+    if (!kind_runs(KIND, mode)) return;  // not selected: exit before touching anything
+    const int sA = desc->sA, sB = desc->sB;
+
+    extern __shared__ uint8_t smem_raw[];
+    TcSmem &S = *reinterpret_cast<TcSmem *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    volatile int *abort_flag = &S.abort;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&S.full[s], 1);
+            mbar_init(&S.empty[s], 1);
+        }
+        mbar_init(&S.acc0_full, 1);
+        mbar_init(&S.acc0_empty, kEpiWarps);
+        mbar_init(&S.drain, 1);
+        S.abort = 0;
+        fence_barrier_init();
+        tma_prefetch_desc(&mapA);
+        tma_prefetch_desc(&mapB);
+    }
+    if (warp == 1) {
+        tmem_alloc(&S.tmem_base, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+
+    const int tiles_m = (m + kBM - 1) / kBM;
+    const int tiles_n = (n + kBN - 1) / kBN;
+    const int num_tiles = tiles_m * tiles_n;
+    constexpr int kElemBytes = (KIND == 1) ? 4 : 2;
+    constexpr int kKPerStage = kRowBytes / kElemBytes;  // 32 (16-bit) or 16 (TF32)
+    const int num_kb = k_pad / kKPerStage;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                int tm, tn;
+                tile_coords(t, tiles_m, tiles_n, tm, tn);
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!mbar_wait(&S.empty[stage], phase ^ 1u, globaltimer_ns() + kWaitBudgetNs,
+                                   abort_flag)) {
+                        if (!*abort_flag) raise_abort(S, d_err, kErrTimeoutProducer);
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&S.full[stage], kStageBytes);
+                    tma_load_3d(S.stage[stage], &mapA, &S.full[stage], kb * kKPerStage, tm * kBM, 0);
+                    tma_load_3d(S.stage[stage] + kOperandStageBytes, &mapB, &S.full[stage],
+                                kb * kKPerStage, tn * kBN, 0);
+                    ++issued;
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // Give the copies already in flight a bounded chance to land
+                // before this CTA's shared memory goes away.
+                int st = stage;
+                uint32_t ph = phase;
+                for (int i = 0; i < kStages && i < issued; ++i) {
+                    st = (st + kStages - 1) % kStages;
+                    if (st == kStages - 1) ph ^= 1u;
+                    volatile int never = 0;
+                    (void)mbar_wait(&S.full[st], ph, globaltimer_ns() + 100000000ull, &never);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            constexpr uint32_t fmt = (KIND == 0) ? 0u : (KIND == 1 ? 2u : 1u);
+            constexpr uint32_t id = idesc_make(fmt, kBM, kBN, 0);
+            constexpr uint32_t idn = idesc_make(fmt, kBM, kBN, 1);  // negated A
+            const uint32_t a0r = tmem, a0i = tmem + 128, a1r = tmem + 256, a1i = tmem + 384;
+            int stage = 0;
+            uint32_t phase = 0, e_phase = 0;
+            bool pending = false;  // an acc0 drain the epilogue has not yet confirmed
+            bool ok = true;
+            auto wait_drained = [&]() -> bool {
+                if (!pending) return true;
+                if (!mbar_wait(&S.acc0_empty, e_phase, globaltimer_ns() + kWaitBudgetNs,
+                               abort_flag))
+                    return false;
+                e_phase ^= 1u;
+                pending = false;
+                tc_fence_after();
+                return true;
+            };
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!mbar_wait(&S.full[stage], phase, globaltimer_ns() + kWaitBudgetNs,
+                                   abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    // acc1 is read by the epilogue at the end of the previous
+                    // tile: wait for that before overwriting it.
+                    if (kb == 0 && !wait_drained()) {
+                        ok = false;
+                        break;
+                    }
+                    // Descriptors differ only in the start-address field (bits 0..13,
+                    // address >> 4), which never carries out for shared memory.
+                    const uint64_t dA = sdesc_kmajor_sw64(smem_u32(S.stage[stage]));
+                    const uint64_t dB = dA + (kOperandStageBytes >> 4);
+#define A_(ks, p) (dA + (uint64_t)(((p) * kTileBytes + (ks) * 32) >> 4))
+#define B_(ks, p) (dB + (uint64_t)(((p) * kTileBytes + (ks) * 32) >> 4))
+                    // correction products: acc1 += lo*hi + hi*lo (planes 0/1 hi.re/im, 2/3 lo.re/im)
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;
+                        mma<KIND>(a1r, A_(ks, 2), B_(ks, 0), id, first);   //  Ar_lo Br_hi
+                        mma<KIND>(a1i, A_(ks, 2), B_(ks, 1), id, first);   //  Ar_lo Bi_hi
+                        mma<KIND>(a1r, A_(ks, 3), B_(ks, 1), idn, 1u);     // -Ai_lo Bi_hi
+                        mma<KIND>(a1i, A_(ks, 3), B_(ks, 0), id, 1u);      //  Ai_lo Br_hi
+                        mma<KIND>(a1r, A_(ks, 0), B_(ks, 2), id, 1u);      //  Ar_hi Br_lo
+                        mma<KIND>(a1i, A_(ks, 0), B_(ks, 3), id, 1u);      //  Ar_hi Bi_lo
+                        mma<KIND>(a1r, A_(ks, 1), B_(ks, 3), idn, 1u);     // -Ai_hi Bi_lo
+                        mma<KIND>(a1i, A_(ks, 1), B_(ks, 2), id, 1u);      //  Ai_hi Br_lo
+                    }
+                    // hi*hi products into a fresh acc0, once the last one was drained
+                    if (!wait_drained()) {
+                        ok = false;
+                        break;
+                    }
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint32_t first = (ks == 0) ? 0u : 1u;
+                        mma<KIND>(a0r, A_(ks, 0), B_(ks, 0), id, first);   //  Ar_hi Br_hi
+                        mma<KIND>(a0i, A_(ks, 0), B_(ks, 1), id, first);   //  Ar_hi Bi_hi
+                        mma<KIND>(a0r, A_(ks, 1), B_(ks, 1), idn, 1u);     // -Ai_hi Bi_hi
+                        mma<KIND>(a0i, A_(ks, 1), B_(ks, 0), id, 1u);      //  Ai_hi Br_hi
+                    }
+#undef A_
+#undef B_
+                    tc_commit(&S.empty[stage]);  // frees the smem stage when these MMAs finish
+                    tc_commit(&S.acc0_full);     // acc0 (and, on a tile's last stage, acc1) ready
+                    pending = true;
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok && !*abort_flag) raise_abort(S, d_err, kErrTimeoutMma);
+            // Wait (bounded) until every MMA this thread issued has finished,
+            // so tensor memory is idle before it is released.
+            tc_commit(&S.drain);
+            volatile int never = 0;
+            (void)mbar_wait(&S.drain, 0, globaltimer_ns() + kWaitBudgetNs, &never);
+        }
+    } else {
+        // ---------------- epilogue (warps 2..9) ----------------
+        const int q = warp & 3;                         // lane quadrant this warp may access
+        const int half = (warp - 2) >> 2;               // which 64 of the 128 columns
+        const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16) + half * kEpiCols;
+        const float unA = ldexpf(1.0f, -sA);
+        const float unB = ldexpf(1.0f, -sB);
+        const bool use_beta = (beta.x != 0.0f) || (beta.y != 0.0f);
+        uint32_t f_phase = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+            int tm, tn;
+            tile_coords(t, tiles_m, tiles_n, tm, tn);
+            float racc[kEpiCols], iacc[kEpiCols];
+#pragma unroll
+            for (int j = 0; j < kEpiCols; ++j) racc[j] = iacc[j] = 0.0f;
+            for (int kb = 0; kb < num_kb; ++kb) {
+                int got = 0;
+                if (lane == 0)
+                    got = mbar_wait(&S.acc0_full, f_phase, globaltimer_ns() + kWaitBudgetNs,
+                                    abort_flag)
+                              ? 1
+                              : 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    if (lane == 0 && !*abort_flag) raise_abort(S, d_err, kErrTimeoutEpilogue);
+                    ok = false;
+                    break;
+                }
+                f_phase ^= 1u;
+                tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < kEpiCols; c += 16) {
+                    uint32_t vr[16], vi[16];
+                    tmem_ld16(trow + 0 + c, vr);
+                    tmem_ld16(trow + 128 + c, vi);
+                    tmem_ld_wait(vr);
+                    tmem_ld_wait(vi);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        racc[c + j] += __uint_as_float(vr[j]);  // round-to-nearest FP32 adds
+                        iacc[c + j] += __uint_as_float(vi[j]);
+                    }
+                }
+                if (kb == num_kb - 1) {
+#pragma unroll
+                    for (int c = 0; c < kEpiCols; c += 16) {
+                        uint32_t vr[16], vi[16];
+                        tmem_ld16(trow + 256 + c, vr);
+                        tmem_ld16(trow + 384 + c, vi);
+                        tmem_ld_wait(vr);
+                        tmem_ld_wait(vi);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            racc[c + j] = fmaf(__uint_as_float(vr[j]), 0x1p-11f, racc[c + j]);
+                            iacc[c + j] = fmaf(__uint_as_float(vi[j]), 0x1p-11f, iacc[c + j]);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S.acc0_empty);
+            }
+            if (!ok) break;
+            const int row = tm * kBM + q * 32 + lane;
+            if (row < m) {
+                float2 *crow = C + row;
+                const int col0 = tn * kBN + half * kEpiCols;
+#pragma unroll
+                for (int j = 0; j < kEpiCols; ++j) {
+                    const int col = col0 + j;
+                    if (col < n) {
+                        const float pr = (racc[j] * unA) * unB;
+                        const float pi = (iacc[j] * unA) * unB;
+                        float2 o;
+                        o.x = alpha.x * pr - alpha.y * pi;
+                        o.y = alpha.x * pi + alpha.y * pr;
+                        float2 *dst = crow + static_cast<int64_t>(col) * ldc;
+                        if (use_beta) {
+                            const float2 c = *dst;
+                            o.x += beta.x * c.x - beta.y * c.y;
+                            o.y += beta.x * c.y + beta.y * c.x;
+                        }
+                        *dst = o;
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        __syncwarp();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+template <int KIND>
+cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
+                        const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad, float2 alpha,
+                        float2 beta, float2 *C, int64_t ldc, int *d_err, int num_sms,
+                        cudaStream_t s) {
+    const size_t smem = sizeof(TcSmem) + 1024;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel<KIND>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int64_t tiles = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
+    if (tiles == 0 || k_pad == 0) return cudaSuccess;
+    const int grid = static_cast<int>(tiles < num_sms ? tiles : num_sms);
+    cgemm_tc_kernel<KIND><<<grid, kTcThreads, smem, s>>>(*mapA, *mapB, desc, (int)m, (int)n,
+                                                         (int)k_pad, alpha, beta, C, ldc, d_err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_cgemm_tc(int kind, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
+                            const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad,
+                            float2 alpha, float2 beta, float2 *C, int64_t ldc, int *d_err,
+                            int num_sms, cudaStream_t s) {
+    switch (kind) {
+        case 0:
+            return launch_kind<0>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
+                                  num_sms, s);
+        case 1:
+            return launch_kind<1>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
+                                  num_sms, s);
+        default:
+            return launch_kind<2>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
+                                  num_sms, s);
+    }
+}
+
+}  // namespace qcs

@@ -1,0 +1,118 @@
+// Internal declarations shared by the translation units of libqcs.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/qcs.h"
+
+namespace qcs {
+
+// Error word codes written by kernels into the handle's device error word.
+enum : int {
+    kErrNone = 0,
+    kErrTimeoutProducer = 1,
+    kErrTimeoutMma = 2,
+    kErrTimeoutEpilogue = 3,
+};
+
+// Wait budget of a device-side bounded wait (nanoseconds).  No legitimate
+// wait inside one launch comes near it.
+constexpr uint64_t kWaitBudgetNs = 2000000000ull;
+
+// Tile geometry of the tensor-core GEMM.
+constexpr int kBM = 128;          // complex rows of C per tile (TMEM lanes)
+constexpr int kBN = 128;          // complex columns of C per tile
+constexpr int kRowBytes = 64;     // K bytes of one smem operand row per stage
+constexpr int kStages = 3;
+constexpr int kPlanes = 4;        // hi.re, hi.im, lo.re, lo.im
+constexpr int kTileBytes = kBM * kRowBytes;                // one plane tile: 8 KB
+constexpr int kOperandStageBytes = kPlanes * kTileBytes;   // 32 KB
+constexpr int kStageBytes = 2 * kOperandStageBytes;        // A + B: 64 KB
+constexpr int kTcThreads = 320;   // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int kTmemCols = 512;    // acc0.re, acc0.im, acc1.re, acc1.im x 128 columns
+
+// Stats grid: blocks x threads, per-block partial histograms of 257 int64
+// (256 bins + zero count).
+constexpr int kStatsThreads = 128;
+constexpr int kPartialStride = 257;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct Workspace {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace qcs
+
+struct qcs_handle_s {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    double tol = 0.0;
+    int size_rule = 1;
+    int *d_err = nullptr;            // device error word
+    qcs::Workspace ws;               // GEMM workspace (planes, partials, descriptor)
+    qcs::Workspace tree_ws;          // contraction-tree intermediates
+    qcs::EncodeTiledFn encode = nullptr;
+};
+
+namespace qcs {
+
+int ensure_workspace(Workspace &w, size_t bytes);
+
+// ---- launchers (kernels.cu) ----------------------------------------------
+// Exponent statistics of ``count_cols`` columns of ``rows`` complex values
+// (leading dim ld) into per-block partials.  Two matrices in one launch:
+// blocks [0, gA) take X0, [gA, gA+gB) take X1.
+cudaError_t launch_stats2(const float2 *X0, int64_t rows0, int64_t cols0, int64_t ld0, int gA,
+                          const float2 *X1, int64_t rows1, int64_t cols1, int64_t ld1, int gB,
+                          int64_t *partials, cudaStream_t s);
+// Reduce partials into qcs_stats_t (optional) and select the mode.
+cudaError_t launch_select(const int64_t *partials, int gA, int gB, int64_t nA, int64_t nB,
+                          double tol, int forced_mode, qcs_stats_t *statsA, qcs_stats_t *statsB,
+                          qcs_gemm_desc_t *desc, cudaStream_t s);
+// Select from two finished qcs_stats_t.
+cudaError_t launch_select_from_stats(const qcs_stats_t *a, const qcs_stats_t *b, double tol,
+                                     qcs_gemm_desc_t *desc, cudaStream_t s);
+// Write a constant descriptor (forced mode).
+cudaError_t launch_set_desc(qcs_gemm_desc_t *desc, int mode, cudaStream_t s);
+
+// Split op(X) into 4 planes (R x K, row pitch ``pitch`` elements, planes
+// ``plane_stride`` elements apart); rows >= R or columns >= K up to
+// R_pad x K_pad are zero-filled.  (sr, sc): element strides of X for a step
+// in r and in c; conj: negate imaginary parts.
+cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
+                         int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
+                         void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s);
+
+cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
+                           const float2 *in, float2 *out, int64_t *stats_partials, int gstats,
+                           cudaStream_t s);
+cudaError_t launch_stats_finalize(const int64_t *partials, int g, int64_t n, qcs_stats_t *out,
+                                  cudaStream_t s);
+cudaError_t launch_accumulate_c128(const float2 *src, double *dst, int64_t count, int overwrite,
+                                   cudaStream_t s);
+
+// ---- GEMM launchers -------------------------------------------------------
+// Plain FP32 SIMT CGEMM (runs only when desc->mode == FP32, or always when
+// desc is NULL).
+cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int64_t m,
+                              int64_t n, int64_t k, float2 alpha, const float2 *A, int64_t lda,
+                              const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc,
+                              cudaStream_t s);
+// Tensor-core emulated CGEMM over split planes.  ``kind``: 0 FP16 (modes
+// FP16X, FP16X_SCALED), 1 TF32, 2 BF16; the kernel returns at once unless
+// desc->mode belongs to its kind.
+cudaError_t launch_cgemm_tc(int kind, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
+                            const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad,
+                            float2 alpha, float2 beta, float2 *C, int64_t ldc, int *d_err,
+                            int num_sms, cudaStream_t s);
+
+}  // namespace qcs

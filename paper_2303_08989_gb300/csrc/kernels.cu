@@ -1,0 +1,715 @@
+// Memory-bound kernels of the emulated-CGEMM path and the plain FP32 CGEMM.
+//
+//   stats2_kernel     exponent statistics (Section 4.1) of one or two
+//                     matrices in one HBM pass: a histogram of biased
+//                     exponents over every real and imaginary scalar,
+//                     counted in lane-private shared-memory bins (no bank
+//                     conflicts, no contended atomics).
+//   select_kernel     the mode-selection rule of Section 4.1 on the device
+//                     (the statistics never go to the host, Section 4.2).
+//   split_kernel      Eq. 1 of Section 2.1 after the power-of-two scaling of
+//                     Section 4.2: op(X) -> four planes hi.re, hi.im, lo.re,
+//                     lo.im in the K-contiguous layout the tensor-core kernel
+//                     loads with TMA (transposing through shared memory when
+//                     the source is contiguous along the other index).
+//   permute_kernel    strided gather of a tensor (TTGT reshaping, slicing).
+//   cgemm_simt_kernel plain FP32 complex GEMM on the CUDA cores (the FP32
+//                     baseline and mode).
+//   cgemm_skinny_kernel  bandwidth-bound CGEMM for very small m, n or k
+//                     (Section 5.3.2 irregular shapes).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.h"
+
+namespace qcs {
+
+// ===========================================================================
+// Exponent statistics
+// ===========================================================================
+
+namespace {
+
+constexpr int kStatsWarps = kStatsThreads / 32;
+constexpr size_t kStatsSmem = size_t(kStatsWarps) * 256 * 32 * sizeof(uint32_t);  // 128 KB
+
+__device__ __forceinline__ void count_scalar(uint32_t *h, int lane, float x, uint32_t &nz) {
+    const uint32_t u = __float_as_uint(x);
+    if ((u & 0x7FFFFFFFu) == 0u) {
+        ++nz;
+    } else {
+        atomicAdd(&h[((u >> 23) & 0xFFu) * 32u + lane], 1u);
+    }
+}
+
+__global__ void __launch_bounds__(kStatsThreads) stats2_kernel(
+    const float2 *__restrict__ X0, int64_t rows0, int64_t cols0, int64_t ld0, int gA,
+    const float2 *__restrict__ X1, int64_t rows1, int64_t cols1, int64_t ld1, int gB,
+    int64_t *__restrict__ partials) {
+    extern __shared__ uint32_t hist[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < kStatsWarps * 256 * 32; i += kStatsThreads) hist[i] = 0u;
+    __syncthreads();
+    uint32_t *h = hist + warp * 256 * 32;
+
+    const bool first = blockIdx.x < gA;
+    const float2 *X = first ? X0 : X1;
+    const int64_t rows = first ? rows0 : rows1, cols = first ? cols0 : cols1;
+    const int64_t ld = first ? ld0 : ld1;
+    const int64_t blk = first ? blockIdx.x : blockIdx.x - gA;
+    const int64_t nblk = first ? gA : gB;
+    uint32_t nz = 0;
+
+    const int64_t nel = rows * cols;  // complex elements
+    if (nel > 0) {
+        const int64_t gtid = blk * kStatsThreads + tid;
+        const int64_t gstride = nblk * kStatsThreads;
+        if (ld == rows && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
+            // contiguous: two complex values per 16-byte load, 8 loads in flight
+            const float4 *p = reinterpret_cast<const float4 *>(X);
+            const int64_t n4 = nel >> 1;
+            constexpr int U = 8;
+            int64_t i = gtid;
+            for (; i + (U - 1) * gstride < n4; i += U * gstride) {
+                float4 v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) v[u] = __ldcs(p + i + u * gstride);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    count_scalar(h, lane, v[u].x, nz);
+                    count_scalar(h, lane, v[u].y, nz);
+                    count_scalar(h, lane, v[u].z, nz);
+                    count_scalar(h, lane, v[u].w, nz);
+                }
+            }
+            for (; i < n4; i += gstride) {
+                const float4 v = __ldcs(p + i);
+                count_scalar(h, lane, v.x, nz);
+                count_scalar(h, lane, v.y, nz);
+                count_scalar(h, lane, v.z, nz);
+                count_scalar(h, lane, v.w, nz);
+            }
+            if ((nel & 1) && gtid == 0) {
+                const float2 v = X[nel - 1];
+                count_scalar(h, lane, v.x, nz);
+                count_scalar(h, lane, v.y, nz);
+            }
+        } else {
+            for (int64_t i = gtid; i < nel; i += gstride) {
+                const int64_t c = i / rows, r = i - c * rows;
+                const float2 v = X[r + c * ld];
+                count_scalar(h, lane, v.x, nz);
+                count_scalar(h, lane, v.y, nz);
+            }
+        }
+    }
+    __syncthreads();
+    int64_t *out = partials + static_cast<int64_t>(blockIdx.x) * kPartialStride;
+    for (int bin = tid; bin < 256; bin += kStatsThreads) {
+        uint64_t s = 0;
+        for (int w = 0; w < kStatsWarps; ++w)
+            for (int l = 0; l < 32; ++l) {
+                const int ll = (l + tid) & 31;  // rotate lanes: conflict-free reads
+                s += hist[(w * 256 + bin) * 32 + ll];
+            }
+        out[bin] = static_cast<int64_t>(s);
+    }
+    // zero count: block reduction
+    __shared__ uint32_t zsum[kStatsWarps];
+    uint32_t z = nz;
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+    if (lane == 0) zsum[warp] = z;
+    __syncthreads();
+    if (tid == 0) {
+        uint64_t t = 0;
+        for (int w = 0; w < kStatsWarps; ++w) t += zsum[w];
+        out[256] = static_cast<int64_t>(t);
+    }
+}
+
+// Section 4.1 readings: zeros enter no count; "larger than the minimum value
+// of FP16" is e >= -14; the scaled window is [e_max - 28, e_max]; binary32
+// subnormals (bin 0) count as outside both windows.
+struct Summary {
+    int64_t nnz, nonfinite, under1, under2;
+    int bmax;  // highest finite bin in use, -1 if none
+};
+
+__device__ Summary summarize(const int64_t *h) {
+    Summary s;
+    s.nonfinite = h[255];
+    s.nnz = 0;
+    s.bmax = -1;
+    s.under1 = 0;
+    for (int b = 0; b < 255; ++b) {
+        s.nnz += h[b];
+        if (h[b] > 0) s.bmax = b;
+        if (b < 127 - 14) s.under1 += h[b];
+    }
+    s.under2 = h[0];
+    for (int b = 1; b < s.bmax - 28; ++b) s.under2 += h[b];
+    return s;
+}
+
+__device__ void select_rule(const Summary &a, const Summary &b, double tol, int forced,
+                            qcs_gemm_desc_t *desc) {
+    auto ok1 = [&](const Summary &s) {
+        return s.bmax < 0 || (s.bmax - 127 <= 14 && (double)s.under1 <= tol * (double)s.nnz);
+    };
+    auto ok2 = [&](const Summary &s) { return (double)s.under2 <= tol * (double)s.nnz; };
+    auto scale = [&](const Summary &s) { return s.bmax < 0 ? 0 : 14 - (s.bmax - 127); };
+    int mode;
+    int sA = 0, sB = 0;
+    if (forced == QCS_MODE_FP16X_SCALED) {
+        mode = QCS_MODE_FP16X_SCALED;
+        sA = scale(a);
+        sB = scale(b);
+    } else if (a.nonfinite > 0 || b.nonfinite > 0 || a.bmax >= 254 || b.bmax >= 254) {
+        mode = QCS_MODE_FP32;
+    } else if (!ok2(a) || !ok2(b)) {
+        mode = QCS_MODE_TF32X;
+    } else if (!ok1(a) || !ok1(b)) {
+        mode = QCS_MODE_FP16X_SCALED;
+        sA = scale(a);
+        sB = scale(b);
+    } else {
+        mode = QCS_MODE_FP16X;
+    }
+    desc->mode = mode;
+    desc->sA = sA;
+    desc->sB = sB;
+    desc->reserved = 0;
+}
+
+__global__ void __launch_bounds__(256) select_kernel(const int64_t *__restrict__ partials, int gA,
+                                                     int gB, int64_t nA, int64_t nB, double tol,
+                                                     int forced, qcs_stats_t *statsA,
+                                                     qcs_stats_t *statsB, qcs_gemm_desc_t *desc) {
+    __shared__ int64_t hA[257], hB[257];
+    for (int bin = threadIdx.x; bin < 257; bin += blockDim.x) {
+        int64_t sa = 0, sb = 0;
+        for (int b = 0; b < gA; ++b) sa += partials[(int64_t)b * kPartialStride + bin];
+        for (int b = 0; b < gB; ++b) sb += partials[(int64_t)(gA + b) * kPartialStride + bin];
+        hA[bin] = sa;
+        hB[bin] = sb;
+    }
+    __syncthreads();
+    for (int bin = threadIdx.x; bin < 256; bin += blockDim.x) {
+        if (statsA) statsA->hist[bin] = hA[bin];
+        if (statsB) statsB->hist[bin] = hB[bin];
+    }
+    if (threadIdx.x == 0) {
+        if (statsA) {
+            statsA->n_zero = hA[256];
+            statsA->n = nA;
+        }
+        if (statsB) {
+            statsB->n_zero = hB[256];
+            statsB->n = nB;
+        }
+        if (desc) select_rule(summarize(hA), summarize(hB), tol, forced, desc);
+    }
+}
+
+__global__ void select_from_stats_kernel(const qcs_stats_t *a, const qcs_stats_t *b, double tol,
+                                         qcs_gemm_desc_t *desc) {
+    __shared__ int64_t hA[256], hB[256];
+    for (int bin = threadIdx.x; bin < 256; bin += blockDim.x) {
+        hA[bin] = a->hist[bin];
+        hB[bin] = b->hist[bin];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) select_rule(summarize(hA), summarize(hB), tol, QCS_MODE_AUTO, desc);
+}
+
+__global__ void set_desc_kernel(qcs_gemm_desc_t *desc, int mode) {
+    desc->mode = mode;
+    desc->sA = 0;
+    desc->sB = 0;
+    desc->reserved = 0;
+}
+
+__global__ void stats_finalize_kernel(const int64_t *__restrict__ partials, int g, int64_t n,
+                                      qcs_stats_t *out) {
+    for (int bin = threadIdx.x; bin < 257; bin += blockDim.x) {
+        int64_t s = 0;
+        for (int b = 0; b < g; ++b) s += partials[(int64_t)b * kPartialStride + bin];
+        if (bin < 256)
+            out->hist[bin] = s;
+        else
+            out->n_zero = s;
+    }
+    if (threadIdx.x == 0) out->n = n;
+}
+
+}  // namespace
+
+static bool g_stats_configured = false;
+
+cudaError_t launch_stats2(const float2 *X0, int64_t rows0, int64_t cols0, int64_t ld0, int gA,
+                          const float2 *X1, int64_t rows1, int64_t cols1, int64_t ld1, int gB,
+                          int64_t *partials, cudaStream_t s) {
+    if (!g_stats_configured) {
+        cudaError_t e = cudaFuncSetAttribute(stats2_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kStatsSmem);
+        if (e != cudaSuccess) return e;
+        g_stats_configured = true;
+    }
+    stats2_kernel<<<gA + gB, kStatsThreads, kStatsSmem, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1,
+                                                            cols1, ld1, gB, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select(const int64_t *partials, int gA, int gB, int64_t nA, int64_t nB,
+                          double tol, int forced_mode, qcs_stats_t *statsA, qcs_stats_t *statsB,
+                          qcs_gemm_desc_t *desc, cudaStream_t s) {
+    select_kernel<<<1, 256, 0, s>>>(partials, gA, gB, nA, nB, tol, forced_mode, statsA, statsB,
+                                    desc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_from_stats(const qcs_stats_t *a, const qcs_stats_t *b, double tol,
+                                     qcs_gemm_desc_t *desc, cudaStream_t s) {
+    select_from_stats_kernel<<<1, 256, 0, s>>>(a, b, tol, desc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_desc(qcs_gemm_desc_t *desc, int mode, cudaStream_t s) {
+    set_desc_kernel<<<1, 1, 0, s>>>(desc, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_finalize(const int64_t *partials, int g, int64_t n, qcs_stats_t *out,
+                                  cudaStream_t s) {
+    stats_finalize_kernel<<<1, 256, 0, s>>>(partials, g, n, out);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Split (Eq. 1) into tensor-core planes
+// ===========================================================================
+
+namespace {
+
+constexpr int kSplitR = 32, kSplitC = 64;
+
+__device__ __forceinline__ uint32_t tf32_rn(float x) {
+    uint32_t r;
+    asm("cvt.rn.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r & 0xFFFFE000u;
+}
+
+__global__ void __launch_bounds__(256) split_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int which, const float2 *__restrict__ X, int64_t sr,
+    int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad, void *planes,
+    int64_t pitch, int64_t plane_stride) {
+    const int mode = desc->mode;
+    if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
+    const int s = (mode == QCS_MODE_FP16X_SCALED) ? (which == 0 ? desc->sA : desc->sB) : 0;
+
+    __shared__ float2 tile[kSplitR][kSplitC + 1];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.y) * kSplitR;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kSplitC;
+    if (sc == 1) {
+#pragma unroll
+        for (int i = 0; i < kSplitR / 8; ++i) {
+            const int rr = warp + 8 * i;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int cc = lane + 32 * h;
+                float2 v = make_float2(0.f, 0.f);
+                if (r0 + rr < R && c0 + cc < K) v = X[(r0 + rr) * sr + (c0 + cc)];
+                tile[rr][cc] = v;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kSplitC / 8; ++i) {
+            const int cc = warp + 8 * i;
+            const int rr = lane;
+            float2 v = make_float2(0.f, 0.f);
+            if (r0 + rr < R && c0 + cc < K) v = X[(r0 + rr) * sr + (c0 + cc) * sc];
+            tile[rr][cc] = v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kSplitR / 8; ++i) {
+        const int rr = warp + 8 * i;
+        const int64_t r = r0 + rr;
+        const int cc = 2 * lane;
+        const int64_t c = c0 + cc;
+        if (r >= R_pad || c >= K_pad) continue;
+        float x[4];
+        x[0] = tile[rr][cc].x;
+        x[1] = conj ? -tile[rr][cc].y : tile[rr][cc].y;
+        x[2] = tile[rr][cc + 1].x;
+        x[3] = conj ? -tile[rr][cc + 1].y : tile[rr][cc + 1].y;
+        // hi/lo of re and im for columns c and c+1
+        uint32_t hib[4], lob[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float xs = (s != 0) ? ldexpf(x[e], s) : x[e];
+            if (mode == QCS_MODE_TF32X) {
+                const uint32_t h = tf32_rn(xs);
+                const float rres = xs - __uint_as_float(h);
+                hib[e] = h;
+                lob[e] = tf32_rn(rres * 2048.0f);
+            } else if (mode == QCS_MODE_BF16X3) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(xs);
+                const float rres = xs - __bfloat162float(h);
+                hib[e] = __bfloat16_as_ushort(h);
+                lob[e] = __bfloat16_as_ushort(__float2bfloat16_rn(rres * 2048.0f));
+            } else {
+                const __half h = __float2half_rn(xs);
+                const float rres = xs - __half2float(h);
+                hib[e] = __half_as_ushort(h);
+                lob[e] = __half_as_ushort(__float2half_rn(rres * 2048.0f));
+            }
+        }
+        const bool two = (c + 1 < K_pad);
+        if (mode == QCS_MODE_TF32X) {
+            uint32_t *P = static_cast<uint32_t *>(planes);
+            uint32_t *p0 = P + r * pitch + c;
+            // plane order: hi.re, hi.im, lo.re, lo.im; x[0]/x[2] real, x[1]/x[3] imaginary
+            if (two && ((reinterpret_cast<uintptr_t>(p0) & 7u) == 0)) {
+                *reinterpret_cast<uint2 *>(p0) = make_uint2(hib[0], hib[2]);
+                *reinterpret_cast<uint2 *>(p0 + plane_stride) = make_uint2(hib[1], hib[3]);
+                *reinterpret_cast<uint2 *>(p0 + 2 * plane_stride) = make_uint2(lob[0], lob[2]);
+                *reinterpret_cast<uint2 *>(p0 + 3 * plane_stride) = make_uint2(lob[1], lob[3]);
+            } else {
+                p0[0] = hib[0];
+                p0[plane_stride] = hib[1];
+                p0[2 * plane_stride] = lob[0];
+                p0[3 * plane_stride] = lob[1];
+                if (two) {
+                    p0[1] = hib[2];
+                    p0[plane_stride + 1] = hib[3];
+                    p0[2 * plane_stride + 1] = lob[2];
+                    p0[3 * plane_stride + 1] = lob[3];
+                }
+            }
+        } else {
+            uint16_t *P = static_cast<uint16_t *>(planes);
+            uint16_t *p0 = P + r * pitch + c;
+            if (two && ((reinterpret_cast<uintptr_t>(p0) & 3u) == 0)) {
+                *reinterpret_cast<uint32_t *>(p0) = hib[0] | (hib[2] << 16);
+                *reinterpret_cast<uint32_t *>(p0 + plane_stride) = hib[1] | (hib[3] << 16);
+                *reinterpret_cast<uint32_t *>(p0 + 2 * plane_stride) = lob[0] | (lob[2] << 16);
+                *reinterpret_cast<uint32_t *>(p0 + 3 * plane_stride) = lob[1] | (lob[3] << 16);
+            } else {
+                p0[0] = (uint16_t)hib[0];
+                p0[plane_stride] = (uint16_t)hib[1];
+                p0[2 * plane_stride] = (uint16_t)lob[0];
+                p0[3 * plane_stride] = (uint16_t)lob[1];
+                if (two) {
+                    p0[1] = (uint16_t)hib[2];
+                    p0[plane_stride + 1] = (uint16_t)hib[3];
+                    p0[2 * plane_stride + 1] = (uint16_t)lob[2];
+                    p0[3 * plane_stride + 1] = (uint16_t)lob[3];
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
+                         int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
+                         void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s) {
+    if (R_pad <= 0 || K_pad <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((K_pad + kSplitC - 1) / kSplitC), (unsigned)((R_pad + kSplitR - 1) / kSplitR));
+    if (grid.y > 65535u) return cudaErrorInvalidValue;
+    split_kernel<<<grid, 256, 0, s>>>(desc, which, X, sr, sc, conj, R, K, R_pad, K_pad, planes,
+                                      pitch, plane_stride);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Permute / gather, FP64 accumulation
+// ===========================================================================
+
+namespace {
+
+struct PermParams {
+    int rank;
+    int64_t dims[24];
+    int64_t strides[24];
+};
+
+__global__ void permute_kernel(PermParams P, int64_t total, int64_t offset,
+                               const float2 *__restrict__ in, float2 *__restrict__ out) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        int64_t rem = o, src = offset;
+        for (int d = 0; d < P.rank; ++d) {
+            const int64_t q = rem / P.dims[d];
+            src += (rem - q * P.dims[d]) * P.strides[d];
+            rem = q;
+        }
+        out[o] = in[src];
+    }
+}
+
+__global__ void accumulate_c128_kernel(const float2 *__restrict__ src, double2 *__restrict__ dst,
+                                       int64_t count, int overwrite) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = src[i];
+        double2 d = overwrite ? make_double2(0.0, 0.0) : dst[i];
+        d.x += (double)v.x;
+        d.y += (double)v.y;
+        dst[i] = d;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
+                           const float2 *in, float2 *out, int64_t *stats_partials, int gstats,
+                           cudaStream_t s) {
+    (void)stats_partials;
+    (void)gstats;
+    PermParams P;
+    P.rank = rank;
+    int64_t total = 1;
+    for (int d = 0; d < rank; ++d) {
+        P.dims[d] = dims[d];
+        P.strides[d] = strides[d];
+        total *= dims[d];
+    }
+    if (total == 0) return cudaSuccess;
+    const int64_t blocks = (total + 255) / 256;
+    permute_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, s>>>(P, total, offset, in,
+                                                                             out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate_c128(const float2 *src, double *dst, int64_t count, int overwrite,
+                                   cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    const int64_t blocks = (count + 255) / 256;
+    accumulate_c128_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, s>>>(
+        src, reinterpret_cast<double2 *>(dst), count, overwrite);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Plain FP32 CGEMM on the CUDA cores
+// ===========================================================================
+
+namespace {
+
+constexpr int kSBM = 128, kSBN = 64, kSBK = 8;  // complex tile; 256 threads, 8 x 4 per thread
+constexpr int kSPadA = 2, kSPadB = 2;
+
+__device__ __forceinline__ float2 ld_op(const float2 *X, int op, int64_t r, int64_t c, int64_t ld) {
+    float2 v = (op == QCS_OP_N) ? X[r + c * ld] : X[c + r * ld];
+    if (op == QCS_OP_C) v.y = -v.y;
+    return v;
+}
+
+__global__ void __launch_bounds__(256) cgemm_simt_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int m, int n, int k, float2 alpha,
+    const float2 *__restrict__ A, int64_t lda, const float2 *__restrict__ B, int64_t ldb,
+    float2 beta, float2 *__restrict__ C, int64_t ldc) {
+    if (desc && desc->mode != QCS_MODE_FP32) return;
+    __shared__ __align__(16) float2 As[2][kSBK][kSBM + kSPadA];
+    __shared__ __align__(16) float2 Bs[2][kSBK][kSBN + kSPadB];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t bm = static_cast<int64_t>(blockIdx.y) * kSBM;
+    const int64_t bn = static_cast<int64_t>(blockIdx.x) * kSBN;
+
+    float2 acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+    float2 ra[4], rb[2];
+    auto load_global = [&](int kt) {
+        const int64_t k0 = static_cast<int64_t>(kt) * kSBK;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int idx = tid + 256 * q;
+            int i, l;
+            if (opA == QCS_OP_N) {
+                i = idx % kSBM;
+                l = idx / kSBM;
+            } else {
+                l = idx % kSBK;
+                i = idx / kSBK;
+            }
+            const int64_t gi = bm + i, gl = k0 + l;
+            ra[q] = (gi < m && gl < k) ? ld_op(A, opA, gi, gl, lda) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int idx = tid + 256 * q;
+            int l, j;
+            if (opB == QCS_OP_N) {
+                l = idx % kSBK;
+                j = idx / kSBK;
+            } else {
+                j = idx % kSBN;
+                l = idx / kSBN;
+            }
+            const int64_t gl = k0 + l, gj = bn + j;
+            rb[q] = (gl < k && gj < n) ? ld_op(B, opB, gl, gj, ldb) : make_float2(0.f, 0.f);
+        }
+    };
+    auto store_shared = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int idx = tid + 256 * q;
+            int i, l;
+            if (opA == QCS_OP_N) {
+                i = idx % kSBM;
+                l = idx / kSBM;
+            } else {
+                l = idx % kSBK;
+                i = idx / kSBK;
+            }
+            As[buf][l][i] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int idx = tid + 256 * q;
+            int l, j;
+            if (opB == QCS_OP_N) {
+                l = idx % kSBK;
+                j = idx / kSBK;
+            } else {
+                j = idx % kSBN;
+                l = idx / kSBN;
+            }
+            Bs[buf][l][j] = rb[q];
+        }
+    };
+
+    const int ktiles = (k + kSBK - 1) / kSBK;
+    if (ktiles > 0) {
+        load_global(0);
+        store_shared(0);
+        __syncthreads();
+    }
+    for (int kt = 0; kt < ktiles; ++kt) {
+        const int buf = kt & 1;
+        if (kt + 1 < ktiles) load_global(kt + 1);
+#pragma unroll
+        for (int l = 0; l < kSBK; ++l) {
+            float2 a[8], b[4];
+            const float4 *ap = reinterpret_cast<const float4 *>(&As[buf][l][ty * 8]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 v = ap[i];
+                a[2 * i] = make_float2(v.x, v.y);
+                a[2 * i + 1] = make_float2(v.z, v.w);
+            }
+            const float4 *bp = reinterpret_cast<const float4 *>(&Bs[buf][l][tx * 4]);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float4 v = bp[j];
+                b[2 * j] = make_float2(v.x, v.y);
+                b[2 * j + 1] = make_float2(v.z, v.w);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
+                    acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
+                    acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
+                    acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
+                }
+        }
+        if (kt + 1 < ktiles) {
+            store_shared(buf ^ 1);
+            __syncthreads();
+        }
+    }
+    const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t gi = bm + ty * 8 + i;
+        if (gi >= m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gj = bn + tx * 4 + j;
+            if (gj >= n) continue;
+            float2 o;
+            o.x = alpha.x * acc[i][j].x - alpha.y * acc[i][j].y;
+            o.y = alpha.x * acc[i][j].y + alpha.y * acc[i][j].x;
+            float2 *dst = C + gi + gj * ldc;
+            if (use_beta) {
+                const float2 c = *dst;
+                o.x += beta.x * c.x - beta.y * c.y;
+                o.y += beta.x * c.y + beta.y * c.x;
+            }
+            *dst = o;
+        }
+    }
+}
+
+// One thread per output element; thread t -> (i = t mod m, j = t div m), so
+// consecutive threads write consecutive elements of a column-major C.
+__global__ void cgemm_skinny_kernel(const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB,
+                                    int64_t m, int64_t n, int64_t k, float2 alpha,
+                                    const float2 *__restrict__ A, int64_t lda,
+                                    const float2 *__restrict__ B, int64_t ldb, float2 beta,
+                                    float2 *__restrict__ C, int64_t ldc) {
+    if (desc && desc->mode != QCS_MODE_FP32) return;
+    const int64_t total = m * n;
+    const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / m, i = t - j * m;
+        float sr = 0.f, si = 0.f;
+        for (int64_t l = 0; l < k; ++l) {
+            const float2 a = ld_op(A, opA, i, l, lda);
+            const float2 b = ld_op(B, opB, l, j, ldb);
+            sr = fmaf(a.x, b.x, sr);
+            sr = fmaf(-a.y, b.y, sr);
+            si = fmaf(a.x, b.y, si);
+            si = fmaf(a.y, b.x, si);
+        }
+        float2 o;
+        o.x = alpha.x * sr - alpha.y * si;
+        o.y = alpha.x * si + alpha.y * sr;
+        float2 *dst = C + i + j * ldc;
+        if (use_beta) {
+            const float2 c = *dst;
+            o.x += beta.x * c.x - beta.y * c.y;
+            o.y += beta.x * c.y + beta.y * c.x;
+        }
+        *dst = o;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int64_t m,
+                              int64_t n, int64_t k, float2 alpha, const float2 *A, int64_t lda,
+                              const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc,
+                              cudaStream_t s) {
+    if (m == 0 || n == 0) return cudaSuccess;
+    const bool skinny = (k <= 16) || (m * n <= 4096);
+    if (skinny || m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) {
+        const int64_t total = m * n;
+        const int64_t blocks = (total + 255) / 256;
+        cgemm_skinny_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, s>>>(
+            desc, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+        return cudaGetLastError();
+    }
+    dim3 grid((unsigned)((n + kSBN - 1) / kSBN), (unsigned)((m + kSBM - 1) / kSBM));
+    if (grid.y > 65535u) return cudaErrorInvalidValue;
+    cgemm_simt_kernel<<<grid, 256, 0, s>>>(desc, opA, opB, (int)m, (int)n, (int)k, alpha, A, lda, B,
+                                           ldb, beta, C, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace qcs

@@ -34,8 +34,18 @@ __all__ = [
 ]
 
 
+def _flatten(seed):
+    if isinstance(seed, (tuple, list)):
+        out = []
+        for s in seed:
+            out.extend(_flatten(s))
+        return out
+    return [int(seed)]
+
+
 def _rng(seed) -> np.random.Generator:
-    return np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed)))
+    """PCG64 generator from an integer seed or a (nested) tuple of integers."""
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence(_flatten(seed))))
 
 
 # ---------------------------------------------------------------------------
