@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Emulated CGEMM throughput at FP32-level error, against plain FP32.
+
+One step = one AUTO-mode qcs_cgemm on the CGEMM-sweep workload: exponent
+statistics of A and B, device-side mode selection, the Eq. 1 split of both
+operands, the tcgen05 error-corrected GEMM (and the candidate kernels that
+exit because they were not selected).  Inputs are resident in HBM when the
+timed region starts; they are larger than L2 (2 GiB per operand at 16384),
+so no flush is needed between steps.
+
+Printed JSON line (rank 0): the contract's keys plus
+  e2e           the same metric through the public API with host buffers:
+                per step, pinned-host -> device copies of A and B, the GEMM,
+                and the device -> host copy of C;
+  roofline      the tcgen05 GEMM kernel's tensor throughput (3 products per
+                real product: 24 m n k flops) against the measured peak;
+  cpu_baseline  the FP64 CPU oracle timed on a row sample of the same GEMM
+                (its output also gives the error of the GPU result);
+  fp32          the plain FP32 SIMT CGEMM and cuBLAS CGEMM (torch) on the same
+                inputs, for the "vs plain FP32" part of the metric.
+
+  --impl reference   times the FP64 CPU oracle alone (rank 0), same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "emulated CGEMM TFLOP/s & contraction s/slice vs plain FP32 at FP32-level error"
+UNIT = "TFLOP/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--size", type=int, default=16384)
+    p.add_argument("--s", type=int, default=0, help="exponent spread of the inputs")
+    p.add_argument("--tol", type=float, default=0.1, help="AUTO-t underflow tolerance")
+    p.add_argument("--mode", default="auto")
+    p.add_argument("--sample-rows", type=int, default=16)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true")
+    return p.parse_args()
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="qcs_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_operand(torch, n: int, s: int, seed: int, device):
+    """n x n column-major complex64; parts N(0,1) * 2^e, e ~ U_int[-s, s]."""
+    g = torch.Generator(device=device).manual_seed(seed)
+    base = torch.empty((n, n), dtype=torch.complex64, device=device)  # (cols, rows) storage
+    re = torch.randn((n, n), generator=g, device=device, dtype=torch.float32)
+    im = torch.randn((n, n), generator=g, device=device, dtype=torch.float32)
+    if s > 0:
+        re.mul_(torch.exp2(torch.randint(-s, s + 1, (n, n), generator=g, device=device).float()))
+        im.mul_(torch.exp2(torch.randint(-s, s + 1, (n, n), generator=g, device=device).float()))
+    base.copy_(torch.complex(re, im))
+    del re, im
+    return base.t()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        return mp.get("bf16_tflops"), mp.get("bf16_tflops_sustained"), "measured"
+    except (OSError, ValueError):
+        return 1900.0, 1700.0, "fallback"
+
+
+def oracle_sample(A_rows_np, B_np, n: int, rows: int):
+    """FP64 oracle on ``rows`` output rows: (seconds, result, threads)."""
+    import numpy as np
+
+    import oracle
+
+    Asub = np.asfortranarray(A_rows_np[:rows])
+    t0 = time.perf_counter()
+    ref = oracle.cgemm(0, 0, rows, n, n, 1.0, Asub, B_np, rows=list(range(rows)))
+    return time.perf_counter() - t0, ref, oracle.num_threads()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle as it stands
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import qcs_inputs as qi
+
+    n = args.size
+    rows = 4
+    A = qi.cgemm_operand(rows, n, args.s, seed=(1, n))
+    B = qi.cgemm_operand(n, n, args.s, seed=(2, n))
+    flops = 8.0 * rows * n * n
+    for _ in range(args.warmup):
+        oracle.cgemm(0, 0, rows, n, n, 1.0, A, B, rows=list(range(rows)))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.cgemm(0, 0, rows, n, n, 1.0, A, B, rows=list(range(rows)))
+    dt = (time.perf_counter() - t0) / args.steps
+    val = flops / dt / 1e12
+    sample = f"{rows} output rows of the m=n=k={n} CGEMM per step (FP64 OpenMP oracle)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": f"CGEMM m=n=k={n}, N(0,1)*2^e parts, s={args.s}", "sample": sample},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    del np
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2303_08989_gb300 as q
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.size
+    flops = 8.0 * n * n * n
+    h = q.Handle(tol=args.tol, size_rule=True)
+    A = make_operand(torch, n, args.s, 1000 + rank, dev)
+    B = make_operand(torch, n, args.s, 2000 + rank, dev)
+    C = q.fortran_empty(n, n, device=dev)
+    desc = torch.zeros(4, dtype=torch.int32, device=dev)
+
+    # ---- warm-up ----
+    for _ in range(args.warmup):
+        q.cgemm(h, A, B, C, mode=args.mode, desc_out=desc)
+    torch.cuda.synchronize()
+    mode_used = q.MODE_NAME[int(desc[0].item())]
+
+    # ---- timed region: device-resident inputs ----
+    clocks = ClockSampler(dev.index if world == 1 else local)
+    h.set_profiling(True)
+    h.get_profile()  # clear
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        q.cgemm(h, A, B, C, mode=args.mode)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = h.get_profile()
+    h.set_profiling(False)
+    ms = max_over_ranks(ms)
+    value = world * flops / (ms * 1e-3) / 1e12
+    launches_per_step = 7  # stats, select, split x2, tcgen05 FP16, tcgen05 TF32, SIMT (gated)
+
+    # ---- dominant kernel roofline (live CUDA-event timing of the tcgen05 GEMM) ----
+    tc_ms, tc_n = prof["gemm_tc"]
+    tc_avg = tc_ms / max(tc_n, 1)
+    burst, sustained, src = peaks()
+    kind_ratio = {"fp16x": 1.0, "fp16x_scaled": 1.0, "bf16x3": 1.0, "tf32x": 1.1 / 2.25}.get(mode_used)
+    roofline = None
+    if kind_ratio is not None and tc_avg > 0:
+        achieved = 24.0 * n * n * n / (tc_avg * 1e-3) / 1e12
+        peak = sustained * kind_ratio
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": f"cgemm_tc_kernel ({mode_used}), 3 tensor products per real product",
+                    "peak_source": f"{src} bf16 sustained" + (" x TF32/BF16 nominal ratio 1.1/2.25"
+                                                              if kind_ratio != 1.0 else "")}
+    stages = {k: {"ms_per_step": v[0] / args.steps, "launches": v[1]} for k, v in prof.items() if v[1]}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64",
+        "data": "synthetic (seeded torch.randn on the device)",
+        "config": {"workload": f"CGEMM m=n=k={n}, parts N(0,1)*2^e, e~U_int[-{args.s},{args.s}], "
+                               f"AUTO-{args.tol:g} (size rule on)",
+                   "m": n, "n": n, "k": n, "s": args.s, "tol": args.tol, "mode": args.mode,
+                   "mode_selected": mode_used,
+                   "l2": "operands 8*n^2 bytes each, larger than L2; no flush",
+                   "parallelism": f"{world} independent GEMMs (one per GPU)"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "stages": stages,
+        "roofline": roofline,
+    }
+
+    # ---- error of the GPU result against the FP64 oracle (row sample) + CPU baseline ----
+    if rank == 0:
+        rows = args.sample_rows
+        A_rows = A[:rows].cpu().numpy().astype(np.complex64)
+        B_np = B.cpu().numpy()
+        C_rows = C[:rows].cpu().numpy().astype(np.complex128)
+        secs, ref, threads = oracle_sample(A_rows, B_np, n, rows)
+        import oracle
+
+        out["error"] = {"rel_fro_vs_fp64": oracle.rel_fro_error(C_rows, ref),
+                        "sample": f"{rows} output rows"}
+        out["cpu_baseline"] = {"value": 8.0 * rows * n * n / secs / 1e12, "unit": UNIT,
+                               "cores": threads, "kind": "oracle",
+                               "sample": f"{rows} of {n} output rows of the same GEMM (FP64, OpenMP)",
+                               "seconds": secs}
+        del B_np
+
+    # ---- plain FP32 on the same inputs ----
+    if not args.no_extras:
+        reps = 2
+        C2 = q.fortran_empty(n, n, device=dev)
+        q.cgemm(h, A, B, C2, mode="fp32")
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            q.cgemm(h, A, B, C2, mode="fp32")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        simt = flops / (e0.elapsed_time(e1) / reps * 1e-3) / 1e12
+        torch.matmul(A, B)  # cuBLAS CGEMM on the column-major views (default math mode)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            torch.matmul(A, B)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cublas = flops / (e0.elapsed_time(e1) / reps * 1e-3) / 1e12
+        out["fp32"] = {"simt_tflops": simt, "cublas_cgemm_tflops": cublas,
+                       "speedup_vs_simt": value / world / simt,
+                       "speedup_vs_cublas": value / world / cublas}
+        if rank == 0:
+            C2r = C2[:args.sample_rows].cpu().numpy().astype(np.complex128)
+            import oracle
+
+            out["fp32"]["rel_fro_vs_fp64"] = oracle.rel_fro_error(C2r, ref)
+        del C2
+
+    # ---- end to end through the public API, host buffers ----
+    if not args.no_e2e:
+        hA = torch.empty((n, n), dtype=torch.complex64, pin_memory=True)
+        hB = torch.empty((n, n), dtype=torch.complex64, pin_memory=True)
+        hC = torch.empty((n, n), dtype=torch.complex64, pin_memory=True)
+        hA.copy_(A.t())
+        hB.copy_(B.t())
+        Ad = torch.empty((n, n), dtype=torch.complex64, device=dev)
+        Bd = torch.empty((n, n), dtype=torch.complex64, device=dev)
+        Cd = torch.empty((n, n), dtype=torch.complex64, device=dev)
+
+        def e2e_step():
+            Ad.copy_(hA, non_blocking=True)
+            Bd.copy_(hB, non_blocking=True)
+            q.cgemm(h, Ad.t(), Bd.t(), Cd.t(), mode=args.mode)
+            hC.copy_(Cd, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ek = max(2, args.steps // 2)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ek):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ems = max_over_ranks(e0.elapsed_time(e1) / ek)
+        out["e2e"] = {"value": world * flops / (ems * 1e-3) / 1e12, "unit": UNIT,
+                      "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8,
+                      "ms_per_step": ems, "steps": ek}
+        del hA, hB, hC, Ad, Bd, Cd
+
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

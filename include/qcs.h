@@ -225,6 +225,18 @@ int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
                                const qcs_c32 *const *leaves, const double *d_grad_out,
                                qcs_c32 *const *d_grad_leaves, qcs_run_info_t *info);
 
+/* Stage timing (tracing aid, off by default).  While enabled, every call
+ * records a pair of CUDA events on the handle's stream around each stage
+ * it launches.  qcs_get_profile() synchronizes the stream, writes the
+ * milliseconds accumulated per stage since the previous read into ms[0..n)
+ * -- [0] exponent statistics, [1] selection, [2] split, [3] tensor-core
+ * GEMM, [4] FP32 SIMT GEMM, [5] permute/gather, [6] FP64 reductions -- and
+ * the number of event pairs per stage into counts (optional), then clears
+ * them.  Enabling it adds no synchronisation to the calls themselves. */
+#define QCS_PROFILE_STAGES 7
+int qcs_set_profiling(qcs_handle_t h, int enabled);
+int qcs_get_profile(qcs_handle_t h, double *ms, int64_t *counts, int n);
+
 /* Wait for the handle's stream; return TIMEOUT if a device-side bounded
  * wait gave up since the last qcs_sync (the word is then cleared), CUDA on
  * a runtime error, else SUCCESS. */

@@ -93,6 +93,17 @@ class Handle:
         _lib.check(self.lib.qcs_set_size_rule(self._h, 1 if on else 0))
         self.size_rule = bool(on)
 
+    def set_profiling(self, on: bool):
+        _lib.check(self.lib.qcs_set_profiling(self._h, 1 if on else 0))
+
+    def get_profile(self):
+        """{stage: (milliseconds, event pairs)} accumulated since the last read."""
+        n = len(_lib.PROFILE_STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        _lib.check(self.lib.qcs_get_profile(self._h, ms, cnt, n), "qcs_get_profile")
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(_lib.PROFILE_STAGES)}
+
     def sync(self):
         _lib.check(self.lib.qcs_sync(self._h), "qcs_sync")
 

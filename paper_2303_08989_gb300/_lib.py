@@ -28,8 +28,10 @@ OP_N, OP_T, OP_C = 0, 1, 2
 EXPORTED = [
     "qcs_create", "qcs_destroy", "qcs_set_stream", "qcs_set_underflow_tol", "qcs_set_size_rule",
     "qcs_exp_stats", "qcs_select", "qcs_cgemm", "qcs_split", "qcs_permute", "qcs_contract_tree",
-    "qcs_contract_tree_backward", "qcs_sync", "qcs_status_string",
+    "qcs_contract_tree_backward", "qcs_set_profiling", "qcs_get_profile", "qcs_sync",
+    "qcs_status_string",
 ]
+PROFILE_STAGES = ["stats", "select", "split", "gemm_tc", "gemm_simt", "permute", "reduce"]
 
 
 class QcsError(RuntimeError):
@@ -109,6 +111,8 @@ def load(path: str = LIB_PATH):
                               ctypes.POINTER(qcs_run_info_t)],
         "qcs_contract_tree_backward": [H, ctypes.POINTER(qcs_tree_t), ctypes.POINTER(P), P,
                                        ctypes.POINTER(P), ctypes.POINTER(qcs_run_info_t)],
+        "qcs_set_profiling": [H, I],
+        "qcs_get_profile": [H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I],
         "qcs_sync": [H],
     }
     for name, args in sig.items():

@@ -43,6 +43,33 @@ int ensure_workspace(Workspace &w, size_t bytes) {
     return QCS_SUCCESS;
 }
 
+static cudaEvent_t pool_get(qcs_handle_s *h) {
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+ProfScope::ProfScope(qcs_handle_s *h, int stage) : h_(h) {
+    if (!h_->profiling) return;
+    ProfEvent pe{stage, pool_get(h_), pool_get(h_)};
+    if (!pe.start || !pe.stop) return;
+    cudaEventRecord(pe.start, h_->stream);
+    h_->prof.push_back(pe);
+    idx_ = static_cast<int>(h_->prof.size()) - 1;
+}
+
+ProfScope::~ProfScope() {
+    if (idx_ >= 0) cudaEventRecord(h_->prof[idx_].stop, h_->stream);
+}
+
 }  // namespace qcs
 
 namespace {
@@ -133,10 +160,16 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
         const int64_t ra = (opA == QCS_OP_N) ? m : k, ca = (opA == QCS_OP_N) ? k : m;
         const int64_t rb = (opB == QCS_OP_N) ? k : n, cb = (opB == QCS_OP_N) ? n : k;
         const int gA = stats_blocks(ra * ca, h->num_sms), gB = stats_blocks(rb * cb, h->num_sms);
-        e = launch_stats2(A, ra, ca, lda, gA, B, rb, cb, ldb, gB, partials, s);
+        {
+            ProfScope ps(h, kProfStats);
+            e = launch_stats2(A, ra, ca, lda, gA, B, rb, cb, ldb, gB, partials, s);
+        }
         if (e != cudaSuccess) return QCS_ERR_CUDA;
-        e = launch_select(partials, gA, gB, 2 * ra * ca, 2 * rb * cb, h->tol, eff, nullptr,
-                          nullptr, desc, s);
+        {
+            ProfScope ps(h, kProfSelect);
+            e = launch_select(partials, gA, gB, 2 * ra * ca, 2 * rb * cb, h->tol, eff, nullptr,
+                              nullptr, desc, s);
+        }
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     } else {
         e = launch_set_desc(desc, eff, s);
@@ -158,12 +191,19 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
         int64_t sr, sc;
         // The split writes with the selected kind's element size; the pitch is
         // kp elements either way, so both tensor maps below describe it.
-        plane_strides(0, opA, lda, sr, sc);
-        e = launch_split(desc, 0, A, sr, sc, opA == QCS_OP_C, m, k, mp, kp, planesA, kp, mp * kp, s);
+        {
+            ProfScope ps(h, kProfSplit);
+            plane_strides(0, opA, lda, sr, sc);
+            e = launch_split(desc, 0, A, sr, sc, opA == QCS_OP_C, m, k, mp, kp, planesA, kp,
+                             mp * kp, s);
+            if (e == cudaSuccess) {
+                plane_strides(1, opB, ldb, sr, sc);
+                e = launch_split(desc, 1, B, sr, sc, opB == QCS_OP_C, n, k, np, kp, planesB, kp,
+                                 np * kp, s);
+            }
+        }
         if (e != cudaSuccess) return QCS_ERR_CUDA;
-        plane_strides(1, opB, ldb, sr, sc);
-        e = launch_split(desc, 1, B, sr, sc, opB == QCS_OP_C, n, k, np, kp, planesB, kp, np * kp, s);
-        if (e != cudaSuccess) return QCS_ERR_CUDA;
+        ProfScope ps_tc(h, kProfGemmTc);
         if (need16) {
             CUtensorMap ma, mb;
             if (encode_planes(h, &ma, planesA, mp, kp, 2) || encode_planes(h, &mb, planesB, np, kp, 2))
@@ -182,10 +222,12 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
             if (e != cudaSuccess) return QCS_ERR_CUDA;
         }
         if (eff == QCS_MODE_AUTO) {
+            ProfScope ps(h, kProfGemmSimt);
             e = launch_cgemm_simt(desc, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
             if (e != cudaSuccess) return QCS_ERR_CUDA;
         }
     } else {
+        ProfScope ps(h, kProfGemmSimt);
         e = launch_cgemm_simt(nullptr, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     }
@@ -261,6 +303,11 @@ int qcs_destroy(qcs_handle_t h) {
     if (h->ws.ptr) cudaFree(h->ws.ptr);
     if (h->tree_ws.ptr) cudaFree(h->tree_ws.ptr);
     if (h->d_err) cudaFree(h->d_err);
+    for (const ProfEvent &pe : h->prof) {
+        cudaEventDestroy(pe.start);
+        cudaEventDestroy(pe.stop);
+    }
+    for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
     delete h;
     return QCS_SUCCESS;
 }
@@ -351,6 +398,39 @@ int qcs_permute(qcs_handle_t h, int rank, const int64_t *dims, const int64_t *st
     if (e != cudaSuccess) return QCS_ERR_CUDA;
     if (d_stats) return qcs_exp_stats(h, total, 1, out, std::max<int64_t>(1, total), d_stats);
     return QCS_SUCCESS;
+}
+
+int qcs_set_profiling(qcs_handle_t h, int enabled) {
+    if (!h) return QCS_ERR_INVALID_ARG;
+    h->profiling = enabled ? 1 : 0;
+    return QCS_SUCCESS;
+}
+
+int qcs_get_profile(qcs_handle_t h, double *ms, int64_t *counts, int n) {
+    if (!h || !ms || n < 0) return QCS_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    for (int i = 0; i < n; ++i) {
+        ms[i] = 0.0;
+        if (counts) counts[i] = 0;
+    }
+    int rc = QCS_SUCCESS;
+    for (const ProfEvent &pe : h->prof) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, pe.start, pe.stop) != cudaSuccess) {
+            cudaGetLastError();
+            rc = QCS_ERR_CUDA;
+        } else if (pe.stage < n) {
+            ms[pe.stage] += t;
+            if (counts) counts[pe.stage] += 1;
+        }
+        h->event_pool.push_back(pe.start);
+        h->event_pool.push_back(pe.stop);
+    }
+    h->prof.clear();
+    return rc;
 }
 
 int qcs_sync(qcs_handle_t h) {

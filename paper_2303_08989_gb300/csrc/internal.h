@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "../../include/qcs.h"
 
@@ -51,6 +52,22 @@ struct Workspace {
 
 }  // namespace qcs
 
+namespace qcs {
+enum ProfStage : int {
+    kProfStats = 0,
+    kProfSelect = 1,
+    kProfSplit = 2,
+    kProfGemmTc = 3,
+    kProfGemmSimt = 4,
+    kProfPermute = 5,
+    kProfReduce = 6,
+};
+struct ProfEvent {
+    int stage;
+    cudaEvent_t start, stop;
+};
+}  // namespace qcs
+
 struct qcs_handle_s {
     int device = 0;
     int num_sms = 0;
@@ -61,7 +78,24 @@ struct qcs_handle_s {
     qcs::Workspace ws;               // GEMM workspace (planes, partials, descriptor)
     qcs::Workspace tree_ws;          // contraction-tree intermediates
     qcs::EncodeTiledFn encode = nullptr;
+    int profiling = 0;
+    std::vector<qcs::ProfEvent> prof;     // recorded, not yet read
+    std::vector<cudaEvent_t> event_pool;  // reusable events
 };
+
+namespace qcs {
+// Records a start event on construction and a stop event on destruction
+// when the handle's profiling is on.
+class ProfScope {
+   public:
+    ProfScope(qcs_handle_s *h, int stage);
+    ~ProfScope();
+
+   private:
+    qcs_handle_s *h_;
+    int idx_ = -1;
+};
+}  // namespace qcs
 
 namespace qcs {
 
