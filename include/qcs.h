@@ -39,6 +39,7 @@ extern "C" {
 #define QCS_ERR_ALLOC (-3)       /* cudaMalloc of the workspace failed */
 #define QCS_ERR_CUDA (-4)        /* a CUDA runtime call failed */
 #define QCS_ERR_TIMEOUT (-5)     /* a device-side bounded wait ran out (see qcs_sync) */
+#define QCS_ERR_SCRATCH_TOO_SMALL (-6) /* qcs_cgemm_noalloc: problem needs more than its fixed scratch */
 
 typedef struct qcs_handle_s *qcs_handle_t;
 
@@ -224,6 +225,43 @@ int qcs_contract_tree(qcs_handle_t h, const qcs_tree_t *tree, const qcs_c32 *con
 int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
                                const qcs_c32 *const *leaves, const double *d_grad_out,
                                qcs_c32 *const *d_grad_leaves, qcs_run_info_t *info);
+
+/* qcs_cgemm without a handle and without allocating device memory.  (The
+ * paper has no counterpart: this serves callers that must not allocate at
+ * call time -- their device memory is owned by another allocator with a
+ * fixed budget, such as a framework's caching allocator or a pre-sized
+ * arena, or they run latency-critical loops that cannot afford cudaMalloc /
+ * cudaFree, which may synchronise the whole device.)
+ *
+ * Same operation, arguments and semantics as qcs_cgemm, on the stream
+ * ``cuda_stream`` (a cudaStream_t; NULL = legacy default stream) of the
+ * current device, with underflow tolerance ``underflow_tol`` (as
+ * qcs_set_underflow_tol) and the size rule of Section 4.3 disabled (AUTO
+ * always selects from the statistics: every problem that fits is below the
+ * rule's threshold).  The
+ * caller still passes A, B, C (and the optional d_desc_out); the workspace
+ * lives in a fixed device array of QCS_NOALLOC_SCRATCH_BYTES (64 MiB) that
+ * every GPU which loads this part of the library keeps until the process
+ * exits.  A problem whose workspace does not fit -- 256 bytes, the
+ * statistics partials, and the split planes of op(A) and op(B): 16 bytes per
+ * element of ceil(m/128)*128 x ceil(k/32)*32 plus ceil(n/128)*128 x
+ * ceil(k/32)*32 for AUTO and TF32X, 8 for the 16-bit modes, none for FP32 --
+ * is rejected with QCS_ERR_SCRATCH_TOO_SMALL before anything is launched
+ * (m = n = k = 1024 fits in every mode).
+ *
+ * Set-up: the first call on a device, with that device current, resolves
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture on the device.  No call allocates or frees
+ * memory.  All calls on a device share the one array and it keeps the last
+ * call's contents (each call clears what must start at zero): calls that
+ * overlap on the GPU, e.g. on two concurrent streams, race and corrupt each
+ * other's results; serialise them.  Device-side wait timeouts are recorded
+ * in the shared array but not reported (there is no handle to qcs_sync). */
+#define QCS_NOALLOC_SCRATCH_BYTES (64u << 20)
+int qcs_cgemm_noalloc(void *cuda_stream, qcs_mode_t mode, double underflow_tol, qcs_op_t transA,
+                      qcs_op_t transB, int64_t m, int64_t n, int64_t k, const qcs_c32 *alpha,
+                      const qcs_c32 *A, int64_t lda, const qcs_c32 *B, int64_t ldb,
+                      const qcs_c32 *beta, qcs_c32 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out);
 
 /* Stage timing (tracing aid, off by default).  While enabled, every call
  * records a pair of CUDA events on the handle's stream around each stage

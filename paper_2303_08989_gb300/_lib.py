@@ -18,6 +18,7 @@ QCS_ERR_UNSUPPORTED = -2
 QCS_ERR_ALLOC = -3
 QCS_ERR_CUDA = -4
 QCS_ERR_TIMEOUT = -5
+QCS_ERR_SCRATCH_TOO_SMALL = -6
 
 MODE_AUTO, MODE_FP16X, MODE_FP16X_SCALED, MODE_TF32X, MODE_FP32, MODE_BF16X3 = range(6)
 MODE_BY_NAME = {"auto": 0, "fp16x": 1, "fp16x_scaled": 2, "tf32x": 3, "fp32": 4, "bf16x3": 5}
@@ -29,7 +30,7 @@ EXPORTED = [
     "qcs_create", "qcs_destroy", "qcs_set_stream", "qcs_set_underflow_tol", "qcs_set_size_rule",
     "qcs_exp_stats", "qcs_select", "qcs_cgemm", "qcs_split", "qcs_permute", "qcs_contract_tree",
     "qcs_contract_tree_backward", "qcs_set_profiling", "qcs_get_profile", "qcs_sync",
-    "qcs_status_string",
+    "qcs_status_string", "qcs_cgemm_noalloc",
 ]
 PROFILE_STAGES = ["stats", "select", "split", "gemm_tc", "gemm_simt", "permute", "reduce"]
 
@@ -114,6 +115,8 @@ def load(path: str = LIB_PATH):
         "qcs_set_profiling": [H, I],
         "qcs_get_profile": [H, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I],
         "qcs_sync": [H],
+        "qcs_cgemm_noalloc": [P, I, ctypes.c_double, I, I, I64, I64, I64, ctypes.POINTER(qcs_c32),
+                              P, I64, P, I64, ctypes.POINTER(qcs_c32), P, I64, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

@@ -457,6 +457,8 @@ const char *qcs_status_string(int status) {
         case QCS_ERR_ALLOC: return "workspace allocation failed";
         case QCS_ERR_CUDA: return "CUDA runtime error";
         case QCS_ERR_TIMEOUT: return "device-side wait timed out";
+        case QCS_ERR_SCRATCH_TOO_SMALL:
+            return "problem needs more than the fixed scratch of qcs_cgemm_noalloc";
         default: return "unknown status";
     }
 }
