@@ -155,7 +155,7 @@ int qcs_split(qcs_handle_t h, const qcs_gemm_desc_t *d_desc, int which, qcs_op_t
  * TTGT contraction (Section 1, Section 2.2).  out (device, contiguous,
  * first index fastest) has ``rank`` dims ``dims[0..rank)``; its element
  * (i_0, ..., i_{r-1}) is in[offset + sum_d i_d * strides[d]] (element
- * strides of the input, device).  dims/strides are host arrays, rank <= 24.
+ * strides of the input, device).  dims/strides are host arrays, rank <= QCS_MAX_RANK.
  * When d_stats is not NULL, the exponent statistics of the output are also
  * written there (fused, Section 4.1). */
 int qcs_permute(qcs_handle_t h, int rank, const int64_t *dims, const int64_t *strides,
@@ -163,65 +163,88 @@ int qcs_permute(qcs_handle_t h, int rank, const int64_t *dims, const int64_t *st
 
 /* ---- contraction tree (Section 2.2, Section 5.3) ---------------------- */
 
-/* One pairwise contraction step of a plan.  Tensors are numbered: leaves
- * 0 .. n_leaves-1, then step s produces tensor n_leaves + s.  Every tensor
- * is stored contiguous, first index fastest.  The step computes
- *   out(m x n) = op_a(A_mat) * op_b(B_mat)
- * where A_mat is the m x k matrix gathered from tensor ``a`` (gather: rank,
- * dims, element strides into the source tensor, and, for leaves, a
- * per-slice offset table) and likewise B_mat (k x n).  A gather with
- * rank == -1 means the source tensor is used as it is (already the m x k /
- * k x n column-major matrix). */
+#define QCS_MAX_RANK 32
+
+/* Where the elements of a column-major matrix live in a source tensor:
+ * element (i, l) of an R x K matrix has column-major index t = i + l R;
+ * decomposing t first-index-fastest over dims[0..rank) gives (x_0, ...),
+ * and the element is at source offset sum_d x_d strides[d] (plus the
+ * instance offset when the source is a leaf).  prod(dims) = R K. */
 typedef struct {
     int32_t rank;
     int32_t pad_;
-    int64_t dims[24];
-    int64_t strides[24];
+    int64_t dims[QCS_MAX_RANK];
+    int64_t strides[QCS_MAX_RANK];
 } qcs_gather_t;
 
+/* One pairwise contraction, reshaped to a CGEMM (TTGT, Section 1):
+ *   out (m x n, column-major, stored contiguous) = A_mat (m x k) B_mat (k x n)
+ * where A_mat is read from tensor ``a`` through map_a and B_mat from tensor
+ * ``b`` through map_b.  Tensors are numbered: leaves 0 .. n_leaves-1, then
+ * step s produces tensor n_leaves + s (m n elements).  direct_a is a
+ * qcs_op_t when tensor a, as stored, already is A_mat (QCS_OP_N, leading
+ * dimension m) or its transpose (QCS_OP_T, leading dimension k) and its
+ * instance offsets are all zero; otherwise -1 and A_mat is gathered
+ * first.  Likewise direct_b (QCS_OP_N: ld k; QCS_OP_T: ld n). */
 typedef struct {
-    int32_t a, b;         /* source tensor ids */
-    int32_t op_a, op_b;   /* qcs_op_t applied after the gather */
+    int32_t a, b;
+    int32_t direct_a, direct_b;
     int64_t m, n, k;
-    qcs_gather_t ga, gb;  /* gathers building A_mat (m x k) and B_mat (k x n) */
-    int32_t mode;         /* qcs_mode_t for this GEMM (AUTO = per-GEMM selection) */
+    qcs_gather_t map_a;
+    qcs_gather_t map_b;
+    int32_t mode;  /* qcs_mode_t of this GEMM (AUTO: size rule + per-GEMM selection) */
     int32_t pad_;
 } qcs_step_t;
 
+/* A contraction plan run for n_instances instances.  An instance is one
+ * assignment of the sliced indices (Section 5.3) and/or one bitstring: it
+ * reads leaf i at element offset instance_offset[inst * n_leaves + i] of the
+ * caller's leaf tensor, contracts all steps, and adds the root tensor (the
+ * last step's output, or leaf 0 when n_steps == 0) -- gathered at out_index
+ * -- into output slot instance_slot[inst], in FP64.  Slices of one bitstring
+ * share a slot, so their sum is the amplitude. */
 typedef struct {
     int32_t n_leaves;
     int32_t n_steps;
-    int32_t n_slices;        /* >= 1 */
-    int32_t pad_;
-    const int64_t *leaf_size;     /* host, n_leaves: elements of each leaf as sliced */
-    const int64_t *slice_offset;  /* host, n_slices * n_leaves: element offset of each
-                                     sliced leaf into the caller's full leaf tensor */
-    const qcs_step_t *steps;      /* host, n_steps; the last step's output is the result */
-    int64_t out_size;             /* elements of the final tensor (1 for an amplitude) */
+    int32_t n_instances;
+    int32_t n_slots;
+    const int64_t *leaf_size;        /* host, n_leaves: elements of each full leaf tensor */
+    const int64_t *instance_offset;  /* host, n_instances * n_leaves */
+    const int32_t *instance_slot;    /* host, n_instances, each in [0, n_slots) */
+    const qcs_step_t *steps;         /* host, n_steps */
+    int64_t out_size;                /* results per slot */
+    const int64_t *out_index;        /* host, out_size indices into the root, or NULL:
+                                        the root itself (then root size == out_size) */
 } qcs_tree_t;
 
 typedef struct {
-    double seconds;            /* host wall time of the call (launch side) */
-    int64_t gemm_count;        /* GEMMs issued (all slices) */
-    int64_t mode_count[6];     /* GEMMs per forced/size-rule mode; AUTO ones are counted in [0] */
-    int64_t workspace_bytes;   /* bytes of intermediates + GEMM workspace in use */
+    double seconds;           /* host wall time of the call (launch side) */
+    int64_t gemm_count;       /* CGEMMs issued (all instances) */
+    int64_t gather_count;     /* gathers / scatters issued */
+    int64_t mode_count[6];    /* GEMMs per effective mode after the size rule (AUTO counted in [0]) */
+    int64_t workspace_bytes;  /* bytes of the tree workspace */
+    double flops;             /* nominal 8 m n k summed over the GEMMs */
 } qcs_run_info_t;
 
-/* Contract the plan for every slice and sum the slices in FP64.
- *   leaves: host array of n_leaves device pointers (complex64, full tensors).
- *   d_out: device complex128 (interleaved double re, im), out_size elements,
- *   overwritten with the sum over slices of the final tensor.
- *   info: optional host out. */
+/* Contract the plan for every instance and accumulate into d_out (device,
+ * complex128 as interleaved doubles, n_slots * out_size values, slot-major;
+ * overwritten).  leaves: host array of n_leaves device pointers (complex64).
+ * info: optional host out.  The plan is validated on the host (ids, ranks,
+ * and every read offset within its tensor) before anything is launched.
+ * Intermediates live in the handle's tree workspace. */
 int qcs_contract_tree(qcs_handle_t h, const qcs_tree_t *tree, const qcs_c32 *const *leaves,
                       double *d_out, qcs_run_info_t *info);
 
 /* Adjoint of qcs_contract_tree.  Given d_grad_out (device complex128,
- * out_size elements: dL/dRe + i dL/dIm of the summed result), accumulates
- * into d_grad_leaves[i] (host array of device complex64 pointers, each the
- * size of the caller's full leaf tensor) the gradient of L with respect to
- * each leaf, in the same convention.  Each GEMM of the forward pass has two
- * adjoint GEMMs, grad_A = grad_C op(B)^H and grad_B = op(A)^H grad_C, run as
- * emulated CGEMMs; intermediates are recomputed per slice. */
+ * n_slots * out_size values: dL/dRe + i dL/dIm of each output), adds to
+ * d_grad_leaves[i] (host array of device complex64 pointers, each the size
+ * of the caller's full leaf tensor; not cleared) the gradient of L with
+ * respect to every leaf element in the same convention.  Each forward GEMM
+ * out = A_mat B_mat has two adjoint GEMMs, grad_A = grad_out B_mat^H and
+ * grad_B = A_mat^H grad_out, run as emulated CGEMMs in the step's mode
+ * (op C flags); the forward intermediates are recomputed per instance
+ * (slice) rather than kept across instances.  Every tensor of the plan must
+ * be used by exactly one step (a tree). */
 int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
                                const qcs_c32 *const *leaves, const double *d_grad_out,
                                qcs_c32 *const *d_grad_leaves, qcs_run_info_t *info);

@@ -54,29 +54,35 @@ class qcs_gemm_desc_t(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+MAX_RANK = 32
+
+
 class qcs_gather_t(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int32), ("pad_", ctypes.c_int32),
-                ("dims", ctypes.c_int64 * 24), ("strides", ctypes.c_int64 * 24)]
+                ("dims", ctypes.c_int64 * MAX_RANK), ("strides", ctypes.c_int64 * MAX_RANK)]
 
 
 class qcs_step_t(ctypes.Structure):
-    _fields_ = [("a", ctypes.c_int32), ("b", ctypes.c_int32), ("op_a", ctypes.c_int32),
-                ("op_b", ctypes.c_int32), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
-                ("k", ctypes.c_int64), ("ga", qcs_gather_t), ("gb", qcs_gather_t),
+    _fields_ = [("a", ctypes.c_int32), ("b", ctypes.c_int32), ("direct_a", ctypes.c_int32),
+                ("direct_b", ctypes.c_int32), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("k", ctypes.c_int64), ("map_a", qcs_gather_t), ("map_b", qcs_gather_t),
                 ("mode", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class qcs_tree_t(ctypes.Structure):
     _fields_ = [("n_leaves", ctypes.c_int32), ("n_steps", ctypes.c_int32),
-                ("n_slices", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("n_instances", ctypes.c_int32), ("n_slots", ctypes.c_int32),
                 ("leaf_size", ctypes.POINTER(ctypes.c_int64)),
-                ("slice_offset", ctypes.POINTER(ctypes.c_int64)),
-                ("steps", ctypes.POINTER(qcs_step_t)), ("out_size", ctypes.c_int64)]
+                ("instance_offset", ctypes.POINTER(ctypes.c_int64)),
+                ("instance_slot", ctypes.POINTER(ctypes.c_int32)),
+                ("steps", ctypes.POINTER(qcs_step_t)), ("out_size", ctypes.c_int64),
+                ("out_index", ctypes.POINTER(ctypes.c_int64))]
 
 
 class qcs_run_info_t(ctypes.Structure):
     _fields_ = [("seconds", ctypes.c_double), ("gemm_count", ctypes.c_int64),
-                ("mode_count", ctypes.c_int64 * 6), ("workspace_bytes", ctypes.c_int64)]
+                ("gather_count", ctypes.c_int64), ("mode_count", ctypes.c_int64 * 6),
+                ("workspace_bytes", ctypes.c_int64), ("flops", ctypes.c_double)]
 
 
 _lib = None

@@ -118,7 +118,7 @@ void plane_strides(int which, int op, int64_t ld, int64_t &sr, int64_t &sc) {
 }  // namespace
 
 // Effective mode after the size rule (host side, sizes are known on the host).
-static int effective_mode(qcs_handle_t h, int mode, int64_t m, int64_t n, int64_t k) {
+int qcs::effective_mode(qcs_handle_t h, int mode, int64_t m, int64_t n, int64_t k) {
     if (mode != QCS_MODE_AUTO || !h->size_rule) return mode;
     const int64_t s = std::min(m, std::min(n, k));
     if (s >= 2048) return QCS_MODE_AUTO;
@@ -386,7 +386,7 @@ int qcs_split(qcs_handle_t h, const qcs_gemm_desc_t *d_desc, int which, qcs_op_t
 
 int qcs_permute(qcs_handle_t h, int rank, const int64_t *dims, const int64_t *strides,
                 int64_t offset, const qcs_c32 *in, qcs_c32 *out, qcs_stats_t *d_stats) {
-    if (!h || rank < 0 || rank > 24 || (rank > 0 && (!dims || !strides)) || !in || !out)
+    if (!h || rank < 0 || rank > QCS_MAX_RANK || (rank > 0 && (!dims || !strides)) || !in || !out)
         return QCS_ERR_INVALID_ARG;
     int64_t total = 1;
     for (int d = 0; d < rank; ++d) {

@@ -133,6 +133,19 @@ cudaError_t launch_stats_finalize(const int64_t *partials, int g, int64_t n, qcs
                                   cudaStream_t s);
 cudaError_t launch_accumulate_c128(const float2 *src, double *dst, int64_t count, int overwrite,
                                    cudaStream_t s);
+cudaError_t launch_scatter(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
+                           const float2 *src, float2 *dst, int accumulate, cudaStream_t s);
+cudaError_t launch_accumulate_gather_c128(const float2 *src, const int64_t *index, double *dst,
+                                          int64_t count, cudaStream_t s);
+cudaError_t launch_seed_grad(const double *g, const int64_t *index, float2 *grad_root,
+                             int64_t count, cudaStream_t s);
+
+// ---- shared with the executor (capi.cu) ------------------------------------
+int effective_mode(qcs_handle_t h, int mode, int64_t m, int64_t n, int64_t k);
+size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms);
+int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n, int64_t k,
+              float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta,
+              float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out, const qcs_gemm_desc_t *d_desc_in);
 
 // ---- GEMM launchers -------------------------------------------------------
 // Plain FP32 SIMT CGEMM (runs only when desc->mode == FP32, or always when

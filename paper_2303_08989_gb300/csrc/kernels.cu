@@ -436,8 +436,8 @@ namespace {
 
 struct PermParams {
     int rank;
-    int64_t dims[24];
-    int64_t strides[24];
+    int64_t dims[QCS_MAX_RANK];
+    int64_t strides[QCS_MAX_RANK];
 };
 
 __global__ void permute_kernel(PermParams P, int64_t total, int64_t offset,
@@ -451,6 +451,56 @@ __global__ void permute_kernel(PermParams P, int64_t total, int64_t offset,
             rem = q;
         }
         out[o] = in[src];
+    }
+}
+
+// Inverse of permute_kernel: dst[offset + sum_d x_d strides_d] (+)= src[o].
+__global__ void scatter_kernel(PermParams P, int64_t total, int64_t offset,
+                               const float2 *__restrict__ src, float2 *__restrict__ dst,
+                               int accumulate) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        int64_t rem = o, d_off = offset;
+        for (int d = 0; d < P.rank; ++d) {
+            const int64_t q = rem / P.dims[d];
+            d_off += (rem - q * P.dims[d]) * P.strides[d];
+            rem = q;
+        }
+        float2 v = src[o];
+        if (accumulate) {
+            const float2 w = dst[d_off];
+            v.x += w.x;
+            v.y += w.y;
+        }
+        dst[d_off] = v;
+    }
+}
+
+// dst[j] += (double) src[index ? index[j] : j], j < count (FP64 sums over
+// slices, Section 5.3).
+__global__ void accumulate_gather_c128_kernel(const float2 *__restrict__ src,
+                                              const int64_t *__restrict__ index,
+                                              double2 *__restrict__ dst, int64_t count) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = src[index ? index[j] : j];
+        double2 d = dst[j];
+        d.x += (double)v.x;
+        d.y += (double)v.y;
+        dst[j] = d;
+    }
+}
+
+// grad_root[index ? index[j] : j] += (float) g[j]; atomics because an index
+// may repeat (the same bitstring asked for twice).
+__global__ void seed_grad_kernel(const double2 *__restrict__ g, const int64_t *__restrict__ index,
+                                 float2 *__restrict__ grad_root, int64_t count) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = g[j];
+        float2 *t = grad_root + (index ? index[j] : j);
+        atomicAdd(&t->x, (float)v.x);
+        atomicAdd(&t->y, (float)v.y);
     }
 }
 
@@ -485,6 +535,42 @@ cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides
     const int64_t blocks = (total + 255) / 256;
     permute_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, s>>>(P, total, offset, in,
                                                                              out);
+    return cudaGetLastError();
+}
+
+static int grid_for(int64_t total) {
+    const int64_t blocks = (total + 255) / 256;
+    return (int)(blocks < 65536 ? (blocks > 0 ? blocks : 1) : 65536);
+}
+
+cudaError_t launch_scatter(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
+                           const float2 *src, float2 *dst, int accumulate, cudaStream_t s) {
+    PermParams P;
+    P.rank = rank;
+    int64_t total = 1;
+    for (int d = 0; d < rank; ++d) {
+        P.dims[d] = dims[d];
+        P.strides[d] = strides[d];
+        total *= dims[d];
+    }
+    if (total == 0) return cudaSuccess;
+    scatter_kernel<<<grid_for(total), 256, 0, s>>>(P, total, offset, src, dst, accumulate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate_gather_c128(const float2 *src, const int64_t *index, double *dst,
+                                          int64_t count, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    accumulate_gather_c128_kernel<<<grid_for(count), 256, 0, s>>>(
+        src, index, reinterpret_cast<double2 *>(dst), count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_grad(const double *g, const int64_t *index, float2 *grad_root,
+                             int64_t count, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    seed_grad_kernel<<<grid_for(count), 256, 0, s>>>(reinterpret_cast<const double2 *>(g), index,
+                                                    grad_root, count);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,563 @@
+"""Tensor-network planning for qcs_contract_tree (host side).
+
+circuit -> tensor network (Section 2.2: |0> and <x| as rank-1 tensors, a
+k-qubit gate as a rank-2k tensor, wires as shared indices) -> seeded greedy
+contraction order -> slicing (Section 5.3: fixed values of chosen indices,
+results summed) -> a TTGT plan (Section 1: each pairwise contraction
+reshaped to one CGEMM) that libqcs executes.  Nothing numerical happens here
+beyond building the leaf tensors; every contraction runs in the CUDA library.
+
+Storage convention: every tensor is stored first-index-fastest (Fortran
+order) over its label list; a tensor whose labels are (M..., K...) is the
+column-major M x K matrix.
+
+Instances.  Sliced indices and the bitstring index of a batch of closed
+amplitudes are "instance labels": they are not contracted; each instance
+fixes their values, which moves each leaf's base by a constant offset, and
+the executor adds the root of every instance into its output slot (one slot
+per bitstring; the slices of a bitstring share it).
+"""
+from __future__ import annotations
+
+import ctypes
+import heapq
+import itertools
+import math
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _lib
+
+BATCH = -1  # label of the bitstring index of batched <x| leaves
+
+
+@dataclass
+class Leaf:
+    data: np.ndarray          # complex64, 1-D, first-index-fastest over ``labels``
+    labels: List[int]
+    dims: List[int]
+    kind: str = "gate"        # "init", "gate", "final"
+    gate: int = -1            # index of the gate in the circuit, for gate leaves
+
+
+@dataclass
+class Network:
+    leaves: List[Leaf]
+    output: List[int]         # open labels, in the order of the returned result
+    dims: Dict[int, int]
+    batch: int = 0            # number of bitstrings in the BATCH label (0: none)
+
+
+def _fortran_flat(t: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(t).ravel(order="F")).astype(np.complex64)
+
+
+def circuit_network(circ, bitstrings: Optional[np.ndarray] = None) -> Network:
+    """The network of <x|U|0> for a circuit (qcs_inputs.Circuit).
+
+    bitstrings None: output legs open (the result is the state U|0>, ordered
+    as numpy's C order over qubits 0..n-1).  Otherwise a (B, n) array: the <x|
+    leaves carry the BATCH label with one column per bitstring.
+    """
+    n = circ.n_qubits
+    leaves: List[Leaf] = []
+    dims: Dict[int, int] = {}
+    wire = list(range(n))
+    for q in range(n):
+        dims[q] = 2
+        leaves.append(Leaf(np.array([1, 0], np.complex64), [q], [2], "init"))
+    nxt = n
+    for gi, g in enumerate(circ.gates):
+        k = len(g.qubits)
+        new = list(range(nxt, nxt + k))
+        nxt += k
+        for l in new:
+            dims[l] = 2
+        t = np.asarray(g.matrix, dtype=np.complex128).reshape((2,) * (2 * k))
+        labels = new + [wire[q] for q in g.qubits]
+        leaves.append(Leaf(_fortran_flat(t), labels, [2] * (2 * k), "gate", gi))
+        for i, q in enumerate(g.qubits):
+            wire[q] = new[i]
+    if bitstrings is None:
+        return Network(leaves, [wire[q] for q in range(n)], dims)
+    bs = np.asarray(bitstrings, dtype=np.int64).reshape(-1, n)
+    B = bs.shape[0]
+    dims[BATCH] = B
+    for q in range(n):
+        v = np.zeros((2, B), np.complex64)
+        v[bs[:, q], np.arange(B)] = 1.0
+        leaves.append(Leaf(_fortran_flat(v), [wire[q], BATCH], [2, B], "final"))
+    return Network(leaves, [], dims, batch=B)
+
+
+# ---------------------------------------------------------------------------
+# contraction order
+# ---------------------------------------------------------------------------
+
+def greedy_order(net: Network, seed: int = 2, skip: Sequence[int] = ()) -> List[Tuple[int, int]]:
+    """Seeded greedy order: repeatedly contract the connected pair with the
+    smallest size(result) - size(a) - size(b) (log-sizes, a random jitter
+    breaks ties).  Labels in ``skip`` (instance labels) are ignored.
+    Returns SSA pairs: tensor ids, each contraction appending a new id."""
+    rng = np.random.default_rng(seed)
+    skip = set(skip)
+    labs: List[frozenset] = [frozenset(l for l in lf.labels if l not in skip) for lf in net.leaves]
+    keep = set(net.output)
+    count: Dict[int, int] = {}
+    where: Dict[int, set] = {}
+    for i, ls in enumerate(labs):
+        for l in ls:
+            count[l] = count.get(l, 0) + 1
+            where.setdefault(l, set()).add(i)
+    alive = set(range(len(labs)))
+    logd = {l: math.log2(d) for l, d in net.dims.items()}
+
+    def lsize(ls):
+        return sum(logd[l] for l in ls)
+
+    def result(i, j):
+        a, b = labs[i], labs[j]
+        return frozenset(l for l in a | b
+                         if not (l in a and l in b and count[l] == 2 and l not in keep))
+
+    def score(i, j):
+        r = result(i, j)
+        return (2.0 ** lsize(r) - 2.0 ** lsize(labs[i]) - 2.0 ** lsize(labs[j])) \
+            * (1.0 + 1e-6 * rng.random()), r
+
+    heap = []
+    for l, ws in where.items():
+        for i, j in itertools.combinations(sorted(ws), 2):
+            sc, _ = score(i, j)
+            heapq.heappush(heap, (sc, i, j))
+    order = []
+    while len(alive) > 1:
+        pair = None
+        while heap:
+            sc, i, j = heapq.heappop(heap)
+            if i in alive and j in alive:
+                pair = (i, j)
+                break
+        if pair is None:  # disconnected components: join the two smallest
+            i, j = sorted(alive, key=lambda u: (lsize(labs[u]), u))[:2]
+            pair = (min(i, j), max(i, j))
+        i, j = pair
+        r = result(i, j)
+        for u in (i, j):
+            for l in labs[u]:
+                count[l] -= 1
+                where[l].discard(u)
+            alive.discard(u)
+        new = len(labs)
+        labs.append(r)
+        for l in r:
+            count[l] = count.get(l, 0) + 1
+            where.setdefault(l, set()).add(new)
+        alive.add(new)
+        order.append((i, j))
+        nb = set()
+        for l in r:
+            nb |= where[l]
+        nb.discard(new)
+        for u in nb:
+            sc, _ = score(min(u, new), max(u, new))
+            heapq.heappush(heap, (sc, min(u, new), max(u, new)))
+    return order
+
+
+def intermediates(net: Network, order, skip: Sequence[int] = ()) -> List[frozenset]:
+    """Label sets of every intermediate of an SSA order (instance labels removed)."""
+    skip = set(skip)
+    labs = [frozenset(l for l in lf.labels if l not in skip) for lf in net.leaves]
+    count: Dict[int, int] = {}
+    for ls in labs:
+        for l in ls:
+            count[l] = count.get(l, 0) + 1
+    keep = set(net.output)
+    out = []
+    for i, j in order:
+        a, b = labs[i], labs[j]
+        r = frozenset(l for l in a | b if not (l in a and l in b and count[l] == 2 and l not in keep))
+        for l in a:
+            count[l] -= 1
+        for l in b:
+            count[l] -= 1
+        for l in r:
+            count[l] = count.get(l, 0) + 1
+        labs.append(r)
+        out.append(r)
+    return out
+
+
+def choose_slices(net: Network, order, n_labels: Optional[int] = None,
+                  max_log2_size: Optional[float] = None, skip: Sequence[int] = ()) -> List[int]:
+    """Pick indices to slice (Section 5.3): repeatedly the index that
+    removes the most work -- the one carried by the largest intermediates,
+    weighted by their sizes -- until ``n_labels`` are chosen or the largest
+    intermediate is at most 2**max_log2_size elements."""
+    sliced: List[int] = []
+    keep = set(net.output) | set(skip)
+    while True:
+        inter = intermediates(net, order, list(skip) + sliced)
+        logs = [sum(math.log2(net.dims[l]) for l in r) for r in inter]
+        biggest = max(logs) if logs else 0.0
+        if n_labels is not None and len(sliced) >= n_labels:
+            break
+        if n_labels is None and (max_log2_size is None or biggest <= max_log2_size):
+            break
+        weight: Dict[int, float] = {}
+        for r, lg in zip(inter, logs):
+            if lg < biggest - 2:
+                continue
+            for l in r:
+                if l not in keep:
+                    weight[l] = weight.get(l, 0.0) + 2.0 ** (lg - biggest)
+        if not weight:
+            break
+        sliced.append(min(weight, key=lambda l: (-weight[l], l)))
+    return sliced
+
+
+# ---------------------------------------------------------------------------
+# TTGT plan
+# ---------------------------------------------------------------------------
+
+def _fortran_strides(dims: Sequence[int]) -> List[int]:
+    st, acc = [], 1
+    for d in dims:
+        st.append(acc)
+        acc *= d
+    return st
+
+
+def _compress(dims: List[int], strides: List[int]) -> Tuple[List[int], List[int]]:
+    """Merge adjacent dims that are contiguous in the source; drop size 1."""
+    od, os_ = [], []
+    for d, s in zip(dims, strides):
+        if d == 1:
+            continue
+        if od and os_[-1] * od[-1] == s:
+            od[-1] *= d
+        else:
+            od.append(d)
+            os_.append(s)
+    return od, os_
+
+
+@dataclass
+class Step:
+    a: int
+    b: int
+    direct_a: int
+    direct_b: int
+    m: int
+    n: int
+    k: int
+    map_a: Tuple[List[int], List[int]]
+    map_b: Tuple[List[int], List[int]]
+    labels_out: List[int]
+    mode: int = 0
+
+
+@dataclass
+class Plan:
+    net: Network
+    steps: List[Step]
+    sliced: List[int]
+    instance_offset: np.ndarray   # (n_instances, n_leaves) int64
+    instance_slot: np.ndarray     # (n_instances,) int32
+    n_slots: int
+    out_size: int
+    out_index: Optional[np.ndarray]
+    root_labels: List[int]
+    max_log2_size: float = 0.0
+    flops: float = 0.0
+
+    @property
+    def n_instances(self) -> int:
+        return int(self.instance_slot.shape[0])
+
+
+def build_plan(net: Network, order, sliced: Sequence[int] = (), mode: int = 0,
+               outputs: Optional[np.ndarray] = None) -> Plan:
+    """Turn an SSA order into executor steps.
+
+    outputs: for an open network, an optional (B, n_out) array of values of
+    the output labels to gather (e.g. bitstrings); default: the whole
+    result in numpy C order over ``net.output``.
+    """
+    sliced = list(sliced)
+    inst = set(sliced) | ({BATCH} if net.batch else set())
+    nl = len(net.leaves)
+    labels: List[List[int]] = [list(lf.labels) for lf in net.leaves]   # storage labels
+    strides: List[Dict[int, int]] = [dict(zip(lf.labels, _fortran_strides(lf.dims)))
+                                     for lf in net.leaves]
+    contiguous = [not (set(lf.labels) & inst) for lf in net.leaves]
+    count: Dict[int, int] = {}
+    for ls in labels:
+        for l in ls:
+            if l not in inst:
+                count[l] = count.get(l, 0) + 1
+    keep = set(net.output)
+    steps: List[Step] = []
+    max_log2 = 0.0
+    flops = 0.0
+    for (i, j) in order:
+        la = [l for l in labels[i] if l not in inst]
+        lb = [l for l in labels[j] if l not in inst]
+        shared = [l for l in la if l in lb]
+        hyper = [l for l in shared if count[l] > 2 or l in keep]
+        if hyper:
+            raise ValueError(f"hyperedge labels {hyper} are not supported")
+        K_a = shared
+        K_b = [l for l in lb if l in shared]
+        M = [l for l in la if l not in shared]
+        N = [l for l in lb if l not in shared]
+        a_dir = {"N": contiguous[i] and la == M + K_a, "T": contiguous[i] and la == K_a + M}
+        b_dir = {"N": contiguous[j] and lb == K_b + N, "T": contiguous[j] and lb == N + K_b}
+        if (a_dir["N"] or a_dir["T"]):
+            K = K_a
+            if K_b != K:
+                b_dir = {"N": False, "T": False}
+        elif (b_dir["N"] or b_dir["T"]):
+            K = K_b
+        else:
+            K = K_a
+            b_dir = {"N": contiguous[j] and lb == K + N, "T": contiguous[j] and lb == N + K}
+        d = net.dims
+        m = int(np.prod([d[l] for l in M], dtype=np.int64)) if M else 1
+        n = int(np.prod([d[l] for l in N], dtype=np.int64)) if N else 1
+        k = int(np.prod([d[l] for l in K], dtype=np.int64)) if K else 1
+        map_a = _compress([d[l] for l in M + K], [strides[i][l] for l in M + K])
+        map_b = _compress([d[l] for l in K + N], [strides[j][l] for l in K + N])
+        if len(map_a[0]) > _lib.MAX_RANK or len(map_b[0]) > _lib.MAX_RANK:
+            raise ValueError("operand rank beyond QCS_MAX_RANK after compression")
+        direct_a = 0 if a_dir["N"] else (1 if a_dir["T"] else -1)
+        direct_b = 0 if b_dir["N"] else (1 if b_dir["T"] else -1)
+        out_labels = M + N
+        steps.append(Step(i, j, direct_a, direct_b, m, n, k, map_a, map_b, out_labels, mode))
+        for l in la + lb:
+            count[l] -= 1
+        for l in out_labels:
+            count[l] = count.get(l, 0) + 1
+        labels.append(out_labels)
+        strides.append(dict(zip(out_labels, _fortran_strides([d[l] for l in out_labels]))))
+        contiguous.append(True)
+        max_log2 = max(max_log2, math.log2(m * n))
+        flops += 8.0 * m * n * k
+    root = len(labels) - 1 if order else 0
+    root_labels = [l for l in labels[root] if l not in inst]
+    if sorted(root_labels) != sorted(net.output):
+        raise ValueError("the order does not contract the network to its output labels")
+    rs = strides[root]
+    if net.output:
+        if outputs is None:
+            nout = len(net.output)
+            vals = np.array(list(itertools.product(*[range(net.dims[l]) for l in net.output])),
+                            dtype=np.int64).reshape(-1, nout)
+        else:
+            vals = np.asarray(outputs, dtype=np.int64)
+        out_index = vals @ np.array([rs[l] for l in net.output], dtype=np.int64)
+        out_size = int(out_index.shape[0])
+    else:
+        out_index = None
+        out_size = 1
+    # instances: bitstring x slice assignment
+    slice_vals = list(itertools.product(*[range(net.dims[l]) for l in sliced])) or [()]
+    B = net.batch if net.batch else 1
+    offs = np.zeros((B * len(slice_vals), nl), dtype=np.int64)
+    slots = np.zeros(B * len(slice_vals), dtype=np.int32)
+    leaf_strides = strides[:nl]
+    r = 0
+    for b in range(B):
+        for sv in slice_vals:
+            val = dict(zip(sliced, sv))
+            if net.batch:
+                val[BATCH] = b
+            for li in range(nl):
+                offs[r, li] = sum(val[l] * leaf_strides[li][l] for l in net.leaves[li].labels
+                                  if l in val)
+            slots[r] = b
+            r += 1
+    return Plan(net, steps, sliced, offs, slots, B, out_size, out_index, root_labels,
+                max_log2, flops)
+
+
+# ---------------------------------------------------------------------------
+# device side: leaves, ctypes plan, forward / backward through libqcs
+# ---------------------------------------------------------------------------
+
+class CompiledPlan:
+    """A plan marshalled into qcs_tree_t, with its leaves on the device."""
+
+    def __init__(self, plan: Plan, device="cuda", leaf_data: Optional[List] = None):
+        import torch
+
+        self.plan = plan
+        self.device = torch.device(device)
+        L = _lib
+        steps = (L.qcs_step_t * max(len(plan.steps), 1))()
+        for s, st in enumerate(plan.steps):
+            c = steps[s]
+            c.a, c.b, c.direct_a, c.direct_b = st.a, st.b, st.direct_a, st.direct_b
+            c.m, c.n, c.k, c.mode = st.m, st.n, st.k, st.mode
+            for mp, dst in ((st.map_a, c.map_a), (st.map_b, c.map_b)):
+                dst.rank = len(mp[0])
+                for q, (dd, ss) in enumerate(zip(*mp)):
+                    dst.dims[q] = dd
+                    dst.strides[q] = ss
+        self._steps = steps
+        nl = len(plan.net.leaves)
+        self._leaf_size = (ctypes.c_int64 * nl)(*[lf.data.size for lf in plan.net.leaves])
+        offs = np.ascontiguousarray(plan.instance_offset.reshape(-1), dtype=np.int64)
+        self._offs = offs
+        slots = np.ascontiguousarray(plan.instance_slot, dtype=np.int32)
+        self._slots = slots
+        self._out_index = (np.ascontiguousarray(plan.out_index, dtype=np.int64)
+                           if plan.out_index is not None else None)
+        t = L.qcs_tree_t()
+        t.n_leaves = nl
+        t.n_steps = len(plan.steps)
+        t.n_instances = plan.n_instances
+        t.n_slots = plan.n_slots
+        t.leaf_size = self._leaf_size
+        t.instance_offset = offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        t.instance_slot = slots.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        t.steps = steps
+        t.out_size = plan.out_size
+        t.out_index = (self._out_index.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+                       if self._out_index is not None else None)
+        self.tree = t
+        if leaf_data is None:
+            leaf_data = [torch.from_numpy(lf.data).to(self.device) for lf in plan.net.leaves]
+        self.leaves = leaf_data
+
+    def _ptrs(self, tensors):
+        return (ctypes.c_void_p * len(tensors))(*[ctypes.c_void_p(t.data_ptr()) for t in tensors])
+
+    def forward(self, h, leaves=None):
+        """Contract every instance; returns complex128 (n_slots, out_size)."""
+        import torch
+
+        leaves = self.leaves if leaves is None else leaves
+        out = torch.empty((self.plan.n_slots, self.plan.out_size), dtype=torch.complex128,
+                          device=self.device)
+        info = _lib.qcs_run_info_t()
+        ptrs = self._ptrs([t.contiguous() for t in leaves])
+        _lib.check(h.lib.qcs_contract_tree(h.ptr, ctypes.byref(self.tree), ptrs,
+                                           ctypes.c_void_p(out.data_ptr()), ctypes.byref(info)),
+                   "qcs_contract_tree")
+        self.last_info = info
+        return out
+
+    def backward(self, h, grad_out, leaves=None):
+        """Leaf gradients (list of complex64 tensors) for dL/d out = grad_out
+        (torch convention: dL/dRe + i dL/dIm)."""
+        import torch
+
+        leaves = [t.contiguous() for t in (self.leaves if leaves is None else leaves)]
+        grads = [torch.zeros_like(t) for t in leaves]
+        g = grad_out.to(torch.complex128).contiguous()
+        info = _lib.qcs_run_info_t()
+        _lib.check(h.lib.qcs_contract_tree_backward(
+            h.ptr, ctypes.byref(self.tree), self._ptrs(leaves), ctypes.c_void_p(g.data_ptr()),
+            self._ptrs(grads), ctypes.byref(info)), "qcs_contract_tree_backward")
+        self.last_info = info
+        return grads
+
+
+def info_dict(info) -> dict:
+    return {"seconds": info.seconds, "gemm_count": info.gemm_count,
+            "gather_count": info.gather_count, "mode_count": list(info.mode_count),
+            "workspace_bytes": info.workspace_bytes, "flops": info.flops}
+
+
+# ---------------------------------------------------------------------------
+# differentiation: torch.autograd.Function over qcs_contract_tree
+# ---------------------------------------------------------------------------
+
+def _torch_fsim_leaf(theta, phi):
+    """First-index-fastest flat complex64 fSim(theta, phi) tensor, built with
+    torch ops so that autograd reaches theta and phi."""
+    import torch
+
+    c = torch.cos(theta).to(torch.complex64)
+    s = torch.sin(theta).to(torch.complex64)
+    e = torch.exp(-1j * phi.to(torch.complex64))
+    one = torch.ones((), dtype=torch.complex64, device=theta.device)
+    zero = torch.zeros((), dtype=torch.complex64, device=theta.device)
+    G = torch.stack([
+        torch.stack([one, zero, zero, zero]),
+        torch.stack([zero, c, -1j * s, zero]),
+        torch.stack([zero, -1j * s, c, zero]),
+        torch.stack([zero, zero, zero, e]),
+    ])
+    return G.reshape(2, 2, 2, 2).permute(3, 2, 1, 0).reshape(-1)
+
+
+def torch_leaves(net: Network, circ, params, device="cuda"):
+    """Device leaf tensors of ``net``; the fSim leaves are functions of
+    ``params`` ((n_fsim, 2) real tensor: theta, phi per fSim gate in circuit
+    order), every other leaf is constant."""
+    import torch
+
+    fs = {g: i for i, g in enumerate(circ.fsim_indices())}
+    out = []
+    for lf in net.leaves:
+        if lf.kind == "gate" and lf.gate in fs:
+            p = params[fs[lf.gate]]
+            out.append(_torch_fsim_leaf(p[0], p[1]).to(device))
+        else:
+            out.append(torch.from_numpy(lf.data).to(device))
+    return out
+
+
+def _make_function():
+    import torch
+
+    class ContractTree(torch.autograd.Function):
+        """out = qcs_contract_tree(plan, leaves); the backward runs
+        qcs_contract_tree_backward (adjoint emulated CGEMMs, recompute per
+        instance)."""
+
+        @staticmethod
+        def forward(ctx, cp, h, *leaves):
+            ctx.cp = cp
+            ctx.h = h
+            ctx.save_for_backward(*leaves)
+            return cp.forward(h, list(leaves))
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            leaves = ctx.saved_tensors
+            grads = ctx.cp.backward(ctx.h, grad_out, list(leaves))
+            return (None, None, *[g if t.requires_grad else None for g, t in zip(grads, leaves)])
+
+    return ContractTree
+
+
+_FN = None
+
+
+def contract(cp: CompiledPlan, h, leaves):
+    """Differentiable contraction of ``leaves`` (complex64 device tensors)."""
+    global _FN
+    if _FN is None:
+        _FN = _make_function()
+    return _FN.apply(cp, h, *leaves)
+
+
+def plan_circuit(circ, bitstrings=None, seed: int = 2, n_slices: int = 0,
+                 max_log2_size: Optional[float] = None, mode: int = 0) -> Plan:
+    """circuit -> network -> greedy order (seeded) -> slices -> plan.
+    ``n_slices``: number of sliced indices (2**n_slices slices)."""
+    net = circuit_network(circ, bitstrings)
+    skip = [BATCH] if net.batch else []
+    order = greedy_order(net, seed=seed, skip=skip)
+    sliced = []
+    if n_slices or max_log2_size is not None:
+        sliced = choose_slices(net, order, n_labels=n_slices or None,
+                               max_log2_size=max_log2_size, skip=skip)
+    return build_plan(net, order, sliced, mode=mode)

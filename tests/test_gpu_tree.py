@@ -1,0 +1,146 @@
+"""GPU parity of the contraction-tree executor and its adjoint (through the
+C ABI) against the FP64 oracle: amplitudes of random grid circuits (closed,
+sliced, batched bitstrings, open), and the gradient of sum log|a|^2 with
+respect to the fSim parameters."""
+import numpy as np
+import pytest
+
+import oracle
+import qcs_inputs as qi
+from gpu_helpers import lib, need_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    need_gpu()
+    hd = lib().Handle(tol=0.0, size_rule=True)
+    yield hd
+    hd.close()
+
+
+def _tn():
+    import paper_2303_08989_gb300.tn as tn
+
+    return tn
+
+
+def _run(h, plan):
+    tn = _tn()
+    cp = tn.CompiledPlan(plan)
+    out = cp.forward(h)
+    torch.cuda.synchronize()
+    h.sync()
+    return out.cpu().numpy(), cp.last_info
+
+
+def test_plain_method_small_grid_fp32(h):
+    """3x4 grid, depth 8, 64 random bitstrings, greedy order; the size rule
+    sends these small GEMMs to plain FP32 on the GPU."""
+    tn = _tn()
+    circ = qi.random_grid_circuit(3, 4, 8, seed=0)
+    bits = qi.random_bitstrings(12, 64, seed=1)
+    plan = tn.plan_circuit(circ, bits, seed=2)
+    got, info = _run(h, plan)
+    ref = oracle.sv_amplitudes(circ, bits)
+    a = got[:, 0]
+    assert oracle.fidelity(ref, a) >= 1 - 1e-5
+    assert np.max(np.abs(a - ref)) <= 1e-5 * np.max(np.abs(ref))
+    assert info.gemm_count == 64 * len(plan.steps)
+    assert info.mode_count[4] == info.gemm_count  # all plain FP32 under the size rule
+
+
+@pytest.mark.parametrize("mode", ["fp16x", "tf32x", "fp16x_scaled", "auto"])
+def test_emulated_modes_on_every_step(h, mode):
+    tn = _tn()
+    q = lib()
+    circ = qi.random_grid_circuit(3, 4, 8, seed=0)
+    bits = qi.random_bitstrings(12, 8, seed=1)
+    plan = tn.plan_circuit(circ, bits, seed=2, mode=q.MODE_BY_NAME[mode])
+    h.set_size_rule(False)
+    try:
+        got, info = _run(h, plan)
+    finally:
+        h.set_size_rule(True)
+    ref = oracle.sv_amplitudes(circ, bits)
+    assert oracle.fidelity(ref, got[:, 0]) >= 1 - 1e-5
+    assert np.max(np.abs(got[:, 0] - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+def test_sliced_amplitudes(h):
+    tn = _tn()
+    circ = qi.random_grid_circuit(3, 4, 8, seed=3)
+    bits = qi.random_bitstrings(12, 4, seed=4)
+    plan = tn.plan_circuit(circ, bits, seed=2, n_slices=3)
+    assert plan.n_instances == 4 * 8
+    got, _ = _run(h, plan)
+    ref = oracle.sv_amplitudes(circ, bits)
+    assert oracle.fidelity(ref, got[:, 0]) >= 1 - 1e-5
+    # the oracle's own sliced contraction agrees
+    net = tn.circuit_network(circ, bits[:1])
+    assert abs(oracle.amplitude(circ, bits[0], sliced=plan.sliced) - ref[0]) < 1e-12
+
+
+def test_open_network_state_vector(h):
+    tn = _tn()
+    circ = qi.random_grid_circuit(2, 3, 6, seed=5)
+    plan = tn.plan_circuit(circ, None, seed=1, n_slices=1)
+    got, _ = _run(h, plan)
+    ref = oracle.statevector(circ).ravel()
+    assert oracle.fidelity(ref, got[0]) >= 1 - 1e-5
+    assert abs(np.sum(np.abs(got[0]) ** 2) - 1.0) < 1e-5
+
+
+def _grad_check(h, mode, n_slices, size_rule):
+    tn = _tn()
+    q = lib()
+    circ = qi.random_grid_circuit(2, 3, 4, seed=4, theta=None, phi=None, param_seed=5)
+    bits = qi.random_bitstrings(6, 8, seed=6)
+    plan = tn.plan_circuit(circ, bits, seed=2, n_slices=n_slices, mode=q.MODE_BY_NAME[mode])
+    params0 = np.array([g.params for g in circ.gates if g.name == "fsim"], dtype=np.float64)
+    params = torch.tensor(params0, dtype=torch.float32, device="cuda", requires_grad=True)
+    cp = tn.CompiledPlan(plan, leaf_data=[])
+    h.set_size_rule(size_rule)
+    try:
+        leaves = tn.torch_leaves(plan.net, circ, params)
+        amps = tn.contract(cp, h, leaves)
+        loss = torch.log(amps.abs() ** 2).sum()
+        loss.backward()
+        torch.cuda.synchronize()
+        h.sync()
+    finally:
+        h.set_size_rule(True)
+    L_ref, g_ref = oracle.loss_and_grad(circ, bits)
+    g = params.grad.double().cpu().numpy()
+    assert abs(loss.item() - L_ref) < 1e-4 * abs(L_ref)
+    rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    assert rel < 1e-4, rel
+    return rel
+
+
+@pytest.mark.parametrize("mode,n_slices,size_rule", [("auto", 0, True), ("fp32", 2, True),
+                                                     ("tf32x", 1, False), ("fp16x", 0, False)])
+def test_backward_matches_oracle_gradient(h, mode, n_slices, size_rule):
+    _grad_check(h, mode, n_slices, size_rule)
+
+
+def test_invalid_plan_is_rejected_before_launch(h):
+    tn = _tn()
+    from paper_2303_08989_gb300 import _lib as L
+
+    circ = qi.random_grid_circuit(2, 2, 2, seed=1)
+    plan = tn.plan_circuit(circ, qi.random_bitstrings(4, 2, seed=1))
+    cp = tn.CompiledPlan(plan)
+    cp._steps[0].map_a.strides[0] = 10 ** 6  # reads far outside the leaf
+    out = torch.zeros((plan.n_slots, 1), dtype=torch.complex128, device="cuda")
+    import ctypes
+
+    rc = h.lib.qcs_contract_tree(h.ptr, ctypes.byref(cp.tree), cp._ptrs(cp.leaves),
+                                 ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == L.QCS_ERR_INVALID_ARG
+    cp2 = tn.CompiledPlan(plan)
+    cp2._steps[1].a = len(plan.net.leaves) + 5  # refers to a later step
+    rc = h.lib.qcs_contract_tree(h.ptr, ctypes.byref(cp2.tree), cp2._ptrs(cp2.leaves),
+                                 ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == L.QCS_ERR_INVALID_ARG

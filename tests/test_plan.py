@@ -1,0 +1,92 @@
+"""Host logic of the contraction planner (no GPU): the plan, interpreted
+with numpy, must give the oracle's amplitudes, for closed and open networks,
+with slicing and bitstring batches; the maps must be bijections."""
+import numpy as np
+import pytest
+
+import oracle
+import qcs_inputs as qi
+from plan_sim import gather_index, run
+
+tn = pytest.importorskip("paper_2303_08989_gb300.tn")
+
+
+def _leaves(plan):
+    return [lf.data for lf in plan.net.leaves]
+
+
+def test_closed_amplitudes_batched_bitstrings():
+    circ = qi.random_grid_circuit(3, 4, 8, seed=0)
+    bits = qi.random_bitstrings(12, 16, seed=1)
+    plan = tn.plan_circuit(circ, bits, seed=2)
+    got = run(plan, _leaves(plan))[:, 0]
+    ref = oracle.sv_amplitudes(circ, bits)
+    np.testing.assert_allclose(got, ref, atol=1e-6)  # complex64 leaves, FP64 arithmetic
+    assert plan.n_instances == 16 and plan.n_slots == 16
+
+
+def test_sliced_plan_sums_to_the_amplitude():
+    circ = qi.random_grid_circuit(3, 3, 6, seed=4)
+    bits = qi.random_bitstrings(9, 3, seed=5)
+    plan = tn.plan_circuit(circ, bits, seed=2, n_slices=3)
+    assert len(plan.sliced) == 3 and plan.n_instances == 3 * 8
+    got = run(plan, _leaves(plan))[:, 0]
+    np.testing.assert_allclose(got, oracle.sv_amplitudes(circ, bits), atol=1e-6)
+
+
+def test_open_network_gives_the_state_vector():
+    circ = qi.random_grid_circuit(2, 3, 5, seed=6)
+    plan = tn.plan_circuit(circ, None, seed=3)
+    got = run(plan, _leaves(plan))[0]
+    np.testing.assert_allclose(got, oracle.statevector(circ).ravel(), atol=1e-6)
+    # bitstring gather from the open result
+    bits = qi.random_bitstrings(6, 5, seed=7)
+    net = tn.circuit_network(circ, None)
+    order = tn.greedy_order(net, seed=3)
+    p2 = tn.build_plan(net, order, outputs=bits)
+    np.testing.assert_allclose(run(p2, _leaves(p2))[0], oracle.sv_amplitudes(circ, bits), atol=1e-6)
+
+
+def test_open_network_sliced():
+    circ = qi.random_grid_circuit(2, 3, 6, seed=8)
+    net = tn.circuit_network(circ, None)
+    order = tn.greedy_order(net, seed=1)
+    sliced = tn.choose_slices(net, order, n_labels=2)
+    plan = tn.build_plan(net, order, sliced)
+    np.testing.assert_allclose(run(plan, _leaves(plan))[0], oracle.statevector(circ).ravel(),
+                               atol=1e-6)
+
+
+def test_maps_are_bijections_and_within_bounds():
+    circ = qi.random_grid_circuit(3, 4, 8, seed=0)
+    plan = tn.plan_circuit(circ, qi.random_bitstrings(12, 4, seed=1), n_slices=2)
+    sizes = [lf.data.size for lf in plan.net.leaves]
+    for st in plan.steps:
+        sizes.append(st.m * st.n)
+    for st in plan.steps:
+        for mp, src, elems in ((st.map_a, st.a, st.m * st.k), (st.map_b, st.b, st.k * st.n)):
+            idx = gather_index(*mp)
+            assert idx.size == elems and len(np.unique(idx)) == elems
+            base = plan.instance_offset[:, src].max() if src < len(plan.net.leaves) else 0
+            assert base + idx.max() < sizes[src]
+
+
+def test_greedy_order_is_seeded_and_contracts_everything():
+    circ = qi.random_grid_circuit(4, 5, 12, seed=3)
+    net = tn.circuit_network(circ, None)
+    o1 = tn.greedy_order(net, seed=2)
+    o2 = tn.greedy_order(net, seed=2)
+    assert o1 == o2
+    assert len(o1) == len(net.leaves) - 1
+    inter = tn.intermediates(net, o1)
+    assert sorted(inter[-1]) == sorted(net.output)
+
+
+def test_slicer_bounds_the_largest_intermediate():
+    circ = qi.random_grid_circuit(4, 5, 12, seed=3)
+    net = tn.circuit_network(circ, None)
+    order = tn.greedy_order(net, seed=2)
+    base = max(len(r) for r in tn.intermediates(net, order))
+    sliced = tn.choose_slices(net, order, max_log2_size=base - 3)
+    after = max(len(r) for r in tn.intermediates(net, order, sliced))
+    assert after <= base - 3 and len(sliced) >= 3
