@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--sample-rows", type=int, default=16)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--no-tree", action="store_true", help="skip the contraction-tree legs")
+    p.add_argument("--tree-slices", type=int, default=4,
+                   help="slices of the 30-qubit network timed per mode")
     return p.parse_args()
 
 
@@ -381,11 +384,123 @@ def main():
                       "ms_per_step": ems, "steps": ek}
         del hA, hB, hC, Ad, Bd, Cd
 
+    if not args.no_tree:
+        out.update(tree_legs(args, q, torch, dev, rank))
+
     if rank == 0:
         print(json.dumps(out), flush=True)
     h.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _time_plan(torch, cp, h, instances=None, reps=1):
+    """Seconds per call of qcs_contract_tree (CUDA events), optionally on the
+    first ``instances`` instances of the plan only."""
+    if instances is not None:
+        cp.tree.n_instances = instances
+    cp.forward(h)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        out = cp.forward(h)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps * 1e-3, out
+
+
+def tree_legs(args, q, torch, dev, rank):
+    """The contraction half of the metric (s/slice, AUTO vs all-FP32), the
+    plain small-grid amplitudes and the differentiated workload."""
+    import numpy as np
+
+    import paper_2303_08989_gb300.tn as tn
+    import qcs_inputs as qi
+
+    res = {}
+    h = q.Handle(tol=args.tol, size_rule=True)
+    # 30-qubit 5x6 grid, depth 14, sliced on 6 indices (64 slices), one bitstring
+    circ = qi.random_grid_circuit(5, 6, 14, seed=0)
+    bits = qi.random_bitstrings(30, 1, seed=1)
+    per = {}
+    for mode in ("auto", "fp32"):
+        plan = tn.plan_circuit(circ, bits, seed=2, n_slices=6, mode=q.MODE_BY_NAME[mode])
+        cp = tn.CompiledPlan(plan, device=dev)
+        ns = min(args.tree_slices, plan.n_instances)
+        secs, out = _time_plan(torch, cp, h, instances=ns)
+        info = tn.info_dict(cp.last_info)
+        per[mode] = {"s_per_slice": secs / ns, "slices_timed": ns,
+                     "tflops": info["flops"] / secs / 1e12,
+                     "gemms_per_slice": info["gemm_count"] / ns,
+                     "gemm_modes": dict(zip(["auto", "fp16x", "fp16x_scaled", "tf32x", "fp32",
+                                             "bf16x3"], info["mode_count"]))}
+        res_plan = plan
+    res["contraction"] = {
+        "workload": "5x6 grid random circuit, depth 14, seeded greedy order, 6 sliced indices "
+                    "(64 slices), 1 bitstring; AUTO-%g vs all-FP32" % args.tol,
+        "slices_total": res_plan.n_instances, "flops_per_slice": res_plan.flops,
+        "max_intermediate_log2": res_plan.max_log2_size,
+        "auto": per["auto"], "fp32": per["fp32"],
+        "speedup_vs_fp32": per["fp32"]["s_per_slice"] / per["auto"]["s_per_slice"],
+    }
+    # plain method, smallest size: 3x4 grid, depth 8, 64 bitstrings (FP32 path by the size rule)
+    c0 = qi.random_grid_circuit(3, 4, 8, seed=0)
+    b0 = qi.random_bitstrings(12, 64, seed=1)
+    p0 = tn.plan_circuit(c0, b0, seed=2)
+    cp0 = tn.CompiledPlan(p0, device=dev)
+    secs0, out0 = _time_plan(torch, cp0, h, reps=3)
+    res["plain_small"] = {"workload": "3x4 grid, depth 8, 64 bitstrings, greedy order",
+                          "s_per_batch": secs0, "gemms": cp0.last_info.gemm_count}
+    if rank == 0:
+        import oracle
+
+        ref = oracle.sv_amplitudes(c0, b0)
+        res["plain_small"]["fidelity_vs_fp64"] = oracle.fidelity(ref, out0.cpu().numpy()[:, 0])
+    # differentiation: 4x5 grid, depth 12, free fSim parameters, 256 bitstrings
+    c4 = qi.random_grid_circuit(4, 5, 12, seed=0, theta=None, phi=None, param_seed=3)
+    b4 = qi.random_bitstrings(20, 256, seed=1)
+    p0s = np.array([g.params for g in c4.gates if g.name == "fsim"])
+    diff = {}
+    for mode in ("auto", "fp32"):
+        net = tn.circuit_network(c4, None)
+        order = tn.greedy_order(net, seed=2)
+        sliced = tn.choose_slices(net, order, n_labels=2)
+        plan = tn.build_plan(net, order, sliced, mode=q.MODE_BY_NAME[mode], outputs=b4)
+        cp = tn.CompiledPlan(plan, device=dev, leaf_data=[])
+        params = torch.tensor(p0s, dtype=torch.float32, device=dev, requires_grad=True)
+
+        def fwd_bwd():
+            params.grad = None
+            leaves = tn.torch_leaves(plan.net, c4, params, device=dev)
+            amps = tn.contract(cp, h, leaves)
+            loss = torch.log(amps.abs() ** 2).sum()
+            loss.backward()
+            return loss
+
+        fwd_bwd()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = fwd_bwd()
+        torch.cuda.synchronize()
+        diff[mode] = {"s_fwd_bwd": time.perf_counter() - t0, "loss": float(loss.item()),
+                      "grad": params.grad.double().cpu().numpy()}
+    out4 = {"workload": "4x5 grid, depth 12, fSim(theta, phi) ~ U[0, pi], loss sum log|a|^2 "
+                        "over 256 bitstrings; open network, 2 sliced indices (4 slices, "
+                        "recomputed in the backward)",
+            "auto_s": diff["auto"]["s_fwd_bwd"], "fp32_s": diff["fp32"]["s_fwd_bwd"],
+            "speedup_vs_fp32": diff["fp32"]["s_fwd_bwd"] / diff["auto"]["s_fwd_bwd"]}
+    if rank == 0:
+        import oracle
+
+        L_ref, g_ref = oracle.loss_and_grad(c4, b4)
+        for mode in ("auto", "fp32"):
+            g = diff[mode]["grad"]
+            out4[f"{mode}_grad_rel_l2_vs_fp64"] = float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))
+            out4[f"{mode}_loss_rel_vs_fp64"] = abs(diff[mode]["loss"] - L_ref) / abs(L_ref)
+    res["differentiation"] = out4
+    h.close()
+    return res
 
 
 if __name__ == "__main__":

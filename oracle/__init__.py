@@ -95,6 +95,8 @@ def _L():
         lib.oracle_contract_pair.argtypes = [I, P, P, P, I, P, P, P, I, P, P]
         lib.oracle_contract_pair.restype = I
         lib.oracle_num_threads.restype = I
+        lib.oracle_sv_apply1.argtypes = [I, P, I, P]
+        lib.oracle_sv_apply2.argtypes = [I, P, I, I, P]
         _lib = lib
     return _lib
 
@@ -335,6 +337,31 @@ def statevector(circ, gates=None) -> np.ndarray:
     for g in (circ.gates if gates is None else gates):
         psi = apply_gate(psi, g.matrix, g.qubits)
     return psi
+
+
+def statevector_inplace(circ) -> np.ndarray:
+    """The same state as ``statevector``, computed in place in C (one FP64
+    vector of 2^n amplitudes, no copies), for circuits up to ~30 qubits.
+    Returns a flat complex128 array in numpy C order over qubits 0..n-1."""
+    n = circ.n_qubits
+    psi = np.zeros(2 ** n, dtype=np.complex128)
+    psi[0] = 1.0
+    lib = _L()
+    for g in circ.gates:
+        m = np.ascontiguousarray(np.asarray(g.matrix, dtype=np.complex128))
+        if len(g.qubits) == 1:
+            lib.oracle_sv_apply1(n, _ptr(psi), int(g.qubits[0]), _ptr(m))
+        else:
+            lib.oracle_sv_apply2(n, _ptr(psi), int(g.qubits[0]), int(g.qubits[1]), _ptr(m))
+    return psi
+
+
+def bit_index(bits) -> int:
+    """Basis index of a bitstring (qubit 0 most significant)."""
+    idx = 0
+    for b in bits:
+        idx = 2 * idx + int(b)
+    return idx
 
 
 def sv_amplitudes(circ, bitstrings: np.ndarray) -> np.ndarray:

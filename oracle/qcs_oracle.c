@@ -430,3 +430,53 @@ int oracle_contract_pair(int ra, const int *la, const int64_t *da, const double 
     }
     return 0;
 }
+
+/*
+ * State-vector method (Section 1; the state of Section 2.2 as a 2^n complex
+ * vector), in place and in FP64, for circuits too large for a copy per
+ * gate.  psi holds 2^n complex128 amplitudes; qubit q is bit (n-1-q) of the
+ * basis index (qubit 0 most significant).  A one-qubit gate g (2x2, row =
+ * output) updates each pair of amplitudes that differ in that bit; a
+ * two-qubit gate (4x4, basis index 2 b(q0) + b(q1)) each quadruple.
+ */
+void oracle_sv_apply1(int n, double *psi, int q, const double *g) {
+    const int64_t N = (int64_t)1 << n;
+    const int64_t bit = (int64_t)1 << (n - 1 - q);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        if (i & bit) continue;
+        const int64_t j = i | bit;
+        const double a0r = psi[2 * i], a0i = psi[2 * i + 1];
+        const double a1r = psi[2 * j], a1i = psi[2 * j + 1];
+        psi[2 * i] = g[0] * a0r - g[1] * a0i + g[2] * a1r - g[3] * a1i;
+        psi[2 * i + 1] = g[0] * a0i + g[1] * a0r + g[2] * a1i + g[3] * a1r;
+        psi[2 * j] = g[4] * a0r - g[5] * a0i + g[6] * a1r - g[7] * a1i;
+        psi[2 * j + 1] = g[4] * a0i + g[5] * a0r + g[6] * a1i + g[7] * a1r;
+    }
+}
+
+void oracle_sv_apply2(int n, double *psi, int q0, int q1, const double *g) {
+    const int64_t N = (int64_t)1 << n;
+    const int64_t b0 = (int64_t)1 << (n - 1 - q0);
+    const int64_t b1 = (int64_t)1 << (n - 1 - q1);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        if ((i & b0) || (i & b1)) continue;
+        const int64_t idx[4] = {i, i | b1, i | b0, i | b0 | b1};
+        double ar[4], ai[4];
+        for (int u = 0; u < 4; ++u) {
+            ar[u] = psi[2 * idx[u]];
+            ai[u] = psi[2 * idx[u] + 1];
+        }
+        for (int r = 0; r < 4; ++r) {
+            double sr = 0.0, si = 0.0;
+            for (int c = 0; c < 4; ++c) {
+                const double gr = g[2 * (4 * r + c)], gi = g[2 * (4 * r + c) + 1];
+                sr += gr * ar[c] - gi * ai[c];
+                si += gr * ai[c] + gi * ar[c];
+            }
+            psi[2 * idx[r]] = sr;
+            psi[2 * idx[r] + 1] = si;
+        }
+    }
+}

@@ -133,6 +133,7 @@ namespace qcs {
 size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms) {
     size_t bytes = 256;  // descriptor
     bytes += align256(size_t(2) * num_sms * kPartialStride * sizeof(int64_t));
+    bytes += align256(kSplitKBytes);
     if (eff != QCS_MODE_FP32) {
         const int esz = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X) ? 4 : 2;
         const int64_t kp = round_up(k, 32), mp = round_up(m, kBM), np = round_up(n, kBN);
@@ -151,6 +152,8 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
     p += 256;
     int64_t *partials = reinterpret_cast<int64_t *>(p);
     p += align256(size_t(2) * h->num_sms * kPartialStride * sizeof(int64_t));
+    float2 *splitk = reinterpret_cast<float2 *>(p);
+    p += align256(kSplitKBytes);
     cudaError_t e = cudaSuccess;
 
     if (d_desc_in) {
@@ -178,7 +181,8 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
 
     if (k == 0) {
         // C = beta C: the SIMT kernel with k = 0 does exactly that (no desc gate).
-        e = launch_cgemm_simt(nullptr, opA, opB, m, n, 0, alpha, A, lda, B, ldb, beta, C, ldc, s);
+        e = launch_cgemm_simt(nullptr, opA, opB, m, n, 0, alpha, A, lda, B, ldb, beta, C, ldc,
+                              nullptr, s);
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     } else if (eff != QCS_MODE_FP32) {
         const int64_t kp = round_up(k, 32), mp = round_up(m, kBM), np = round_up(n, kBN);
@@ -223,12 +227,14 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
         }
         if (eff == QCS_MODE_AUTO) {
             ProfScope ps(h, kProfGemmSimt);
-            e = launch_cgemm_simt(desc, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+            e = launch_cgemm_simt(desc, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                                  splitk, s);
             if (e != cudaSuccess) return QCS_ERR_CUDA;
         }
     } else {
         ProfScope ps(h, kProfGemmSimt);
-        e = launch_cgemm_simt(nullptr, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+        e = launch_cgemm_simt(nullptr, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                              splitk, s);
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     }
     if (d_desc_out) {

@@ -35,6 +35,12 @@ constexpr int kStageBytes = 2 * kOperandStageBytes;        // A + B: 64 KB
 constexpr int kTcThreads = 320;   // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr int kTmemCols = 512;    // acc0.re, acc0.im, acc1.re, acc1.im x 128 columns
 
+// Split-K FP32 path for small outputs with long k: at most this many
+// outputs, and at most this many (output, k chunk) partials in the scratch.
+constexpr int64_t kSplitKMaxOutputs = 4096;
+constexpr int64_t kSplitKMaxPartials = 16384;
+constexpr size_t kSplitKBytes = size_t(kSplitKMaxPartials) * 8;
+
 // Stats grid: blocks x threads, per-block partial histograms of 257 int64
 // (256 bins + zero count).
 constexpr int kStatsThreads = 128;
@@ -153,7 +159,7 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
 cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int64_t m,
                               int64_t n, int64_t k, float2 alpha, const float2 *A, int64_t lda,
                               const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc,
-                              cudaStream_t s);
+                              float2 *splitk, cudaStream_t s);
 // Tensor-core emulated CGEMM over split planes.  ``kind``: 0 FP16 (modes
 // FP16X, FP16X_SCALED), 1 TF32, 2 BF16; the kernel returns at once unless
 // desc->mode belongs to its kind.

@@ -20,6 +20,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace qcs {
@@ -432,48 +434,248 @@ cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X
 // Permute / gather, FP64 accumulation
 // ===========================================================================
 
+static int grid_for(int64_t total) {
+    const int64_t blocks = (total + 255) / 256;
+    return (int)(blocks < 65536 ? (blocks > 0 ? blocks : 1) : 65536);
+}
+
 namespace {
 
-struct PermParams {
+// Strided copy over a common index space of ``rank`` dims (first fastest):
+// out[sum x_d os_d] (+)= in[sum x_d is_d].  A gather has dense output strides,
+// a scatter dense input strides.  When some dims form a contiguous run in the
+// output (group X, the run starting at stride 1) and others a contiguous run
+// in the input (group Y), a 32 x 32 tile of (x, y) goes through shared
+// memory: it is read with lanes along y (coalesced input) and written with
+// lanes along x (coalesced output).  The remaining dims index the tiles.
+struct CopyParams {
     int rank;
+    int nx, ny, nr;       // sizes of the X, Y and rest groups
+    int64_t px, py;       // products of the X and Y dims
+    int64_t tiles_x, tiles_y;
     int64_t dims[QCS_MAX_RANK];
-    int64_t strides[QCS_MAX_RANK];
+    int64_t is[QCS_MAX_RANK];
+    int64_t os[QCS_MAX_RANK];
+    int8_t gx[QCS_MAX_RANK], gy[QCS_MAX_RANK], gr[QCS_MAX_RANK];  // dim ids per group
 };
 
-__global__ void permute_kernel(PermParams P, int64_t total, int64_t offset,
-                               const float2 *__restrict__ in, float2 *__restrict__ out) {
-    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
-         o += (int64_t)gridDim.x * blockDim.x) {
-        int64_t rem = o, src = offset;
-        for (int d = 0; d < P.rank; ++d) {
-            const int64_t q = rem / P.dims[d];
-            src += (rem - q * P.dims[d]) * P.strides[d];
-            rem = q;
-        }
-        out[o] = in[src];
+__device__ __forceinline__ void decompose(const CopyParams &P, const int8_t *g, int ng, int64_t v,
+                                          int64_t &io, int64_t &oo) {
+    io = 0;
+    oo = 0;
+    for (int t = 0; t < ng; ++t) {
+        const int d = g[t];
+        const int64_t q = v / P.dims[d];
+        const int64_t c = v - q * P.dims[d];
+        io += c * P.is[d];
+        oo += c * P.os[d];
+        v = q;
     }
 }
 
-// Inverse of permute_kernel: dst[offset + sum_d x_d strides_d] (+)= src[o].
-__global__ void scatter_kernel(PermParams P, int64_t total, int64_t offset,
-                               const float2 *__restrict__ src, float2 *__restrict__ dst,
-                               int accumulate) {
+__global__ void __launch_bounds__(256) copy_tiled_kernel(CopyParams P, const float2 *__restrict__ in,
+                                                         float2 *__restrict__ out, int accumulate) {
+    __shared__ float2 tile[32][33];
+    __shared__ int64_t sxi[32], sxo[32], syi[32], syo[32], sr[2];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    int64_t b = blockIdx.x;
+    const int64_t bx = b % P.tiles_x;
+    b /= P.tiles_x;
+    const int64_t by = b % P.tiles_y;
+    const int64_t br = b / P.tiles_y;
+    const int64_t x0 = bx * 32, y0 = by * 32;
+    // offsets of this tile's rows, columns and of the rest index, computed once
+    if (threadIdx.x < 32) {
+        const int64_t x = x0 + threadIdx.x;
+        int64_t io = 0, oo = 0;
+        if (x < P.px) decompose(P, P.gx, P.nx, x, io, oo);
+        sxi[threadIdx.x] = io;
+        sxo[threadIdx.x] = oo;
+    } else if (threadIdx.x < 64) {
+        const int64_t y = y0 + threadIdx.x - 32;
+        int64_t io = 0, oo = 0;
+        if (y < P.py) decompose(P, P.gy, P.ny, y, io, oo);
+        syi[threadIdx.x - 32] = io;
+        syo[threadIdx.x - 32] = oo;
+    } else if (threadIdx.x == 64) {
+        int64_t io, oo;
+        decompose(P, P.gr, P.nr, br, io, oo);
+        sr[0] = io;
+        sr[1] = oo;
+    }
+    __syncthreads();
+    const int64_t ri = sr[0], ro = sr[1];
+    // read: lanes along y (contiguous input)
+    const bool yok = (y0 + tx) < P.py;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int xl = ty + 8 * r;
+        if (yok && x0 + xl < P.px) tile[xl][tx] = in[ri + sxi[xl] + syi[tx]];
+    }
+    __syncthreads();
+    // write: lanes along x (contiguous output)
+    const bool xok = (x0 + tx) < P.px;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int yl = ty + 8 * r;
+        if (xok && y0 + yl < P.py) {
+            float2 v = tile[tx][yl];
+            float2 *dst = out + ro + sxo[tx] + syo[yl];
+            if (accumulate) {
+                const float2 w = *dst;
+                v.x += w.x;
+                v.y += w.y;
+            }
+            *dst = v;
+        }
+    }
+}
+
+// Shared contiguous prefix (dims 0..nv-1 contiguous from stride 1 in both
+// input and output, product pv): one block per ``per_block`` outer indices,
+// threads copy the contiguous runs.
+__global__ void __launch_bounds__(256) copy_vector_kernel(CopyParams P, int nv, int64_t pv,
+                                                          int64_t outer, const float2 *__restrict__ in,
+                                                          float2 *__restrict__ out, int accumulate) {
+    __shared__ int64_t so[2];
+    for (int64_t q = blockIdx.x; q < outer; q += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t rem = q, io = 0, oo = 0;
+            for (int d = nv; d < P.rank; ++d) {
+                const int64_t t = rem / P.dims[d];
+                const int64_t c = rem - t * P.dims[d];
+                io += c * P.is[d];
+                oo += c * P.os[d];
+                rem = t;
+            }
+            so[0] = io;
+            so[1] = oo;
+        }
+        __syncthreads();
+        const float2 *src = in + so[0];
+        float2 *dst = out + so[1];
+        for (int64_t v = threadIdx.x; v < pv; v += blockDim.x) {
+            float2 x = src[v];
+            if (accumulate) {
+                const float2 w = dst[v];
+                x.x += w.x;
+                x.y += w.y;
+            }
+            dst[v] = x;
+        }
+    }
+}
+
+// Element-wise fallback (neither a tile nor a contiguous run applies).
+__global__ void copy_simple_kernel(CopyParams P, int64_t total, const float2 *__restrict__ in,
+                                   float2 *__restrict__ out, int accumulate) {
     for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
          o += (int64_t)gridDim.x * blockDim.x) {
-        int64_t rem = o, d_off = offset;
+        int64_t rem = o, io = 0, oo = 0;
         for (int d = 0; d < P.rank; ++d) {
             const int64_t q = rem / P.dims[d];
-            d_off += (rem - q * P.dims[d]) * P.strides[d];
+            const int64_t c = rem - q * P.dims[d];
+            io += c * P.is[d];
+            oo += c * P.os[d];
             rem = q;
         }
-        float2 v = src[o];
+        float2 v = in[io];
         if (accumulate) {
-            const float2 w = dst[d_off];
+            const float2 w = out[oo];
             v.x += w.x;
             v.y += w.y;
         }
-        dst[d_off] = v;
+        out[oo] = v;
     }
+}
+
+// X: the dims forming the output's contiguous run from stride 1 (up to 32
+// elements).  Y: the dims outside X met while walking the input's
+// contiguous run from stride 1 (dims of X may lie on that run too; their
+// elements are read by neighbouring tile rows) until Y holds 32 elements.
+void choose_groups(CopyParams &P) {
+    bool inx[QCS_MAX_RANK] = {false};
+    P.nx = 0;
+    P.px = 1;
+    {
+        bool used[QCS_MAX_RANK] = {false};
+        while (P.px < 32) {
+            int f = -1;
+            for (int d = 0; d < P.rank; ++d)
+                if (!used[d] && P.os[d] == P.px && P.dims[d] > 1) f = d;
+            if (f < 0) break;
+            used[f] = inx[f] = true;
+            P.gx[P.nx++] = (int8_t)f;
+            P.px *= P.dims[f];
+        }
+    }
+    P.ny = 0;
+    P.py = 1;
+    {
+        bool used[QCS_MAX_RANK] = {false};
+        int64_t run = 1;
+        while (P.py < 32) {
+            int f = -1;
+            for (int d = 0; d < P.rank; ++d)
+                if (!used[d] && P.is[d] == run && P.dims[d] > 1) f = d;
+            if (f < 0) break;
+            used[f] = true;
+            run *= P.dims[f];
+            if (!inx[f]) {
+                P.gy[P.ny++] = (int8_t)f;
+                P.py *= P.dims[f];
+            }
+        }
+    }
+}
+
+cudaError_t launch_copy(int rank, const int64_t *dims, const int64_t *is, const int64_t *os,
+                        const float2 *in, float2 *out, int accumulate, cudaStream_t s) {
+    CopyParams P{};
+    P.rank = rank;
+    int64_t total = 1;
+    for (int d = 0; d < rank; ++d) {
+        P.dims[d] = dims[d];
+        P.is[d] = is[d];
+        P.os[d] = os[d];
+        total *= dims[d];
+    }
+    if (total == 0) return cudaSuccess;
+    // dims contiguous from stride 1 on both sides (same dims, same order)
+    int nv = 0;
+    int64_t pv = 1;
+    while (nv < rank && P.is[nv] == pv && P.os[nv] == pv) pv *= P.dims[nv++];
+    choose_groups(P);
+    const bool tiled_ok = P.nx > 0 && P.ny > 0 && P.px >= 4 && P.py >= 4;
+    if (pv >= 32 || (!tiled_ok && pv >= 4)) {
+        const int64_t outer = total / pv;
+        const int64_t blocks = outer < 65536 ? outer : 65536;
+        copy_vector_kernel<<<(unsigned)blocks, pv >= 256 ? 256 : (pv >= 128 ? 128 : 64), 0, s>>>(
+            P, nv, pv, outer, in, out, accumulate);
+        return cudaGetLastError();
+    }
+    if (!tiled_ok) {
+        copy_simple_kernel<<<grid_for(total), 256, 0, s>>>(P, total, in, out, accumulate);
+        return cudaGetLastError();
+    }
+    P.nr = 0;
+    int64_t rest = 1;
+    for (int d = 0; d < rank; ++d) {
+        bool in_group = false;
+        for (int a = 0; a < P.nx; ++a) in_group |= (P.gx[a] == d);
+        for (int c = 0; c < P.ny; ++c) in_group |= (P.gy[c] == d);
+        if (!in_group) {
+            P.gr[P.nr++] = (int8_t)d;
+            rest *= dims[d];
+        }
+    }
+    P.tiles_x = (P.px + 31) / 32;
+    P.tiles_y = (P.py + 31) / 32;
+    const int64_t blocks = P.tiles_x * P.tiles_y * rest;
+    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+    copy_tiled_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, in, out, accumulate);
+    return cudaGetLastError();
 }
 
 // dst[j] += (double) src[index ? index[j] : j], j < count (FP64 sums over
@@ -523,39 +725,24 @@ cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides
                            cudaStream_t s) {
     (void)stats_partials;
     (void)gstats;
-    PermParams P;
-    P.rank = rank;
-    int64_t total = 1;
+    int64_t dense[QCS_MAX_RANK];
+    int64_t acc = 1;
     for (int d = 0; d < rank; ++d) {
-        P.dims[d] = dims[d];
-        P.strides[d] = strides[d];
-        total *= dims[d];
+        dense[d] = acc;
+        acc *= dims[d];
     }
-    if (total == 0) return cudaSuccess;
-    const int64_t blocks = (total + 255) / 256;
-    permute_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, s>>>(P, total, offset, in,
-                                                                             out);
-    return cudaGetLastError();
-}
-
-static int grid_for(int64_t total) {
-    const int64_t blocks = (total + 255) / 256;
-    return (int)(blocks < 65536 ? (blocks > 0 ? blocks : 1) : 65536);
+    return launch_copy(rank, dims, strides, dense, in + offset, out, 0, s);
 }
 
 cudaError_t launch_scatter(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
                            const float2 *src, float2 *dst, int accumulate, cudaStream_t s) {
-    PermParams P;
-    P.rank = rank;
-    int64_t total = 1;
+    int64_t dense[QCS_MAX_RANK];
+    int64_t acc = 1;
     for (int d = 0; d < rank; ++d) {
-        P.dims[d] = dims[d];
-        P.strides[d] = strides[d];
-        total *= dims[d];
+        dense[d] = acc;
+        acc *= dims[d];
     }
-    if (total == 0) return cudaSuccess;
-    scatter_kernel<<<grid_for(total), 256, 0, s>>>(P, total, offset, src, dst, accumulate);
-    return cudaGetLastError();
+    return launch_copy(rank, dims, dense, strides, src, dst + offset, accumulate, s);
 }
 
 cudaError_t launch_accumulate_gather_c128(const float2 *src, const int64_t *index, double *dst,
@@ -776,13 +963,92 @@ __global__ void cgemm_skinny_kernel(const qcs_gemm_desc_t *__restrict__ desc, in
     }
 }
 
+// Split-K for small m*n with long k (the end of a contraction tree reduces
+// large tensors to a few numbers): warp w handles output o = w mod (m n) over
+// the w-th k chunk; lanes stride along k, a warp shuffle reduces, and the
+// partial goes to part[chunk * m n + o].  cgemm_splitk_reduce then adds the
+// chunks in order (deterministic) and applies alpha/beta.
+__global__ void __launch_bounds__(256) cgemm_splitk_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int64_t k,
+    int64_t chunk, int64_t chunks, const float2 *__restrict__ A, int64_t lda,
+    const float2 *__restrict__ B, int64_t ldb, float2 *__restrict__ part) {
+    if (desc && desc->mode != QCS_MODE_FP32) return;
+    const int64_t mn = m * n;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= mn * chunks) return;
+    const int64_t o = w % mn, c = w / mn;
+    const int64_t i = o % m, j = o / m;
+    const int64_t l0 = c * chunk, l1 = min(k, l0 + chunk);
+    float sr = 0.f, si = 0.f;
+    for (int64_t l = l0 + lane; l < l1; l += 32) {
+        const float2 a = ld_op(A, opA, i, l, lda);
+        const float2 b = ld_op(B, opB, l, j, ldb);
+        sr = fmaf(a.x, b.x, sr);
+        sr = fmaf(-a.y, b.y, sr);
+        si = fmaf(a.x, b.y, si);
+        si = fmaf(a.y, b.x, si);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, off);
+        si += __shfl_xor_sync(0xffffffffu, si, off);
+    }
+    if (lane == 0) part[c * mn + o] = make_float2(sr, si);
+}
+
+__global__ void cgemm_splitk_reduce(const qcs_gemm_desc_t *__restrict__ desc, int64_t m, int64_t n,
+                                    int64_t chunks, const float2 *__restrict__ part, float2 alpha,
+                                    float2 beta, float2 *__restrict__ C, int64_t ldc) {
+    if (desc && desc->mode != QCS_MODE_FP32) return;
+    const int64_t mn = m * n;
+    const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < mn;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        float sr = 0.f, si = 0.f;
+        for (int64_t c = 0; c < chunks; ++c) {
+            const float2 v = part[c * mn + o];
+            sr += v.x;
+            si += v.y;
+        }
+        const int64_t i = o % m, j = o / m;
+        float2 r;
+        r.x = alpha.x * sr - alpha.y * si;
+        r.y = alpha.x * si + alpha.y * sr;
+        float2 *dst = C + i + j * ldc;
+        if (use_beta) {
+            const float2 cv = *dst;
+            r.x += beta.x * cv.x - beta.y * cv.y;
+            r.y += beta.x * cv.y + beta.y * cv.x;
+        }
+        *dst = r;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int64_t m,
                               int64_t n, int64_t k, float2 alpha, const float2 *A, int64_t lda,
                               const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc,
-                              cudaStream_t s) {
+                              float2 *splitk, cudaStream_t s) {
     if (m == 0 || n == 0) return cudaSuccess;
+    const int64_t mn = m * n;
+    if (splitk && mn <= kSplitKMaxOutputs && k >= 1024) {
+        // enough warps to fill the GPU, at least 256 k values per warp
+        int64_t chunks = kSplitKMaxPartials / mn;
+        chunks = std::min<int64_t>(chunks, (k + 255) / 256);
+        chunks = std::max<int64_t>(chunks, 1);
+        const int64_t chunk = (k + chunks - 1) / chunks;
+        chunks = (k + chunk - 1) / chunk;
+        const int64_t warps = mn * chunks;
+        const int64_t blocks = (warps * 32 + 255) / 256;
+        cgemm_splitk_kernel<<<(unsigned)blocks, 256, 0, s>>>(desc, opA, opB, m, n, k, chunk, chunks,
+                                                             A, lda, B, ldb, splitk);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        cgemm_splitk_reduce<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(desc, m, n, chunks, splitk,
+                                                                        alpha, beta, C, ldc);
+        return cudaGetLastError();
+    }
     const bool skinny = (k <= 16) || (m * n <= 4096);
     if (skinny || m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) {
         const int64_t total = m * n;

@@ -561,3 +561,28 @@ def plan_circuit(circ, bitstrings=None, seed: int = 2, n_slices: int = 0,
         sliced = choose_slices(net, order, n_labels=n_slices or None,
                                max_log2_size=max_log2_size, skip=skip)
     return build_plan(net, order, sliced, mode=mode)
+
+
+# ---------------------------------------------------------------------------
+# several GPUs: instances (slices, bitstrings) are independent (Section 5.3)
+# ---------------------------------------------------------------------------
+
+def shard_plan(plan: Plan, rank: int, world: int) -> Plan:
+    """The instances of ``plan`` that rank ``rank`` of ``world`` runs
+    (round-robin).  Summing every rank's output slots gives the full result."""
+    import copy
+
+    idx = np.arange(rank, plan.n_instances, world)
+    sub = copy.copy(plan)
+    sub.instance_offset = np.ascontiguousarray(plan.instance_offset[idx])
+    sub.instance_slot = np.ascontiguousarray(plan.instance_slot[idx])
+    return sub
+
+
+def allreduce_slots(out, group=None):
+    """Sum complex128 output slots over the ranks of ``group`` in place."""
+    import torch
+    import torch.distributed as dist
+
+    dist.all_reduce(torch.view_as_real(out), op=dist.ReduceOp.SUM, group=group)
+    return out

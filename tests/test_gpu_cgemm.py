@@ -245,3 +245,18 @@ def test_invalid_arguments_are_rejected(h):
     assert f(h.ptr, 0, 0, 0, 2, 2, 2, ctypes.byref(one), odd, 2, P, 2, ctypes.byref(zero), P, 2, None) == L.QCS_ERR_UNSUPPORTED
     assert h.lib.qcs_set_underflow_tol(h.ptr, 1.5) == L.QCS_ERR_INVALID_ARG
     del q
+
+
+@pytest.mark.parametrize("m,n,k,opA,opB", [(1, 1, 100000, 0, 0), (4, 4, 50000, 1, 2),
+                                           (16, 3, 70000, 2, 0), (64, 64, 4096, 0, 1)])
+def test_cgemm_fp32_split_k_small_outputs(h, m, n, k, opA, opB):
+    """End-of-tree reductions: few outputs, long k (split over warps)."""
+    A, B = _operands(m, n, k, opA, opB, 2, seed=(m, n, k))
+    C0 = qi.cgemm_operand(m, n, 0, seed=4)
+    got, d = _run(h, "fp32", m, n, k, opA, opB, A, B, 1.5 - 0.5j, 0.5j, C0)
+    ref = oracle.cgemm(opA, opB, m, n, k, 1.5 - 0.5j, A, B, 0.5j, C0)
+    bound = (2 * k + 8) * 2.0 ** -24 * (1.6 * 2 * abs_bound(A, B, opA, opB, m, k, n)
+                                        + 0.5 * 2 * np.abs(C0[:m, :n]))
+    # the element-wise FP32 bound: a single long dot product cancels too much for a
+    # relative-error bar to apply to it
+    assert np.all(np.abs(got - ref) <= bound)

@@ -144,3 +144,40 @@ def test_invalid_plan_is_rejected_before_launch(h):
     rc = h.lib.qcs_contract_tree(h.ptr, ctypes.byref(cp2.tree), cp2._ptrs(cp2.leaves),
                                  ctypes.c_void_p(out.data_ptr()), None)
     assert rc == L.QCS_ERR_INVALID_ARG
+
+
+def _golden_amplitudes(path):
+    bits, amps = [], []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            b, re, im = line.split()
+            bits.append([int(c) for c in b])
+            amps.append(float(re) + 1j * float(im))
+    return np.array(bits, dtype=np.uint8), np.array(amps)
+
+
+def test_full_size_30_qubit_sliced_amplitudes_vs_fp64_golden(h, golden_dir):
+    """The contraction workload at full size: 5x6 grid, depth 14, 6 sliced
+    indices (64 slices), AUTO-0.1 per GEMM, against FP64 amplitudes the
+    oracle's state vector wrote to tests/golden (the oracle cannot contract
+    this network itself in reasonable time)."""
+    import os
+
+    tn = _tn()
+    bits_all, ref_all = _golden_amplitudes(os.path.join(golden_dir, "grid5x6_d14_amplitudes.txt"))
+    assert np.array_equal(bits_all, qi.random_bitstrings(30, 8, seed=1))
+    circ = qi.random_grid_circuit(5, 6, 14, seed=0)
+    bits, ref = bits_all[:2], ref_all[:2]
+    plan = tn.plan_circuit(circ, bits, seed=2, n_slices=6)
+    assert plan.n_instances == 2 * 64
+    h.set_tol(0.1)
+    try:
+        got, info = _run(h, plan)
+    finally:
+        h.set_tol(0.0)
+    a = got[:, 0]
+    assert oracle.fidelity(ref, a) >= 1 - 1e-5
+    assert np.all(np.abs(a - ref) <= 1e-4 * np.abs(ref)), (a, ref)
+    assert info.mode_count[0] > 0  # some GEMMs took the statistics-based selection

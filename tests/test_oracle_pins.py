@@ -465,3 +465,14 @@ def test_fidelity_definition():
     assert abs(oracle.fidelity(a, a) - 1) < 1e-15
     assert abs(oracle.fidelity(a, a * np.exp(0.7j)) - 1) < 1e-15   # global phase invariant
     assert oracle.fidelity(np.array([1, 0]), np.array([0, 1])) == 0
+
+
+def test_inplace_statevector_matches_tensordot_statevector():
+    # two independent implementations of the same definition (C in place vs numpy tensordot)
+    for rows, cols, depth, seed in ((3, 4, 8, 0), (2, 5, 6, 3), (1, 3, 3, 1)):
+        circ = qi.random_grid_circuit(rows, cols, depth, seed=seed)
+        a = oracle.statevector_inplace(circ)
+        b = oracle.statevector(circ).ravel()
+        np.testing.assert_allclose(a, b, atol=1e-13)
+        x = qi.random_bitstrings(rows * cols, 1, seed=9)[0]
+        assert a[oracle.bit_index(x)] == b[oracle.bit_index(x)] or abs(a[oracle.bit_index(x)] - b[oracle.bit_index(x)]) < 1e-14

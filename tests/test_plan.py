@@ -90,3 +90,16 @@ def test_slicer_bounds_the_largest_intermediate():
     sliced = tn.choose_slices(net, order, max_log2_size=base - 3)
     after = max(len(r) for r in tn.intermediates(net, order, sliced))
     assert after <= base - 3 and len(sliced) >= 3
+
+
+def test_open_network_sliced_with_bitstring_gather():
+    # the differentiation workload's plan shape: open legs, sliced, amplitudes gathered
+    circ = qi.random_grid_circuit(3, 3, 6, seed=2, theta=None, phi=None, param_seed=3)
+    bits = qi.random_bitstrings(9, 12, seed=1)
+    net = tn.circuit_network(circ, None)
+    order = tn.greedy_order(net, seed=2)
+    sliced = tn.choose_slices(net, order, n_labels=2)
+    plan = tn.build_plan(net, order, sliced, outputs=bits)
+    assert plan.n_instances == 4 and plan.n_slots == 1 and plan.out_size == 12
+    got = run(plan, _leaves(plan))[0]
+    np.testing.assert_allclose(got, oracle.sv_amplitudes(circ, bits), atol=1e-6)
