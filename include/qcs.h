@@ -108,6 +108,15 @@ int qcs_set_underflow_tol(qcs_handle_t h, double t);
  * statistics. */
 int qcs_set_size_rule(qcs_handle_t h, int enabled);
 
+/* Round-to-nearest drain interval of the tensor-core kernels: the hi*hi
+ * products are summed in tensor memory for ``stages`` pipeline stages (each
+ * two tensor-core K steps: 32 complex k for FP16/BF16, 16 for TF32), where
+ * the hardware accumulation truncates, then added to round-to-nearest FP32
+ * sums (Section 2.1's remedy for the tensor core's rounding toward zero,
+ * applied per group of MMAs).  1, 2 or 4; default 4 (environment override
+ * QCS_DRAIN_STAGES).  Larger groups are faster and slightly less accurate. */
+int qcs_set_drain_stages(qcs_handle_t h, int stages);
+
 /* Exponent statistics (Section 4.1, Stage 1 and Stage 2 in one pass) of the
  * rows x cols complex matrix X (device, leading dim ldx >= rows), written
  * to d_stats (device, caller-owned).  rows or cols may be 0. */

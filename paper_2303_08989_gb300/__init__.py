@@ -93,6 +93,10 @@ class Handle:
         _lib.check(self.lib.qcs_set_size_rule(self._h, 1 if on else 0))
         self.size_rule = bool(on)
 
+    def set_drain_stages(self, stages: int):
+        _lib.check(self.lib.qcs_set_drain_stages(self._h, int(stages)), "qcs_set_drain_stages")
+        self.drain_stages = int(stages)
+
     def set_profiling(self, on: bool):
         _lib.check(self.lib.qcs_set_profiling(self._h, 1 if on else 0))
 

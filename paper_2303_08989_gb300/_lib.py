@@ -28,6 +28,7 @@ OP_N, OP_T, OP_C = 0, 1, 2
 #: every entry point include/qcs.h declares
 EXPORTED = [
     "qcs_create", "qcs_destroy", "qcs_set_stream", "qcs_set_underflow_tol", "qcs_set_size_rule",
+    "qcs_set_drain_stages",
     "qcs_exp_stats", "qcs_select", "qcs_cgemm", "qcs_split", "qcs_permute", "qcs_contract_tree",
     "qcs_contract_tree_backward", "qcs_set_profiling", "qcs_get_profile", "qcs_sync",
     "qcs_status_string", "qcs_cgemm_noalloc",
@@ -108,6 +109,7 @@ def load(path: str = LIB_PATH):
         "qcs_set_stream": [H, P],
         "qcs_set_underflow_tol": [H, ctypes.c_double],
         "qcs_set_size_rule": [H, I],
+        "qcs_set_drain_stages": [H, I],
         "qcs_exp_stats": [H, I64, I64, P, I64, P],
         "qcs_select": [H, P, P, P],
         "qcs_cgemm": [H, I, I, I, I64, I64, I64, ctypes.POINTER(qcs_c32), P, I64, P, I64,

@@ -213,16 +213,16 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
             if (encode_planes(h, &ma, planesA, mp, kp, 2) || encode_planes(h, &mb, planesB, np, kp, 2))
                 return QCS_ERR_CUDA;
             const int kind = (eff == QCS_MODE_BF16X3) ? 2 : 0;
-            e = launch_cgemm_tc(kind, desc, &ma, &mb, m, n, kp, alpha, beta, C, ldc, h->d_err,
-                                h->num_sms, s);
+            e = launch_cgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
+                                ldc, h->d_err, h->num_sms, s);
             if (e != cudaSuccess) return QCS_ERR_CUDA;
         }
         if (need32) {
             CUtensorMap ma, mb;
             if (encode_planes(h, &ma, planesA, mp, kp, 4) || encode_planes(h, &mb, planesB, np, kp, 4))
                 return QCS_ERR_CUDA;
-            e = launch_cgemm_tc(1, desc, &ma, &mb, m, n, kp, alpha, beta, C, ldc, h->d_err,
-                                h->num_sms, s);
+            e = launch_cgemm_tc(1, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
+                                ldc, h->d_err, h->num_sms, s);
             if (e != cudaSuccess) return QCS_ERR_CUDA;
         }
         if (eff == QCS_MODE_AUTO) {
@@ -299,6 +299,10 @@ int qcs_create(qcs_handle_t *out, void *cuda_stream) {
     h->encode = reinterpret_cast<EncodeTiledFn>(fn);
     if (const char *t = std::getenv("QCS_UNDERFLOW_TOL")) h->tol = std::atof(t);
     if (const char *r = std::getenv("QCS_SIZE_RULE")) h->size_rule = std::atoi(r) != 0;
+    if (const char *d = std::getenv("QCS_DRAIN_STAGES")) {
+        const int v = std::atoi(d);
+        h->drain_stages = (v >= 4) ? 4 : (v == 2 ? 2 : 1);
+    }
     *out = h;
     return QCS_SUCCESS;
 }
@@ -327,6 +331,12 @@ int qcs_set_stream(qcs_handle_t h, void *cuda_stream) {
 int qcs_set_underflow_tol(qcs_handle_t h, double t) {
     if (!h || !(t >= 0.0 && t <= 1.0)) return QCS_ERR_INVALID_ARG;
     h->tol = t;
+    return QCS_SUCCESS;
+}
+
+int qcs_set_drain_stages(qcs_handle_t h, int stages) {
+    if (!h || (stages != 1 && stages != 2 && stages != 4)) return QCS_ERR_INVALID_ARG;
+    h->drain_stages = stages;
     return QCS_SUCCESS;
 }
 

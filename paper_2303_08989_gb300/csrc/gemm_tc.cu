@@ -14,9 +14,10 @@
 // accumulation.  The sm_103a tensor core truncates too (measured: 1 + 0.75 ulp
 // accumulates to 1, within one MMA and across MMAs, for FP16 and TF32
 // inputs), which makes the error of a TMEM-resident hi*hi sum grow linearly
-// with k.  So accumulator 0 is drained every pipeline stage (two UMMA K
-// steps): the stage's hi*hi sum is computed fresh in tensor memory and added
-// with round-to-nearest FP32 adds into registers of the epilogue warps.  The
+// with k.  So accumulator 0 is drained every DRAIN pipeline stages (two UMMA
+// K steps each): that group's hi*hi sum is computed fresh in tensor memory
+// and added with round-to-nearest FP32 adds into registers of the epilogue
+// warps.  The
 // correction products (accumulator 1, weight 2^-11) stay in tensor memory for
 // the whole K loop: their truncation error enters the result scaled by 2^-11.
 //
@@ -92,7 +93,7 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
         mma_f16(d, a, b, idesc, acc);
 }
 
-template <int KIND>
+template <int KIND, int DRAIN>
 __global__ void __launch_bounds__(kTcThreads, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                     const __grid_constant__ CUtensorMap mapB,
@@ -234,14 +235,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         mma<KIND>(a1r, A_(ks, 1), B_(ks, 3), idn, 1u);     // -Ai_hi Bi_lo
                         mma<KIND>(a1i, A_(ks, 1), B_(ks, 2), id, 1u);      //  Ai_hi Br_lo
                     }
-                    // hi*hi products into a fresh acc0, once the last one was drained
-                    if (!wait_drained()) {
+                    // hi*hi products: a fresh acc0 every DRAIN stages, once the
+                    // previous one was drained
+                    const bool group_start = (kb % DRAIN) == 0;
+                    const bool group_end = (kb % DRAIN) == DRAIN - 1 || kb == num_kb - 1;
+                    if (group_start && !wait_drained()) {
                         ok = false;
                         break;
                     }
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
-                        const uint32_t first = (ks == 0) ? 0u : 1u;
+                        const uint32_t first = (ks == 0 && group_start) ? 0u : 1u;
                         mma<KIND>(a0r, A_(ks, 0), B_(ks, 0), id, first);   //  Ar_hi Br_hi
                         mma<KIND>(a0i, A_(ks, 0), B_(ks, 1), id, first);   //  Ar_hi Bi_hi
                         mma<KIND>(a0r, A_(ks, 1), B_(ks, 1), idn, 1u);     // -Ai_hi Bi_hi
@@ -250,8 +254,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #undef A_
 #undef B_
                     tc_commit(&S.empty[stage]);  // frees the smem stage when these MMAs finish
-                    tc_commit(&S.acc0_full);     // acc0 (and, on a tile's last stage, acc1) ready
-                    pending = true;
+                    if (group_end) {
+                        tc_commit(&S.acc0_full);  // acc0 (and, on a tile's last stage, acc1) ready
+                        pending = true;
+                    }
                     if (++stage == kStages) {
                         stage = 0;
                         phase ^= 1u;
@@ -281,7 +287,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             float racc[kEpiCols], iacc[kEpiCols];
 #pragma unroll
             for (int j = 0; j < kEpiCols; ++j) racc[j] = iacc[j] = 0.0f;
-            for (int kb = 0; kb < num_kb; ++kb) {
+            for (int kb = DRAIN - 1; kb < num_kb + DRAIN - 1; kb += DRAIN) {
+                const bool last = kb >= num_kb - 1;  // the group holding the tile's last stage
                 int got = 0;
                 if (lane == 0)
                     got = mbar_wait(&S.acc0_full, f_phase, globaltimer_ns() + kWaitBudgetNs,
@@ -309,7 +316,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         iacc[c + j] += __uint_as_float(vi[j]);
                     }
                 }
-                if (kb == num_kb - 1) {
+                if (last) {
 #pragma unroll
                     for (int c = 0; c < kEpiCols; c += 16) {
                         uint32_t vr[16], vi[16];
@@ -364,7 +371,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
 }
 
-template <int KIND>
+template <int KIND, int DRAIN>
 cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
                         const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad, float2 alpha,
                         float2 beta, float2 *C, int64_t ldc, int *d_err, int num_sms,
@@ -372,7 +379,7 @@ cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
     const size_t smem = sizeof(TcSmem) + 1024;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel<KIND>,
+        cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel<KIND, DRAIN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
@@ -380,27 +387,42 @@ cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
     const int64_t tiles = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
     if (tiles == 0 || k_pad == 0) return cudaSuccess;
     const int grid = static_cast<int>(tiles < num_sms ? tiles : num_sms);
-    cgemm_tc_kernel<KIND><<<grid, kTcThreads, smem, s>>>(*mapA, *mapB, desc, (int)m, (int)n,
-                                                         (int)k_pad, alpha, beta, C, ldc, d_err);
+    cgemm_tc_kernel<KIND, DRAIN><<<grid, kTcThreads, smem, s>>>(
+        *mapA, *mapB, desc, (int)m, (int)n, (int)k_pad, alpha, beta, C, ldc, d_err);
     return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_drain(int drain, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
+                         const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad,
+                         float2 alpha, float2 beta, float2 *C, int64_t ldc, int *d_err,
+                         int num_sms, cudaStream_t s) {
+    if (drain >= 4)
+        return launch_kind<KIND, 4>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
+                                    num_sms, s);
+    if (drain == 2)
+        return launch_kind<KIND, 2>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
+                                    num_sms, s);
+    return launch_kind<KIND, 1>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
+                                num_sms, s);
 }
 
 }  // namespace
 
-cudaError_t launch_cgemm_tc(int kind, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
-                            const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad,
-                            float2 alpha, float2 beta, float2 *C, int64_t ldc, int *d_err,
-                            int num_sms, cudaStream_t s) {
+cudaError_t launch_cgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
+                            const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
+                            int64_t n, int64_t k_pad, float2 alpha, float2 beta, float2 *C,
+                            int64_t ldc, int *d_err, int num_sms, cudaStream_t s) {
     switch (kind) {
         case 0:
-            return launch_kind<0>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                  num_sms, s);
+            return launch_drain<0>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
+                                   d_err, num_sms, s);
         case 1:
-            return launch_kind<1>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                  num_sms, s);
+            return launch_drain<1>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
+                                   d_err, num_sms, s);
         default:
-            return launch_kind<2>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                  num_sms, s);
+            return launch_drain<2>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
+                                   d_err, num_sms, s);
     }
 }
 

@@ -80,6 +80,7 @@ struct qcs_handle_s {
     cudaStream_t stream = nullptr;
     double tol = 0.0;
     int size_rule = 1;
+    int drain_stages = 4;            // stages per RN drain of the tensor-core hi*hi sum
     int *d_err = nullptr;            // device error word
     qcs::Workspace ws;               // GEMM workspace (planes, partials, descriptor)
     qcs::Workspace tree_ws;          // contraction-tree intermediates
@@ -163,9 +164,11 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
 // Tensor-core emulated CGEMM over split planes.  ``kind``: 0 FP16 (modes
 // FP16X, FP16X_SCALED), 1 TF32, 2 BF16; the kernel returns at once unless
 // desc->mode belongs to its kind.
-cudaError_t launch_cgemm_tc(int kind, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
-                            const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad,
-                            float2 alpha, float2 beta, float2 *C, int64_t ldc, int *d_err,
-                            int num_sms, cudaStream_t s);
+// ``drain``: pipeline stages per round-to-nearest drain of the hi*hi
+// accumulator (1, 2 or 4).
+cudaError_t launch_cgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
+                            const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
+                            int64_t n, int64_t k_pad, float2 alpha, float2 beta, float2 *C,
+                            int64_t ldc, int *d_err, int num_sms, cudaStream_t s);
 
 }  // namespace qcs

@@ -67,10 +67,11 @@ __global__ void __launch_bounds__(kStatsThreads) stats2_kernel(
         const int64_t gtid = blk * kStatsThreads + tid;
         const int64_t gstride = nblk * kStatsThreads;
         if (ld == rows && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
-            // contiguous: two complex values per 16-byte load, 8 loads in flight
+            // contiguous: two complex values per 16-byte load, 16 loads in
+            // flight per thread (4 warps per SM must cover the HBM latency)
             const float4 *p = reinterpret_cast<const float4 *>(X);
             const int64_t n4 = nel >> 1;
-            constexpr int U = 8;
+            constexpr int U = 16;
             int64_t i = gtid;
             for (; i + (U - 1) * gstride < n4; i += U * gstride) {
                 float4 v[U];

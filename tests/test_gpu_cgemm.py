@@ -195,16 +195,22 @@ def test_cgemm_auto_picks_oracle_mode(h, s, tol):
     assert oracle.rel_fro_error(got, exact) < 1e-6
 
 
-def test_cgemm_error_bars_unit_inputs(h):
+@pytest.mark.parametrize("drain", [1, 2, 4])
+def test_cgemm_error_bars_unit_inputs(h, drain):
     """FP32-level accuracy: U(-1,1) inputs, k = 4096 (Section 3 unit test):
-    relative Frobenius error <= 1e-6 and <= 2x the plain FP32 GPU error."""
+    relative Frobenius error <= 1e-6 and <= 2x the plain FP32 GPU error, for
+    every round-to-nearest drain interval."""
     m, n, k = 256, 192, 4096
     A, B = _operands(m, n, k, 0, 0, 0, seed=42, uniform=True)
     exact = oracle.cgemm(0, 0, m, n, k, 1.0, A, B)
     e32 = oracle.rel_fro_error(_run(h, "fp32", m, n, k, 0, 0, A, B)[0], exact)
-    for mode in ("fp16x", "tf32x", "auto"):
-        e = oracle.rel_fro_error(_run(h, mode, m, n, k, 0, 0, A, B)[0], exact)
-        assert e <= 1e-6 and e <= 2 * e32, (mode, e, e32)
+    h.set_drain_stages(drain)
+    try:
+        for mode in ("fp16x", "tf32x", "auto"):
+            e = oracle.rel_fro_error(_run(h, mode, m, n, k, 0, 0, A, B)[0], exact)
+            assert e <= 1e-6 and e <= 2 * e32, (mode, e, e32)
+    finally:
+        h.set_drain_stages(4)
 
 
 def test_nonfinite_inputs_route_to_fp32(h):

@@ -39,24 +39,31 @@ def h():
     hd.close()
 
 
+@pytest.mark.parametrize("drain", [1, 4])
 @pytest.mark.parametrize("mode", ["fp16x", "tf32x"])
-def test_accumulation_rounding(h, mode, capsys):
-    """Inside one pipeline stage the sum stays in tensor memory and is
-    truncated by the hardware (1 + 0.75 ulp -> 1); across stages it goes
-    through the epilogue's round-to-nearest FP32 adds (-> 1 + 1 ulp)."""
+def test_accumulation_rounding(h, mode, drain, capsys):
+    """Inside one drain group the sum stays in tensor memory and is truncated
+    by the hardware (1 + 0.75 ulp -> 1); across groups it goes through the
+    epilogue's round-to-nearest FP32 adds (-> 1 + 1 ulp)."""
+    h.set_drain_stages(drain)
     k_mma, k_stage = (16, 32) if mode == "fp16x" else (8, 16)
+    k_group = k_stage * drain
     small_a, small_b = 2.0 ** -12, 1.5 * 2.0 ** -12  # product 0.75 ulp(1)
     cases = {
         "within one MMA": ([(0, 1.0, 1.0), (1, small_a, small_b)], 0.0),
         "across MMAs of one stage": ([(0, 1.0, 1.0), (k_mma, small_a, small_b)], 0.0),
         "small first, one stage": ([(0, small_a, small_b), (k_mma, 1.0, 1.0)], 0.0),
-        "across stages": ([(0, 1.0, 1.0), (k_stage, small_a, small_b)], ULP1),
-        "across stages, small first": ([(0, small_a, small_b), (k_stage, 1.0, 1.0)], ULP1),
+        "last stage of the group": ([(0, 1.0, 1.0), (k_group - 1, small_a, small_b)], 0.0),
+        "across drain groups": ([(0, 1.0, 1.0), (k_group, small_a, small_b)], ULP1),
+        "across drain groups, small first": ([(0, small_a, small_b), (k_group, 1.0, 1.0)], ULP1),
     }
-    for name, (pairs, want) in cases.items():
-        c = _dot(h, mode, pairs, 64)
-        assert c.imag == 0.0
-        got = float(c.real) - 1.0
-        with capsys.disabled():
-            print(f"[tcgen05 {mode}] {name}: result - 1 = {got / ULP1:+.3f} ulp")
-        assert got == want, name
+    try:
+        for name, (pairs, want) in cases.items():
+            c = _dot(h, mode, pairs, 2 * k_group)
+            assert c.imag == 0.0
+            got = float(c.real) - 1.0
+            with capsys.disabled():
+                print(f"[tcgen05 {mode} drain {drain}] {name}: result - 1 = {got / ULP1:+.3f} ulp")
+            assert got == want, name
+    finally:
+        h.set_drain_stages(4)
