@@ -268,7 +268,8 @@ def main():
     h.set_profiling(False)
     ms = max_over_ranks(ms)
     value = world * flops / (ms * 1e-3) / 1e12
-    launches_per_step = 7  # stats, select, split x2, tcgen05 FP16, tcgen05 TF32, SIMT (gated)
+    # statistics pass 1 and 2, selection, split x2, tcgen05 FP16, tcgen05 TF32, SIMT (gated)
+    launches_per_step = 8
 
     # ---- dominant kernel roofline (live CUDA-event timing of the tcgen05 GEMM) ----
     tc_ms, tc_n = prof["gemm_tc"]

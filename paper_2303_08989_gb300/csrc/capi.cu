@@ -87,6 +87,14 @@ int stats_blocks(int64_t nel, int num_sms) {
     return static_cast<int>(g);
 }
 
+// Blocks of the two-stage statistics for ``nel`` complex values: up to four
+// 256-thread blocks per SM, at least 2048 complex values per block.
+int stats2_blocks(int64_t nel, int num_sms) {
+    int64_t g = (nel + 2047) / 2048;
+    g = std::max<int64_t>(1, std::min<int64_t>(g, 4 * (int64_t)num_sms));
+    return static_cast<int>(g);
+}
+
 int encode_planes(qcs_handle_t h, CUtensorMap *map, void *base, int64_t R_pad, int64_t K_pad,
                   int esz) {
     const CUtensorMapDataType dt =
@@ -162,16 +170,11 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
         // Statistics of both operands as stored (a transpose does not change the multiset).
         const int64_t ra = (opA == QCS_OP_N) ? m : k, ca = (opA == QCS_OP_N) ? k : m;
         const int64_t rb = (opB == QCS_OP_N) ? k : n, cb = (opB == QCS_OP_N) ? n : k;
-        const int gA = stats_blocks(ra * ca, h->num_sms), gB = stats_blocks(rb * cb, h->num_sms);
+        const int gA = stats2_blocks(ra * ca, h->num_sms), gB = stats2_blocks(rb * cb, h->num_sms);
         {
             ProfScope ps(h, kProfStats);
-            e = launch_stats2(A, ra, ca, lda, gA, B, rb, cb, ldb, gB, partials, s);
-        }
-        if (e != cudaSuccess) return QCS_ERR_CUDA;
-        {
-            ProfScope ps(h, kProfSelect);
-            e = launch_select(partials, gA, gB, 2 * ra * ca, 2 * rb * cb, h->tol, eff, nullptr,
-                              nullptr, desc, s);
+            e = launch_stats_select_2stage(A, ra, ca, lda, gA, B, rb, cb, ldb, gB, h->tol, eff,
+                                           partials, partials + 5 * (gA + gB), desc, s);
         }
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     } else {

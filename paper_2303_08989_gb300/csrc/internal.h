@@ -119,6 +119,14 @@ cudaError_t launch_stats2(const float2 *X0, int64_t rows0, int64_t cols0, int64_
 cudaError_t launch_select(const int64_t *partials, int gA, int gB, int64_t nA, int64_t nB,
                           double tol, int forced_mode, qcs_stats_t *statsA, qcs_stats_t *statsB,
                           qcs_gemm_desc_t *desc, cudaStream_t s);
+// Two-stage statistics + selection for the GEMM path: pass 1 (e_max,
+// zeros, Inf/NaN, count below 2^-14), pass 2 only when needed (count below
+// the shifted window), final selection.  gA / gB blocks of 256 threads per
+// matrix; p1 holds 5 int64 per block, p2 one.
+cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t cols0, int64_t ld0,
+                                       int gA, const float2 *X1, int64_t rows1, int64_t cols1,
+                                       int64_t ld1, int gB, double tol, int forced, int64_t *p1,
+                                       int64_t *p2, qcs_gemm_desc_t *desc, cudaStream_t s);
 // Select from two finished qcs_stats_t.
 cudaError_t launch_select_from_stats(const qcs_stats_t *a, const qcs_stats_t *b, double tol,
                                      qcs_gemm_desc_t *desc, cudaStream_t s);

@@ -247,6 +247,228 @@ __global__ void stats_finalize_kernel(const int64_t *__restrict__ partials, int 
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Two-stage statistics for the GEMM path (Section 4.1 Stage 1 / Stage 2),
+// register-only so that every SM runs at full occupancy.
+//   pass 1: e_max (largest biased exponent of a finite nonzero scalar), the
+//           number of zeros, of Inf/NaN and of finite nonzero scalars below
+//           2^-14 (N - N1).
+//   pass 2: only when the Stage 1 outcome does not decide the mode: the
+//           number below the window shifted so that e_max becomes 14 (N - N2).
+// Per-block partials: pass 1 five int64 (bmax, 0, zeros, nonfinite, under1),
+// pass 2 one int64.
+// ---------------------------------------------------------------------------
+
+constexpr int kS2Threads = 256;
+
+struct Acc1 {
+    uint32_t bmax;
+    uint32_t zeros, nonfinite, under1;
+};
+
+__device__ __forceinline__ void acc1_scalar(Acc1 &a, float x) {
+    const uint32_t mag = __float_as_uint(x) & 0x7FFFFFFFu;
+    const uint32_t be = mag >> 23;
+    const bool zero = mag == 0u;
+    const bool nonfin = be == 255u;
+    const bool fin_nz = !zero && !nonfin;
+    a.bmax = fin_nz ? max(a.bmax, be) : a.bmax;
+    a.zeros += zero;
+    a.nonfinite += nonfin;
+    a.under1 += (fin_nz && be < 113u);  // e < -14 (binary32 subnormals included)
+}
+
+template <class F>
+__device__ __forceinline__ void for_each_scalar(const float2 *X, int64_t rows, int64_t cols,
+                                                int64_t ld, int64_t gtid, int64_t gstride, F f) {
+    const int64_t nel = rows * cols;
+    if (nel <= 0) return;
+    if (ld == rows && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
+        const float4 *p = reinterpret_cast<const float4 *>(X);
+        const int64_t n4 = nel >> 1;
+        constexpr int U = 8;
+        int64_t i = gtid;
+        for (; i + (U - 1) * gstride < n4; i += U * gstride) {
+            float4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = __ldcs(p + i + u * gstride);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                f(v[u].x);
+                f(v[u].y);
+                f(v[u].z);
+                f(v[u].w);
+            }
+        }
+        for (; i < n4; i += gstride) {
+            const float4 v = __ldcs(p + i);
+            f(v.x);
+            f(v.y);
+            f(v.z);
+            f(v.w);
+        }
+        if ((nel & 1) && gtid == 0) {
+            const float2 v = X[nel - 1];
+            f(v.x);
+            f(v.y);
+        }
+    } else {
+        for (int64_t i = gtid; i < nel; i += gstride) {
+            const int64_t c = i / rows, r = i - c * rows;
+            const float2 v = X[r + c * ld];
+            f(v.x);
+            f(v.y);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t block_max(uint32_t v, uint32_t *sh) {
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    uint32_t r = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = max(r, sh[w]);
+    return r;
+}
+
+__device__ __forceinline__ uint64_t block_sum(uint64_t v, uint64_t *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    uint64_t r = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+    return r;
+}
+
+__global__ void __launch_bounds__(kS2Threads) stats_pass1_kernel(
+    const float2 *__restrict__ X0, int64_t rows0, int64_t cols0, int64_t ld0, int gA,
+    const float2 *__restrict__ X1, int64_t rows1, int64_t cols1, int64_t ld1, int gB,
+    int64_t *__restrict__ p1) {
+    __shared__ uint32_t shm[kS2Threads / 32];
+    __shared__ uint64_t shs[kS2Threads / 32];
+    const bool first = blockIdx.x < gA;
+    const float2 *X = first ? X0 : X1;
+    const int64_t blk = first ? blockIdx.x : blockIdx.x - gA;
+    const int64_t nblk = first ? gA : gB;
+    Acc1 a{0u, 0u, 0u, 0u};
+    for_each_scalar(X, first ? rows0 : rows1, first ? cols0 : cols1, first ? ld0 : ld1,
+                    blk * kS2Threads + threadIdx.x, nblk * kS2Threads,
+                    [&](float x) { acc1_scalar(a, x); });
+    const uint32_t bmax = block_max(a.bmax, shm);
+    const uint64_t zeros = block_sum(a.zeros, shs);
+    const uint64_t nonfin = block_sum(a.nonfinite, shs);
+    const uint64_t under1 = block_sum(a.under1, shs);
+    if (threadIdx.x == 0) {
+        int64_t *o = p1 + (int64_t)blockIdx.x * 5;
+        o[0] = bmax;
+        o[1] = 0;
+        o[2] = (int64_t)zeros;
+        o[3] = (int64_t)nonfin;
+        o[4] = (int64_t)under1;
+    }
+}
+
+struct Sum1 {
+    int64_t bmax, nnz, zeros, nonfinite, under1;
+};
+
+// Block-cooperative reduction of pass-1 partials [b0, b1); every thread
+// returns the same result.
+__device__ Sum1 reduce_p1(const int64_t *p1, int b0, int b1, int64_t total, uint32_t *shm,
+                          uint64_t *shs) {
+    uint32_t bmax = 0;
+    uint64_t zeros = 0, nonfin = 0, under1 = 0;
+    for (int b = b0 + (int)threadIdx.x; b < b1; b += (int)blockDim.x) {
+        const int64_t *o = p1 + (int64_t)b * 5;
+        bmax = max(bmax, (uint32_t)o[0]);
+        zeros += (uint64_t)o[2];
+        nonfin += (uint64_t)o[3];
+        under1 += (uint64_t)o[4];
+    }
+    Sum1 s;
+    s.bmax = block_max(bmax, shm);
+    s.zeros = (int64_t)block_sum(zeros, shs);
+    s.nonfinite = (int64_t)block_sum(nonfin, shs);
+    s.under1 = (int64_t)block_sum(under1, shs);
+    s.nnz = total - s.zeros - s.nonfinite;
+    if (s.nnz == 0) s.bmax = -1;
+    return s;
+}
+
+// Does the rule need Stage 2 (the shifted-window count)?  Same function in
+// pass 2 and in the final selection, so both take the same decision.
+__device__ bool needs_stage2(const Sum1 &a, const Sum1 &b, double tol, int forced) {
+    if (forced == QCS_MODE_FP16X_SCALED) return false;
+    if (a.nonfinite > 0 || b.nonfinite > 0 || a.bmax >= 254 || b.bmax >= 254) return false;
+    auto ok1 = [&](const Sum1 &s) {
+        return s.bmax < 0 || (s.bmax - 127 <= 14 && (double)s.under1 <= tol * (double)s.nnz);
+    };
+    return !(ok1(a) && ok1(b));
+}
+
+__global__ void __launch_bounds__(kS2Threads) stats_pass2_kernel(
+    const float2 *__restrict__ X0, int64_t rows0, int64_t cols0, int64_t ld0, int gA,
+    const float2 *__restrict__ X1, int64_t rows1, int64_t cols1, int64_t ld1, int gB,
+    const int64_t *__restrict__ p1, double tol, int forced, int64_t *__restrict__ p2) {
+    __shared__ uint64_t shs[kS2Threads / 32];
+    __shared__ uint32_t shm[kS2Threads / 32];
+    const Sum1 a = reduce_p1(p1, 0, gA, 2 * rows0 * cols0, shm, shs);
+    const Sum1 b = reduce_p1(p1, gA, gA + gB, 2 * rows1 * cols1, shm, shs);
+    if (!needs_stage2(a, b, tol, forced)) return;  // uniform across the block
+    const int64_t bmax = (blockIdx.x < gA) ? a.bmax : b.bmax;
+    const uint32_t thr = (uint32_t)(bmax - 28 > 1 ? bmax - 28 : 1);  // biased exponents below are outside
+    const bool first = blockIdx.x < gA;
+    const float2 *X = first ? X0 : X1;
+    const int64_t blk = first ? blockIdx.x : blockIdx.x - gA;
+    const int64_t nblk = first ? gA : gB;
+    uint32_t under2 = 0;
+    for_each_scalar(X, first ? rows0 : rows1, first ? cols0 : cols1, first ? ld0 : ld1,
+                    blk * kS2Threads + threadIdx.x, nblk * kS2Threads, [&](float x) {
+                        const uint32_t mag = __float_as_uint(x) & 0x7FFFFFFFu;
+                        under2 += (mag != 0u && (mag >> 23) < thr);
+                    });
+    const uint64_t tot = block_sum(under2, shs);
+    if (threadIdx.x == 0) p2[blockIdx.x] = (int64_t)tot;
+}
+
+__global__ void select2_kernel(const int64_t *__restrict__ p1, const int64_t *__restrict__ p2,
+                               int gA, int gB, int64_t nA, int64_t nB, double tol, int forced,
+                               qcs_gemm_desc_t *desc) {
+    __shared__ uint64_t shs[kS2Threads / 32];
+    __shared__ uint32_t shm[kS2Threads / 32];
+    const Sum1 a = reduce_p1(p1, 0, gA, nA, shm, shs);
+    const Sum1 b = reduce_p1(p1, gA, gA + gB, nB, shm, shs);
+    uint64_t u2a = 0, u2b = 0;
+    const bool need2 = needs_stage2(a, b, tol, forced);
+    if (need2) {
+        for (int i = (int)threadIdx.x; i < gA + gB; i += (int)blockDim.x) {
+            if (i < gA)
+                u2a += (uint64_t)p2[i];
+            else
+                u2b += (uint64_t)p2[i];
+        }
+    }
+    u2a = block_sum(u2a, shs);
+    u2b = block_sum(u2b, shs);
+    if (threadIdx.x != 0) return;
+    Summary sa, sb;
+    sa.nnz = a.nnz;
+    sa.nonfinite = a.nonfinite;
+    sa.under1 = a.under1;
+    sa.bmax = (int)a.bmax;
+    sb.nnz = b.nnz;
+    sb.nonfinite = b.nonfinite;
+    sb.under1 = b.under1;
+    sb.bmax = (int)b.bmax;
+    sa.under2 = (int64_t)u2a;
+    sb.under2 = (int64_t)u2b;
+    select_rule(sa, sb, tol, forced, desc);
+}
+
 static bool g_stats_configured = false;
 
 cudaError_t launch_stats2(const float2 *X0, int64_t rows0, int64_t cols0, int64_t ld0, int gA,
@@ -269,6 +491,23 @@ cudaError_t launch_select(const int64_t *partials, int gA, int gB, int64_t nA, i
                           qcs_gemm_desc_t *desc, cudaStream_t s) {
     select_kernel<<<1, 256, 0, s>>>(partials, gA, gB, nA, nB, tol, forced_mode, statsA, statsB,
                                     desc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t cols0, int64_t ld0,
+                                       int gA, const float2 *X1, int64_t rows1, int64_t cols1,
+                                       int64_t ld1, int gB, double tol, int forced, int64_t *p1,
+                                       int64_t *p2, qcs_gemm_desc_t *desc, cudaStream_t s) {
+    stats_pass1_kernel<<<gA + gB, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1, cols1,
+                                                      ld1, gB, p1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    stats_pass2_kernel<<<gA + gB, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1, cols1,
+                                                      ld1, gB, p1, tol, forced, p2);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    select2_kernel<<<1, kS2Threads, 0, s>>>(p1, p2, gA, gB, 2 * rows0 * cols0, 2 * rows1 * cols1,
+                                            tol, forced, desc);
     return cudaGetLastError();
 }
 
