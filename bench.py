@@ -451,8 +451,20 @@ def tree_legs(args, q, torch, dev, rank):
     p0 = tn.plan_circuit(c0, b0, seed=2)
     cp0 = tn.CompiledPlan(p0, device=dev)
     secs0, out0 = _time_plan(torch, cp0, h, reps=3)
+    g0, gout = cp0.graph(h)
+    g0.launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        g0.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    secs_g = e0.elapsed_time(e1) / 3 * 1e-3
+    g0.close()
     res["plain_small"] = {"workload": "3x4 grid, depth 8, 64 bitstrings, greedy order",
-                          "s_per_batch": secs0, "gemms": cp0.last_info.gemm_count}
+                          "s_per_batch": secs0, "s_per_batch_cuda_graph": secs_g,
+                          "gemms": cp0.last_info.gemm_count}
     if rank == 0:
         import oracle
 

@@ -244,6 +244,23 @@ typedef struct {
 int qcs_contract_tree(qcs_handle_t h, const qcs_tree_t *tree, const qcs_c32 *const *leaves,
                       double *d_out, qcs_run_info_t *info);
 
+/* The launches of one qcs_contract_tree call, captured into a CUDA graph
+ * (Section 5.3's slices are independent instances of one step sequence, so
+ * the whole sequence replays with one launch).  qcs_tree_graph_create
+ * validates the plan, allocates the graph's own workspace (cudaMalloc; not
+ * during a capture), records every kernel the call would launch for these
+ * leaves and this d_out into a graph and instantiates it; nothing is
+ * computed.  qcs_tree_graph_launch replays it on the handle's current
+ * stream: the same result qcs_contract_tree would write to d_out, from the
+ * current contents of the same leaf buffers.  The leaf and output buffers
+ * and the handle must outlive the graph.  qcs_tree_graph_destroy
+ * synchronizes the handle's stream and frees the graph and its workspace. */
+typedef struct qcs_tree_graph_s *qcs_tree_graph_t;
+int qcs_tree_graph_create(qcs_handle_t h, const qcs_tree_t *tree, const qcs_c32 *const *leaves,
+                          double *d_out, qcs_tree_graph_t *out);
+int qcs_tree_graph_launch(qcs_tree_graph_t g);
+int qcs_tree_graph_destroy(qcs_tree_graph_t g);
+
 /* Adjoint of qcs_contract_tree.  Given d_grad_out (device complex128,
  * n_slots * out_size values: dL/dRe + i dL/dIm of each output), adds to
  * d_grad_leaves[i] (host array of device complex64 pointers, each the size

@@ -31,7 +31,8 @@ EXPORTED = [
     "qcs_set_drain_stages",
     "qcs_exp_stats", "qcs_select", "qcs_cgemm", "qcs_split", "qcs_permute", "qcs_contract_tree",
     "qcs_contract_tree_backward", "qcs_set_profiling", "qcs_get_profile", "qcs_sync",
-    "qcs_status_string", "qcs_cgemm_noalloc",
+    "qcs_status_string", "qcs_cgemm_noalloc", "qcs_tree_graph_create", "qcs_tree_graph_launch",
+    "qcs_tree_graph_destroy",
 ]
 PROFILE_STAGES = ["stats", "select", "split", "gemm_tc", "gemm_simt", "permute", "reduce"]
 
@@ -125,6 +126,10 @@ def load(path: str = LIB_PATH):
         "qcs_sync": [H],
         "qcs_cgemm_noalloc": [P, I, ctypes.c_double, I, I, I64, I64, I64, ctypes.POINTER(qcs_c32),
                               P, I64, P, I64, ctypes.POINTER(qcs_c32), P, I64, P],
+        "qcs_tree_graph_create": [H, ctypes.POINTER(qcs_tree_t), ctypes.POINTER(P), P,
+                                  ctypes.POINTER(ctypes.c_void_p)],
+        "qcs_tree_graph_launch": [P],
+        "qcs_tree_graph_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

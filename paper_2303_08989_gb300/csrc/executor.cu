@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <new>
 #include <vector>
 
 #include "internal.h"
@@ -244,13 +245,14 @@ const float2 *root_ptr(const Ctx &c, int inst) {
 }
 
 int begin(qcs_handle_t h, const qcs_tree_t *t, bool backward, std::vector<int64_t> &size_of,
-          Ctx &c) {
+          Ctx &c, Workspace *own = nullptr) {
     if (int r = validate(t, size_of, backward)) return r;
     c.h = h;
     c.t = t;
     c.L = plan_layout(h, t, backward);
-    if (int r = ensure_workspace(h->tree_ws, c.L.total)) return r;
-    c.ws = static_cast<uint8_t *>(h->tree_ws.ptr);
+    Workspace &w = own ? *own : h->tree_ws;
+    if (int r = ensure_workspace(w, c.L.total)) return r;
+    c.ws = static_cast<uint8_t *>(w.ptr);
     if (t->out_index) {
         if (cudaMemcpyAsync(c.ws + c.L.out_index, t->out_index, sizeof(int64_t) * t->out_size,
                             cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
@@ -266,8 +268,37 @@ const int64_t *dev_index(const Ctx &c) {
     return c.t->out_index ? reinterpret_cast<const int64_t *>(c.ws + c.L.out_index) : nullptr;
 }
 
+// Every launch of a forward call after begin(): clear d_out, then per
+// instance the steps and the FP64 accumulation of the root.
+int forward_all(const Ctx &c, double *d_out) {
+    const qcs_tree_t *tree = c.t;
+    qcs_handle_t h = c.h;
+    if (cudaMemsetAsync(d_out, 0, sizeof(double) * 2 * tree->n_slots * tree->out_size, h->stream) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    for (int inst = 0; inst < tree->n_instances; ++inst) {
+        if (int r = forward_instance(c, inst)) return r;
+        ProfScope ps(h, kProfReduce);
+        const int64_t slot = tree->instance_slot[inst];
+        if (launch_accumulate_gather_c128(root_ptr(c, inst), dev_index(c),
+                                          d_out + 2 * slot * tree->out_size, tree->out_size,
+                                          h->stream) != cudaSuccess)
+            return QCS_ERR_CUDA;
+    }
+    return QCS_SUCCESS;
+}
+
 }  // namespace
 }  // namespace qcs
+
+struct qcs_tree_graph_s {
+    qcs_handle_t h = nullptr;
+    qcs::Workspace ws;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
 
 using namespace qcs;
 
@@ -285,20 +316,7 @@ int qcs_contract_tree(qcs_handle_t h, const qcs_tree_t *tree, const qcs_c32 *con
     c.leaves = leaves;
     c.info = info;
     if (int r = begin(h, tree, false, size_of, c)) return r;
-    if (cudaMemsetAsync(d_out, 0, sizeof(double) * 2 * tree->n_slots * tree->out_size, h->stream) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return QCS_ERR_CUDA;
-    }
-    for (int inst = 0; inst < tree->n_instances; ++inst) {
-        if (int r = forward_instance(c, inst)) return r;
-        ProfScope ps(h, kProfReduce);
-        const int64_t slot = tree->instance_slot[inst];
-        if (launch_accumulate_gather_c128(root_ptr(c, inst), dev_index(c),
-                                          d_out + 2 * slot * tree->out_size, tree->out_size,
-                                          h->stream) != cudaSuccess)
-            return QCS_ERR_CUDA;
-    }
+    if (int r = forward_all(c, d_out)) return r;
     if (info)
         info->seconds =
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -373,6 +391,71 @@ int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
     if (info)
         info->seconds =
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return QCS_SUCCESS;
+}
+
+int qcs_tree_graph_create(qcs_handle_t h, const qcs_tree_t *tree, const qcs_c32 *const *leaves,
+                          double *d_out, qcs_tree_graph_t *out) {
+    if (!h || !tree || !leaves || !d_out || !out) return QCS_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < tree->n_leaves; ++i)
+        if (!leaves[i] || (reinterpret_cast<uintptr_t>(leaves[i]) & 7u)) return QCS_ERR_INVALID_ARG;
+    qcs_tree_graph_s *g = new (std::nothrow) qcs_tree_graph_s;
+    if (!g) return QCS_ERR_ALLOC;
+    g->h = h;
+    std::vector<int64_t> size_of;
+    Ctx c;
+    c.leaves = leaves;
+    c.info = nullptr;
+    // begin() validates, allocates the graph's workspace and uploads the
+    // output index, all before the capture starts.
+    int r = begin(h, tree, false, size_of, c, &g->ws);
+    if (r == QCS_SUCCESS && cudaStreamSynchronize(h->stream) != cudaSuccess) r = QCS_ERR_CUDA;
+    // Capture on a private stream (the legacy default stream cannot be
+    // captured); the instantiated graph then launches on the handle's stream.
+    const int profiling = h->profiling;
+    cudaStream_t user = h->stream, cap = nullptr;
+    h->profiling = 0;
+    if (r == QCS_SUCCESS && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+        r = QCS_ERR_CUDA;
+    if (r == QCS_SUCCESS) {
+        h->stream = cap;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            r = QCS_ERR_CUDA;
+        } else {
+            const int rf = forward_all(c, d_out);
+            const cudaError_t e = cudaStreamEndCapture(cap, &g->graph);
+            r = rf ? rf : (e == cudaSuccess ? QCS_SUCCESS : QCS_ERR_CUDA);
+        }
+    }
+    h->stream = user;
+    h->profiling = profiling;
+    if (cap) cudaStreamDestroy(cap);
+    if (r == QCS_SUCCESS && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess)
+        r = QCS_ERR_CUDA;
+    if (r != QCS_SUCCESS) {
+        cudaGetLastError();
+        if (g->graph) cudaGraphDestroy(g->graph);
+        if (g->ws.ptr) cudaFree(g->ws.ptr);
+        delete g;
+        return r;
+    }
+    *out = g;
+    return QCS_SUCCESS;
+}
+
+int qcs_tree_graph_launch(qcs_tree_graph_t g) {
+    if (!g || !g->exec) return QCS_ERR_INVALID_ARG;
+    return cudaGraphLaunch(g->exec, g->h->stream) == cudaSuccess ? QCS_SUCCESS : QCS_ERR_CUDA;
+}
+
+int qcs_tree_graph_destroy(qcs_tree_graph_t g) {
+    if (!g) return QCS_ERR_INVALID_ARG;
+    cudaStreamSynchronize(g->h->stream);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->ws.ptr) cudaFree(g->ws.ptr);
+    delete g;
     return QCS_SUCCESS;
 }
 

@@ -452,6 +452,18 @@ class CompiledPlan:
         self.last_info = info
         return out
 
+    def graph(self, h, out=None):
+        """Capture this plan's forward call into a CUDA graph (qcs_tree_graph_*);
+        returns (graph, out).  ``graph.launch()`` recomputes ``out`` from the
+        current contents of ``self.leaves``."""
+        import torch
+
+        if out is None:
+            out = torch.empty((self.plan.n_slots, self.plan.out_size), dtype=torch.complex128,
+                              device=self.device)
+        g = TreeGraph(h, self, out)
+        return g, out
+
     def backward(self, h, grad_out, leaves=None):
         """Leaf gradients (list of complex64 tensors) for dL/d out = grad_out
         (torch convention: dL/dRe + i dL/dIm)."""
@@ -466,6 +478,36 @@ class CompiledPlan:
             self._ptrs(grads), ctypes.byref(info)), "qcs_contract_tree_backward")
         self.last_info = info
         return grads
+
+
+class TreeGraph:
+    """An instantiated CUDA graph of one plan's forward call."""
+
+    def __init__(self, h, cp: CompiledPlan, out):
+        self.h = h
+        self.cp = cp
+        self.out = out
+        self._leaves = [t.contiguous() for t in cp.leaves]
+        self._ptrs = cp._ptrs(self._leaves)
+        self._g = ctypes.c_void_p()
+        _lib.check(h.lib.qcs_tree_graph_create(h.ptr, ctypes.byref(cp.tree), self._ptrs,
+                                               ctypes.c_void_p(out.data_ptr()),
+                                               ctypes.byref(self._g)), "qcs_tree_graph_create")
+
+    def launch(self):
+        _lib.check(self.h.lib.qcs_tree_graph_launch(self._g), "qcs_tree_graph_launch")
+        return self.out
+
+    def close(self):
+        if self._g:
+            self.h.lib.qcs_tree_graph_destroy(self._g)
+            self._g = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def info_dict(info) -> dict:

@@ -181,3 +181,36 @@ def test_full_size_30_qubit_sliced_amplitudes_vs_fp64_golden(h, golden_dir):
     assert oracle.fidelity(ref, a) >= 1 - 1e-5
     assert np.all(np.abs(a - ref) <= 1e-4 * np.abs(ref)), (a, ref)
     assert info.mode_count[0] > 0  # some GEMMs took the statistics-based selection
+
+
+@pytest.mark.parametrize("mode,n_slices", [("auto", 0), ("tf32x", 2)])
+def test_graph_replay_equals_eager(h, mode, n_slices):
+    """qcs_tree_graph_*: the captured launch sequence replays to the same bits as
+    the eager call, also after the leaf buffers were overwritten in place."""
+    tn = _tn()
+    q = lib()
+    circ = qi.random_grid_circuit(3, 4, 8, seed=0)
+    bits = qi.random_bitstrings(12, 16, seed=1)
+    plan = tn.plan_circuit(circ, bits, seed=2, n_slices=n_slices, mode=q.MODE_BY_NAME[mode])
+    h.set_size_rule(False)
+    try:
+        cp = tn.CompiledPlan(plan)
+        eager = cp.forward(h).clone()
+        g, out = cp.graph(h)
+        g.launch()
+        torch.cuda.synchronize()
+        h.sync()
+        assert torch.equal(out, eager)
+        # new gate values in the same buffers: the replay reads the current contents
+        circ2 = qi.random_grid_circuit(3, 4, 8, seed=7)
+        for t, lf in zip(cp.leaves, tn.circuit_network(circ2, bits).leaves):
+            t.copy_(torch.from_numpy(lf.data))
+        g.launch()
+        eager2 = cp.forward(h)
+        torch.cuda.synchronize()
+        assert torch.equal(out, eager2)
+        ref = oracle.sv_amplitudes(circ2, bits)
+        assert oracle.fidelity(ref, out.cpu().numpy()[:, 0]) >= 1 - 1e-5
+        g.close()
+    finally:
+        h.set_size_rule(True)
