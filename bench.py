@@ -385,6 +385,9 @@ def main():
                       "ms_per_step": ems, "steps": ek}
         del hA, hB, hC, Ad, Bd, Cd
 
+    if not args.no_extras:
+        out["hbm_kernels"] = hbm_legs(q, torch, dev, h, stages, n)
+
     if not args.no_tree:
         out.update(tree_legs(args, q, torch, dev, rank))
 
@@ -393,6 +396,66 @@ def main():
     h.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def hbm_legs(q, torch, dev, h, stages, n):
+    """Bandwidth of the memory-bound kernels of the path, against the
+    measured HBM copy bandwidth: statistics and split (from the CGEMM
+    step's live stage timings), a standalone gather (a random permutation
+    of a 2^28-element tensor of 28 binary indices, the shape of the
+    contraction's reshapes) and the skinny CGEMMs of Section 5.1.2."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm, src = float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        hbm, src = 6800.0, "fallback"
+    res = {"peak_gbs": hbm, "peak_source": src}
+
+    def entry(bytes_, ms):
+        gbs = bytes_ / (ms * 1e-3) / 1e9
+        return {"GB/s": gbs, "frac": gbs / hbm, "ms": ms, "bytes": bytes_}
+
+    if "stats" in stages:
+        res["exp_stats"] = entry(2 * 8 * n * n, stages["stats"]["ms_per_step"])
+        res["exp_stats"]["note"] = "pass 1 over A and B (pass 2 not needed by this input)"
+    if "split" in stages:
+        res["split"] = entry(2 * (8 + 8) * n * n, stages["split"]["ms_per_step"])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # gather: random permutation of 28 binary indices
+    r = 28
+    g = torch.Generator(device="cpu").manual_seed(5)
+    perm = torch.randperm(r, generator=g).tolist()
+    src = torch.empty(2 ** r, dtype=torch.complex64, device=dev)
+    out = torch.empty_like(src)
+    dims = [2] * r
+    strides = [2 ** p for p in perm]
+    ms = timed(lambda: q.permute(h, src, dims, strides, out=out))
+    res["gather_perm_2^28"] = entry(2 * 8 * 2 ** r, ms)
+    del src, out
+    # skinny CGEMMs (FP32 path): (2, 2^26, 2) and (2^26, 2, 2)
+    N = 2 ** 26
+    A = torch.zeros((2, 2), dtype=torch.complex64, device=dev).t()
+    B = torch.zeros((N, 2), dtype=torch.complex64, device=dev).t()  # 2 x N column-major
+    C = torch.empty((N, 2), dtype=torch.complex64, device=dev).t()   # 2 x N
+    ms = timed(lambda: q.cgemm(h, A, B, C, mode="fp32"))
+    res["skinny_2xNx2"] = entry(8 * (2 * 2 + 2 * N + 2 * N), ms)
+    A2 = torch.zeros((2, N), dtype=torch.complex64, device=dev).t()   # N x 2
+    B2 = torch.zeros((2, 2), dtype=torch.complex64, device=dev).t()
+    C2 = torch.empty((2, N), dtype=torch.complex64, device=dev).t()   # N x 2
+    ms = timed(lambda: q.cgemm(h, A2, B2, C2, mode="fp32"))
+    res["skinny_Nx2x2"] = entry(8 * (N * 2 + 4 + N * 2), ms)
+    return res
 
 
 def _time_plan(torch, cp, h, instances=None, reps=1):
@@ -512,8 +575,67 @@ def tree_legs(args, q, torch, dev, rank):
             out4[f"{mode}_grad_rel_l2_vs_fp64"] = float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))
             out4[f"{mode}_loss_rel_vs_fp64"] = abs(diff[mode]["loss"] - L_ref) / abs(L_ref)
     res["differentiation"] = out4
+    res["precision_at_scale"] = scale_leg(args, q, torch, dev, h, tn, qi, rank)
     h.close()
     return res
+
+
+def scale_leg(args, q, torch, dev, h, tn, qi, rank):
+    """40-qubit 5x8 grid, depth 12 (the depth a seeded greedy order slices to
+    <= 2^30 with 256 slices), sliced on the 8 indices the oracle chose for its
+    FP64 sample: AUTO vs all-FP32 seconds per slice on a sample of slices, the
+    GEMM modes AUTO picked, and the four FP64-checked slices."""
+    import copy
+
+    import numpy as np
+
+    path = os.path.join(ROOT, "tests", "golden", "slices5x8_d12.txt")
+    if not os.path.exists(path):
+        return {"skipped": "tests/golden/slices5x8_d12.txt missing"}
+    labels, rows = None, []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("sliced"):
+                labels = [int(v) for v in line.split()[1:]]
+            elif line.strip() and not line.startswith("#"):
+                v, re, im = line.split()
+                rows.append((v, float(re) + 1j * float(im)))
+    circ = qi.random_grid_circuit(5, 8, 12, seed=0)
+    bits = qi.random_bitstrings(40, 1, seed=1)
+    net = tn.circuit_network(circ, bits)
+    order = tn.greedy_order(net, seed=5, skip=[tn.BATCH] + labels)
+    out = {"workload": "5x8 grid (40 qubits), depth 12, 8 sliced indices (256 slices), seeded "
+                       "greedy order, 1 bitstring; AUTO-%g vs all-FP32" % args.tol}
+    per = {}
+    for mode in ("auto", "fp32"):
+        plan = tn.build_plan(net, order, labels, mode=q.MODE_BY_NAME[mode])
+        cp = tn.CompiledPlan(plan, device=dev)
+        ns = min(16, plan.n_instances)
+        secs, amp = _time_plan(torch, cp, h, instances=ns)
+        info = tn.info_dict(cp.last_info)
+        per[mode] = {"s_per_slice": secs / ns, "slices_timed": ns, "partial_sum": complex(amp.cpu().numpy()[0, 0]),
+                     "gemm_modes": dict(zip(["auto", "fp16x", "fp16x_scaled", "tf32x", "fp32", "bf16x3"],
+                                            info["mode_count"]))}
+        out["flops_per_slice"] = plan.flops
+        out["max_intermediate_log2"] = plan.max_log2_size
+        if mode == "auto":
+            idx = [int(v, 2) for v, _ in rows]
+            sub = copy.copy(plan)
+            sub.instance_offset = np.ascontiguousarray(plan.instance_offset[idx])
+            sub.instance_slot = np.arange(len(idx), dtype=np.int32)
+            sub.n_slots = len(idx)
+            got = tn.CompiledPlan(sub, device=dev).forward(h).cpu().numpy()[:, 0]
+            if rank == 0:
+                import oracle
+
+                ref = np.array([a for _, a in rows])
+                out["sampled_slices_fidelity_vs_fp64"] = oracle.fidelity(ref, got)
+                out["sampled_slices_max_rel_err_vs_fp64"] = float(np.max(np.abs(got - ref) / np.abs(ref)))
+    a, b = per["auto"].pop("partial_sum"), per["fp32"].pop("partial_sum")
+    out["auto"], out["fp32"] = per["auto"], per["fp32"]
+    out["auto_vs_fp32_rel_diff"] = abs(a - b) / abs(b)
+    out["speedup_vs_fp32"] = per["fp32"]["s_per_slice"] / per["auto"]["s_per_slice"]
+    return out
 
 
 if __name__ == "__main__":

@@ -505,6 +505,152 @@ def greedy_order(tensors, output_labels) -> List[Tuple[int, int]]:
     return order
 
 
+def order_cost(tensors, order, output_labels=()) -> Tuple[float, int]:
+    """(flops of a pairwise order with 8 flops per complex multiply-add,
+    log2 of the largest intermediate)."""
+    from collections import Counter
+
+    dims = {}
+    for t, ls in tensors:
+        for d, l in zip(np.shape(t), ls):
+            dims[l] = d
+    labs = [list(ls) for _, ls in tensors]
+    cnt = Counter(l for ls in labs for l in ls)
+    for l in output_labels:
+        cnt[l] += 1
+    flops, big = 0.0, 0
+    for i, j in order:
+        a, b = labs[i], labs[j]
+        sh = set(a) & set(b)
+        res = [l for l in dict.fromkeys(a + b) if not (l in sh and cnt[l] == 2)]
+        flops += 8.0 * float(np.prod([dims[l] for l in set(a) | set(b)]))
+        big = max(big, int(round(sum(np.log2(dims[l]) for l in res))))
+        for l in a + b:
+            cnt[l] -= 1
+        for l in res:
+            cnt[l] += 1
+        labs.append(res)
+    return flops, big
+
+
+def random_greedy_order(tensors, output_labels, seeds=range(8)) -> List[Tuple[int, int]]:
+    """Best (fewest flops) of several randomised greedy orders: like
+    ``greedy_order`` but each candidate's cost is multiplied by a random
+    factor in [1, 1.5) drawn per pair from a seeded generator, which breaks
+    the many ties differently per seed."""
+    from collections import defaultdict
+    import heapq
+
+    best = None
+    for seed in seeds:
+        rng = np.random.default_rng(seed)
+        labs = [list(ls) for _, ls in tensors]
+        dims = {}
+        for t, ls in tensors:
+            for d, l in zip(np.shape(t), ls):
+                dims[l] = d
+        count = defaultdict(int)
+        where = defaultdict(set)
+        for i, ls in enumerate(labs):
+            for l in ls:
+                count[l] += 1
+                where[l].add(i)
+        for l in output_labels:
+            count[l] += 1
+        alive = set(range(len(labs)))
+
+        def size(ls):
+            return float(np.prod([dims[l] for l in ls])) if ls else 1.0
+
+        def result(i, j):
+            si, sj = set(labs[i]), set(labs[j])
+            return [l for l in dict.fromkeys(labs[i] + labs[j])
+                    if not (l in si and l in sj and count[l] == 2)]
+
+        heap = []
+
+        def push(i, j):
+            r = result(i, j)
+            c = (size(r) - size(labs[i]) - size(labs[j])) * (1.0 + 0.5 * rng.random())
+            heapq.heappush(heap, (c, i, j))
+
+        for l, ws in list(where.items()):
+            ws = sorted(ws)
+            for a in range(len(ws)):
+                for b in range(a + 1, len(ws)):
+                    push(ws[a], ws[b])
+        order = []
+        while len(alive) > 1:
+            pair = None
+            while heap:
+                _, i, j = heapq.heappop(heap)
+                if i in alive and j in alive:
+                    pair = (i, j)
+                    break
+            if pair is None:
+                i, j = sorted(alive)[:2]
+            else:
+                i, j = pair
+            res = result(i, j)
+            order.append((i, j))
+            for u in (i, j):
+                for l in labs[u]:
+                    count[l] -= 1
+                    where[l].discard(u)
+                alive.discard(u)
+            labs.append(res)
+            nu = len(labs) - 1
+            for l in res:
+                count[l] += 1
+                where[l].add(nu)
+            alive.add(nu)
+            nb = set()
+            for l in res:
+                nb |= where[l]
+            nb.discard(nu)
+            for u in nb:
+                push(min(u, nu), max(u, nu))
+        cost = order_cost(tensors, order, output_labels)
+        if best is None or cost[0] < best[0][0]:
+            best = (cost, order)
+    return best[1]
+
+
+def slice_labels_by_weight(tensors, output_labels, order, count: int) -> List[int]:
+    """Indices to slice: repeatedly the label that appears in the most of the
+    largest intermediates of ``order`` (intermediate sizes recomputed after
+    each choice)."""
+    chosen: List[int] = []
+    for _ in range(count):
+        sub = slice_network(tensors, {l: 0 for l in chosen})
+        labs = [list(ls) for _, ls in sub]
+        from collections import Counter
+
+        cnt = Counter(l for ls in labs for l in ls)
+        for l in output_labels:
+            cnt[l] += 1
+        inter = []
+        for i, j in order:
+            a, b = labs[i], labs[j]
+            sh = set(a) & set(b)
+            res = [l for l in dict.fromkeys(a + b) if not (l in sh and cnt[l] == 2)]
+            for l in a + b:
+                cnt[l] -= 1
+            for l in res:
+                cnt[l] += 1
+            labs.append(res)
+            inter.append(res)
+        top = max(len(r) for r in inter)
+        weight: Dict[int, float] = {}
+        for r in inter:
+            if len(r) >= top - 2:
+                for l in r:
+                    if l not in output_labels:
+                        weight[l] = weight.get(l, 0.0) + 2.0 ** (len(r) - top)
+        chosen.append(min(weight, key=lambda l: (-weight[l], l)))
+    return chosen
+
+
 def contract_network(tensors, output_labels, order=None, use_loops: bool = False) -> np.ndarray:
     """Contract a whole network pairwise in ``order`` (default: greedy_order).
     A label is summed at the step after which no other tensor and not the

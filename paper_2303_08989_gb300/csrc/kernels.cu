@@ -691,8 +691,11 @@ namespace {
 struct CopyParams {
     int rank;
     int nx, ny, nr;       // sizes of the X, Y and rest groups
+    int pow2;             // every dim is a power of two: decompose with shifts
     int64_t px, py;       // products of the X and Y dims
     int64_t tiles_x, tiles_y;
+    int64_t rest;         // product of the rest dims
+    int8_t lg[QCS_MAX_RANK];  // log2 of each dim (when pow2)
     int64_t dims[QCS_MAX_RANK];
     int64_t is[QCS_MAX_RANK];
     int64_t os[QCS_MAX_RANK];
@@ -703,6 +706,16 @@ __device__ __forceinline__ void decompose(const CopyParams &P, const int8_t *g, 
                                           int64_t &io, int64_t &oo) {
     io = 0;
     oo = 0;
+    if (P.pow2) {
+        for (int t = 0; t < ng; ++t) {
+            const int d = g[t];
+            const int64_t c = v & ((int64_t(1) << P.lg[d]) - 1);
+            io += c * P.is[d];
+            oo += c * P.os[d];
+            v >>= P.lg[d];
+        }
+        return;
+    }
     for (int t = 0; t < ng; ++t) {
         const int d = g[t];
         const int64_t q = v / P.dims[d];
@@ -713,18 +726,21 @@ __device__ __forceinline__ void decompose(const CopyParams &P, const int8_t *g, 
     }
 }
 
+constexpr int kTilesPerBlock = 8;
+
 __global__ void __launch_bounds__(256) copy_tiled_kernel(CopyParams P, const float2 *__restrict__ in,
                                                          float2 *__restrict__ out, int accumulate) {
     __shared__ float2 tile[32][33];
-    __shared__ int64_t sxi[32], sxo[32], syi[32], syo[32], sr[2];
+    __shared__ int64_t sxi[32], sxo[32], syi[32], syo[32], sr[kTilesPerBlock][2];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     int64_t b = blockIdx.x;
     const int64_t bx = b % P.tiles_x;
     b /= P.tiles_x;
     const int64_t by = b % P.tiles_y;
-    const int64_t br = b / P.tiles_y;
+    const int64_t rb = (b / P.tiles_y) * kTilesPerBlock;  // first rest index of this block
     const int64_t x0 = bx * 32, y0 = by * 32;
-    // offsets of this tile's rows, columns and of the rest index, computed once
+    // offsets of the tile's rows and columns (shared by all its rest indices)
+    // and of each rest index, computed once
     if (threadIdx.x < 32) {
         const int64_t x = x0 + threadIdx.x;
         int64_t io = 0, oo = 0;
@@ -737,36 +753,40 @@ __global__ void __launch_bounds__(256) copy_tiled_kernel(CopyParams P, const flo
         if (y < P.py) decompose(P, P.gy, P.ny, y, io, oo);
         syi[threadIdx.x - 32] = io;
         syo[threadIdx.x - 32] = oo;
-    } else if (threadIdx.x == 64) {
-        int64_t io, oo;
-        decompose(P, P.gr, P.nr, br, io, oo);
-        sr[0] = io;
-        sr[1] = oo;
+    } else if (threadIdx.x < 64 + kTilesPerBlock) {
+        const int t = threadIdx.x - 64;
+        int64_t io = 0, oo = 0;
+        if (rb + t < P.rest) decompose(P, P.gr, P.nr, rb + t, io, oo);
+        sr[t][0] = io;
+        sr[t][1] = oo;
     }
     __syncthreads();
-    const int64_t ri = sr[0], ro = sr[1];
-    // read: lanes along y (contiguous input)
     const bool yok = (y0 + tx) < P.py;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int xl = ty + 8 * r;
-        if (yok && x0 + xl < P.px) tile[xl][tx] = in[ri + sxi[xl] + syi[tx]];
-    }
-    __syncthreads();
-    // write: lanes along x (contiguous output)
     const bool xok = (x0 + tx) < P.px;
+    for (int t = 0; t < kTilesPerBlock && rb + t < P.rest; ++t) {
+        const int64_t ri = sr[t][0], ro = sr[t][1];
+        if (t > 0) __syncthreads();  // the previous tile has been written out
+        // read: lanes along y (contiguous input)
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int yl = ty + 8 * r;
-        if (xok && y0 + yl < P.py) {
-            float2 v = tile[tx][yl];
-            float2 *dst = out + ro + sxo[tx] + syo[yl];
-            if (accumulate) {
-                const float2 w = *dst;
-                v.x += w.x;
-                v.y += w.y;
+        for (int r = 0; r < 4; ++r) {
+            const int xl = ty + 8 * r;
+            if (yok && x0 + xl < P.px) tile[xl][tx] = in[ri + sxi[xl] + syi[tx]];
+        }
+        __syncthreads();
+        // write: lanes along x (contiguous output)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int yl = ty + 8 * r;
+            if (xok && y0 + yl < P.py) {
+                float2 v = tile[tx][yl];
+                float2 *dst = out + ro + sxo[tx] + syo[yl];
+                if (accumulate) {
+                    const float2 w = *dst;
+                    v.x += w.x;
+                    v.y += w.y;
+                }
+                *dst = v;
             }
-            *dst = v;
         }
     }
 }
@@ -874,12 +894,17 @@ cudaError_t launch_copy(int rank, const int64_t *dims, const int64_t *is, const 
                         const float2 *in, float2 *out, int accumulate, cudaStream_t s) {
     CopyParams P{};
     P.rank = rank;
+    P.pow2 = 1;
     int64_t total = 1;
     for (int d = 0; d < rank; ++d) {
         P.dims[d] = dims[d];
         P.is[d] = is[d];
         P.os[d] = os[d];
         total *= dims[d];
+        if (dims[d] & (dims[d] - 1)) P.pow2 = 0;
+        int lg = 0;
+        while ((int64_t(1) << lg) < dims[d]) ++lg;
+        P.lg[d] = (int8_t)lg;
     }
     if (total == 0) return cudaSuccess;
     // dims contiguous from stride 1 on both sides (same dims, same order)
@@ -912,7 +937,8 @@ cudaError_t launch_copy(int rank, const int64_t *dims, const int64_t *is, const 
     }
     P.tiles_x = (P.px + 31) / 32;
     P.tiles_y = (P.py + 31) / 32;
-    const int64_t blocks = P.tiles_x * P.tiles_y * rest;
+    P.rest = rest;
+    const int64_t blocks = P.tiles_x * P.tiles_y * ((rest + kTilesPerBlock - 1) / kTilesPerBlock);
     if (blocks > INT32_MAX) return cudaErrorInvalidValue;
     copy_tiled_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, in, out, accumulate);
     return cudaGetLastError();
@@ -1168,19 +1194,99 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(
     }
 }
 
-// One thread per output element; thread t -> (i = t mod m, j = t div m), so
-// consecutive threads write consecutive elements of a column-major C.
-__global__ void cgemm_skinny_kernel(const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB,
-                                    int64_t m, int64_t n, int64_t k, float2 alpha,
-                                    const float2 *__restrict__ A, int64_t lda,
-                                    const float2 *__restrict__ B, int64_t ldb, float2 beta,
-                                    float2 *__restrict__ C, int64_t ldc) {
+// Small k with one small output side: the (2, 2^N, 2) and (2^N, 2, 2)
+// shapes of Section 5.1.2.
+//   rows: n <= 16, k <= KMAX: a thread per output row i keeps op(A)[i, :] in
+//         KMAX registers and writes its n outputs (consecutive threads write
+//         consecutive elements of each column of C).
+//   cols: m <= 16, k <= 16: a thread per output element, i = lane bits below
+//         log2(M2) (M2 = m rounded up to a power of two), j from the rest, so
+//         that a warp writes C contiguously when ldc == m; op(B)[:, j] is read
+//         by the M2 threads of column j (L1 broadcast).
+template <int KMAX>
+__global__ void __launch_bounds__(256) cgemm_skinny_rows_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int k,
+    float2 alpha, const float2 *__restrict__ A, int64_t lda, const float2 *__restrict__ B,
+    int64_t ldb, float2 beta, float2 *__restrict__ C, int64_t ldc) {
     if (desc && desc->mode != QCS_MODE_FP32) return;
-    const int64_t total = m * n;
     const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float2 a[KMAX];
+#pragma unroll
+        for (int l = 0; l < KMAX; ++l) a[l] = (l < k) ? ld_op(A, opA, i, l, lda) : make_float2(0.f, 0.f);
+        for (int64_t j = 0; j < n; ++j) {
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int l = 0; l < KMAX; ++l) {
+                if (l < k) {
+                    const float2 b = ld_op(B, opB, l, j, ldb);
+                    sr = fmaf(a[l].x, b.x, sr);
+                    sr = fmaf(-a[l].y, b.y, sr);
+                    si = fmaf(a[l].x, b.y, si);
+                    si = fmaf(a[l].y, b.x, si);
+                }
+            }
+            float2 o;
+            o.x = alpha.x * sr - alpha.y * si;
+            o.y = alpha.x * si + alpha.y * sr;
+            float2 *dst = C + i + j * ldc;
+            if (use_beta) {
+                const float2 c = *dst;
+                o.x += beta.x * c.x - beta.y * c.y;
+                o.y += beta.x * c.y + beta.y * c.x;
+            }
+            *dst = o;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) cgemm_skinny_cols_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int k,
+    int lg_m2, float2 alpha, const float2 *__restrict__ A, int64_t lda, const float2 *__restrict__ B,
+    int64_t ldb, float2 beta, float2 *__restrict__ C, int64_t ldc) {
+    if (desc && desc->mode != QCS_MODE_FP32) return;
+    const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
+    const int64_t total = n << lg_m2;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = t / m, i = t - j * m;
+        const int64_t i = t & ((int64_t(1) << lg_m2) - 1), j = t >> lg_m2;
+        if (i >= m) continue;
+        float sr = 0.f, si = 0.f;
+        for (int l = 0; l < k; ++l) {
+            const float2 a = ld_op(A, opA, i, l, lda);
+            const float2 b = ld_op(B, opB, l, j, ldb);
+            sr = fmaf(a.x, b.x, sr);
+            sr = fmaf(-a.y, b.y, sr);
+            si = fmaf(a.x, b.y, si);
+            si = fmaf(a.y, b.x, si);
+        }
+        float2 o;
+        o.x = alpha.x * sr - alpha.y * si;
+        o.y = alpha.x * si + alpha.y * sr;
+        float2 *dst = C + i + j * ldc;
+        if (use_beta) {
+            const float2 c = *dst;
+            o.x += beta.x * c.x - beta.y * c.y;
+            o.y += beta.x * c.y + beta.y * c.x;
+        }
+        *dst = o;
+    }
+}
+
+// One thread per output element on a 2-D grid (x: rows, consecutive threads
+// write consecutive elements of a column-major C; y: columns), k loop in the
+// thread: small k with both output sides large, or small outputs with
+// moderate k.
+__global__ void __launch_bounds__(256) cgemm_perelem_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int64_t k,
+    float2 alpha, const float2 *__restrict__ A, int64_t lda, const float2 *__restrict__ B,
+    int64_t ldb, float2 beta, float2 *__restrict__ C, int64_t ldc) {
+    if (desc && desc->mode != QCS_MODE_FP32) return;
+    const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
         float sr = 0.f, si = 0.f;
         for (int64_t l = 0; l < k; ++l) {
             const float2 a = ld_op(A, opA, i, l, lda);
@@ -1289,12 +1395,41 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
                                                                         alpha, beta, C, ldc);
         return cudaGetLastError();
     }
-    const bool skinny = (k <= 16) || (m * n <= 4096);
-    if (skinny || m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) {
-        const int64_t total = m * n;
-        const int64_t blocks = (total + 255) / 256;
-        cgemm_skinny_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, s>>>(
-            desc, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    if (k <= 16 && (m <= 16 || n <= 16)) {
+        if (m >= n) {  // then n <= 16: a thread per row
+            const int64_t blocks = (m + 255) / 256;
+            const unsigned grid = (unsigned)(blocks < 65536 ? blocks : 65536);
+            const int kk = (int)k;
+            if (kk <= 2)
+                cgemm_skinny_rows_kernel<2><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, kk, alpha, A,
+                                                                lda, B, ldb, beta, C, ldc);
+            else if (kk <= 4)
+                cgemm_skinny_rows_kernel<4><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, kk, alpha, A,
+                                                                lda, B, ldb, beta, C, ldc);
+            else if (kk <= 8)
+                cgemm_skinny_rows_kernel<8><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, kk, alpha, A,
+                                                                lda, B, ldb, beta, C, ldc);
+            else
+                cgemm_skinny_rows_kernel<16><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, kk, alpha, A,
+                                                                 lda, B, ldb, beta, C, ldc);
+        } else {  // m <= 16: a thread per element, rows in the low bits
+            int lg = 0;
+            while ((int64_t(1) << lg) < m) ++lg;
+            const int64_t total = n << lg;
+            const int64_t blocks = (total + 255) / 256;
+            const unsigned grid = (unsigned)(blocks < 65536 ? blocks : 65536);
+            cgemm_skinny_cols_kernel<<<grid, 256, 0, s>>>(desc, opA, opB, m, n, (int)k, lg, alpha, A,
+                                                          lda, B, ldb, beta, C, ldc);
+        }
+        return cudaGetLastError();
+    }
+    const bool perelem = (k <= 16) || (mn <= 4096);
+    if (perelem || m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) {
+        const int64_t bx = (m + 255) / 256;
+        if (bx > INT32_MAX) return cudaErrorInvalidValue;
+        dim3 grid((unsigned)bx, (unsigned)(n < 65535 ? n : 65535));
+        cgemm_perelem_kernel<<<grid, 256, 0, s>>>(desc, opA, opB, m, n, k, alpha, A, lda, B, ldb,
+                                                  beta, C, ldc);
         return cudaGetLastError();
     }
     dim3 grid((unsigned)((n + kSBN - 1) / kSBN), (unsigned)((m + kSBM - 1) / kSBM));

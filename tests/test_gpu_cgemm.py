@@ -266,3 +266,18 @@ def test_cgemm_fp32_split_k_small_outputs(h, m, n, k, opA, opB):
     # the element-wise FP32 bound: a single long dot product cancels too much for a
     # relative-error bar to apply to it
     assert np.all(np.abs(got - ref) <= bound)
+
+
+@pytest.mark.parametrize("m,n,k,opA,opB", [(2, 5000, 2, 0, 0), (5000, 2, 2, 0, 0), (3, 1000, 16, 1, 2),
+                                           (1000, 16, 7, 2, 1), (16, 16, 16, 0, 1), (2048, 300, 8, 0, 0),
+                                           (50, 60, 40, 1, 0)])
+def test_cgemm_fp32_skinny_and_per_element_shapes(h, m, n, k, opA, opB):
+    """The bandwidth-bound FP32 kernels of Section 5.1.2's irregular shapes."""
+    A, B = _operands(m, n, k, opA, opB, 3, seed=(m, n, k, 9), ldpad=2)
+    C0 = qi.cgemm_operand(m, n, 0, seed=6, ld=m + 1)
+    alpha, beta = 0.5 + 1j, -0.25
+    got, d = _run(h, "fp32", m, n, k, opA, opB, A, B, alpha, beta, C0)
+    ref = oracle.cgemm(opA, opB, m, n, k, alpha, A, B, beta, C0)
+    bound = (2 * k + 8) * 2.0 ** -24 * (abs(alpha) * 2 * abs_bound(A, B, opA, opB, m, k, n)
+                                        + abs(beta) * 2 * np.abs(C0[:m, :n]))
+    assert np.all(np.abs(got - ref) <= bound + 1e-30)

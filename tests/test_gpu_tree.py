@@ -214,3 +214,58 @@ def test_graph_replay_equals_eager(h, mode, n_slices):
         g.close()
     finally:
         h.set_size_rule(True)
+
+
+def _golden_slices(path):
+    labels, rows = None, []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            if line.startswith("sliced"):
+                labels = [int(v) for v in line.split()[1:]]
+                continue
+            v, re, im = line.split()
+            rows.append((v, float(re) + 1j * float(im)))
+    return labels, rows
+
+
+def sampled_slice_plan(tn, circ, bits, labels, values, seed=5):
+    """The plan restricted to the given slice assignments, one output slot each."""
+    import copy
+
+    net = tn.circuit_network(circ, bits)
+    order = tn.greedy_order(net, seed=seed, skip=[tn.BATCH] + labels)
+    plan = tn.build_plan(net, order, labels)
+    idx = [int(v, 2) for v in values]  # the first sliced index varies slowest
+    sub = copy.copy(plan)
+    sub.instance_offset = np.ascontiguousarray(plan.instance_offset[idx])
+    sub.instance_slot = np.arange(len(idx), dtype=np.int32)
+    sub.n_slots = len(idx)
+    return plan, sub
+
+
+def test_40_qubit_sampled_slices_vs_fp64_golden(h, golden_dir):
+    """Precision at scale: a 40-qubit 5x8 grid circuit (depth 12), sliced on
+    8 indices (256 slices); four sampled slices, contracted with AUTO-0.1 per
+    GEMM, against the oracle's FP64 contraction of the same slices."""
+    import os
+
+    path = os.path.join(golden_dir, "slices5x8_d12.txt")
+    if not os.path.exists(path):
+        pytest.skip("golden file not written")
+    tn = _tn()
+    labels, rows = _golden_slices(path)
+    circ = qi.random_grid_circuit(5, 8, 12, seed=0)
+    bits = qi.random_bitstrings(40, 1, seed=1)
+    plan, sub = sampled_slice_plan(tn, circ, bits, labels, [v for v, _ in rows])
+    assert plan.n_instances == 256 and plan.max_log2_size <= 30
+    h.set_tol(0.1)
+    try:
+        got, info = _run(h, sub)
+    finally:
+        h.set_tol(0.0)
+    ref = np.array([a for _, a in rows])
+    a = got[:, 0]
+    assert oracle.fidelity(ref, a) >= 1 - 1e-5
+    assert np.all(np.abs(a - ref) <= 1e-4 * np.abs(ref)), (a, ref)

@@ -476,3 +476,21 @@ def test_inplace_statevector_matches_tensordot_statevector():
         np.testing.assert_allclose(a, b, atol=1e-13)
         x = qi.random_bitstrings(rows * cols, 1, seed=9)[0]
         assert a[oracle.bit_index(x)] == b[oracle.bit_index(x)] or abs(a[oracle.bit_index(x)] - b[oracle.bit_index(x)]) < 1e-14
+
+
+def test_random_greedy_order_and_slice_chooser_preserve_the_amplitude():
+    circ = qi.random_grid_circuit(3, 3, 6, seed=2)
+    bits = qi.random_bitstrings(9, 1, seed=3)[0]
+    tn, outl = oracle.circuit_tn(circ, bits)
+    ref = oracle.statevector(circ)[tuple(int(b) for b in bits)]
+    order = oracle.random_greedy_order(tn, outl, seeds=range(3))
+    assert abs(complex(oracle.contract_network(tn, outl, order)) - ref) < 1e-13
+    flops, big = oracle.order_cost(tn, order, outl)
+    for seed in range(3):  # the best of the seeds is no worse than any one of them
+        single = oracle.random_greedy_order(tn, outl, seeds=[seed])
+        assert flops <= oracle.order_cost(tn, single, outl)[0]
+    labels = oracle.slice_labels_by_weight(tn, outl, order, 3)
+    assert len(set(labels)) == 3
+    total = sum(complex(oracle.contract_network(oracle.slice_network(tn, dict(zip(labels, v))), outl))
+                for v in np.ndindex(2, 2, 2))
+    assert abs(total - ref) < 1e-13
