@@ -458,6 +458,9 @@ def hbm_legs(q, torch, dev, h, stages, n):
     return res
 
 
+MODE_KEYS = ["auto", "fp16x", "fp16x_scaled", "tf32x", "fp32", "bf16x3"]
+
+
 def _time_plan(torch, cp, h, instances=None, reps=1):
     """Seconds per call of qcs_contract_tree (CUDA events), optionally on the
     first ``instances`` instances of the plan only."""
@@ -474,6 +477,67 @@ def _time_plan(torch, cp, h, instances=None, reps=1):
     return e0.elapsed_time(e1) / reps * 1e-3, out
 
 
+def _time_graph(torch, cp, h, reps=2):
+    """Seconds per replay of the plan's forward captured in a CUDA graph."""
+    g, out = cp.graph(h)
+    g.launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    g.close()
+    return e0.elapsed_time(e1) / reps * 1e-3, out
+
+
+def _routing(info, counts):
+    """GEMMs per mode that actually ran in one call: the host-decided modes of
+    qcs_run_info_t, with the AUTO ones replaced by what the device selected."""
+    host = dict(zip(MODE_KEYS, info["mode_count"]))
+    ran = {k: host[k] + counts.get(k, 0) for k in MODE_KEYS[1:]}
+    total = max(sum(ran.values()), 1)
+    return {"gemms": ran, "fraction": {k: round(v / total, 4) for k, v in ran.items()}}
+
+
+def _contract_variants(args, q, tn, torch, dev, make_plan, ns, variants):
+    """Seconds per instance (slice) of one plan under several (mode, size
+    rule) variants, each on its own handle: eager calls and a CUDA-graph
+    replay of ``ns`` instances, the routing of the GEMMs, and for the tuned
+    rule the tuning cost and decisions."""
+    res = {}
+    for name, mode, rule in variants:
+        h = q.Handle(tol=args.tol, size_rule=rule)
+        plan = make_plan(q.MODE_BY_NAME[mode])
+        cp = tn.CompiledPlan(plan, device=dev)
+        cp.tree.n_instances = ns
+        e = {}
+        if rule == q.SIZE_RULE_TUNED:
+            t0 = time.perf_counter()
+            e["shapes_tuned"] = cp.autotune(h, reps=2)
+            e["tuning_s"] = time.perf_counter() - t0
+            best = {}
+            for t in h.tuning():
+                best[t["best"]] = best.get(t["best"], 0) + 1
+            e["tuned_decisions"] = best
+        secs, _ = _time_plan(torch, cp, h)
+        h.auto_counts(reset=True)
+        out = cp.forward(h)
+        counts = h.auto_counts(reset=True)
+        info = tn.info_dict(cp.last_info)
+        gsecs, gout = _time_graph(torch, cp, h)
+        e.update({"s_per_slice": gsecs / ns, "s_per_slice_eager": secs / ns, "slices_timed": ns,
+                  "tflops": info["flops"] / gsecs / 1e12, "gemms_per_slice": info["gemm_count"] / ns,
+                  "routing": _routing(info, counts)})
+        e["_out"] = out.cpu().numpy()
+        res[name] = e
+        h.close()
+        del cp
+        torch.cuda.empty_cache()
+    return res
+
+
 def tree_legs(args, q, torch, dev, rank):
     """The contraction half of the metric (s/slice, AUTO vs all-FP32), the
     plain small-grid amplitudes and the differentiated workload."""
@@ -483,48 +547,40 @@ def tree_legs(args, q, torch, dev, rank):
     import qcs_inputs as qi
 
     res = {}
-    h = q.Handle(tol=args.tol, size_rule=True)
+    variants = [("auto", "auto", q.SIZE_RULE_TUNED), ("auto_paper_rule", "auto", q.SIZE_RULE_PAPER),
+                ("fp32", "fp32", q.SIZE_RULE_PAPER)]
     # 30-qubit 5x6 grid, depth 14, sliced on 6 indices (64 slices), one bitstring
     circ = qi.random_grid_circuit(5, 6, 14, seed=0)
     bits = qi.random_bitstrings(30, 1, seed=1)
-    per = {}
-    for mode in ("auto", "fp32"):
-        plan = tn.plan_circuit(circ, bits, seed=2, n_slices=6, mode=q.MODE_BY_NAME[mode])
-        cp = tn.CompiledPlan(plan, device=dev)
-        ns = min(args.tree_slices, plan.n_instances)
-        secs, out = _time_plan(torch, cp, h, instances=ns)
-        info = tn.info_dict(cp.last_info)
-        per[mode] = {"s_per_slice": secs / ns, "slices_timed": ns,
-                     "tflops": info["flops"] / secs / 1e12,
-                     "gemms_per_slice": info["gemm_count"] / ns,
-                     "gemm_modes": dict(zip(["auto", "fp16x", "fp16x_scaled", "tf32x", "fp32",
-                                             "bf16x3"], info["mode_count"]))}
-        res_plan = plan
+    plans = {}
+
+    def make_plan(mode):
+        plans[mode] = tn.plan_circuit(circ, bits, seed=2, n_slices=6, mode=mode)
+        return plans[mode]
+
+    ns = min(args.tree_slices, 64)
+    per = _contract_variants(args, q, tn, torch, dev, make_plan, ns, variants)
+    p = plans[q.MODE_AUTO]
+    a, b = per["auto"].pop("_out")[0, 0], per["fp32"].pop("_out")[0, 0]
+    per["auto_paper_rule"].pop("_out")
     res["contraction"] = {
         "workload": "5x6 grid random circuit, depth 14, seeded greedy order, 6 sliced indices "
-                    "(64 slices), 1 bitstring; AUTO-%g vs all-FP32" % args.tol,
-        "slices_total": res_plan.n_instances, "flops_per_slice": res_plan.flops,
-        "max_intermediate_log2": res_plan.max_log2_size,
-        "auto": per["auto"], "fp32": per["fp32"],
+                    "(64 slices), 1 bitstring; AUTO-%g (measured size rule) vs all-FP32, "
+                    "CUDA-graph replays of %d slices" % (args.tol, ns),
+        "slices_total": p.n_instances, "flops_per_slice": p.flops,
+        "max_intermediate_log2": p.max_log2_size,
+        "auto": per["auto"], "auto_paper_rule": per["auto_paper_rule"], "fp32": per["fp32"],
+        "auto_vs_fp32_rel_diff": float(abs(a - b) / abs(b)),
         "speedup_vs_fp32": per["fp32"]["s_per_slice"] / per["auto"]["s_per_slice"],
     }
+    h = q.Handle(tol=args.tol, size_rule=True)
     # plain method, smallest size: 3x4 grid, depth 8, 64 bitstrings (FP32 path by the size rule)
     c0 = qi.random_grid_circuit(3, 4, 8, seed=0)
     b0 = qi.random_bitstrings(12, 64, seed=1)
     p0 = tn.plan_circuit(c0, b0, seed=2)
     cp0 = tn.CompiledPlan(p0, device=dev)
     secs0, out0 = _time_plan(torch, cp0, h, reps=3)
-    g0, gout = cp0.graph(h)
-    g0.launch()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(3):
-        g0.launch()
-    e1.record()
-    torch.cuda.synchronize()
-    secs_g = e0.elapsed_time(e1) / 3 * 1e-3
-    g0.close()
+    secs_g, _ = _time_graph(torch, cp0, h, reps=3)
     res["plain_small"] = {"workload": "3x4 grid, depth 8, 64 bitstrings, greedy order",
                           "s_per_batch": secs0, "s_per_batch_cuda_graph": secs_g,
                           "gemms": cp0.last_info.gemm_count}
@@ -533,23 +589,27 @@ def tree_legs(args, q, torch, dev, rank):
 
         ref = oracle.sv_amplitudes(c0, b0)
         res["plain_small"]["fidelity_vs_fp64"] = oracle.fidelity(ref, out0.cpu().numpy()[:, 0])
+    h.close()
     # differentiation: 4x5 grid, depth 12, free fSim parameters, 256 bitstrings
     c4 = qi.random_grid_circuit(4, 5, 12, seed=0, theta=None, phi=None, param_seed=3)
     b4 = qi.random_bitstrings(20, 256, seed=1)
     p0s = np.array([g.params for g in c4.gates if g.name == "fsim"])
     diff = {}
-    for mode in ("auto", "fp32"):
+    for mode, rule in (("auto", q.SIZE_RULE_TUNED), ("fp32", q.SIZE_RULE_PAPER)):
+        hd = q.Handle(tol=args.tol, size_rule=rule)
         net = tn.circuit_network(c4, None)
         order = tn.greedy_order(net, seed=2)
         sliced = tn.choose_slices(net, order, n_labels=2)
         plan = tn.build_plan(net, order, sliced, mode=q.MODE_BY_NAME[mode], outputs=b4)
         cp = tn.CompiledPlan(plan, device=dev, leaf_data=[])
+        if rule == q.SIZE_RULE_TUNED:
+            cp.autotune(hd, backward=True, reps=2)
         params = torch.tensor(p0s, dtype=torch.float32, device=dev, requires_grad=True)
 
         def fwd_bwd():
             params.grad = None
             leaves = tn.torch_leaves(plan.net, c4, params, device=dev)
-            amps = tn.contract(cp, h, leaves)
+            amps = tn.contract(cp, hd, leaves)
             loss = torch.log(amps.abs() ** 2).sum()
             loss.backward()
             return loss
@@ -561,9 +621,10 @@ def tree_legs(args, q, torch, dev, rank):
         torch.cuda.synchronize()
         diff[mode] = {"s_fwd_bwd": time.perf_counter() - t0, "loss": float(loss.item()),
                       "grad": params.grad.double().cpu().numpy()}
+        hd.close()
     out4 = {"workload": "4x5 grid, depth 12, fSim(theta, phi) ~ U[0, pi], loss sum log|a|^2 "
                         "over 256 bitstrings; open network, 2 sliced indices (4 slices, "
-                        "recomputed in the backward)",
+                        "recomputed in the backward); AUTO with the measured size rule",
             "auto_s": diff["auto"]["s_fwd_bwd"], "fp32_s": diff["fp32"]["s_fwd_bwd"],
             "speedup_vs_fp32": diff["fp32"]["s_fwd_bwd"] / diff["auto"]["s_fwd_bwd"]}
     if rank == 0:
@@ -575,16 +636,15 @@ def tree_legs(args, q, torch, dev, rank):
             out4[f"{mode}_grad_rel_l2_vs_fp64"] = float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))
             out4[f"{mode}_loss_rel_vs_fp64"] = abs(diff[mode]["loss"] - L_ref) / abs(L_ref)
     res["differentiation"] = out4
-    res["precision_at_scale"] = scale_leg(args, q, torch, dev, h, tn, qi, rank)
-    h.close()
+    res["precision_at_scale"] = scale_leg(args, q, torch, dev, tn, qi, rank)
     return res
 
 
-def scale_leg(args, q, torch, dev, h, tn, qi, rank):
+def scale_leg(args, q, torch, dev, tn, qi, rank):
     """40-qubit 5x8 grid, depth 12 (the depth a seeded greedy order slices to
     <= 2^30 with 256 slices), sliced on the 8 indices the oracle chose for its
     FP64 sample: AUTO vs all-FP32 seconds per slice on a sample of slices, the
-    GEMM modes AUTO picked, and the four FP64-checked slices."""
+    fraction of GEMMs routed to each mode, and the four FP64-checked slices."""
     import copy
 
     import numpy as np
@@ -604,36 +664,38 @@ def scale_leg(args, q, torch, dev, h, tn, qi, rank):
     bits = qi.random_bitstrings(40, 1, seed=1)
     net = tn.circuit_network(circ, bits)
     order = tn.greedy_order(net, seed=5, skip=[tn.BATCH] + labels)
-    out = {"workload": "5x8 grid (40 qubits), depth 12, 8 sliced indices (256 slices), seeded "
-                       "greedy order, 1 bitstring; AUTO-%g vs all-FP32" % args.tol}
-    per = {}
-    for mode in ("auto", "fp32"):
-        plan = tn.build_plan(net, order, labels, mode=q.MODE_BY_NAME[mode])
-        cp = tn.CompiledPlan(plan, device=dev)
-        ns = min(16, plan.n_instances)
-        secs, amp = _time_plan(torch, cp, h, instances=ns)
-        info = tn.info_dict(cp.last_info)
-        per[mode] = {"s_per_slice": secs / ns, "slices_timed": ns, "partial_sum": complex(amp.cpu().numpy()[0, 0]),
-                     "gemm_modes": dict(zip(["auto", "fp16x", "fp16x_scaled", "tf32x", "fp32", "bf16x3"],
-                                            info["mode_count"]))}
-        out["flops_per_slice"] = plan.flops
-        out["max_intermediate_log2"] = plan.max_log2_size
-        if mode == "auto":
-            idx = [int(v, 2) for v, _ in rows]
-            sub = copy.copy(plan)
-            sub.instance_offset = np.ascontiguousarray(plan.instance_offset[idx])
-            sub.instance_slot = np.arange(len(idx), dtype=np.int32)
-            sub.n_slots = len(idx)
-            got = tn.CompiledPlan(sub, device=dev).forward(h).cpu().numpy()[:, 0]
-            if rank == 0:
-                import oracle
+    plans = {}
 
-                ref = np.array([a for _, a in rows])
-                out["sampled_slices_fidelity_vs_fp64"] = oracle.fidelity(ref, got)
-                out["sampled_slices_max_rel_err_vs_fp64"] = float(np.max(np.abs(got - ref) / np.abs(ref)))
-    a, b = per["auto"].pop("partial_sum"), per["fp32"].pop("partial_sum")
+    def make_plan(mode):
+        plans[mode] = tn.build_plan(net, order, labels, mode=mode)
+        return plans[mode]
+
+    variants = [("auto", "auto", q.SIZE_RULE_TUNED), ("fp32", "fp32", q.SIZE_RULE_PAPER)]
+    per = _contract_variants(args, q, tn, torch, dev, make_plan, 16, variants)
+    plan = plans[q.MODE_AUTO]
+    out = {"workload": "5x8 grid (40 qubits), depth 12, 8 sliced indices (256 slices), seeded "
+                       "greedy order, 1 bitstring; AUTO-%g (measured size rule) vs all-FP32, "
+                       "CUDA-graph replays of 16 slices" % args.tol,
+           "flops_per_slice": plan.flops, "max_intermediate_log2": plan.max_log2_size}
+    h = q.Handle(tol=args.tol, size_rule=q.SIZE_RULE_TUNED)
+    idx = [int(v, 2) for v, _ in rows]
+    sub = copy.copy(plan)
+    sub.instance_offset = np.ascontiguousarray(plan.instance_offset[idx])
+    sub.instance_slot = np.arange(len(idx), dtype=np.int32)
+    sub.n_slots = len(idx)
+    cps = tn.CompiledPlan(sub, device=dev)
+    cps.autotune(h, reps=2)
+    got = cps.forward(h).cpu().numpy()[:, 0]
+    h.close()
+    if rank == 0:
+        import oracle
+
+        ref = np.array([a for _, a in rows])
+        out["sampled_slices_fidelity_vs_fp64"] = oracle.fidelity(ref, got)
+        out["sampled_slices_max_rel_err_vs_fp64"] = float(np.max(np.abs(got - ref) / np.abs(ref)))
+    a, b = per["auto"].pop("_out")[0, 0], per["fp32"].pop("_out")[0, 0]
     out["auto"], out["fp32"] = per["auto"], per["fp32"]
-    out["auto_vs_fp32_rel_diff"] = abs(a - b) / abs(b)
+    out["auto_vs_fp32_rel_diff"] = float(abs(a - b) / abs(b))
     out["speedup_vs_fp32"] = per["fp32"]["s_per_slice"] / per["auto"]["s_per_slice"]
     return out
 

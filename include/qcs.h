@@ -55,6 +55,7 @@ typedef enum {
     QCS_MODE_FP32 = 4,
     QCS_MODE_BF16X3 = 5
 } qcs_mode_t;
+#define QCS_NUM_MODES 6
 
 typedef enum { QCS_OP_N = 0, QCS_OP_T = 1, QCS_OP_C = 2 } qcs_op_t;
 
@@ -102,11 +103,21 @@ int qcs_set_stream(qcs_handle_t h, void *cuda_stream);
  * fall outside that mode's exponent window.  Default 0 (no underflow). */
 int qcs_set_underflow_tol(qcs_handle_t h, double t);
 
-/* Enable (1, default) or disable (0) the size rule of Section 4.3 for
- * QCS_MODE_AUTO: min(m,n,k) >= 2048 -> automatic selection; >= 512 ->
- * TF32X; else FP32.  With the rule disabled AUTO always selects from the
- * statistics. */
-int qcs_set_size_rule(qcs_handle_t h, int enabled);
+/* Size rule for QCS_MODE_AUTO (Section 4.3: small GEMMs do not repay the
+ * statistics and split passes):
+ *   QCS_SIZE_RULE_OFF    AUTO always selects from the statistics;
+ *   QCS_SIZE_RULE_PAPER  the paper's cut-offs, measured on its GPU:
+ *                        min(m,n,k) >= 2048 -> automatic selection, >= 512 ->
+ *                        TF32X, else FP32 (default);
+ *   QCS_SIZE_RULE_TUNED  the decision measured on this GPU for the shape by
+ *                        qcs_autotune_gemm / qcs_autotune_tree (or loaded
+ *                        with qcs_set_tuning); shapes never tuned fall back
+ *                        to the PAPER cut-offs.
+ * Any other nonzero value means PAPER. */
+#define QCS_SIZE_RULE_OFF 0
+#define QCS_SIZE_RULE_PAPER 1
+#define QCS_SIZE_RULE_TUNED 2
+int qcs_set_size_rule(qcs_handle_t h, int rule);
 
 /* Round-to-nearest drain interval of the tensor-core kernels: the hi*hi
  * products are summed in tensor memory for ``stages`` pipeline stages (each
@@ -312,6 +323,53 @@ int qcs_cgemm_noalloc(void *cuda_stream, qcs_mode_t mode, double underflow_tol, 
                       const qcs_c32 *A, int64_t lda, const qcs_c32 *B, int64_t ldb,
                       const qcs_c32 *beta, qcs_c32 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out);
 
+/* ---- autotuning: the size rule re-derived on this GPU ------------------ */
+
+/* One tuned shape.  The key is (m, n, k, opA, opB) as qcs_cgemm receives
+ * them.  ms[mode] is the measured time of one call in that forced mode
+ * (QCS_MODE_AUTO: statistics + selection + the selected path), negative
+ * when the candidate was not run (pruned: an FP32 call that cannot win).
+ * best is what QCS_SIZE_RULE_TUNED then runs for an AUTO GEMM of this shape:
+ * QCS_MODE_AUTO (statistics decide), QCS_MODE_TF32X (no statistics: TF32
+ * has FP32's exponent range) or QCS_MODE_FP32. */
+typedef struct {
+    int64_t m, n, k;
+    int32_t opA, opB;
+    float ms[QCS_NUM_MODES];
+    int32_t best;
+    int32_t reps;
+} qcs_tune_entry_t;
+
+/* Time the candidates for one shape on the handle's stream and record the
+ * fastest in the handle's table (replacing an earlier entry for the key).
+ * Operands are synthetic, allocated by this call (cudaMalloc of op(A),
+ * op(B) and C) and freed before it returns: parts of magnitude in [1, 2)
+ * with random signs, so that the statistics select FP16X.  Each candidate
+ * runs once untimed, then ``reps`` (>= 1) times between CUDA events;
+ * FP32 is not run when 8 m n k / 45 TFLOP/s is above 4x the faster
+ * emulated candidate.  Ties go to the earlier of AUTO, TF32X, FP32.
+ * Synchronizes the stream; not during a stream capture.  out (host,
+ * optional) receives the entry.  m, n, k >= 1. */
+int qcs_autotune_gemm(qcs_handle_t h, qcs_op_t transA, qcs_op_t transB, int64_t m, int64_t n,
+                      int64_t k, int reps, qcs_tune_entry_t *out);
+
+/* qcs_autotune_gemm for every distinct AUTO GEMM shape that
+ * qcs_contract_tree (and, with backward != 0, qcs_contract_tree_backward)
+ * issues for the plan, skipping shapes already in the table.  n_tuned
+ * (host, optional) receives the number of shapes timed.  The plan is
+ * validated as qcs_contract_tree validates it. */
+int qcs_autotune_tree(qcs_handle_t h, const qcs_tree_t *tree, int backward, int reps,
+                      int64_t *n_tuned);
+
+/* Read the handle's table: up to ``capacity`` entries (in key order) into
+ * ``entries`` (host); *count receives the table's size. */
+int qcs_get_tuning(qcs_handle_t h, qcs_tune_entry_t *entries, int64_t capacity, int64_t *count);
+
+/* Add entries (host) to the handle's table, e.g. decisions saved from an
+ * earlier process on the same GPU; each replaces the entry of its key.
+ * best must be AUTO, TF32X or FP32. */
+int qcs_set_tuning(qcs_handle_t h, const qcs_tune_entry_t *entries, int64_t count);
+
 /* Stage timing (tracing aid, off by default).  While enabled, every call
  * records a pair of CUDA events on the handle's stream around each stage
  * it launches.  qcs_get_profile() synchronizes the stream, writes the
@@ -323,6 +381,16 @@ int qcs_cgemm_noalloc(void *cuda_stream, qcs_mode_t mode, double underflow_tol, 
 #define QCS_PROFILE_STAGES 7
 int qcs_set_profiling(qcs_handle_t h, int enabled);
 int qcs_get_profile(qcs_handle_t h, double *ms, int64_t *counts, int n);
+
+/* What the automatic selection (Section 4.1) chose: counts[i] (host array of
+ * QCS_NUM_MODES) receives how many GEMMs of mode AUTO on this handle -- after
+ * the size rule, so only those that ran the statistics -- selected
+ * qcs_mode_t i on the device since the handle was created or last reset.
+ * (The selection happens on the device, so the host-side mode counts of
+ * qcs_run_info_t only know that such a GEMM was AUTO.)  Synchronizes the
+ * handle's stream.  reset != 0 clears the counters afterwards.  Graph
+ * replays count too. */
+int qcs_get_auto_counts(qcs_handle_t h, int64_t *counts, int reset);
 
 /* Wait for the handle's stream; return TIMEOUT if a device-side bounded
  * wait gave up since the last qcs_sync (the word is then cleared), CUDA on

@@ -12,12 +12,14 @@ from typing import Optional
 
 from . import _lib
 from ._lib import (MODE_AUTO, MODE_BF16X3, MODE_BY_NAME, MODE_FP16X, MODE_FP16X_SCALED, MODE_FP32,
-                   MODE_NAME, MODE_TF32X, OP_C, OP_N, OP_T, QcsError)
+                   MODE_NAME, MODE_TF32X, OP_C, OP_N, OP_T, SIZE_RULE_OFF, SIZE_RULE_PAPER,
+                   SIZE_RULE_TUNED, QcsError)
 
 __all__ = [
     "Handle", "cgemm", "exp_stats", "select", "split", "permute", "fortran_empty", "to_fortran",
     "MODE_AUTO", "MODE_FP16X", "MODE_FP16X_SCALED", "MODE_TF32X", "MODE_FP32", "MODE_BF16X3",
     "MODE_BY_NAME", "MODE_NAME", "OP_N", "OP_T", "OP_C", "QcsError",
+    "SIZE_RULE_OFF", "SIZE_RULE_PAPER", "SIZE_RULE_TUNED",
 ]
 
 
@@ -64,9 +66,11 @@ def to_fortran(x, device="cuda"):
 
 
 class Handle:
-    """Owns a qcs handle (workspace, tolerance, size rule) bound to a stream."""
+    """Owns a qcs handle (workspace, tolerance, size rule, tuning table)
+    bound to a stream.  ``size_rule``: True/1 the paper's cut-offs, False/0
+    none, 2 (SIZE_RULE_TUNED) the per-shape decisions of ``autotune_*``."""
 
-    def __init__(self, stream=None, tol: float = 0.0, size_rule: bool = True):
+    def __init__(self, stream=None, tol: float = 0.0, size_rule=True):
         torch = _torch()
         self.lib = _lib.load()
         self._h = ctypes.c_void_p()
@@ -89,9 +93,47 @@ class Handle:
         _lib.check(self.lib.qcs_set_underflow_tol(self._h, float(t)), "qcs_set_underflow_tol")
         self.tol = float(t)
 
-    def set_size_rule(self, on: bool):
-        _lib.check(self.lib.qcs_set_size_rule(self._h, 1 if on else 0))
-        self.size_rule = bool(on)
+    def set_size_rule(self, rule):
+        rule = int(rule) if not isinstance(rule, bool) else (SIZE_RULE_PAPER if rule else SIZE_RULE_OFF)
+        _lib.check(self.lib.qcs_set_size_rule(self._h, rule))
+        self.size_rule = rule
+
+    def auto_counts(self, reset: bool = True):
+        """{mode name: count} of what AUTO GEMMs on this handle selected on the
+        device (qcs_get_auto_counts); synchronizes the stream."""
+        c = (ctypes.c_int64 * _lib.NUM_MODES)()
+        _lib.check(self.lib.qcs_get_auto_counts(self._h, c, 1 if reset else 0), "qcs_get_auto_counts")
+        return {MODE_NAME[i]: int(c[i]) for i in range(_lib.NUM_MODES)}
+
+    def autotune_gemm(self, m: int, n: int, k: int, opA: int = OP_N, opB: int = OP_N,
+                      reps: int = 3) -> dict:
+        """Time AUTO / TF32X / FP32 for one shape and record the fastest in the
+        handle's table (qcs_autotune_gemm)."""
+        e = _lib.qcs_tune_entry_t()
+        _lib.check(self.lib.qcs_autotune_gemm(self._h, int(opA), int(opB), int(m), int(n), int(k),
+                                              int(reps), ctypes.byref(e)), "qcs_autotune_gemm")
+        return _tune_dict(e)
+
+    def tuning(self) -> list:
+        """The handle's tuning table as a list of dicts (qcs_get_tuning)."""
+        cnt = ctypes.c_int64()
+        _lib.check(self.lib.qcs_get_tuning(self._h, None, 0, ctypes.byref(cnt)), "qcs_get_tuning")
+        arr = (_lib.qcs_tune_entry_t * max(cnt.value, 1))()
+        _lib.check(self.lib.qcs_get_tuning(self._h, arr, cnt.value, ctypes.byref(cnt)),
+                   "qcs_get_tuning")
+        return [_tune_dict(arr[i]) for i in range(cnt.value)]
+
+    def set_tuning(self, entries: list):
+        """Load entries (dicts as returned by ``tuning``) into the table."""
+        arr = (_lib.qcs_tune_entry_t * max(len(entries), 1))()
+        for i, d in enumerate(entries):
+            e = arr[i]
+            e.m, e.n, e.k, e.opA, e.opB = d["m"], d["n"], d["k"], d["opA"], d["opB"]
+            for j in range(_lib.NUM_MODES):
+                e.ms[j] = d["ms"].get(MODE_NAME[j], -1.0)
+            e.best = MODE_BY_NAME[d["best"]]
+            e.reps = d.get("reps", 0)
+        _lib.check(self.lib.qcs_set_tuning(self._h, arr, len(entries)), "qcs_set_tuning")
 
     def set_drain_stages(self, stages: int):
         _lib.check(self.lib.qcs_set_drain_stages(self._h, int(stages)), "qcs_set_drain_stages")
@@ -121,6 +163,12 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+
+def _tune_dict(e) -> dict:
+    return {"m": e.m, "n": e.n, "k": e.k, "opA": e.opA, "opB": e.opB,
+            "ms": {MODE_NAME[j]: e.ms[j] for j in range(_lib.NUM_MODES) if e.ms[j] >= 0},
+            "best": MODE_NAME[e.best], "reps": e.reps}
 
 
 def cgemm(h: Handle, A, B, C=None, *, m=None, n=None, k=None, alpha=1.0, beta=0.0,

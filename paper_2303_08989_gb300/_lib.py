@@ -32,8 +32,11 @@ EXPORTED = [
     "qcs_exp_stats", "qcs_select", "qcs_cgemm", "qcs_split", "qcs_permute", "qcs_contract_tree",
     "qcs_contract_tree_backward", "qcs_set_profiling", "qcs_get_profile", "qcs_sync",
     "qcs_status_string", "qcs_cgemm_noalloc", "qcs_tree_graph_create", "qcs_tree_graph_launch",
-    "qcs_tree_graph_destroy",
+    "qcs_tree_graph_destroy", "qcs_get_auto_counts", "qcs_autotune_gemm", "qcs_autotune_tree",
+    "qcs_get_tuning", "qcs_set_tuning",
 ]
+SIZE_RULE_OFF, SIZE_RULE_PAPER, SIZE_RULE_TUNED = 0, 1, 2
+NUM_MODES = 6
 PROFILE_STAGES = ["stats", "select", "split", "gemm_tc", "gemm_simt", "permute", "reduce"]
 
 
@@ -57,6 +60,12 @@ class qcs_gemm_desc_t(ctypes.Structure):
 
 
 MAX_RANK = 32
+
+
+class qcs_tune_entry_t(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("opA", ctypes.c_int32), ("opB", ctypes.c_int32),
+                ("ms", ctypes.c_float * 6), ("best", ctypes.c_int32), ("reps", ctypes.c_int32)]
 
 
 class qcs_gather_t(ctypes.Structure):
@@ -130,6 +139,11 @@ def load(path: str = LIB_PATH):
                                   ctypes.POINTER(ctypes.c_void_p)],
         "qcs_tree_graph_launch": [P],
         "qcs_tree_graph_destroy": [P],
+        "qcs_get_auto_counts": [H, ctypes.POINTER(I64), I],
+        "qcs_autotune_gemm": [H, I, I, I64, I64, I64, I, ctypes.POINTER(qcs_tune_entry_t)],
+        "qcs_autotune_tree": [H, ctypes.POINTER(qcs_tree_t), I, I, ctypes.POINTER(I64)],
+        "qcs_get_tuning": [H, ctypes.POINTER(qcs_tune_entry_t), I64, ctypes.POINTER(I64)],
+        "qcs_set_tuning": [H, ctypes.POINTER(qcs_tune_entry_t), I64],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

@@ -1,0 +1,183 @@
+// Autotuning of the AUTO size rule (qcs_autotune_gemm, qcs_get_tuning,
+// qcs_set_tuning; qcs_autotune_tree lives with the executor).
+//
+// Section 4.3 decides from min(m, n, k) alone whether a GEMM is worth the
+// statistics and split passes, with cut-offs measured on the paper's GPU.
+// Here the decision is measured per shape on this GPU: the candidates AUTO
+// (statistics + selection + the selected emulated path), TF32X (split +
+// tensor-core GEMM, no statistics) and FP32 (SIMT) run on synthetic operands
+// of the shape and the fastest is recorded in the handle's table, which
+// QCS_SIZE_RULE_TUNED consults.  Every candidate keeps the FP32 accuracy
+// level, so the choice is about time only.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <tuple>
+
+#include "internal.h"
+
+namespace qcs {
+namespace {
+
+// Complex parts of magnitude in [1, 2) with random signs: every exponent is
+// 0, so the statistics select FP16X whatever the tolerance.  The bits come
+// from SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom
+// number generators", 2014) of the element index.
+__global__ void fill_unit_binade(float2 *__restrict__ x, int64_t n, uint64_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const uint32_t a = (uint32_t)z, b = (uint32_t)(z >> 32);
+        x[i] = make_float2(__uint_as_float(0x3F800000u | (a & 0x807FFFFFu)),
+                           __uint_as_float(0x3F800000u | (b & 0x807FFFFFu)));
+    }
+}
+
+constexpr double kFp32BoundFlops = 45e12;  // above the SIMT CGEMM's measured rate
+constexpr float kFp32Prune = 4.0f;
+const int kCandidates[3] = {QCS_MODE_AUTO, QCS_MODE_TF32X, QCS_MODE_FP32};
+
+struct DeviceBuffer {
+    void *p = nullptr;
+    ~DeviceBuffer() {
+        if (p) cudaFree(p);
+    }
+};
+
+}  // namespace
+
+int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k, int reps,
+               qcs_tune_entry_t *out) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return QCS_ERR_UNSUPPORTED;
+    const int64_t ra = (opA == QCS_OP_N) ? m : k, ca = (opA == QCS_OP_N) ? k : m;
+    const int64_t rb = (opB == QCS_OP_N) ? k : n, cb = (opB == QCS_OP_N) ? n : k;
+    size_t ws = 0;
+    for (int c : kCandidates) ws = std::max(ws, gemm_workspace_bytes(c, m, n, k, h->num_sms));
+    if (int r = ensure_workspace(h->ws, ws)) return r;
+    DeviceBuffer A, B, C;
+    if (cudaMalloc(&A.p, sizeof(float2) * ra * ca) != cudaSuccess ||
+        cudaMalloc(&B.p, sizeof(float2) * rb * cb) != cudaSuccess ||
+        cudaMalloc(&C.p, sizeof(float2) * m * n) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_ALLOC;
+    }
+    float2 *dA = static_cast<float2 *>(A.p), *dB = static_cast<float2 *>(B.p);
+    float2 *dC = static_cast<float2 *>(C.p);
+    const unsigned grid = (unsigned)(4 * h->num_sms);
+    fill_unit_binade<<<grid, 256, 0, h->stream>>>(dA, ra * ca, 0x5151ull);
+    fill_unit_binade<<<grid, 256, 0, h->stream>>>(dB, rb * cb, 0xA2A2ull);
+    if (cudaGetLastError() != cudaSuccess) return QCS_ERR_CUDA;
+
+    qcs_tune_entry_t e{};
+    e.m = m;
+    e.n = n;
+    e.k = k;
+    e.opA = opA;
+    e.opB = opB;
+    e.reps = reps;
+    for (float &v : e.ms) v = -1.f;
+
+    // Tuning calls are not the caller's work: no profile records, no
+    // selection counts.
+    const int profiling = h->profiling;
+    unsigned long long *counts = h->d_counts;
+    h->profiling = 0;
+    h->d_counts = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = QCS_SUCCESS;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = QCS_ERR_CUDA;
+    auto run = [&](int mode) {
+        return run_cgemm(h, h->ws.ptr, mode, opA, opB, m, n, k, make_float2(1.f, 0.f), dA, ra, dB,
+                         rb, make_float2(0.f, 0.f), dC, m, nullptr, nullptr);
+    };
+    auto time_mode = [&](int mode) -> int {
+        if (int r = run(mode)) return r;  // untimed first call
+        if (cudaEventRecord(e0, h->stream) != cudaSuccess) return QCS_ERR_CUDA;
+        for (int i = 0; i < reps; ++i)
+            if (int r = run(mode)) return r;
+        if (cudaEventRecord(e1, h->stream) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess)
+            return QCS_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return QCS_ERR_CUDA;
+        e.ms[mode] = ms / (float)reps;
+        return QCS_SUCCESS;
+    };
+    if (rc == QCS_SUCCESS) rc = time_mode(QCS_MODE_AUTO);
+    if (rc == QCS_SUCCESS) rc = time_mode(QCS_MODE_TF32X);
+    if (rc == QCS_SUCCESS) {
+        const float emulated = std::min(e.ms[QCS_MODE_AUTO], e.ms[QCS_MODE_TF32X]);
+        const double fp32_bound_ms = 8.0 * (double)m * (double)n * (double)k / kFp32BoundFlops * 1e3;
+        if (fp32_bound_ms <= kFp32Prune * emulated) rc = time_mode(QCS_MODE_FP32);
+    }
+    h->profiling = profiling;
+    h->d_counts = counts;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc != QCS_SUCCESS) {
+        cudaGetLastError();
+        return rc;
+    }
+    e.best = QCS_MODE_AUTO;
+    for (int c : kCandidates)
+        if (e.ms[c] >= 0.f && e.ms[c] < e.ms[e.best]) e.best = c;
+    h->tuned[std::make_tuple(m, n, k, opA, opB)] = e;
+    if (out) *out = e;
+    return QCS_SUCCESS;
+}
+
+}  // namespace qcs
+
+using namespace qcs;
+
+namespace {
+bool valid_tune_op(int op) { return op == QCS_OP_N || op == QCS_OP_T || op == QCS_OP_C; }
+}  // namespace
+
+extern "C" {
+
+int qcs_autotune_gemm(qcs_handle_t h, qcs_op_t transA, qcs_op_t transB, int64_t m, int64_t n,
+                      int64_t k, int reps, qcs_tune_entry_t *out) {
+    if (!h || !valid_tune_op(transA) || !valid_tune_op(transB) || m < 1 || n < 1 || k < 1 ||
+        reps < 1)
+        return QCS_ERR_INVALID_ARG;
+    if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) return QCS_ERR_UNSUPPORTED;
+    return tune_shape(h, transA, transB, m, n, k, reps, out);
+}
+
+int qcs_get_tuning(qcs_handle_t h, qcs_tune_entry_t *entries, int64_t capacity, int64_t *count) {
+    if (!h || capacity < 0 || (capacity > 0 && !entries)) return QCS_ERR_INVALID_ARG;
+    int64_t i = 0;
+    for (const auto &kv : h->tuned) {
+        if (i >= capacity) break;
+        entries[i++] = kv.second;
+    }
+    if (count) *count = (int64_t)h->tuned.size();
+    return QCS_SUCCESS;
+}
+
+int qcs_set_tuning(qcs_handle_t h, const qcs_tune_entry_t *entries, int64_t count) {
+    if (!h || count < 0 || (count > 0 && !entries)) return QCS_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < count; ++i) {
+        const qcs_tune_entry_t &e = entries[i];
+        if (e.m < 1 || e.n < 1 || e.k < 1 || !valid_tune_op(e.opA) || !valid_tune_op(e.opB) ||
+            (e.best != QCS_MODE_AUTO && e.best != QCS_MODE_TF32X && e.best != QCS_MODE_FP32))
+            return QCS_ERR_INVALID_ARG;
+    }
+    for (int64_t i = 0; i < count; ++i) {
+        const qcs_tune_entry_t &e = entries[i];
+        h->tuned[std::make_tuple(e.m, e.n, e.k, (int)e.opA, (int)e.opB)] = e;
+    }
+    return QCS_SUCCESS;
+}
+
+}  // extern "C"

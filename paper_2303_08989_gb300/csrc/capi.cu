@@ -126,8 +126,13 @@ void plane_strides(int which, int op, int64_t ld, int64_t &sr, int64_t &sc) {
 }  // namespace
 
 // Effective mode after the size rule (host side, sizes are known on the host).
-int qcs::effective_mode(qcs_handle_t h, int mode, int64_t m, int64_t n, int64_t k) {
-    if (mode != QCS_MODE_AUTO || !h->size_rule) return mode;
+int qcs::effective_mode(qcs_handle_t h, int mode, int opA, int opB, int64_t m, int64_t n,
+                        int64_t k) {
+    if (mode != QCS_MODE_AUTO || h->size_rule == QCS_SIZE_RULE_OFF) return mode;
+    if (h->size_rule == QCS_SIZE_RULE_TUNED) {
+        const auto it = h->tuned.find(std::make_tuple(m, n, k, opA, opB));
+        if (it != h->tuned.end()) return it->second.best;
+    }
     const int64_t s = std::min(m, std::min(n, k));
     if (s >= 2048) return QCS_MODE_AUTO;
     if (s >= 512) return QCS_MODE_TF32X;
@@ -174,10 +179,12 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
         {
             ProfScope ps(h, kProfStats);
             e = launch_stats_select_2stage(A, ra, ca, lda, gA, B, rb, cb, ldb, gB, h->tol, eff,
-                                           partials, partials + 5 * (gA + gB), desc, s);
+                                           partials, partials + 5 * (gA + gB), desc,
+                                           h->d_counts, s);
         }
         if (e != cudaSuccess) return QCS_ERR_CUDA;
-    } else {
+    } else if (eff != QCS_MODE_FP32 || d_desc_out) {
+        // A plain FP32 GEMM runs ungated; it needs a descriptor only to report it.
         e = launch_set_desc(desc, eff, s);
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     }
@@ -283,12 +290,14 @@ int qcs_create(qcs_handle_t *out, void *cuda_stream) {
         return QCS_ERR_CUDA;
     }
     h->stream = static_cast<cudaStream_t>(cuda_stream);
-    if (cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess) {
+    // One block: the error word at byte 0, the selection counters at byte 8.
+    if (cudaMalloc(&h->d_err, kStatusBlockBytes) != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return QCS_ERR_ALLOC;
     }
-    cudaMemset(h->d_err, 0, sizeof(int));
+    cudaMemset(h->d_err, 0, kStatusBlockBytes);
+    h->d_counts = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(h->d_err) + 8);
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
@@ -301,7 +310,10 @@ int qcs_create(qcs_handle_t *out, void *cuda_stream) {
     }
     h->encode = reinterpret_cast<EncodeTiledFn>(fn);
     if (const char *t = std::getenv("QCS_UNDERFLOW_TOL")) h->tol = std::atof(t);
-    if (const char *r = std::getenv("QCS_SIZE_RULE")) h->size_rule = std::atoi(r) != 0;
+    if (const char *r = std::getenv("QCS_SIZE_RULE")) {
+        const int v = std::atoi(r);
+        h->size_rule = (v == QCS_SIZE_RULE_OFF || v == QCS_SIZE_RULE_TUNED) ? v : QCS_SIZE_RULE_PAPER;
+    }
     if (const char *d = std::getenv("QCS_DRAIN_STAGES")) {
         const int v = std::atoi(d);
         h->drain_stages = (v >= 4) ? 4 : (v == 2 ? 2 : 1);
@@ -343,9 +355,10 @@ int qcs_set_drain_stages(qcs_handle_t h, int stages) {
     return QCS_SUCCESS;
 }
 
-int qcs_set_size_rule(qcs_handle_t h, int enabled) {
+int qcs_set_size_rule(qcs_handle_t h, int rule) {
     if (!h) return QCS_ERR_INVALID_ARG;
-    h->size_rule = enabled ? 1 : 0;
+    h->size_rule = (rule == QCS_SIZE_RULE_OFF || rule == QCS_SIZE_RULE_TUNED) ? rule
+                                                                              : QCS_SIZE_RULE_PAPER;
     return QCS_SUCCESS;
 }
 
@@ -380,7 +393,7 @@ int qcs_cgemm(qcs_handle_t h, qcs_mode_t mode, qcs_op_t transA, qcs_op_t transB,
         return r;
     if (m == 0 || n == 0) return QCS_SUCCESS;
     if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) return QCS_ERR_UNSUPPORTED;
-    const int eff = effective_mode(h, mode, m, n, k);
+    const int eff = effective_mode(h, mode, transA, transB, m, n, k);
     if (int r = ensure_workspace(h->ws, gemm_workspace_bytes(eff, m, n, k, h->num_sms))) return r;
     const float2 al = make_float2(alpha->x, alpha->y), be = make_float2(beta->x, beta->y);
     return run_cgemm(h, h->ws.ptr, eff, transA, transB, m, n, k, al,
@@ -464,6 +477,25 @@ int qcs_sync(qcs_handle_t h) {
     if (err != 0) {
         cudaMemset(h->d_err, 0, sizeof(int));
         return QCS_ERR_TIMEOUT;
+    }
+    return QCS_SUCCESS;
+}
+
+int qcs_get_auto_counts(qcs_handle_t h, int64_t *counts, int reset) {
+    if (!h || !counts) return QCS_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    unsigned long long c[QCS_NUM_MODES];
+    if (cudaMemcpy(c, h->d_counts, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    for (int i = 0; i < QCS_NUM_MODES; ++i) counts[i] = (int64_t)c[i];
+    if (reset && cudaMemset(h->d_counts, 0, sizeof(c)) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
     }
     return QCS_SUCCESS;
 }

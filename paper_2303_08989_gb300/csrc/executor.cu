@@ -20,6 +20,8 @@
 #include <algorithm>
 #include <chrono>
 #include <new>
+#include <set>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -133,12 +135,17 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward) {
         p += align256(sizeof(float2) * st.m * st.n);
         maxA = std::max(maxA, st.m * st.k);
         maxB = std::max(maxB, st.k * st.n);
-        gemm = std::max(gemm, gemm_workspace_bytes(effective_mode(h, st.mode, st.m, st.n, st.k),
+        const int opA = st.direct_a == QCS_OP_T ? QCS_OP_T : QCS_OP_N;
+        const int opB = st.direct_b == QCS_OP_T ? QCS_OP_T : QCS_OP_N;
+        gemm = std::max(gemm, gemm_workspace_bytes(effective_mode(h, st.mode, opA, opB, st.m, st.n,
+                                                                  st.k),
                                                    st.m, st.n, st.k, h->num_sms));
         if (backward) {
-            gemm = std::max(gemm, gemm_workspace_bytes(effective_mode(h, st.mode, st.m, st.k, st.n),
+            gemm = std::max(gemm, gemm_workspace_bytes(effective_mode(h, st.mode, QCS_OP_N,
+                                                                      QCS_OP_C, st.m, st.k, st.n),
                                                        st.m, st.k, st.n, h->num_sms));
-            gemm = std::max(gemm, gemm_workspace_bytes(effective_mode(h, st.mode, st.k, st.n, st.m),
+            gemm = std::max(gemm, gemm_workspace_bytes(effective_mode(h, st.mode, QCS_OP_C,
+                                                                      QCS_OP_N, st.k, st.n, st.m),
                                                        st.k, st.n, st.m, h->num_sms));
         }
     }
@@ -203,7 +210,7 @@ int gather(const Ctx &c, const qcs_gather_t &g, const float2 *src, float2 *dst) 
 
 int gemm(const Ctx &c, int mode, int opA, int opB, int64_t m, int64_t n, int64_t k,
          const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 *C) {
-    const int eff = effective_mode(c.h, mode, m, n, k);
+    const int eff = effective_mode(c.h, mode, opA, opB, m, n, k);
     count_gemm(c, eff, m, n, k);
     return run_cgemm(c.h, c.ws + c.L.gemm, eff, opA, opB, m, n, k, make_float2(1.f, 0.f), A, lda,
                      B, ldb, make_float2(0.f, 0.f), C, m, nullptr, nullptr);
@@ -391,6 +398,41 @@ int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
     if (info)
         info->seconds =
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return QCS_SUCCESS;
+}
+
+int qcs_autotune_tree(qcs_handle_t h, const qcs_tree_t *tree, int backward, int reps,
+                      int64_t *n_tuned) {
+    if (n_tuned) *n_tuned = 0;
+    if (!h || !tree || reps < 1) return QCS_ERR_INVALID_ARG;
+    std::vector<int64_t> size_of;
+    if (int r = validate(tree, size_of, backward != 0)) return r;
+    // The (m, n, k, opA, opB) of every AUTO GEMM the executor issues: the
+    // forward GEMM of each step (op T for a direct transposed operand,
+    // else N) and, for the adjoint, grad_A = grad_out B_mat^H and
+    // grad_B = A_mat^H grad_out on gathered operands.
+    std::set<std::tuple<int64_t, int64_t, int64_t, int, int>> keys;
+    for (int s = 0; s < tree->n_steps; ++s) {
+        const qcs_step_t &st = tree->steps[s];
+        if (st.mode != QCS_MODE_AUTO) continue;
+        keys.insert(std::make_tuple(st.m, st.n, st.k,
+                                    st.direct_a == QCS_OP_T ? (int)QCS_OP_T : (int)QCS_OP_N,
+                                    st.direct_b == QCS_OP_T ? (int)QCS_OP_T : (int)QCS_OP_N));
+        if (backward) {
+            keys.insert(std::make_tuple(st.m, st.k, st.n, (int)QCS_OP_N, (int)QCS_OP_C));
+            keys.insert(std::make_tuple(st.k, st.n, st.m, (int)QCS_OP_C, (int)QCS_OP_N));
+        }
+    }
+    int64_t count = 0;
+    for (const auto &key : keys) {
+        if (h->tuned.count(key)) continue;
+        const int64_t m = std::get<0>(key), n = std::get<1>(key), k = std::get<2>(key);
+        if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) continue;
+        if (int r = tune_shape(h, std::get<3>(key), std::get<4>(key), m, n, k, reps, nullptr))
+            return r;
+        ++count;
+    }
+    if (n_tuned) *n_tuned = count;
     return QCS_SUCCESS;
 }
 

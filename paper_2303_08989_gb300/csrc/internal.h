@@ -5,6 +5,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "../../include/qcs.h"
@@ -45,6 +47,7 @@ constexpr size_t kSplitKBytes = size_t(kSplitKMaxPartials) * 8;
 // (256 bins + zero count).
 constexpr int kStatsThreads = 128;
 constexpr int kPartialStride = 257;
+constexpr size_t kStatusBlockBytes = 64;  // handle's error word + AUTO selection counters
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -81,13 +84,16 @@ struct qcs_handle_s {
     double tol = 0.0;
     int size_rule = 1;
     int drain_stages = 4;            // stages per RN drain of the tensor-core hi*hi sum
-    int *d_err = nullptr;            // device error word
+    int *d_err = nullptr;            // device error word (start of a 64-byte block)
+    unsigned long long *d_counts = nullptr;  // in that block: AUTO selections per mode
     qcs::Workspace ws;               // GEMM workspace (planes, partials, descriptor)
     qcs::Workspace tree_ws;          // contraction-tree intermediates
     qcs::EncodeTiledFn encode = nullptr;
     int profiling = 0;
     std::vector<qcs::ProfEvent> prof;     // recorded, not yet read
     std::vector<cudaEvent_t> event_pool;  // reusable events
+    // (m, n, k, opA, opB) -> measured decision (QCS_SIZE_RULE_TUNED)
+    std::map<std::tuple<int64_t, int64_t, int64_t, int, int>, qcs_tune_entry_t> tuned;
 };
 
 namespace qcs {
@@ -122,11 +128,13 @@ cudaError_t launch_select(const int64_t *partials, int gA, int gB, int64_t nA, i
 // Two-stage statistics + selection for the GEMM path: pass 1 (e_max,
 // zeros, Inf/NaN, count below 2^-14), pass 2 only when needed (count below
 // the shifted window), final selection.  gA / gB blocks of 256 threads per
-// matrix; p1 holds 5 int64 per block, p2 one.
+// matrix; p1 holds 5 int64 per block, p2 one.  ``counts`` (optional, 6
+// entries indexed by qcs_mode_t) gets one increment for the selected mode.
 cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t cols0, int64_t ld0,
                                        int gA, const float2 *X1, int64_t rows1, int64_t cols1,
                                        int64_t ld1, int gB, double tol, int forced, int64_t *p1,
-                                       int64_t *p2, qcs_gemm_desc_t *desc, cudaStream_t s);
+                                       int64_t *p2, qcs_gemm_desc_t *desc,
+                                       unsigned long long *counts, cudaStream_t s);
 // Select from two finished qcs_stats_t.
 cudaError_t launch_select_from_stats(const qcs_stats_t *a, const qcs_stats_t *b, double tol,
                                      qcs_gemm_desc_t *desc, cudaStream_t s);
@@ -156,7 +164,10 @@ cudaError_t launch_seed_grad(const double *g, const int64_t *index, float2 *grad
                              int64_t count, cudaStream_t s);
 
 // ---- shared with the executor (capi.cu) ------------------------------------
-int effective_mode(qcs_handle_t h, int mode, int64_t m, int64_t n, int64_t k);
+int effective_mode(qcs_handle_t h, int mode, int opA, int opB, int64_t m, int64_t n, int64_t k);
+// Time the candidate modes of one shape (qcs_autotune_gemm without validation).
+int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k, int reps,
+               qcs_tune_entry_t *out);
 size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms);
 int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n, int64_t k,
               float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta,

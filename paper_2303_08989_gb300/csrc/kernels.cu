@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(kS2Threads) stats_pass2_kernel(
 
 __global__ void select2_kernel(const int64_t *__restrict__ p1, const int64_t *__restrict__ p2,
                                int gA, int gB, int64_t nA, int64_t nB, double tol, int forced,
-                               qcs_gemm_desc_t *desc) {
+                               qcs_gemm_desc_t *desc, unsigned long long *counts) {
     __shared__ uint64_t shs[kS2Threads / 32];
     __shared__ uint32_t shm[kS2Threads / 32];
     const Sum1 a = reduce_p1(p1, 0, gA, nA, shm, shs);
@@ -467,6 +467,7 @@ __global__ void select2_kernel(const int64_t *__restrict__ p1, const int64_t *__
     sa.under2 = (int64_t)u2a;
     sb.under2 = (int64_t)u2b;
     select_rule(sa, sb, tol, forced, desc);
+    if (counts) atomicAdd(&counts[desc->mode], 1ULL);
 }
 
 static bool g_stats_configured = false;
@@ -497,7 +498,8 @@ cudaError_t launch_select(const int64_t *partials, int gA, int gB, int64_t nA, i
 cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t cols0, int64_t ld0,
                                        int gA, const float2 *X1, int64_t rows1, int64_t cols1,
                                        int64_t ld1, int gB, double tol, int forced, int64_t *p1,
-                                       int64_t *p2, qcs_gemm_desc_t *desc, cudaStream_t s) {
+                                       int64_t *p2, qcs_gemm_desc_t *desc,
+                                       unsigned long long *counts, cudaStream_t s) {
     stats_pass1_kernel<<<gA + gB, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1, cols1,
                                                       ld1, gB, p1);
     cudaError_t e = cudaGetLastError();
@@ -507,7 +509,7 @@ cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     select2_kernel<<<1, kS2Threads, 0, s>>>(p1, p2, gA, gB, 2 * rows0 * cols0, 2 * rows1 * cols1,
-                                            tol, forced, desc);
+                                            tol, forced, desc, counts);
     return cudaGetLastError();
 }
 
@@ -1342,32 +1344,46 @@ __global__ void __launch_bounds__(256) cgemm_splitk_kernel(
     if (lane == 0) part[c * mn + o] = make_float2(sr, si);
 }
 
-__global__ void cgemm_splitk_reduce(const qcs_gemm_desc_t *__restrict__ desc, int64_t m, int64_t n,
-                                    int64_t chunks, const float2 *__restrict__ part, float2 alpha,
-                                    float2 beta, float2 *__restrict__ C, int64_t ldc) {
+// One block per output: thread t adds chunks t, t + 256, ... in order, then a
+// fixed shared-memory tree adds the 256 sums, so the result does not depend
+// on scheduling.
+__global__ void __launch_bounds__(256) cgemm_splitk_reduce(
+    const qcs_gemm_desc_t *__restrict__ desc, int64_t m, int64_t n, int64_t chunks,
+    const float2 *__restrict__ part, float2 alpha, float2 beta, float2 *__restrict__ C,
+    int64_t ldc) {
     if (desc && desc->mode != QCS_MODE_FP32) return;
+    __shared__ float2 red[256];
     const int64_t mn = m * n;
-    const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
-    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < mn;
-         o += (int64_t)gridDim.x * blockDim.x) {
-        float sr = 0.f, si = 0.f;
-        for (int64_t c = 0; c < chunks; ++c) {
-            const float2 v = part[c * mn + o];
-            sr += v.x;
-            si += v.y;
-        }
-        const int64_t i = o % m, j = o / m;
-        float2 r;
-        r.x = alpha.x * sr - alpha.y * si;
-        r.y = alpha.x * si + alpha.y * sr;
-        float2 *dst = C + i + j * ldc;
-        if (use_beta) {
-            const float2 cv = *dst;
-            r.x += beta.x * cv.x - beta.y * cv.y;
-            r.y += beta.x * cv.y + beta.y * cv.x;
-        }
-        *dst = r;
+    const int64_t o = blockIdx.x;
+    float sr = 0.f, si = 0.f;
+    for (int64_t c = threadIdx.x; c < chunks; c += 256) {
+        const float2 v = part[c * mn + o];
+        sr += v.x;
+        si += v.y;
     }
+    red[threadIdx.x] = make_float2(sr, si);
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            const float2 a = red[threadIdx.x], b = red[threadIdx.x + w];
+            red[threadIdx.x] = make_float2(a.x + b.x, a.y + b.y);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    sr = red[0].x;
+    si = red[0].y;
+    const int64_t i = o % m, j = o / m;
+    float2 r;
+    r.x = alpha.x * sr - alpha.y * si;
+    r.y = alpha.x * si + alpha.y * sr;
+    float2 *dst = C + i + j * ldc;
+    if ((beta.x != 0.f) || (beta.y != 0.f)) {
+        const float2 cv = *dst;
+        r.x += beta.x * cv.x - beta.y * cv.y;
+        r.y += beta.x * cv.y + beta.y * cv.x;
+    }
+    *dst = r;
 }
 
 }  // namespace
@@ -1391,8 +1407,8 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
                                                              A, lda, B, ldb, splitk);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        cgemm_splitk_reduce<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(desc, m, n, chunks, splitk,
-                                                                        alpha, beta, C, ldc);
+        cgemm_splitk_reduce<<<(unsigned)mn, 256, 0, s>>>(desc, m, n, chunks, splitk, alpha, beta, C,
+                                                         ldc);
         return cudaGetLastError();
     }
     if (k <= 16 && (m <= 16 || n <= 16)) {

@@ -479,6 +479,15 @@ class CompiledPlan:
         self.last_info = info
         return grads
 
+    def autotune(self, h, backward: bool = False, reps: int = 3) -> int:
+        """Time the candidate modes of every AUTO GEMM shape this plan issues
+        (qcs_autotune_tree) and record them in ``h``'s table; returns the
+        number of shapes timed.  Use with ``h.set_size_rule(SIZE_RULE_TUNED)``."""
+        n = ctypes.c_int64()
+        _lib.check(h.lib.qcs_autotune_tree(h.ptr, ctypes.byref(self.tree), 1 if backward else 0,
+                                           int(reps), ctypes.byref(n)), "qcs_autotune_tree")
+        return int(n.value)
+
 
 class TreeGraph:
     """An instantiated CUDA graph of one plan's forward call."""

@@ -126,9 +126,21 @@ SQRT_GATES = {
 _SQRT_NAMES = ("sqrtX", "sqrtY", "sqrtW")
 
 
+def _cos_sin(theta: float) -> Tuple[float, float]:
+    """cos and sin of theta, evaluated on arguments reduced against pi/2 and
+    pi so that a quarter or half turn gives an exact zero.  np.cos(np.pi / 2)
+    is 6.1e-17, the rounding error of the double nearest pi/2, not a
+    property of the gate: left in, it makes every "zero" of fSim(pi/2, .) a
+    tiny nonzero that spreads through a network's intermediates."""
+    theta = float(theta)
+    c = np.sin(np.pi / 2 - abs(theta))
+    s = np.sin(theta) if abs(theta) <= np.pi / 2 else np.sin(np.copysign(np.pi, theta) - theta)
+    return float(c), float(s)
+
+
 def fsim(theta: float, phi: float) -> np.ndarray:
     """fSim(theta, phi) in the basis |00>, |01>, |10>, |11> (complex128)."""
-    c, s = np.cos(theta), np.sin(theta)
+    c, s = _cos_sin(theta)
     return np.array(
         [
             [1, 0, 0, 0],
