@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--no-tree", action="store_true", help="skip the contraction-tree legs")
     p.add_argument("--tree-slices", type=int, default=4,
                    help="slices of the 30-qubit network timed per mode")
+    p.add_argument("--instance-batch", type=int, default=4,
+                   help="contraction instances per group (plain-FP32 steps batched)")
     return p.parse_args()
 
 
@@ -501,16 +503,19 @@ def _routing(info, counts):
     return {"gemms": ran, "fraction": {k: round(v / total, 4) for k, v in ran.items()}}
 
 
-def _contract_variants(args, q, tn, torch, dev, make_plan, ns, variants):
+def _contract_variants(args, q, tn, torch, dev, make_plan, ns, variants, full=False):
     """Seconds per instance (slice) of one plan under several (mode, size
-    rule) variants, each on its own handle: eager calls and a CUDA-graph
-    replay of ``ns`` instances, the routing of the GEMMs, and for the tuned
-    rule the tuning cost and decisions."""
+    rule, tolerance) variants, each on its own handle: eager calls and a
+    CUDA-graph replay of ``ns`` instances, the routing of the GEMMs, for the
+    tuned rule the tuning cost and decisions, and with ``full`` the result of
+    all instances (``_full``)."""
     res = {}
-    for name, mode, rule in variants:
-        h = q.Handle(tol=args.tol, size_rule=rule)
+    for name, mode, rule, tol in variants:
+        h = q.Handle(tol=tol, size_rule=rule)
+        h.set_instance_batch(args.instance_batch)
         plan = make_plan(q.MODE_BY_NAME[mode])
         cp = tn.CompiledPlan(plan, device=dev)
+        n_all = cp.tree.n_instances
         cp.tree.n_instances = ns
         e = {}
         if rule == q.SIZE_RULE_TUNED:
@@ -528,9 +533,14 @@ def _contract_variants(args, q, tn, torch, dev, make_plan, ns, variants):
         info = tn.info_dict(cp.last_info)
         gsecs, gout = _time_graph(torch, cp, h)
         e.update({"s_per_slice": gsecs / ns, "s_per_slice_eager": secs / ns, "slices_timed": ns,
+                  "instance_batch": args.instance_batch,
+                  "workspace_gb": info["workspace_bytes"] / 1e9,
                   "tflops": info["flops"] / gsecs / 1e12, "gemms_per_slice": info["gemm_count"] / ns,
                   "routing": _routing(info, counts)})
         e["_out"] = out.cpu().numpy()
+        if full:
+            cp.tree.n_instances = n_all
+            e["_full"] = cp.forward(h).cpu().numpy()
         res[name] = e
         h.close()
         del cp
@@ -547,8 +557,10 @@ def tree_legs(args, q, torch, dev, rank):
     import qcs_inputs as qi
 
     res = {}
-    variants = [("auto", "auto", q.SIZE_RULE_TUNED), ("auto_paper_rule", "auto", q.SIZE_RULE_PAPER),
-                ("fp32", "fp32", q.SIZE_RULE_PAPER)]
+    variants = [("auto", "auto", q.SIZE_RULE_TUNED, args.tol),
+                ("auto_t0.5", "auto", q.SIZE_RULE_TUNED, 0.5),
+                ("auto_paper_rule", "auto", q.SIZE_RULE_PAPER, args.tol),
+                ("fp32", "fp32", q.SIZE_RULE_PAPER, 0.0)]
     # 30-qubit 5x6 grid, depth 14, sliced on 6 indices (64 slices), one bitstring
     circ = qi.random_grid_circuit(5, 6, 14, seed=0)
     bits = qi.random_bitstrings(30, 1, seed=1)
@@ -559,19 +571,34 @@ def tree_legs(args, q, torch, dev, rank):
         return plans[mode]
 
     ns = min(args.tree_slices, 64)
-    per = _contract_variants(args, q, tn, torch, dev, make_plan, ns, variants)
+    per = _contract_variants(args, q, tn, torch, dev, make_plan, ns, variants, full=True)
     p = plans[q.MODE_AUTO]
-    a, b = per["auto"].pop("_out")[0, 0], per["fp32"].pop("_out")[0, 0]
-    per["auto_paper_rule"].pop("_out")
+    # the FP64 amplitude of this bitstring (oracle state vector, tests/golden)
+    ref = None
+    gpath = os.path.join(ROOT, "tests", "golden", "grid5x6_d14_amplitudes.txt")
+    want = "".join(str(int(v)) for v in bits[0])
+    if os.path.exists(gpath):
+        with open(gpath) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 3 and parts[0] == want:
+                    ref = float(parts[1]) + 1j * float(parts[2])
+    for v in per.values():
+        v.pop("_out")
+        amp = complex(v.pop("_full")[0, 0])
+        if ref is not None:
+            v["amplitude_rel_err_vs_fp64"] = abs(amp - ref) / abs(ref)
     res["contraction"] = {
         "workload": "5x6 grid random circuit, depth 14, seeded greedy order, 6 sliced indices "
                     "(64 slices), 1 bitstring; AUTO-%g (measured size rule) vs all-FP32, "
-                    "CUDA-graph replays of %d slices" % (args.tol, ns),
+                    "CUDA-graph replays of %d slices; amplitude over all 64 slices vs the FP64 "
+                    "state vector" % (args.tol, ns),
         "slices_total": p.n_instances, "flops_per_slice": p.flops,
         "max_intermediate_log2": p.max_log2_size,
-        "auto": per["auto"], "auto_paper_rule": per["auto_paper_rule"], "fp32": per["fp32"],
-        "auto_vs_fp32_rel_diff": float(abs(a - b) / abs(b)),
+        "auto": per["auto"], "auto_t0.5": per["auto_t0.5"],
+        "auto_paper_rule": per["auto_paper_rule"], "fp32": per["fp32"],
         "speedup_vs_fp32": per["fp32"]["s_per_slice"] / per["auto"]["s_per_slice"],
+        "speedup_vs_fp32_t0.5": per["fp32"]["s_per_slice"] / per["auto_t0.5"]["s_per_slice"],
     }
     h = q.Handle(tol=args.tol, size_rule=True)
     # plain method, smallest size: 3x4 grid, depth 8, 64 bitstrings (FP32 path by the size rule)
@@ -581,8 +608,14 @@ def tree_legs(args, q, torch, dev, rank):
     cp0 = tn.CompiledPlan(p0, device=dev)
     secs0, out0 = _time_plan(torch, cp0, h, reps=3)
     secs_g, _ = _time_graph(torch, cp0, h, reps=3)
+    # all 64 bitstrings as one group: every step one batched launch
+    h.set_instance_batch(64)
+    secs_b, out_b = _time_plan(torch, cp0, h, reps=3)
+    secs_bg, _ = _time_graph(torch, cp0, h, reps=3)
     res["plain_small"] = {"workload": "3x4 grid, depth 8, 64 bitstrings, greedy order",
                           "s_per_batch": secs0, "s_per_batch_cuda_graph": secs_g,
+                          "s_per_batch_grouped": secs_b, "s_per_batch_grouped_cuda_graph": secs_bg,
+                          "grouped_bit_identical": bool(torch.equal(out0, out_b)),
                           "gemms": cp0.last_info.gemm_count}
     if rank == 0:
         import oracle
@@ -670,33 +703,40 @@ def scale_leg(args, q, torch, dev, tn, qi, rank):
         plans[mode] = tn.build_plan(net, order, labels, mode=mode)
         return plans[mode]
 
-    variants = [("auto", "auto", q.SIZE_RULE_TUNED), ("fp32", "fp32", q.SIZE_RULE_PAPER)]
+    variants = [("auto", "auto", q.SIZE_RULE_TUNED, args.tol),
+                ("auto_t0.5", "auto", q.SIZE_RULE_TUNED, 0.5),
+                ("fp32", "fp32", q.SIZE_RULE_PAPER, 0.0)]
     per = _contract_variants(args, q, tn, torch, dev, make_plan, 16, variants)
     plan = plans[q.MODE_AUTO]
     out = {"workload": "5x8 grid (40 qubits), depth 12, 8 sliced indices (256 slices), seeded "
                        "greedy order, 1 bitstring; AUTO-%g (measured size rule) vs all-FP32, "
                        "CUDA-graph replays of 16 slices" % args.tol,
            "flops_per_slice": plan.flops, "max_intermediate_log2": plan.max_log2_size}
-    h = q.Handle(tol=args.tol, size_rule=q.SIZE_RULE_TUNED)
     idx = [int(v, 2) for v, _ in rows]
     sub = copy.copy(plan)
     sub.instance_offset = np.ascontiguousarray(plan.instance_offset[idx])
     sub.instance_slot = np.arange(len(idx), dtype=np.int32)
     sub.n_slots = len(idx)
     cps = tn.CompiledPlan(sub, device=dev)
-    cps.autotune(h, reps=2)
-    got = cps.forward(h).cpu().numpy()[:, 0]
-    h.close()
-    if rank == 0:
-        import oracle
+    for tol, key in ((args.tol, ""), (0.5, "_t0.5")):
+        h = q.Handle(tol=tol, size_rule=q.SIZE_RULE_TUNED)
+        cps.autotune(h, reps=2)
+        got = cps.forward(h).cpu().numpy()[:, 0]
+        h.close()
+        if rank == 0:
+            import oracle
 
-        ref = np.array([a for _, a in rows])
-        out["sampled_slices_fidelity_vs_fp64"] = oracle.fidelity(ref, got)
-        out["sampled_slices_max_rel_err_vs_fp64"] = float(np.max(np.abs(got - ref) / np.abs(ref)))
-    a, b = per["auto"].pop("_out")[0, 0], per["fp32"].pop("_out")[0, 0]
-    out["auto"], out["fp32"] = per["auto"], per["fp32"]
-    out["auto_vs_fp32_rel_diff"] = float(abs(a - b) / abs(b))
+            ref = np.array([a for _, a in rows])
+            out["sampled_slices_fidelity_vs_fp64" + key] = oracle.fidelity(ref, got)
+            out["sampled_slices_max_rel_err_vs_fp64" + key] = float(
+                np.max(np.abs(got - ref) / np.abs(ref)))
+    b = per["fp32"]["_out"][0, 0]
+    for v in per.values():
+        a = v.pop("_out")[0, 0]
+        v["partial_sum_rel_diff_vs_fp32"] = float(abs(a - b) / abs(b))
+    out["auto"], out["auto_t0.5"], out["fp32"] = per["auto"], per["auto_t0.5"], per["fp32"]
     out["speedup_vs_fp32"] = per["fp32"]["s_per_slice"] / per["auto"]["s_per_slice"]
+    out["speedup_vs_fp32_t0.5"] = per["fp32"]["s_per_slice"] / per["auto_t0.5"]["s_per_slice"]
     return out
 
 

@@ -246,6 +246,18 @@ typedef struct {
     double flops;             /* nominal 8 m n k summed over the GEMMs */
 } qcs_run_info_t;
 
+/* Instances per group of qcs_contract_tree and qcs_tree_graph_create (1 to
+ * 65535; default 1).  With G > 1 the forward pass runs the instances in
+ * groups of G: every step whose GEMM runs in plain FP32 (after the size rule)
+ * is one batched launch per group -- its gathers and its G equal-shape GEMMs
+ * (Section 5.3: slices and bitstrings are independent instances of one step
+ * sequence) -- and the other steps, large enough to fill the GPU alone, loop
+ * over the group.  Step outputs then hold G instances each (the tree
+ * workspace grows about G-fold; intermediates share memory by liveness).
+ * Results do not depend on G.  The backward always runs one instance at a
+ * time. */
+int qcs_set_instance_batch(qcs_handle_t h, int instances);
+
 /* Contract the plan for every instance and accumulate into d_out (device,
  * complex128 as interleaved doubles, n_slots * out_size values, slot-major;
  * overwritten).  leaves: host array of n_leaves device pointers (complex64).

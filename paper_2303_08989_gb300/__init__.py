@@ -135,6 +135,12 @@ class Handle:
             e.reps = d.get("reps", 0)
         _lib.check(self.lib.qcs_set_tuning(self._h, arr, len(entries)), "qcs_set_tuning")
 
+    def set_instance_batch(self, instances: int):
+        """Contraction-tree instances (slices / bitstrings) per group: plain
+        FP32 steps become one batched launch per group (qcs_set_instance_batch)."""
+        _lib.check(self.lib.qcs_set_instance_batch(self._h, int(instances)), "qcs_set_instance_batch")
+        self.instance_batch = int(instances)
+
     def set_drain_stages(self, stages: int):
         _lib.check(self.lib.qcs_set_drain_stages(self._h, int(stages)), "qcs_set_drain_stages")
         self.drain_stages = int(stages)

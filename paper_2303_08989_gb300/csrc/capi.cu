@@ -158,15 +158,18 @@ size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sm
 
 int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n, int64_t k,
               float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta,
-              float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out, const qcs_gemm_desc_t *d_desc_in) {
+              float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out, const qcs_gemm_desc_t *d_desc_in,
+              const GemmBatch &bt) {
     cudaStream_t s = h->stream;
+    if (bt.count != 1 && (eff != QCS_MODE_FP32 || k == 0 || d_desc_out || d_desc_in))
+        return QCS_ERR_UNSUPPORTED;
     uint8_t *p = static_cast<uint8_t *>(ws);
     qcs_gemm_desc_t *desc = reinterpret_cast<qcs_gemm_desc_t *>(p);
     p += 256;
     int64_t *partials = reinterpret_cast<int64_t *>(p);
     p += align256(size_t(2) * h->num_sms * kPartialStride * sizeof(int64_t));
-    float2 *splitk = reinterpret_cast<float2 *>(p);
-    p += align256(kSplitKBytes);
+    float2 *splitk = reinterpret_cast<float2 *>(p);  // kSplitKBytes per batch entry (FP32 batches
+    p += align256(kSplitKBytes);                      // run without planes, so the rest follows)
     cudaError_t e = cudaSuccess;
 
     if (d_desc_in) {
@@ -244,7 +247,7 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
     } else {
         ProfScope ps(h, kProfGemmSimt);
         e = launch_cgemm_simt(nullptr, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
-                              splitk, s);
+                              splitk, s, bt);
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     }
     if (d_desc_out) {
@@ -352,6 +355,12 @@ int qcs_set_underflow_tol(qcs_handle_t h, double t) {
 int qcs_set_drain_stages(qcs_handle_t h, int stages) {
     if (!h || (stages != 1 && stages != 2 && stages != 4)) return QCS_ERR_INVALID_ARG;
     h->drain_stages = stages;
+    return QCS_SUCCESS;
+}
+
+int qcs_set_instance_batch(qcs_handle_t h, int instances) {
+    if (!h || instances < 1 || instances > 65535) return QCS_ERR_INVALID_ARG;
+    h->instance_batch = instances;
     return QCS_SUCCESS;
 }
 

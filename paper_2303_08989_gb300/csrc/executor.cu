@@ -32,10 +32,14 @@ namespace {
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    std::vector<size_t> inter_off;  // byte offset of each step's output
+    int G = 1;                      // instances per group
+    std::vector<size_t> inter_off;  // byte offset of each step's output ([G][m n])
     std::vector<size_t> grad_off;   // byte offset of each step's output gradient (backward)
-    size_t out_index = 0, bufA = 0, bufB = 0, tmpA = 0, tmpB = 0, gemm = 0, total = 0;
-    size_t gemm_bytes = 0;
+    std::vector<char> batched;      // step runs as one batched launch per group
+    int P = 0;                      // steps [0, P): batched; [P, ns): one instance at a time
+    std::vector<int> eff;           // effective mode of each step's forward GEMM
+    size_t out_index = 0, offsets = 0, bufA = 0, bufB = 0, tmpA = 0, tmpB = 0, gemm = 0, total = 0;
+    size_t gemm_bytes = 0, inter_bytes = 0;
 };
 
 int64_t root_size(const qcs_tree_t *t, const std::vector<int64_t> &size_of) {
@@ -120,26 +124,92 @@ int validate(const qcs_tree_t *t, std::vector<int64_t> &size_of, bool need_tree)
     return QCS_SUCCESS;
 }
 
-Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward) {
-    Layout L;
+inline int fwd_op(int direct) { return direct == QCS_OP_T ? QCS_OP_T : QCS_OP_N; }
+
+// Offsets of the step outputs when intermediates may share memory: the
+// output of step s is live from step s until its last reader (the root until
+// the end), and is placed first-fit among the blocks live at step s.  A
+// step's output never overlaps its operands, which are still live then.
+// Steps from P on run once per instance of the group, so an output of an
+// earlier step that one of them reads stays live to the end.
+size_t place_by_liveness(const qcs_tree_t *t, const std::vector<size_t> &bytes, int P,
+                         std::vector<size_t> &off) {
     const int nl = t->n_leaves, ns = t->n_steps;
+    std::vector<int> last(ns, ns);  // last reading step of each output; the root: the end
+    for (int s = 0; s < ns; ++s) last[s] = (s == ns - 1) ? ns : -1;
+    for (int s = 0; s < ns; ++s) {
+        const qcs_step_t &st = t->steps[s];
+        for (const int id : {st.a, st.b}) {
+            if (id < nl) continue;
+            const int p = id - nl;
+            last[p] = std::max(last[p], (s >= P && p < P) ? ns : s);
+        }
+    }
+    struct Block {
+        size_t off, size;
+        int id;
+    };
+    std::vector<Block> live;  // sorted by offset
+    size_t peak = 0;
+    off.assign(ns, 0);
+    for (int s = 0; s < ns; ++s) {
+        live.erase(std::remove_if(live.begin(), live.end(),
+                                  [&](const Block &b) { return last[b.id] < s; }),
+                   live.end());
+        size_t at = 0;
+        for (const Block &b : live) {
+            if (b.off >= at + bytes[s]) break;
+            at = std::max(at, b.off + b.size);
+        }
+        off[s] = at;
+        live.insert(std::upper_bound(live.begin(), live.end(), at,
+                                     [](size_t v, const Block &b) { return v < b.off; }),
+                    Block{at, bytes[s], s});
+        peak = std::max(peak, at + bytes[s]);
+    }
+    return peak;
+}
+
+// Workspace of one call.  Forward: the instances run in groups of G that
+// share the buffers.  The steps before P -- the first step whose GEMM does
+// not run in plain FP32 -- are batched: one launch per group, outputs
+// holding G instances.  The steps from P on (in a tree from a greedy order,
+// the few large contractions at the end) run one instance after another,
+// outputs holding one instance.  Outputs reuse memory by liveness.
+// Backward (G = 1): every output is kept.
+Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
+    Layout L;
+    L.G = G;
+    const int ns = t->n_steps;
     size_t p = 0;
     L.out_index = p;
     p += align256(sizeof(int64_t) * (t->out_index ? t->out_size : 1));
+    L.offsets = p;
+    p += align256(sizeof(int64_t) * (size_t)t->n_instances * t->n_leaves);
     int64_t maxA = 1, maxB = 1;
     size_t gemm = 0;
-    L.inter_off.resize(ns);
+    L.eff.resize(ns);
+    L.batched.assign(ns, 0);
+    std::vector<size_t> bytes(ns);
     for (int s = 0; s < ns; ++s) {
         const qcs_step_t &st = t->steps[s];
-        L.inter_off[s] = p;
-        p += align256(sizeof(float2) * st.m * st.n);
-        maxA = std::max(maxA, st.m * st.k);
-        maxB = std::max(maxB, st.k * st.n);
-        const int opA = st.direct_a == QCS_OP_T ? QCS_OP_T : QCS_OP_N;
-        const int opB = st.direct_b == QCS_OP_T ? QCS_OP_T : QCS_OP_N;
-        gemm = std::max(gemm, gemm_workspace_bytes(effective_mode(h, st.mode, opA, opB, st.m, st.n,
-                                                                  st.k),
-                                                   st.m, st.n, st.k, h->num_sms));
+        L.eff[s] = effective_mode(h, st.mode, fwd_op(st.direct_a), fwd_op(st.direct_b), st.m, st.n,
+                                  st.k);
+        L.batched[s] = (G > 1 && L.eff[s] == QCS_MODE_FP32) ? 1 : 0;
+    }
+    L.P = 0;
+    while (L.P < ns && L.batched[L.P]) ++L.P;
+    for (int s = L.P; s < ns; ++s) L.batched[s] = 0;
+    for (int s = 0; s < ns; ++s) {
+        const qcs_step_t &st = t->steps[s];
+        const int64_t gb = L.batched[s] ? G : 1;
+        bytes[s] = align256(sizeof(float2) * st.m * st.n * gb);
+        maxA = std::max(maxA, st.m * st.k * gb);
+        maxB = std::max(maxB, st.k * st.n * gb);
+        // a batched plain-FP32 GEMM keeps a split-K partial buffer per instance,
+        // at the end of its workspace
+        gemm = std::max(gemm, gemm_workspace_bytes(L.eff[s], st.m, st.n, st.k, h->num_sms) +
+                                  (size_t)(gb - 1) * kSplitKBytes);
         if (backward) {
             gemm = std::max(gemm, gemm_workspace_bytes(effective_mode(h, st.mode, QCS_OP_N,
                                                                       QCS_OP_C, st.m, st.k, st.n),
@@ -149,7 +219,19 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward) {
                                                        st.k, st.n, st.m, h->num_sms));
         }
     }
-    (void)nl;
+    L.inter_off.resize(ns);
+    if (backward) {
+        for (int s = 0; s < ns; ++s) {
+            L.inter_off[s] = p;
+            p += bytes[s];
+        }
+    } else {
+        std::vector<size_t> rel;
+        const size_t inter = place_by_liveness(t, bytes, L.P, rel);
+        for (int s = 0; s < ns; ++s) L.inter_off[s] = p + rel[s];
+        p += align256(inter);
+    }
+    L.inter_bytes = p - L.offsets;
     L.bufA = p;
     p += align256(sizeof(float2) * maxA);
     L.bufB = p;
@@ -178,31 +260,35 @@ struct Ctx {
     const qcs_c32 *const *leaves;
     uint8_t *ws;
     Layout L;
+    std::vector<int64_t> size_of;  // elements of every tensor (leaves, then step outputs)
     qcs_run_info_t *info;
 };
 
 float2 *inter_ptr(const Ctx &c, int s) { return reinterpret_cast<float2 *>(c.ws + c.L.inter_off[s]); }
 float2 *grad_ptr(const Ctx &c, int s) { return reinterpret_cast<float2 *>(c.ws + c.L.grad_off[s]); }
 
-const float2 *tensor_ptr(const Ctx &c, int id, int inst) {
+// Tensor ``id`` as seen by instance ``inst`` at position g of its group
+// (outputs of batched steps hold the whole group, the others one instance).
+const float2 *tensor_ptr(const Ctx &c, int id, int inst, int g = 0) {
     const int nl = c.t->n_leaves;
     if (id < nl)
         return reinterpret_cast<const float2 *>(c.leaves[id]) +
                c.t->instance_offset[(int64_t)inst * nl + id];
-    return inter_ptr(c, id - nl);
+    return inter_ptr(c, id - nl) + (c.L.batched[id - nl] ? (int64_t)g * c.size_of[id] : 0);
 }
 
-void count_gemm(const Ctx &c, int eff, int64_t m, int64_t n, int64_t k) {
+void count_gemm(const Ctx &c, int eff, int64_t m, int64_t n, int64_t k, int64_t count = 1) {
     if (!c.info) return;
-    c.info->gemm_count++;
-    if (eff >= 0 && eff < 6) c.info->mode_count[eff]++;
-    c.info->flops += 8.0 * (double)m * (double)n * (double)k;
+    c.info->gemm_count += count;
+    if (eff >= 0 && eff < 6) c.info->mode_count[eff] += count;
+    c.info->flops += 8.0 * (double)m * (double)n * (double)k * (double)count;
 }
 
-int gather(const Ctx &c, const qcs_gather_t &g, const float2 *src, float2 *dst) {
-    if (c.info) c.info->gather_count++;
+int gather(const Ctx &c, const qcs_gather_t &g, const float2 *src, float2 *dst,
+           const CopyBatch &cb = CopyBatch{}) {
+    if (c.info) c.info->gather_count += cb.count;
     ProfScope ps(c.h, kProfPermute);
-    return launch_permute(g.rank, g.dims, g.strides, 0, src, dst, nullptr, 0, c.h->stream) ==
+    return launch_permute(g.rank, g.dims, g.strides, 0, src, dst, nullptr, 0, c.h->stream, cb) ==
                    cudaSuccess
                ? QCS_SUCCESS
                : QCS_ERR_CUDA;
@@ -216,47 +302,128 @@ int gemm(const Ctx &c, int mode, int opA, int opB, int64_t m, int64_t n, int64_t
                      B, ldb, make_float2(0.f, 0.f), C, m, nullptr, nullptr);
 }
 
-// Forward pass of one instance: every step's output into its slot.
-int forward_instance(const Ctx &c, int inst) {
-    const qcs_tree_t *t = c.t;
-    for (int s = 0; s < t->n_steps; ++s) {
-        const qcs_step_t &st = t->steps[s];
-        const float2 *A = tensor_ptr(c, st.a, inst);
-        const float2 *B = tensor_ptr(c, st.b, inst);
-        int opA = QCS_OP_N, opB = QCS_OP_N;
-        int64_t lda = st.m, ldb = st.k;
-        if (st.direct_a == -1) {
-            float2 *buf = reinterpret_cast<float2 *>(c.ws + c.L.bufA);
-            if (int r = gather(c, st.map_a, A, buf)) return r;
-            A = buf;
-        } else if (st.direct_a == QCS_OP_T) {
-            opA = QCS_OP_T;
-            lda = st.k;
-        }
-        if (st.direct_b == -1) {
-            float2 *buf = reinterpret_cast<float2 *>(c.ws + c.L.bufB);
-            if (int r = gather(c, st.map_b, B, buf)) return r;
-            B = buf;
-        } else if (st.direct_b == QCS_OP_T) {
-            opB = QCS_OP_T;
-            ldb = st.n;
-        }
-        if (int r = gemm(c, st.mode, opA, opB, st.m, st.n, st.k, A, lda, B, ldb, inter_ptr(c, s)))
+// One operand of a batched step: the gathered matrices of the group in
+// ``buf`` (stride rows x cols), or the tensor itself (a leaf shared by every
+// instance: stride 0; an intermediate: stride of its instance slots).
+int batched_operand(const Ctx &c, int id, int direct, const qcs_gather_t &map, int inst0, int G,
+                    int64_t elems, float2 *buf, const float2 *&X, int64_t &stride) {
+    const int nl = c.t->n_leaves;
+    if (direct != -1) {
+        X = tensor_ptr(c, id, inst0, 0);
+        stride = id < nl ? 0 : c.size_of[id];
+        return QCS_SUCCESS;
+    }
+    CopyBatch cb;
+    cb.count = G;
+    cb.out_stride = elems;
+    const float2 *src;
+    if (id < nl) {
+        src = reinterpret_cast<const float2 *>(c.leaves[id]);
+        cb.off = reinterpret_cast<const int64_t *>(c.ws + c.L.offsets) + (int64_t)inst0 * nl + id;
+        cb.off_stride = nl;
+    } else {
+        src = inter_ptr(c, id - nl);
+        cb.in_stride = c.size_of[id];
+    }
+    X = buf;
+    stride = elems;
+    return gather(c, map, src, buf, cb);
+}
+
+// One step for one instance (position g of its group): gathers, then
+// qcs_cgemm's launch sequence, output into the step's slot.
+int step_instance(const Ctx &c, int s, int inst, int g) {
+    const qcs_step_t &st = c.t->steps[s];
+    float2 *bufA = reinterpret_cast<float2 *>(c.ws + c.L.bufA);
+    float2 *bufB = reinterpret_cast<float2 *>(c.ws + c.L.bufB);
+    const int opA = fwd_op(st.direct_a), opB = fwd_op(st.direct_b);
+    const int64_t lda = opA == QCS_OP_T ? st.k : st.m, ldb = opB == QCS_OP_T ? st.n : st.k;
+    const float2 *A = tensor_ptr(c, st.a, inst, g);
+    const float2 *B = tensor_ptr(c, st.b, inst, g);
+    if (st.direct_a == -1) {
+        if (int r = gather(c, st.map_a, A, bufA)) return r;
+        A = bufA;
+    }
+    if (st.direct_b == -1) {
+        if (int r = gather(c, st.map_b, B, bufB)) return r;
+        B = bufB;
+    }
+    float2 *C = inter_ptr(c, s) + (c.L.batched[s] ? (int64_t)g * st.m * st.n : 0);
+    return gemm(c, st.mode, opA, opB, st.m, st.n, st.k, A, lda, B, ldb, C);
+}
+
+// One batched step for the G instances of a group: batched gathers, one
+// batched plain-FP32 GEMM launch.
+int step_batched(const Ctx &c, int s, int inst0, int G) {
+    const qcs_step_t &st = c.t->steps[s];
+    float2 *bufA = reinterpret_cast<float2 *>(c.ws + c.L.bufA);
+    float2 *bufB = reinterpret_cast<float2 *>(c.ws + c.L.bufB);
+    const int opA = fwd_op(st.direct_a), opB = fwd_op(st.direct_b);
+    const int64_t lda = opA == QCS_OP_T ? st.k : st.m, ldb = opB == QCS_OP_T ? st.n : st.k;
+    const float2 *A, *B;
+    GemmBatch bt;
+    bt.count = G;
+    bt.sC = st.m * st.n;
+    if (int r = batched_operand(c, st.a, st.direct_a, st.map_a, inst0, G, st.m * st.k, bufA, A,
+                                bt.sA))
+        return r;
+    if (int r = batched_operand(c, st.b, st.direct_b, st.map_b, inst0, G, st.k * st.n, bufB, B,
+                                bt.sB))
+        return r;
+    count_gemm(c, c.L.eff[s], st.m, st.n, st.k, G);
+    return run_cgemm(c.h, c.ws + c.L.gemm, c.L.eff[s], opA, opB, st.m, st.n, st.k,
+                     make_float2(1.f, 0.f), A, lda, B, ldb, make_float2(0.f, 0.f), inter_ptr(c, s),
+                     st.m, nullptr, nullptr, bt);
+}
+
+const int64_t *dev_index(const Ctx &c) {
+    return c.t->out_index ? reinterpret_cast<const int64_t *>(c.ws + c.L.out_index) : nullptr;
+}
+
+const float2 *root_ptr(const Ctx &c, int inst, int g = 0) {
+    return c.t->n_steps > 0 ? tensor_ptr(c, c.t->n_leaves + c.t->n_steps - 1, inst, g)
+                            : tensor_ptr(c, 0, inst);
+}
+
+int accumulate_root(const Ctx &c, int inst, int g, double *d_out) {
+    ProfScope ps(c.h, kProfReduce);
+    const int64_t slot = c.t->instance_slot[inst];
+    return launch_accumulate_gather_c128(root_ptr(c, inst, g), dev_index(c),
+                                         d_out + 2 * slot * c.t->out_size, c.t->out_size,
+                                         c.h->stream) == cudaSuccess
+               ? QCS_SUCCESS
+               : QCS_ERR_CUDA;
+}
+
+// Forward pass of the G instances inst0 .. inst0 + G - 1: the batched steps
+// once for the group, then the remaining steps instance by instance, each
+// root added into its output slot (when d_out is not NULL).
+int forward_group(const Ctx &c, int inst0, int G, double *d_out) {
+    const int ns = c.t->n_steps;
+    for (int s = 0; s < c.L.P; ++s) {
+        if (G > 1) {
+            if (int r = step_batched(c, s, inst0, G)) return r;
+        } else if (int r = step_instance(c, s, inst0, 0)) {
             return r;
+        }
+    }
+    for (int g = 0; g < G; ++g) {
+        for (int s = c.L.P; s < ns; ++s)
+            if (int r = step_instance(c, s, inst0 + g, g)) return r;
+        if (d_out)
+            if (int r = accumulate_root(c, inst0 + g, g, d_out)) return r;
     }
     return QCS_SUCCESS;
 }
 
-const float2 *root_ptr(const Ctx &c, int inst) {
-    return c.t->n_steps > 0 ? inter_ptr(c, c.t->n_steps - 1) : tensor_ptr(c, 0, inst);
-}
+int forward_instance(const Ctx &c, int inst) { return forward_group(c, inst, 1, nullptr); }
 
-int begin(qcs_handle_t h, const qcs_tree_t *t, bool backward, std::vector<int64_t> &size_of,
-          Ctx &c, Workspace *own = nullptr) {
-    if (int r = validate(t, size_of, backward)) return r;
+int begin(qcs_handle_t h, const qcs_tree_t *t, bool backward, Ctx &c, Workspace *own = nullptr) {
+    if (int r = validate(t, c.size_of, backward)) return r;
     c.h = h;
     c.t = t;
-    c.L = plan_layout(h, t, backward);
+    const int G = backward ? 1 : std::max(1, std::min(h->instance_batch, t->n_instances));
+    c.L = plan_layout(h, t, backward, G);
     Workspace &w = own ? *own : h->tree_ws;
     if (int r = ensure_workspace(w, c.L.total)) return r;
     c.ws = static_cast<uint8_t *>(w.ptr);
@@ -267,16 +434,18 @@ int begin(qcs_handle_t h, const qcs_tree_t *t, bool backward, std::vector<int64_
             return QCS_ERR_CUDA;
         }
     }
+    if (G > 1 && cudaMemcpyAsync(c.ws + c.L.offsets, t->instance_offset,
+                                 sizeof(int64_t) * (size_t)t->n_instances * t->n_leaves,
+                                 cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
     if (c.info) c.info->workspace_bytes = (int64_t)c.L.total;
     return QCS_SUCCESS;
 }
 
-const int64_t *dev_index(const Ctx &c) {
-    return c.t->out_index ? reinterpret_cast<const int64_t *>(c.ws + c.L.out_index) : nullptr;
-}
-
-// Every launch of a forward call after begin(): clear d_out, then per
-// instance the steps and the FP64 accumulation of the root.
+// Every launch of a forward call after begin(): clear d_out, then per group
+// of instances the steps and the FP64 accumulation of each root.
 int forward_all(const Ctx &c, double *d_out) {
     const qcs_tree_t *tree = c.t;
     qcs_handle_t h = c.h;
@@ -285,14 +454,9 @@ int forward_all(const Ctx &c, double *d_out) {
         cudaGetLastError();
         return QCS_ERR_CUDA;
     }
-    for (int inst = 0; inst < tree->n_instances; ++inst) {
-        if (int r = forward_instance(c, inst)) return r;
-        ProfScope ps(h, kProfReduce);
-        const int64_t slot = tree->instance_slot[inst];
-        if (launch_accumulate_gather_c128(root_ptr(c, inst), dev_index(c),
-                                          d_out + 2 * slot * tree->out_size, tree->out_size,
-                                          h->stream) != cudaSuccess)
-            return QCS_ERR_CUDA;
+    for (int inst0 = 0; inst0 < tree->n_instances; inst0 += c.L.G) {
+        const int G = std::min(c.L.G, tree->n_instances - inst0);
+        if (int r = forward_group(c, inst0, G, d_out)) return r;
     }
     return QCS_SUCCESS;
 }
@@ -318,11 +482,10 @@ int qcs_contract_tree(qcs_handle_t h, const qcs_tree_t *tree, const qcs_c32 *con
     if (info) *info = qcs_run_info_t{};
     for (int i = 0; i < tree->n_leaves; ++i)
         if (!leaves[i] || (reinterpret_cast<uintptr_t>(leaves[i]) & 7u)) return QCS_ERR_INVALID_ARG;
-    std::vector<int64_t> size_of;
     Ctx c;
     c.leaves = leaves;
     c.info = info;
-    if (int r = begin(h, tree, false, size_of, c)) return r;
+    if (int r = begin(h, tree, false, c)) return r;
     if (int r = forward_all(c, d_out)) return r;
     if (info)
         info->seconds =
@@ -340,11 +503,11 @@ int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
         if (!leaves[i] || !d_grad_leaves[i] || (reinterpret_cast<uintptr_t>(leaves[i]) & 7u) ||
             (reinterpret_cast<uintptr_t>(d_grad_leaves[i]) & 7u))
             return QCS_ERR_INVALID_ARG;
-    std::vector<int64_t> size_of;
     Ctx c;
     c.leaves = leaves;
     c.info = info;
-    if (int r = begin(h, tree, true, size_of, c)) return r;
+    if (int r = begin(h, tree, true, c)) return r;
+    const std::vector<int64_t> &size_of = c.size_of;
     const int nl = tree->n_leaves, ns = tree->n_steps;
     cudaStream_t s = h->stream;
     auto scatter_into = [&](int id, int inst, const qcs_gather_t &g, const float2 *src) -> int {
@@ -445,13 +608,12 @@ int qcs_tree_graph_create(qcs_handle_t h, const qcs_tree_t *tree, const qcs_c32 
     qcs_tree_graph_s *g = new (std::nothrow) qcs_tree_graph_s;
     if (!g) return QCS_ERR_ALLOC;
     g->h = h;
-    std::vector<int64_t> size_of;
     Ctx c;
     c.leaves = leaves;
     c.info = nullptr;
     // begin() validates, allocates the graph's workspace and uploads the
     // output index, all before the capture starts.
-    int r = begin(h, tree, false, size_of, c, &g->ws);
+    int r = begin(h, tree, false, c, &g->ws);
     if (r == QCS_SUCCESS && cudaStreamSynchronize(h->stream) != cudaSuccess) r = QCS_ERR_CUDA;
     // Capture on a private stream (the legacy default stream cannot be
     // captured); the instantiated graph then launches on the handle's stream.

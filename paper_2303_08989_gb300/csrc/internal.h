@@ -84,6 +84,7 @@ struct qcs_handle_s {
     double tol = 0.0;
     int size_rule = 1;
     int drain_stages = 4;            // stages per RN drain of the tensor-core hi*hi sum
+    int instance_batch = 1;          // contraction-tree instances per group (forward)
     int *d_err = nullptr;            // device error word (start of a 64-byte block)
     unsigned long long *d_counts = nullptr;  // in that block: AUTO selections per mode
     qcs::Workspace ws;               // GEMM workspace (planes, partials, descriptor)
@@ -113,6 +114,23 @@ class ProfScope {
 namespace qcs {
 
 int ensure_workspace(Workspace &w, size_t bytes);
+
+// A batch of equal-shape CGEMMs in one launch: entry g reads A + g sA,
+// B + g sB and writes C + g sC (a stride of 0 shares the operand).
+struct GemmBatch {
+    int64_t count = 1;
+    int64_t sA = 0, sB = 0, sC = 0;
+};
+
+// A batch of equal-shape copies in one launch: copy g reads from
+// in + off[g * off_stride] (a device table; or in + g in_stride when off is
+// NULL) and writes to out + g out_stride.
+struct CopyBatch {
+    int64_t count = 1;
+    const int64_t *off = nullptr;
+    int64_t off_stride = 0;
+    int64_t in_stride = 0, out_stride = 0;
+};
 
 // ---- launchers (kernels.cu) ----------------------------------------------
 // Exponent statistics of ``count_cols`` columns of ``rows`` complex values
@@ -151,7 +169,7 @@ cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X
 
 cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
                            const float2 *in, float2 *out, int64_t *stats_partials, int gstats,
-                           cudaStream_t s);
+                           cudaStream_t s, const CopyBatch &cb = CopyBatch{});
 cudaError_t launch_stats_finalize(const int64_t *partials, int g, int64_t n, qcs_stats_t *out,
                                   cudaStream_t s);
 cudaError_t launch_accumulate_c128(const float2 *src, double *dst, int64_t count, int overwrite,
@@ -169,9 +187,11 @@ int effective_mode(qcs_handle_t h, int mode, int opA, int opB, int64_t m, int64_
 int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k, int reps,
                qcs_tune_entry_t *out);
 size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms);
+// ``bt``: a batch of equal-shape GEMMs (plain FP32 only; UNSUPPORTED otherwise).
 int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n, int64_t k,
               float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta,
-              float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out, const qcs_gemm_desc_t *d_desc_in);
+              float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out, const qcs_gemm_desc_t *d_desc_in,
+              const GemmBatch &bt = GemmBatch{});
 
 // ---- GEMM launchers -------------------------------------------------------
 // Plain FP32 SIMT CGEMM (runs only when desc->mode == FP32, or always when
@@ -179,7 +199,7 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
 cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int64_t m,
                               int64_t n, int64_t k, float2 alpha, const float2 *A, int64_t lda,
                               const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc,
-                              float2 *splitk, cudaStream_t s);
+                              float2 *splitk, cudaStream_t s, const GemmBatch &bt = GemmBatch{});
 // Tensor-core emulated CGEMM over split planes.  ``kind``: 0 FP16 (modes
 // FP16X, FP16X_SCALED), 1 TF32, 2 BF16; the kernel returns at once unless
 // desc->mode belongs to its kind.

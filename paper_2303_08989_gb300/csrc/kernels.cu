@@ -702,7 +702,16 @@ struct CopyParams {
     int64_t is[QCS_MAX_RANK];
     int64_t os[QCS_MAX_RANK];
     int8_t gx[QCS_MAX_RANK], gy[QCS_MAX_RANK], gr[QCS_MAX_RANK];  // dim ids per group
+    // Batch (blockIdx.y = g): the input of copy g starts boff[g * boff_stride]
+    // elements in (or g * bin when boff is NULL), its output g * bout.
+    const int64_t *boff;
+    int64_t boff_stride, bin, bout;
 };
+
+__device__ __forceinline__ int64_t batch_in(const CopyParams &P) {
+    const int64_t g = blockIdx.y;
+    return P.boff ? P.boff[g * P.boff_stride] : g * P.bin;
+}
 
 __device__ __forceinline__ void decompose(const CopyParams &P, const int8_t *g, int ng, int64_t v,
                                           int64_t &io, int64_t &oo) {
@@ -734,6 +743,8 @@ __global__ void __launch_bounds__(256) copy_tiled_kernel(CopyParams P, const flo
                                                          float2 *__restrict__ out, int accumulate) {
     __shared__ float2 tile[32][33];
     __shared__ int64_t sxi[32], sxo[32], syi[32], syo[32], sr[kTilesPerBlock][2];
+    in += batch_in(P);
+    out += blockIdx.y * P.bout;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     int64_t b = blockIdx.x;
     const int64_t bx = b % P.tiles_x;
@@ -800,6 +811,8 @@ __global__ void __launch_bounds__(256) copy_vector_kernel(CopyParams P, int nv, 
                                                           int64_t outer, const float2 *__restrict__ in,
                                                           float2 *__restrict__ out, int accumulate) {
     __shared__ int64_t so[2];
+    in += batch_in(P);
+    out += blockIdx.y * P.bout;
     for (int64_t q = blockIdx.x; q < outer; q += gridDim.x) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -832,6 +845,8 @@ __global__ void __launch_bounds__(256) copy_vector_kernel(CopyParams P, int nv, 
 // Element-wise fallback (neither a tile nor a contiguous run applies).
 __global__ void copy_simple_kernel(CopyParams P, int64_t total, const float2 *__restrict__ in,
                                    float2 *__restrict__ out, int accumulate) {
+    in += batch_in(P);
+    out += blockIdx.y * P.bout;
     for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
          o += (int64_t)gridDim.x * blockDim.x) {
         int64_t rem = o, io = 0, oo = 0;
@@ -893,9 +908,16 @@ void choose_groups(CopyParams &P) {
 }
 
 cudaError_t launch_copy(int rank, const int64_t *dims, const int64_t *is, const int64_t *os,
-                        const float2 *in, float2 *out, int accumulate, cudaStream_t s) {
+                        const float2 *in, float2 *out, int accumulate, cudaStream_t s,
+                        const CopyBatch &cb = CopyBatch{}) {
+    if (cb.count < 1 || cb.count > 65535) return cudaErrorInvalidValue;
     CopyParams P{};
     P.rank = rank;
+    P.boff = cb.off;
+    P.boff_stride = cb.off_stride;
+    P.bin = cb.in_stride;
+    P.bout = cb.out_stride;
+    const unsigned G = (unsigned)cb.count;
     P.pow2 = 1;
     int64_t total = 1;
     for (int d = 0; d < rank; ++d) {
@@ -918,12 +940,12 @@ cudaError_t launch_copy(int rank, const int64_t *dims, const int64_t *is, const 
     if (pv >= 32 || (!tiled_ok && pv >= 4)) {
         const int64_t outer = total / pv;
         const int64_t blocks = outer < 65536 ? outer : 65536;
-        copy_vector_kernel<<<(unsigned)blocks, pv >= 256 ? 256 : (pv >= 128 ? 128 : 64), 0, s>>>(
-            P, nv, pv, outer, in, out, accumulate);
+        copy_vector_kernel<<<dim3((unsigned)blocks, G), pv >= 256 ? 256 : (pv >= 128 ? 128 : 64), 0,
+                             s>>>(P, nv, pv, outer, in, out, accumulate);
         return cudaGetLastError();
     }
     if (!tiled_ok) {
-        copy_simple_kernel<<<grid_for(total), 256, 0, s>>>(P, total, in, out, accumulate);
+        copy_simple_kernel<<<dim3(grid_for(total), G), 256, 0, s>>>(P, total, in, out, accumulate);
         return cudaGetLastError();
     }
     P.nr = 0;
@@ -942,7 +964,7 @@ cudaError_t launch_copy(int rank, const int64_t *dims, const int64_t *is, const 
     P.rest = rest;
     const int64_t blocks = P.tiles_x * P.tiles_y * ((rest + kTilesPerBlock - 1) / kTilesPerBlock);
     if (blocks > INT32_MAX) return cudaErrorInvalidValue;
-    copy_tiled_kernel<<<(unsigned)blocks, 256, 0, s>>>(P, in, out, accumulate);
+    copy_tiled_kernel<<<dim3((unsigned)blocks, G), 256, 0, s>>>(P, in, out, accumulate);
     return cudaGetLastError();
 }
 
@@ -990,7 +1012,7 @@ __global__ void accumulate_c128_kernel(const float2 *__restrict__ src, double2 *
 
 cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
                            const float2 *in, float2 *out, int64_t *stats_partials, int gstats,
-                           cudaStream_t s) {
+                           cudaStream_t s, const CopyBatch &cb) {
     (void)stats_partials;
     (void)gstats;
     int64_t dense[QCS_MAX_RANK];
@@ -999,7 +1021,7 @@ cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides
         dense[d] = acc;
         acc *= dims[d];
     }
-    return launch_copy(rank, dims, strides, dense, in + offset, out, 0, s);
+    return launch_copy(rank, dims, strides, dense, in + offset, out, 0, s, cb);
 }
 
 cudaError_t launch_scatter(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
@@ -1056,8 +1078,11 @@ __device__ __forceinline__ float2 ld_op(const float2 *X, int op, int64_t r, int6
 __global__ void __launch_bounds__(256) cgemm_simt_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int m, int n, int k, float2 alpha,
     const float2 *__restrict__ A, int64_t lda, const float2 *__restrict__ B, int64_t ldb,
-    float2 beta, float2 *__restrict__ C, int64_t ldc) {
+    float2 beta, float2 *__restrict__ C, int64_t ldc, GemmBatch bt) {
     if (desc && desc->mode != QCS_MODE_FP32) return;
+    A += blockIdx.z * bt.sA;
+    B += blockIdx.z * bt.sB;
+    C += blockIdx.z * bt.sC;
     __shared__ __align__(16) float2 As[2][kSBK][kSBM + kSPadA];
     __shared__ __align__(16) float2 Bs[2][kSBK][kSBN + kSPadB];
     const int tid = threadIdx.x;
@@ -1209,8 +1234,11 @@ template <int KMAX>
 __global__ void __launch_bounds__(256) cgemm_skinny_rows_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int k,
     float2 alpha, const float2 *__restrict__ A, int64_t lda, const float2 *__restrict__ B,
-    int64_t ldb, float2 beta, float2 *__restrict__ C, int64_t ldc) {
+    int64_t ldb, float2 beta, float2 *__restrict__ C, int64_t ldc, GemmBatch bt) {
     if (desc && desc->mode != QCS_MODE_FP32) return;
+    A += blockIdx.y * bt.sA;
+    B += blockIdx.y * bt.sB;
+    C += blockIdx.y * bt.sC;
     const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -1246,8 +1274,11 @@ __global__ void __launch_bounds__(256) cgemm_skinny_rows_kernel(
 __global__ void __launch_bounds__(256) cgemm_skinny_cols_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int k,
     int lg_m2, float2 alpha, const float2 *__restrict__ A, int64_t lda, const float2 *__restrict__ B,
-    int64_t ldb, float2 beta, float2 *__restrict__ C, int64_t ldc) {
+    int64_t ldb, float2 beta, float2 *__restrict__ C, int64_t ldc, GemmBatch bt) {
     if (desc && desc->mode != QCS_MODE_FP32) return;
+    A += blockIdx.y * bt.sA;
+    B += blockIdx.y * bt.sB;
+    C += blockIdx.y * bt.sC;
     const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
     const int64_t total = n << lg_m2;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -1283,8 +1314,11 @@ __global__ void __launch_bounds__(256) cgemm_skinny_cols_kernel(
 __global__ void __launch_bounds__(256) cgemm_perelem_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int64_t k,
     float2 alpha, const float2 *__restrict__ A, int64_t lda, const float2 *__restrict__ B,
-    int64_t ldb, float2 beta, float2 *__restrict__ C, int64_t ldc) {
+    int64_t ldb, float2 beta, float2 *__restrict__ C, int64_t ldc, GemmBatch bt) {
     if (desc && desc->mode != QCS_MODE_FP32) return;
+    A += blockIdx.z * bt.sA;
+    B += blockIdx.z * bt.sB;
+    C += blockIdx.z * bt.sC;
     const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= m) return;
@@ -1319,9 +1353,12 @@ __global__ void __launch_bounds__(256) cgemm_perelem_kernel(
 __global__ void __launch_bounds__(256) cgemm_splitk_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int64_t k,
     int64_t chunk, int64_t chunks, const float2 *__restrict__ A, int64_t lda,
-    const float2 *__restrict__ B, int64_t ldb, float2 *__restrict__ part) {
+    const float2 *__restrict__ B, int64_t ldb, float2 *__restrict__ part, GemmBatch bt) {
     if (desc && desc->mode != QCS_MODE_FP32) return;
     const int64_t mn = m * n;
+    A += blockIdx.y * bt.sA;
+    B += blockIdx.y * bt.sB;
+    part += blockIdx.y * chunks * mn;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= mn * chunks) return;
@@ -1350,10 +1387,12 @@ __global__ void __launch_bounds__(256) cgemm_splitk_kernel(
 __global__ void __launch_bounds__(256) cgemm_splitk_reduce(
     const qcs_gemm_desc_t *__restrict__ desc, int64_t m, int64_t n, int64_t chunks,
     const float2 *__restrict__ part, float2 alpha, float2 beta, float2 *__restrict__ C,
-    int64_t ldc) {
+    int64_t ldc, GemmBatch bt) {
     if (desc && desc->mode != QCS_MODE_FP32) return;
     __shared__ float2 red[256];
     const int64_t mn = m * n;
+    C += blockIdx.y * bt.sC;
+    part += blockIdx.y * chunks * mn;
     const int64_t o = blockIdx.x;
     float sr = 0.f, si = 0.f;
     for (int64_t c = threadIdx.x; c < chunks; c += 256) {
@@ -1391,11 +1430,15 @@ __global__ void __launch_bounds__(256) cgemm_splitk_reduce(
 cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int64_t m,
                               int64_t n, int64_t k, float2 alpha, const float2 *A, int64_t lda,
                               const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc,
-                              float2 *splitk, cudaStream_t s) {
+                              float2 *splitk, cudaStream_t s, const GemmBatch &bt) {
     if (m == 0 || n == 0) return cudaSuccess;
+    if (bt.count < 1 || bt.count > 65535) return cudaErrorInvalidValue;
+    const unsigned G = (unsigned)bt.count;
     const int64_t mn = m * n;
     if (splitk && mn <= kSplitKMaxOutputs && k >= 1024) {
-        // enough warps to fill the GPU, at least 256 k values per warp
+        // enough warps to fill the GPU, at least 256 k values per warp; the
+        // buffer holds kSplitKMaxPartials partials per batch entry, so the
+        // chunking (and the result) does not depend on the batch
         int64_t chunks = kSplitKMaxPartials / mn;
         chunks = std::min<int64_t>(chunks, (k + 255) / 256);
         chunks = std::max<int64_t>(chunks, 1);
@@ -1403,39 +1446,39 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
         chunks = (k + chunk - 1) / chunk;
         const int64_t warps = mn * chunks;
         const int64_t blocks = (warps * 32 + 255) / 256;
-        cgemm_splitk_kernel<<<(unsigned)blocks, 256, 0, s>>>(desc, opA, opB, m, n, k, chunk, chunks,
-                                                             A, lda, B, ldb, splitk);
+        cgemm_splitk_kernel<<<dim3((unsigned)blocks, G), 256, 0, s>>>(
+            desc, opA, opB, m, n, k, chunk, chunks, A, lda, B, ldb, splitk, bt);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        cgemm_splitk_reduce<<<(unsigned)mn, 256, 0, s>>>(desc, m, n, chunks, splitk, alpha, beta, C,
-                                                         ldc);
+        cgemm_splitk_reduce<<<dim3((unsigned)mn, G), 256, 0, s>>>(desc, m, n, chunks, splitk, alpha,
+                                                                  beta, C, ldc, bt);
         return cudaGetLastError();
     }
     if (k <= 16 && (m <= 16 || n <= 16)) {
         if (m >= n) {  // then n <= 16: a thread per row
             const int64_t blocks = (m + 255) / 256;
-            const unsigned grid = (unsigned)(blocks < 65536 ? blocks : 65536);
+            const dim3 grid((unsigned)(blocks < 65536 ? blocks : 65536), G);
             const int kk = (int)k;
             if (kk <= 2)
                 cgemm_skinny_rows_kernel<2><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, kk, alpha, A,
-                                                                lda, B, ldb, beta, C, ldc);
+                                                                lda, B, ldb, beta, C, ldc, bt);
             else if (kk <= 4)
                 cgemm_skinny_rows_kernel<4><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, kk, alpha, A,
-                                                                lda, B, ldb, beta, C, ldc);
+                                                                lda, B, ldb, beta, C, ldc, bt);
             else if (kk <= 8)
                 cgemm_skinny_rows_kernel<8><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, kk, alpha, A,
-                                                                lda, B, ldb, beta, C, ldc);
+                                                                lda, B, ldb, beta, C, ldc, bt);
             else
                 cgemm_skinny_rows_kernel<16><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, kk, alpha, A,
-                                                                 lda, B, ldb, beta, C, ldc);
+                                                                 lda, B, ldb, beta, C, ldc, bt);
         } else {  // m <= 16: a thread per element, rows in the low bits
             int lg = 0;
             while ((int64_t(1) << lg) < m) ++lg;
             const int64_t total = n << lg;
             const int64_t blocks = (total + 255) / 256;
-            const unsigned grid = (unsigned)(blocks < 65536 ? blocks : 65536);
+            const dim3 grid((unsigned)(blocks < 65536 ? blocks : 65536), G);
             cgemm_skinny_cols_kernel<<<grid, 256, 0, s>>>(desc, opA, opB, m, n, (int)k, lg, alpha, A,
-                                                          lda, B, ldb, beta, C, ldc);
+                                                          lda, B, ldb, beta, C, ldc, bt);
         }
         return cudaGetLastError();
     }
@@ -1443,15 +1486,15 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
     if (perelem || m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) {
         const int64_t bx = (m + 255) / 256;
         if (bx > INT32_MAX) return cudaErrorInvalidValue;
-        dim3 grid((unsigned)bx, (unsigned)(n < 65535 ? n : 65535));
+        dim3 grid((unsigned)bx, (unsigned)(n < 65535 ? n : 65535), G);
         cgemm_perelem_kernel<<<grid, 256, 0, s>>>(desc, opA, opB, m, n, k, alpha, A, lda, B, ldb,
-                                                  beta, C, ldc);
+                                                  beta, C, ldc, bt);
         return cudaGetLastError();
     }
-    dim3 grid((unsigned)((n + kSBN - 1) / kSBN), (unsigned)((m + kSBM - 1) / kSBM));
+    dim3 grid((unsigned)((n + kSBN - 1) / kSBN), (unsigned)((m + kSBM - 1) / kSBM), G);
     if (grid.y > 65535u) return cudaErrorInvalidValue;
     cgemm_simt_kernel<<<grid, 256, 0, s>>>(desc, opA, opB, (int)m, (int)n, (int)k, alpha, A, lda, B,
-                                           ldb, beta, C, ldc);
+                                           ldb, beta, C, ldc, bt);
     return cudaGetLastError();
 }
 

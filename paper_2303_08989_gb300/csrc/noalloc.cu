@@ -25,10 +25,6 @@ constexpr size_t kNoallocBytes = QCS_NOALLOC_SCRATCH_BYTES;
 constexpr size_t kNoallocHeader = 256;  // device error word, then unused bytes
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms);
-int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n, int64_t k,
-              float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta,
-              float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out, const qcs_gemm_desc_t *d_desc_in);
 int validate_cgemm(int mode, int opA, int opB, int64_t m, int64_t n, int64_t k, const void *alpha,
                    const void *A, int64_t lda, const void *B, int64_t ldb, const void *beta,
                    const void *C, int64_t ldc);

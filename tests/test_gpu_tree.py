@@ -269,3 +269,69 @@ def test_40_qubit_sampled_slices_vs_fp64_golden(h, golden_dir):
     a = got[:, 0]
     assert oracle.fidelity(ref, a) >= 1 - 1e-5
     assert np.all(np.abs(a - ref) <= 1e-4 * np.abs(ref)), (a, ref)
+
+
+@pytest.mark.parametrize("G", [2, 5, 32])
+def test_instance_groups_are_bit_identical(G):
+    """qcs_set_instance_batch: plain-FP32 steps run as one batched launch per
+    group of G instances (slices x bitstrings), the emulated steps loop over
+    the group; every GEMM computes exactly what it computes alone, so the
+    result equals the one-instance-at-a-time result bit for bit, eagerly and
+    replayed from a CUDA graph, and matches the FP64 oracle."""
+    need_gpu()
+    tn = _tn()
+    q = lib()
+    circ = qi.random_grid_circuit(3, 4, 8, seed=3)
+    bits = qi.random_bitstrings(12, 4, seed=4)
+    plan = tn.plan_circuit(circ, bits, seed=2, n_slices=3)
+    # every third step emulated on the tensor cores, the rest plain FP32
+    for i, st in enumerate(plan.steps):
+        st.mode = q.MODE_FP16X if i % 3 == 2 else q.MODE_FP32
+    hd = q.Handle(tol=0.0, size_rule=False)
+    try:
+        one, _ = _run(hd, plan)
+        hd.set_instance_batch(G)
+        cp = tn.CompiledPlan(plan)
+        grouped = cp.forward(hd)
+        torch.cuda.synchronize()
+        hd.sync()
+        info = cp.last_info
+        assert info.gemm_count == plan.n_instances * len(plan.steps)
+        g, out = cp.graph(hd)
+        out.zero_()
+        g.launch()
+        torch.cuda.synchronize()
+        hd.sync()
+        replay = out.cpu().numpy()
+        g.close()
+    finally:
+        hd.close()
+    assert np.array_equal(grouped.cpu().numpy(), one)
+    assert np.array_equal(replay, one)
+    ref = oracle.sv_amplitudes(circ, bits)
+    assert oracle.fidelity(ref, one[:, 0]) >= 1 - 1e-5
+
+
+def test_instance_groups_with_direct_and_split_k_steps():
+    """Groups over a network whose last step reduces a long k into one output
+    (the split-K FP32 path, one partial buffer per instance) and whose steps
+    read leaves directly: bit-identical to one instance at a time."""
+    need_gpu()
+    tn = _tn()
+    q = lib()
+    circ = qi.random_grid_circuit(4, 4, 10, seed=8)
+    bits = qi.random_bitstrings(16, 6, seed=9)
+    plan = tn.plan_circuit(circ, bits, seed=4, n_slices=2, mode=q.MODE_FP32)
+    assert any(s.m * s.n <= 4096 and s.k >= 1024 for s in plan.steps)
+    assert any(st.direct_a != -1 or st.direct_b != -1 for st in plan.steps)
+    hd = q.Handle(tol=0.0, size_rule=False)
+    try:
+        one, _ = _run(hd, plan)
+        for G in (3, 24):
+            hd.set_instance_batch(G)
+            got, _ = _run(hd, plan)
+            assert np.array_equal(got, one), G
+    finally:
+        hd.close()
+    ref = oracle.sv_amplitudes(circ, bits)
+    assert oracle.fidelity(ref, one[:, 0]) >= 1 - 1e-5
