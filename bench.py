@@ -161,6 +161,16 @@ def oracle_sample(A_rows_np, B_np, n: int, rows: int):
 # reference arm: the FP64 CPU oracle as it stands
 # ---------------------------------------------------------------------------
 
+def gemm_config(args, world: int) -> dict:
+    """The workload both arms report (the CGEMM-sweep point bench.py times)."""
+    n = args.size
+    return {"workload": f"CGEMM m=n=k={n}, parts N(0,1)*2^e, e~U_int[-{args.s},{args.s}], "
+                        f"AUTO-{args.tol:g} (size rule on)",
+            "m": n, "n": n, "k": n, "s": args.s, "tol": args.tol, "mode": args.mode,
+            "l2": "operands 8*n^2 bytes each, larger than L2; no flush",
+            "parallelism": f"{world} independent GEMMs (one per GPU)"}
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
@@ -187,7 +197,7 @@ def run_reference(args, rank: int):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
         "data": "synthetic",
-        "config": {"workload": f"CGEMM m=n=k={n}, N(0,1)*2^e parts, s={args.s}", "sample": sample},
+        "config": dict(gemm_config(args, 1), sample=sample),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -294,12 +304,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64",
         "data": "synthetic (seeded torch.randn on the device)",
-        "config": {"workload": f"CGEMM m=n=k={n}, parts N(0,1)*2^e, e~U_int[-{args.s},{args.s}], "
-                               f"AUTO-{args.tol:g} (size rule on)",
-                   "m": n, "n": n, "k": n, "s": args.s, "tol": args.tol, "mode": args.mode,
-                   "mode_selected": mode_used,
-                   "l2": "operands 8*n^2 bytes each, larger than L2; no flush",
-                   "parallelism": f"{world} independent GEMMs (one per GPU)"},
+        "config": dict(gemm_config(args, world), mode_selected=mode_used),
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "stages": stages,
@@ -494,13 +499,18 @@ def _time_graph(torch, cp, h, reps=2):
     return e0.elapsed_time(e1) / reps * 1e-3, out
 
 
-def _routing(info, counts):
-    """GEMMs per mode that actually ran in one call: the host-decided modes of
-    qcs_run_info_t, with the AUTO ones replaced by what the device selected."""
+def _routing(info, counts, flops):
+    """GEMMs per mode that actually ran in one call, by count and by nominal
+    flops: the host-decided modes of qcs_run_info_t, with the AUTO ones
+    replaced by what the device selected."""
     host = dict(zip(MODE_KEYS, info["mode_count"]))
+    hostf = dict(zip(MODE_KEYS, info["mode_flops"]))
     ran = {k: host[k] + counts.get(k, 0) for k in MODE_KEYS[1:]}
+    ranf = {k: hostf[k] + flops.get(k, 0.0) for k in MODE_KEYS[1:]}
     total = max(sum(ran.values()), 1)
-    return {"gemms": ran, "fraction": {k: round(v / total, 4) for k, v in ran.items()}}
+    totalf = max(sum(ranf.values()), 1.0)
+    return {"gemms": ran, "fraction": {k: round(v / total, 4) for k, v in ran.items()},
+            "flops_fraction": {k: round(v / totalf, 4) for k, v in ranf.items()}}
 
 
 def _contract_variants(args, q, tn, torch, dev, make_plan, ns, variants, full=False):
@@ -529,14 +539,14 @@ def _contract_variants(args, q, tn, torch, dev, make_plan, ns, variants, full=Fa
         secs, _ = _time_plan(torch, cp, h)
         h.auto_counts(reset=True)
         out = cp.forward(h)
-        counts = h.auto_counts(reset=True)
+        counts, cflops = h.auto_counts(reset=True, flops=True)
         info = tn.info_dict(cp.last_info)
         gsecs, gout = _time_graph(torch, cp, h)
         e.update({"s_per_slice": gsecs / ns, "s_per_slice_eager": secs / ns, "slices_timed": ns,
                   "instance_batch": args.instance_batch,
                   "workspace_gb": info["workspace_bytes"] / 1e9,
                   "tflops": info["flops"] / gsecs / 1e12, "gemms_per_slice": info["gemm_count"] / ns,
-                  "routing": _routing(info, counts)})
+                  "routing": _routing(info, counts, cflops)})
         e["_out"] = out.cpu().numpy()
         if full:
             cp.tree.n_instances = n_all

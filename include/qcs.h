@@ -244,6 +244,7 @@ typedef struct {
     int64_t mode_count[6];    /* GEMMs per effective mode after the size rule (AUTO counted in [0]) */
     int64_t workspace_bytes;  /* bytes of the tree workspace */
     double flops;             /* nominal 8 m n k summed over the GEMMs */
+    double mode_flops[6];     /* the same per effective mode (as mode_count) */
 } qcs_run_info_t;
 
 /* Instances per group of qcs_contract_tree and qcs_tree_graph_create (1 to
@@ -397,12 +398,13 @@ int qcs_get_profile(qcs_handle_t h, double *ms, int64_t *counts, int n);
 /* What the automatic selection (Section 4.1) chose: counts[i] (host array of
  * QCS_NUM_MODES) receives how many GEMMs of mode AUTO on this handle -- after
  * the size rule, so only those that ran the statistics -- selected
- * qcs_mode_t i on the device since the handle was created or last reset.
- * (The selection happens on the device, so the host-side mode counts of
+ * qcs_mode_t i on the device since the handle was created or last reset,
+ * and flops[i] (host, optional) their nominal 8 m n k summed.  (The
+ * selection happens on the device, so the host-side counts of
  * qcs_run_info_t only know that such a GEMM was AUTO.)  Synchronizes the
  * handle's stream.  reset != 0 clears the counters afterwards.  Graph
  * replays count too. */
-int qcs_get_auto_counts(qcs_handle_t h, int64_t *counts, int reset);
+int qcs_get_auto_counts(qcs_handle_t h, int64_t *counts, double *flops, int reset);
 
 /* Wait for the handle's stream; return TIMEOUT if a device-side bounded
  * wait gave up since the last qcs_sync (the word is then cleared), CUDA on

@@ -98,12 +98,18 @@ class Handle:
         _lib.check(self.lib.qcs_set_size_rule(self._h, rule))
         self.size_rule = rule
 
-    def auto_counts(self, reset: bool = True):
+    def auto_counts(self, reset: bool = True, flops: bool = False):
         """{mode name: count} of what AUTO GEMMs on this handle selected on the
-        device (qcs_get_auto_counts); synchronizes the stream."""
+        device (qcs_get_auto_counts); synchronizes the stream.  With
+        ``flops`` returns (counts, {mode name: summed 8 m n k})."""
         c = (ctypes.c_int64 * _lib.NUM_MODES)()
-        _lib.check(self.lib.qcs_get_auto_counts(self._h, c, 1 if reset else 0), "qcs_get_auto_counts")
-        return {MODE_NAME[i]: int(c[i]) for i in range(_lib.NUM_MODES)}
+        f = (ctypes.c_double * _lib.NUM_MODES)()
+        _lib.check(self.lib.qcs_get_auto_counts(self._h, c, f, 1 if reset else 0),
+                   "qcs_get_auto_counts")
+        counts = {MODE_NAME[i]: int(c[i]) for i in range(_lib.NUM_MODES)}
+        if flops:
+            return counts, {MODE_NAME[i]: float(f[i]) for i in range(_lib.NUM_MODES)}
+        return counts
 
     def autotune_gemm(self, m: int, n: int, k: int, opA: int = OP_N, opB: int = OP_N,
                       reps: int = 3) -> dict:

@@ -93,7 +93,8 @@ class qcs_tree_t(ctypes.Structure):
 class qcs_run_info_t(ctypes.Structure):
     _fields_ = [("seconds", ctypes.c_double), ("gemm_count", ctypes.c_int64),
                 ("gather_count", ctypes.c_int64), ("mode_count", ctypes.c_int64 * 6),
-                ("workspace_bytes", ctypes.c_int64), ("flops", ctypes.c_double)]
+                ("workspace_bytes", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("mode_flops", ctypes.c_double * 6)]
 
 
 _lib = None
@@ -139,7 +140,7 @@ def load(path: str = LIB_PATH):
                                   ctypes.POINTER(ctypes.c_void_p)],
         "qcs_tree_graph_launch": [P],
         "qcs_tree_graph_destroy": [P],
-        "qcs_get_auto_counts": [H, ctypes.POINTER(I64), I],
+        "qcs_get_auto_counts": [H, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double), I],
         "qcs_autotune_gemm": [H, I, I, I64, I64, I64, I, ctypes.POINTER(qcs_tune_entry_t)],
         "qcs_autotune_tree": [H, ctypes.POINTER(qcs_tree_t), I, I, ctypes.POINTER(I64)],
         "qcs_get_tuning": [H, ctypes.POINTER(qcs_tune_entry_t), I64, ctypes.POINTER(I64)],

@@ -183,7 +183,8 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
             ProfScope ps(h, kProfStats);
             e = launch_stats_select_2stage(A, ra, ca, lda, gA, B, rb, cb, ldb, gB, h->tol, eff,
                                            partials, partials + 5 * (gA + gB), desc,
-                                           h->d_counts, s);
+                                           h->d_counts, 8.0 * (double)m * (double)n * (double)k,
+                                           s);
         }
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     } else if (eff != QCS_MODE_FP32 || d_desc_out) {
@@ -490,19 +491,26 @@ int qcs_sync(qcs_handle_t h) {
     return QCS_SUCCESS;
 }
 
-int qcs_get_auto_counts(qcs_handle_t h, int64_t *counts, int reset) {
+int qcs_get_auto_counts(qcs_handle_t h, int64_t *counts, double *flops, int reset) {
     if (!h || !counts) return QCS_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
         cudaGetLastError();
         return QCS_ERR_CUDA;
     }
-    unsigned long long c[QCS_NUM_MODES];
-    if (cudaMemcpy(c, h->d_counts, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    struct {
+        unsigned long long c[QCS_NUM_MODES];
+        double f[QCS_NUM_MODES];
+    } d;
+    static_assert(sizeof(d) + 8 <= kStatusBlockBytes, "status block");
+    if (cudaMemcpy(&d, h->d_counts, sizeof(d), cudaMemcpyDeviceToHost) != cudaSuccess) {
         cudaGetLastError();
         return QCS_ERR_CUDA;
     }
-    for (int i = 0; i < QCS_NUM_MODES; ++i) counts[i] = (int64_t)c[i];
-    if (reset && cudaMemset(h->d_counts, 0, sizeof(c)) != cudaSuccess) {
+    for (int i = 0; i < QCS_NUM_MODES; ++i) {
+        counts[i] = (int64_t)d.c[i];
+        if (flops) flops[i] = d.f[i];
+    }
+    if (reset && cudaMemset(h->d_counts, 0, sizeof(d)) != cudaSuccess) {
         cudaGetLastError();
         return QCS_ERR_CUDA;
     }

@@ -280,8 +280,12 @@ const float2 *tensor_ptr(const Ctx &c, int id, int inst, int g = 0) {
 void count_gemm(const Ctx &c, int eff, int64_t m, int64_t n, int64_t k, int64_t count = 1) {
     if (!c.info) return;
     c.info->gemm_count += count;
-    if (eff >= 0 && eff < 6) c.info->mode_count[eff] += count;
-    c.info->flops += 8.0 * (double)m * (double)n * (double)k * (double)count;
+    const double f = 8.0 * (double)m * (double)n * (double)k * (double)count;
+    if (eff >= 0 && eff < 6) {
+        c.info->mode_count[eff] += count;
+        c.info->mode_flops[eff] += f;
+    }
+    c.info->flops += f;
 }
 
 int gather(const Ctx &c, const qcs_gather_t &g, const float2 *src, float2 *dst,

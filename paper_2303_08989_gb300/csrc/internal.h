@@ -47,7 +47,9 @@ constexpr size_t kSplitKBytes = size_t(kSplitKMaxPartials) * 8;
 // (256 bins + zero count).
 constexpr int kStatsThreads = 128;
 constexpr int kPartialStride = 257;
-constexpr size_t kStatusBlockBytes = 64;  // handle's error word + AUTO selection counters
+// handle's device status block: error word at byte 0, AUTO selection
+// counts (6 uint64) at byte 8, their flops (6 doubles) at byte 56
+constexpr size_t kStatusBlockBytes = 128;
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -86,7 +88,7 @@ struct qcs_handle_s {
     int drain_stages = 4;            // stages per RN drain of the tensor-core hi*hi sum
     int instance_batch = 1;          // contraction-tree instances per group (forward)
     int *d_err = nullptr;            // device error word (start of a 64-byte block)
-    unsigned long long *d_counts = nullptr;  // in that block: AUTO selections per mode
+    unsigned long long *d_counts = nullptr;  // in that block: AUTO selections per mode, flops
     qcs::Workspace ws;               // GEMM workspace (planes, partials, descriptor)
     qcs::Workspace tree_ws;          // contraction-tree intermediates
     qcs::EncodeTiledFn encode = nullptr;
@@ -146,13 +148,14 @@ cudaError_t launch_select(const int64_t *partials, int gA, int gB, int64_t nA, i
 // Two-stage statistics + selection for the GEMM path: pass 1 (e_max,
 // zeros, Inf/NaN, count below 2^-14), pass 2 only when needed (count below
 // the shifted window), final selection.  gA / gB blocks of 256 threads per
-// matrix; p1 holds 5 int64 per block, p2 one.  ``counts`` (optional, 6
-// entries indexed by qcs_mode_t) gets one increment for the selected mode.
+// matrix; p1 holds 5 int64 per block, p2 one.  ``counts`` (optional: 6
+// uint64 indexed by qcs_mode_t, then 6 doubles) gets one increment and
+// ``work`` (the GEMM's 8 m n k) added for the selected mode.
 cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t cols0, int64_t ld0,
                                        int gA, const float2 *X1, int64_t rows1, int64_t cols1,
                                        int64_t ld1, int gB, double tol, int forced, int64_t *p1,
                                        int64_t *p2, qcs_gemm_desc_t *desc,
-                                       unsigned long long *counts, cudaStream_t s);
+                                       unsigned long long *counts, double work, cudaStream_t s);
 // Select from two finished qcs_stats_t.
 cudaError_t launch_select_from_stats(const qcs_stats_t *a, const qcs_stats_t *b, double tol,
                                      qcs_gemm_desc_t *desc, cudaStream_t s);

@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(kS2Threads) stats_pass2_kernel(
 
 __global__ void select2_kernel(const int64_t *__restrict__ p1, const int64_t *__restrict__ p2,
                                int gA, int gB, int64_t nA, int64_t nB, double tol, int forced,
-                               qcs_gemm_desc_t *desc, unsigned long long *counts) {
+                               qcs_gemm_desc_t *desc, unsigned long long *counts, double work) {
     __shared__ uint64_t shs[kS2Threads / 32];
     __shared__ uint32_t shm[kS2Threads / 32];
     const Sum1 a = reduce_p1(p1, 0, gA, nA, shm, shs);
@@ -467,7 +467,11 @@ __global__ void select2_kernel(const int64_t *__restrict__ p1, const int64_t *__
     sa.under2 = (int64_t)u2a;
     sb.under2 = (int64_t)u2b;
     select_rule(sa, sb, tol, forced, desc);
-    if (counts) atomicAdd(&counts[desc->mode], 1ULL);
+    if (counts) {
+        // counts[0..5]: GEMMs per selected mode; then 6 doubles of their 8 m n k
+        atomicAdd(&counts[desc->mode], 1ULL);
+        atomicAdd(reinterpret_cast<double *>(counts + QCS_NUM_MODES) + desc->mode, work);
+    }
 }
 
 static bool g_stats_configured = false;
@@ -499,7 +503,7 @@ cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t 
                                        int gA, const float2 *X1, int64_t rows1, int64_t cols1,
                                        int64_t ld1, int gB, double tol, int forced, int64_t *p1,
                                        int64_t *p2, qcs_gemm_desc_t *desc,
-                                       unsigned long long *counts, cudaStream_t s) {
+                                       unsigned long long *counts, double work, cudaStream_t s) {
     stats_pass1_kernel<<<gA + gB, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1, cols1,
                                                       ld1, gB, p1);
     cudaError_t e = cudaGetLastError();
@@ -509,7 +513,7 @@ cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     select2_kernel<<<1, kS2Threads, 0, s>>>(p1, p2, gA, gB, 2 * rows0 * cols0, 2 * rows1 * cols1,
-                                            tol, forced, desc, counts);
+                                            tol, forced, desc, counts, work);
     return cudaGetLastError();
 }
 

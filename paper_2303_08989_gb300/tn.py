@@ -522,7 +522,8 @@ class TreeGraph:
 def info_dict(info) -> dict:
     return {"seconds": info.seconds, "gemm_count": info.gemm_count,
             "gather_count": info.gather_count, "mode_count": list(info.mode_count),
-            "workspace_bytes": info.workspace_bytes, "flops": info.flops}
+            "workspace_bytes": info.workspace_bytes, "flops": info.flops,
+            "mode_flops": list(info.mode_flops)}
 
 
 # ---------------------------------------------------------------------------

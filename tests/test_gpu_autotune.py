@@ -48,7 +48,9 @@ def test_auto_counts_follow_the_device_selection(h):
         mode = oracle.select_mode(oracle.stats_summary(*oracle.exp_stats(X)),
                                   oracle.stats_summary(*oracle.exp_stats(Y)), 0.1)[0]
         want[lib().MODE_NAME[mode]] += 1
-    assert h.auto_counts(reset=True) == want
+    counts, flops = h.auto_counts(reset=True, flops=True)
+    assert counts == want
+    assert flops == {mode: 8.0 * m * n * k * cnt for mode, cnt in want.items()}
     assert sum(h.auto_counts(reset=False).values()) == 0
 
 
