@@ -160,9 +160,44 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
               float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta,
               float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out, const qcs_gemm_desc_t *d_desc_in,
               const GemmBatch &bt) {
+    OperandView va, vb;
+    va.X = A;
+    va.ld = lda;
+    vb.X = B;
+    vb.ld = ldb;
+    return run_cgemm_views(h, ws, eff, opA, opB, m, n, k, alpha, va, vb, beta, C, ldc, d_desc_out,
+                           d_desc_in, bt);
+}
+
+namespace {
+
+// Gather op(X) of a mapped view into its buffer (only if the GEMM selected
+// FP32 when gate is not NULL); the view then reads it as a matrix.
+int gather_view(qcs_handle_t h, OperandView &v, int64_t rows, const qcs_gemm_desc_t *gate) {
+    ProfScope ps(h, kProfPermute);
+    CopyBatch cb;
+    cb.gate = gate;
+    if (launch_permute(v.map->rank, v.map->dims, v.map->strides, 0, v.X, v.buf, nullptr, 0,
+                       h->stream, cb) != cudaSuccess)
+        return QCS_ERR_CUDA;
+    v.X = v.buf;
+    v.ld = rows;
+    v.map = nullptr;
+    return QCS_SUCCESS;
+}
+
+}  // namespace
+
+int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n,
+                    int64_t k, float2 alpha, const OperandView &A_in, const OperandView &B_in,
+                    float2 beta, float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out,
+                    const qcs_gemm_desc_t *d_desc_in, const GemmBatch &bt) {
     cudaStream_t s = h->stream;
-    if (bt.count != 1 && (eff != QCS_MODE_FP32 || k == 0 || d_desc_out || d_desc_in))
+    if (bt.count != 1 && (eff != QCS_MODE_FP32 || k == 0 || d_desc_out || d_desc_in ||
+                          A_in.map || B_in.map))
         return QCS_ERR_UNSUPPORTED;
+    if ((A_in.map && (opA != QCS_OP_N || !A_in.buf)) || (B_in.map && (opB != QCS_OP_N || !B_in.buf)))
+        return QCS_ERR_INVALID_ARG;
     uint8_t *p = static_cast<uint8_t *>(ws);
     qcs_gemm_desc_t *desc = reinterpret_cast<qcs_gemm_desc_t *>(p);
     p += 256;
@@ -171,17 +206,36 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
     float2 *splitk = reinterpret_cast<float2 *>(p);  // kSplitKBytes per batch entry (FP32 batches
     p += align256(kSplitKBytes);                      // run without planes, so the rest follows)
     cudaError_t e = cudaSuccess;
+    const int64_t kp = round_up(k, 32), mp = round_up(m, kBM), np = round_up(n, kBN);
+
+    // A mapped operand is split straight from its tensor when the emulated
+    // path runs and the map tiles with no plane padding; otherwise it is
+    // gathered here, once, and read as a matrix from then on.
+    OperandView A = A_in, B = B_in;
+    const bool emulated = (eff != QCS_MODE_FP32 && k > 0);
+    const bool fusedA = A.map && emulated && mp == m && kp == k &&
+                        split_gather_supported(0, A.map->rank, A.map->dims, A.map->strides, m, kp);
+    const bool fusedB = B.map && emulated && np == n && kp == k &&
+                        split_gather_supported(1, B.map->rank, B.map->dims, B.map->strides, k, kp);
+    if (A.map && !fusedA)
+        if (int r = gather_view(h, A, m, nullptr)) return r;
+    if (B.map && !fusedB)
+        if (int r = gather_view(h, B, k, nullptr)) return r;
 
     if (d_desc_in) {
         desc = const_cast<qcs_gemm_desc_t *>(d_desc_in);
     } else if (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X_SCALED) {
-        // Statistics of both operands as stored (a transpose does not change the multiset).
-        const int64_t ra = (opA == QCS_OP_N) ? m : k, ca = (opA == QCS_OP_N) ? k : m;
-        const int64_t rb = (opB == QCS_OP_N) ? k : n, cb = (opB == QCS_OP_N) ? n : k;
+        // Statistics of both operands as stored (a transpose or a whole-tensor
+        // permutation does not change the multiset).
+        const int64_t ra = fusedA ? A.flat : ((opA == QCS_OP_N) ? m : k);
+        const int64_t ca = fusedA ? 1 : ((opA == QCS_OP_N) ? k : m);
+        const int64_t rb = fusedB ? B.flat : ((opB == QCS_OP_N) ? k : n);
+        const int64_t cb = fusedB ? 1 : ((opB == QCS_OP_N) ? n : k);
+        const int64_t lda = fusedA ? A.flat : A.ld, ldb = fusedB ? B.flat : B.ld;
         const int gA = stats2_blocks(ra * ca, h->num_sms), gB = stats2_blocks(rb * cb, h->num_sms);
         {
             ProfScope ps(h, kProfStats);
-            e = launch_stats_select_2stage(A, ra, ca, lda, gA, B, rb, cb, ldb, gB, h->tol, eff,
+            e = launch_stats_select_2stage(A.X, ra, ca, lda, gA, B.X, rb, cb, ldb, gB, h->tol, eff,
                                            partials, partials + 5 * (gA + gB), desc,
                                            h->d_counts, 8.0 * (double)m * (double)n * (double)k,
                                            s);
@@ -195,11 +249,10 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
 
     if (k == 0) {
         // C = beta C: the SIMT kernel with k = 0 does exactly that (no desc gate).
-        e = launch_cgemm_simt(nullptr, opA, opB, m, n, 0, alpha, A, lda, B, ldb, beta, C, ldc,
+        e = launch_cgemm_simt(nullptr, opA, opB, m, n, 0, alpha, A.X, A.ld, B.X, B.ld, beta, C, ldc,
                               nullptr, s);
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     } else if (eff != QCS_MODE_FP32) {
-        const int64_t kp = round_up(k, 32), mp = round_up(m, kBM), np = round_up(n, kBN);
         const bool need16 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X ||
                              eff == QCS_MODE_FP16X_SCALED || eff == QCS_MODE_BF16X3);
         const bool need32 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X);
@@ -211,43 +264,62 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
         // kp elements either way, so both tensor maps below describe it.
         {
             ProfScope ps(h, kProfSplit);
-            plane_strides(0, opA, lda, sr, sc);
-            e = launch_split(desc, 0, A, sr, sc, opA == QCS_OP_C, m, k, mp, kp, planesA, kp,
-                             mp * kp, s);
+            if (fusedA) {
+                e = launch_split_gather(desc, 0, A.map->rank, A.map->dims, A.map->strides, A.X, m,
+                                        planesA, kp, mp * kp, s);
+            } else {
+                plane_strides(0, opA, A.ld, sr, sc);
+                e = launch_split(desc, 0, A.X, sr, sc, opA == QCS_OP_C, m, k, mp, kp, planesA, kp,
+                                 mp * kp, s);
+            }
             if (e == cudaSuccess) {
-                plane_strides(1, opB, ldb, sr, sc);
-                e = launch_split(desc, 1, B, sr, sc, opB == QCS_OP_C, n, k, np, kp, planesB, kp,
-                                 np * kp, s);
+                if (fusedB) {
+                    e = launch_split_gather(desc, 1, B.map->rank, B.map->dims, B.map->strides, B.X,
+                                            k, planesB, kp, np * kp, s);
+                } else {
+                    plane_strides(1, opB, B.ld, sr, sc);
+                    e = launch_split(desc, 1, B.X, sr, sc, opB == QCS_OP_C, n, k, np, kp, planesB,
+                                     kp, np * kp, s);
+                }
             }
         }
         if (e != cudaSuccess) return QCS_ERR_CUDA;
-        ProfScope ps_tc(h, kProfGemmTc);
-        if (need16) {
-            CUtensorMap ma, mb;
-            if (encode_planes(h, &ma, planesA, mp, kp, 2) || encode_planes(h, &mb, planesB, np, kp, 2))
-                return QCS_ERR_CUDA;
-            const int kind = (eff == QCS_MODE_BF16X3) ? 2 : 0;
-            e = launch_cgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
-                                ldc, h->d_err, h->num_sms, s);
-            if (e != cudaSuccess) return QCS_ERR_CUDA;
-        }
-        if (need32) {
-            CUtensorMap ma, mb;
-            if (encode_planes(h, &ma, planesA, mp, kp, 4) || encode_planes(h, &mb, planesB, np, kp, 4))
-                return QCS_ERR_CUDA;
-            e = launch_cgemm_tc(1, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
-                                ldc, h->d_err, h->num_sms, s);
-            if (e != cudaSuccess) return QCS_ERR_CUDA;
+        {
+            ProfScope ps_tc(h, kProfGemmTc);
+            if (need16) {
+                CUtensorMap ma, mb;
+                if (encode_planes(h, &ma, planesA, mp, kp, 2) ||
+                    encode_planes(h, &mb, planesB, np, kp, 2))
+                    return QCS_ERR_CUDA;
+                const int kind = (eff == QCS_MODE_BF16X3) ? 2 : 0;
+                e = launch_cgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
+                                    ldc, h->d_err, h->num_sms, s);
+                if (e != cudaSuccess) return QCS_ERR_CUDA;
+            }
+            if (need32) {
+                CUtensorMap ma, mb;
+                if (encode_planes(h, &ma, planesA, mp, kp, 4) ||
+                    encode_planes(h, &mb, planesB, np, kp, 4))
+                    return QCS_ERR_CUDA;
+                e = launch_cgemm_tc(1, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
+                                    ldc, h->d_err, h->num_sms, s);
+                if (e != cudaSuccess) return QCS_ERR_CUDA;
+            }
         }
         if (eff == QCS_MODE_AUTO) {
+            // the FP32 candidate: mapped operands are gathered only if it was selected
+            if (fusedA)
+                if (int r = gather_view(h, A, m, desc)) return r;
+            if (fusedB)
+                if (int r = gather_view(h, B, k, desc)) return r;
             ProfScope ps(h, kProfGemmSimt);
-            e = launch_cgemm_simt(desc, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+            e = launch_cgemm_simt(desc, opA, opB, m, n, k, alpha, A.X, A.ld, B.X, B.ld, beta, C, ldc,
                                   splitk, s);
             if (e != cudaSuccess) return QCS_ERR_CUDA;
         }
     } else {
         ProfScope ps(h, kProfGemmSimt);
-        e = launch_cgemm_simt(nullptr, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+        e = launch_cgemm_simt(nullptr, opA, opB, m, n, k, alpha, A.X, A.ld, B.X, B.ld, beta, C, ldc,
                               splitk, s, bt);
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     }

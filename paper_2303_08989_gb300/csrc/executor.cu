@@ -334,26 +334,72 @@ int batched_operand(const Ctx &c, int id, int direct, const qcs_gather_t &map, i
     return gather(c, map, src, buf, cb);
 }
 
-// One step for one instance (position g of its group): gathers, then
-// qcs_cgemm's launch sequence, output into the step's slot.
+// Does the map read every element of a tensor of ``size`` elements exactly
+// once (a permutation of the whole tensor, as for every intermediate)?
+bool whole_permutation(const qcs_gather_t &g, int64_t size) {
+    int64_t st[QCS_MAX_RANK], dm[QCS_MAX_RANK];
+    int r = 0;
+    for (int d = 0; d < g.rank; ++d)
+        if (g.dims[d] > 1) {
+            st[r] = g.strides[d];
+            dm[r++] = g.dims[d];
+        }
+    for (int i = 1; i < r; ++i)  // insertion sort by stride
+        for (int j = i; j > 0 && st[j] < st[j - 1]; --j) {
+            std::swap(st[j], st[j - 1]);
+            std::swap(dm[j], dm[j - 1]);
+        }
+    int64_t expect = 1;
+    for (int i = 0; i < r; ++i) {
+        if (st[i] != expect) return false;
+        expect *= dm[i];
+    }
+    return expect == size;
+}
+
+// The view of one operand of a step: the tensor through its map when the GEMM
+// is emulated and the operand is an intermediate permuted as a whole (the
+// split then reads through the map: no gather), else the gathered matrix or
+// the directly usable tensor.
+int operand_view(const Ctx &c, int s, int id, int direct, const qcs_gather_t &map, int inst, int g,
+                 int64_t rows, int64_t ld_direct, float2 *buf, OperandView &v) {
+    const float2 *X = tensor_ptr(c, id, inst, g);
+    if (direct != -1) {
+        v.X = X;
+        v.ld = ld_direct;
+        return QCS_SUCCESS;
+    }
+    if (c.L.eff[s] != QCS_MODE_FP32 && id >= c.t->n_leaves && whole_permutation(map, c.size_of[id])) {
+        v.X = X;
+        v.map = &map;
+        v.flat = c.size_of[id];
+        v.buf = buf;
+        return QCS_SUCCESS;
+    }
+    if (int r = gather(c, map, X, buf)) return r;
+    v.X = buf;
+    v.ld = rows;
+    return QCS_SUCCESS;
+}
+
+// One step for one instance (position g of its group): operand views (gathers
+// where needed), then qcs_cgemm's launch sequence, output into the step's slot.
 int step_instance(const Ctx &c, int s, int inst, int g) {
     const qcs_step_t &st = c.t->steps[s];
     float2 *bufA = reinterpret_cast<float2 *>(c.ws + c.L.bufA);
     float2 *bufB = reinterpret_cast<float2 *>(c.ws + c.L.bufB);
     const int opA = fwd_op(st.direct_a), opB = fwd_op(st.direct_b);
     const int64_t lda = opA == QCS_OP_T ? st.k : st.m, ldb = opB == QCS_OP_T ? st.n : st.k;
-    const float2 *A = tensor_ptr(c, st.a, inst, g);
-    const float2 *B = tensor_ptr(c, st.b, inst, g);
-    if (st.direct_a == -1) {
-        if (int r = gather(c, st.map_a, A, bufA)) return r;
-        A = bufA;
-    }
-    if (st.direct_b == -1) {
-        if (int r = gather(c, st.map_b, B, bufB)) return r;
-        B = bufB;
-    }
+    OperandView va, vb;
+    if (int r = operand_view(c, s, st.a, st.direct_a, st.map_a, inst, g, st.m, lda, bufA, va))
+        return r;
+    if (int r = operand_view(c, s, st.b, st.direct_b, st.map_b, inst, g, st.k, ldb, bufB, vb))
+        return r;
     float2 *C = inter_ptr(c, s) + (c.L.batched[s] ? (int64_t)g * st.m * st.n : 0);
-    return gemm(c, st.mode, opA, opB, st.m, st.n, st.k, A, lda, B, ldb, C);
+    count_gemm(c, c.L.eff[s], st.m, st.n, st.k);
+    return run_cgemm_views(c.h, c.ws + c.L.gemm, c.L.eff[s], opA, opB, st.m, st.n, st.k,
+                           make_float2(1.f, 0.f), va, vb, make_float2(0.f, 0.f), C, st.m, nullptr,
+                           nullptr);
 }
 
 // One batched step for the G instances of a group: batched gathers, one

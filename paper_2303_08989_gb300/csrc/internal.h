@@ -132,6 +132,7 @@ struct CopyBatch {
     const int64_t *off = nullptr;
     int64_t off_stride = 0;
     int64_t in_stride = 0, out_stride = 0;
+    const qcs_gemm_desc_t *gate = nullptr;  // not NULL: copy only if that GEMM selected FP32
 };
 
 // ---- launchers (kernels.cu) ----------------------------------------------
@@ -170,6 +171,20 @@ cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X
                          int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
                          void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s);
 
+// The split stage reading its operand through a gather map (the reshape of
+// a contraction folded into the split pass): op(X) is the rows x cols
+// column-major matrix whose element t = i + l rows is
+// src[sum_d x_d strides[d]] with t decomposed over dims (first fastest), as
+// qcs_gather_t describes it; ``which`` 0 writes it as the A planes (R = rows,
+// K = cols), 1 as the B planes (R = cols, K = rows).  No padding is written:
+// the caller needs R and K to be the padded sizes.  NotSupported (nothing
+// launched) when the map does not tile; split_gather_supported tells first.
+bool split_gather_supported(int which, int rank, const int64_t *dims, const int64_t *strides,
+                            int64_t rows, int64_t pitch);
+cudaError_t launch_split_gather(const qcs_gemm_desc_t *desc, int which, int rank,
+                                const int64_t *dims, const int64_t *strides, const float2 *src,
+                                int64_t rows, void *planes, int64_t pitch, int64_t plane_stride,
+                                cudaStream_t s);
 cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
                            const float2 *in, float2 *out, int64_t *stats_partials, int gstats,
                            cudaStream_t s, const CopyBatch &cb = CopyBatch{});
@@ -195,6 +210,29 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
               float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta,
               float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out, const qcs_gemm_desc_t *d_desc_in,
               const GemmBatch &bt = GemmBatch{});
+
+// An operand of run_cgemm_views: the column-major matrix X (leading
+// dimension ld, the GEMM's op applied), or -- when ``map`` is set -- op(X)
+// (op must be N) read through that gather map from the tensor X, whose
+// ``flat`` elements the map permutes as a whole.  ``buf`` (room for the
+// gathered matrix) receives op(X) when a kernel needs it as a matrix: the
+// FP32 path, or a split that cannot read through the map.
+struct OperandView {
+    const float2 *X = nullptr;
+    int64_t ld = 0;
+    const qcs_gather_t *map = nullptr;
+    int64_t flat = 0;
+    float2 *buf = nullptr;
+};
+// run_cgemm with operand views: a mapped operand of an emulated GEMM is never
+// gathered -- its statistics read the tensor as stored (a permutation keeps
+// the multiset of exponents), its split reads through the map, and only the
+// FP32 candidate of AUTO gathers it, when (and only when) that candidate was
+// selected.
+int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n,
+                    int64_t k, float2 alpha, const OperandView &A, const OperandView &B,
+                    float2 beta, float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out,
+                    const qcs_gemm_desc_t *d_desc_in, const GemmBatch &bt = GemmBatch{});
 
 // ---- GEMM launchers -------------------------------------------------------
 // Plain FP32 SIMT CGEMM (runs only when desc->mode == FP32, or always when

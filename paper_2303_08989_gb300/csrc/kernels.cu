@@ -548,6 +548,24 @@ __device__ __forceinline__ uint32_t tf32_rn(float x) {
     return r & 0xFFFFE000u;
 }
 
+// Eq. 1 for one scaled value xs: hi = toLow(xs), lo = toLow((xs - hi) 2^11),
+// as bit patterns of the mode's low-precision type.
+__device__ __forceinline__ void split_value(int mode, float xs, uint32_t &hi, uint32_t &lo) {
+    if (mode == QCS_MODE_TF32X) {
+        const uint32_t h = tf32_rn(xs);
+        hi = h;
+        lo = tf32_rn((xs - __uint_as_float(h)) * 2048.0f);
+    } else if (mode == QCS_MODE_BF16X3) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(xs);
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(__float2bfloat16_rn((xs - __bfloat162float(h)) * 2048.0f));
+    } else {
+        const __half h = __float2half_rn(xs);
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(__float2half_rn((xs - __half2float(h)) * 2048.0f));
+    }
+}
+
 __global__ void __launch_bounds__(256) split_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int which, const float2 *__restrict__ X, int64_t sr,
     int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad, void *planes,
@@ -598,25 +616,7 @@ __global__ void __launch_bounds__(256) split_kernel(
         // hi/lo of re and im for columns c and c+1
         uint32_t hib[4], lob[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float xs = (s != 0) ? ldexpf(x[e], s) : x[e];
-            if (mode == QCS_MODE_TF32X) {
-                const uint32_t h = tf32_rn(xs);
-                const float rres = xs - __uint_as_float(h);
-                hib[e] = h;
-                lob[e] = tf32_rn(rres * 2048.0f);
-            } else if (mode == QCS_MODE_BF16X3) {
-                const __nv_bfloat16 h = __float2bfloat16_rn(xs);
-                const float rres = xs - __bfloat162float(h);
-                hib[e] = __bfloat16_as_ushort(h);
-                lob[e] = __bfloat16_as_ushort(__float2bfloat16_rn(rres * 2048.0f));
-            } else {
-                const __half h = __float2half_rn(xs);
-                const float rres = xs - __half2float(h);
-                hib[e] = __half_as_ushort(h);
-                lob[e] = __half_as_ushort(__float2half_rn(rres * 2048.0f));
-            }
-        }
+        for (int e = 0; e < 4; ++e) split_value(mode, (s != 0) ? ldexpf(x[e], s) : x[e], hib[e], lob[e]);
         const bool two = (c + 1 < K_pad);
         if (mode == QCS_MODE_TF32X) {
             uint32_t *P = static_cast<uint32_t *>(planes);
@@ -710,6 +710,16 @@ struct CopyParams {
     // elements in (or g * bin when boff is NULL), its output g * bout.
     const int64_t *boff;
     int64_t boff_stride, bin, bout;
+    const qcs_gemm_desc_t *gate;  // not NULL: copy only if the GEMM selected plain FP32
+};
+
+// The split form of the tiled copy: each element is stored as its Eq. 1
+// planes (hi.re, hi.im, lo.re, lo.im), element ``out offset`` of each plane.
+struct SplitOut {
+    const qcs_gemm_desc_t *desc;
+    int which;  // 0: op(A), scale sA; 1: op(B), scale sB
+    void *planes;
+    int64_t plane_stride;
 };
 
 __device__ __forceinline__ int64_t batch_in(const CopyParams &P) {
@@ -743,9 +753,26 @@ __device__ __forceinline__ void decompose(const CopyParams &P, const int8_t *g, 
 
 constexpr int kTilesPerBlock = 8;
 
-__global__ void __launch_bounds__(256) copy_tiled_kernel(CopyParams P, const float2 *__restrict__ in,
-                                                         float2 *__restrict__ out, int accumulate) {
-    __shared__ float2 tile[32][33];
+// Up to kTilesPerBlock tiles (consecutive rest indices) per block, software
+// pipelined over two shared-memory buffers: the loads of tile t + 1 are in
+// flight while tile t is written out, so a warp keeps global reads and
+// writes outstanding at once.  Buffer t & 1 is rewritten two tiles later,
+// after a barrier that every thread reaches only once it has finished
+// reading that buffer.
+template <bool SPLIT>
+__global__ void __launch_bounds__(256, 6) copy_tiled_kernel(CopyParams P,
+                                                            const float2 *__restrict__ in,
+                                                            float2 *__restrict__ out,
+                                                            int accumulate, SplitOut so) {
+    int mode = 0, scale = 0;
+    if (SPLIT) {
+        mode = so.desc->mode;
+        if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
+        if (mode == QCS_MODE_FP16X_SCALED) scale = so.which == 0 ? so.desc->sA : so.desc->sB;
+    } else if (P.gate && P.gate->mode != QCS_MODE_FP32) {
+        return;
+    }
+    __shared__ float2 tile[2][32][33];
     __shared__ int64_t sxi[32], sxo[32], syi[32], syo[32], sr[kTilesPerBlock][2];
     in += batch_in(P);
     out += blockIdx.y * P.bout;
@@ -780,29 +807,59 @@ __global__ void __launch_bounds__(256) copy_tiled_kernel(CopyParams P, const flo
     __syncthreads();
     const bool yok = (y0 + tx) < P.py;
     const bool xok = (x0 + tx) < P.px;
-    for (int t = 0; t < kTilesPerBlock && rb + t < P.rest; ++t) {
-        const int64_t ri = sr[t][0], ro = sr[t][1];
-        if (t > 0) __syncthreads();  // the previous tile has been written out
-        // read: lanes along y (contiguous input)
+    const int nt = (int)min((int64_t)kTilesPerBlock, P.rest - rb);
+    // read: lanes along y (contiguous input)
+    float2 v[4];
+    auto load = [&](int t) {
+        const int64_t ri = sr[t][0];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int xl = ty + 8 * r;
-            if (yok && x0 + xl < P.px) tile[xl][tx] = in[ri + sxi[xl] + syi[tx]];
+            if (yok && x0 + xl < P.px) v[r] = in[ri + sxi[xl] + syi[tx]];
         }
+    };
+    load(0);
+    for (int t = 0; t < nt; ++t) {
+        const int buf = t & 1;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) tile[buf][ty + 8 * r][tx] = v[r];
         __syncthreads();
+        if (t + 1 < nt) load(t + 1);
         // write: lanes along x (contiguous output)
+        const int64_t ro = sr[t][1];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int yl = ty + 8 * r;
             if (xok && y0 + yl < P.py) {
-                float2 v = tile[tx][yl];
-                float2 *dst = out + ro + sxo[tx] + syo[yl];
-                if (accumulate) {
-                    const float2 w = *dst;
-                    v.x += w.x;
-                    v.y += w.y;
+                float2 w = tile[buf][tx][yl];
+                const int64_t o = ro + sxo[tx] + syo[yl];
+                if (SPLIT) {
+                    uint32_t h0, l0, h1, l1;
+                    split_value(mode, scale ? ldexpf(w.x, scale) : w.x, h0, l0);
+                    split_value(mode, scale ? ldexpf(w.y, scale) : w.y, h1, l1);
+                    const int64_t ps = so.plane_stride;
+                    if (mode == QCS_MODE_TF32X) {
+                        uint32_t *p = static_cast<uint32_t *>(so.planes) + o;
+                        p[0] = h0;
+                        p[ps] = h1;
+                        p[2 * ps] = l0;
+                        p[3 * ps] = l1;
+                    } else {
+                        uint16_t *p = static_cast<uint16_t *>(so.planes) + o;
+                        p[0] = (uint16_t)h0;
+                        p[ps] = (uint16_t)h1;
+                        p[2 * ps] = (uint16_t)l0;
+                        p[3 * ps] = (uint16_t)l1;
+                    }
+                    continue;
                 }
-                *dst = v;
+                float2 *dst = out + o;
+                if (accumulate) {
+                    const float2 u = *dst;
+                    w.x += u.x;
+                    w.y += u.y;
+                }
+                *dst = w;
             }
         }
     }
@@ -814,6 +871,7 @@ __global__ void __launch_bounds__(256) copy_tiled_kernel(CopyParams P, const flo
 __global__ void __launch_bounds__(256) copy_vector_kernel(CopyParams P, int nv, int64_t pv,
                                                           int64_t outer, const float2 *__restrict__ in,
                                                           float2 *__restrict__ out, int accumulate) {
+    if (P.gate && P.gate->mode != QCS_MODE_FP32) return;
     __shared__ int64_t so[2];
     in += batch_in(P);
     out += blockIdx.y * P.bout;
@@ -849,6 +907,7 @@ __global__ void __launch_bounds__(256) copy_vector_kernel(CopyParams P, int nv, 
 // Element-wise fallback (neither a tile nor a contiguous run applies).
 __global__ void copy_simple_kernel(CopyParams P, int64_t total, const float2 *__restrict__ in,
                                    float2 *__restrict__ out, int accumulate) {
+    if (P.gate && P.gate->mode != QCS_MODE_FP32) return;
     in += batch_in(P);
     out += blockIdx.y * P.bout;
     for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
@@ -911,36 +970,64 @@ void choose_groups(CopyParams &P) {
     }
 }
 
-cudaError_t launch_copy(int rank, const int64_t *dims, const int64_t *is, const int64_t *os,
-                        const float2 *in, float2 *out, int accumulate, cudaStream_t s,
-                        const CopyBatch &cb = CopyBatch{}) {
-    if (cb.count < 1 || cb.count > 65535) return cudaErrorInvalidValue;
-    CopyParams P{};
+// Dims, strides and the power-of-two shortcut of a copy.
+void set_dims(CopyParams &P, int rank, const int64_t *dims, const int64_t *is, const int64_t *os) {
     P.rank = rank;
-    P.boff = cb.off;
-    P.boff_stride = cb.off_stride;
-    P.bin = cb.in_stride;
-    P.bout = cb.out_stride;
-    const unsigned G = (unsigned)cb.count;
     P.pow2 = 1;
-    int64_t total = 1;
     for (int d = 0; d < rank; ++d) {
         P.dims[d] = dims[d];
         P.is[d] = is[d];
         P.os[d] = os[d];
-        total *= dims[d];
         if (dims[d] & (dims[d] - 1)) P.pow2 = 0;
         int lg = 0;
         while ((int64_t(1) << lg) < dims[d]) ++lg;
         P.lg[d] = (int8_t)lg;
     }
+}
+
+// With the X and Y groups chosen: the rest group and the tile counts.
+// Returns the number of blocks of the tiled kernel.
+int64_t finish_tiled(CopyParams &P) {
+    P.nr = 0;
+    int64_t rest = 1;
+    for (int d = 0; d < P.rank; ++d) {
+        bool in_group = false;
+        for (int a = 0; a < P.nx; ++a) in_group |= (P.gx[a] == d);
+        for (int c = 0; c < P.ny; ++c) in_group |= (P.gy[c] == d);
+        if (!in_group) {
+            P.gr[P.nr++] = (int8_t)d;
+            rest *= P.dims[d];
+        }
+    }
+    P.tiles_x = (P.px + 31) / 32;
+    P.tiles_y = (P.py + 31) / 32;
+    P.rest = rest;
+    return P.tiles_x * P.tiles_y * ((rest + kTilesPerBlock - 1) / kTilesPerBlock);
+}
+
+bool tiles_well(const CopyParams &P) { return P.nx > 0 && P.ny > 0 && P.px >= 4 && P.py >= 4; }
+
+cudaError_t launch_copy(int rank, const int64_t *dims, const int64_t *is, const int64_t *os,
+                        const float2 *in, float2 *out, int accumulate, cudaStream_t s,
+                        const CopyBatch &cb = CopyBatch{}) {
+    if (cb.count < 1 || cb.count > 65535) return cudaErrorInvalidValue;
+    CopyParams P{};
+    set_dims(P, rank, dims, is, os);
+    P.boff = cb.off;
+    P.boff_stride = cb.off_stride;
+    P.bin = cb.in_stride;
+    P.bout = cb.out_stride;
+    P.gate = cb.gate;
+    const unsigned G = (unsigned)cb.count;
+    int64_t total = 1;
+    for (int d = 0; d < rank; ++d) total *= dims[d];
     if (total == 0) return cudaSuccess;
     // dims contiguous from stride 1 on both sides (same dims, same order)
     int nv = 0;
     int64_t pv = 1;
     while (nv < rank && P.is[nv] == pv && P.os[nv] == pv) pv *= P.dims[nv++];
     choose_groups(P);
-    const bool tiled_ok = P.nx > 0 && P.ny > 0 && P.px >= 4 && P.py >= 4;
+    const bool tiled_ok = tiles_well(P);
     if (pv >= 32 || (!tiled_ok && pv >= 4)) {
         const int64_t outer = total / pv;
         const int64_t blocks = outer < 65536 ? outer : 65536;
@@ -952,25 +1039,76 @@ cudaError_t launch_copy(int rank, const int64_t *dims, const int64_t *is, const 
         copy_simple_kernel<<<dim3(grid_for(total), G), 256, 0, s>>>(P, total, in, out, accumulate);
         return cudaGetLastError();
     }
-    P.nr = 0;
-    int64_t rest = 1;
-    for (int d = 0; d < rank; ++d) {
-        bool in_group = false;
-        for (int a = 0; a < P.nx; ++a) in_group |= (P.gx[a] == d);
-        for (int c = 0; c < P.ny; ++c) in_group |= (P.gy[c] == d);
-        if (!in_group) {
-            P.gr[P.nr++] = (int8_t)d;
-            rest *= dims[d];
-        }
-    }
-    P.tiles_x = (P.px + 31) / 32;
-    P.tiles_y = (P.py + 31) / 32;
-    P.rest = rest;
-    const int64_t blocks = P.tiles_x * P.tiles_y * ((rest + kTilesPerBlock - 1) / kTilesPerBlock);
+    const int64_t blocks = finish_tiled(P);
     if (blocks > INT32_MAX) return cudaErrorInvalidValue;
-    copy_tiled_kernel<<<dim3((unsigned)blocks, G), 256, 0, s>>>(P, in, out, accumulate);
+    copy_tiled_kernel<false><<<dim3((unsigned)blocks, G), 256, 0, s>>>(P, in, out, accumulate,
+                                                                      SplitOut{});
     return cudaGetLastError();
 }
+
+// The split of a gathered operand as one tiled copy (see launch_split_gather).
+bool split_gather_params(int which, int rank, const int64_t *dims, const int64_t *strides,
+                         int64_t rows, int64_t pitch, CopyParams &P) {
+    int64_t d2[QCS_MAX_RANK], is[QCS_MAX_RANK], os[QCS_MAX_RANK];
+    int r2 = 0;
+    // a dim of the gather view contributes x * cum to the view's linear index
+    // t = (fast index) + rows * (slow index); its plane offset is fixed by
+    // which part it lies in
+    auto push = [&](int64_t dim, int64_t stride, int64_t cum) {
+        if (r2 >= QCS_MAX_RANK) return false;
+        const bool fast = cum < rows;
+        const int64_t unit = fast ? cum : cum / rows;
+        // op(A): plane row = fast index, column = slow; op(B): the other way round
+        const bool to_row = (which == 0) == fast;
+        d2[r2] = dim;
+        is[r2] = stride;
+        os[r2] = to_row ? unit * pitch : unit;
+        ++r2;
+        return true;
+    };
+    int64_t cum = 1;
+    for (int d = 0; d < rank; ++d) {
+        const int64_t dd = dims[d];
+        if (cum < rows && cum * dd > rows) {  // straddles the boundary: two dims
+            if (rows % cum != 0) return false;
+            const int64_t d1 = rows / cum;
+            if (dd % d1 != 0) return false;
+            if (!push(d1, strides[d], cum) || !push(dd / d1, strides[d] * d1, cum * d1)) return false;
+        } else if (!push(dd, strides[d], cum)) {
+            return false;
+        }
+        cum *= dd;
+    }
+    P = CopyParams{};
+    set_dims(P, r2, d2, is, os);
+    choose_groups(P);
+    return tiles_well(P);
+}
+
+}  // namespace
+
+bool split_gather_supported(int which, int rank, const int64_t *dims, const int64_t *strides,
+                            int64_t rows, int64_t pitch) {
+    CopyParams P;
+    return split_gather_params(which, rank, dims, strides, rows, pitch, P);
+}
+
+cudaError_t launch_split_gather(const qcs_gemm_desc_t *desc, int which, int rank,
+                                const int64_t *dims, const int64_t *strides, const float2 *src,
+                                int64_t rows, void *planes, int64_t pitch, int64_t plane_stride,
+                                cudaStream_t s) {
+    CopyParams P;
+    if (!split_gather_params(which, rank, dims, strides, rows, pitch, P))
+        return cudaErrorNotSupported;
+    const int64_t blocks = finish_tiled(P);
+    if (blocks == 0) return cudaSuccess;
+    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+    SplitOut so{desc, which, planes, plane_stride};
+    copy_tiled_kernel<true><<<dim3((unsigned)blocks, 1), 256, 0, s>>>(P, src, nullptr, 0, so);
+    return cudaGetLastError();
+}
+
+namespace {
 
 // dst[j] += (double) src[index ? index[j] : j], j < count (FP64 sums over
 // slices, Section 5.3).

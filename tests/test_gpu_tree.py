@@ -335,3 +335,56 @@ def test_instance_groups_with_direct_and_split_k_steps():
         hd.close()
     ref = oracle.sv_amplitudes(circ, bits)
     assert oracle.fidelity(ref, one[:, 0]) >= 1 - 1e-5
+
+
+@pytest.mark.parametrize("mode", ["fp16x", "tf32x", "auto"])
+def test_split_through_the_map_equals_gather_then_split(mode):
+    """An emulated step whose operand is a permuted intermediate is split
+    straight from the intermediate through its gather map (no gather pass;
+    statistics read the intermediate as stored).  The result must equal, bit
+    for bit, gathering the operand first and running qcs_cgemm on it."""
+    need_gpu()
+    tn = _tn()
+    q = lib()
+    rng = np.random.default_rng(11)
+
+    def leaf(labels, dims):
+        x = (rng.standard_normal(int(np.prod(dims))) + 1j * rng.standard_normal(int(np.prod(dims))))
+        return tn.Leaf(x.astype(np.complex64), list(labels), list(dims))
+
+    I, J, P, Q, R = 0, 1, 2, 3, 4
+    d = {I: 128, J: 8, P: 16, Q: 32, R: 256}
+    L0 = leaf([J, I, P], [d[J], d[I], d[P]])
+    L1 = leaf([P, Q], [d[P], d[Q]])
+    L2 = leaf([J, Q, R], [d[J], d[Q], d[R]])
+    net = tn.Network([L0, L1, L2], [I, R], d)
+    plan = tn.build_plan(net, [(0, 1), (3, 2)], mode=q.MODE_FP32)
+    s1 = plan.steps[1]
+    assert s1.direct_a == -1 and (s1.m, s1.n, s1.k) == (128, 256, 256)
+    s1.mode = q.MODE_BY_NAME[mode]
+    hd = q.Handle(tol=0.0, size_rule=False)
+    try:
+        cp = tn.CompiledPlan(plan)
+        got = cp.forward(hd)
+        torch.cuda.synchronize()
+        hd.sync()
+        got = got.cpu().numpy()[0]
+        # the same two GEMMs by hand: step 0 in FP32, gather with torch, qcs_cgemm
+        s0 = plan.steps[0]
+        A0 = torch.as_strided(torch.from_numpy(L0.data).cuda(), tuple(s0.map_a[0][::-1]),
+                              tuple(s0.map_a[1][::-1])).reshape(s0.k, s0.m).t()
+        B0 = torch.as_strided(torch.from_numpy(L1.data).cuda(), tuple(s0.map_b[0][::-1]),
+                              tuple(s0.map_b[1][::-1])).reshape(s0.n, s0.k).t()
+        T = q.cgemm(hd, q.to_fortran(A0), q.to_fortran(B0), mode="fp32")
+        Tflat = T.t().reshape(-1)  # column-major storage of the intermediate
+        A1 = torch.as_strided(Tflat, tuple(s1.map_a[0][::-1]), tuple(s1.map_a[1][::-1]))
+        A1 = q.to_fortran(A1.reshape(s1.k, s1.m).t())
+        B1 = torch.as_strided(torch.from_numpy(L2.data).cuda(), tuple(s1.map_b[0][::-1]),
+                              tuple(s1.map_b[1][::-1])).reshape(s1.n, s1.k).t()
+        C1 = q.cgemm(hd, A1, q.to_fortran(B1), mode=mode)
+        torch.cuda.synchronize()
+        want = C1.cpu().numpy().astype(np.complex128)  # [i, r]
+    finally:
+        hd.close()
+    # the open result is ordered like numpy C order over the output labels (I, R)
+    assert np.array_equal(got.reshape(d[I], d[R]), want)
