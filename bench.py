@@ -426,7 +426,8 @@ def hbm_legs(q, torch, dev, h, stages, n):
         res["exp_stats"] = entry(2 * 8 * n * n, stages["stats"]["ms_per_step"])
         res["exp_stats"]["note"] = "pass 1 over A and B (pass 2 not needed by this input)"
     if "split" in stages:
-        res["split"] = entry(2 * (8 + 8) * n * n, stages["split"]["ms_per_step"])
+        # A: 8 B read + 4 FP16 planes (8 B) written; B: 8 B read + 5 planes (10 B)
+        res["split"] = entry((8 + 8 + 8 + 10) * n * n, stages["split"]["ms_per_step"])
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def timed(fn, reps=5):

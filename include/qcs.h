@@ -120,12 +120,13 @@ int qcs_set_underflow_tol(qcs_handle_t h, double t);
 int qcs_set_size_rule(qcs_handle_t h, int rule);
 
 /* Round-to-nearest drain interval of the tensor-core kernels: the hi*hi
- * products are summed in tensor memory for ``stages`` pipeline stages (each
- * two tensor-core K steps: 32 complex k for FP16/BF16, 16 for TF32), where
- * the hardware accumulation truncates, then added to round-to-nearest FP32
- * sums (Section 2.1's remedy for the tensor core's rounding toward zero,
- * applied per group of MMAs).  1, 2 or 4; default 4 (environment override
- * QCS_DRAIN_STAGES).  Larger groups are faster and slightly less accurate. */
+ * products are summed in tensor memory over groups of 2 x ``stages``
+ * tensor-core K steps (32 x ``stages`` complex k for FP16/BF16, 16 x
+ * ``stages`` for TF32), where the hardware accumulation truncates, then
+ * added to round-to-nearest FP32 sums (Section 2.1's remedy for the tensor
+ * core's rounding toward zero, applied per group of MMAs).  1, 2 or 4;
+ * default 4 (environment override QCS_DRAIN_STAGES).  Larger groups are
+ * faster and slightly less accurate. */
 int qcs_set_drain_stages(qcs_handle_t h, int stages);
 
 /* Exponent statistics (Section 4.1, Stage 1 and Stage 2 in one pass) of the
@@ -316,9 +317,10 @@ int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
  * lives in a fixed device array of QCS_NOALLOC_SCRATCH_BYTES (64 MiB) that
  * every GPU which loads this part of the library keeps until the process
  * exits.  A problem whose workspace does not fit -- 256 bytes, the
- * statistics partials, and the split planes of op(A) and op(B): 16 bytes per
- * element of ceil(m/128)*128 x ceil(k/32)*32 plus ceil(n/128)*128 x
- * ceil(k/32)*32 for AUTO and TF32X, 8 for the 16-bit modes, none for FP32 --
+ * statistics partials, the split-K buffer and the split planes: for op(A)
+ * 16 bytes per element of ceil(m/128)*128 x ceil(k/32)*32 and for op(B) 20
+ * bytes per element of ceil(n/128)*128 x ceil(k/32)*32 in AUTO and TF32X,
+ * half that in the 16-bit modes, none in FP32 --
  * is rejected with QCS_ERR_SCRATCH_TOO_SMALL before anything is launched
  * (m = n = k = 1024 fits in every mode).
  *

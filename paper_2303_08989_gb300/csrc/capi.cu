@@ -95,13 +95,16 @@ int stats2_blocks(int64_t nel, int num_sms) {
     return static_cast<int>(g);
 }
 
+// Tensor map of one operand's planes: {K, R, nplanes}, box = one stage of all
+// planes (kRowBytes of K x 128 rows), 64-byte swizzle (the layout the
+// kernel's shared-memory descriptors describe).
 int encode_planes(qcs_handle_t h, CUtensorMap *map, void *base, int64_t R_pad, int64_t K_pad,
-                  int esz) {
+                  int esz, int nplanes) {
     const CUtensorMapDataType dt =
         esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    cuuint64_t gdim[3] = {(cuuint64_t)K_pad, (cuuint64_t)R_pad, (cuuint64_t)kPlanes};
+    cuuint64_t gdim[3] = {(cuuint64_t)K_pad, (cuuint64_t)R_pad, (cuuint64_t)nplanes};
     cuuint64_t gstride[2] = {(cuuint64_t)(K_pad * esz), (cuuint64_t)(K_pad * R_pad * esz)};
-    cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)kBM, (cuuint32_t)kPlanes};
+    cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)kBM, (cuuint32_t)nplanes};
     cuuint32_t estride[3] = {1, 1, 1};
     CUresult r = h->encode(map, dt, 3, base, gdim, gstride, box, estride,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -151,7 +154,7 @@ size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sm
         const int esz = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X) ? 4 : 2;
         const int64_t kp = round_up(k, 32), mp = round_up(m, kBM), np = round_up(n, kBN);
         bytes += align256(size_t(kPlanes) * mp * kp * esz);
-        bytes += align256(size_t(kPlanes) * np * kp * esz);
+        bytes += align256(size_t(kPlanesB) * np * kp * esz);
     }
     return bytes;
 }
@@ -266,7 +269,7 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
             ProfScope ps(h, kProfSplit);
             if (fusedA) {
                 e = launch_split_gather(desc, 0, A.map->rank, A.map->dims, A.map->strides, A.X, m,
-                                        planesA, kp, mp * kp, s);
+                                        planesA, kp, mp * kp, s, 0);
             } else {
                 plane_strides(0, opA, A.ld, sr, sc);
                 e = launch_split(desc, 0, A.X, sr, sc, opA == QCS_OP_C, m, k, mp, kp, planesA, kp,
@@ -275,11 +278,11 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
             if (e == cudaSuccess) {
                 if (fusedB) {
                     e = launch_split_gather(desc, 1, B.map->rank, B.map->dims, B.map->strides, B.X,
-                                            k, planesB, kp, np * kp, s);
+                                            k, planesB, kp, np * kp, s, 1);
                 } else {
                     plane_strides(1, opB, B.ld, sr, sc);
                     e = launch_split(desc, 1, B.X, sr, sc, opB == QCS_OP_C, n, k, np, kp, planesB,
-                                     kp, np * kp, s);
+                                     kp, np * kp, s, 1);
                 }
             }
         }
@@ -288,8 +291,8 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
             ProfScope ps_tc(h, kProfGemmTc);
             if (need16) {
                 CUtensorMap ma, mb;
-                if (encode_planes(h, &ma, planesA, mp, kp, 2) ||
-                    encode_planes(h, &mb, planesB, np, kp, 2))
+                if (encode_planes(h, &ma, planesA, mp, kp, 2, kPlanes) ||
+                    encode_planes(h, &mb, planesB, np, kp, 2, kPlanesB))
                     return QCS_ERR_CUDA;
                 const int kind = (eff == QCS_MODE_BF16X3) ? 2 : 0;
                 e = launch_cgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
@@ -298,8 +301,8 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
             }
             if (need32) {
                 CUtensorMap ma, mb;
-                if (encode_planes(h, &ma, planesA, mp, kp, 4) ||
-                    encode_planes(h, &mb, planesB, np, kp, 4))
+                if (encode_planes(h, &ma, planesA, mp, kp, 4, kPlanes) ||
+                    encode_planes(h, &mb, planesB, np, kp, 4, kPlanesB))
                     return QCS_ERR_CUDA;
                 e = launch_cgemm_tc(1, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
                                     ldc, h->d_err, h->num_sms, s);

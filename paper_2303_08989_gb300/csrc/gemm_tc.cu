@@ -2,40 +2,51 @@
 // (tcgen05, sm_103a).
 //
 // Method (Section 2.1, Eq. 1; Section 3): every FP32 operand x is split into
-// hi = toLow(x 2^s) and lo = toLow((x 2^s - hi) 2^11) (done by the split
-// kernel, which writes four planes per operand: hi.re, hi.im, lo.re, lo.im).
+// hi = toLow(x 2^s) and lo = toLow((x 2^s - hi) 2^11) by the split kernel.
 // A complex product is four real products (Re = ArBr - AiBi,
 // Im = ArBi + AiBr); each real product is emulated by three tensor-core
 // products, hi*hi into accumulator 0 and lo*hi + hi*lo into accumulator 1:
 //   C = 2^-(sA+sB) (acc0 + 2^-11 acc1).
+//
+// Complex products as N = 256 MMAs.  op(A) has four planes (hi.re, hi.im,
+// lo.re, lo.im); op(B) has five, -Bi_hi, Br_hi, Bi_hi, Br_lo, Bi_lo, so that
+// two consecutive hi planes are one 256-row operand.  With an accumulator
+// laid out as [re | im] (256 columns),
+//   Ar x [Br; Bi]  adds [Ar Br | Ar Bi],   Ai x [-Bi; Br]  adds [-Ai Bi | Ai Br],
+// so the hi*hi and lo*hi products of a complex product are two MMAs each
+// that read 12 KB of shared memory for 128 x 256 x 16 instead of two 8 KB
+// reads per 128 x 128 x 16; the hi*lo products stay N = 128 MMAs (the
+// -Ai Bi term through the negate-A bit), which keeps a stage at 72 KB so that
+// three stages fit.  Per K step the tensor core reads 80 KB of shared memory
+// instead of 96 KB: those reads paced the all-N = 128 form.
 //
 // Rounding.  Section 2.1 adds the hi*hi products outside the tensor core with
 // round-to-nearest because the A100 tensor core truncates inside its
 // accumulation.  The sm_103a tensor core truncates too (measured: 1 + 0.75 ulp
 // accumulates to 1, within one MMA and across MMAs, for FP16 and TF32
 // inputs), which makes the error of a TMEM-resident hi*hi sum grow linearly
-// with k.  So accumulator 0 is drained every DRAIN pipeline stages (two UMMA
+// with k.  So accumulator 0 is drained every DRAIN pipeline stages (two MMA
 // K steps each): that group's hi*hi sum is computed fresh in tensor memory
 // and added with round-to-nearest FP32 adds into registers of the epilogue
-// warps.  The
-// correction products (accumulator 1, weight 2^-11) stay in tensor memory for
-// the whole K loop: their truncation error enters the result scaled by 2^-11.
+// warps.  The correction products (accumulator 1, weight 2^-11) stay in
+// tensor memory for the whole K loop: their truncation error enters the
+// result scaled by 2^-11.
 //
 // Kernel structure (one CTA per SM, persistent over 128 x 128 complex tiles):
 //   warp 0     TMA producer: per stage, one 3-D box of the four A planes and
-//              one of the four B planes (128 rows x 64 bytes each, 64-byte
+//              one of the five B planes (128 rows x 64 bytes each, 64-byte
 //              swizzle) into a 3-stage shared-memory ring.
-//   warp 1     MMA issuer (one thread).  Per stage: the 16 correction MMAs into
-//              acc1 first; then, once the epilogue has drained the previous
-//              stage's acc0, the 8 hi*hi MMAs into a fresh acc0.  The drain thus
-//              overlaps the correction MMAs.  Tensor memory: 512 columns =
-//              acc0.re, acc0.im, acc1.re, acc1.im x 128.  The -Ai*Bi terms use
-//              the instruction descriptor's negate-A bit.
+//   warp 1     MMA issuer (one thread).  Per stage (two K steps): the 12
+//              correction MMAs into acc1 first; then, once the epilogue has
+//              drained the previous group's acc0, the 4 hi*hi MMAs (into a
+//              fresh acc0 at a group's first stage).  The drain thus overlaps
+//              the correction MMAs.
+//              Tensor memory: 512 columns = acc0 [re | im], acc1 [re | im].
 //   warps 2-9  epilogue, two warps per tensor-memory lane quadrant (each owns
-//              64 columns of its 32 rows): per stage, tcgen05.ld of acc0 and
-//              round-to-nearest adds into 128 registers; at the end of a tile,
-//              + 2^-11 acc1, the alpha/beta epilogue and coalesced stores (32
-//              consecutive complex values of one column per store).
+//              64 columns of its 32 rows): per drain group, tcgen05.ld of acc0
+//              and round-to-nearest adds into 128 registers; at the end of a
+//              tile, + 2^-11 acc1, the alpha/beta epilogue and coalesced stores
+//              (32 consecutive complex values of one column per store).
 // The descriptor the selector wrote decides at run time whether this
 // instantiation runs at all (the "launch all candidates, the unselected one
 // exits" scheme of Section 4.2).
@@ -137,7 +148,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int tiles_n = (n + kBN - 1) / kBN;
     const int num_tiles = tiles_m * tiles_n;
     constexpr int kElemBytes = (KIND == 1) ? 4 : 2;
-    constexpr int kKPerStage = kRowBytes / kElemBytes;  // 32 (16-bit) or 16 (TF32)
+    constexpr int kKPerStage = kRowBytes / kElemBytes;  // two MMA K steps: 32 (16-bit) or 16 (TF32)
     const int num_kb = k_pad / kKPerStage;
 
     if (warp == 0) {
@@ -159,7 +170,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     mbar_arrive_expect_tx(&S.full[stage], kStageBytes);
                     tma_load_3d(S.stage[stage], &mapA, &S.full[stage], kb * kKPerStage, tm * kBM, 0);
-                    tma_load_3d(S.stage[stage] + kOperandStageBytes, &mapB, &S.full[stage],
+                    tma_load_3d(S.stage[stage] + kAStageBytes, &mapB, &S.full[stage],
                                 kb * kKPerStage, tn * kBN, 0);
                     ++issued;
                     if (++stage == kStages) {
@@ -185,9 +196,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             constexpr uint32_t fmt = (KIND == 0) ? 0u : (KIND == 1 ? 2u : 1u);
-            constexpr uint32_t id = idesc_make(fmt, kBM, kBN, 0);
-            constexpr uint32_t idn = idesc_make(fmt, kBM, kBN, 1);  // negated A
-            const uint32_t a0r = tmem, a0i = tmem + 128, a1r = tmem + 256, a1i = tmem + 384;
+            constexpr uint32_t id = idesc_make(fmt, kBM, 2 * kBN, 0);   // M 128, N 256
+            constexpr uint32_t idh = idesc_make(fmt, kBM, kBN, 0);      // M 128, N 128
+            constexpr uint32_t idhn = idesc_make(fmt, kBM, kBN, 1);     // ... negated A
+            const uint32_t a0 = tmem, a1 = tmem + 256;  // [re | im] each
+            const uint32_t a1r = a1, a1i = a1 + 128;
             int stage = 0;
             uint32_t phase = 0, e_phase = 0;
             bool pending = false;  // an acc0 drain the epilogue has not yet confirmed
@@ -218,22 +231,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     // Descriptors differ only in the start-address field (bits 0..13,
                     // address >> 4), which never carries out for shared memory.
+                    // A planes: 0 Ar_hi, 1 Ai_hi, 2 Ar_lo, 3 Ai_lo.  B planes:
+                    // 0 -Bi_hi, 1 Br_hi, 2 Bi_hi, 3 Br_lo, 4 Bi_lo; the 256-row
+                    // operand at plane p covers planes p and p + 1.  K step ks
+                    // starts 32 bytes into each 64-byte row.
                     const uint64_t dA = sdesc_kmajor_sw64(smem_u32(S.stage[stage]));
-                    const uint64_t dB = dA + (kOperandStageBytes >> 4);
+                    const uint64_t dB = dA + (kAStageBytes >> 4);
 #define A_(ks, p) (dA + (uint64_t)(((p) * kTileBytes + (ks) * 32) >> 4))
 #define B_(ks, p) (dB + (uint64_t)(((p) * kTileBytes + (ks) * 32) >> 4))
-                    // correction products: acc1 += lo*hi + hi*lo (planes 0/1 hi.re/im, 2/3 lo.re/im)
+                    // correction products: acc1 += lo*hi + hi*lo
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
                         const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;
-                        mma<KIND>(a1r, A_(ks, 2), B_(ks, 0), id, first);   //  Ar_lo Br_hi
-                        mma<KIND>(a1i, A_(ks, 2), B_(ks, 1), id, first);   //  Ar_lo Bi_hi
-                        mma<KIND>(a1r, A_(ks, 3), B_(ks, 1), idn, 1u);     // -Ai_lo Bi_hi
-                        mma<KIND>(a1i, A_(ks, 3), B_(ks, 0), id, 1u);      //  Ai_lo Br_hi
-                        mma<KIND>(a1r, A_(ks, 0), B_(ks, 2), id, 1u);      //  Ar_hi Br_lo
-                        mma<KIND>(a1i, A_(ks, 0), B_(ks, 3), id, 1u);      //  Ar_hi Bi_lo
-                        mma<KIND>(a1r, A_(ks, 1), B_(ks, 3), idn, 1u);     // -Ai_hi Bi_lo
-                        mma<KIND>(a1i, A_(ks, 1), B_(ks, 2), id, 1u);      //  Ai_hi Br_lo
+                        mma<KIND>(a1, A_(ks, 2), B_(ks, 1), id, first);   // Ar_lo [Br_hi; Bi_hi]
+                        mma<KIND>(a1, A_(ks, 3), B_(ks, 0), id, 1u);      // Ai_lo [-Bi_hi; Br_hi]
+                        mma<KIND>(a1r, A_(ks, 0), B_(ks, 3), idh, 1u);    //  Ar_hi Br_lo
+                        mma<KIND>(a1i, A_(ks, 0), B_(ks, 4), idh, 1u);    //  Ar_hi Bi_lo
+                        mma<KIND>(a1r, A_(ks, 1), B_(ks, 4), idhn, 1u);   // -Ai_hi Bi_lo
+                        mma<KIND>(a1i, A_(ks, 1), B_(ks, 3), idh, 1u);    //  Ai_hi Br_lo
                     }
                     // hi*hi products: a fresh acc0 every DRAIN stages, once the
                     // previous one was drained
@@ -246,10 +261,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
                         const uint32_t first = (ks == 0 && group_start) ? 0u : 1u;
-                        mma<KIND>(a0r, A_(ks, 0), B_(ks, 0), id, first);   //  Ar_hi Br_hi
-                        mma<KIND>(a0i, A_(ks, 0), B_(ks, 1), id, first);   //  Ar_hi Bi_hi
-                        mma<KIND>(a0r, A_(ks, 1), B_(ks, 1), idn, 1u);     // -Ai_hi Bi_hi
-                        mma<KIND>(a0i, A_(ks, 1), B_(ks, 0), id, 1u);      //  Ai_hi Br_hi
+                        mma<KIND>(a0, A_(ks, 0), B_(ks, 1), id, first);   // Ar_hi [Br_hi; Bi_hi]
+                        mma<KIND>(a0, A_(ks, 1), B_(ks, 0), id, 1u);      // Ai_hi [-Bi_hi; Br_hi]
                     }
 #undef A_
 #undef B_
@@ -392,6 +405,8 @@ cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
     return cudaGetLastError();
 }
 
+// ``drain``: pipeline stages per group, each two MMA K steps (32 k for the
+// 16-bit kinds, 16 for TF32).
 template <int KIND>
 cudaError_t launch_drain(int drain, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
                          const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad,

@@ -28,14 +28,18 @@ constexpr uint64_t kWaitBudgetNs = 2000000000ull;
 // Tile geometry of the tensor-core GEMM.
 constexpr int kBM = 128;          // complex rows of C per tile (TMEM lanes)
 constexpr int kBN = 128;          // complex columns of C per tile
-constexpr int kRowBytes = 64;     // K bytes of one smem operand row per stage
+constexpr int kRowBytes = 64;     // K bytes of one smem operand row per stage (two MMA K steps)
 constexpr int kStages = 3;
-constexpr int kPlanes = 4;        // hi.re, hi.im, lo.re, lo.im
+constexpr int kPlanes = 4;        // planes of op(A), and of op(B) in qcs_split: hi.re, hi.im, lo.re, lo.im
+// op(B) in the GEMM path: five planes, so that the hi planes pair up as the
+// 256-row B operands [-Bi; Br] and [Br; Bi] of N = 256 MMAs.
+constexpr int kPlanesB = 5;       // -hi.im, hi.re, hi.im, lo.re, lo.im
 constexpr int kTileBytes = kBM * kRowBytes;                // one plane tile: 8 KB
-constexpr int kOperandStageBytes = kPlanes * kTileBytes;   // 32 KB
-constexpr int kStageBytes = 2 * kOperandStageBytes;        // A + B: 64 KB
+constexpr int kAStageBytes = kPlanes * kTileBytes;         // 32 KB
+constexpr int kBStageBytes = kPlanesB * kTileBytes;        // 40 KB
+constexpr int kStageBytes = kAStageBytes + kBStageBytes;   // 72 KB
 constexpr int kTcThreads = 320;   // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
-constexpr int kTmemCols = 512;    // acc0.re, acc0.im, acc1.re, acc1.im x 128 columns
+constexpr int kTmemCols = 512;    // acc0 [re | im], acc1 [re | im] x 128 columns
 
 // Split-K FP32 path for small outputs with long k: at most this many
 // outputs, and at most this many (output, k chunk) partials in the scratch.
@@ -166,10 +170,13 @@ cudaError_t launch_set_desc(qcs_gemm_desc_t *desc, int mode, cudaStream_t s);
 // Split op(X) into 4 planes (R x K, row pitch ``pitch`` elements, planes
 // ``plane_stride`` elements apart); rows >= R or columns >= K up to
 // R_pad x K_pad are zero-filled.  (sr, sc): element strides of X for a step
-// in r and in c; conj: negate imaginary parts.
+// in r and in c; conj: negate imaginary parts.  planes6 (the name predates
+// the layout): the kPlanesB-plane op(B) layout of the tensor-core GEMM
+// (-hi.im, hi.re, hi.im, lo.re, lo.im).
 cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
                          int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
-                         void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s);
+                         void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
+                         int planes6 = 0);
 
 // The split stage reading its operand through a gather map (the reshape of
 // a contraction folded into the split pass): op(X) is the rows x cols
@@ -184,7 +191,7 @@ bool split_gather_supported(int which, int rank, const int64_t *dims, const int6
 cudaError_t launch_split_gather(const qcs_gemm_desc_t *desc, int which, int rank,
                                 const int64_t *dims, const int64_t *strides, const float2 *src,
                                 int64_t rows, void *planes, int64_t pitch, int64_t plane_stride,
-                                cudaStream_t s);
+                                cudaStream_t s, int planes6 = 0);
 cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
                            const float2 *in, float2 *out, int64_t *stats_partials, int gstats,
                            cudaStream_t s, const CopyBatch &cb = CopyBatch{});

@@ -566,10 +566,12 @@ __device__ __forceinline__ void split_value(int mode, float xs, uint32_t &hi, ui
     }
 }
 
-__global__ void __launch_bounds__(256) split_kernel(
+// planes6: write op(B) as the five planes of the GEMM path (-hi.im, hi.re,
+// hi.im, lo.re, lo.im) instead of hi.re, hi.im, lo.re, lo.im.
+__global__ void __launch_bounds__(256, 8) split_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int which, const float2 *__restrict__ X, int64_t sr,
     int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad, void *planes,
-    int64_t pitch, int64_t plane_stride) {
+    int64_t pitch, int64_t plane_stride, int planes6) {
     const int mode = desc->mode;
     if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
     const int s = (mode == QCS_MODE_FP16X_SCALED) ? (which == 0 ? desc->sA : desc->sB) : 0;
@@ -618,46 +620,56 @@ __global__ void __launch_bounds__(256) split_kernel(
 #pragma unroll
         for (int e = 0; e < 4; ++e) split_value(mode, (s != 0) ? ldexpf(x[e], s) : x[e], hib[e], lob[e]);
         const bool two = (c + 1 < K_pad);
+        // x[0]/x[2] real, x[1]/x[3] imaginary parts of columns c, c+1; the
+        // planes in the order written, two consecutive values each
+        uint32_t v0[5], v1[5];
+        int nv;
+        if (!planes6) {
+            v0[0] = hib[0], v1[0] = hib[2];
+            v0[1] = hib[1], v1[1] = hib[3];
+            v0[2] = lob[0], v1[2] = lob[2];
+            v0[3] = lob[1], v1[3] = lob[3];
+            nv = 4;
+        } else {
+            const uint32_t sg = (mode == QCS_MODE_TF32X) ? 0x80000000u : 0x8000u;
+            v0[0] = hib[1] ^ sg, v1[0] = hib[3] ^ sg;
+            v0[1] = hib[0], v1[1] = hib[2];
+            v0[2] = hib[1], v1[2] = hib[3];
+            v0[3] = lob[0], v1[3] = lob[2];
+            v0[4] = lob[1], v1[4] = lob[3];
+            nv = 5;
+        }
+        // plane_stride is even (K_pad is a multiple of 32), so every plane has
+        // the alignment of the first
         if (mode == QCS_MODE_TF32X) {
-            uint32_t *P = static_cast<uint32_t *>(planes);
-            uint32_t *p0 = P + r * pitch + c;
-            // plane order: hi.re, hi.im, lo.re, lo.im; x[0]/x[2] real, x[1]/x[3] imaginary
-            if (two && ((reinterpret_cast<uintptr_t>(p0) & 7u) == 0)) {
-                *reinterpret_cast<uint2 *>(p0) = make_uint2(hib[0], hib[2]);
-                *reinterpret_cast<uint2 *>(p0 + plane_stride) = make_uint2(hib[1], hib[3]);
-                *reinterpret_cast<uint2 *>(p0 + 2 * plane_stride) = make_uint2(lob[0], lob[2]);
-                *reinterpret_cast<uint2 *>(p0 + 3 * plane_stride) = make_uint2(lob[1], lob[3]);
-            } else {
-                p0[0] = hib[0];
-                p0[plane_stride] = hib[1];
-                p0[2 * plane_stride] = lob[0];
-                p0[3 * plane_stride] = lob[1];
-                if (two) {
-                    p0[1] = hib[2];
-                    p0[plane_stride + 1] = hib[3];
-                    p0[2 * plane_stride + 1] = lob[2];
-                    p0[3 * plane_stride + 1] = lob[3];
+            uint32_t *p = static_cast<uint32_t *>(planes) + r * pitch + c;
+            const bool vec = two && ((reinterpret_cast<uintptr_t>(p) & 7u) == 0);
+#pragma unroll
+            for (int pl = 0; pl < 5; ++pl) {
+                if (pl < nv) {
+                    if (vec) {
+                        *reinterpret_cast<uint2 *>(p) = make_uint2(v0[pl], v1[pl]);
+                    } else {
+                        p[0] = v0[pl];
+                        if (two) p[1] = v1[pl];
+                    }
                 }
+                p += plane_stride;
             }
         } else {
-            uint16_t *P = static_cast<uint16_t *>(planes);
-            uint16_t *p0 = P + r * pitch + c;
-            if (two && ((reinterpret_cast<uintptr_t>(p0) & 3u) == 0)) {
-                *reinterpret_cast<uint32_t *>(p0) = hib[0] | (hib[2] << 16);
-                *reinterpret_cast<uint32_t *>(p0 + plane_stride) = hib[1] | (hib[3] << 16);
-                *reinterpret_cast<uint32_t *>(p0 + 2 * plane_stride) = lob[0] | (lob[2] << 16);
-                *reinterpret_cast<uint32_t *>(p0 + 3 * plane_stride) = lob[1] | (lob[3] << 16);
-            } else {
-                p0[0] = (uint16_t)hib[0];
-                p0[plane_stride] = (uint16_t)hib[1];
-                p0[2 * plane_stride] = (uint16_t)lob[0];
-                p0[3 * plane_stride] = (uint16_t)lob[1];
-                if (two) {
-                    p0[1] = (uint16_t)hib[2];
-                    p0[plane_stride + 1] = (uint16_t)hib[3];
-                    p0[2 * plane_stride + 1] = (uint16_t)lob[2];
-                    p0[3 * plane_stride + 1] = (uint16_t)lob[3];
+            uint16_t *p = static_cast<uint16_t *>(planes) + r * pitch + c;
+            const bool vec = two && ((reinterpret_cast<uintptr_t>(p) & 3u) == 0);
+#pragma unroll
+            for (int pl = 0; pl < 5; ++pl) {
+                if (pl < nv) {
+                    if (vec) {
+                        *reinterpret_cast<uint32_t *>(p) = v0[pl] | (v1[pl] << 16);
+                    } else {
+                        p[0] = (uint16_t)v0[pl];
+                        if (two) p[1] = (uint16_t)v1[pl];
+                    }
                 }
+                p += plane_stride;
             }
         }
     }
@@ -667,12 +679,13 @@ __global__ void __launch_bounds__(256) split_kernel(
 
 cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
                          int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
-                         void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s) {
+                         void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
+                         int planes6) {
     if (R_pad <= 0 || K_pad <= 0) return cudaSuccess;
     dim3 grid((unsigned)((K_pad + kSplitC - 1) / kSplitC), (unsigned)((R_pad + kSplitR - 1) / kSplitR));
     if (grid.y > 65535u) return cudaErrorInvalidValue;
     split_kernel<<<grid, 256, 0, s>>>(desc, which, X, sr, sc, conj, R, K, R_pad, K_pad, planes,
-                                      pitch, plane_stride);
+                                      pitch, plane_stride, planes6);
     return cudaGetLastError();
 }
 
@@ -720,6 +733,7 @@ struct SplitOut {
     int which;  // 0: op(A), scale sA; 1: op(B), scale sB
     void *planes;
     int64_t plane_stride;
+    int planes6;  // the five-plane op(B) layout of the GEMM path
 };
 
 __device__ __forceinline__ int64_t batch_in(const CopyParams &P) {
@@ -838,18 +852,29 @@ __global__ void __launch_bounds__(256, 6) copy_tiled_kernel(CopyParams P,
                     split_value(mode, scale ? ldexpf(w.x, scale) : w.x, h0, l0);
                     split_value(mode, scale ? ldexpf(w.y, scale) : w.y, h1, l1);
                     const int64_t ps = so.plane_stride;
+                    const uint32_t sg = (mode == QCS_MODE_TF32X) ? 0x80000000u : 0x8000u;
+                    uint32_t v[5];
+                    int nv;
+                    if (so.planes6) {
+                        v[0] = h1 ^ sg;
+                        v[1] = h0;
+                        v[2] = h1;
+                        v[3] = l0;
+                        v[4] = l1;
+                        nv = 5;
+                    } else {
+                        v[0] = h0;
+                        v[1] = h1;
+                        v[2] = l0;
+                        v[3] = l1;
+                        nv = 4;
+                    }
                     if (mode == QCS_MODE_TF32X) {
                         uint32_t *p = static_cast<uint32_t *>(so.planes) + o;
-                        p[0] = h0;
-                        p[ps] = h1;
-                        p[2 * ps] = l0;
-                        p[3 * ps] = l1;
+                        for (int pl = 0; pl < nv; ++pl) p[pl * ps] = v[pl];
                     } else {
                         uint16_t *p = static_cast<uint16_t *>(so.planes) + o;
-                        p[0] = (uint16_t)h0;
-                        p[ps] = (uint16_t)h1;
-                        p[2 * ps] = (uint16_t)l0;
-                        p[3 * ps] = (uint16_t)l1;
+                        for (int pl = 0; pl < nv; ++pl) p[pl * ps] = (uint16_t)v[pl];
                     }
                     continue;
                 }
@@ -1096,14 +1121,14 @@ bool split_gather_supported(int which, int rank, const int64_t *dims, const int6
 cudaError_t launch_split_gather(const qcs_gemm_desc_t *desc, int which, int rank,
                                 const int64_t *dims, const int64_t *strides, const float2 *src,
                                 int64_t rows, void *planes, int64_t pitch, int64_t plane_stride,
-                                cudaStream_t s) {
+                                cudaStream_t s, int planes6) {
     CopyParams P;
     if (!split_gather_params(which, rank, dims, strides, rows, pitch, P))
         return cudaErrorNotSupported;
     const int64_t blocks = finish_tiled(P);
     if (blocks == 0) return cudaSuccess;
     if (blocks > INT32_MAX) return cudaErrorInvalidValue;
-    SplitOut so{desc, which, planes, plane_stride};
+    SplitOut so{desc, which, planes, plane_stride, planes6};
     copy_tiled_kernel<true><<<dim3((unsigned)blocks, 1), 256, 0, s>>>(P, src, nullptr, 0, so);
     return cudaGetLastError();
 }

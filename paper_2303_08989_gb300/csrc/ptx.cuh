@@ -180,6 +180,19 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor of a K-major operand in the 32-byte swizzle
+// layout (rows of 32 bytes, 8-row atoms 256 bytes apart: SBO 256; layout
+// type 6 in bits 61..63, descriptor version bit 46).
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw32(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(256u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)6 << 61;
+    return d;
+}
+
 // Instruction descriptor for kind::f16 / kind::tf32 with FP32 accumulation,
 // both operands K-major.  fmt: 0 FP16, 1 BF16, 2 TF32.
 __host__ __device__ constexpr uint32_t idesc_make(uint32_t fmt, uint32_t M, uint32_t N,

@@ -44,16 +44,17 @@ def h():
 def test_accumulation_rounding(h, mode, drain, capsys):
     """Inside one drain group the sum stays in tensor memory and is truncated
     by the hardware (1 + 0.75 ulp -> 1); across groups it goes through the
-    epilogue's round-to-nearest FP32 adds (-> 1 + 1 ulp)."""
+    epilogue's round-to-nearest FP32 adds (-> 1 + 1 ulp).  A drain setting of
+    d groups 2 d MMA K steps (32 d values of k for FP16, 16 d for TF32)."""
     h.set_drain_stages(drain)
-    k_mma, k_stage = (16, 32) if mode == "fp16x" else (8, 16)
-    k_group = k_stage * drain
+    k_mma = 16 if mode == "fp16x" else 8
+    k_group = 2 * k_mma * drain
     small_a, small_b = 2.0 ** -12, 1.5 * 2.0 ** -12  # product 0.75 ulp(1)
     cases = {
         "within one MMA": ([(0, 1.0, 1.0), (1, small_a, small_b)], 0.0),
-        "across MMAs of one stage": ([(0, 1.0, 1.0), (k_mma, small_a, small_b)], 0.0),
-        "small first, one stage": ([(0, small_a, small_b), (k_mma, 1.0, 1.0)], 0.0),
-        "last stage of the group": ([(0, 1.0, 1.0), (k_group - 1, small_a, small_b)], 0.0),
+        "across MMAs of one group": ([(0, 1.0, 1.0), (k_mma, small_a, small_b)], 0.0),
+        "small first, one group": ([(0, small_a, small_b), (k_mma, 1.0, 1.0)], 0.0),
+        "last K step of the group": ([(0, 1.0, 1.0), (k_group - 1, small_a, small_b)], 0.0),
         "across drain groups": ([(0, 1.0, 1.0), (k_group, small_a, small_b)], ULP1),
         "across drain groups, small first": ([(0, small_a, small_b), (k_group, 1.0, 1.0)], ULP1),
     }
