@@ -24,6 +24,7 @@ Printed JSON line (rank 0): the contract's keys plus
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -161,6 +162,36 @@ def oracle_sample(A_rows_np, B_np, n: int, rows: int):
 # reference arm: the FP64 CPU oracle as it stands
 # ---------------------------------------------------------------------------
 
+TC_SOURCES = ["paper_2303_08989_gb300/csrc/gemm_tc.cu", "paper_2303_08989_gb300/csrc/ptx.cuh",
+              "paper_2303_08989_gb300/csrc/internal.h"]
+TC_TRAFFIC_PROFILE = "profiles/cgemm_tc_fp16x_16384_dram.md"
+
+
+def tc_sources_sha256() -> str:
+    h = hashlib.sha256()
+    for rel in TC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def tc_traffic(mode_used: str, n: int):
+    """DRAM bytes per launch of the tensor-core kernel from the committed ncu
+    capture (read + write), or None when that capture does not describe this
+    launch: another workload, or kernel sources changed since."""
+    if mode_used != "fp16x" or n != 16384:
+        return None
+    try:
+        with open(os.path.join(ROOT, TC_TRAFFIC_PROFILE)) as f:
+            fields = dict(line.strip("- \n").split(": ", 1) for line in f
+                          if line.startswith("- ") and ": " in line)
+        if fields.get("kernel_source_sha256") != tc_sources_sha256():
+            return None
+        return int(fields["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def gemm_config(args, world: int) -> dict:
     """The workload both arms report (the CGEMM-sweep point bench.py times)."""
     n = args.size
@@ -293,7 +324,7 @@ def main():
         achieved = 24.0 * n * n * n / (tc_avg * 1e-3) / 1e12
         peak = sustained * kind_ratio
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": tc_traffic(mode_used, n),
                     "kernel": f"cgemm_tc_kernel ({mode_used}), 3 tensor products per real product",
                     "peak_source": f"{src} bf16 sustained" + (" x TF32/BF16 nominal ratio 1.1/2.25"
                                                               if kind_ratio != 1.0 else "")}

@@ -129,6 +129,15 @@ int qcs_set_size_rule(qcs_handle_t h, int rule);
  * faster and slightly less accurate. */
 int qcs_set_drain_stages(qcs_handle_t h, int stages);
 
+/* Schedule of the tensor-core kernels (a performance knob; results do not
+ * depend on it): output tiles are processed in a raster of groups of
+ * ``group_m`` tile rows (1 to 1024; default 8), column after column inside a
+ * group, so that tiles in flight share operand panels in L2; the split
+ * planes are loaded with an L2 promotion of ``l2_promotion`` bytes (0, 64,
+ * 128 or 256; default 256).  Environment overrides QCS_TC_GROUP_M and
+ * QCS_TC_L2_PROMOTION. */
+int qcs_set_tc_schedule(qcs_handle_t h, int group_m, int l2_promotion);
+
 /* Exponent statistics (Section 4.1, Stage 1 and Stage 2 in one pass) of the
  * rows x cols complex matrix X (device, leading dim ldx >= rows), written
  * to d_stats (device, caller-owned).  rows or cols may be 0. */

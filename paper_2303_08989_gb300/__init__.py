@@ -147,6 +147,12 @@ class Handle:
         _lib.check(self.lib.qcs_set_instance_batch(self._h, int(instances)), "qcs_set_instance_batch")
         self.instance_batch = int(instances)
 
+    def set_tc_schedule(self, group_m: int = 8, l2_promotion: int = 256):
+        """Raster group and L2 promotion of the tensor-core kernels
+        (qcs_set_tc_schedule); a performance knob only."""
+        _lib.check(self.lib.qcs_set_tc_schedule(self._h, int(group_m), int(l2_promotion)),
+                   "qcs_set_tc_schedule")
+
     def set_drain_stages(self, stages: int):
         _lib.check(self.lib.qcs_set_drain_stages(self._h, int(stages)), "qcs_set_drain_stages")
         self.drain_stages = int(stages)

@@ -33,7 +33,7 @@ EXPORTED = [
     "qcs_contract_tree_backward", "qcs_set_profiling", "qcs_get_profile", "qcs_sync",
     "qcs_status_string", "qcs_cgemm_noalloc", "qcs_tree_graph_create", "qcs_tree_graph_launch",
     "qcs_tree_graph_destroy", "qcs_get_auto_counts", "qcs_autotune_gemm", "qcs_autotune_tree",
-    "qcs_get_tuning", "qcs_set_tuning", "qcs_set_instance_batch",
+    "qcs_get_tuning", "qcs_set_tuning", "qcs_set_instance_batch", "qcs_set_tc_schedule",
 ]
 SIZE_RULE_OFF, SIZE_RULE_PAPER, SIZE_RULE_TUNED = 0, 1, 2
 NUM_MODES = 6
@@ -146,6 +146,7 @@ def load(path: str = LIB_PATH):
         "qcs_get_tuning": [H, ctypes.POINTER(qcs_tune_entry_t), I64, ctypes.POINTER(I64)],
         "qcs_set_tuning": [H, ctypes.POINTER(qcs_tune_entry_t), I64],
         "qcs_set_instance_batch": [H, I],
+        "qcs_set_tc_schedule": [H, I, I],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

@@ -106,9 +106,14 @@ int encode_planes(qcs_handle_t h, CUtensorMap *map, void *base, int64_t R_pad, i
     cuuint64_t gstride[2] = {(cuuint64_t)(K_pad * esz), (cuuint64_t)(K_pad * R_pad * esz)};
     cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)kBM, (cuuint32_t)nplanes};
     cuuint32_t estride[3] = {1, 1, 1};
+    const CUtensorMapL2promotion promo =
+        h->tc_l2_promotion >= 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
+        : h->tc_l2_promotion >= 128 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+        : h->tc_l2_promotion >= 64  ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B
+                                    : CU_TENSOR_MAP_L2_PROMOTION_NONE;
     CUresult r = h->encode(map, dt, 3, base, gdim, gstride, box, estride,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, promo,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? QCS_SUCCESS : QCS_ERR_CUDA;
 }
 
@@ -296,7 +301,7 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                     return QCS_ERR_CUDA;
                 const int kind = (eff == QCS_MODE_BF16X3) ? 2 : 0;
                 e = launch_cgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
-                                    ldc, h->d_err, h->num_sms, s);
+                                    ldc, h->d_err, h->num_sms, h->tc_group_m, s);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             }
             if (need32) {
@@ -305,7 +310,7 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                     encode_planes(h, &mb, planesB, np, kp, 4, kPlanesB))
                     return QCS_ERR_CUDA;
                 e = launch_cgemm_tc(1, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
-                                    ldc, h->d_err, h->num_sms, s);
+                                    ldc, h->d_err, h->num_sms, h->tc_group_m, s);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             }
         }
@@ -393,6 +398,8 @@ int qcs_create(qcs_handle_t *out, void *cuda_stream) {
         const int v = std::atoi(r);
         h->size_rule = (v == QCS_SIZE_RULE_OFF || v == QCS_SIZE_RULE_TUNED) ? v : QCS_SIZE_RULE_PAPER;
     }
+    if (const char *g = std::getenv("QCS_TC_GROUP_M")) h->tc_group_m = std::max(1, std::atoi(g));
+    if (const char *p = std::getenv("QCS_TC_L2_PROMOTION")) h->tc_l2_promotion = std::atoi(p);
     if (const char *d = std::getenv("QCS_DRAIN_STAGES")) {
         const int v = std::atoi(d);
         h->drain_stages = (v >= 4) ? 4 : (v == 2 ? 2 : 1);
@@ -431,6 +438,15 @@ int qcs_set_underflow_tol(qcs_handle_t h, double t) {
 int qcs_set_drain_stages(qcs_handle_t h, int stages) {
     if (!h || (stages != 1 && stages != 2 && stages != 4)) return QCS_ERR_INVALID_ARG;
     h->drain_stages = stages;
+    return QCS_SUCCESS;
+}
+
+int qcs_set_tc_schedule(qcs_handle_t h, int group_m, int l2_promotion) {
+    if (!h || group_m < 1 || group_m > 1024 ||
+        (l2_promotion != 0 && l2_promotion != 64 && l2_promotion != 128 && l2_promotion != 256))
+        return QCS_ERR_INVALID_ARG;
+    h->tc_group_m = group_m;
+    h->tc_l2_promotion = l2_promotion;
     return QCS_SUCCESS;
 }
 

@@ -59,7 +59,6 @@ namespace qcs {
 
 namespace {
 
-constexpr int kGroupM = 8;        // tile rows per raster group (L2 reuse of B panels)
 constexpr int kEpiWarps = 8;
 constexpr int kEpiCols = kBN / 2;  // columns per epilogue warp
 
@@ -74,11 +73,14 @@ struct TcSmem {
     int abort;
 };
 
-__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int &tm, int &tn) {
-    const int per_group = kGroupM * tiles_n;
+// Tile t of the raster: groups of group_m tile rows, column after column
+// inside a group, so that the tiles in flight share A and B panels in L2.
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int group_m, int &tm,
+                                            int &tn) {
+    const int per_group = group_m * tiles_n;
     const int g = t / per_group;
-    const int first_m = g * kGroupM;
-    const int gsize = min(tiles_m - first_m, kGroupM);
+    const int first_m = g * group_m;
+    const int gsize = min(tiles_m - first_m, group_m);
     const int r = t - g * per_group;
     tm = first_m + r % gsize;
     tn = r / gsize;
@@ -109,7 +111,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                     const __grid_constant__ CUtensorMap mapB,
                     const qcs_gemm_desc_t *__restrict__ desc, int m, int n, int k_pad,
-                    float2 alpha, float2 beta, float2 *__restrict__ C, int64_t ldc, int *d_err) {
+                    float2 alpha, float2 beta, float2 *__restrict__ C, int64_t ldc, int *d_err,
+                    int group_m) {
     const int mode = desc->mode;
     if (!kind_runs(KIND, mode)) return;  // not selected: exit before touching anything
     const int sA = desc->sA, sB = desc->sB;
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
                 int tm, tn;
-                tile_coords(t, tiles_m, tiles_n, tm, tn);
+                tile_coords(t, tiles_m, tiles_n, group_m, tm, tn);
                 for (int kb = 0; kb < num_kb; ++kb) {
                     if (!mbar_wait(&S.empty[stage], phase ^ 1u, globaltimer_ns() + kWaitBudgetNs,
                                    abort_flag)) {
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         bool ok = true;
         for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
             int tm, tn;
-            tile_coords(t, tiles_m, tiles_n, tm, tn);
+            tile_coords(t, tiles_m, tiles_n, group_m, tm, tn);
             float racc[kEpiCols], iacc[kEpiCols];
 #pragma unroll
             for (int j = 0; j < kEpiCols; ++j) racc[j] = iacc[j] = 0.0f;
@@ -388,7 +391,7 @@ template <int KIND, int DRAIN>
 cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
                         const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad, float2 alpha,
                         float2 beta, float2 *C, int64_t ldc, int *d_err, int num_sms,
-                        cudaStream_t s) {
+                        int group_m, cudaStream_t s) {
     const size_t smem = sizeof(TcSmem) + 1024;
     static bool configured = false;
     if (!configured) {
@@ -401,7 +404,8 @@ cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
     if (tiles == 0 || k_pad == 0) return cudaSuccess;
     const int grid = static_cast<int>(tiles < num_sms ? tiles : num_sms);
     cgemm_tc_kernel<KIND, DRAIN><<<grid, kTcThreads, smem, s>>>(
-        *mapA, *mapB, desc, (int)m, (int)n, (int)k_pad, alpha, beta, C, ldc, d_err);
+        *mapA, *mapB, desc, (int)m, (int)n, (int)k_pad, alpha, beta, C, ldc, d_err,
+        group_m < 1 ? 1 : group_m);
     return cudaGetLastError();
 }
 
@@ -411,15 +415,15 @@ template <int KIND>
 cudaError_t launch_drain(int drain, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
                          const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad,
                          float2 alpha, float2 beta, float2 *C, int64_t ldc, int *d_err,
-                         int num_sms, cudaStream_t s) {
+                         int num_sms, int group_m, cudaStream_t s) {
     if (drain >= 4)
         return launch_kind<KIND, 4>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                    num_sms, s);
+                                    num_sms, group_m, s);
     if (drain == 2)
         return launch_kind<KIND, 2>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                    num_sms, s);
+                                    num_sms, group_m, s);
     return launch_kind<KIND, 1>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                num_sms, s);
+                                num_sms, group_m, s);
 }
 
 }  // namespace
@@ -427,17 +431,17 @@ cudaError_t launch_drain(int drain, const qcs_gemm_desc_t *desc, const CUtensorM
 cudaError_t launch_cgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
                             const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
                             int64_t n, int64_t k_pad, float2 alpha, float2 beta, float2 *C,
-                            int64_t ldc, int *d_err, int num_sms, cudaStream_t s) {
+                            int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s) {
     switch (kind) {
         case 0:
             return launch_drain<0>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                   d_err, num_sms, s);
+                                   d_err, num_sms, group_m, s);
         case 1:
             return launch_drain<1>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                   d_err, num_sms, s);
+                                   d_err, num_sms, group_m, s);
         default:
             return launch_drain<2>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                   d_err, num_sms, s);
+                                   d_err, num_sms, group_m, s);
     }
 }
 

@@ -91,6 +91,8 @@ struct qcs_handle_s {
     int size_rule = 1;
     int drain_stages = 4;            // stages per RN drain of the tensor-core hi*hi sum
     int instance_batch = 1;          // contraction-tree instances per group (forward)
+    int tc_group_m = 8;              // tensor-core raster: tile rows per group
+    int tc_l2_promotion = 256;       // L2 promotion of the plane loads (bytes; 0 = none)
     int *d_err = nullptr;            // device error word (start of a 64-byte block)
     unsigned long long *d_counts = nullptr;  // in that block: AUTO selections per mode, flops
     qcs::Workspace ws;               // GEMM workspace (planes, partials, descriptor)
@@ -256,6 +258,6 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
 cudaError_t launch_cgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
                             const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
                             int64_t n, int64_t k_pad, float2 alpha, float2 beta, float2 *C,
-                            int64_t ldc, int *d_err, int num_sms, cudaStream_t s);
+                            int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s);
 
 }  // namespace qcs

@@ -1438,6 +1438,60 @@ __global__ void __launch_bounds__(256) cgemm_skinny_rows_kernel(
     }
 }
 
+// (2, n, 2) with op(B) = B stored 2 x n contiguous and C 2 x n contiguous
+// (the (2, 2^N, 2) shape of Section 5.1.2): a thread per column, one 16-byte
+// load of B's column and one 16-byte store of C's, four columns in flight.
+__global__ void __launch_bounds__(256) cgemm_2x2_cols_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int opA, const float2 *__restrict__ A, int64_t lda,
+    const float4 *__restrict__ B, float4 *__restrict__ C, int64_t n, float2 alpha, float2 beta,
+    GemmBatch bt) {
+    if (desc && desc->mode != QCS_MODE_FP32) return;
+    A += blockIdx.y * bt.sA;
+    B += blockIdx.y * (bt.sB >> 1);
+    C += blockIdx.y * (bt.sC >> 1);
+    const float2 a00 = ld_op(A, opA, 0, 0, lda), a01 = ld_op(A, opA, 0, 1, lda);
+    const float2 a10 = ld_op(A, opA, 1, 0, lda), a11 = ld_op(A, opA, 1, 1, lda);
+    const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
+    constexpr int U = 4;
+    const int64_t S = (int64_t)gridDim.x * blockDim.x;
+    auto cmul_add = [](float2 a, float2 b, float2 c, float2 d) {  // a b + c d
+        float2 r;
+        r.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, fmaf(c.x, d.x, -c.y * d.y)));
+        r.y = fmaf(a.x, b.y, fmaf(a.y, b.x, fmaf(c.x, d.y, c.y * d.x)));
+        return r;
+    };
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j0 < n; j0 += U * S) {
+        float4 b[U], cold[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t j = j0 + u * S;
+            if (j < n) {
+                b[u] = __ldcs(B + j);
+                if (use_beta) cold[u] = C[j];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t j = j0 + u * S;
+            if (j >= n) continue;
+            const float2 b0 = make_float2(b[u].x, b[u].y), b1 = make_float2(b[u].z, b[u].w);
+            const float2 s0 = cmul_add(a00, b0, a01, b1), s1 = cmul_add(a10, b0, a11, b1);
+            float4 o;
+            o.x = alpha.x * s0.x - alpha.y * s0.y;
+            o.y = alpha.x * s0.y + alpha.y * s0.x;
+            o.z = alpha.x * s1.x - alpha.y * s1.y;
+            o.w = alpha.x * s1.y + alpha.y * s1.x;
+            if (use_beta) {
+                o.x += beta.x * cold[u].x - beta.y * cold[u].y;
+                o.y += beta.x * cold[u].y + beta.y * cold[u].x;
+                o.z += beta.x * cold[u].z - beta.y * cold[u].w;
+                o.w += beta.x * cold[u].w + beta.y * cold[u].z;
+            }
+            __stcs(C + j, o);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) cgemm_skinny_cols_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int k,
     int lg_m2, float2 alpha, const float2 *__restrict__ A, int64_t lda, const float2 *__restrict__ B,
@@ -1638,6 +1692,14 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
             else
                 cgemm_skinny_rows_kernel<16><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, kk, alpha, A,
                                                                  lda, B, ldb, beta, C, ldc, bt);
+        } else if (m == 2 && k == 2 && opB == QCS_OP_N && ldb == 2 && ldc == 2 &&
+                   ((reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(C)) & 15u) == 0 &&
+                   (bt.sB % 2) == 0 && (bt.sC % 2) == 0) {
+            const int64_t blocks = (n + 4 * 256 - 1) / (4 * 256);
+            const dim3 grid((unsigned)(blocks < 65536 ? blocks : 65536), G);
+            cgemm_2x2_cols_kernel<<<grid, 256, 0, s>>>(
+                desc, opA, A, lda, reinterpret_cast<const float4 *>(B), reinterpret_cast<float4 *>(C),
+                n, alpha, beta, bt);
         } else {  // m <= 16: a thread per element, rows in the low bits
             int lg = 0;
             while ((int64_t(1) << lg) < m) ++lg;

@@ -281,3 +281,27 @@ def test_cgemm_fp32_skinny_and_per_element_shapes(h, m, n, k, opA, opB):
     bound = (2 * k + 8) * 2.0 ** -24 * (abs(alpha) * 2 * abs_bound(A, B, opA, opB, m, k, n)
                                         + abs(beta) * 2 * np.abs(C0[:m, :n]))
     assert np.all(np.abs(got - ref) <= bound + 1e-30)
+
+
+@pytest.mark.parametrize("n", [1, 7, 5000, 65539])
+@pytest.mark.parametrize("opA", [0, 1, 2])
+def test_cgemm_fp32_two_by_n_columns(h, n, opA):
+    """The (2, 2^N, 2) shape of Section 5.1.2 with B and C stored contiguous
+    (a column of each is 16 bytes): the column-vector kernel."""
+    m, k = 2, 2
+    A = _operands(m, n, k, opA, 0, 3, seed=(n, opA, 1))[0]
+    B = qi.cgemm_operand(k, n, 3, seed=(n, opA, 2))
+    C0 = qi.cgemm_operand(m, n, 0, seed=(n, 6))
+    alpha, beta = 0.5 + 0.25j, -1.0 + 0.5j
+    q = lib()
+    Cd = dev(C0)
+    assert Cd.stride(1) == 2
+    q.cgemm(h, dev(A)[:(m if opA == 0 else k)], dev(B), Cd, m=m, n=n, k=k, alpha=alpha,
+            beta=beta, opA=opA, mode="fp32")
+    torch.cuda.synchronize()
+    h.sync()
+    got = host(Cd).astype(np.complex128)
+    ref = oracle.cgemm(opA, 0, m, n, k, alpha, A, B, beta, C0)
+    bound = (2 * k + 8) * 2.0 ** -24 * (abs(alpha) * 2 * abs_bound(A, B, opA, 0, m, k, n)
+                                        + abs(beta) * 2 * np.abs(C0[:m, :n]))
+    assert np.all(np.abs(got - ref) <= bound + 1e-30)
