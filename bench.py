@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-tree", action="store_true", help="skip the contraction-tree legs")
     p.add_argument("--tree-slices", type=int, default=4,
                    help="slices of the 30-qubit network timed per mode")
+    p.add_argument("--no-sweep", action="store_true", help="skip the CGEMM-sweep leg")
+    p.add_argument("--sweep-sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192, 16384])
     p.add_argument("--instance-batch", type=int, default=4,
                    help="contraction instances per group (plain-FP32 steps batched)")
     return p.parse_args()
@@ -491,6 +493,8 @@ def main():
 
     if not args.no_extras:
         out["hbm_kernels"] = hbm_legs(q, torch, dev, h, stages, n)
+    if not args.no_extras and not args.no_sweep:
+        out["sweep"] = sweep_leg(args, q, torch, dev, rank)
 
     if not args.no_tree:
         out.update(tree_legs(args, q, torch, dev, rank))
@@ -561,6 +565,94 @@ def hbm_legs(q, torch, dev, h, stages, n):
     ms = timed(lambda: q.cgemm(h, A2, B2, C2, mode="fp32"))
     res["skinny_Nx2x2"] = entry(8 * (N * 2 + 4 + N * 2), ms)
     return res
+
+
+def _finite_or_none(x: float):
+    import math
+
+    return x if math.isfinite(x) else None
+
+
+def sweep_leg(args, q, torch, dev, rank):
+    """The whole CGEMM sweep: m = n = k in ``args.sweep_sizes``, parts
+    N(0,1) 2^e with e ~ U_int[-s, s] for s in {0, 8, 20, 40}; per point the
+    TFLOP/s of FP32 (SIMT), TF32X, FP16X, FP16X_SCALED and AUTO-t (t =
+    ``args.tol``, the paper's size rule on) forced on the same inputs, cuBLAS
+    CGEMM (torch, default math mode), the relative Frobenius error of each
+    against the FP64 oracle on ``args.sample_rows`` output rows, and the mode
+    the device-side selection picks at t in {0, 1e-3, 0.1, 0.5} (statistics
+    and selection alone, no size rule)."""
+    import numpy as np
+
+    import oracle
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        # one untimed call, then enough calls for ~0.2 s (at least 2)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        first = e0.elapsed_time(e1)
+        reps = int(max(2, min(50, 200.0 / max(first, 1e-3))))
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    h = q.Handle(tol=args.tol, size_rule=True)
+    hsel = q.Handle(tol=0.0, size_rule=False)
+    rows = args.sample_rows
+    points = []
+    for n in args.sweep_sizes:
+        flops = 8.0 * n * n * n
+        for s in (0, 8, 20, 40):
+            A = make_operand(torch, n, s, 31 * n + s, dev)
+            B = make_operand(torch, n, s, 37 * n + s, dev)
+            C = q.fortran_empty(n, n, device=dev)
+            pt = {"size": n, "s": s, "modes": {}}
+            ref = None
+            if rank == 0:
+                _, ref, _ = oracle_sample(A[:rows].cpu().numpy().astype(np.complex64),
+                                          B.cpu().numpy(), n, rows)
+            desc = torch.zeros(4, dtype=torch.int32, device=dev)
+            for mode in ("fp32", "tf32x", "fp16x", "fp16x_scaled", "auto"):
+                ms = timed(lambda: q.cgemm(h, A, B, C, mode=mode))
+                entry = {"tflops": flops / (ms * 1e-3) / 1e12, "ms": ms}
+                if mode == "auto":
+                    q.cgemm(h, A, B, C, mode=mode, desc_out=desc)
+                    entry["selected"] = q.MODE_NAME[int(desc[0].item())]
+                if rank == 0:
+                    got = C[:rows].cpu().numpy().astype(np.complex128)
+                    entry["rel_fro_vs_fp64"] = (_finite_or_none(oracle.rel_fro_error(got, ref))
+                                                if np.isfinite(got).all() else None)
+                pt["modes"][mode] = entry
+            ms = timed(lambda: torch.matmul(A, B))
+            pt["cublas_cgemm_tflops"] = flops / (ms * 1e-3) / 1e12
+            sA, sB = q.exp_stats(hsel, A), q.exp_stats(hsel, B)
+            picks = {}
+            for t in (0.0, 1e-3, 0.1, 0.5):
+                hsel.set_tol(t)
+                picks[f"{t:g}"] = q.MODE_NAME[int(q.select(hsel, sA, sB)[0].item())]
+            pt["auto_pick_by_tol"] = picks
+            fp32 = pt["modes"]["fp32"]
+            auto = pt["modes"]["auto"]
+            pt["auto_speedup_vs_fp32"] = auto["tflops"] / fp32["tflops"]
+            if auto.get("rel_fro_vs_fp64") is not None and fp32.get("rel_fro_vs_fp64"):
+                pt["auto_err_ratio_vs_fp32"] = auto["rel_fro_vs_fp64"] / fp32["rel_fro_vs_fp64"]
+            points.append(pt)
+            del A, B, C
+            torch.cuda.empty_cache()
+    h.close()
+    hsel.close()
+    return {"workload": "CGEMM m=n=k, column-major, alpha=1, beta=0; parts N(0,1)*2^e, "
+                        "e~U_int[-s,s] per real scalar; forced modes and AUTO-"
+                        f"{args.tol:g} with the paper's size rule",
+            "error_sample": f"{rows} output rows vs the FP64 oracle",
+            "points": points}
 
 
 MODE_KEYS = ["auto", "fp16x", "fp16x_scaled", "tf32x", "fp32", "bf16x3"]

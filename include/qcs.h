@@ -138,6 +138,20 @@ int qcs_set_drain_stages(qcs_handle_t h, int stages);
  * QCS_TC_L2_PROMOTION. */
 int qcs_set_tc_schedule(qcs_handle_t h, int group_m, int l2_promotion);
 
+/* K ranges of the tensor-core kernels.  A GEMM with few 128 x 128 output
+ * tiles for its K (for example m = n = 1024: 64 tiles on 152 SMs) leaves
+ * SMs idle; its K loop can be cut into ``splits`` equal ranges that run as
+ * separate work units.  Each range writes its partial product (FP32, in the
+ * handle's workspace: splits x m x n complex) and one more kernel adds the
+ * ranges in a fixed order and applies alpha and beta, so results are
+ * deterministic but differ from the unsplit GEMM by FP32 rounding of the
+ * partial sums.  ``splits`` = 0 (default) chooses the count per shape from
+ * the number of tile waves and the partials' memory traffic; 1 to 16 forces
+ * it (at most one range per 32 k).  Environment override QCS_TC_SPLITS.
+ * This is a schedule of Section 2.1's emulation, not a step of the paper.
+ * Returns QCS_ERR_INVALID_ARG for other values. */
+int qcs_set_tc_splits(qcs_handle_t h, int splits);
+
 /* Exponent statistics (Section 4.1, Stage 1 and Stage 2 in one pass) of the
  * rows x cols complex matrix X (device, leading dim ldx >= rows), written
  * to d_stats (device, caller-owned).  rows or cols may be 0. */

@@ -153,6 +153,11 @@ class Handle:
         _lib.check(self.lib.qcs_set_tc_schedule(self._h, int(group_m), int(l2_promotion)),
                    "qcs_set_tc_schedule")
 
+    def set_tc_splits(self, splits: int = 0):
+        """K ranges per tensor-core GEMM (qcs_set_tc_splits): 0 chooses per
+        shape, 1..16 forces the count."""
+        _lib.check(self.lib.qcs_set_tc_splits(self._h, int(splits)), "qcs_set_tc_splits")
+
     def set_drain_stages(self, stages: int):
         _lib.check(self.lib.qcs_set_drain_stages(self._h, int(stages)), "qcs_set_drain_stages")
         self.drain_stages = int(stages)

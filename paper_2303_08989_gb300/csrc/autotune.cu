@@ -61,7 +61,7 @@ int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k
     const int64_t ra = (opA == QCS_OP_N) ? m : k, ca = (opA == QCS_OP_N) ? k : m;
     const int64_t rb = (opB == QCS_OP_N) ? k : n, cb = (opB == QCS_OP_N) ? n : k;
     size_t ws = 0;
-    for (int c : kCandidates) ws = std::max(ws, gemm_workspace_bytes(c, m, n, k, h->num_sms));
+    for (int c : kCandidates) ws = std::max(ws, gemm_workspace_bytes(c, m, n, k, h->num_sms, h->tc_splits));
     if (int r = ensure_workspace(h->ws, ws)) return r;
     DeviceBuffer A, B, C;
     if (cudaMalloc(&A.p, sizeof(float2) * ra * ca) != cudaSuccess ||

@@ -151,7 +151,7 @@ int qcs::effective_mode(qcs_handle_t h, int mode, int opA, int opB, int64_t m, i
 // come from ``ws`` (a device buffer of at least gemm_workspace_bytes()).
 namespace qcs {
 
-size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms) {
+size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits) {
     size_t bytes = 256;  // descriptor
     bytes += align256(size_t(2) * num_sms * kPartialStride * sizeof(int64_t));
     bytes += align256(kSplitKBytes);
@@ -160,6 +160,8 @@ size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sm
         const int64_t kp = round_up(k, 32), mp = round_up(m, kBM), np = round_up(n, kBN);
         bytes += align256(size_t(kPlanes) * mp * kp * esz);
         bytes += align256(size_t(kPlanesB) * np * kp * esz);
+        const int S = tc_split_count(m, n, k, 1, num_sms, splits);
+        if (S > 1) bytes += align256(sizeof(float2) * S * m * n);  // K-range partials
     }
     return bytes;
 }
@@ -267,6 +269,11 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
         const int esz_max = need32 ? 4 : 2;
         uint8_t *planesA = p;
         uint8_t *planesB = p + align256(size_t(kPlanes) * mp * kp * esz_max);
+        TcWork w;
+        w.S = tc_split_count(m, n, k, 1, h->num_sms, h->tc_splits);
+        if (w.S > 1)
+            w.P = reinterpret_cast<float2 *>(planesB +
+                                             align256(size_t(kPlanesB) * np * kp * esz_max));
         int64_t sr, sc;
         // The split writes with the selected kind's element size; the pitch is
         // kp elements either way, so both tensor maps below describe it.
@@ -301,7 +308,7 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                     return QCS_ERR_CUDA;
                 const int kind = (eff == QCS_MODE_BF16X3) ? 2 : 0;
                 e = launch_cgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
-                                    ldc, h->d_err, h->num_sms, h->tc_group_m, s);
+                                    ldc, h->d_err, h->num_sms, h->tc_group_m, s, w);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             }
             if (need32) {
@@ -310,9 +317,11 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                     encode_planes(h, &mb, planesB, np, kp, 4, kPlanesB))
                     return QCS_ERR_CUDA;
                 e = launch_cgemm_tc(1, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
-                                    ldc, h->d_err, h->num_sms, h->tc_group_m, s);
+                                    ldc, h->d_err, h->num_sms, h->tc_group_m, s, w);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             }
+            e = launch_tc_reduce(desc, m, n, alpha, beta, C, ldc, h->num_sms, w, s);
+            if (e != cudaSuccess) return QCS_ERR_CUDA;
         }
         if (eff == QCS_MODE_AUTO) {
             // the FP32 candidate: mapped operands are gathered only if it was selected
@@ -400,6 +409,8 @@ int qcs_create(qcs_handle_t *out, void *cuda_stream) {
     }
     if (const char *g = std::getenv("QCS_TC_GROUP_M")) h->tc_group_m = std::max(1, std::atoi(g));
     if (const char *p = std::getenv("QCS_TC_L2_PROMOTION")) h->tc_l2_promotion = std::atoi(p);
+    if (const char *k = std::getenv("QCS_TC_SPLITS"))
+        h->tc_splits = std::min(kMaxSplits, std::max(0, std::atoi(k)));
     if (const char *d = std::getenv("QCS_DRAIN_STAGES")) {
         const int v = std::atoi(d);
         h->drain_stages = (v >= 4) ? 4 : (v == 2 ? 2 : 1);
@@ -450,6 +461,12 @@ int qcs_set_tc_schedule(qcs_handle_t h, int group_m, int l2_promotion) {
     return QCS_SUCCESS;
 }
 
+int qcs_set_tc_splits(qcs_handle_t h, int splits) {
+    if (!h || splits < 0 || splits > kMaxSplits) return QCS_ERR_INVALID_ARG;
+    h->tc_splits = splits;
+    return QCS_SUCCESS;
+}
+
 int qcs_set_instance_batch(qcs_handle_t h, int instances) {
     if (!h || instances < 1 || instances > 65535) return QCS_ERR_INVALID_ARG;
     h->instance_batch = instances;
@@ -495,7 +512,8 @@ int qcs_cgemm(qcs_handle_t h, qcs_mode_t mode, qcs_op_t transA, qcs_op_t transB,
     if (m == 0 || n == 0) return QCS_SUCCESS;
     if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) return QCS_ERR_UNSUPPORTED;
     const int eff = effective_mode(h, mode, transA, transB, m, n, k);
-    if (int r = ensure_workspace(h->ws, gemm_workspace_bytes(eff, m, n, k, h->num_sms))) return r;
+    if (int r = ensure_workspace(h->ws, gemm_workspace_bytes(eff, m, n, k, h->num_sms, h->tc_splits)))
+        return r;
     const float2 al = make_float2(alpha->x, alpha->y), be = make_float2(beta->x, beta->y);
     return run_cgemm(h, h->ws.ptr, eff, transA, transB, m, n, k, al,
                      reinterpret_cast<const float2 *>(A), lda, reinterpret_cast<const float2 *>(B),

@@ -208,15 +208,15 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
         maxB = std::max(maxB, st.k * st.n * gb);
         // a batched plain-FP32 GEMM keeps a split-K partial buffer per instance,
         // at the end of its workspace
-        gemm = std::max(gemm, gemm_workspace_bytes(L.eff[s], st.m, st.n, st.k, h->num_sms) +
+        gemm = std::max(gemm, gemm_workspace_bytes(L.eff[s], st.m, st.n, st.k, h->num_sms, h->tc_splits) +
                                   (size_t)(gb - 1) * kSplitKBytes);
         if (backward) {
             gemm = std::max(gemm, gemm_workspace_bytes(effective_mode(h, st.mode, QCS_OP_N,
                                                                       QCS_OP_C, st.m, st.k, st.n),
-                                                       st.m, st.k, st.n, h->num_sms));
+                                                       st.m, st.k, st.n, h->num_sms, h->tc_splits));
             gemm = std::max(gemm, gemm_workspace_bytes(effective_mode(h, st.mode, QCS_OP_C,
                                                                       QCS_OP_N, st.k, st.n, st.m),
-                                                       st.k, st.n, st.m, h->num_sms));
+                                                       st.k, st.n, st.m, h->num_sms, h->tc_splits));
         }
     }
     L.inter_off.resize(ns);

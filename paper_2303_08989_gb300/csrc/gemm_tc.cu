@@ -50,6 +50,17 @@
 // The descriptor the selector wrote decides at run time whether this
 // instantiation runs at all (the "launch all candidates, the unselected one
 // exits" scheme of Section 4.2).
+//
+// Work units.  One launch covers G equal-shape GEMMs (a group of
+// contraction instances: instance g has its own planes, descriptor and
+// output) and splits each GEMM's K loop into S equal ranges; a unit is
+// (instance, K range, output tile) and the persistent CTAs walk the units in
+// that order, tiles fastest.  Units of an instance whose descriptor selected
+// another kind are skipped.  With S > 1 a unit writes its scaled partial
+// 2^-(sA+sB) (acc0 + 2^-11 acc1) to a partial buffer and tc_splitk_reduce
+// forms C = alpha sum_s P_s + beta C, summing the ranges in a fixed order,
+// so the result does not depend on scheduling.  Splitting K fills the SMs
+// when a GEMM has few output tiles for its K (1024^3: 64 tiles on 152 SMs).
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -106,16 +117,28 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
         mma_f16(d, a, b, idesc, acc);
 }
 
+// Unit u of a launch: instance g, K range r (of S), tile t (of tiles).
+struct Unit {
+    int g, r, t;
+};
+__device__ __forceinline__ Unit unit_of(int u, int tiles, int S) {
+    Unit x;
+    x.t = u % tiles;
+    const int q = u / tiles;
+    x.r = q % S;
+    x.g = q / S;
+    return x;
+}
+
 template <int KIND, int DRAIN>
 __global__ void __launch_bounds__(kTcThreads, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                     const __grid_constant__ CUtensorMap mapB,
                     const qcs_gemm_desc_t *__restrict__ desc, int m, int n, int k_pad,
                     float2 alpha, float2 beta, float2 *__restrict__ C, int64_t ldc, int *d_err,
-                    int group_m) {
-    const int mode = desc->mode;
-    if (!kind_runs(KIND, mode)) return;  // not selected: exit before touching anything
-    const int sA = desc->sA, sB = desc->sB;
+                    int group_m, const TcWork w) {
+    // a single GEMM that did not select this kind exits before touching anything
+    if (w.G == 1 && !kind_runs(KIND, desc->mode)) return;
 
     extern __shared__ uint8_t smem_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(
@@ -150,9 +173,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int tiles_m = (m + kBM - 1) / kBM;
     const int tiles_n = (n + kBN - 1) / kBN;
     const int num_tiles = tiles_m * tiles_n;
+    const int num_units = w.G * w.S * num_tiles;
     constexpr int kElemBytes = (KIND == 1) ? 4 : 2;
     constexpr int kKPerStage = kRowBytes / kElemBytes;  // two MMA K steps: 32 (16-bit) or 16 (TF32)
     const int num_kb = k_pad / kKPerStage;
+    // stages [kb_begin(r), kb_begin(r + 1)) of K range r; S <= num_kb, so none is empty
+    auto kb_begin = [&](int r) { return static_cast<int>((int64_t)r * num_kb / w.S); };
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -161,10 +187,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             uint32_t phase = 0;
             int issued = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+            for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+                const Unit x = unit_of(u, num_tiles, w.S);
+                if (w.G > 1 && !kind_runs(KIND, desc[x.g].mode)) continue;
                 int tm, tn;
-                tile_coords(t, tiles_m, tiles_n, group_m, tm, tn);
-                for (int kb = 0; kb < num_kb; ++kb) {
+                tile_coords(x.t, tiles_m, tiles_n, group_m, tm, tn);
+                const int rowA = static_cast<int>(x.g * w.a_rows) + tm * kBM;
+                const int rowB = static_cast<int>(x.g * w.b_rows) + tn * kBN;
+                const int kb1 = kb_begin(x.r + 1);
+                for (int kb = kb_begin(x.r); kb < kb1; ++kb) {
                     if (!mbar_wait(&S.empty[stage], phase ^ 1u, globaltimer_ns() + kWaitBudgetNs,
                                    abort_flag)) {
                         if (!*abort_flag) raise_abort(S, d_err, kErrTimeoutProducer);
@@ -172,9 +203,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         break;
                     }
                     mbar_arrive_expect_tx(&S.full[stage], kStageBytes);
-                    tma_load_3d(S.stage[stage], &mapA, &S.full[stage], kb * kKPerStage, tm * kBM, 0);
+                    tma_load_3d(S.stage[stage], &mapA, &S.full[stage], kb * kKPerStage, rowA, 0);
                     tma_load_3d(S.stage[stage] + kAStageBytes, &mapB, &S.full[stage],
-                                kb * kKPerStage, tn * kBN, 0);
+                                kb * kKPerStage, rowB, 0);
                     ++issued;
                     if (++stage == kStages) {
                         stage = 0;
@@ -218,8 +249,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc_fence_after();
                 return true;
             };
-            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-                for (int kb = 0; kb < num_kb; ++kb) {
+            for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+                const Unit x = unit_of(u, num_tiles, w.S);
+                if (w.G > 1 && !kind_runs(KIND, desc[x.g].mode)) continue;
+                const int kb0 = kb_begin(x.r), kb1 = kb_begin(x.r + 1);
+                for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(&S.full[stage], phase, globaltimer_ns() + kWaitBudgetNs,
                                    abort_flag)) {
                         ok = false;
@@ -227,8 +261,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     tc_fence_after();
                     // acc1 is read by the epilogue at the end of the previous
-                    // tile: wait for that before overwriting it.
-                    if (kb == 0 && !wait_drained()) {
+                    // unit: wait for that before overwriting it.
+                    if (kb == kb0 && !wait_drained()) {
                         ok = false;
                         break;
                     }
@@ -245,7 +279,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     // correction products: acc1 += lo*hi + hi*lo
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
-                        const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;
+                        const uint32_t first = (kb == kb0 && ks == 0) ? 0u : 1u;
                         mma<KIND>(a1, A_(ks, 2), B_(ks, 1), id, first);   // Ar_lo [Br_hi; Bi_hi]
                         mma<KIND>(a1, A_(ks, 3), B_(ks, 0), id, 1u);      // Ai_lo [-Bi_hi; Br_hi]
                         mma<KIND>(a1r, A_(ks, 0), B_(ks, 3), idh, 1u);    //  Ar_hi Br_lo
@@ -255,8 +289,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     // hi*hi products: a fresh acc0 every DRAIN stages, once the
                     // previous one was drained
-                    const bool group_start = (kb % DRAIN) == 0;
-                    const bool group_end = (kb % DRAIN) == DRAIN - 1 || kb == num_kb - 1;
+                    const bool group_start = ((kb - kb0) % DRAIN) == 0;
+                    const bool group_end = ((kb - kb0) % DRAIN) == DRAIN - 1 || kb == kb1 - 1;
                     if (group_start && !wait_drained()) {
                         ok = false;
                         break;
@@ -292,19 +326,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int q = warp & 3;                         // lane quadrant this warp may access
         const int half = (warp - 2) >> 2;               // which 64 of the 128 columns
         const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16) + half * kEpiCols;
-        const float unA = ldexpf(1.0f, -sA);
-        const float unB = ldexpf(1.0f, -sB);
         const bool use_beta = (beta.x != 0.0f) || (beta.y != 0.0f);
         uint32_t f_phase = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+        for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+            const Unit x = unit_of(u, num_tiles, w.S);
+            const qcs_gemm_desc_t dg = desc[x.g];
+            if (w.G > 1 && !kind_runs(KIND, dg.mode)) continue;
+            const float unA = ldexpf(1.0f, -dg.sA);
+            const float unB = ldexpf(1.0f, -dg.sB);
+            const int nkb = kb_begin(x.r + 1) - kb_begin(x.r);
             int tm, tn;
-            tile_coords(t, tiles_m, tiles_n, group_m, tm, tn);
+            tile_coords(x.t, tiles_m, tiles_n, group_m, tm, tn);
             float racc[kEpiCols], iacc[kEpiCols];
 #pragma unroll
             for (int j = 0; j < kEpiCols; ++j) racc[j] = iacc[j] = 0.0f;
-            for (int kb = DRAIN - 1; kb < num_kb + DRAIN - 1; kb += DRAIN) {
-                const bool last = kb >= num_kb - 1;  // the group holding the tile's last stage
+            for (int kb = DRAIN - 1; kb < nkb + DRAIN - 1; kb += DRAIN) {
+                const bool last = kb >= nkb - 1;  // the group holding the unit's last stage
                 int got = 0;
                 if (lane == 0)
                     got = mbar_wait(&S.acc0_full, f_phase, globaltimer_ns() + kWaitBudgetNs,
@@ -353,9 +391,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             if (!ok) break;
             const int row = tm * kBM + q * 32 + lane;
+            const int col0 = tn * kBN + half * kEpiCols;
+            if (w.S > 1) {
+                // a K range's partial, scaled back, into its [r][g] block (ld m)
+                if (row < m) {
+                    float2 *prow = w.P + ((int64_t)x.r * w.G + x.g) * (int64_t)m * n + row;
+#pragma unroll
+                    for (int j = 0; j < kEpiCols; ++j) {
+                        const int col = col0 + j;
+                        if (col < n)
+                            prow[(int64_t)col * m] =
+                                make_float2((racc[j] * unA) * unB, (iacc[j] * unA) * unB);
+                    }
+                }
+                continue;
+            }
             if (row < m) {
-                float2 *crow = C + row;
-                const int col0 = tn * kBN + half * kEpiCols;
+                float2 *crow = C + x.g * w.c_stride + row;
 #pragma unroll
                 for (int j = 0; j < kEpiCols; ++j) {
                     const int col = col0 + j;
@@ -387,11 +439,45 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
 }
 
+// C_g = alpha sum_r P[r][g] + beta C_g for every instance g whose GEMM ran on
+// the tensor cores (its descriptor did not select FP32); the K ranges are
+// added in order r = 0, 1, ... with round-to-nearest FP32 adds.
+__global__ void __launch_bounds__(256)
+    tc_splitk_reduce_kernel(const qcs_gemm_desc_t *__restrict__ desc, int G, int S, int64_t m,
+                            int64_t n, const float2 *__restrict__ P, float2 alpha, float2 beta,
+                            float2 *__restrict__ C, int64_t ldc, int64_t c_stride) {
+    const int g = blockIdx.y;
+    if (desc[g].mode == QCS_MODE_FP32) return;
+    const int64_t mn = m * n;
+    const bool use_beta = (beta.x != 0.0f) || (beta.y != 0.0f);
+    float2 *Cg = C + g * c_stride;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mn;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float2 acc = P[(int64_t)g * mn + i];
+        for (int r = 1; r < S; ++r) {
+            const float2 v = P[((int64_t)r * G + g) * mn + i];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        const int64_t col = i / m;
+        float2 *dst = Cg + col * ldc + (i - col * m);
+        float2 o;
+        o.x = alpha.x * acc.x - alpha.y * acc.y;
+        o.y = alpha.x * acc.y + alpha.y * acc.x;
+        if (use_beta) {
+            const float2 c = *dst;
+            o.x += beta.x * c.x - beta.y * c.y;
+            o.y += beta.x * c.y + beta.y * c.x;
+        }
+        *dst = o;
+    }
+}
+
 template <int KIND, int DRAIN>
 cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
                         const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad, float2 alpha,
                         float2 beta, float2 *C, int64_t ldc, int *d_err, int num_sms,
-                        int group_m, cudaStream_t s) {
+                        int group_m, const TcWork &w, cudaStream_t s) {
     const size_t smem = sizeof(TcSmem) + 1024;
     static bool configured = false;
     if (!configured) {
@@ -400,12 +486,12 @@ cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int64_t tiles = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
-    if (tiles == 0 || k_pad == 0) return cudaSuccess;
-    const int grid = static_cast<int>(tiles < num_sms ? tiles : num_sms);
+    const int64_t units = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN) * w.G * w.S;
+    if (units == 0 || k_pad == 0) return cudaSuccess;
+    const int grid = static_cast<int>(units < num_sms ? units : num_sms);
     cgemm_tc_kernel<KIND, DRAIN><<<grid, kTcThreads, smem, s>>>(
         *mapA, *mapB, desc, (int)m, (int)n, (int)k_pad, alpha, beta, C, ldc, d_err,
-        group_m < 1 ? 1 : group_m);
+        group_m < 1 ? 1 : group_m, w);
     return cudaGetLastError();
 }
 
@@ -415,15 +501,15 @@ template <int KIND>
 cudaError_t launch_drain(int drain, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
                          const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad,
                          float2 alpha, float2 beta, float2 *C, int64_t ldc, int *d_err,
-                         int num_sms, int group_m, cudaStream_t s) {
+                         int num_sms, int group_m, const TcWork &w, cudaStream_t s) {
     if (drain >= 4)
         return launch_kind<KIND, 4>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                    num_sms, group_m, s);
+                                    num_sms, group_m, w, s);
     if (drain == 2)
         return launch_kind<KIND, 2>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                    num_sms, group_m, s);
+                                    num_sms, group_m, w, s);
     return launch_kind<KIND, 1>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                num_sms, group_m, s);
+                                num_sms, group_m, w, s);
 }
 
 }  // namespace
@@ -431,18 +517,59 @@ cudaError_t launch_drain(int drain, const qcs_gemm_desc_t *desc, const CUtensorM
 cudaError_t launch_cgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
                             const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
                             int64_t n, int64_t k_pad, float2 alpha, float2 beta, float2 *C,
-                            int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s) {
+                            int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s,
+                            const TcWork &w) {
+    if (w.G < 1 || w.S < 1 || (w.S > 1 && !w.P)) return cudaErrorInvalidValue;
     switch (kind) {
         case 0:
             return launch_drain<0>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                   d_err, num_sms, group_m, s);
+                                   d_err, num_sms, group_m, w, s);
         case 1:
             return launch_drain<1>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                   d_err, num_sms, group_m, s);
+                                   d_err, num_sms, group_m, w, s);
         default:
             return launch_drain<2>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                   d_err, num_sms, group_m, s);
+                                   d_err, num_sms, group_m, w, s);
     }
+}
+
+cudaError_t launch_tc_reduce(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, float2 alpha,
+                             float2 beta, float2 *C, int64_t ldc, int num_sms, const TcWork &w,
+                             cudaStream_t s) {
+    if (w.S <= 1 || m == 0 || n == 0) return cudaSuccess;
+    const int64_t blocks_needed = (m * n + 255) / 256;
+    const int64_t cap = (int64_t)num_sms * 8;
+    dim3 grid(static_cast<unsigned>(blocks_needed < cap ? blocks_needed : cap),
+              static_cast<unsigned>(w.G));
+    tc_splitk_reduce_kernel<<<grid, 256, 0, s>>>(desc, w.G, w.S, m, n, w.P, alpha, beta, C, ldc,
+                                                 w.c_stride);
+    return cudaGetLastError();
+}
+
+// Stages of the K loop per unit are ~1.2 us on one SM (measured: 16384^3
+// FP16X, 16384 tiles x 512 stages over 152 SMs in 67 ms); the partials cost
+// (2 S + 1) m n 8 bytes of HBM traffic per GEMM at ~6 TB/s plus a launch.
+// The count minimises waves x stages per unit + that cost.
+int tc_split_count(int64_t m, int64_t n, int64_t k, int64_t G, int num_sms, int forced) {
+    const int64_t nkb = (k + 31) / 32;  // 16-bit stages (TF32 has twice as many)
+    if (nkb <= 1) return 1;
+    if (forced > 0) return static_cast<int>(forced < nkb ? forced : nkb);
+    const int64_t tiles = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN) * G;
+    if (tiles == 0 || num_sms <= 0) return 1;
+    const double stage_us = 1.2;
+    double best = -1.0;
+    int best_s = 1;
+    for (int S = 1; S <= kMaxSplits && S <= nkb; ++S) {
+        const int64_t units = tiles * S;
+        const int64_t waves = (units + num_sms - 1) / num_sms;
+        double t = (double)waves * (double)((nkb + S - 1) / S) * stage_us;
+        if (S > 1) t += (2.0 * S + 1.0) * (double)(m * n * G) * 8.0 / 6.0e6 + 4.0;
+        if (best < 0 || t < best * 0.97) {  // a split must win by 3% to be taken
+            best = t;
+            best_s = S;
+        }
+    }
+    return best_s;
 }
 
 }  // namespace qcs

@@ -93,6 +93,7 @@ struct qcs_handle_s {
     int instance_batch = 1;          // contraction-tree instances per group (forward)
     int tc_group_m = 8;              // tensor-core raster: tile rows per group
     int tc_l2_promotion = 256;       // L2 promotion of the plane loads (bytes; 0 = none)
+    int tc_splits = 0;               // K ranges per tensor-core GEMM (0 = chosen per shape)
     int *d_err = nullptr;            // device error word (start of a 64-byte block)
     unsigned long long *d_counts = nullptr;  // in that block: AUTO selections per mode, flops
     qcs::Workspace ws;               // GEMM workspace (planes, partials, descriptor)
@@ -174,11 +175,14 @@ cudaError_t launch_set_desc(qcs_gemm_desc_t *desc, int mode, cudaStream_t s);
 // R_pad x K_pad are zero-filled.  (sr, sc): element strides of X for a step
 // in r and in c; conj: negate imaginary parts.  planes6 (the name predates
 // the layout): the kPlanesB-plane op(B) layout of the tensor-core GEMM
-// (-hi.im, hi.re, hi.im, lo.re, lo.im).
+// (-hi.im, hi.re, hi.im, lo.re, lo.im).  plane_off: element offset of row 0
+// in every plane (instance g of a group of equal-shape GEMMs writes its rows
+// after those of instances 0 .. g-1); elements are those of the kind the
+// descriptor selected, so the offset holds for every kind.
 cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
                          int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
                          void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
-                         int planes6 = 0);
+                         int planes6 = 0, int64_t plane_off = 0);
 
 // The split stage reading its operand through a gather map (the reshape of
 // a contraction folded into the split pass): op(X) is the rows x cols
@@ -193,7 +197,7 @@ bool split_gather_supported(int which, int rank, const int64_t *dims, const int6
 cudaError_t launch_split_gather(const qcs_gemm_desc_t *desc, int which, int rank,
                                 const int64_t *dims, const int64_t *strides, const float2 *src,
                                 int64_t rows, void *planes, int64_t pitch, int64_t plane_stride,
-                                cudaStream_t s, int planes6 = 0);
+                                cudaStream_t s, int planes6 = 0, int64_t plane_off = 0);
 cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
                            const float2 *in, float2 *out, int64_t *stats_partials, int gstats,
                            cudaStream_t s, const CopyBatch &cb = CopyBatch{});
@@ -213,7 +217,8 @@ int effective_mode(qcs_handle_t h, int mode, int opA, int opB, int64_t m, int64_
 // Time the candidate modes of one shape (qcs_autotune_gemm without validation).
 int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k, int reps,
                qcs_tune_entry_t *out);
-size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms);
+// ``splits``: the handle's K-range setting (0 = chosen per shape).
+size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits);
 // ``bt``: a batch of equal-shape GEMMs (plain FP32 only; UNSUPPORTED otherwise).
 int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n, int64_t k,
               float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta,
@@ -250,14 +255,37 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
                               int64_t n, int64_t k, float2 alpha, const float2 *A, int64_t lda,
                               const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc,
                               float2 *splitk, cudaStream_t s, const GemmBatch &bt = GemmBatch{});
+// Work of one tensor-core launch: G equal-shape GEMMs, each with its K loop
+// split into S ranges.  Instance g reads its A planes from row g * a_rows of
+// the A tensor map (its B planes from row g * b_rows), its descriptor from
+// desc[g], and writes C + g * c_stride.  S > 1: every range writes its
+// partial into P ([r][g] blocks of m x n complex, column-major, ld m) and
+// launch_tc_reduce then forms C.
+struct TcWork {
+    int G = 1, S = 1;
+    int64_t a_rows = 0, b_rows = 0, c_stride = 0;
+    float2 *P = nullptr;
+};
+constexpr int kMaxSplits = 16;
+// K ranges for a launch over G GEMMs of m x n x k: ``forced`` > 0 is taken
+// (at most one range per 32 k), 0 chooses from the wave count and the cost
+// of the partials.
+int tc_split_count(int64_t m, int64_t n, int64_t k, int64_t G, int num_sms, int forced);
+
 // Tensor-core emulated CGEMM over split planes.  ``kind``: 0 FP16 (modes
 // FP16X, FP16X_SCALED), 1 TF32, 2 BF16; the kernel returns at once unless
-// desc->mode belongs to its kind.
+// desc->mode belongs to its kind (per instance when w.G > 1).
 // ``drain``: pipeline stages per round-to-nearest drain of the hi*hi
 // accumulator (1, 2 or 4).
 cudaError_t launch_cgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
                             const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
                             int64_t n, int64_t k_pad, float2 alpha, float2 beta, float2 *C,
-                            int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s);
+                            int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s,
+                            const TcWork &w = TcWork{});
+// C = alpha sum_r P_r + beta C after a split-K launch (nothing when w.S == 1),
+// for the instances whose descriptor did not select FP32.
+cudaError_t launch_tc_reduce(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, float2 alpha,
+                             float2 beta, float2 *C, int64_t ldc, int num_sms, const TcWork &w,
+                             cudaStream_t s);
 
 }  // namespace qcs

@@ -113,7 +113,7 @@ extern "C" int qcs_cgemm_noalloc(void *cuda_stream, qcs_mode_t mode, double unde
     h.d_err = reinterpret_cast<int *>(d->scratch);
     h.encode = g_encode;
     const int eff = mode;
-    if (kNoallocHeader + gemm_workspace_bytes(eff, m, n, k, d->num_sms) > kNoallocBytes)
+    if (kNoallocHeader + gemm_workspace_bytes(eff, m, n, k, d->num_sms, 0) > kNoallocBytes)
         return QCS_ERR_SCRATCH_TOO_SMALL;
     // The error word must start at zero; everything else in the scratch is
     // overwritten by the launches below before it is read.

@@ -305,3 +305,84 @@ def test_cgemm_fp32_two_by_n_columns(h, n, opA):
     bound = (2 * k + 8) * 2.0 ** -24 * (abs(alpha) * 2 * abs_bound(A, B, opA, 0, m, k, n)
                                         + abs(beta) * 2 * np.abs(C0[:m, :n]))
     assert np.all(np.abs(got - ref) <= bound + 1e-30)
+
+
+# ---------------------------------------------------------------------------
+# K ranges as separate work units (qcs_set_tc_splits)
+# ---------------------------------------------------------------------------
+
+def _model_bound(kind, sA, sB, m, n, k, opA, opB, A, B, alpha, beta, C0):
+    model = oracle.tcec_cgemm(kind, sA, sB, opA, opB, m, n, k, alpha, A, B, beta, C0)
+    bound = (2 * k + 8) * 2.0 ** -24 * (abs(alpha) * 2 * abs_bound(A, B, opA, opB, m, k, n)
+                                        + abs(beta) * 2 * np.abs(C0[:m, :n]))
+    return model, bound
+
+
+@pytest.mark.parametrize("mode,kind", [("fp16x", 0), ("tf32x", 1), ("bf16x3", 2)])
+@pytest.mark.parametrize("m,n,k,splits", [(257, 129, 100, 2), (130, 70, 1000, 5), (300, 40, 513, 16),
+                                          (128, 256, 64, 3), (13, 7, 5, 4)])
+def test_cgemm_tc_split_k_matches_emulation_model(h, mode, kind, m, n, k, splits):
+    """Each K range's partial and their fixed-order sum stay inside the FP32
+    bound of the emulation model; alpha and beta are applied once, by the
+    reduction.  (128, 256, 64) asks for 3 ranges of 2 stages: capped at 2;
+    (13, 7, 5) has one stage: no split."""
+    opA, opB = (1, 2) if splits % 2 else (0, 0)
+    A, B = _operands(m, n, k, opA, opB, 0, seed=(m, n, k, splits, kind), ldpad=1)
+    C0 = qi.cgemm_operand(m, n, 0, seed=(splits, 3), ld=m + 1)
+    alpha, beta = 0.5 + 0.25j, -0.75 + 0.5j
+    h.set_tc_splits(splits)
+    try:
+        got, d = _run(h, mode, m, n, k, opA, opB, A, B, alpha, beta, C0)
+    finally:
+        h.set_tc_splits(0)
+    assert d[0] == {"fp16x": 1, "tf32x": 3, "bf16x3": 5}[mode]
+    model, bound = _model_bound(kind, 0, 0, m, n, k, opA, opB, A, B, alpha, beta, C0)
+    bad = np.abs(got - model) > bound + 1e-30
+    assert not bad.any(), (np.argwhere(bad)[:5], got[bad][:5], model[bad][:5])
+
+
+@pytest.mark.parametrize("s,tol,kind", [(0, 0.5, 0), (20, 0.0, 1), (8, 0.001, 0)])
+def test_cgemm_tc_split_k_under_auto(h, s, tol, kind):
+    """AUTO launches every candidate: with split K the selected kind writes the
+    partials and the reduction (gated by the descriptor) forms C.  One output
+    tile and long k: the per-shape choice splits (the count is not forced)."""
+    m, n, k = 128, 96, 2048
+    A, B = _operands(m, n, k, 0, 0, s, seed=(s, 21))
+    C0 = qi.cgemm_operand(m, n, 0, seed=(s, 22))
+    h.set_tol(tol)
+    try:
+        got, d = _run(h, "auto", m, n, k, 0, 0, A, B, 1.0, 0.5, C0)
+    finally:
+        h.set_tol(0.0)
+    want = oracle.select_mode(oracle.stats_summary(*oracle.exp_stats(A)),
+                              oracle.stats_summary(*oracle.exp_stats(B)), tol)
+    assert tuple(int(v) for v in d[:3]) == want
+    assert {1: 0, 2: 0, 3: 1}[int(d[0])] == kind
+    model, bound = _model_bound(kind, int(d[1]), int(d[2]), m, n, k, 0, 0, A, B, 1.0, 0.5, C0)
+    assert np.all(np.abs(got - model) <= bound + 1e-30)
+
+
+def test_cgemm_tc_split_k_leaves_fp32_result(h):
+    """A GEMM that AUTO sends to FP32 (a NaN input): the gated reduction must
+    not overwrite the SIMT kernel's output."""
+    m, n, k = 128, 64, 1024
+    A, B = _operands(m, n, k, 0, 0, 0, seed=23)
+    A[3, 9] = complex(np.nan, 0)
+    h.set_tc_splits(8)
+    try:
+        got, d = _run(h, "auto", m, n, k, 0, 0, A, B)
+    finally:
+        h.set_tc_splits(0)
+    assert d[0] == oracle.MODE_FP32
+    assert np.isnan(got[3]).all() and np.isfinite(np.delete(got, 3, axis=0)).all()
+    ref = oracle.cgemm(0, 0, m, n, k, 1.0, np.where(np.isnan(A), 0, A), B)
+    keep = np.delete(np.arange(m), 3)
+    assert oracle.rel_fro_error(got[keep], ref[keep]) < 1e-5
+
+
+def test_set_tc_splits_rejects_out_of_range(h):
+    from paper_2303_08989_gb300 import _lib as L
+
+    assert h.lib.qcs_set_tc_splits(h.ptr, -1) == L.QCS_ERR_INVALID_ARG
+    assert h.lib.qcs_set_tc_splits(h.ptr, 17) == L.QCS_ERR_INVALID_ARG
+    assert h.lib.qcs_set_tc_splits(h.ptr, 0) == 0

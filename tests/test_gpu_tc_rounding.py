@@ -35,6 +35,9 @@ def _dot(h, mode, pairs, k):
 def h():
     need_gpu()
     hd = lib().Handle(size_rule=False)
+    # one unbroken K loop, so that the drain groups start at k = 0 (the
+    # per-shape choice would cut these one-tile GEMMs into K ranges)
+    hd.set_tc_splits(1)
     yield hd
     hd.close()
 
