@@ -273,14 +273,18 @@ typedef struct {
 
 /* Instances per group of qcs_contract_tree and qcs_tree_graph_create (1 to
  * 65535; default 1).  With G > 1 the forward pass runs the instances in
- * groups of G: every step whose GEMM runs in plain FP32 (after the size rule)
- * is one batched launch per group -- its gathers and its G equal-shape GEMMs
- * (Section 5.3: slices and bitstrings are independent instances of one step
- * sequence) -- and the other steps, large enough to fill the GPU alone, loop
- * over the group.  Step outputs then hold G instances each (the tree
- * workspace grows about G-fold; intermediates share memory by liveness).
- * Results do not depend on G.  The backward always runs one instance at a
- * time. */
+ * groups of G (Section 5.3: slices and bitstrings are independent instances
+ * of one step sequence).  Each step up to the first emulated step with at
+ * least one 128 x 128 output tile per SM runs once per group: a step whose
+ * GEMM runs in plain FP32 (after the size rule) as one batched gather and
+ * one batched GEMM launch; an emulated step as per-instance statistics,
+ * selection and split followed by one persistent tensor-core launch per
+ * kind over the output tiles of all G instances (each instance keeps its
+ * own selected mode; for AUTO the FP32 candidate of each instance is
+ * launched gated).  Their outputs hold G instances each (intermediates share
+ * memory by liveness).  The later steps -- large enough to fill the GPU
+ * alone -- loop over the group.  Results do not depend on G.  The backward
+ * always runs one instance at a time. */
 int qcs_set_instance_batch(qcs_handle_t h, int instances);
 
 /* Contract the plan for every instance and accumulate into d_out (device,
@@ -369,13 +373,20 @@ int qcs_cgemm_noalloc(void *cuda_stream, qcs_mode_t mode, double underflow_tol, 
  * when the candidate was not run (pruned: an FP32 call that cannot win).
  * best is what QCS_SIZE_RULE_TUNED then runs for an AUTO GEMM of this shape:
  * QCS_MODE_AUTO (statistics decide), QCS_MODE_TF32X (no statistics: TF32
- * has FP32's exponent range) or QCS_MODE_FP32. */
+ * has FP32's exponent range) or QCS_MODE_FP32.  splits is the tensor-core
+ * schedule measured for the shape: the number of K ranges (see
+ * qcs_set_tc_splits) that ran the faster emulated candidate fastest; under
+ * QCS_SIZE_RULE_TUNED the tensor-core GEMMs of this shape use it unless
+ * qcs_set_tc_splits forces a count.  0: not measured (the per-shape rule
+ * applies); ms[] of the emulated candidate is its time at that count. */
 typedef struct {
     int64_t m, n, k;
     int32_t opA, opB;
     float ms[QCS_NUM_MODES];
     int32_t best;
     int32_t reps;
+    int32_t splits;
+    int32_t reserved;
 } qcs_tune_entry_t;
 
 /* Time the candidates for one shape on the handle's stream and record the
@@ -385,7 +396,11 @@ typedef struct {
  * with random signs, so that the statistics select FP16X.  Each candidate
  * runs once untimed, then ``reps`` (>= 1) times between CUDA events;
  * FP32 is not run when 8 m n k / 45 TFLOP/s is above 4x the faster
- * emulated candidate.  Ties go to the earlier of AUTO, TF32X, FP32.
+ * emulated candidate.  Ties go to the earlier of AUTO, TF32X, FP32.  For a
+ * shape with fewer 128 x 128 output tiles than twice the SM count, the
+ * faster emulated candidate is also timed at 1, 2, 4, 8 and 16 K ranges
+ * (at most one per 32 k; not when qcs_set_tc_splits forces a count) and the
+ * fastest count is recorded in ``splits``.
  * Synchronizes the stream; not during a stream capture.  out (host,
  * optional) receives the entry.  m, n, k >= 1. */
 int qcs_autotune_gemm(qcs_handle_t h, qcs_op_t transA, qcs_op_t transB, int64_t m, int64_t n,

@@ -1,4 +1,5 @@
-"""Build libqcs.so (all CUDA sources of the package) for sm_103a with nvcc.
+"""Build libqcs.so (all CUDA sources of the package) for sm_103a with nvcc,
+and libqcs_cublas.so (the cuBLAS complex-GEMM interception) over it.
 
 Objects and the library go to ``paper_2303_08989_gb300/_build`` (git-ignored).
 Translation units compile in parallel; a unit is rebuilt only when it or a
@@ -45,6 +46,27 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
+SHIM_SRC = os.path.join(CSRC, "cublas_shim.cpp")
+SHIM = os.path.join(BUILD, "libqcs_cublas.so")
+CUDA_INCLUDE = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+
+
+def build_shim() -> str:
+    """libqcs_cublas.so: the cuBLAS complex-GEMM interception (host code
+    only) over libqcs.so, found next to it at run time."""
+    if os.path.exists(SHIM) and os.path.getmtime(SHIM) >= max(
+            os.path.getmtime(SHIM_SRC), os.path.getmtime(LIB), _headers_mtime()):
+        return SHIM
+    cmd = [os.environ.get("CXX", "g++"), "-O2", "-std=c++17", "-fPIC", "-shared", "-Wall",
+           "-I", CUDA_INCLUDE, SHIM_SRC, "-o", SHIM + ".tmp", "-L", BUILD, "-lqcs",
+           "-Wl,-rpath,$ORIGIN", "-ldl", "-lpthread"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"shim build failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(SHIM + ".tmp", SHIM)
+    return SHIM
+
+
 def build(verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = _sources()
@@ -56,6 +78,7 @@ def build(verbose: bool = False, extra=()) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(LIB + ".tmp", LIB)
+    build_shim()
     if verbose:
         print(LIB)
     return LIB

@@ -8,7 +8,9 @@
 // tensor-core GEMM, no statistics) and FP32 (SIMT) run on synthetic operands
 // of the shape and the fastest is recorded in the handle's table, which
 // QCS_SIZE_RULE_TUNED consults.  Every candidate keeps the FP32 accuracy
-// level, so the choice is about time only.
+// level, so the choice is about time only.  For shapes with few output tiles
+// the tensor-core schedule is measured too: the K-range count (split K) that
+// runs the faster emulated candidate fastest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,8 +62,10 @@ int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k
     if (cs != cudaStreamCaptureStatusNone) return QCS_ERR_UNSUPPORTED;
     const int64_t ra = (opA == QCS_OP_N) ? m : k, ca = (opA == QCS_OP_N) ? k : m;
     const int64_t rb = (opB == QCS_OP_N) ? k : n, cb = (opB == QCS_OP_N) ? n : k;
+    // the largest K-range count any timing below uses
     size_t ws = 0;
-    for (int c : kCandidates) ws = std::max(ws, gemm_workspace_bytes(c, m, n, k, h->num_sms, h->tc_splits));
+    for (int c : kCandidates)
+        ws = std::max(ws, gemm_workspace_bytes(c, m, n, k, h->num_sms, kMaxSplits));
     if (int r = ensure_workspace(h->ws, ws)) return r;
     DeviceBuffer A, B, C;
     if (cudaMalloc(&A.p, sizeof(float2) * ra * ca) != cudaSuccess ||
@@ -87,11 +91,16 @@ int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k
     for (float &v : e.ms) v = -1.f;
 
     // Tuning calls are not the caller's work: no profile records, no
-    // selection counts.
+    // selection counts.  The emulated candidates run at the per-shape K-range
+    // count (or the one qcs_set_tc_splits forces) unless a count is being
+    // measured.
     const int profiling = h->profiling;
     unsigned long long *counts = h->d_counts;
+    const int forced_splits = h->tc_splits;
     h->profiling = 0;
     h->d_counts = nullptr;
+    h->tc_splits = forced_splits > 0 ? forced_splits
+                                     : tc_split_count(m, n, k, 1, h->num_sms, 0);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = QCS_SUCCESS;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = QCS_ERR_CUDA;
@@ -114,6 +123,28 @@ int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k
     };
     if (rc == QCS_SUCCESS) rc = time_mode(QCS_MODE_AUTO);
     if (rc == QCS_SUCCESS) rc = time_mode(QCS_MODE_TF32X);
+    // The tensor-core schedule: with few output tiles, time the faster
+    // emulated candidate at other K-range counts and keep the fastest.
+    const int64_t tiles = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
+    if (rc == QCS_SUCCESS && forced_splits == 0 && tiles < 2 * (int64_t)h->num_sms) {
+        const int emu = e.ms[QCS_MODE_TF32X] < e.ms[QCS_MODE_AUTO] ? QCS_MODE_TF32X : QCS_MODE_AUTO;
+        const int heuristic = h->tc_splits;
+        int best_s = heuristic;
+        float best_ms = e.ms[emu];
+        const int64_t nkb = (k + 31) / 32;
+        for (int S : {1, 2, 4, 8, 16}) {
+            if (S == heuristic || S > nkb) continue;
+            h->tc_splits = S;
+            if ((rc = time_mode(emu)) != QCS_SUCCESS) break;
+            if (e.ms[emu] < best_ms) {
+                best_ms = e.ms[emu];
+                best_s = S;
+            }
+        }
+        e.ms[emu] = best_ms;
+        e.splits = best_s;
+    }
+    h->tc_splits = forced_splits;
     if (rc == QCS_SUCCESS) {
         const float emulated = std::min(e.ms[QCS_MODE_AUTO], e.ms[QCS_MODE_TF32X]);
         const double fp32_bound_ms = 8.0 * (double)m * (double)n * (double)k / kFp32BoundFlops * 1e3;
@@ -121,6 +152,7 @@ int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k
     }
     h->profiling = profiling;
     h->d_counts = counts;
+    h->tc_splits = forced_splits;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (rc != QCS_SUCCESS) {
@@ -170,7 +202,8 @@ int qcs_set_tuning(qcs_handle_t h, const qcs_tune_entry_t *entries, int64_t coun
     for (int64_t i = 0; i < count; ++i) {
         const qcs_tune_entry_t &e = entries[i];
         if (e.m < 1 || e.n < 1 || e.k < 1 || !valid_tune_op(e.opA) || !valid_tune_op(e.opB) ||
-            (e.best != QCS_MODE_AUTO && e.best != QCS_MODE_TF32X && e.best != QCS_MODE_FP32))
+            (e.best != QCS_MODE_AUTO && e.best != QCS_MODE_TF32X && e.best != QCS_MODE_FP32) ||
+            e.splits < 0 || e.splits > kMaxSplits)
             return QCS_ERR_INVALID_ARG;
     }
     for (int64_t i = 0; i < count; ++i) {

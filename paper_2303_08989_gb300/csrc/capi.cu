@@ -147,22 +147,72 @@ int qcs::effective_mode(qcs_handle_t h, int mode, int opA, int opB, int64_t m, i
     return QCS_MODE_FP32;
 }
 
+// K ranges of a tensor-core GEMM of this shape: the count qcs_set_tc_splits
+// forces, else the count the tuner measured for the shape (under the tuned
+// size rule), else 0 (tc_split_count's per-shape rule).
+int qcs::gemm_splits(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k) {
+    if (h->tc_splits > 0) return h->tc_splits;
+    if (h->size_rule == QCS_SIZE_RULE_TUNED) {
+        const auto it = h->tuned.find(std::make_tuple(m, n, k, opA, opB));
+        if (it != h->tuned.end() && it->second.splits > 0) return it->second.splits;
+    }
+    return 0;
+}
+
 // The whole emulated CGEMM on the handle's stream.  desc_ws/partials/planes
 // come from ``ws`` (a device buffer of at least gemm_workspace_bytes()).
 namespace qcs {
 
-size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits) {
-    size_t bytes = 256;  // descriptor
+namespace {
+
+// Byte offsets, from the start of the plane area, of the split planes of a
+// group of G GEMMs and of the K-range partials.  A group whose instances may
+// select different kinds (AUTO, G > 1) keeps 2-byte and 4-byte planes apart
+// (instance g's rows sit at the same element offset in either, which in
+// bytes depends on the kind); otherwise one region serves the selected kind.
+struct PlaneLayout {
+    size_t a16 = 0, b16 = 0, a32 = 0, b32 = 0, partials = 0, total = 0;
+};
+
+PlaneLayout plane_layout(int eff, int64_t m, int64_t n, int64_t k, int G, int S) {
+    PlaneLayout L;
+    const bool need16 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X ||
+                         eff == QCS_MODE_FP16X_SCALED || eff == QCS_MODE_BF16X3);
+    const bool need32 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X);
+    const int64_t kp = round_up(k, 32), mp = round_up(m, kBM), np = round_up(n, kBN);
+    size_t off = 0;
+    auto region = [&](int esz, int planes, int64_t rows) {
+        const size_t o = off;
+        off += align256(size_t(planes) * G * rows * kp * esz);
+        return o;
+    };
+    if (G > 1 && need16 && need32) {
+        L.a16 = region(2, kPlanes, mp);
+        L.b16 = region(2, kPlanesB, np);
+        L.a32 = region(4, kPlanes, mp);
+        L.b32 = region(4, kPlanesB, np);
+    } else {
+        const int esz = need32 ? 4 : 2;
+        L.a16 = L.a32 = region(esz, kPlanes, mp);
+        L.b16 = L.b32 = region(esz, kPlanesB, np);
+    }
+    if (S > 1) {
+        L.partials = off;
+        off += align256(sizeof(float2) * S * G * m * n);
+    }
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits,
+                            int G) {
+    size_t bytes = align256(sizeof(qcs_gemm_desc_t) * G);  // descriptors
     bytes += align256(size_t(2) * num_sms * kPartialStride * sizeof(int64_t));
     bytes += align256(kSplitKBytes);
-    if (eff != QCS_MODE_FP32) {
-        const int esz = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X) ? 4 : 2;
-        const int64_t kp = round_up(k, 32), mp = round_up(m, kBM), np = round_up(n, kBN);
-        bytes += align256(size_t(kPlanes) * mp * kp * esz);
-        bytes += align256(size_t(kPlanesB) * np * kp * esz);
-        const int S = tc_split_count(m, n, k, 1, num_sms, splits);
-        if (S > 1) bytes += align256(sizeof(float2) * S * m * n);  // K-range partials
-    }
+    if (eff != QCS_MODE_FP32)
+        bytes += plane_layout(eff, m, n, k, G, tc_split_count(m, n, k, 1, num_sms, splits)).total;
     return bytes;
 }
 
@@ -202,109 +252,139 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                     int64_t k, float2 alpha, const OperandView &A_in, const OperandView &B_in,
                     float2 beta, float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out,
                     const qcs_gemm_desc_t *d_desc_in, const GemmBatch &bt) {
+    return run_cgemm_group(h, ws, eff, opA, opB, m, n, k, alpha, &A_in, &B_in, 1, beta, C, ldc, 0,
+                           d_desc_out, d_desc_in, bt);
+}
+
+int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n,
+                    int64_t k, float2 alpha, const OperandView *A_in, const OperandView *B_in,
+                    int G, float2 beta, float2 *C, int64_t ldc, int64_t c_stride,
+                    qcs_gemm_desc_t *d_desc_out, const qcs_gemm_desc_t *d_desc_in,
+                    const GemmBatch &bt) {
     cudaStream_t s = h->stream;
-    if (bt.count != 1 && (eff != QCS_MODE_FP32 || k == 0 || d_desc_out || d_desc_in ||
-                          A_in.map || B_in.map))
+    if (G < 1) return QCS_ERR_INVALID_ARG;
+    if (bt.count != 1 && (eff != QCS_MODE_FP32 || k == 0 || d_desc_out || d_desc_in || G != 1 ||
+                          A_in[0].map || B_in[0].map))
         return QCS_ERR_UNSUPPORTED;
-    if ((A_in.map && (opA != QCS_OP_N || !A_in.buf)) || (B_in.map && (opB != QCS_OP_N || !B_in.buf)))
-        return QCS_ERR_INVALID_ARG;
+    if (G > 1 && (eff == QCS_MODE_FP32 || k == 0 || d_desc_out || d_desc_in))
+        return QCS_ERR_UNSUPPORTED;
+    for (int g = 0; g < G; ++g)
+        if ((A_in[g].map && (opA != QCS_OP_N || !A_in[g].buf)) ||
+            (B_in[g].map && (opB != QCS_OP_N || !B_in[g].buf)))
+            return QCS_ERR_INVALID_ARG;
     uint8_t *p = static_cast<uint8_t *>(ws);
     qcs_gemm_desc_t *desc = reinterpret_cast<qcs_gemm_desc_t *>(p);
-    p += 256;
+    p += align256(sizeof(qcs_gemm_desc_t) * G);
     int64_t *partials = reinterpret_cast<int64_t *>(p);
     p += align256(size_t(2) * h->num_sms * kPartialStride * sizeof(int64_t));
     float2 *splitk = reinterpret_cast<float2 *>(p);  // kSplitKBytes per batch entry (FP32 batches
     p += align256(kSplitKBytes);                      // run without planes, so the rest follows)
     cudaError_t e = cudaSuccess;
     const int64_t kp = round_up(k, 32), mp = round_up(m, kBM), np = round_up(n, kBN);
+    if (G > 1 && (G * mp > INT32_MAX || G * np > INT32_MAX)) return QCS_ERR_UNSUPPORTED;
 
     // A mapped operand is split straight from its tensor when the emulated
-    // path runs and the map tiles with no plane padding; otherwise it is
-    // gathered here, once, and read as a matrix from then on.
-    OperandView A = A_in, B = B_in;
+    // path runs, the map permutes that tensor as a whole (``flat``) and tiles
+    // with no plane padding; otherwise it is gathered here and read as a
+    // matrix (for G = 1 once, and the FP32 candidate reuses it; for a group
+    // per instance into the one buffer, and the FP32 candidate gathers again,
+    // only if it was selected).
+    std::vector<OperandView> Av(A_in, A_in + G), Bv(B_in, B_in + G);
     const bool emulated = (eff != QCS_MODE_FP32 && k > 0);
-    const bool fusedA = A.map && emulated && mp == m && kp == k &&
-                        split_gather_supported(0, A.map->rank, A.map->dims, A.map->strides, m, kp);
-    const bool fusedB = B.map && emulated && np == n && kp == k &&
-                        split_gather_supported(1, B.map->rank, B.map->dims, B.map->strides, k, kp);
-    if (A.map && !fusedA)
-        if (int r = gather_view(h, A, m, nullptr)) return r;
-    if (B.map && !fusedB)
-        if (int r = gather_view(h, B, k, nullptr)) return r;
+    const OperandView &A0 = Av[0], &B0 = Bv[0];
+    const bool fusedA = A0.map && A0.flat > 0 && emulated && mp == m && kp == k &&
+                        split_gather_supported(0, A0.map->rank, A0.map->dims, A0.map->strides, m, kp);
+    const bool fusedB = B0.map && B0.flat > 0 && emulated && np == n && kp == k &&
+                        split_gather_supported(1, B0.map->rank, B0.map->dims, B0.map->strides, k, kp);
 
-    if (d_desc_in) {
-        desc = const_cast<qcs_gemm_desc_t *>(d_desc_in);
-    } else if (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X_SCALED) {
-        // Statistics of both operands as stored (a transpose or a whole-tensor
-        // permutation does not change the multiset).
-        const int64_t ra = fusedA ? A.flat : ((opA == QCS_OP_N) ? m : k);
-        const int64_t ca = fusedA ? 1 : ((opA == QCS_OP_N) ? k : m);
-        const int64_t rb = fusedB ? B.flat : ((opB == QCS_OP_N) ? k : n);
-        const int64_t cb = fusedB ? 1 : ((opB == QCS_OP_N) ? n : k);
-        const int64_t lda = fusedA ? A.flat : A.ld, ldb = fusedB ? B.flat : B.ld;
-        const int gA = stats2_blocks(ra * ca, h->num_sms), gB = stats2_blocks(rb * cb, h->num_sms);
-        {
+    // The per-instance front of the sequence: gathers, statistics and
+    // selection (or the constant descriptor), the split of both operands.
+    const bool need16 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X ||
+                         eff == QCS_MODE_FP16X_SCALED || eff == QCS_MODE_BF16X3);
+    const bool need32 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X);
+    TcWork w;
+    w.G = G;
+    w.a_rows = mp;
+    w.b_rows = np;
+    w.c_stride = c_stride;
+    // K ranges are chosen per GEMM, not per group, so that an instance's
+    // result does not depend on the group it ran in
+    w.S = emulated ? tc_split_count(m, n, k, 1, h->num_sms, gemm_splits(h, opA, opB, m, n, k)) : 1;
+    const PlaneLayout PL = plane_layout(eff, m, n, k, G, w.S);
+    uint8_t *planesA = p + PL.a16, *planesB = p + PL.b16;
+    uint8_t *planesA32 = p + PL.a32, *planesB32 = p + PL.b32;
+    void *sepA32 = (PL.a32 != PL.a16) ? planesA32 : nullptr;
+    void *sepB32 = (PL.b32 != PL.b16) ? planesB32 : nullptr;
+    if (w.S > 1) w.P = reinterpret_cast<float2 *>(p + PL.partials);
+    for (int g = 0; g < G; ++g) {
+        OperandView &A = Av[g], &B = Bv[g];
+        qcs_gemm_desc_t *dg = desc + g;
+        if (A.map && !fusedA)
+            if (int r = gather_view(h, A, m, nullptr)) return r;
+        if (B.map && !fusedB)
+            if (int r = gather_view(h, B, k, nullptr)) return r;
+        if (d_desc_in) {
+            dg = const_cast<qcs_gemm_desc_t *>(d_desc_in);
+            desc = dg;
+        } else if (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X_SCALED) {
+            // Statistics of both operands as stored (a transpose or a
+            // whole-tensor permutation does not change the multiset).
+            const int64_t ra = fusedA ? A.flat : ((opA == QCS_OP_N) ? m : k);
+            const int64_t ca = fusedA ? 1 : ((opA == QCS_OP_N) ? k : m);
+            const int64_t rb = fusedB ? B.flat : ((opB == QCS_OP_N) ? k : n);
+            const int64_t cb = fusedB ? 1 : ((opB == QCS_OP_N) ? n : k);
+            const int64_t lda = fusedA ? A.flat : A.ld, ldb = fusedB ? B.flat : B.ld;
+            const int gA = stats2_blocks(ra * ca, h->num_sms), gB = stats2_blocks(rb * cb, h->num_sms);
             ProfScope ps(h, kProfStats);
             e = launch_stats_select_2stage(A.X, ra, ca, lda, gA, B.X, rb, cb, ldb, gB, h->tol, eff,
-                                           partials, partials + 5 * (gA + gB), desc,
-                                           h->d_counts, 8.0 * (double)m * (double)n * (double)k,
-                                           s);
+                                           partials, partials + 5 * (gA + gB), dg, h->d_counts,
+                                           8.0 * (double)m * (double)n * (double)k, s);
+            if (e != cudaSuccess) return QCS_ERR_CUDA;
+        } else if (eff != QCS_MODE_FP32 || d_desc_out) {
+            // A plain FP32 GEMM runs ungated; it needs a descriptor only to report it.
+            e = launch_set_desc(dg, eff, s);
+            if (e != cudaSuccess) return QCS_ERR_CUDA;
         }
-        if (e != cudaSuccess) return QCS_ERR_CUDA;
-    } else if (eff != QCS_MODE_FP32 || d_desc_out) {
-        // A plain FP32 GEMM runs ungated; it needs a descriptor only to report it.
-        e = launch_set_desc(desc, eff, s);
+        if (!emulated) continue;
+        // The split writes with the selected kind's element size; the pitch
+        // is kp elements either way, so both tensor maps below describe it.
+        // Instance g owns rows [g R_pad, (g + 1) R_pad) of every plane.
+        int64_t sr, sc;
+        ProfScope ps(h, kProfSplit);
+        if (fusedA) {
+            e = launch_split_gather(dg, 0, A.map->rank, A.map->dims, A.map->strides, A.X, m,
+                                    planesA, kp, G * mp * kp, s, 0, g * mp * kp, sepA32);
+        } else {
+            plane_strides(0, opA, A.ld, sr, sc);
+            e = launch_split(dg, 0, A.X, sr, sc, opA == QCS_OP_C, m, k, mp, kp, planesA, kp,
+                             G * mp * kp, s, 0, g * mp * kp, sepA32);
+        }
+        if (e == cudaSuccess) {
+            if (fusedB) {
+                e = launch_split_gather(dg, 1, B.map->rank, B.map->dims, B.map->strides, B.X, k,
+                                        planesB, kp, G * np * kp, s, 1, g * np * kp, sepB32);
+            } else {
+                plane_strides(1, opB, B.ld, sr, sc);
+                e = launch_split(dg, 1, B.X, sr, sc, opB == QCS_OP_C, n, k, np, kp, planesB, kp,
+                                 G * np * kp, s, 1, g * np * kp, sepB32);
+            }
+        }
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     }
 
     if (k == 0) {
         // C = beta C: the SIMT kernel with k = 0 does exactly that (no desc gate).
-        e = launch_cgemm_simt(nullptr, opA, opB, m, n, 0, alpha, A.X, A.ld, B.X, B.ld, beta, C, ldc,
-                              nullptr, s);
+        e = launch_cgemm_simt(nullptr, opA, opB, m, n, 0, alpha, Av[0].X, Av[0].ld, Bv[0].X,
+                              Bv[0].ld, beta, C, ldc, nullptr, s);
         if (e != cudaSuccess) return QCS_ERR_CUDA;
-    } else if (eff != QCS_MODE_FP32) {
-        const bool need16 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X ||
-                             eff == QCS_MODE_FP16X_SCALED || eff == QCS_MODE_BF16X3);
-        const bool need32 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X);
-        const int esz_max = need32 ? 4 : 2;
-        uint8_t *planesA = p;
-        uint8_t *planesB = p + align256(size_t(kPlanes) * mp * kp * esz_max);
-        TcWork w;
-        w.S = tc_split_count(m, n, k, 1, h->num_sms, h->tc_splits);
-        if (w.S > 1)
-            w.P = reinterpret_cast<float2 *>(planesB +
-                                             align256(size_t(kPlanesB) * np * kp * esz_max));
-        int64_t sr, sc;
-        // The split writes with the selected kind's element size; the pitch is
-        // kp elements either way, so both tensor maps below describe it.
+    } else if (emulated) {
         {
-            ProfScope ps(h, kProfSplit);
-            if (fusedA) {
-                e = launch_split_gather(desc, 0, A.map->rank, A.map->dims, A.map->strides, A.X, m,
-                                        planesA, kp, mp * kp, s, 0);
-            } else {
-                plane_strides(0, opA, A.ld, sr, sc);
-                e = launch_split(desc, 0, A.X, sr, sc, opA == QCS_OP_C, m, k, mp, kp, planesA, kp,
-                                 mp * kp, s);
-            }
-            if (e == cudaSuccess) {
-                if (fusedB) {
-                    e = launch_split_gather(desc, 1, B.map->rank, B.map->dims, B.map->strides, B.X,
-                                            k, planesB, kp, np * kp, s, 1);
-                } else {
-                    plane_strides(1, opB, B.ld, sr, sc);
-                    e = launch_split(desc, 1, B.X, sr, sc, opB == QCS_OP_C, n, k, np, kp, planesB,
-                                     kp, np * kp, s, 1);
-                }
-            }
-        }
-        if (e != cudaSuccess) return QCS_ERR_CUDA;
-        {
+            // One launch per kind over the tiles of all G instances.
             ProfScope ps_tc(h, kProfGemmTc);
             if (need16) {
                 CUtensorMap ma, mb;
-                if (encode_planes(h, &ma, planesA, mp, kp, 2, kPlanes) ||
-                    encode_planes(h, &mb, planesB, np, kp, 2, kPlanesB))
+                if (encode_planes(h, &ma, planesA, G * mp, kp, 2, kPlanes) ||
+                    encode_planes(h, &mb, planesB, G * np, kp, 2, kPlanesB))
                     return QCS_ERR_CUDA;
                 const int kind = (eff == QCS_MODE_BF16X3) ? 2 : 0;
                 e = launch_cgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
@@ -313,8 +393,8 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
             }
             if (need32) {
                 CUtensorMap ma, mb;
-                if (encode_planes(h, &ma, planesA, mp, kp, 4, kPlanes) ||
-                    encode_planes(h, &mb, planesB, np, kp, 4, kPlanesB))
+                if (encode_planes(h, &ma, planesA32, G * mp, kp, 4, kPlanes) ||
+                    encode_planes(h, &mb, planesB32, G * np, kp, 4, kPlanesB))
                     return QCS_ERR_CUDA;
                 e = launch_cgemm_tc(1, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
                                     ldc, h->d_err, h->num_sms, h->tc_group_m, s, w);
@@ -324,20 +404,30 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
             if (e != cudaSuccess) return QCS_ERR_CUDA;
         }
         if (eff == QCS_MODE_AUTO) {
-            // the FP32 candidate: mapped operands are gathered only if it was selected
-            if (fusedA)
-                if (int r = gather_view(h, A, m, desc)) return r;
-            if (fusedB)
-                if (int r = gather_view(h, B, k, desc)) return r;
-            ProfScope ps(h, kProfGemmSimt);
-            e = launch_cgemm_simt(desc, opA, opB, m, n, k, alpha, A.X, A.ld, B.X, B.ld, beta, C, ldc,
-                                  splitk, s);
-            if (e != cudaSuccess) return QCS_ERR_CUDA;
+            // the FP32 candidate of each instance: mapped operands are
+            // gathered only if it was selected
+            for (int g = 0; g < G; ++g) {
+                OperandView &A = Av[g], &B = Bv[g];
+                const bool regatherA = fusedA || (G > 1 && A_in[g].map);
+                const bool regatherB = fusedB || (G > 1 && B_in[g].map);
+                if (regatherA) {
+                    A = A_in[g];
+                    if (int r = gather_view(h, A, m, desc + g)) return r;
+                }
+                if (regatherB) {
+                    B = B_in[g];
+                    if (int r = gather_view(h, B, k, desc + g)) return r;
+                }
+                ProfScope ps(h, kProfGemmSimt);
+                e = launch_cgemm_simt(desc + g, opA, opB, m, n, k, alpha, A.X, A.ld, B.X, B.ld,
+                                      beta, C + g * c_stride, ldc, splitk, s);
+                if (e != cudaSuccess) return QCS_ERR_CUDA;
+            }
         }
     } else {
         ProfScope ps(h, kProfGemmSimt);
-        e = launch_cgemm_simt(nullptr, opA, opB, m, n, k, alpha, A.X, A.ld, B.X, B.ld, beta, C, ldc,
-                              splitk, s, bt);
+        e = launch_cgemm_simt(nullptr, opA, opB, m, n, k, alpha, Av[0].X, Av[0].ld, Bv[0].X,
+                              Bv[0].ld, beta, C, ldc, splitk, s, bt);
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     }
     if (d_desc_out) {
@@ -512,7 +602,8 @@ int qcs_cgemm(qcs_handle_t h, qcs_mode_t mode, qcs_op_t transA, qcs_op_t transB,
     if (m == 0 || n == 0) return QCS_SUCCESS;
     if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) return QCS_ERR_UNSUPPORTED;
     const int eff = effective_mode(h, mode, transA, transB, m, n, k);
-    if (int r = ensure_workspace(h->ws, gemm_workspace_bytes(eff, m, n, k, h->num_sms, h->tc_splits)))
+    if (int r = ensure_workspace(h->ws, gemm_workspace_bytes(eff, m, n, k, h->num_sms,
+                                                            gemm_splits(h, transA, transB, m, n, k), 1)))
         return r;
     const float2 al = make_float2(alpha->x, alpha->y), be = make_float2(beta->x, beta->y);
     return run_cgemm(h, h->ws.ptr, eff, transA, transB, m, n, k, al,

@@ -8,7 +8,10 @@
 // slice-gather kernel), then qcs_cgemm's launch sequence (statistics,
 // selection, split, tensor-core or FP32 GEMM), writing the step's output
 // into its own slot of the tree workspace.  The root of each instance is
-// accumulated in FP64 into its output slot.
+// accumulated in FP64 into its output slot.  Instances run in groups
+// (qcs_set_instance_batch): the steps up to the first emulated one that
+// fills the GPU alone run once for the group, their GEMMs as one batched
+// FP32 launch or one grouped tensor-core launch.
 //
 // The adjoint recomputes an instance's forward pass, then walks the steps
 // backwards: grad_A = grad_out B_mat^H and grad_B = A_mat^H grad_out as two
@@ -171,12 +174,15 @@ size_t place_by_liveness(const qcs_tree_t *t, const std::vector<size_t> &bytes, 
 }
 
 // Workspace of one call.  Forward: the instances run in groups of G that
-// share the buffers.  The steps before P -- the first step whose GEMM does
-// not run in plain FP32 -- are batched: one launch per group, outputs
-// holding G instances.  The steps from P on (in a tree from a greedy order,
-// the few large contractions at the end) run one instance after another,
-// outputs holding one instance.  Outputs reuse memory by liveness.
-// Backward (G = 1): every output is kept.
+// share the buffers.  The steps before P run once per group: a plain-FP32
+// step as one batched gather and one batched GEMM launch, an emulated step as
+// one grouped sequence (run_cgemm_group: one tensor-core launch per kind over
+// the tiles of all G instances), outputs holding G instances.  P is the first
+// emulated step with at least one output tile per SM: it fills the GPU alone,
+// so from there on (in a tree from a greedy order, the few large
+// contractions at the end) the steps run one instance after another, outputs
+// holding one instance.  Outputs reuse memory by liveness.  Backward (G = 1):
+// every output is kept.
 Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
     Layout L;
     L.G = G;
@@ -195,7 +201,12 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
         const qcs_step_t &st = t->steps[s];
         L.eff[s] = effective_mode(h, st.mode, fwd_op(st.direct_a), fwd_op(st.direct_b), st.m, st.n,
                                   st.k);
-        L.batched[s] = (G > 1 && L.eff[s] == QCS_MODE_FP32) ? 1 : 0;
+        // An emulated step whose output tiles fill the GPU alone gains nothing
+        // from running its instances in one launch, and a group would hold G
+        // copies of its planes: it and every later step run per instance.
+        const int64_t tiles = ((st.m + kBM - 1) / kBM) * ((st.n + kBN - 1) / kBN);
+        const bool fills = L.eff[s] != QCS_MODE_FP32 && tiles >= h->num_sms;
+        L.batched[s] = (G > 1 && !fills) ? 1 : 0;
     }
     L.P = 0;
     while (L.P < ns && L.batched[L.P]) ++L.P;
@@ -204,19 +215,37 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
         const qcs_step_t &st = t->steps[s];
         const int64_t gb = L.batched[s] ? G : 1;
         bytes[s] = align256(sizeof(float2) * st.m * st.n * gb);
-        maxA = std::max(maxA, st.m * st.k * gb);
-        maxB = std::max(maxB, st.k * st.n * gb);
-        // a batched plain-FP32 GEMM keeps a split-K partial buffer per instance,
-        // at the end of its workspace
-        gemm = std::max(gemm, gemm_workspace_bytes(L.eff[s], st.m, st.n, st.k, h->num_sms, h->tc_splits) +
-                                  (size_t)(gb - 1) * kSplitKBytes);
+        if (L.eff[s] == QCS_MODE_FP32) {
+            // a batched plain-FP32 GEMM reads the gathered operands of the whole
+            // group and keeps a split-K partial buffer per instance, at the end
+            // of its workspace
+            maxA = std::max(maxA, st.m * st.k * gb);
+            maxB = std::max(maxB, st.k * st.n * gb);
+            gemm = std::max(gemm, gemm_workspace_bytes(QCS_MODE_FP32, st.m, st.n, st.k, h->num_sms,
+                                                       0) +
+                                      (size_t)(gb - 1) * kSplitKBytes);
+        } else {
+            // an emulated step gathers one instance at a time; its planes and
+            // descriptors hold the whole group
+            maxA = std::max(maxA, st.m * st.k);
+            maxB = std::max(maxB, st.k * st.n);
+            gemm = std::max(gemm, gemm_workspace_bytes(
+                                      L.eff[s], st.m, st.n, st.k, h->num_sms,
+                                      gemm_splits(h, fwd_op(st.direct_a), fwd_op(st.direct_b),
+                                                  st.m, st.n, st.k),
+                                      (int)gb));
+        }
         if (backward) {
-            gemm = std::max(gemm, gemm_workspace_bytes(effective_mode(h, st.mode, QCS_OP_N,
-                                                                      QCS_OP_C, st.m, st.k, st.n),
-                                                       st.m, st.k, st.n, h->num_sms, h->tc_splits));
-            gemm = std::max(gemm, gemm_workspace_bytes(effective_mode(h, st.mode, QCS_OP_C,
-                                                                      QCS_OP_N, st.k, st.n, st.m),
-                                                       st.k, st.n, st.m, h->num_sms, h->tc_splits));
+            gemm = std::max(gemm, gemm_workspace_bytes(
+                                      effective_mode(h, st.mode, QCS_OP_N, QCS_OP_C, st.m, st.k,
+                                                     st.n),
+                                      st.m, st.k, st.n, h->num_sms,
+                                      gemm_splits(h, QCS_OP_N, QCS_OP_C, st.m, st.k, st.n)));
+            gemm = std::max(gemm, gemm_workspace_bytes(
+                                      effective_mode(h, st.mode, QCS_OP_C, QCS_OP_N, st.k, st.n,
+                                                     st.m),
+                                      st.k, st.n, st.m, h->num_sms,
+                                      gemm_splits(h, QCS_OP_C, QCS_OP_N, st.k, st.n, st.m)));
         }
     }
     L.inter_off.resize(ns);
@@ -402,6 +431,45 @@ int step_instance(const Ctx &c, int s, int inst, int g) {
                            nullptr);
 }
 
+// One emulated step for the G instances of a group: per instance the
+// operand views (mapped operands are read through their maps or gathered
+// inside the GEMM sequence, one instance at a time), then run_cgemm_group:
+// statistics, selection and split per instance, one tensor-core launch per
+// kind over the tiles of all G instances.
+int step_grouped(const Ctx &c, int s, int inst0, int G) {
+    const qcs_step_t &st = c.t->steps[s];
+    float2 *bufA = reinterpret_cast<float2 *>(c.ws + c.L.bufA);
+    float2 *bufB = reinterpret_cast<float2 *>(c.ws + c.L.bufB);
+    const int opA = fwd_op(st.direct_a), opB = fwd_op(st.direct_b);
+    const int64_t lda = opA == QCS_OP_T ? st.k : st.m, ldb = opB == QCS_OP_T ? st.n : st.k;
+    std::vector<OperandView> va(G), vb(G);
+    const int ids[2] = {st.a, st.b};
+    const int direct[2] = {st.direct_a, st.direct_b};
+    const qcs_gather_t *maps[2] = {&st.map_a, &st.map_b};
+    const int64_t lds[2] = {lda, ldb};
+    float2 *bufs[2] = {bufA, bufB};
+    for (int o = 0; o < 2; ++o) {
+        const int id = ids[o];
+        const bool whole = id >= c.t->n_leaves && whole_permutation(*maps[o], c.size_of[id]);
+        for (int g = 0; g < G; ++g) {
+            OperandView &v = (o == 0 ? va : vb)[g];
+            v.X = tensor_ptr(c, id, inst0 + g, g);
+            if (direct[o] != -1) {
+                v.ld = lds[o];
+                continue;
+            }
+            v.map = maps[o];
+            v.flat = whole ? c.size_of[id] : 0;
+            v.buf = bufs[o];
+            if (c.info && !whole) c.info->gather_count++;
+        }
+    }
+    count_gemm(c, c.L.eff[s], st.m, st.n, st.k, G);
+    return run_cgemm_group(c.h, c.ws + c.L.gemm, c.L.eff[s], opA, opB, st.m, st.n, st.k,
+                           make_float2(1.f, 0.f), va.data(), vb.data(), G, make_float2(0.f, 0.f),
+                           inter_ptr(c, s), st.m, st.m * st.n, nullptr, nullptr);
+}
+
 // One batched step for the G instances of a group: batched gathers, one
 // batched plain-FP32 GEMM launch.
 int step_batched(const Ctx &c, int s, int inst0, int G) {
@@ -452,7 +520,9 @@ int forward_group(const Ctx &c, int inst0, int G, double *d_out) {
     const int ns = c.t->n_steps;
     for (int s = 0; s < c.L.P; ++s) {
         if (G > 1) {
-            if (int r = step_batched(c, s, inst0, G)) return r;
+            if (int r = (c.L.eff[s] == QCS_MODE_FP32 ? step_batched(c, s, inst0, G)
+                                                     : step_grouped(c, s, inst0, G)))
+                return r;
         } else if (int r = step_instance(c, s, inst0, 0)) {
             return r;
         }

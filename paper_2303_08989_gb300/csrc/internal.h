@@ -178,11 +178,13 @@ cudaError_t launch_set_desc(qcs_gemm_desc_t *desc, int mode, cudaStream_t s);
 // (-hi.im, hi.re, hi.im, lo.re, lo.im).  plane_off: element offset of row 0
 // in every plane (instance g of a group of equal-shape GEMMs writes its rows
 // after those of instances 0 .. g-1); elements are those of the kind the
-// descriptor selected, so the offset holds for every kind.
+// descriptor selected.  planes32 (not NULL): where a TF32 selection writes
+// instead of ``planes`` -- a group whose instances may select different
+// kinds keeps the 2-byte and 4-byte planes in separate regions.
 cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
                          int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
                          void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
-                         int planes6 = 0, int64_t plane_off = 0);
+                         int planes6 = 0, int64_t plane_off = 0, void *planes32 = nullptr);
 
 // The split stage reading its operand through a gather map (the reshape of
 // a contraction folded into the split pass): op(X) is the rows x cols
@@ -197,7 +199,8 @@ bool split_gather_supported(int which, int rank, const int64_t *dims, const int6
 cudaError_t launch_split_gather(const qcs_gemm_desc_t *desc, int which, int rank,
                                 const int64_t *dims, const int64_t *strides, const float2 *src,
                                 int64_t rows, void *planes, int64_t pitch, int64_t plane_stride,
-                                cudaStream_t s, int planes6 = 0, int64_t plane_off = 0);
+                                cudaStream_t s, int planes6 = 0, int64_t plane_off = 0,
+                                void *planes32 = nullptr);
 cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
                            const float2 *in, float2 *out, int64_t *stats_partials, int gstats,
                            cudaStream_t s, const CopyBatch &cb = CopyBatch{});
@@ -214,11 +217,15 @@ cudaError_t launch_seed_grad(const double *g, const int64_t *index, float2 *grad
 
 // ---- shared with the executor (capi.cu) ------------------------------------
 int effective_mode(qcs_handle_t h, int mode, int opA, int opB, int64_t m, int64_t n, int64_t k);
+// K-range setting for a GEMM of this shape: forced, tuned, or 0 (per-shape rule).
+int gemm_splits(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k);
 // Time the candidate modes of one shape (qcs_autotune_gemm without validation).
 int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k, int reps,
                qcs_tune_entry_t *out);
-// ``splits``: the handle's K-range setting (0 = chosen per shape).
-size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits);
+// ``splits``: the handle's K-range setting (0 = chosen per shape); ``G``:
+// equal-shape GEMMs run as one group (run_cgemm_group).
+size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits,
+                            int G = 1);
 // ``bt``: a batch of equal-shape GEMMs (plain FP32 only; UNSUPPORTED otherwise).
 int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n, int64_t k,
               float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta,
@@ -228,9 +235,10 @@ int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
 // An operand of run_cgemm_views: the column-major matrix X (leading
 // dimension ld, the GEMM's op applied), or -- when ``map`` is set -- op(X)
 // (op must be N) read through that gather map from the tensor X, whose
-// ``flat`` elements the map permutes as a whole.  ``buf`` (room for the
-// gathered matrix) receives op(X) when a kernel needs it as a matrix: the
-// FP32 path, or a split that cannot read through the map.
+// ``flat`` elements the map permutes as a whole (``flat`` = 0: the map reads
+// part of X, for instance one slice, and op(X) is always gathered).  ``buf``
+// (room for the gathered matrix) receives op(X) when a kernel needs it as a
+// matrix: the FP32 path, or a split that cannot read through the map.
 struct OperandView {
     const float2 *X = nullptr;
     int64_t ld = 0;
@@ -247,6 +255,18 @@ int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                     int64_t k, float2 alpha, const OperandView &A, const OperandView &B,
                     float2 beta, float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out,
                     const qcs_gemm_desc_t *d_desc_in, const GemmBatch &bt = GemmBatch{});
+// G equal-shape emulated GEMMs as one group (the instances of a contraction
+// step): instance g reads A[g], B[g] and writes C + g c_stride.  Per instance
+// the gathers, statistics, selection (its own descriptor) and split; then one
+// tensor-core launch per kind over the tiles of every instance (each unit
+// runs only if its instance selected that kind), and for AUTO the FP32
+// candidate of each instance, gated by its descriptor.  G = 1 is
+// run_cgemm_views.  ``ws``: gemm_workspace_bytes(..., G) bytes.
+int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n,
+                    int64_t k, float2 alpha, const OperandView *A, const OperandView *B, int G,
+                    float2 beta, float2 *C, int64_t ldc, int64_t c_stride,
+                    qcs_gemm_desc_t *d_desc_out, const qcs_gemm_desc_t *d_desc_in,
+                    const GemmBatch &bt = GemmBatch{});
 
 // ---- GEMM launchers -------------------------------------------------------
 // Plain FP32 SIMT CGEMM (runs only when desc->mode == FP32, or always when

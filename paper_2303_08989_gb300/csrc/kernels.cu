@@ -571,7 +571,7 @@ __device__ __forceinline__ void split_value(int mode, float xs, uint32_t &hi, ui
 __global__ void __launch_bounds__(256, 8) split_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int which, const float2 *__restrict__ X, int64_t sr,
     int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad, void *planes,
-    int64_t pitch, int64_t plane_stride, int planes6, int64_t plane_off) {
+    int64_t pitch, int64_t plane_stride, int planes6, int64_t plane_off, void *planes32) {
     const int mode = desc->mode;
     if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
     const int s = (mode == QCS_MODE_FP16X_SCALED) ? (which == 0 ? desc->sA : desc->sB) : 0;
@@ -642,7 +642,8 @@ __global__ void __launch_bounds__(256, 8) split_kernel(
         // plane_stride is even (K_pad is a multiple of 32), so every plane has
         // the alignment of the first
         if (mode == QCS_MODE_TF32X) {
-            uint32_t *p = static_cast<uint32_t *>(planes) + plane_off + r * pitch + c;
+            uint32_t *p = static_cast<uint32_t *>(planes32 ? planes32 : planes) + plane_off +
+                          r * pitch + c;
             const bool vec = two && ((reinterpret_cast<uintptr_t>(p) & 7u) == 0);
 #pragma unroll
             for (int pl = 0; pl < 5; ++pl) {
@@ -680,12 +681,12 @@ __global__ void __launch_bounds__(256, 8) split_kernel(
 cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
                          int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
                          void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
-                         int planes6, int64_t plane_off) {
+                         int planes6, int64_t plane_off, void *planes32) {
     if (R_pad <= 0 || K_pad <= 0) return cudaSuccess;
     dim3 grid((unsigned)((K_pad + kSplitC - 1) / kSplitC), (unsigned)((R_pad + kSplitR - 1) / kSplitR));
     if (grid.y > 65535u) return cudaErrorInvalidValue;
     split_kernel<<<grid, 256, 0, s>>>(desc, which, X, sr, sc, conj, R, K, R_pad, K_pad, planes,
-                                      pitch, plane_stride, planes6, plane_off);
+                                      pitch, plane_stride, planes6, plane_off, planes32);
     return cudaGetLastError();
 }
 
@@ -735,6 +736,7 @@ struct SplitOut {
     int64_t plane_stride;
     int planes6;  // the five-plane op(B) layout of the GEMM path
     int64_t off;  // element offset of this operand's rows in every plane
+    void *planes32;  // not NULL: the planes of a TF32 selection (else ``planes``)
 };
 
 __device__ __forceinline__ int64_t batch_in(const CopyParams &P) {
@@ -871,7 +873,8 @@ __global__ void __launch_bounds__(256, 6) copy_tiled_kernel(CopyParams P,
                         nv = 4;
                     }
                     if (mode == QCS_MODE_TF32X) {
-                        uint32_t *p = static_cast<uint32_t *>(so.planes) + so.off + o;
+                        uint32_t *p =
+                            static_cast<uint32_t *>(so.planes32 ? so.planes32 : so.planes) + so.off + o;
                         for (int pl = 0; pl < nv; ++pl) p[pl * ps] = v[pl];
                     } else {
                         uint16_t *p = static_cast<uint16_t *>(so.planes) + so.off + o;
@@ -1122,14 +1125,14 @@ bool split_gather_supported(int which, int rank, const int64_t *dims, const int6
 cudaError_t launch_split_gather(const qcs_gemm_desc_t *desc, int which, int rank,
                                 const int64_t *dims, const int64_t *strides, const float2 *src,
                                 int64_t rows, void *planes, int64_t pitch, int64_t plane_stride,
-                                cudaStream_t s, int planes6, int64_t plane_off) {
+                                cudaStream_t s, int planes6, int64_t plane_off, void *planes32) {
     CopyParams P;
     if (!split_gather_params(which, rank, dims, strides, rows, pitch, P))
         return cudaErrorNotSupported;
     const int64_t blocks = finish_tiled(P);
     if (blocks == 0) return cudaSuccess;
     if (blocks > INT32_MAX) return cudaErrorInvalidValue;
-    SplitOut so{desc, which, planes, plane_stride, planes6, plane_off};
+    SplitOut so{desc, which, planes, plane_stride, planes6, plane_off, planes32};
     copy_tiled_kernel<true><<<dim3((unsigned)blocks, 1), 256, 0, s>>>(P, src, nullptr, 0, so);
     return cudaGetLastError();
 }

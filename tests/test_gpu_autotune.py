@@ -133,3 +133,35 @@ def test_autotuned_tree_matches_oracle():
         assert np.max(np.abs(a - ref)) <= 1e-5 * np.max(np.abs(ref))
     finally:
         hd.close()
+
+
+def test_autotune_measures_the_k_range_count():
+    """One output tile and a long k: the tuner also times the faster emulated
+    candidate at several K-range counts and records the fastest in
+    ``splits``; under the tuned rule that count runs.  A table entry's count
+    round-trips through qcs_get_tuning / qcs_set_tuning, is validated, and
+    results stay at the FP32 level against the FP64 oracle."""
+    need_gpu()
+    q = lib()
+    m, n, k = 128, 96, 4096
+    hd = q.Handle(tol=0.1, size_rule=False)
+    try:
+        e = hd.autotune_gemm(m, n, k, reps=2)
+        assert 1 <= e["splits"] <= 16
+        big = hd.autotune_gemm(4096, 2048, 64, reps=1)  # 512 tiles >= 2 x 152: not measured
+        assert big["splits"] == 0
+        A = qi.cgemm_operand(m, k, 0, seed=(5, 1))
+        B = qi.cgemm_operand(k, n, 0, seed=(5, 2))
+        exact = oracle.cgemm(0, 0, m, n, k, 1.0, A, B)
+        hd.set_size_rule(q.SIZE_RULE_TUNED)
+        for splits in (e["splits"], 3, 1):
+            entry = dict(e, splits=splits, best="auto")
+            hd.set_tuning([entry])
+            assert [x["splits"] for x in hd.tuning() if x["k"] == k] == [splits]
+            got, d = _gemm(hd, "auto", A, B, m, n, k)
+            assert d[0] == q.MODE_FP16X
+            assert oracle.rel_fro_error(got, exact) < 1e-6, splits
+        with pytest.raises(q.QcsError):
+            hd.set_tuning([dict(e, splits=17)])
+    finally:
+        hd.close()

@@ -388,3 +388,58 @@ def test_split_through_the_map_equals_gather_then_split(mode):
         hd.close()
     # the open result is ordered like numpy C order over the output labels (I, R)
     assert np.array_equal(got.reshape(d[I], d[R]), want)
+
+
+@pytest.mark.parametrize("splits", [1, 3])
+def test_grouped_emulated_step_with_a_mode_per_instance(splits):
+    """One emulated step over a group of 4 instances whose operands select
+    four different modes (FP16X, TF32X, FP16X_SCALED and, for an operand with
+    a NaN, FP32): the grouped tensor-core launches run only the units of the
+    instances that selected their kind, with each instance's scales, the
+    FP32 candidates and the split-K reduction are gated per instance, and
+    every instance equals, bit for bit, its result when run alone."""
+    need_gpu()
+    tn = _tn()
+    q = lib()
+    B_, I, K, J = tn.BATCH, 0, 1, 2
+    d = {B_: 4, I: 256, K: 192, J: 160}
+    rng = np.random.default_rng(31)
+
+    def normal(shape):
+        return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+    a = normal((4, d[I], d[K]))  # [b, i, k]
+    a[1] *= 2.0 ** rng.integers(-40, 41, size=(d[I], d[K]))
+    a[2] *= 2.0 ** -30
+    a[3, 5, 7] = complex(np.nan, 0)
+    b = normal((d[K], d[J]))
+    # leaves store their labels first-index-fastest
+    L0 = tn.Leaf(np.ascontiguousarray(a.transpose(2, 1, 0).ravel()).astype(np.complex64),
+                 [B_, I, K], [d[B_], d[I], d[K]])
+    L1 = tn.Leaf(np.ascontiguousarray(b.T.ravel()).astype(np.complex64), [K, J], [d[K], d[J]])
+    net = tn.Network([L0, L1], [I, J], d, batch=4)
+    plan = tn.build_plan(net, [(0, 1)], mode=q.MODE_AUTO)
+    assert plan.n_instances == 4 and plan.steps[0].direct_a == -1
+    hd = q.Handle(tol=1e-3, size_rule=False)
+    try:
+        hd.set_tc_splits(splits)
+        hd.auto_counts()
+        one, _ = _run(hd, plan)
+        assert hd.auto_counts() == {"auto": 0, "fp16x": 1, "fp16x_scaled": 1, "tf32x": 1,
+                                    "fp32": 1, "bf16x3": 0}
+        hd.set_instance_batch(4)
+        grouped, info = _run(hd, plan)
+        assert info.gemm_count == 4
+    finally:
+        hd.close()
+    np.testing.assert_array_equal(grouped, one)  # NaN where NaN
+    a64 = a.astype(np.complex64).astype(np.complex128)
+    b64 = b.astype(np.complex64).astype(np.complex128)
+    for inst in range(4):
+        got = one[inst].reshape(d[I], d[J])
+        if inst == 3:
+            assert np.isnan(got[5]).all() and np.isfinite(np.delete(got, 5, axis=0)).all()
+            got, want = np.delete(got, 5, axis=0), np.delete(a64[3], 5, axis=0) @ b64
+        else:
+            want = a64[inst] @ b64
+        assert oracle.rel_fro_error(got, want) < (1e-5 if inst == 3 else 2e-6), inst
