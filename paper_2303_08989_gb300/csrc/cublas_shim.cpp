@@ -51,9 +51,21 @@ std::atomic<long long> g_taken{0}, g_passed{0};
 std::mutex g_lock;
 std::map<cudaStream_t, qcs_handle_t> g_handles;
 
+// cuBLAS's own definition of ``name``.  RTLD_NEXT finds it when cuBLAS is
+// in the global scope; an application that loads cuBLAS as the dependency of
+// a library opened with RTLD_LOCAL (Python extensions) keeps it out of that
+// scope, so the already-loaded cuBLAS is then looked up by its soname.
 template <typename F>
 F next_symbol(const char *name) {
-    return reinterpret_cast<F>(dlsym(RTLD_NEXT, name));
+    if (void *p = dlsym(RTLD_NEXT, name)) return reinterpret_cast<F>(p);
+    static void *lib = [] {
+        for (const char *so : {"libcublas.so.13", "libcublas.so.12", "libcublas.so"})
+            if (void *h = dlopen(so, RTLD_NOW | RTLD_LOCAL | RTLD_NOLOAD)) return h;
+        for (const char *so : {"libcublas.so.13", "libcublas.so.12", "libcublas.so"})
+            if (void *h = dlopen(so, RTLD_NOW | RTLD_LOCAL)) return h;
+        return static_cast<void *>(nullptr);
+    }();
+    return lib ? reinterpret_cast<F>(dlsym(lib, name)) : nullptr;
 }
 
 // -1: pass every call to cuBLAS; otherwise the qcs mode.
