@@ -58,6 +58,10 @@ def parse():
                    help="slices of the 30-qubit network timed per mode")
     p.add_argument("--no-sweep", action="store_true", help="skip the CGEMM-sweep leg")
     p.add_argument("--sweep-sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192, 16384])
+    p.add_argument("--profile", choices=["slice", "gather"], default=None,
+                   help="run one workload for an ncu capture (NVTX range 'measure') and exit: "
+                        "'slice' one slice of the 30-qubit network (AUTO-t, tuned rule), "
+                        "'gather' a random permutation of 2^26 elements (26 binary indices)")
     p.add_argument("--instance-batch", type=int, default=4,
                    help="contraction instances per group (plain-FP32 steps batched)")
     return p.parse_args()
@@ -243,6 +247,52 @@ def run_reference(args, rank: int):
 # our arm
 # ---------------------------------------------------------------------------
 
+def profile_run(args):
+    """One workload between torch.cuda.nvtx range 'measure' (after one
+    untimed run), for ``ncu --nvtx --nvtx-include "measure/"``; prints a
+    short JSON line with the CUDA-event time of the measured run."""
+    import torch
+
+    import paper_2303_08989_gb300 as q
+    import paper_2303_08989_gb300.tn as tn
+    import qcs_inputs as qi
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.profile == "slice":
+        circ = qi.random_grid_circuit(5, 6, 14, seed=0)
+        bits = qi.random_bitstrings(30, 1, seed=1)
+        plan = tn.plan_circuit(circ, bits, seed=2, n_slices=6, mode=q.MODE_AUTO)
+        cp = tn.CompiledPlan(plan, device=dev)
+        cp.tree.n_instances = 1  # one slice
+        h = q.Handle(tol=args.tol, size_rule=q.SIZE_RULE_TUNED)
+        cp.autotune(h)
+        run = lambda: cp.forward(h)
+        what = "one slice of the 5x6 depth-14 network, AUTO-%g, tuned rule" % args.tol
+    else:
+        r = 26
+        g = torch.Generator(device="cpu").manual_seed(5)
+        perm = torch.randperm(r, generator=g).tolist()
+        src = torch.empty(2 ** r, dtype=torch.complex64, device=dev)
+        out = torch.empty_like(src)
+        h = q.Handle()
+        strides = [2 ** p for p in perm]
+        run = lambda: q.permute(h, src, [2] * r, strides, out=out)
+        what = "permutation of 2^26 complex64 (26 binary indices, seeded)"
+    run()
+    torch.cuda.synchronize()
+    with torch.cuda.nvtx.range("measure"):
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+    h.sync()
+    print(json.dumps({"profile": args.profile, "workload": what, "ms": e0.elapsed_time(e1)}),
+          flush=True)
+    h.close()
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -250,6 +300,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.profile:
+        profile_run(args)
         return
 
     import numpy as np
