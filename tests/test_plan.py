@@ -103,3 +103,27 @@ def test_open_network_sliced_with_bitstring_gather():
     assert plan.n_instances == 4 and plan.n_slots == 1 and plan.out_size == 12
     got = run(plan, _leaves(plan))[0]
     np.testing.assert_allclose(got, oracle.sv_amplitudes(circ, bits), atol=1e-6)
+
+
+def test_best_greedy_order_is_the_cheapest_seed():
+    """best_greedy_order returns the order (and slicing) with the fewest
+    flops per instance among its seeds; order_cost agrees with the plan's
+    own count; the chosen plan still contracts to the oracle's amplitudes."""
+    circ = qi.random_grid_circuit(3, 4, 8, seed=0)
+    bits = qi.random_bitstrings(12, 2, seed=1)
+    net = tn.circuit_network(circ, bits)
+    skip = [tn.BATCH]
+    costs = {}
+    for seed in range(8):
+        order = tn.greedy_order(net, seed=seed, skip=skip)
+        sliced = tn.choose_slices(net, order, n_labels=2, skip=skip)
+        flops, big = tn.order_cost(net, order, skip + sliced)
+        plan = tn.build_plan(net, order, sliced)
+        assert flops == pytest.approx(plan.flops) and big == plan.max_log2_size
+        costs[seed] = (flops, big, seed)
+    order, sliced, seed = tn.best_greedy_order(net, range(8), skip=skip, n_slices=2)
+    assert costs[seed] == min(costs.values())
+    plan = tn.plan_circuit(circ, bits, seed=0, n_slices=2, trials=8)
+    assert plan.flops == pytest.approx(costs[seed][0])
+    got = run(plan, _leaves(plan))[:, 0]
+    np.testing.assert_allclose(got, oracle.sv_amplitudes(circ, bits), atol=1e-6)
