@@ -58,10 +58,11 @@ def parse():
                    help="slices of the 30-qubit network timed per mode")
     p.add_argument("--no-sweep", action="store_true", help="skip the CGEMM-sweep leg")
     p.add_argument("--sweep-sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192, 16384])
-    p.add_argument("--profile", choices=["slice", "gather"], default=None,
+    p.add_argument("--profile", choices=["slice", "slice_seed2", "gather"], default=None,
                    help="run one workload for an ncu capture (NVTX range 'measure') and exit: "
-                        "'slice' one slice of the 30-qubit network (AUTO-t, tuned rule), "
-                        "'gather' a random permutation of 2^26 elements (26 binary indices)")
+                        "'slice' one group of 16 slices of the 30-qubit network in the cheapest "
+                        "of 64 greedy orders (AUTO-t, tuned rule), 'slice_seed2' one slice in the "
+                        "order of seed 2, 'gather' a random permutation of 2^26 elements")
     p.add_argument("--instance-batch", type=int, default=16,
                    help="contraction instances per group (plain-FP32 steps batched)")
     return p.parse_args()
@@ -260,16 +261,23 @@ def profile_run(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if args.profile == "slice":
+    if args.profile in ("slice", "slice_seed2"):
         circ = qi.random_grid_circuit(5, 6, 14, seed=0)
         bits = qi.random_bitstrings(30, 1, seed=1)
-        plan = tn.plan_circuit(circ, bits, seed=2, n_slices=6, mode=q.MODE_AUTO)
+        if args.profile == "slice":
+            plan = tn.plan_circuit(circ, bits, seed=0, n_slices=6, mode=q.MODE_AUTO, trials=64)
+            ni, what = 16, ("16 slices (one group) of the 5x6 depth-14 network in the cheapest "
+                            "of 64 greedy orders, AUTO-%g, tuned rule" % args.tol)
+        else:
+            plan = tn.plan_circuit(circ, bits, seed=2, n_slices=6, mode=q.MODE_AUTO)
+            ni, what = 1, ("one slice of the 5x6 depth-14 network in the greedy order of "
+                           "seed 2, AUTO-%g, tuned rule" % args.tol)
         cp = tn.CompiledPlan(plan, device=dev)
-        cp.tree.n_instances = 1  # one slice
+        cp.tree.n_instances = ni
         h = q.Handle(tol=args.tol, size_rule=q.SIZE_RULE_TUNED)
+        h.set_instance_batch(ni)
         cp.autotune(h)
         run = lambda: cp.forward(h)
-        what = "one slice of the 5x6 depth-14 network, AUTO-%g, tuned rule" % args.tol
     else:
         r = 26
         g = torch.Generator(device="cpu").manual_seed(5)
