@@ -1570,6 +1570,65 @@ __global__ void __launch_bounds__(256) cgemm_perelem_kernel(
     }
 }
 
+// Small k (<= KMAX <= 16) with both output sides large -- the contraction
+// of a tensor with a gate or a few-index tensor: a block owns R rows
+// (R = 256 / lanes, the rows of op(A) kept in registers) and a chunk of
+// kSmallKCols columns, whose op(B) values it stages in shared memory; each
+// thread then produces the outputs of its row for every lanes-th column of
+// the chunk.  C is written column by column, R consecutive rows at a time.
+constexpr int kSmallKCols = 64;
+
+template <int KMAX>
+__global__ void __launch_bounds__(256) cgemm_smallk_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int k,
+    int rows, float2 alpha, const float2 *__restrict__ A, int64_t lda,
+    const float2 *__restrict__ B, int64_t ldb, float2 beta, float2 *__restrict__ C, int64_t ldc,
+    GemmBatch bt) {
+    if (desc && desc->mode != QCS_MODE_FP32) return;
+    A += blockIdx.z * bt.sA;
+    B += blockIdx.z * bt.sB;
+    C += blockIdx.z * bt.sC;
+    __shared__ float2 sb[kSmallKCols][KMAX + 1];
+    const int64_t j0 = (int64_t)blockIdx.y * kSmallKCols;
+    const int jn = (int)min((int64_t)kSmallKCols, n - j0);
+    for (int t = threadIdx.x; t < kSmallKCols * KMAX; t += blockDim.x) {
+        const int jj = t / KMAX, l = t - jj * KMAX;
+        float2 v = make_float2(0.f, 0.f);
+        if (l < k && jj < jn) v = ld_op(B, opB, l, j0 + jj, ldb);
+        sb[jj][l] = v;
+    }
+    const int r = threadIdx.x % rows, lane_c = threadIdx.x / rows, lanes = blockDim.x / rows;
+    const int64_t i = (int64_t)blockIdx.x * rows + r;
+    float2 a[KMAX];
+#pragma unroll
+    for (int l = 0; l < KMAX; ++l)
+        a[l] = (i < m && l < k) ? ld_op(A, opA, i, l, lda) : make_float2(0.f, 0.f);
+    __syncthreads();
+    if (i >= m) return;
+    const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
+    for (int jj = lane_c; jj < jn; jj += lanes) {
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int l = 0; l < KMAX; ++l) {
+            const float2 b = sb[jj][l];
+            sr = fmaf(a[l].x, b.x, sr);
+            sr = fmaf(-a[l].y, b.y, sr);
+            si = fmaf(a[l].x, b.y, si);
+            si = fmaf(a[l].y, b.x, si);
+        }
+        float2 o;
+        o.x = alpha.x * sr - alpha.y * si;
+        o.y = alpha.x * si + alpha.y * sr;
+        float2 *dst = C + i + (j0 + jj) * ldc;
+        if (use_beta) {
+            const float2 c = *dst;
+            o.x += beta.x * c.x - beta.y * c.y;
+            o.y += beta.x * c.y + beta.y * c.x;
+        }
+        *dst = o;
+    }
+}
+
 // Split-K for small m*n with long k (the end of a contraction tree reduces
 // large tensors to a few numbers): warp w handles output o = w mod (m n) over
 // the w-th k chunk; lanes stride along k, a warp shuffle reduces, and the
@@ -1714,6 +1773,25 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
                                                           lda, B, ldb, beta, C, ldc, bt);
         }
         return cudaGetLastError();
+    }
+    if (k <= 16 && mn > 4096 && m <= INT32_MAX) {
+        // rows per block: all of m up to 256, at least a warp
+        const int rows = m >= 256 ? 256 : (m <= 32 ? 32 : (m <= 64 ? 64 : (m <= 128 ? 128 : 256)));
+        const int64_t gy = (n + kSmallKCols - 1) / kSmallKCols;
+        const int64_t gx = (m + rows - 1) / rows;
+        if (gy <= 65535 && gx <= INT32_MAX) {
+            dim3 grid((unsigned)gx, (unsigned)gy, G);
+            if (k <= 4)
+                cgemm_smallk_kernel<4><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, (int)k, rows, alpha,
+                                                            A, lda, B, ldb, beta, C, ldc, bt);
+            else if (k <= 8)
+                cgemm_smallk_kernel<8><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, (int)k, rows, alpha,
+                                                            A, lda, B, ldb, beta, C, ldc, bt);
+            else
+                cgemm_smallk_kernel<16><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, (int)k, rows,
+                                                             alpha, A, lda, B, ldb, beta, C, ldc, bt);
+            return cudaGetLastError();
+        }
     }
     const bool perelem = (k <= 16) || (mn <= 4096);
     if (perelem || m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) {
