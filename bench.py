@@ -63,6 +63,10 @@ def parse():
                         "'slice' one group of 16 slices of the 30-qubit network in the cheapest "
                         "of 64 greedy orders (AUTO-t, tuned rule), 'slice_seed2' one slice in the "
                         "order of seed 2, 'gather' a random permutation of 2^26 elements")
+    p.add_argument("--tuning-file", default=None,
+                   help="with --profile slice*: load the size-rule tuning table from this JSON "
+                        "file if it exists, else measure it and write it there (a run under ncu "
+                        "would measure distorted times: ncu slows every launch)")
     p.add_argument("--instance-batch", type=int, default=16,
                    help="contraction instances per group (plain-FP32 steps batched)")
     return p.parse_args()
@@ -276,7 +280,14 @@ def profile_run(args):
         cp.tree.n_instances = ni
         h = q.Handle(tol=args.tol, size_rule=q.SIZE_RULE_TUNED)
         h.set_instance_batch(ni)
-        cp.autotune(h)
+        if args.tuning_file and os.path.exists(args.tuning_file):
+            with open(args.tuning_file) as f:
+                h.set_tuning(json.load(f))
+        else:
+            cp.autotune(h)
+            if args.tuning_file:
+                with open(args.tuning_file, "w") as f:
+                    json.dump(h.tuning(), f)
         run = lambda: cp.forward(h)
     else:
         r = 26
