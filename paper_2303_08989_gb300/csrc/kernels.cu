@@ -566,6 +566,23 @@ __device__ __forceinline__ void split_value(int mode, float xs, uint32_t &hi, ui
     }
 }
 
+// Multiplication by 2^s as one or two exact power-of-two factors: x * m1 * m2
+// is the correctly rounded x 2^s, the value ldexpf(x, s) returns, at the cost
+// of one or two multiplications.  s = 14 - e_max lies in [-113, 163]: one
+// factor up to 2^127, two (each exact: the operand only grows) above.
+struct Pow2Scale {
+    float m1 = 1.f, m2 = 1.f;
+};
+__device__ __forceinline__ Pow2Scale pow2_scale(int s) {
+    Pow2Scale p;
+    const int s1 = s > 127 ? 127 : (s < -126 ? -126 : s);
+    p.m1 = __int_as_float((127 + s1) << 23);
+    const int s2 = s - s1;  // 0 unless s > 127 (s < -126 does not occur)
+    p.m2 = __int_as_float((127 + (s2 > 127 ? 127 : s2)) << 23);
+    return p;
+}
+__device__ __forceinline__ float apply_scale(float x, Pow2Scale p) { return (x * p.m1) * p.m2; }
+
 // planes6: write op(B) as the five planes of the GEMM path (-hi.im, hi.re,
 // hi.im, lo.re, lo.im) instead of hi.re, hi.im, lo.re, lo.im.
 __global__ void __launch_bounds__(256, 8) split_kernel(
@@ -575,6 +592,7 @@ __global__ void __launch_bounds__(256, 8) split_kernel(
     const int mode = desc->mode;
     if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
     const int s = (mode == QCS_MODE_FP16X_SCALED) ? (which == 0 ? desc->sA : desc->sB) : 0;
+    const Pow2Scale ps2 = pow2_scale(s);
 
     __shared__ float2 tile[kSplitR][kSplitC + 1];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -618,7 +636,7 @@ __global__ void __launch_bounds__(256, 8) split_kernel(
         // hi/lo of re and im for columns c and c+1
         uint32_t hib[4], lob[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) split_value(mode, (s != 0) ? ldexpf(x[e], s) : x[e], hib[e], lob[e]);
+        for (int e = 0; e < 4; ++e) split_value(mode, (s != 0) ? apply_scale(x[e], ps2) : x[e], hib[e], lob[e]);
         const bool two = (c + 1 < K_pad);
         // x[0]/x[2] real, x[1]/x[3] imaginary parts of columns c, c+1; the
         // planes in the order written, two consecutive values each
@@ -782,10 +800,12 @@ __global__ void __launch_bounds__(256, 6) copy_tiled_kernel(CopyParams P,
                                                             float2 *__restrict__ out,
                                                             int accumulate, SplitOut so) {
     int mode = 0, scale = 0;
+    Pow2Scale pscale;
     if (SPLIT) {
         mode = so.desc->mode;
         if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
         if (mode == QCS_MODE_FP16X_SCALED) scale = so.which == 0 ? so.desc->sA : so.desc->sB;
+        pscale = pow2_scale(scale);
     } else if (P.gate && P.gate->mode != QCS_MODE_FP32) {
         return;
     }
@@ -852,8 +872,8 @@ __global__ void __launch_bounds__(256, 6) copy_tiled_kernel(CopyParams P,
                 const int64_t o = ro + sxo[tx] + syo[yl];
                 if (SPLIT) {
                     uint32_t h0, l0, h1, l1;
-                    split_value(mode, scale ? ldexpf(w.x, scale) : w.x, h0, l0);
-                    split_value(mode, scale ? ldexpf(w.y, scale) : w.y, h1, l1);
+                    split_value(mode, scale ? apply_scale(w.x, pscale) : w.x, h0, l0);
+                    split_value(mode, scale ? apply_scale(w.y, pscale) : w.y, h1, l1);
                     const int64_t ps = so.plane_stride;
                     const uint32_t sg = (mode == QCS_MODE_TF32X) ? 0x80000000u : 0x8000u;
                     uint32_t v[5];
@@ -872,13 +892,19 @@ __global__ void __launch_bounds__(256, 6) copy_tiled_kernel(CopyParams P,
                         v[3] = l1;
                         nv = 4;
                     }
+                    // unrolled over the five possible planes, so that v stays in
+                    // registers
                     if (mode == QCS_MODE_TF32X) {
                         uint32_t *p =
                             static_cast<uint32_t *>(so.planes32 ? so.planes32 : so.planes) + so.off + o;
-                        for (int pl = 0; pl < nv; ++pl) p[pl * ps] = v[pl];
+#pragma unroll
+                        for (int pl = 0; pl < 5; ++pl)
+                            if (pl < nv) p[pl * ps] = v[pl];
                     } else {
                         uint16_t *p = static_cast<uint16_t *>(so.planes) + so.off + o;
-                        for (int pl = 0; pl < nv; ++pl) p[pl * ps] = (uint16_t)v[pl];
+#pragma unroll
+                        for (int pl = 0; pl < 5; ++pl)
+                            if (pl < nv) p[pl * ps] = (uint16_t)v[pl];
                     }
                     continue;
                 }
