@@ -795,7 +795,7 @@ constexpr int kTilesPerBlock = 8;
 // after a barrier that every thread reaches only once it has finished
 // reading that buffer.
 template <bool SPLIT>
-__global__ void __launch_bounds__(256, 6) copy_tiled_kernel(CopyParams P,
+__global__ void __launch_bounds__(256, SPLIT ? 4 : 5) copy_tiled_kernel(CopyParams P,
                                                             const float2 *__restrict__ in,
                                                             float2 *__restrict__ out,
                                                             int accumulate, SplitOut so) {
@@ -845,15 +845,25 @@ __global__ void __launch_bounds__(256, 6) copy_tiled_kernel(CopyParams P,
     const bool yok = (y0 + tx) < P.py;
     const bool xok = (x0 + tx) < P.px;
     const int nt = (int)min((int64_t)kTilesPerBlock, P.rest - rb);
+    // this thread's four read and four write offsets within a tile, the same
+    // for every rest index: kept in registers
+    int64_t rin[4], rout[4];
+    bool okin[4], okout[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int l = ty + 8 * r;
+        rin[r] = sxi[l] + syi[tx];
+        okin[r] = yok && x0 + l < P.px;
+        rout[r] = sxo[tx] + syo[l];
+        okout[r] = xok && y0 + l < P.py;
+    }
     // read: lanes along y (contiguous input)
     float2 v[4];
     auto load = [&](int t) {
         const int64_t ri = sr[t][0];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int xl = ty + 8 * r;
-            if (yok && x0 + xl < P.px) v[r] = in[ri + sxi[xl] + syi[tx]];
-        }
+        for (int r = 0; r < 4; ++r)
+            if (okin[r]) v[r] = in[ri + rin[r]];
     };
     load(0);
     for (int t = 0; t < nt; ++t) {
@@ -867,9 +877,9 @@ __global__ void __launch_bounds__(256, 6) copy_tiled_kernel(CopyParams P,
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int yl = ty + 8 * r;
-            if (xok && y0 + yl < P.py) {
+            if (okout[r]) {
                 float2 w = tile[buf][tx][yl];
-                const int64_t o = ro + sxo[tx] + syo[yl];
+                const int64_t o = ro + rout[r];
                 if (SPLIT) {
                     uint32_t h0, l0, h1, l1;
                     split_value(mode, scale ? apply_scale(w.x, pscale) : w.x, h0, l0);
