@@ -648,8 +648,9 @@ def _finite_or_none(x: float):
 def sweep_leg(args, q, torch, dev, rank):
     """The whole CGEMM sweep: m = n = k in ``args.sweep_sizes``, parts
     N(0,1) 2^e with e ~ U_int[-s, s] for s in {0, 8, 20, 40}; per point the
-    TFLOP/s of FP32 (SIMT), TF32X, FP16X, FP16X_SCALED and AUTO-t (t =
-    ``args.tol``, the paper's size rule on) forced on the same inputs, cuBLAS
+    TFLOP/s of FP32 (SIMT), TF32X, FP16X, FP16X_SCALED, AUTO-t (t =
+    ``args.tol``, the paper's size rule on) and AUTO-t under the size rule
+    measured for the shape (qcs_autotune_gemm) on the same inputs, cuBLAS
     CGEMM (torch, default math mode), the relative Frobenius error of each
     against the FP64 oracle on ``args.sample_rows`` output rows, and the mode
     the device-side selection picks at t in {0, 1e-3, 0.1, 0.5} (statistics
@@ -676,6 +677,7 @@ def sweep_leg(args, q, torch, dev, rank):
         return e0.elapsed_time(e1) / reps
 
     h = q.Handle(tol=args.tol, size_rule=True)
+    ht = q.Handle(tol=args.tol, size_rule=q.SIZE_RULE_TUNED)
     hsel = q.Handle(tol=0.0, size_rule=False)
     rows = args.sample_rows
     points = []
@@ -691,11 +693,14 @@ def sweep_leg(args, q, torch, dev, rank):
                 _, ref, _ = oracle_sample(A[:rows].cpu().numpy().astype(np.complex64),
                                           B.cpu().numpy(), n, rows)
             desc = torch.zeros(4, dtype=torch.int32, device=dev)
-            for mode in ("fp32", "tf32x", "fp16x", "fp16x_scaled", "auto"):
-                ms = timed(lambda: q.cgemm(h, A, B, C, mode=mode))
+            if s == 0:
+                ht.autotune_gemm(n, n, n, reps=3)  # the measured size rule for this shape
+            for mode in ("fp32", "tf32x", "fp16x", "fp16x_scaled", "auto", "auto_tuned"):
+                hh, mm = (ht, "auto") if mode == "auto_tuned" else (h, mode)
+                ms = timed(lambda: q.cgemm(hh, A, B, C, mode=mm))
                 entry = {"tflops": flops / (ms * 1e-3) / 1e12, "ms": ms}
-                if mode == "auto":
-                    q.cgemm(h, A, B, C, mode=mode, desc_out=desc)
+                if mm == "auto":
+                    q.cgemm(hh, A, B, C, mode=mm, desc_out=desc)
                     entry["selected"] = q.MODE_NAME[int(desc[0].item())]
                 if rank == 0:
                     got = C[:rows].cpu().numpy().astype(np.complex128)
@@ -719,10 +724,12 @@ def sweep_leg(args, q, torch, dev, rank):
             del A, B, C
             torch.cuda.empty_cache()
     h.close()
+    ht.close()
     hsel.close()
     return {"workload": "CGEMM m=n=k, column-major, alpha=1, beta=0; parts N(0,1)*2^e, "
-                        "e~U_int[-s,s] per real scalar; forced modes and AUTO-"
-                        f"{args.tol:g} with the paper's size rule",
+                        "e~U_int[-s,s] per real scalar; forced modes, AUTO-"
+                        f"{args.tol:g} with the paper's size rule and with the size rule "
+                        "measured on this GPU (auto_tuned)",
             "error_sample": f"{rows} output rows vs the FP64 oracle",
             "points": points}
 
