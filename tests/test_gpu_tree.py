@@ -183,6 +183,47 @@ def test_full_size_30_qubit_sliced_amplitudes_vs_fp64_golden(h, golden_dir):
     assert info.mode_count[0] > 0  # some GEMMs took the statistics-based selection
 
 
+def test_full_size_30_qubit_in_the_bench_configuration_vs_fp64_golden(golden_dir):
+    """The contraction as bench.py times it: the cheapest of 64 seeded greedy
+    orders, 6 sliced indices, instances in groups of 16 (grouped tensor-core
+    launches, batched FP32 steps), AUTO-0.1 under the measured size rule with
+    K ranges from the tuner; two bitstrings x 64 slices against the FP64
+    amplitudes of tests/golden, eagerly and replayed from a CUDA graph."""
+    import os
+
+    need_gpu()
+    tn = _tn()
+    q = lib()
+    bits_all, ref_all = _golden_amplitudes(os.path.join(golden_dir, "grid5x6_d14_amplitudes.txt"))
+    circ = qi.random_grid_circuit(5, 6, 14, seed=0)
+    bits, ref = bits_all[2:4], ref_all[2:4]
+    plan = tn.plan_circuit(circ, bits, seed=0, n_slices=6, mode=q.MODE_AUTO, trials=64)
+    assert plan.n_instances == 2 * 64 and plan.max_log2_size <= 25
+    hd = q.Handle(tol=0.1, size_rule=q.SIZE_RULE_TUNED)
+    try:
+        hd.set_instance_batch(16)
+        cp = tn.CompiledPlan(plan)
+        assert cp.autotune(hd, reps=2) > 0
+        eager = cp.forward(hd)
+        torch.cuda.synchronize()
+        hd.sync()
+        info = cp.last_info
+        g, out = cp.graph(hd)
+        out.zero_()
+        g.launch()
+        torch.cuda.synchronize()
+        hd.sync()
+        replay = out.cpu().numpy()
+        g.close()
+    finally:
+        hd.close()
+    a = eager.cpu().numpy()[:, 0]
+    assert np.array_equal(replay[:, 0], a)
+    assert oracle.fidelity(ref, a) >= 1 - 1e-5
+    assert np.all(np.abs(a - ref) <= 1e-4 * np.abs(ref)), (a, ref)
+    assert info.mode_count[q.MODE_FP32] > 0 and info.mode_count[q.MODE_FP32] < info.gemm_count
+
+
 @pytest.mark.parametrize("mode,n_slices", [("auto", 0), ("tf32x", 2)])
 def test_graph_replay_equals_eager(h, mode, n_slices):
     """qcs_tree_graph_*: the captured launch sequence replays to the same bits as
