@@ -57,11 +57,14 @@ def parse():
     p.add_argument("--tree-slices", type=int, default=16,
                    help="slices of the 30-qubit network timed per mode")
     p.add_argument("--no-sweep", action="store_true", help="skip the CGEMM-sweep leg")
+    p.add_argument("--greedy-trials", type=int, default=256,
+                   help="seeded greedy orders tried per network (the cheapest is contracted)")
     p.add_argument("--sweep-sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192, 16384])
     p.add_argument("--profile", choices=["slice", "slice_seed2", "gather", "gemm"], default=None,
                    help="run one workload for an ncu capture (NVTX range 'measure') and exit: "
                         "'slice' one group of 16 slices of the 30-qubit network in the cheapest "
-                        "of 64 greedy orders (AUTO-t, tuned rule), 'slice_seed2' one slice in the "
+                        "of --greedy-trials greedy orders (AUTO-t, tuned rule), 'slice_seed2' one "
+                        "slice in the "
                         "order of seed 2, 'gather' a random permutation of 2^26 elements, 'gemm' "
                         "ten qcs_cgemm calls of --gemm-shape in --mode")
     p.add_argument("--gemm-shape", type=int, nargs=3, default=[2048, 8192, 32],
@@ -272,9 +275,11 @@ def profile_run(args):
         circ = qi.random_grid_circuit(5, 6, 14, seed=0)
         bits = qi.random_bitstrings(30, 1, seed=1)
         if args.profile == "slice":
-            plan = tn.plan_circuit(circ, bits, seed=0, n_slices=6, mode=q.MODE_AUTO, trials=64)
+            plan = tn.plan_circuit(circ, bits, seed=0, n_slices=6, mode=q.MODE_AUTO,
+                                   trials=args.greedy_trials)
             ni, what = 16, ("16 slices (one group) of the 5x6 depth-14 network in the cheapest "
-                            "of 64 greedy orders, AUTO-%g, tuned rule" % args.tol)
+                            "of %d greedy orders, AUTO-%g, tuned rule"
+                            % (args.greedy_trials, args.tol))
         else:
             plan = tn.plan_circuit(circ, bits, seed=2, n_slices=6, mode=q.MODE_AUTO)
             ni, what = 1, ("one slice of the 5x6 depth-14 network in the greedy order of "
@@ -856,12 +861,13 @@ def tree_legs(args, q, torch, dev, rank):
                 ("auto_paper_rule", "auto", q.SIZE_RULE_PAPER, args.tol),
                 ("fp32", "fp32", q.SIZE_RULE_PAPER, 0.0)]
     # 30-qubit 5x6 grid, depth 14, sliced on 6 indices (64 slices), one bitstring,
-    # contracted in the cheapest of 64 seeded greedy orders
+    # contracted in the cheapest of --greedy-trials seeded greedy orders
     circ = qi.random_grid_circuit(5, 6, 14, seed=0)
     bits = qi.random_bitstrings(30, 1, seed=1)
     net = tn.circuit_network(circ, bits)
     t0 = time.perf_counter()
-    order, sliced, seed_used = tn.best_greedy_order(net, range(64), skip=[tn.BATCH], n_slices=6)
+    order, sliced, seed_used = tn.best_greedy_order(net, range(args.greedy_trials),
+                                                    skip=[tn.BATCH], n_slices=6)
     planning_s = time.perf_counter() - t0
     plans = {}
 
@@ -888,10 +894,11 @@ def tree_legs(args, q, torch, dev, rank):
         if ref is not None:
             v["amplitude_rel_err_vs_fp64"] = abs(amp - ref) / abs(ref)
     res["contraction"] = {
-        "workload": "5x6 grid random circuit, depth 14, the cheapest of 64 seeded greedy orders "
-                    "(seeds 0-63), 6 sliced indices (64 slices), 1 bitstring; AUTO-%g (measured "
+        "workload": "5x6 grid random circuit, depth 14, the cheapest of %d seeded greedy orders "
+                    "(seeds 0-%d), 6 sliced indices (64 slices), 1 bitstring; AUTO-%g (measured "
                     "size rule) vs all-FP32, CUDA-graph replays of %d slices; amplitude over all "
-                    "64 slices vs the FP64 state vector" % (args.tol, ns),
+                    "64 slices vs the FP64 state vector"
+                    % (args.greedy_trials, args.greedy_trials - 1, args.tol, ns),
         "greedy_seed": seed_used, "planning_s": planning_s,
         "slices_total": p.n_instances, "flops_per_slice": p.flops,
         "max_intermediate_log2": p.max_log2_size,
@@ -953,10 +960,10 @@ def tree_legs(args, q, torch, dev, rank):
     diff = {}
     net4 = tn.circuit_network(c4, None)
     # the greedy order of seed 2 (4.2e11 flops per slice: the adjoint GEMMs are
-    # large enough for the tensor cores) and the cheapest of 64 orders (2.8e9)
+    # large enough for the tensor cores) and the cheapest of --greedy-trials orders
     o_s2 = tn.greedy_order(net4, seed=2)
     orders = {"seed2": (o_s2, tn.choose_slices(net4, o_s2, n_labels=2))}
-    o_b, sl_b, _ = tn.best_greedy_order(net4, range(64), n_slices=2)
+    o_b, sl_b, _ = tn.best_greedy_order(net4, range(args.greedy_trials), n_slices=2)
     orders["cheapest"] = (o_b, sl_b)
     for mode, rule, which in (("auto", q.SIZE_RULE_TUNED, "seed2"),
                               ("fp32", q.SIZE_RULE_PAPER, "seed2"),
@@ -994,8 +1001,9 @@ def tree_legs(args, q, torch, dev, rank):
             "speedup_vs_fp32": diff["fp32"]["s_fwd_bwd"] / diff["auto"]["s_fwd_bwd"],
             "cheapest_order": {"auto_s": diff["auto_cheapest_order"]["s_fwd_bwd"],
                                "fp32_s": diff["fp32_cheapest_order"]["s_fwd_bwd"],
-                               "note": "the cheapest of 64 seeded greedy orders: 150x fewer "
-                                       "flops, GEMMs too small for emulation to matter"}}
+                               "note": "the cheapest of %d seeded greedy orders: 100x and more "
+                                       "fewer flops, GEMMs too small for emulation to matter"
+                                       % args.greedy_trials}}
     if rank == 0:
         import oracle
 
@@ -1032,7 +1040,8 @@ def scale_leg(args, q, torch, dev, tn, qi, rank):
     circ = qi.random_grid_circuit(5, 8, 12, seed=0)
     bits = qi.random_bitstrings(40, 1, seed=1)
     net = tn.circuit_network(circ, bits)
-    order, _, seed_used = tn.best_greedy_order(net, range(64), skip=[tn.BATCH] + labels)
+    order, _, seed_used = tn.best_greedy_order(net, range(args.greedy_trials),
+                                               skip=[tn.BATCH] + labels)
     plans = {}
 
     def make_plan(mode):
@@ -1045,9 +1054,9 @@ def scale_leg(args, q, torch, dev, tn, qi, rank):
     per = _contract_variants(args, q, tn, torch, dev, make_plan, 16, variants)
     plan = plans[q.MODE_AUTO]
     out = {"workload": "5x8 grid (40 qubits), depth 12, 8 sliced indices (256 slices), the "
-                       "cheapest of 64 seeded greedy orders of the sliced network, 1 bitstring; "
+                       "cheapest of %d seeded greedy orders of the sliced network, 1 bitstring; "
                        "AUTO-%g (measured size rule) vs all-FP32, CUDA-graph replays of 16 "
-                       "slices" % args.tol,
+                       "slices" % (args.greedy_trials, args.tol),
            "greedy_seed": seed_used,
            "flops_per_slice": plan.flops, "max_intermediate_log2": plan.max_log2_size}
     idx = [int(v, 2) for v, _ in rows]

@@ -184,7 +184,7 @@ def test_full_size_30_qubit_sliced_amplitudes_vs_fp64_golden(h, golden_dir):
 
 
 def test_full_size_30_qubit_in_the_bench_configuration_vs_fp64_golden(golden_dir):
-    """The contraction as bench.py times it: the cheapest of 64 seeded greedy
+    """The contraction as bench.py times it: the cheapest of 256 seeded greedy
     orders, 6 sliced indices, instances in groups of 16 (grouped tensor-core
     launches, batched FP32 steps), AUTO-0.1 under the measured size rule with
     K ranges from the tuner; two bitstrings x 64 slices against the FP64
@@ -197,7 +197,7 @@ def test_full_size_30_qubit_in_the_bench_configuration_vs_fp64_golden(golden_dir
     bits_all, ref_all = _golden_amplitudes(os.path.join(golden_dir, "grid5x6_d14_amplitudes.txt"))
     circ = qi.random_grid_circuit(5, 6, 14, seed=0)
     bits, ref = bits_all[2:4], ref_all[2:4]
-    plan = tn.plan_circuit(circ, bits, seed=0, n_slices=6, mode=q.MODE_AUTO, trials=64)
+    plan = tn.plan_circuit(circ, bits, seed=0, n_slices=6, mode=q.MODE_AUTO, trials=256)
     assert plan.n_instances == 2 * 64 and plan.max_log2_size <= 25
     hd = q.Handle(tol=0.1, size_rule=q.SIZE_RULE_TUNED)
     try:
