@@ -10,7 +10,8 @@ What it computes, each following a passage of the paper (Ootomo et al. 2023):
 
 * ``cgemm``: complex GEMM by the textbook triple loop (Section 3, the FP64
   reference of the CGEMM unit test), and a row-sampled OpenMP variant for
-  large shapes.
+  large shapes.  ``sgemm`` / ``tcec_sgemm`` / ``exp_stats_real``: the same
+  for real matrices (the SGEMM that Section 2.1 emulates).
 * ``split`` / ``f32_to_f16`` / ``f32_to_tf32``: the hi/lo split of Eq. 1
   (Section 2.1) with IEEE round-to-nearest-even restated in C.
 * ``exp_stats`` / ``stats_summary`` / ``select_mode``: the exponent statistics
@@ -82,6 +83,12 @@ def _L():
         lib.oracle_cgemm_naive.argtypes = [I, I, I64, I64, I64, P, P, I64, P, I64, P, P, I64, P]
         lib.oracle_cgemm_rows.argtypes = [I, I, I64, I64, I64, P, P, I64, P, I64, P, P, I64, P, I64, P]
         lib.oracle_tcec_cgemm.argtypes = [I, I, I, I, I, I64, I64, I64, P, P, I64, P, I64, P, P, I64, P]
+        D = ctypes.c_double
+        lib.oracle_sgemm_rows.argtypes = [I, I, I64, I64, I64, D, P, I64, P, I64, D, P, I64, P,
+                                          I64, P]
+        lib.oracle_tcec_sgemm.argtypes = [I, I, I, I, I, I64, I64, I64, D, P, I64, P, I64, D, P,
+                                          I64, P]
+        lib.oracle_exp_stats_real.argtypes = [I64, I64, P, I64, P, P]
         lib.oracle_f32_to_f16.argtypes = [ctypes.c_float]
         lib.oracle_f32_to_f16.restype = ctypes.c_uint16
         lib.oracle_f16_to_f32.argtypes = [ctypes.c_uint16]
@@ -178,6 +185,59 @@ def tcec_cgemm(kind: int, sA: int, sB: int, opA: int, opB: int, m: int, n: int, 
     return out
 
 
+def _mat_view_real(X: np.ndarray):
+    """Column-major float32 matrix -> (array, leading dim)."""
+    assert X.dtype == np.float32
+    if X.ndim == 1:
+        X = X.reshape(-1, 1)
+    assert X.flags.f_contiguous, "column-major (Fortran-ordered) input expected"
+    return X, X.shape[0]
+
+
+def sgemm(opA: int, opB: int, m: int, n: int, k: int, alpha, A, B, beta=0.0, C=None,
+          rows: Optional[Sequence[int]] = None) -> np.ndarray:
+    """alpha * op(A) op(B) + beta * C in float64 for real matrices: the SGEMM
+    that Section 2.1 emulates, by the textbook sum (OpenMP over columns).
+
+    A, B, C are Fortran-ordered float32 arrays; op T and C both transpose.
+    With ``rows`` only those output rows are computed (len(rows) x n)."""
+    A, lda = _mat_view_real(A)
+    B, ldb = _mat_view_real(B)
+    if C is not None:
+        C, ldc = _mat_view_real(C)
+        cp = _ptr(C)
+    else:
+        ldc, cp = 1, None
+    if rows is None:
+        rp, nr = None, m
+    else:
+        r = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+        rp, nr = _ptr(r), len(r)
+    out = np.zeros((nr, n), dtype=np.float64, order="F")
+    _L().oracle_sgemm_rows(opA, opB, m, n, k, float(alpha), _ptr(A), lda, _ptr(B), ldb,
+                           float(beta), cp, ldc, rp, nr, _ptr(out))
+    return out
+
+
+def tcec_sgemm(kind: int, sA: int, sB: int, opA: int, opB: int, m: int, n: int, k: int,
+               alpha, A, B, beta=0.0, C=None) -> np.ndarray:
+    """Exact (FP64) value of the emulated real product of Eq. 1.
+    kind: 0 FP16, 1 TF32, 2 BF16."""
+    A, lda = _mat_view_real(A)
+    B, ldb = _mat_view_real(B)
+    if C is not None:
+        C, ldc = _mat_view_real(C)
+        cp = _ptr(C)
+    else:
+        ldc, cp = 1, None
+    out = np.zeros((m, n), dtype=np.float64, order="F")
+    rc = _L().oracle_tcec_sgemm(kind, sA, sB, opA, opB, m, n, k, float(alpha), _ptr(A), lda,
+                                _ptr(B), ldb, float(beta), cp, ldc, _ptr(out))
+    if rc != 0:
+        raise MemoryError("oracle_tcec_sgemm failed")
+    return out
+
+
 def rel_fro_error(C: np.ndarray, C64: np.ndarray) -> float:
     """Relative Frobenius error ||C - C64||_F / ||C64||_F (Section 3)."""
     C = np.asarray(C, dtype=np.complex128)
@@ -230,6 +290,15 @@ def exp_stats(X: np.ndarray, rows: Optional[int] = None, cols: Optional[int] = N
     hist = np.zeros(256, dtype=np.int64)
     nz = np.zeros(1, dtype=np.int64)
     _L().oracle_exp_stats(rows, cols, _ptr(X), ldx, _ptr(hist), _ptr(nz))
+    return hist, int(nz[0])
+
+
+def exp_stats_real(X: np.ndarray):
+    """exp_stats over the scalars of a Fortran-ordered float32 matrix."""
+    X, ldx = _mat_view_real(X)
+    hist = np.zeros(256, dtype=np.int64)
+    nz = np.zeros(1, dtype=np.int64)
+    _L().oracle_exp_stats_real(X.shape[0], X.shape[1], _ptr(X), ldx, _ptr(hist), _ptr(nz))
     return hist, int(nz[0])
 
 

@@ -363,6 +363,114 @@ int oracle_tcec_cgemm(int kind, int sA, int sB, int opA, int opB, int64_t m, int
     return 0;
 }
 
+/* ------------------------------------------------------------------------
+ * Real matrices (the SGEMM that Section 2.1 emulates).  Column-major
+ * binary32 with a leading dimension; op 0 = N, 1 or 2 = T.  Results are
+ * binary64, column-major.
+ * ---------------------------------------------------------------------- */
+
+/* Element (r, c) of op(X). */
+static inline double op_elem_real(const float *X, int op, int64_t r, int64_t c, int64_t ldx) {
+    return (double)X[(op == 0) ? (r + c * ldx) : (c + r * ldx)];
+}
+
+/*
+ * C = alpha op(A) op(B) + beta C_in for the output rows listed in ``rows``
+ * (all m rows, in order, when rows is NULL), by the textbook sum over l in
+ * binary64, parallel over output columns.  C_in (binary32, ld ldc_in) may
+ * be NULL when beta is zero.  C_out is nrows x n, leading dim nrows.
+ */
+int oracle_sgemm_rows(int opA, int opB, int64_t m, int64_t n, int64_t k, double alpha,
+                      const float *A, int64_t lda, const float *B, int64_t ldb, double beta,
+                      const float *C_in, int64_t ldc_in, const int64_t *rows, int64_t nrows,
+                      double *C_out) {
+    if (!rows) nrows = m;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t r = 0; r < nrows; ++r) {
+            const int64_t i = rows ? rows[r] : r;
+            double acc = 0.0;
+            for (int64_t l = 0; l < k; ++l)
+                acc += op_elem_real(A, opA, i, l, lda) * op_elem_real(B, opB, l, j, ldb);
+            double c = alpha * acc;
+            if (C_in && beta != 0.0) c += beta * (double)C_in[i + j * ldc_in];
+            C_out[r + j * nrows] = c;
+        }
+    }
+    return err;
+}
+
+/*
+ * The emulated real product of Eq. 1 in exact arithmetic:
+ *   2^-(sA+sB) (hi_A hi_B + (lo_A hi_B + hi_A lo_B) / 2^11)
+ * summed over l in binary64, then alpha P + beta C_in.  The tensor-core
+ * kernel differs from this only by binary32 accumulation rounding.
+ * kind: 0 FP16, 1 TF32, 2 BF16.  Output as oracle_sgemm_rows (all rows).
+ */
+int oracle_tcec_sgemm(int kind, int sA, int sB, int opA, int opB, int64_t m, int64_t n, int64_t k,
+                      double alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
+                      double beta, const float *C_in, int64_t ldc_in, double *C_out) {
+    size_t na = (size_t)m * (size_t)k, nb = (size_t)k * (size_t)n;
+    float *a = (float *)malloc(sizeof(float) * (na ? na : 1));
+    float *b = (float *)malloc(sizeof(float) * (nb ? nb : 1));
+    float *ah = (float *)malloc(sizeof(float) * (na ? na : 1));
+    float *al = (float *)malloc(sizeof(float) * (na ? na : 1));
+    float *bh = (float *)malloc(sizeof(float) * (nb ? nb : 1));
+    float *bl = (float *)malloc(sizeof(float) * (nb ? nb : 1));
+    if (!a || !b || !ah || !al || !bh || !bl) {
+        free(a); free(b); free(ah); free(al); free(bh); free(bl);
+        return -1;
+    }
+    for (int64_t l = 0; l < k; ++l)
+        for (int64_t i = 0; i < m; ++i) a[i + l * m] = (float)op_elem_real(A, opA, i, l, lda);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t l = 0; l < k; ++l) b[l + j * k] = (float)op_elem_real(B, opB, l, j, ldb);
+    oracle_split(kind, sA, (int64_t)na, a, ah, al);
+    oracle_split(kind, sB, (int64_t)nb, b, bh, bl);
+    double unscale = ldexp(1.0, -(sA + sB));
+    double corr = ldexp(1.0, -11);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i) {
+            double p0 = 0, p1 = 0;
+            for (int64_t l = 0; l < k; ++l) {
+                size_t ia = (size_t)(i + l * m), ib = (size_t)(l + j * k);
+                p0 += (double)ah[ia] * (double)bh[ib];
+                p1 += (double)al[ia] * (double)bh[ib] + (double)ah[ia] * (double)bl[ib];
+            }
+            double c = alpha * ((p0 + corr * p1) * unscale);
+            if (C_in && beta != 0.0) c += beta * (double)C_in[i + j * ldc_in];
+            C_out[i + j * m] = c;
+        }
+    free(a); free(b); free(ah); free(al); free(bh); free(bl);
+    return 0;
+}
+
+/*
+ * Exponent statistics of Section 4.1 over the scalars of a real matrix
+ * (rows x cols, leading dim ldx); bins as oracle_exp_stats.
+ */
+void oracle_exp_stats_real(int64_t rows, int64_t cols, const float *X, int64_t ldx,
+                           int64_t *hist, int64_t *n_zero) {
+    for (int b = 0; b < 256; ++b) hist[b] = 0;
+    *n_zero = 0;
+    for (int64_t c = 0; c < cols; ++c)
+        for (int64_t r = 0; r < rows; ++r) {
+            float v = X[r + c * ldx];
+            if (!isfinite(v)) {
+                hist[255]++;
+            } else if (v == 0.0f) {
+                (*n_zero)++;
+            } else {
+                int ex;
+                (void)frexp((double)v, &ex);
+                int bin = ex - 1 + 127;
+                if (bin < 1) bin = 0;
+                hist[bin]++;
+            }
+        }
+}
+
 /*
  * Pairwise tensor contraction by nested loops (Section 2.2: connected edges
  * are summed, Einstein convention), with no reshaping to a GEMM.  Tensors

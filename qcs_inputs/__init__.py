@@ -74,6 +74,20 @@ def cgemm_operand(rows: int, cols: int, s: int, seed, ld: int | None = None) -> 
     return out
 
 
+def sgemm_operand(rows: int, cols: int, s: int, seed, ld: int | None = None) -> np.ndarray:
+    """Column-major float32 matrix with ``ld >= rows``: entries N(0, 1) * 2**e
+    with e ~ Uniform int [-s, s] per scalar; padding rows hold NaN."""
+    ld = rows if ld is None else ld
+    assert ld >= rows
+    g = _rng(seed)
+    x = g.standard_normal((rows, cols), dtype=np.float64)
+    if s > 0:
+        x = x * np.exp2(g.integers(-s, s + 1, size=(rows, cols)))
+    out = np.full((ld, cols), np.nan, dtype=np.float32, order="F")
+    out[:rows, :] = x.astype(np.float32)
+    return out
+
+
 def uniform_operand(rows: int, cols: int, seed) -> np.ndarray:
     """Column-major complex64 matrix with parts ~ U(-1, 1) (Section 3 unit test)."""
     g = _rng(seed)

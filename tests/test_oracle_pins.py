@@ -331,6 +331,93 @@ def test_tcec_model_scaled_recovers_tiny_inputs():
 
 
 # ---------------------------------------------------------------------------
+# Real matrices: the SGEMM of Section 2.1
+# ---------------------------------------------------------------------------
+
+def test_sgemm_hand_values_and_ops():
+    A = np.asfortranarray(np.array([[1, 2, 3], [4, 5, 6]], dtype=np.float32))  # 2 x 3
+    B = np.asfortranarray(np.array([[1, 0], [0, 1], [1, 1]], dtype=np.float32))  # 3 x 2
+    # A B = [[4, 5], [10, 11]], by hand
+    assert np.array_equal(oracle.sgemm(OP_N, OP_N, 2, 2, 3, 1.0, A, B), [[4, 5], [10, 11]])
+    # op T: A^T A (3 x 3) = [[17, 22, 27], [22, 29, 36], [27, 36, 45]]
+    assert np.array_equal(oracle.sgemm(OP_T, OP_N, 3, 3, 2, 1.0, A, A),
+                          [[17, 22, 27], [22, 29, 36], [27, 36, 45]])
+    # OP_C on a real matrix is the transpose
+    assert np.array_equal(oracle.sgemm(OP_C, OP_N, 3, 3, 2, 1.0, A, A),
+                          oracle.sgemm(OP_T, OP_N, 3, 3, 2, 1.0, A, A))
+    # alpha, beta, C read through its leading dimension
+    C = np.asfortranarray(np.array([[1, 1], [2, 2], [9, 9]], dtype=np.float32))  # ld 3
+    got = oracle.sgemm(OP_N, OP_N, 2, 2, 3, 2.0, A, B, beta=-1.0, C=C)
+    assert np.array_equal(got, [[7, 9], [18, 20]])
+
+
+@pytest.mark.parametrize("opA,opB", [(OP_N, OP_N), (OP_T, OP_N), (OP_N, OP_T), (OP_T, OP_T)])
+def test_sgemm_vs_numpy_and_complex_oracle(opA, opB):
+    m, n, k = 13, 11, 17
+    A = qi.sgemm_operand(*((m, k) if opA == OP_N else (k, m)), 4, (1, opA))
+    B = qi.sgemm_operand(*((k, n) if opB == OP_N else (n, k)), 4, (2, opB))
+    a = A.astype(np.float64) if opA == OP_N else A.T.astype(np.float64)
+    b = B.astype(np.float64) if opB == OP_N else B.T.astype(np.float64)
+    got = oracle.sgemm(opA, opB, m, n, k, 1.0, A, B)
+    assert np.allclose(got, a @ b, rtol=1e-13, atol=1e-13)
+    # a real matrix is a complex one with zero imaginary parts
+    Ac = np.asfortranarray(A.astype(np.complex64))
+    Bc = np.asfortranarray(B.astype(np.complex64))
+    gc = oracle.cgemm(opA, opB, m, n, k, 1, Ac, Bc)
+    assert np.array_equal(gc.imag, np.zeros_like(got)) and np.allclose(gc.real, got, rtol=1e-13)
+    # sampled rows are those rows of the full product
+    rows = [12, 0, 5]
+    assert np.array_equal(oracle.sgemm(opA, opB, m, n, k, 1.0, A, B, rows=rows), got[rows])
+
+
+def test_tcec_sgemm_reduces_to_the_complex_model_and_is_exact_on_integers():
+    m, n, k = 9, 10, 40
+    A = qi.sgemm_operand(m, k, 8, 5)
+    B = qi.sgemm_operand(k, n, 8, 6)
+    Ac = np.asfortranarray(A.astype(np.complex64))
+    Bc = np.asfortranarray(B.astype(np.complex64))
+    for kind, sA, sB in ((0, 0, 0), (0, 3, -2), (1, 0, 0), (2, 0, 0)):
+        r = oracle.tcec_sgemm(kind, sA, sB, OP_N, OP_N, m, n, k, 1.0, A, B)
+        c = oracle.tcec_cgemm(kind, sA, sB, OP_N, OP_N, m, n, k, 1, Ac, Bc)
+        assert np.allclose(r, c.real, rtol=1e-14, atol=0), kind
+    g = np.random.default_rng(3)
+    Ai = np.asfortranarray(g.integers(-8, 9, (7, 5)).astype(np.float32))
+    Bi = np.asfortranarray(g.integers(-8, 9, (6, 7)).astype(np.float32))
+    ref = Ai.T.astype(np.float64) @ Bi.T.astype(np.float64)
+    for kind in (0, 1, 2):
+        assert np.array_equal(oracle.tcec_sgemm(kind, 0, 0, OP_T, OP_T, 5, 6, 7, 1.0, Ai, Bi), ref)
+    assert np.array_equal(oracle.tcec_sgemm(0, 4, -3, OP_T, OP_T, 5, 6, 7, 1.0, Ai, Bi), ref)
+
+
+def test_tcec_sgemm_accuracy_bound():
+    # hi + lo carries 22 significant bits; the dropped lo*lo term is ~2^-22
+    # relative, so the emulated product is FP32-accurate (Section 2.1)
+    m, n, k = 32, 24, 256
+    A = np.asfortranarray(np.random.default_rng(4).uniform(-1, 1, (m, k)).astype(np.float32))
+    B = np.asfortranarray(np.random.default_rng(5).uniform(-1, 1, (k, n)).astype(np.float32))
+    exact = oracle.sgemm(OP_N, OP_N, m, n, k, 1.0, A, B)
+    for kind in (0, 1):
+        err = oracle.rel_fro_error(oracle.tcec_sgemm(kind, 0, 0, OP_N, OP_N, m, n, k, 1.0, A, B),
+                                   exact)
+        assert 1e-9 < err < 1e-6, (kind, err)
+    err_bf = oracle.rel_fro_error(oracle.tcec_sgemm(2, 0, 0, OP_N, OP_N, m, n, k, 1.0, A, B), exact)
+    assert err_bf > 1e-6
+
+
+def test_exp_stats_real_hand_values_and_complex_equivalence():
+    x = np.array([1.0, 0.5, 0.0, 3.0, 2.0 ** -130, np.inf, -0.75, 2.0 ** 20], dtype=np.float32)
+    hist, nz = oracle.exp_stats_real(np.asfortranarray(x.reshape(4, 2, order="F")))
+    want = np.zeros(256, dtype=np.int64)
+    for b in (127, 126, 128, 0, 255, 126, 147):
+        want[b] += 1
+    assert nz == 1 and np.array_equal(hist, want)
+    X = qi.sgemm_operand(30, 20, 20, 8)
+    h_r, z_r = oracle.exp_stats_real(X)
+    h_c, z_c = oracle.exp_stats(np.asfortranarray(X.astype(np.complex64)))
+    assert np.array_equal(h_r, h_c) and z_c == z_r + X.size
+
+
+# ---------------------------------------------------------------------------
 # Circuits, tensor networks, amplitudes (Section 2.2, Section 5.3)
 # ---------------------------------------------------------------------------
 
