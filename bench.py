@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--tree-slices", type=int, default=16,
                    help="slices of the 30-qubit network timed per mode")
     p.add_argument("--no-sweep", action="store_true", help="skip the CGEMM-sweep leg")
+    p.add_argument("--no-sgemm", action="store_true", help="skip the real-GEMM leg")
+    p.add_argument("--sgemm-sizes", type=int, nargs="+", default=[8192, 16384])
     p.add_argument("--greedy-trials", type=int, default=256,
                    help="seeded greedy orders tried per network (the cheapest is contracted)")
     p.add_argument("--sweep-sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192, 16384])
@@ -587,6 +589,8 @@ def main():
         out["hbm_kernels"] = hbm_legs(q, torch, dev, h, stages, n)
     if not args.no_extras and not args.no_sweep:
         out["sweep"] = sweep_leg(args, q, torch, dev, rank)
+    if not args.no_extras and not args.no_sgemm:
+        out["sgemm"] = sgemm_leg(args, q, torch, dev, rank)
 
     if not args.no_tree:
         out.update(tree_legs(args, q, torch, dev, rank))
@@ -750,6 +754,101 @@ def sweep_leg(args, q, torch, dev, rank):
                         "e~U_int[-s,s] per real scalar; forced modes, AUTO-"
                         f"{args.tol:g} with the paper's size rule and with the size rule "
                         "measured on this GPU (auto_tuned)",
+            "error_sample": f"{rows} output rows vs the FP64 oracle",
+            "points": points}
+
+
+def sgemm_leg(args, q, torch, dev, rank):
+    """Real GEMMs through qcs_sgemm (the SGEMM emulation of Section 2.1):
+    m = n = k in ``args.sgemm_sizes``, entries N(0,1) 2^e with e ~ U_int[-s, s]
+    for s in {0, 20}; per point the TFLOP/s (2 m n k) of the plain FP32
+    kernel, TF32X, FP16X and AUTO-t under the paper's size rule, cuBLAS SGEMM
+    through torch (TF32 off), the relative Frobenius error of each against
+    the FP64 oracle on ``args.sample_rows`` output rows, and the tensor-core
+    work 6 m n k of the FP16X call as a fraction of the sustained bf16 peak
+    (the whole call: statistics-free split + tensor-core kernel)."""
+    import numpy as np
+
+    import oracle
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        first = e0.elapsed_time(e1)
+        reps = int(max(2, min(50, 200.0 / max(first, 1e-3))))
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def operand(n, s, seed):
+        g = torch.Generator(device=dev).manual_seed(seed)
+        x = torch.randn((n, n), generator=g, device=dev, dtype=torch.float32)
+        if s > 0:
+            x.mul_(torch.exp2(torch.randint(-s, s + 1, (n, n), generator=g, device=dev).float()))
+        return x.t()  # column-major view
+
+    _, sustained, src = peaks()
+    h = q.Handle(tol=args.tol, size_rule=True)
+    rows = args.sample_rows
+    points = []
+    allow = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for n in args.sgemm_sizes:
+            flops = 2.0 * n * n * n
+            for s in (0, 20):
+                A = operand(n, s, 41 * n + s)
+                B = operand(n, s, 43 * n + s)
+                C = q.fortran_empty_real(n, n, device=dev)
+                pt = {"size": n, "s": s, "modes": {}}
+                ref = None
+                if rank == 0:
+                    pick = np.random.default_rng(n + s).choice(n, rows, replace=False)
+                    At = np.asfortranarray(A[torch.from_numpy(pick).to(dev)].cpu().numpy().T)
+                    ref = oracle.sgemm(oracle.OP_T, oracle.OP_N, rows, n, n, 1.0, At,
+                                       np.asfortranarray(B.cpu().numpy()))
+                desc = torch.zeros(4, dtype=torch.int32, device=dev)
+                for mode in ("fp32", "tf32x", "fp16x", "auto"):
+                    ms = timed(lambda: q.sgemm(h, A, B, C, mode=mode))
+                    entry = {"tflops": flops / (ms * 1e-3) / 1e12, "ms": ms}
+                    if mode == "auto":
+                        q.sgemm(h, A, B, C, mode=mode, desc_out=desc)
+                        entry["selected"] = q.MODE_NAME[int(desc[0].item())]
+                    if mode == "fp16x":
+                        entry["tensor_frac_of_sustained_bf16"] = (
+                            3 * flops / (ms * 1e-3) / 1e12 / sustained)
+                    if rank == 0:
+                        got = C[torch.from_numpy(pick).to(dev)].cpu().numpy().astype(np.float64)
+                        entry["rel_fro_vs_fp64"] = (_finite_or_none(oracle.rel_fro_error(got, ref))
+                                                    if np.isfinite(got).all() else None)
+                    pt["modes"][mode] = entry
+                Ar, Br = A.t().contiguous(), B.t().contiguous()  # row-major copies: C^T = B^T A^T
+                ms = timed(lambda: torch.matmul(Br, Ar))
+                pt["cublas_sgemm_tflops"] = flops / (ms * 1e-3) / 1e12
+                if rank == 0:
+                    got = torch.matmul(Br, Ar).t()[torch.from_numpy(pick).to(dev)]
+                    pt["cublas_sgemm_rel_fro_vs_fp64"] = _finite_or_none(
+                        oracle.rel_fro_error(got.cpu().numpy().astype(np.float64), ref))
+                pt["auto_speedup_vs_fp32"] = (pt["modes"]["auto"]["tflops"]
+                                              / pt["modes"]["fp32"]["tflops"])
+                points.append(pt)
+                del A, B, C, Ar, Br
+                torch.cuda.empty_cache()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = allow
+        h.close()
+    return {"workload": "real GEMM m=n=k, column-major, alpha=1, beta=0; entries N(0,1)*2^e, "
+                        f"e~U_int[-s,s]; forced modes and AUTO-{args.tol:g} with the paper's "
+                        "size rule",
+            "flops": "2 m n k",
+            "peak_source": src,
             "error_sample": f"{rows} output rows vs the FP64 oracle",
             "points": points}
 

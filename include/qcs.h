@@ -182,6 +182,27 @@ int qcs_cgemm(qcs_handle_t h, qcs_mode_t mode, qcs_op_t transA, qcs_op_t transB,
               const qcs_c32 *B, int64_t ldb, const qcs_c32 *beta, qcs_c32 *C, int64_t ldc,
               qcs_gemm_desc_t *d_desc_out);
 
+/* C = alpha * op(A) * op(B) + beta * C for real FP32 matrices: the SGEMM
+ * emulation of Section 2.1 (Eq. 1: one real product as hi*hi + (lo*hi +
+ * hi*lo) / 2^11 on the tensor cores, the hi*hi sum added with
+ * round-to-nearest) with the automatic selection of Section 4.
+ *   op(A) is m x k, op(B) is k x n, C is m x n, column-major, all device
+ *   pointers (4-byte aligned); lda >= rows of A as stored (m for OP_N, k
+ *   otherwise), likewise ldb, and ldc >= m.  OP_C is OP_T.  alpha and beta
+ *   are host pointers.  m, n, k >= 0 (each at most 2^31 - 1, else
+ *   UNSUPPORTED).  C must not overlap A or B.
+ *   mode AUTO runs statistics (every scalar of A and B as stored) and the
+ *   selection rule on the device; the size rule of the handle applies with
+ *   the paper's cut-offs (Section 4.3) -- QCS_SIZE_RULE_TUNED acts as
+ *   QCS_SIZE_RULE_PAPER here, the tuned table holding complex shapes.  The
+ *   K-range count set by qcs_set_tc_splits applies.  d_desc_out (device,
+ *   optional) receives the descriptor the GEMM ran with; the selection
+ *   counters of qcs_get_auto_counts add 2 m n k flops per AUTO call. */
+int qcs_sgemm(qcs_handle_t h, qcs_mode_t mode, qcs_op_t transA, qcs_op_t transB, int64_t m,
+              int64_t n, int64_t k, const float *alpha, const float *A, int64_t lda,
+              const float *B, int64_t ldb, const float *beta, float *C, int64_t ldc,
+              qcs_gemm_desc_t *d_desc_out);
+
 /* The split stage of qcs_cgemm alone (Eq. 1 of Section 2.1 after the
  * scaling of Section 4.2), for inspection: op(X) (R x K for which == 0, i.e.
  * the A operand; K x R for which == 1, the B operand) is split under the

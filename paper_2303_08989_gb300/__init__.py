@@ -16,7 +16,7 @@ from ._lib import (MODE_AUTO, MODE_BF16X3, MODE_BY_NAME, MODE_FP16X, MODE_FP16X_
                    SIZE_RULE_TUNED, QcsError)
 
 __all__ = [
-    "Handle", "cgemm", "exp_stats", "select", "split", "permute", "fortran_empty", "to_fortran",
+    "Handle", "cgemm", "sgemm", "fortran_empty_real", "exp_stats", "select", "split", "permute", "fortran_empty", "to_fortran",
     "MODE_AUTO", "MODE_FP16X", "MODE_FP16X_SCALED", "MODE_TF32X", "MODE_FP32", "MODE_BF16X3",
     "MODE_BY_NAME", "MODE_NAME", "OP_N", "OP_T", "OP_C", "QcsError",
     "SIZE_RULE_OFF", "SIZE_RULE_PAPER", "SIZE_RULE_TUNED",
@@ -51,6 +51,14 @@ def fortran_empty(rows: int, cols: int, ld: Optional[int] = None, device="cuda")
     torch = _torch()
     ld = rows if ld is None else ld
     base = torch.empty((cols, ld), dtype=torch.complex64, device=device)
+    return base.t()[:rows]
+
+
+def fortran_empty_real(rows: int, cols: int, ld: Optional[int] = None, device="cuda"):
+    """Uninitialised column-major float32 (rows x cols) with leading dim ld."""
+    torch = _torch()
+    ld = rows if ld is None else ld
+    base = torch.empty((cols, ld), dtype=torch.float32, device=device)
     return base.t()[:rows]
 
 
@@ -225,6 +233,35 @@ def cgemm(h: Handle, A, B, C=None, *, m=None, n=None, k=None, alpha=1.0, beta=0.
                          ctypes.byref(be), ctypes.c_void_p(C.data_ptr()), ldc, dp)
     _lib.check(rc, "qcs_cgemm")
     del torch
+    return C
+
+
+def sgemm(h: Handle, A, B, C=None, *, m=None, n=None, k=None, alpha=1.0, beta=0.0,
+          opA=OP_N, opB=OP_N, mode="auto", desc_out=None):
+    """C = alpha op(A) op(B) + beta C for real matrices with qcs_sgemm;
+    returns C.  A, B, C are column-major float32 device tensors; OP_C acts
+    as OP_T.  If C is None a new m x n tensor is allocated (beta must then
+    be 0).  ``desc_out`` as for cgemm."""
+    rA, cA = A.shape
+    rB, cB = B.shape
+    m = (rA if opA == OP_N else cA) if m is None else m
+    k = (cA if opA == OP_N else rA) if k is None else k
+    n = (cB if opB == OP_N else rB) if n is None else n
+    for X in (A, B) + ((C,) if C is not None else ()):
+        if X.dtype != _torch().float32:
+            raise TypeError("sgemm takes float32 tensors")
+    if C is None:
+        if float(beta) != 0:
+            raise ValueError("beta != 0 needs C")
+        C = fortran_empty_real(m, n, device=A.device)
+    al = ctypes.c_float(float(alpha))
+    be = ctypes.c_float(float(beta))
+    dp = ctypes.c_void_p(desc_out.data_ptr()) if desc_out is not None else None
+    rc = h.lib.qcs_sgemm(h.ptr, _mode(mode), int(opA), int(opB), m, n, k, ctypes.byref(al),
+                         ctypes.c_void_p(A.data_ptr()), _ld(A, rA), ctypes.c_void_p(B.data_ptr()),
+                         _ld(B, rB), ctypes.byref(be), ctypes.c_void_p(C.data_ptr()),
+                         _ld(C, C.shape[0]), dp)
+    _lib.check(rc, "qcs_sgemm")
     return C
 
 

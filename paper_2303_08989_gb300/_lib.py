@@ -34,7 +34,7 @@ EXPORTED = [
     "qcs_status_string", "qcs_cgemm_noalloc", "qcs_tree_graph_create", "qcs_tree_graph_launch",
     "qcs_tree_graph_destroy", "qcs_get_auto_counts", "qcs_autotune_gemm", "qcs_autotune_tree",
     "qcs_get_tuning", "qcs_set_tuning", "qcs_set_instance_batch", "qcs_set_tc_schedule",
-    "qcs_set_tc_splits",
+    "qcs_set_tc_splits", "qcs_sgemm",
 ]
 SIZE_RULE_OFF, SIZE_RULE_PAPER, SIZE_RULE_TUNED = 0, 1, 2
 NUM_MODES = 6
@@ -127,6 +127,8 @@ def load(path: str = LIB_PATH):
         "qcs_select": [H, P, P, P],
         "qcs_cgemm": [H, I, I, I, I64, I64, I64, ctypes.POINTER(qcs_c32), P, I64, P, I64,
                       ctypes.POINTER(qcs_c32), P, I64, P],
+        "qcs_sgemm": [H, I, I, I, I64, I64, I64, ctypes.POINTER(ctypes.c_float), P, I64, P, I64,
+                      ctypes.POINTER(ctypes.c_float), P, I64, P],
         "qcs_split": [H, P, I, I, I64, I64, P, I64, P, I64, I64],
         "qcs_permute": [H, I, ctypes.POINTER(I64), ctypes.POINTER(I64), I64, P, P, P],
         "qcs_contract_tree": [H, ctypes.POINTER(qcs_tree_t), ctypes.POINTER(P), P,

@@ -99,12 +99,12 @@ int stats2_blocks(int64_t nel, int num_sms) {
 // planes (kRowBytes of K x 128 rows), 64-byte swizzle (the layout the
 // kernel's shared-memory descriptors describe).
 int encode_planes(qcs_handle_t h, CUtensorMap *map, void *base, int64_t R_pad, int64_t K_pad,
-                  int esz, int nplanes) {
+                  int esz, int nplanes, int box_rows = kBM) {
     const CUtensorMapDataType dt =
         esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     cuuint64_t gdim[3] = {(cuuint64_t)K_pad, (cuuint64_t)R_pad, (cuuint64_t)nplanes};
     cuuint64_t gstride[2] = {(cuuint64_t)(K_pad * esz), (cuuint64_t)(K_pad * R_pad * esz)};
-    cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)kBM, (cuuint32_t)nplanes};
+    cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)box_rows, (cuuint32_t)nplanes};
     cuuint32_t estride[3] = {1, 1, 1};
     const CUtensorMapL2promotion promo =
         h->tc_l2_promotion >= 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
@@ -437,6 +437,132 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
     return QCS_SUCCESS;
 }
 
+// ---- real GEMM --------------------------------------------------------------
+
+namespace {
+
+// Plane areas of one real GEMM: A two planes of mp rows, B two planes of
+// np rows (n rounded up to the real tile's 256 columns), then the partials.
+struct RealLayout {
+    int64_t kp = 0, mp = 0, np = 0;
+    size_t a = 0, b = 0, partials = 0, total = 0;
+};
+
+RealLayout real_layout(int eff, int64_t m, int64_t n, int64_t k, int S) {
+    RealLayout L;
+    L.kp = round_up(k, 32);
+    L.mp = round_up(m, kBM);
+    L.np = round_up(n, 2 * kBN);
+    const int esz = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X) ? 4 : 2;
+    L.a = 0;
+    L.b = align256(size_t(2) * L.mp * L.kp * esz);
+    L.partials = L.b + align256(size_t(2) * L.np * L.kp * esz);
+    L.total = L.partials + (S > 1 ? align256(sizeof(float) * S * m * n) : 0);
+    return L;
+}
+
+// The size rule for a real GEMM: the paper's cut-offs (the tuned table
+// holds complex shapes).
+int effective_mode_real(qcs_handle_t h, int mode, int64_t m, int64_t n, int64_t k) {
+    if (mode != QCS_MODE_AUTO || h->size_rule == QCS_SIZE_RULE_OFF) return mode;
+    const int64_t s = std::min(m, std::min(n, k));
+    if (s >= 2048) return QCS_MODE_AUTO;
+    if (s >= 512) return QCS_MODE_TF32X;
+    return QCS_MODE_FP32;
+}
+
+}  // namespace
+
+size_t sgemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits) {
+    size_t bytes = align256(sizeof(qcs_gemm_desc_t));
+    bytes += align256(size_t(2) * num_sms * kPartialStride * sizeof(int64_t));
+    if (eff != QCS_MODE_FP32 && k > 0)
+        bytes += real_layout(eff, m, n, k, tc_split_count(m, n, k, 1, num_sms, splits, true)).total;
+    return bytes;
+}
+
+int run_sgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n, int64_t k,
+              float alpha, const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
+              float *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out) {
+    cudaStream_t s = h->stream;
+    uint8_t *p = static_cast<uint8_t *>(ws);
+    qcs_gemm_desc_t *desc = reinterpret_cast<qcs_gemm_desc_t *>(p);
+    p += align256(sizeof(qcs_gemm_desc_t));
+    int64_t *partials = reinterpret_cast<int64_t *>(p);
+    p += align256(size_t(2) * h->num_sms * kPartialStride * sizeof(int64_t));
+    cudaError_t e = cudaSuccess;
+    const bool emulated = (eff != QCS_MODE_FP32 && k > 0);
+    if (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X_SCALED) {
+        // statistics of both operands as stored (a transpose keeps the multiset)
+        const int64_t ra = (opA == QCS_OP_N) ? m : k, ca = (opA == QCS_OP_N) ? k : m;
+        const int64_t rb = (opB == QCS_OP_N) ? k : n, cb = (opB == QCS_OP_N) ? n : k;
+        const int gA = stats2_blocks((ra * ca + 1) / 2, h->num_sms);
+        const int gB = stats2_blocks((rb * cb + 1) / 2, h->num_sms);
+        ProfScope ps(h, kProfStats);
+        e = launch_stats_select_2stage_real(A, ra, ca, lda, gA, B, rb, cb, ldb, gB, h->tol, eff,
+                                            partials, partials + 5 * (gA + gB), desc, h->d_counts,
+                                            2.0 * (double)m * (double)n * (double)k, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    } else if (eff != QCS_MODE_FP32 || d_desc_out) {
+        e = launch_set_desc(desc, eff, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    }
+    if (!emulated) {
+        ProfScope ps(h, kProfGemmSimt);
+        e = launch_sgemm_simt(nullptr, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    } else {
+        TcWork w;
+        w.S = tc_split_count(m, n, k, 1, h->num_sms, h->tc_splits, true);
+        const RealLayout L = real_layout(eff, m, n, k, w.S);
+        uint8_t *planesA = p + L.a, *planesB = p + L.b;
+        if (w.S > 1) w.P = reinterpret_cast<float2 *>(p + L.partials);
+        w.a_rows = L.mp;
+        w.b_rows = L.np;
+        {
+            int64_t sr, sc;
+            ProfScope ps(h, kProfSplit);
+            plane_strides(0, opA, lda, sr, sc);
+            e = launch_split_real(desc, 0, A, sr, sc, m, k, L.mp, L.kp, planesA, L.kp, L.mp * L.kp, s);
+            if (e == cudaSuccess) {
+                plane_strides(1, opB, ldb, sr, sc);
+                e = launch_split_real(desc, 1, B, sr, sc, n, k, L.np, L.kp, planesB, L.kp,
+                                      L.np * L.kp, s);
+            }
+            if (e != cudaSuccess) return QCS_ERR_CUDA;
+        }
+        const bool need16 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X ||
+                             eff == QCS_MODE_FP16X_SCALED || eff == QCS_MODE_BF16X3);
+        const bool need32 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X);
+        {
+            ProfScope ps_tc(h, kProfGemmTc);
+            for (int esz = 2; esz <= 4; esz += 2) {
+                if ((esz == 2 && !need16) || (esz == 4 && !need32)) continue;
+                CUtensorMap ma, mb;
+                if (encode_planes(h, &ma, planesA, L.mp, L.kp, esz, 2, kBM) ||
+                    encode_planes(h, &mb, planesB, L.np, L.kp, esz, 2, 2 * kBN))
+                    return QCS_ERR_CUDA;
+                const int kind = (esz == 4) ? 1 : (eff == QCS_MODE_BF16X3 ? 2 : 0);
+                e = launch_sgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, L.kp, alpha, beta,
+                                    C, ldc, h->d_err, h->num_sms, h->tc_group_m, s, w);
+                if (e != cudaSuccess) return QCS_ERR_CUDA;
+            }
+            e = launch_tc_reduce_real(desc, m, n, alpha, beta, C, ldc, h->num_sms, w, s);
+            if (e != cudaSuccess) return QCS_ERR_CUDA;
+        }
+        if (eff == QCS_MODE_AUTO) {
+            ProfScope ps(h, kProfGemmSimt);
+            e = launch_sgemm_simt(desc, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
+            if (e != cudaSuccess) return QCS_ERR_CUDA;
+        }
+    }
+    if (d_desc_out) {
+        e = cudaMemcpyAsync(d_desc_out, desc, sizeof(qcs_gemm_desc_t), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    }
+    return QCS_SUCCESS;
+}
+
 int validate_cgemm(int mode, int opA, int opB, int64_t m, int64_t n, int64_t k, const void *alpha,
                    const void *A, int64_t lda, const void *B, int64_t ldb, const void *beta,
                    const void *C, int64_t ldc) {
@@ -609,6 +735,31 @@ int qcs_cgemm(qcs_handle_t h, qcs_mode_t mode, qcs_op_t transA, qcs_op_t transB,
     return run_cgemm(h, h->ws.ptr, eff, transA, transB, m, n, k, al,
                      reinterpret_cast<const float2 *>(A), lda, reinterpret_cast<const float2 *>(B),
                      ldb, be, reinterpret_cast<float2 *>(C), ldc, d_desc_out, nullptr);
+}
+
+int qcs_sgemm(qcs_handle_t h, qcs_mode_t mode, qcs_op_t transA, qcs_op_t transB, int64_t m,
+              int64_t n, int64_t k, const float *alpha, const float *A, int64_t lda,
+              const float *B, int64_t ldb, const float *beta, float *C, int64_t ldc,
+              qcs_gemm_desc_t *d_desc_out) {
+    if (!h) return QCS_ERR_INVALID_ARG;
+    if (!valid_mode(mode) || !valid_op(transA) || !valid_op(transB)) return QCS_ERR_INVALID_ARG;
+    if (m < 0 || n < 0 || k < 0 || !alpha || !beta) return QCS_ERR_INVALID_ARG;
+    const int64_t rowsA = (transA == QCS_OP_N) ? m : k;
+    const int64_t rowsB = (transB == QCS_OP_N) ? k : n;
+    if (lda < std::max<int64_t>(1, rowsA) || ldb < std::max<int64_t>(1, rowsB) ||
+        ldc < std::max<int64_t>(1, m))
+        return QCS_ERR_INVALID_ARG;
+    if (m == 0 || n == 0) return QCS_SUCCESS;
+    if (!C || (k > 0 && (!A || !B))) return QCS_ERR_INVALID_ARG;
+    auto mis = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 3u) != 0; };
+    if (mis(A) || mis(B) || mis(C)) return QCS_ERR_UNSUPPORTED;
+    if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) return QCS_ERR_UNSUPPORTED;
+    const int eff = effective_mode_real(h, mode, m, n, k);
+    if (int r = ensure_workspace(h->ws, sgemm_workspace_bytes(eff, m, n, k, h->num_sms,
+                                                             h->tc_splits)))
+        return r;
+    return run_sgemm(h, h->ws.ptr, eff, transA, transB, m, n, k, *alpha, A, lda, B, ldb, *beta, C,
+                     ldc, d_desc_out);
 }
 
 int qcs_split(qcs_handle_t h, const qcs_gemm_desc_t *d_desc, int which, qcs_op_t op, int64_t R,

@@ -3,10 +3,12 @@
 // The paper's library is used by linking it in front of cuBLAS: calls to the
 // cuBLAS GEMM routines of an unmodified application are redirected to the
 // emulated GEMM, and an environment variable picks the mode (Section 3).
-// This library does the same for the complex single-precision GEMMs: loaded
-// before cuBLAS (LD_PRELOAD, or linked ahead of it), it defines
-//   cublasCgemm_v2, cublasCgemmStridedBatched, cublasCgemmBatched
-// and runs them through qcs_cgemm on the cuBLAS handle's stream.  Calls it
+// This library does the same for the single-precision GEMMs: loaded before
+// cuBLAS (LD_PRELOAD, or linked ahead of it), it defines
+//   cublasCgemm_v2, cublasCgemmStridedBatched, cublasCgemmBatched,
+//   cublasSgemm_v2, cublasSgemmStridedBatched
+// and runs them through qcs_cgemm / qcs_sgemm on the cuBLAS handle's
+// stream.  Calls it
 // cannot take -- alpha/beta in device memory (CUBLAS_POINTER_MODE_DEVICE),
 // an argument qcs_cgemm rejects, or QCS_CUBLAS_MODE=cublas -- go to the next
 // definition in the link order, the real cuBLAS.
@@ -42,6 +44,13 @@ typedef cublasStatus_t (*CgemmStridedFn)(cublasHandle_t, cublasOperation_t, cubl
                                          int, int, int, const cuComplex *, const cuComplex *, int,
                                          long long, const cuComplex *, int, long long,
                                          const cuComplex *, cuComplex *, int, long long, int);
+typedef cublasStatus_t (*SgemmFn)(cublasHandle_t, cublasOperation_t, cublasOperation_t, int, int,
+                                  int, const float *, const float *, int, const float *, int,
+                                  const float *, float *, int);
+typedef cublasStatus_t (*SgemmStridedFn)(cublasHandle_t, cublasOperation_t, cublasOperation_t,
+                                         int, int, int, const float *, const float *, int,
+                                         long long, const float *, int, long long, const float *,
+                                         float *, int, long long, int);
 typedef cublasStatus_t (*CgemmBatchedFn)(cublasHandle_t, cublasOperation_t, cublasOperation_t, int,
                                          int, int, const cuComplex *, const cuComplex *const[],
                                          int, const cuComplex *const[], int, const cuComplex *,
@@ -99,11 +108,8 @@ bool takeable(cublasHandle_t handle, cudaStream_t *stream) {
     return get_stream(handle, stream) == CUBLAS_STATUS_SUCCESS;
 }
 
-// qcs_cgemm on ``stream`` under the lock of its handle; QCS status.
-int run(cudaStream_t stream, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
-        const cuComplex *alpha, const cuComplex *A, int lda, const cuComplex *B, int ldb,
-        const cuComplex *beta, cuComplex *C, int ldc) {
-    std::lock_guard<std::mutex> guard(g_lock);
+// The qcs handle of ``stream`` (created on first use); call with g_lock held.
+int handle_of(cudaStream_t stream, qcs_handle_t *out) {
     qcs_handle_t &h = g_handles[stream];
     if (!h) {
         if (int r = qcs_create(&h, stream)) {
@@ -111,6 +117,28 @@ int run(cudaStream_t stream, cublasOperation_t ta, cublasOperation_t tb, int m, 
             return r;
         }
     }
+    *out = h;
+    return QCS_SUCCESS;
+}
+
+// qcs_sgemm on ``stream`` under the lock of its handle; QCS status.
+int run_real(cudaStream_t stream, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
+             const float *alpha, const float *A, int lda, const float *B, int ldb,
+             const float *beta, float *C, int ldc) {
+    std::lock_guard<std::mutex> guard(g_lock);
+    qcs_handle_t h;
+    if (int r = handle_of(stream, &h)) return r;
+    return qcs_sgemm(h, (qcs_mode_t)shim_mode(), to_op(ta), to_op(tb), m, n, k, alpha, A, lda, B,
+                     ldb, beta, C, ldc, nullptr);
+}
+
+// qcs_cgemm on ``stream`` under the lock of its handle; QCS status.
+int run(cudaStream_t stream, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k,
+        const cuComplex *alpha, const cuComplex *A, int lda, const cuComplex *B, int ldb,
+        const cuComplex *beta, cuComplex *C, int ldc) {
+    std::lock_guard<std::mutex> guard(g_lock);
+    qcs_handle_t h;
+    if (int r = handle_of(stream, &h)) return r;
     static_assert(sizeof(cuComplex) == sizeof(qcs_c32), "complex layouts differ");
     return qcs_cgemm(h, (qcs_mode_t)shim_mode(), to_op(ta), to_op(tb), m, n, k,
                      reinterpret_cast<const qcs_c32 *>(alpha), reinterpret_cast<const qcs_c32 *>(A),
@@ -184,7 +212,52 @@ cublasStatus_t cublasCgemmBatched(cublasHandle_t handle, cublasOperation_t trans
                 batchCount);
 }
 
-// Calls this library ran through qcs_cgemm (*taken) and passed to cuBLAS
+cublasStatus_t cublasSgemm_v2(cublasHandle_t handle, cublasOperation_t transa,
+                              cublasOperation_t transb, int m, int n, int k, const float *alpha,
+                              const float *A, int lda, const float *B, int ldb, const float *beta,
+                              float *C, int ldc) {
+    cudaStream_t stream;
+    if (takeable(handle, &stream) &&
+        run_real(stream, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc) ==
+            QCS_SUCCESS) {
+        g_taken++;
+        return CUBLAS_STATUS_SUCCESS;
+    }
+    static SgemmFn real = next_symbol<SgemmFn>("cublasSgemm_v2");
+    if (!real) return CUBLAS_STATUS_NOT_SUPPORTED;
+    g_passed++;
+    return real(handle, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+cublasStatus_t cublasSgemmStridedBatched(cublasHandle_t handle, cublasOperation_t transa,
+                                         cublasOperation_t transb, int m, int n, int k,
+                                         const float *alpha, const float *A, int lda,
+                                         long long strideA, const float *B, int ldb,
+                                         long long strideB, const float *beta, float *C, int ldc,
+                                         long long strideC, int batchCount) {
+    cudaStream_t stream;
+    if (batchCount >= 0 && takeable(handle, &stream)) {
+        int r = QCS_SUCCESS, b = 0;
+        for (; b < batchCount && r == QCS_SUCCESS; ++b)
+            r = run_real(stream, transa, transb, m, n, k, alpha, A + b * strideA, lda,
+                         B + b * strideB, ldb, beta, C + b * strideC, ldc);
+        if (r == QCS_SUCCESS) {
+            g_taken++;
+            return CUBLAS_STATUS_SUCCESS;
+        }
+        // as for cublasCgemmStridedBatched: only a rejection of the first
+        // entry can be handed to cuBLAS
+        if (b > 1 || (r != QCS_ERR_UNSUPPORTED && r != QCS_ERR_INVALID_ARG))
+            return CUBLAS_STATUS_EXECUTION_FAILED;
+    }
+    static SgemmStridedFn real = next_symbol<SgemmStridedFn>("cublasSgemmStridedBatched");
+    if (!real) return CUBLAS_STATUS_NOT_SUPPORTED;
+    g_passed++;
+    return real(handle, transa, transb, m, n, k, alpha, A, lda, strideA, B, ldb, strideB, beta, C,
+                ldc, strideC, batchCount);
+}
+
+// Calls this library ran through qcs_cgemm / qcs_sgemm (*taken) and passed to cuBLAS
 // (*passed) since it was loaded.
 void qcs_cublas_shim_counts(long long *taken, long long *passed) {
     if (taken) *taken = g_taken.load();

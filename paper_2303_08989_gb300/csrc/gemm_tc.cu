@@ -61,6 +61,13 @@
 // forms C = alpha sum_s P_s + beta C, summing the ranges in a fixed order,
 // so the result does not depend on scheduling.  Splitting K fills the SMs
 // when a GEMM has few output tiles for its K (1024^3: 64 tiles on 152 SMs).
+//
+// Real GEMMs (REAL = true; the SGEMM of Section 2.1 itself).  op(A) has two
+// planes (hi, lo), op(B) two planes (hi, lo) of 256 rows, and a tile is
+// 128 x 256 real outputs: per K step one N = 256 MMA of hi*hi into acc0 and
+// two of lo*hi and hi*lo into acc1, the same tensor-memory layout (the
+// "re" and "im" halves of an accumulator are output columns 0-127 and
+// 128-255 of the tile) and the same drain.  A stage is 48 KB, so four fit.
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -73,10 +80,21 @@ namespace {
 constexpr int kEpiWarps = 8;
 constexpr int kEpiCols = kBN / 2;  // columns per epilogue warp
 
+// Stage geometry of the complex (REAL = false) and real kernels.
+template <bool REAL>
+struct TcGeom {
+    static constexpr int stages = REAL ? 4 : kStages;
+    static constexpr int a_bytes = REAL ? 2 * kTileBytes : kAStageBytes;  // 16 | 32 KB
+    static constexpr int b_bytes = REAL ? 4 * kTileBytes : kBStageBytes;  // 32 | 40 KB
+    static constexpr int stage_bytes = a_bytes + b_bytes;                 // 48 | 72 KB
+    static constexpr int tile_n = REAL ? 2 * kBN : kBN;  // output columns of a tile
+};
+
+template <bool REAL>
 struct TcSmem {
-    uint8_t stage[kStages][kStageBytes];
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
+    uint8_t stage[TcGeom<REAL>::stages][TcGeom<REAL>::stage_bytes];
+    uint64_t full[TcGeom<REAL>::stages];
+    uint64_t empty[TcGeom<REAL>::stages];
     uint64_t acc0_full;
     uint64_t acc0_empty;
     uint64_t drain;
@@ -97,7 +115,8 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
     tn = r / gsize;
 }
 
-__device__ __forceinline__ void raise_abort(TcSmem &S, int *d_err, int code) {
+template <class Smem>
+__device__ __forceinline__ void raise_abort(Smem &S, int *d_err, int code) {
     *reinterpret_cast<volatile int *>(&S.abort) = 1;
     atomicCAS(d_err, 0, code);
 }
@@ -130,7 +149,7 @@ __device__ __forceinline__ Unit unit_of(int u, int tiles, int S) {
     return x;
 }
 
-template <int KIND, int DRAIN>
+template <int KIND, int DRAIN, bool REAL>
 __global__ void __launch_bounds__(kTcThreads, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                     const __grid_constant__ CUtensorMap mapB,
@@ -140,8 +159,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // a single GEMM that did not select this kind exits before touching anything
     if (w.G == 1 && !kind_runs(KIND, desc->mode)) return;
 
+    using Geo = TcGeom<REAL>;
+    constexpr int NST = Geo::stages;
     extern __shared__ uint8_t smem_raw[];
-    TcSmem &S = *reinterpret_cast<TcSmem *>(
+    TcSmem<REAL> &S = *reinterpret_cast<TcSmem<REAL> *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
 
     const int warp = threadIdx.x >> 5;
@@ -149,7 +170,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     volatile int *abort_flag = &S.abort;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&S.full[s], 1);
             mbar_init(&S.empty[s], 1);
         }
@@ -171,7 +192,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t tmem = S.tmem_base;
 
     const int tiles_m = (m + kBM - 1) / kBM;
-    const int tiles_n = (n + kBN - 1) / kBN;
+    const int tiles_n = (n + Geo::tile_n - 1) / Geo::tile_n;
     const int num_tiles = tiles_m * tiles_n;
     const int num_units = w.G * w.S * num_tiles;
     constexpr int kElemBytes = (KIND == 1) ? 4 : 2;
@@ -193,7 +214,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 int tm, tn;
                 tile_coords(x.t, tiles_m, tiles_n, group_m, tm, tn);
                 const int rowA = static_cast<int>(x.g * w.a_rows) + tm * kBM;
-                const int rowB = static_cast<int>(x.g * w.b_rows) + tn * kBN;
+                const int rowB = static_cast<int>(x.g * w.b_rows) + tn * Geo::tile_n;
                 const int kb1 = kb_begin(x.r + 1);
                 for (int kb = kb_begin(x.r); kb < kb1; ++kb) {
                     if (!mbar_wait(&S.empty[stage], phase ^ 1u, globaltimer_ns() + kWaitBudgetNs,
@@ -202,12 +223,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&S.full[stage], kStageBytes);
+                    mbar_arrive_expect_tx(&S.full[stage], Geo::stage_bytes);
                     tma_load_3d(S.stage[stage], &mapA, &S.full[stage], kb * kKPerStage, rowA, 0);
-                    tma_load_3d(S.stage[stage] + kAStageBytes, &mapB, &S.full[stage],
+                    tma_load_3d(S.stage[stage] + Geo::a_bytes, &mapB, &S.full[stage],
                                 kb * kKPerStage, rowB, 0);
                     ++issued;
-                    if (++stage == kStages) {
+                    if (++stage == NST) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -218,9 +239,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 // before this CTA's shared memory goes away.
                 int st = stage;
                 uint32_t ph = phase;
-                for (int i = 0; i < kStages && i < issued; ++i) {
-                    st = (st + kStages - 1) % kStages;
-                    if (st == kStages - 1) ph ^= 1u;
+                for (int i = 0; i < NST && i < issued; ++i) {
+                    st = (st + NST - 1) % NST;
+                    if (st == NST - 1) ph ^= 1u;
                     volatile int never = 0;
                     (void)mbar_wait(&S.full[st], ph, globaltimer_ns() + 100000000ull, &never);
                 }
@@ -272,20 +293,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     // 0 -Bi_hi, 1 Br_hi, 2 Bi_hi, 3 Br_lo, 4 Bi_lo; the 256-row
                     // operand at plane p covers planes p and p + 1.  K step ks
                     // starts 32 bytes into each 64-byte row.
+                    // Real kernel: A planes 0 hi, 1 lo; B planes of 256 rows, hi at
+                    // tile offset 0, lo at 2.
                     const uint64_t dA = sdesc_kmajor_sw64(smem_u32(S.stage[stage]));
-                    const uint64_t dB = dA + (kAStageBytes >> 4);
+                    const uint64_t dB = dA + (Geo::a_bytes >> 4);
 #define A_(ks, p) (dA + (uint64_t)(((p) * kTileBytes + (ks) * 32) >> 4))
 #define B_(ks, p) (dB + (uint64_t)(((p) * kTileBytes + (ks) * 32) >> 4))
                     // correction products: acc1 += lo*hi + hi*lo
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
                         const uint32_t first = (kb == kb0 && ks == 0) ? 0u : 1u;
-                        mma<KIND>(a1, A_(ks, 2), B_(ks, 1), id, first);   // Ar_lo [Br_hi; Bi_hi]
-                        mma<KIND>(a1, A_(ks, 3), B_(ks, 0), id, 1u);      // Ai_lo [-Bi_hi; Br_hi]
-                        mma<KIND>(a1r, A_(ks, 0), B_(ks, 3), idh, 1u);    //  Ar_hi Br_lo
-                        mma<KIND>(a1i, A_(ks, 0), B_(ks, 4), idh, 1u);    //  Ar_hi Bi_lo
-                        mma<KIND>(a1r, A_(ks, 1), B_(ks, 4), idhn, 1u);   // -Ai_hi Bi_lo
-                        mma<KIND>(a1i, A_(ks, 1), B_(ks, 3), idh, 1u);    //  Ai_hi Br_lo
+                        if constexpr (REAL) {
+                            mma<KIND>(a1, A_(ks, 1), B_(ks, 0), id, first);   // A_lo B_hi
+                            mma<KIND>(a1, A_(ks, 0), B_(ks, 2), id, 1u);      // A_hi B_lo
+                        } else {
+                            mma<KIND>(a1, A_(ks, 2), B_(ks, 1), id, first);   // Ar_lo [Br_hi; Bi_hi]
+                            mma<KIND>(a1, A_(ks, 3), B_(ks, 0), id, 1u);      // Ai_lo [-Bi_hi; Br_hi]
+                            mma<KIND>(a1r, A_(ks, 0), B_(ks, 3), idh, 1u);    //  Ar_hi Br_lo
+                            mma<KIND>(a1i, A_(ks, 0), B_(ks, 4), idh, 1u);    //  Ar_hi Bi_lo
+                            mma<KIND>(a1r, A_(ks, 1), B_(ks, 4), idhn, 1u);   // -Ai_hi Bi_lo
+                            mma<KIND>(a1i, A_(ks, 1), B_(ks, 3), idh, 1u);    //  Ai_hi Br_lo
+                        }
                     }
                     // hi*hi products: a fresh acc0 every DRAIN stages, once the
                     // previous one was drained
@@ -298,8 +326,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
                         const uint32_t first = (ks == 0 && group_start) ? 0u : 1u;
-                        mma<KIND>(a0, A_(ks, 0), B_(ks, 1), id, first);   // Ar_hi [Br_hi; Bi_hi]
-                        mma<KIND>(a0, A_(ks, 1), B_(ks, 0), id, 1u);      // Ai_hi [-Bi_hi; Br_hi]
+                        if constexpr (REAL) {
+                            mma<KIND>(a0, A_(ks, 0), B_(ks, 0), id, first);   // A_hi B_hi
+                        } else {
+                            mma<KIND>(a0, A_(ks, 0), B_(ks, 1), id, first);   // Ar_hi [Br_hi; Bi_hi]
+                            mma<KIND>(a0, A_(ks, 1), B_(ks, 0), id, 1u);      // Ai_hi [-Bi_hi; Br_hi]
+                        }
                     }
 #undef A_
 #undef B_
@@ -308,7 +340,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         tc_commit(&S.acc0_full);  // acc0 (and, on a tile's last stage, acc1) ready
                         pending = true;
                     }
-                    if (++stage == kStages) {
+                    if (++stage == NST) {
                         stage = 0;
                         phase ^= 1u;
                     }
@@ -391,6 +423,40 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             if (!ok) break;
             const int row = tm * kBM + q * 32 + lane;
+            if constexpr (REAL) {
+                // the two accumulator halves are output columns c0 and c0 + 128
+                if (row < m) {
+                    const int c0 = tn * Geo::tile_n + half * kEpiCols;
+                    float *out;
+                    int64_t ld;
+                    if (w.S > 1) {
+                        out = reinterpret_cast<float *>(w.P) +
+                              ((int64_t)x.r * w.G + x.g) * (int64_t)m * n + row;
+                        ld = m;
+                    } else {
+                        out = reinterpret_cast<float *>(C) + x.g * w.c_stride + row;
+                        ld = ldc;
+                    }
+                    const bool epi = w.S == 1;
+#pragma unroll
+                    for (int hv = 0; hv < 2; ++hv) {
+#pragma unroll
+                        for (int j = 0; j < kEpiCols; ++j) {
+                            const int col = c0 + hv * kBN + j;
+                            if (col < n) {
+                                float v = ((hv ? iacc[j] : racc[j]) * unA) * unB;
+                                float *dst = out + static_cast<int64_t>(col) * ld;
+                                if (epi) {
+                                    v *= alpha.x;
+                                    if (use_beta) v = fmaf(beta.x, *dst, v);
+                                }
+                                *dst = v;
+                            }
+                        }
+                    }
+                }
+                continue;
+            }
             const int col0 = tn * kBN + half * kEpiCols;
             if (w.S > 1) {
                 // a K range's partial, scaled back, into its [r][g] block (ld m)
@@ -473,23 +539,46 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-template <int KIND, int DRAIN>
+// The real counterpart: C_g = alpha sum_r P[r][g] + beta C_g over m x n
+// floats.
+__global__ void __launch_bounds__(256)
+    tc_splitk_reduce_real_kernel(const qcs_gemm_desc_t *__restrict__ desc, int G, int S,
+                                 int64_t m, int64_t n, const float *__restrict__ P, float alpha,
+                                 float beta, float *__restrict__ C, int64_t ldc, int64_t c_stride) {
+    const int g = blockIdx.y;
+    if (desc[g].mode == QCS_MODE_FP32) return;
+    const int64_t mn = m * n;
+    float *Cg = C + g * c_stride;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mn;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float acc = P[(int64_t)g * mn + i];
+        for (int r = 1; r < S; ++r) acc += P[((int64_t)r * G + g) * mn + i];
+        const int64_t col = i / m;
+        float *dst = Cg + col * ldc + (i - col * m);
+        float o = alpha * acc;
+        if (beta != 0.0f) o = fmaf(beta, *dst, o);
+        *dst = o;
+    }
+}
+
+template <int KIND, int DRAIN, bool REAL>
 cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
                         const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad, float2 alpha,
                         float2 beta, float2 *C, int64_t ldc, int *d_err, int num_sms,
                         int group_m, const TcWork &w, cudaStream_t s) {
-    const size_t smem = sizeof(TcSmem) + 1024;
+    const size_t smem = sizeof(TcSmem<REAL>) + 1024;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel<KIND, DRAIN>,
+        cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel<KIND, DRAIN, REAL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int64_t units = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN) * w.G * w.S;
+    constexpr int tn = TcGeom<REAL>::tile_n;
+    const int64_t units = ((m + kBM - 1) / kBM) * ((n + tn - 1) / tn) * w.G * w.S;
     if (units == 0 || k_pad == 0) return cudaSuccess;
     const int grid = static_cast<int>(units < num_sms ? units : num_sms);
-    cgemm_tc_kernel<KIND, DRAIN><<<grid, kTcThreads, smem, s>>>(
+    cgemm_tc_kernel<KIND, DRAIN, REAL><<<grid, kTcThreads, smem, s>>>(
         *mapA, *mapB, desc, (int)m, (int)n, (int)k_pad, alpha, beta, C, ldc, d_err,
         group_m < 1 ? 1 : group_m, w);
     return cudaGetLastError();
@@ -497,19 +586,38 @@ cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
 
 // ``drain``: pipeline stages per group, each two MMA K steps (32 k for the
 // 16-bit kinds, 16 for TF32).
-template <int KIND>
+template <int KIND, bool REAL>
 cudaError_t launch_drain(int drain, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
                          const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad,
                          float2 alpha, float2 beta, float2 *C, int64_t ldc, int *d_err,
                          int num_sms, int group_m, const TcWork &w, cudaStream_t s) {
     if (drain >= 4)
-        return launch_kind<KIND, 4>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                    num_sms, group_m, w, s);
+        return launch_kind<KIND, 4, REAL>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
+                                          d_err, num_sms, group_m, w, s);
     if (drain == 2)
-        return launch_kind<KIND, 2>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                    num_sms, group_m, w, s);
-    return launch_kind<KIND, 1>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                num_sms, group_m, w, s);
+        return launch_kind<KIND, 2, REAL>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
+                                          d_err, num_sms, group_m, w, s);
+    return launch_kind<KIND, 1, REAL>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
+                                      num_sms, group_m, w, s);
+}
+
+template <bool REAL>
+cudaError_t launch_any(int kind, int drain, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
+                       const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad, float2 alpha,
+                       float2 beta, float2 *C, int64_t ldc, int *d_err, int num_sms, int group_m,
+                       cudaStream_t s, const TcWork &w) {
+    if (w.G < 1 || w.S < 1 || (w.S > 1 && !w.P)) return cudaErrorInvalidValue;
+    switch (kind) {
+        case 0:
+            return launch_drain<0, REAL>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
+                                         d_err, num_sms, group_m, w, s);
+        case 1:
+            return launch_drain<1, REAL>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
+                                         d_err, num_sms, group_m, w, s);
+        default:
+            return launch_drain<2, REAL>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
+                                         d_err, num_sms, group_m, w, s);
+    }
 }
 
 }  // namespace
@@ -519,18 +627,18 @@ cudaError_t launch_cgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
                             int64_t n, int64_t k_pad, float2 alpha, float2 beta, float2 *C,
                             int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s,
                             const TcWork &w) {
-    if (w.G < 1 || w.S < 1 || (w.S > 1 && !w.P)) return cudaErrorInvalidValue;
-    switch (kind) {
-        case 0:
-            return launch_drain<0>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                   d_err, num_sms, group_m, w, s);
-        case 1:
-            return launch_drain<1>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                   d_err, num_sms, group_m, w, s);
-        default:
-            return launch_drain<2>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                   d_err, num_sms, group_m, w, s);
-    }
+    return launch_any<false>(kind, drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
+                             d_err, num_sms, group_m, s, w);
+}
+
+cudaError_t launch_sgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
+                            const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
+                            int64_t n, int64_t k_pad, float alpha, float beta, float *C,
+                            int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s,
+                            const TcWork &w) {
+    return launch_any<true>(kind, drain, desc, mapA, mapB, m, n, k_pad, make_float2(alpha, 0.f),
+                            make_float2(beta, 0.f), reinterpret_cast<float2 *>(C), ldc, d_err,
+                            num_sms, group_m, s, w);
 }
 
 cudaError_t launch_tc_reduce(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, float2 alpha,
@@ -546,24 +654,42 @@ cudaError_t launch_tc_reduce(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, 
     return cudaGetLastError();
 }
 
-// Stages of the K loop per unit are ~1.2 us on one SM (measured: 16384^3
-// FP16X, 16384 tiles x 512 stages over 152 SMs in 67 ms); the partials cost
-// (2 S + 1) m n 8 bytes of HBM traffic per GEMM at ~6 TB/s plus a launch.
-// The count minimises waves x stages per unit + that cost.
-int tc_split_count(int64_t m, int64_t n, int64_t k, int64_t G, int num_sms, int forced) {
+cudaError_t launch_tc_reduce_real(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, float alpha,
+                                  float beta, float *C, int64_t ldc, int num_sms, const TcWork &w,
+                                  cudaStream_t s) {
+    if (w.S <= 1 || m == 0 || n == 0) return cudaSuccess;
+    const int64_t blocks_needed = (m * n + 255) / 256;
+    const int64_t cap = (int64_t)num_sms * 8;
+    dim3 grid(static_cast<unsigned>(blocks_needed < cap ? blocks_needed : cap),
+              static_cast<unsigned>(w.G));
+    tc_splitk_reduce_real_kernel<<<grid, 256, 0, s>>>(desc, w.G, w.S, m, n,
+                                                      reinterpret_cast<const float *>(w.P), alpha,
+                                                      beta, C, ldc, w.c_stride);
+    return cudaGetLastError();
+}
+
+// Stages of the K loop per unit are ~1.2 us on one SM for a complex tile
+// (measured: 16384^3 FP16X, 16384 tiles x 512 stages over 152 SMs in 67 ms)
+// and take half the MMAs for a real one; the partials cost (2 S + 1) m n
+// bytes-per-output of HBM traffic per GEMM at ~6 TB/s plus a launch.  The
+// count minimises waves x stages per unit + that cost.
+int tc_split_count(int64_t m, int64_t n, int64_t k, int64_t G, int num_sms, int forced,
+                   bool real) {
     const int64_t nkb = (k + 31) / 32;  // 16-bit stages (TF32 has twice as many)
     if (nkb <= 1) return 1;
     if (forced > 0) return static_cast<int>(forced < nkb ? forced : nkb);
-    const int64_t tiles = ((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN) * G;
+    const int64_t tile_n = real ? 2 * kBN : kBN;
+    const int64_t tiles = ((m + kBM - 1) / kBM) * ((n + tile_n - 1) / tile_n) * G;
     if (tiles == 0 || num_sms <= 0) return 1;
-    const double stage_us = 1.2;
+    const double stage_us = real ? 0.65 : 1.2;
+    const double out_bytes = real ? 4.0 : 8.0;
     double best = -1.0;
     int best_s = 1;
     for (int S = 1; S <= kMaxSplits && S <= nkb; ++S) {
         const int64_t units = tiles * S;
         const int64_t waves = (units + num_sms - 1) / num_sms;
         double t = (double)waves * (double)((nkb + S - 1) / S) * stage_us;
-        if (S > 1) t += (2.0 * S + 1.0) * (double)(m * n * G) * 8.0 / 6.0e6 + 4.0;
+        if (S > 1) t += (2.0 * S + 1.0) * (double)(m * n * G) * out_bytes / 6.0e6 + 4.0;
         if (best < 0 || t < best * 0.97) {  // a split must win by 3% to be taken
             best = t;
             best_s = S;

@@ -290,7 +290,9 @@ constexpr int kMaxSplits = 16;
 // K ranges for a launch over G GEMMs of m x n x k: ``forced`` > 0 is taken
 // (at most one range per 32 k), 0 chooses from the wave count and the cost
 // of the partials.
-int tc_split_count(int64_t m, int64_t n, int64_t k, int64_t G, int num_sms, int forced);
+// ``real``: the real kernel's 128 x 256 tiles and 4-byte outputs.
+int tc_split_count(int64_t m, int64_t n, int64_t k, int64_t G, int num_sms, int forced,
+                   bool real = false);
 
 // Tensor-core emulated CGEMM over split planes.  ``kind``: 0 FP16 (modes
 // FP16X, FP16X_SCALED), 1 TF32, 2 BF16; the kernel returns at once unless
@@ -307,5 +309,43 @@ cudaError_t launch_cgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
 cudaError_t launch_tc_reduce(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, float2 alpha,
                              float2 beta, float2 *C, int64_t ldc, int num_sms, const TcWork &w,
                              cudaStream_t s);
+
+// ---- real GEMM (qcs_sgemm) ------------------------------------------------
+// The two-stage statistics + selection over real matrices (one scalar per
+// element); otherwise as launch_stats_select_2stage.
+cudaError_t launch_stats_select_2stage_real(const float *X0, int64_t rows0, int64_t cols0,
+                                            int64_t ld0, int gA, const float *X1, int64_t rows1,
+                                            int64_t cols1, int64_t ld1, int gB, double tol,
+                                            int forced, int64_t *p1, int64_t *p2,
+                                            qcs_gemm_desc_t *desc, unsigned long long *counts,
+                                            double work, cudaStream_t s);
+// Split a real op(X) (element (r, c) at X[r sr + c sc]) into the planes hi
+// and lo (R_pad x K_pad, pitch elements per row, plane_stride apart), zero
+// beyond R x K; elements of the kind the descriptor selected.
+cudaError_t launch_split_real(const qcs_gemm_desc_t *desc, int which, const float *X, int64_t sr,
+                              int64_t sc, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
+                              void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s);
+// Plain FP32 real GEMM (runs only when desc->mode == FP32, or always when
+// desc is NULL).
+cudaError_t launch_sgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int64_t m,
+                              int64_t n, int64_t k, float alpha, const float *A, int64_t lda,
+                              const float *B, int64_t ldb, float beta, float *C, int64_t ldc,
+                              cudaStream_t s);
+// The tensor-core kernel on real planes: A two planes (hi, lo) read in
+// 128-row boxes, B two planes in 256-row boxes, tiles of 128 x 256 floats of
+// C; w.P (when w.S > 1) holds S G m n floats.
+cudaError_t launch_sgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
+                            const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
+                            int64_t n, int64_t k_pad, float alpha, float beta, float *C,
+                            int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s,
+                            const TcWork &w = TcWork{});
+cudaError_t launch_tc_reduce_real(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, float alpha,
+                                  float beta, float *C, int64_t ldc, int num_sms, const TcWork &w,
+                                  cudaStream_t s);
+// Workspace of one real GEMM and its launch sequence (as run_cgemm, G = 1).
+size_t sgemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits);
+int run_sgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n, int64_t k,
+              float alpha, const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
+              float *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out);
 
 }  // namespace qcs

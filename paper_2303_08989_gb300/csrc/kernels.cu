@@ -17,6 +17,8 @@
 //                     baseline and mode).
 //   cgemm_skinny_kernel  bandwidth-bound CGEMM for very small m, n or k
 //                     (Section 5.3.2 irregular shapes).
+//   split_real_kernel, sgemm_simt_kernel, the statistics on float input:
+//                     the same stages for real operands (qcs_sgemm).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -322,6 +324,50 @@ __device__ __forceinline__ void for_each_scalar(const float2 *X, int64_t rows, i
     }
 }
 
+// The same walk over a real matrix (one scalar per element).
+template <class F>
+__device__ __forceinline__ void for_each_scalar(const float *X, int64_t rows, int64_t cols,
+                                                int64_t ld, int64_t gtid, int64_t gstride, F f) {
+    const int64_t nel = rows * cols;
+    if (nel <= 0) return;
+    if (ld == rows && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
+        const float4 *p = reinterpret_cast<const float4 *>(X);
+        const int64_t n4 = nel >> 2;
+        constexpr int U = 8;
+        int64_t i = gtid;
+        for (; i + (U - 1) * gstride < n4; i += U * gstride) {
+            float4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = __ldcs(p + i + u * gstride);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                f(v[u].x);
+                f(v[u].y);
+                f(v[u].z);
+                f(v[u].w);
+            }
+        }
+        for (; i < n4; i += gstride) {
+            const float4 v = __ldcs(p + i);
+            f(v.x);
+            f(v.y);
+            f(v.z);
+            f(v.w);
+        }
+        if (gtid == 0)
+            for (int64_t t = n4 << 2; t < nel; ++t) f(X[t]);
+    } else {
+        for (int64_t i = gtid; i < nel; i += gstride) {
+            const int64_t c = i / rows, r = i - c * rows;
+            f(X[r + c * ld]);
+        }
+    }
+}
+
+// Scalars per element: 2 for complex64, 1 for float.
+template <class T>
+__host__ __device__ constexpr int64_t scalars_per() { return (int64_t)(sizeof(T) / sizeof(float)); }
+
 __device__ __forceinline__ uint32_t block_max(uint32_t v, uint32_t *sh) {
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -344,14 +390,15 @@ __device__ __forceinline__ uint64_t block_sum(uint64_t v, uint64_t *sh) {
     return r;
 }
 
+template <class T>
 __global__ void __launch_bounds__(kS2Threads) stats_pass1_kernel(
-    const float2 *__restrict__ X0, int64_t rows0, int64_t cols0, int64_t ld0, int gA,
-    const float2 *__restrict__ X1, int64_t rows1, int64_t cols1, int64_t ld1, int gB,
+    const T *__restrict__ X0, int64_t rows0, int64_t cols0, int64_t ld0, int gA,
+    const T *__restrict__ X1, int64_t rows1, int64_t cols1, int64_t ld1, int gB,
     int64_t *__restrict__ p1) {
     __shared__ uint32_t shm[kS2Threads / 32];
     __shared__ uint64_t shs[kS2Threads / 32];
     const bool first = blockIdx.x < gA;
-    const float2 *X = first ? X0 : X1;
+    const T *X = first ? X0 : X1;
     const int64_t blk = first ? blockIdx.x : blockIdx.x - gA;
     const int64_t nblk = first ? gA : gB;
     Acc1 a{0u, 0u, 0u, 0u};
@@ -410,19 +457,20 @@ __device__ bool needs_stage2(const Sum1 &a, const Sum1 &b, double tol, int force
     return !(ok1(a) && ok1(b));
 }
 
+template <class T>
 __global__ void __launch_bounds__(kS2Threads) stats_pass2_kernel(
-    const float2 *__restrict__ X0, int64_t rows0, int64_t cols0, int64_t ld0, int gA,
-    const float2 *__restrict__ X1, int64_t rows1, int64_t cols1, int64_t ld1, int gB,
+    const T *__restrict__ X0, int64_t rows0, int64_t cols0, int64_t ld0, int gA,
+    const T *__restrict__ X1, int64_t rows1, int64_t cols1, int64_t ld1, int gB,
     const int64_t *__restrict__ p1, double tol, int forced, int64_t *__restrict__ p2) {
     __shared__ uint64_t shs[kS2Threads / 32];
     __shared__ uint32_t shm[kS2Threads / 32];
-    const Sum1 a = reduce_p1(p1, 0, gA, 2 * rows0 * cols0, shm, shs);
-    const Sum1 b = reduce_p1(p1, gA, gA + gB, 2 * rows1 * cols1, shm, shs);
+    const Sum1 a = reduce_p1(p1, 0, gA, scalars_per<T>() * rows0 * cols0, shm, shs);
+    const Sum1 b = reduce_p1(p1, gA, gA + gB, scalars_per<T>() * rows1 * cols1, shm, shs);
     if (!needs_stage2(a, b, tol, forced)) return;  // uniform across the block
     const int64_t bmax = (blockIdx.x < gA) ? a.bmax : b.bmax;
     const uint32_t thr = (uint32_t)(bmax - 28 > 1 ? bmax - 28 : 1);  // biased exponents below are outside
     const bool first = blockIdx.x < gA;
-    const float2 *X = first ? X0 : X1;
+    const T *X = first ? X0 : X1;
     const int64_t blk = first ? blockIdx.x : blockIdx.x - gA;
     const int64_t nblk = first ? gA : gB;
     uint32_t under2 = 0;
@@ -499,22 +547,43 @@ cudaError_t launch_select(const int64_t *partials, int gA, int gB, int64_t nA, i
     return cudaGetLastError();
 }
 
+template <class T>
+static cudaError_t stats_select_2stage(const T *X0, int64_t rows0, int64_t cols0, int64_t ld0,
+                                       int gA, const T *X1, int64_t rows1, int64_t cols1,
+                                       int64_t ld1, int gB, double tol, int forced, int64_t *p1,
+                                       int64_t *p2, qcs_gemm_desc_t *desc,
+                                       unsigned long long *counts, double work, cudaStream_t s) {
+    stats_pass1_kernel<T><<<gA + gB, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1,
+                                                         cols1, ld1, gB, p1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    stats_pass2_kernel<T><<<gA + gB, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1,
+                                                         cols1, ld1, gB, p1, tol, forced, p2);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    select2_kernel<<<1, kS2Threads, 0, s>>>(p1, p2, gA, gB, scalars_per<T>() * rows0 * cols0,
+                                            scalars_per<T>() * rows1 * cols1, tol, forced, desc,
+                                            counts, work);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t cols0, int64_t ld0,
                                        int gA, const float2 *X1, int64_t rows1, int64_t cols1,
                                        int64_t ld1, int gB, double tol, int forced, int64_t *p1,
                                        int64_t *p2, qcs_gemm_desc_t *desc,
                                        unsigned long long *counts, double work, cudaStream_t s) {
-    stats_pass1_kernel<<<gA + gB, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1, cols1,
-                                                      ld1, gB, p1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    stats_pass2_kernel<<<gA + gB, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1, cols1,
-                                                      ld1, gB, p1, tol, forced, p2);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    select2_kernel<<<1, kS2Threads, 0, s>>>(p1, p2, gA, gB, 2 * rows0 * cols0, 2 * rows1 * cols1,
-                                            tol, forced, desc, counts, work);
-    return cudaGetLastError();
+    return stats_select_2stage(X0, rows0, cols0, ld0, gA, X1, rows1, cols1, ld1, gB, tol, forced,
+                               p1, p2, desc, counts, work, s);
+}
+
+cudaError_t launch_stats_select_2stage_real(const float *X0, int64_t rows0, int64_t cols0,
+                                            int64_t ld0, int gA, const float *X1, int64_t rows1,
+                                            int64_t cols1, int64_t ld1, int gB, double tol,
+                                            int forced, int64_t *p1, int64_t *p2,
+                                            qcs_gemm_desc_t *desc, unsigned long long *counts,
+                                            double work, cudaStream_t s) {
+    return stats_select_2stage(X0, rows0, cols0, ld0, gA, X1, rows1, cols1, ld1, gB, tol, forced,
+                               p1, p2, desc, counts, work, s);
 }
 
 cudaError_t launch_select_from_stats(const qcs_stats_t *a, const qcs_stats_t *b, double tol,
@@ -705,6 +774,107 @@ cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X
     if (grid.y > 65535u) return cudaErrorInvalidValue;
     split_kernel<<<grid, 256, 0, s>>>(desc, which, X, sr, sc, conj, R, K, R_pad, K_pad, planes,
                                       pitch, plane_stride, planes6, plane_off, planes32);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// Eq. 1 for a real operand: op(X) (R x K, element (r, c) at X[r sr + c sc])
+// into two planes, hi and lo, of R_pad x K_pad (row pitch ``pitch``, planes
+// ``plane_stride`` elements apart), zero beyond R x K.  Elements are FP16,
+// BF16 (2 bytes) or TF32 (4 bytes), the kind the descriptor selected.
+__global__ void __launch_bounds__(256) split_real_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int which, const float *__restrict__ X, int64_t sr,
+    int64_t sc, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad, void *planes, int64_t pitch,
+    int64_t plane_stride) {
+    const int mode = desc->mode;
+    if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
+    const int s = (mode == QCS_MODE_FP16X_SCALED) ? (which == 0 ? desc->sA : desc->sB) : 0;
+    const Pow2Scale ps2 = pow2_scale(s);
+
+    __shared__ float tile[kSplitR][kSplitC + 1];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.y) * kSplitR;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kSplitC;
+    if (sc == 1) {
+#pragma unroll
+        for (int i = 0; i < kSplitR / 8; ++i) {
+            const int rr = warp + 8 * i;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int cc = lane + 32 * h;
+                float v = 0.f;
+                if (r0 + rr < R && c0 + cc < K) v = X[(r0 + rr) * sr + (c0 + cc)];
+                tile[rr][cc] = v;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kSplitC / 8; ++i) {
+            const int cc = warp + 8 * i;
+            const int rr = lane;
+            float v = 0.f;
+            if (r0 + rr < R && c0 + cc < K) v = X[(r0 + rr) * sr + (c0 + cc) * sc];
+            tile[rr][cc] = v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kSplitR / 8; ++i) {
+        const int rr = warp + 8 * i;
+        const int64_t r = r0 + rr;
+        const int cc = 2 * lane;
+        const int64_t c = c0 + cc;
+        if (r >= R_pad || c >= K_pad) continue;
+        uint32_t hib[2], lob[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float x = tile[rr][cc + e];
+            split_value(mode, (s != 0) ? apply_scale(x, ps2) : x, hib[e], lob[e]);
+        }
+        const bool two = (c + 1 < K_pad);
+        if (mode == QCS_MODE_TF32X) {
+            uint32_t *p = static_cast<uint32_t *>(planes) + r * pitch + c;
+            const bool vec = two && ((reinterpret_cast<uintptr_t>(p) & 7u) == 0);
+            if (vec) {
+                *reinterpret_cast<uint2 *>(p) = make_uint2(hib[0], hib[1]);
+                *reinterpret_cast<uint2 *>(p + plane_stride) = make_uint2(lob[0], lob[1]);
+            } else {
+                p[0] = hib[0];
+                p[plane_stride] = lob[0];
+                if (two) {
+                    p[1] = hib[1];
+                    p[plane_stride + 1] = lob[1];
+                }
+            }
+        } else {
+            uint16_t *p = static_cast<uint16_t *>(planes) + r * pitch + c;
+            const bool vec = two && ((reinterpret_cast<uintptr_t>(p) & 3u) == 0);
+            if (vec) {
+                *reinterpret_cast<uint32_t *>(p) = hib[0] | (hib[1] << 16);
+                *reinterpret_cast<uint32_t *>(p + plane_stride) = lob[0] | (lob[1] << 16);
+            } else {
+                p[0] = (uint16_t)hib[0];
+                p[plane_stride] = (uint16_t)lob[0];
+                if (two) {
+                    p[1] = (uint16_t)hib[1];
+                    p[plane_stride + 1] = (uint16_t)lob[1];
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_split_real(const qcs_gemm_desc_t *desc, int which, const float *X, int64_t sr,
+                              int64_t sc, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
+                              void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s) {
+    if (R_pad <= 0 || K_pad <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((K_pad + kSplitC - 1) / kSplitC), (unsigned)((R_pad + kSplitR - 1) / kSplitR));
+    if (grid.y > 65535u) return cudaErrorInvalidValue;
+    split_real_kernel<<<grid, 256, 0, s>>>(desc, which, X, sr, sc, R, K, R_pad, K_pad, planes,
+                                           pitch, plane_stride);
     return cudaGetLastError();
 }
 
@@ -1842,6 +2012,147 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
     if (grid.y > 65535u) return cudaErrorInvalidValue;
     cgemm_simt_kernel<<<grid, 256, 0, s>>>(desc, opA, opB, (int)m, (int)n, (int)k, alpha, A, lda, B,
                                            ldb, beta, C, ldc, bt);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// Plain FP32 real GEMM (the FP32 mode of qcs_sgemm and its AUTO candidate)
+// ===========================================================================
+
+namespace {
+
+constexpr int kRT = 128;    // output rows and columns of a tile
+constexpr int kRK = 8;      // k per shared-memory step
+constexpr int kRPad = 132;  // row length of a shared tile (transposed stores spread over banks)
+
+// C = alpha op(A) op(B) + beta C on the CUDA cores: 128 x 128 tiles, 256
+// threads with 8 x 8 outputs each (rows 4t..4t+3 and 64+4t..64+4t+3 of the
+// tile, likewise columns), the next k step loaded into registers while the
+// current one is multiplied.  Runs only when the descriptor selected FP32
+// (always when desc is NULL).  Tiles in y are walked in a grid-stride loop.
+__global__ void __launch_bounds__(256, 2) sgemm_simt_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int64_t k,
+    float alpha, const float *__restrict__ A, int64_t lda, const float *__restrict__ B,
+    int64_t ldb, float beta, float *__restrict__ C, int64_t ldc) {
+    if (desc && desc->mode != QCS_MODE_FP32) return;
+    __shared__ __align__(16) float As[2][kRK][kRPad];
+    __shared__ __align__(16) float Bs[2][kRK][kRPad];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    // element (i, l) of op(A) is A[i sAi + l sAl]; (l, j) of op(B) is B[l sBl + j sBj]
+    const int64_t sAi = (opA == QCS_OP_N) ? 1 : lda, sAl = (opA == QCS_OP_N) ? lda : 1;
+    const int64_t sBl = (opB == QCS_OP_N) ? 1 : ldb, sBj = (opB == QCS_OP_N) ? ldb : 1;
+    const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kRT;
+    const int64_t tiles_n = (n + kRT - 1) / kRT;
+    for (int64_t tj = blockIdx.y; tj < tiles_n; tj += gridDim.y) {
+        const int64_t j0 = tj * kRT;
+        float ra[4], rb[4];
+        // loads of a k step: 1024 elements of each operand, 4 per thread,
+        // consecutive threads along the operand's contiguous index
+        auto load = [&](int64_t l0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int idx = tid + 256 * q;
+                int i, l;
+                if (sAi == 1) { i = idx & 127; l = idx >> 7; } else { l = idx & 7; i = idx >> 3; }
+                const int64_t gi = i0 + i, gl = l0 + l;
+                ra[q] = (gi < m && gl < k) ? A[gi * sAi + gl * sAl] : 0.f;
+                int j, lb;
+                if (sBj == 1) { j = idx & 127; lb = idx >> 7; } else { lb = idx & 7; j = idx >> 3; }
+                const int64_t gj = j0 + j, glb = l0 + lb;
+                rb[q] = (gj < n && glb < k) ? B[glb * sBl + gj * sBj] : 0.f;
+            }
+        };
+        auto store = [&](int buf) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int idx = tid + 256 * q;
+                if (sAi == 1) As[buf][idx >> 7][idx & 127] = ra[q];
+                else As[buf][idx & 7][idx >> 3] = ra[q];
+                if (sBj == 1) Bs[buf][idx >> 7][idx & 127] = rb[q];
+                else Bs[buf][idx & 7][idx >> 3] = rb[q];
+            }
+        };
+        float acc[8][8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+        __syncthreads();  // the previous tile's readers are done with both buffers
+        load(0);
+        store(0);
+        __syncthreads();
+        int buf = 0;
+        for (int64_t l0 = 0; l0 < k; l0 += kRK) {
+            const bool more = l0 + kRK < k;
+            if (more) load(l0 + kRK);
+#pragma unroll
+            for (int kk = 0; kk < kRK; ++kk) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][tx * 4]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + tx * 4]);
+                const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][ty * 4]);
+                const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + ty * 4]);
+                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+            }
+            if (more) {
+                store(buf ^ 1);
+                __syncthreads();
+                buf ^= 1;
+            }
+        }
+        const bool vec = ((reinterpret_cast<uintptr_t>(C) & 15u) == 0) && (ldc % 4 == 0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int64_t col = j0 + (c < 4 ? ty * 4 + c : 64 + ty * 4 + (c - 4));
+            if (col >= n) continue;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t row = i0 + h * 64 + tx * 4;
+                float *dst = C + col * ldc + row;
+                float v[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) v[r] = alpha * acc[h * 4 + r][c];
+                if (vec && row + 3 < m) {
+                    if (beta != 0.0f) {
+                        const float4 o = *reinterpret_cast<const float4 *>(dst);
+                        v[0] = fmaf(beta, o.x, v[0]);
+                        v[1] = fmaf(beta, o.y, v[1]);
+                        v[2] = fmaf(beta, o.z, v[2]);
+                        v[3] = fmaf(beta, o.w, v[3]);
+                    }
+                    *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        if (row + r < m) {
+                            float o = v[r];
+                            if (beta != 0.0f) o = fmaf(beta, dst[r], o);
+                            dst[r] = o;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int64_t m,
+                              int64_t n, int64_t k, float alpha, const float *A, int64_t lda,
+                              const float *B, int64_t ldb, float beta, float *C, int64_t ldc,
+                              cudaStream_t s) {
+    if (m == 0 || n == 0) return cudaSuccess;
+    const int64_t gx = (m + kRT - 1) / kRT, gy = (n + kRT - 1) / kRT;
+    if (gx > INT32_MAX) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)gx, (unsigned)(gy < 65535 ? gy : 65535));
+    sgemm_simt_kernel<<<grid, 256, 0, s>>>(desc, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C,
+                                           ldc);
     return cudaGetLastError();
 }
 

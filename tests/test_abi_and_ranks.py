@@ -29,14 +29,14 @@ def test_library_loads_and_exports_every_declared_symbol():
 
 
 def test_cublas_interception_library_exports_its_entry_points():
-    """libqcs_cublas.so (the drop-in route) defines the cuBLAS complex GEMMs
-    it intercepts and its counter, and finds libqcs.so next to itself."""
+    """libqcs_cublas.so (the drop-in route) defines the cuBLAS GEMMs it
+    intercepts and its counter, and finds libqcs.so next to itself."""
     from paper_2303_08989_gb300 import build
 
     build.build()
     shim = ctypes.CDLL(build.SHIM)
     for name in ("cublasCgemm_v2", "cublasCgemmStridedBatched", "cublasCgemmBatched",
-                 "qcs_cublas_shim_counts"):
+                 "cublasSgemm_v2", "cublasSgemmStridedBatched", "qcs_cublas_shim_counts"):
         assert hasattr(shim, name), name
     taken, passed = ctypes.c_longlong(-1), ctypes.c_longlong(-1)
     shim.qcs_cublas_shim_counts(ctypes.byref(taken), ctypes.byref(passed))

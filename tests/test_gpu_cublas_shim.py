@@ -1,8 +1,9 @@
 """The drop-in route of the paper's library (Section 3): an unmodified
-application's cuBLAS complex GEMMs, redirected by libqcs_cublas.so loaded
-ahead of cuBLAS, run as emulated CGEMMs.  Here the application is PyTorch in
-a child process started with LD_PRELOAD: torch.matmul (cublasCgemm) and
-torch.bmm (cublasCgemmStridedBatched) on complex64 CUDA tensors.  Results are
+application's cuBLAS GEMMs, redirected by libqcs_cublas.so loaded ahead of
+cuBLAS, run as emulated GEMMs.  Here the application is PyTorch in a child
+process started with LD_PRELOAD: torch.matmul (cublasCgemm, cublasSgemm) and
+torch.bmm (cublasCgemmStridedBatched, cublasSgemmStridedBatched) on complex64
+and float32 CUDA tensors.  Results are
 checked against the FP64 oracle, and the library's own counters show which
 calls it took and which it passed to cuBLAS."""
 import json
@@ -33,11 +34,15 @@ Ab = torch.from_numpy(d["Ab"]).cuda()
 Bb = torch.from_numpy(d["Bb"]).cuda()
 C = torch.matmul(A, B)
 Cb = torch.bmm(Ab, Bb)
+torch.backends.cuda.matmul.allow_tf32 = False
+R = torch.matmul(A.real.contiguous(), B.real.contiguous())
+Rb = torch.bmm(Ab.real.contiguous(), Bb.real.contiguous())
 torch.cuda.synchronize()
 shim = ctypes.CDLL(sys.argv[2])
 taken, passed = ctypes.c_longlong(), ctypes.c_longlong()
 shim.qcs_cublas_shim_counts(ctypes.byref(taken), ctypes.byref(passed))
-np.savez(sys.argv[3], C=C.cpu().numpy(), Cb=Cb.cpu().numpy())
+np.savez(sys.argv[3], C=C.cpu().numpy(), Cb=Cb.cpu().numpy(), R=R.cpu().numpy(),
+         Rb=Rb.cpu().numpy())
 print(json.dumps({"taken": taken.value, "passed": passed.value}))
 """
 
@@ -66,34 +71,38 @@ def _run_child(tmp_path, env_extra):
     errs = {"matmul": oracle.rel_fro_error(res["C"], A64 @ B64),
             "bmm": max(oracle.rel_fro_error(res["Cb"][b], Ab[b].astype(np.complex128)
                                             @ Bb[b].astype(np.complex128))
-                       for b in range(batch))}
+                       for b in range(batch)),
+            "smatmul": oracle.rel_fro_error(res["R"], A64.real @ B64.real),
+            "sbmm": max(oracle.rel_fro_error(res["Rb"][b], Ab[b].real.astype(np.float64)
+                                             @ Bb[b].real.astype(np.float64))
+                        for b in range(batch))}
     return counts, errs
 
 
 def test_cublas_complex_gemms_run_emulated(tmp_path):
-    """QCS_CUBLAS_MODE=auto with the size rule off: both calls run through
-    qcs_cgemm (statistics, selection, tensor-core emulation) at FP32-level
-    error."""
+    """QCS_CUBLAS_MODE=auto with the size rule off: all four calls run
+    through qcs_cgemm / qcs_sgemm (statistics, selection, tensor-core
+    emulation) at FP32-level error."""
     need_gpu()
     assert os.path.exists(SHIM), "build() makes libqcs_cublas.so"
     counts, errs = _run_child(tmp_path, {"QCS_CUBLAS_MODE": "auto", "QCS_SIZE_RULE": "0",
                                          "QCS_UNDERFLOW_TOL": "0.1"})
-    assert counts == {"taken": 2, "passed": 0}, counts
-    assert errs["matmul"] < 1e-6 and errs["bmm"] < 1e-6, errs
+    assert counts == {"taken": 4, "passed": 0}, counts
+    assert max(errs.values()) < 1e-6, errs
 
 
 @pytest.mark.parametrize("mode", ["tf32x", "fp32"])
 def test_cublas_shim_forced_modes(tmp_path, mode):
     need_gpu()
     counts, errs = _run_child(tmp_path, {"QCS_CUBLAS_MODE": mode})
-    assert counts == {"taken": 2, "passed": 0}, counts
+    assert counts == {"taken": 4, "passed": 0}, counts
     bar = 1e-6 if mode == "tf32x" else 5e-6
-    assert errs["matmul"] < bar and errs["bmm"] < bar, errs
+    assert max(errs.values()) < bar, errs
 
 
 def test_cublas_shim_passes_through_when_asked(tmp_path):
     """QCS_CUBLAS_MODE=cublas: every call goes to the next cuBLAS definition."""
     need_gpu()
     counts, errs = _run_child(tmp_path, {"QCS_CUBLAS_MODE": "cublas"})
-    assert counts == {"taken": 0, "passed": 2}, counts
-    assert errs["matmul"] < 1e-4 and errs["bmm"] < 1e-4, errs
+    assert counts == {"taken": 0, "passed": 4}, counts
+    assert max(errs.values()) < 1e-4, errs
