@@ -62,13 +62,15 @@ def parse():
     p.add_argument("--greedy-trials", type=int, default=256,
                    help="seeded greedy orders tried per network (the cheapest is contracted)")
     p.add_argument("--sweep-sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192, 16384])
-    p.add_argument("--profile", choices=["slice", "slice_seed2", "gather", "gemm"], default=None,
+    p.add_argument("--profile", choices=["slice", "slice_seed2", "gather", "gemm", "sgemm"],
+                   default=None,
                    help="run one workload for an ncu capture (NVTX range 'measure') and exit: "
                         "'slice' one group of 16 slices of the 30-qubit network in the cheapest "
                         "of --greedy-trials greedy orders (AUTO-t, tuned rule), 'slice_seed2' one "
                         "slice in the "
                         "order of seed 2, 'gather' a random permutation of 2^26 elements, 'gemm' "
-                        "ten qcs_cgemm calls of --gemm-shape in --mode")
+                        "ten qcs_cgemm calls of --gemm-shape in --mode, 'sgemm' ten qcs_sgemm "
+                        "calls of --gemm-shape in --mode")
     p.add_argument("--gemm-shape", type=int, nargs=3, default=[2048, 8192, 32],
                    metavar=("M", "N", "K"), help="the GEMM of --profile gemm")
     p.add_argument("--tuning-file", default=None,
@@ -311,6 +313,18 @@ def profile_run(args):
             for _ in range(10):
                 q.cgemm(h, A, B, C, mode=args.mode)
         what = "10 x qcs_cgemm (%d, %d, %d), mode %s, parts N(0,1)" % (m, n, k, args.mode)
+    elif args.profile == "sgemm":
+        m, n, k = args.gemm_shape
+        g = torch.Generator(device=dev).manual_seed(9)
+        A = torch.randn((k, m), dtype=torch.float32, device=dev, generator=g).t()
+        B = torch.randn((n, k), dtype=torch.float32, device=dev, generator=g).t()
+        C = q.fortran_empty_real(m, n, device=dev)
+        h = q.Handle(tol=args.tol, size_rule=False)
+
+        def run():
+            for _ in range(10):
+                q.sgemm(h, A, B, C, mode=args.mode)
+        what = "10 x qcs_sgemm (%d, %d, %d), mode %s, entries N(0,1)" % (m, n, k, args.mode)
     else:
         r = 26
         g = torch.Generator(device="cpu").manual_seed(5)
