@@ -18,7 +18,8 @@ What it computes, each following a passage of the paper (Ootomo et al. 2023):
   and the mode-selection rule of Section 4.1, and the size rule of
   Section 4.3.
 * ``tcec_cgemm``: the emulated product of Eq. 1 with the complex expansion of
-  Section 3, evaluated exactly in FP64.
+  Section 3, evaluated exactly in FP64; ``tcec_cgemm_3m`` the same with
+  Gauss's three real products (a variant beyond the paper).
 * ``statevector`` / ``circuit_tn`` / ``amplitude``: the state-vector method and
   the tensor-network representation of a circuit (Section 2.2), the amplitude
   <x|U|0> of Eq. prob_dist (Section 5.3), with slicing (Section 5.3).
@@ -89,6 +90,8 @@ def _L():
         lib.oracle_tcec_sgemm.argtypes = [I, I, I, I, I, I64, I64, I64, D, P, I64, P, I64, D, P,
                                           I64, P]
         lib.oracle_exp_stats_real.argtypes = [I64, I64, P, I64, P, P]
+        lib.oracle_tcec_cgemm_3m.argtypes = [I, I, I, I, I, I64, I64, I64, P, P, I64, P, I64, P,
+                                             P, I64, P]
         lib.oracle_f32_to_f16.argtypes = [ctypes.c_float]
         lib.oracle_f32_to_f16.restype = ctypes.c_uint16
         lib.oracle_f16_to_f32.argtypes = [ctypes.c_uint16]
@@ -235,6 +238,30 @@ def tcec_sgemm(kind: int, sA: int, sB: int, opA: int, opB: int, m: int, n: int, 
                                 _ptr(B), ldb, float(beta), cp, ldc, _ptr(out))
     if rc != 0:
         raise MemoryError("oracle_tcec_sgemm failed")
+    return out
+
+
+def tcec_cgemm_3m(kind: int, sA: int, sB: int, opA: int, opB: int, m: int, n: int, k: int,
+                  alpha, A, B, beta=0.0, C=None) -> np.ndarray:
+    """Exact (FP64) value of Gauss's three-product form of the emulated
+    complex product: T1 = Ar Br, T2 = Ai Bi, T3 = (Ar + Ai)(Br + Bi), each an
+    Eq. 1 compensated product (operand sums in binary32, scaled by one binade
+    less for FP16), Re = T1 - T2, Im = T3 - T1 - T2.  A variant beyond the
+    paper.  kind: 0 FP16, 1 TF32, 2 BF16."""
+    A, lda = _mat_view(A)
+    B, ldb = _mat_view(B)
+    al = np.array([complex(alpha).real, complex(alpha).imag], dtype=np.float64)
+    be = np.array([complex(beta).real, complex(beta).imag], dtype=np.float64)
+    if C is not None:
+        C, ldc = _mat_view(C)
+        cp = _ptr(C)
+    else:
+        ldc, cp = 1, None
+    out = np.zeros((m, n), dtype=np.complex128, order="F")
+    rc = _L().oracle_tcec_cgemm_3m(kind, sA, sB, opA, opB, m, n, k, _ptr(al), _ptr(A), lda,
+                                   _ptr(B), ldb, _ptr(be), cp, ldc, _ptr(out))
+    if rc != 0:
+        raise MemoryError("oracle_tcec_cgemm_3m failed")
     return out
 
 

@@ -363,6 +363,83 @@ int oracle_tcec_cgemm(int kind, int sA, int sB, int opA, int opB, int64_t m, int
     return 0;
 }
 
+/*
+ * Gauss's three-product form of the emulated complex product (a variant
+ * beyond the paper): with ar, ai the parts of op(A) and br, bi those of
+ * op(B) (conjugation applied),
+ *   T1 = ar br,  T2 = ai bi,  T3 = (ar + ai)(br + bi),
+ *   Re = T1 - T2,  Im = T3 - T1 - T2,
+ * where each real product is Eq. 1's compensated product in exact
+ * arithmetic, the operand sums are binary32 additions, and for the FP16 kind
+ * (kind 0) the sums are scaled by 2^(sA - 1), 2^(sB - 1) instead of 2^sA,
+ * 2^sB.  Then alpha P + beta C_in.  Output as oracle_cgemm_naive.
+ */
+int oracle_tcec_cgemm_3m(int kind, int sA, int sB, int opA, int opB, int64_t m, int64_t n,
+                         int64_t k, const double *alpha, const float *A, int64_t lda,
+                         const float *B, int64_t ldb, const double *beta, const float *C_in,
+                         int64_t ldc_in, double *C_out) {
+    size_t na = (size_t)m * (size_t)k, nb = (size_t)k * (size_t)n;
+    size_t ta = 3 * (na ? na : 1), tb = 3 * (nb ? nb : 1);
+    float *a = (float *)malloc(sizeof(float) * ta), *b = (float *)malloc(sizeof(float) * tb);
+    float *ah = (float *)malloc(sizeof(float) * ta), *al = (float *)malloc(sizeof(float) * ta);
+    float *bh = (float *)malloc(sizeof(float) * tb), *bl = (float *)malloc(sizeof(float) * tb);
+    if (!a || !b || !ah || !al || !bh || !bl) {
+        free(a); free(b); free(ah); free(al); free(bh); free(bl);
+        return -1;
+    }
+    /* part p of op(A) at a + p na, index (i + l m); likewise for op(B), (l + j k) */
+    for (int64_t l = 0; l < k; ++l)
+        for (int64_t i = 0; i < m; ++i) {
+            cd v = op_elem(A, opA, i, l, lda);
+            float re = (float)v.re, im = (float)v.im;
+            a[i + l * m] = re;
+            a[na + i + l * m] = im;
+            a[2 * na + i + l * m] = re + im;
+        }
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t l = 0; l < k; ++l) {
+            cd v = op_elem(B, opB, l, j, ldb);
+            float re = (float)v.re, im = (float)v.im;
+            b[l + j * k] = re;
+            b[nb + l + j * k] = im;
+            b[2 * nb + l + j * k] = re + im;
+        }
+    const int s3A = (kind == 0) ? sA - 1 : sA, s3B = (kind == 0) ? sB - 1 : sB;
+    oracle_split(kind, sA, 2 * (int64_t)na, a, ah, al);
+    oracle_split(kind, s3A, (int64_t)na, a + 2 * na, ah + 2 * na, al + 2 * na);
+    oracle_split(kind, sB, 2 * (int64_t)nb, b, bh, bl);
+    oracle_split(kind, s3B, (int64_t)nb, b + 2 * nb, bh + 2 * nb, bl + 2 * nb);
+    const double corr = ldexp(1.0, -11);
+    const double un12 = ldexp(1.0, -(sA + sB)), un3 = ldexp(1.0, -(s3A + s3B));
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i) {
+            double T[3];
+            for (int p = 0; p < 3; ++p) {
+                double p0 = 0, p1 = 0;
+                for (int64_t l = 0; l < k; ++l) {
+                    size_t ia = p * na + (size_t)(i + l * m), ib = p * nb + (size_t)(l + j * k);
+                    p0 += (double)ah[ia] * (double)bh[ib];
+                    p1 += (double)al[ia] * (double)bh[ib] + (double)ah[ia] * (double)bl[ib];
+                }
+                T[p] = (p0 + corr * p1) * (p == 2 ? un3 : un12);
+            }
+            double sr = T[0] - T[1];
+            double si = T[2] - T[0] - T[1];
+            double cr = alpha[0] * sr - alpha[1] * si;
+            double ci = alpha[0] * si + alpha[1] * sr;
+            if (C_in && (beta[0] != 0.0 || beta[1] != 0.0)) {
+                double xr = (double)C_in[2 * (i + j * ldc_in)];
+                double xi = (double)C_in[2 * (i + j * ldc_in) + 1];
+                cr += beta[0] * xr - beta[1] * xi;
+                ci += beta[0] * xi + beta[1] * xr;
+            }
+            C_out[2 * (i + j * m)] = cr;
+            C_out[2 * (i + j * m) + 1] = ci;
+        }
+    free(a); free(b); free(ah); free(al); free(bh); free(bl);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------
  * Real matrices (the SGEMM that Section 2.1 emulates).  Column-major
  * binary32 with a leading dimension; op 0 = N, 1 or 2 = T.  Results are

@@ -330,6 +330,39 @@ def test_tcec_model_scaled_recovers_tiny_inputs():
     assert err_scaled < 1e-6 and err_plain > 0.5
 
 
+def test_tcec_3m_model_exact_on_small_integers_and_ops():
+    # integer parts and their sums are exact in every kind (also halved, for
+    # FP16's one binade less of scaling): the three-product form then gives
+    # the exact product, whatever the op -- a wrong sign or part fails here
+    g = np.random.default_rng(12)
+    A = np.asfortranarray((g.integers(-8, 9, (7, 5)) + 1j * g.integers(-8, 9, (7, 5))).astype(np.complex64))
+    B = np.asfortranarray((g.integers(-8, 9, (6, 7)) + 1j * g.integers(-8, 9, (6, 7))).astype(np.complex64))
+    for opA, opB, ra, rb in ((OP_T, OP_C, A.T, B.conj().T), (OP_C, OP_T, A.conj().T, B.T)):
+        ref = ra.astype(np.complex128) @ rb.astype(np.complex128)
+        for kind in (0, 1, 2):
+            got = oracle.tcec_cgemm_3m(kind, 0, 0, opA, opB, 5, 6, 7, 1, A, B)
+            assert np.array_equal(got, ref), (kind, opA)
+        assert np.array_equal(oracle.tcec_cgemm_3m(0, 3, -2, opA, opB, 5, 6, 7, 1, A, B), ref)
+    # alpha and beta as in the four-product model
+    C = np.asfortranarray((g.integers(-4, 5, (5, 6)) + 1j * g.integers(-4, 5, (5, 6))).astype(np.complex64))
+    ref = (0.5 - 1j) * (A.T.astype(np.complex128) @ B.conj().T.astype(np.complex128)) + 2j * C
+    got = oracle.tcec_cgemm_3m(1, 0, 0, OP_T, OP_C, 5, 6, 7, 0.5 - 1j, A, B, 2j, C)
+    assert np.array_equal(got, ref)
+
+
+def test_tcec_3m_model_accuracy_uniform_inputs():
+    # the three-product form stays at FP32 level on U(-1,1) parts, close to
+    # the four-product model's error
+    m, n, k = 24, 20, 64
+    A = qi.uniform_operand(m, k, 1)
+    B = qi.uniform_operand(k, n, 2)
+    exact = oracle.cgemm(OP_N, OP_N, m, n, k, 1, A, B)
+    for kind in (0, 1):
+        e3 = oracle.rel_fro_error(oracle.tcec_cgemm_3m(kind, 0, 0, OP_N, OP_N, m, n, k, 1, A, B), exact)
+        e4 = oracle.rel_fro_error(oracle.tcec_cgemm(kind, 0, 0, OP_N, OP_N, m, n, k, 1, A, B), exact)
+        assert 1e-9 < e3 < 1e-6 and e3 < 4 * e4, (kind, e3, e4)
+
+
 # ---------------------------------------------------------------------------
 # Real matrices: the SGEMM of Section 2.1
 # ---------------------------------------------------------------------------
