@@ -513,6 +513,25 @@ def main():
                 entry["rel_fro_vs_fp64"] = oracle.rel_fro_error(
                     C2[:args.sample_rows].cpu().numpy().astype(np.complex128), ref)
             out["candidates"][mode] = entry
+        # Gauss's three-product form (a variant beyond the paper): AUTO-t and
+        # forced FP16X on the same inputs, nominal 8 m n k flops
+        h3 = q.Handle(tol=args.tol, size_rule=True)
+        h3.set_complex_products(3)
+        for mode in ("auto", "fp16x"):
+            q.cgemm(h3, A, B, C2, mode=mode)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                q.cgemm(h3, A, B, C2, mode=mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            entry = {"tflops": flops / (e0.elapsed_time(e1) / reps * 1e-3) / 1e12,
+                     "complex_products": 3}
+            if rank == 0:
+                entry["rel_fro_vs_fp64"] = oracle.rel_fro_error(
+                    C2[:args.sample_rows].cpu().numpy().astype(np.complex128), ref)
+            out["candidates"][mode + "_3m"] = entry
+        h3.close()
         del C2
 
     # ---- end to end through the public API, host buffers ----

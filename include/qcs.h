@@ -152,6 +152,22 @@ int qcs_set_tc_schedule(qcs_handle_t h, int group_m, int l2_promotion);
  * Returns QCS_ERR_INVALID_ARG for other values. */
 int qcs_set_tc_splits(qcs_handle_t h, int splits);
 
+/* Real products per emulated complex product of qcs_cgemm: 4 (default; the
+ * complex expansion of Section 3, Re = ArBr - AiBi, Im = ArBi + AiBr) or 3
+ * (Gauss's form, a variant beyond the paper: T1 = Ar Br, T2 = Ai Bi,
+ * T3 = (Ar + Ai)(Br + Bi) as three emulated real GEMMs, Re = T1 - T2,
+ * Im = T3 - T1 - T2; 9 tensor-core products instead of 12).  With 3 the
+ * statistics and selection are still those of A and B; the operand sums of
+ * T3 are formed in binary32 and, for the FP16 kind, split with one binade
+ * less of scaling (2^(s-1)) so that they cannot overflow.  Applies to
+ * qcs_cgemm calls whose mode (after the size rule) is emulated and k > 0;
+ * the FP32 mode, the contraction tree and qcs_cgemm_noalloc keep 4.  The
+ * error differs from the four-product form (the imaginary part is a
+ * difference of products); the parity tests bound it against the exact
+ * three-product model and FP64.  Environment override QCS_COMPLEX_PRODUCTS.
+ * Returns QCS_ERR_INVALID_ARG for other values. */
+int qcs_set_complex_products(qcs_handle_t h, int products);
+
 /* Exponent statistics (Section 4.1, Stage 1 and Stage 2 in one pass) of the
  * rows x cols complex matrix X (device, leading dim ldx >= rows), written
  * to d_stats (device, caller-owned).  rows or cols may be 0. */

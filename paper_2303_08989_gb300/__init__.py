@@ -167,6 +167,12 @@ class Handle:
         shape, 1..16 forces the count."""
         _lib.check(self.lib.qcs_set_tc_splits(self._h, int(splits)), "qcs_set_tc_splits")
 
+    def set_complex_products(self, products: int = 4):
+        """Real products per emulated complex product of cgemm
+        (qcs_set_complex_products): 4, the paper's expansion, or 3, Gauss's."""
+        _lib.check(self.lib.qcs_set_complex_products(self._h, int(products)),
+                   "qcs_set_complex_products")
+
     def set_drain_stages(self, stages: int):
         _lib.check(self.lib.qcs_set_drain_stages(self._h, int(stages)), "qcs_set_drain_stages")
         self.drain_stages = int(stages)

@@ -563,6 +563,134 @@ int run_sgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
     return QCS_SUCCESS;
 }
 
+// ---- Gauss's three-product CGEMM --------------------------------------------
+
+namespace {
+
+// The three real operands of each side (Ar, Ai, Ar + Ai) as instances 0, 1,
+// 2 of a group: two planes each, instance g's rows after those of g - 1;
+// then the three real products T (m x n floats each) and the partials.
+struct Gauss3Layout {
+    int64_t kp = 0, mp = 0, np = 0;
+    size_t a = 0, b = 0, t = 0, partials = 0, total = 0;
+};
+
+Gauss3Layout gauss3_layout(int eff, int64_t m, int64_t n, int64_t k, int S) {
+    Gauss3Layout L;
+    L.kp = round_up(k, 32);
+    L.mp = round_up(m, kBM);
+    L.np = round_up(n, 2 * kBN);
+    const int esz = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X) ? 4 : 2;
+    L.a = 0;
+    L.b = align256(size_t(2) * 3 * L.mp * L.kp * esz);
+    L.t = L.b + align256(size_t(2) * 3 * L.np * L.kp * esz);
+    L.partials = L.t + align256(sizeof(float) * 3 * m * n);
+    L.total = L.partials + (S > 1 ? align256(sizeof(float) * S * 3 * m * n) : 0);
+    return L;
+}
+
+}  // namespace
+
+size_t cgemm3m_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits) {
+    size_t bytes = align256(3 * sizeof(qcs_gemm_desc_t));
+    bytes += align256(size_t(2) * num_sms * kPartialStride * sizeof(int64_t));
+    bytes += align256(kSplitKBytes);
+    bytes += gauss3_layout(eff, m, n, k, tc_split_count(m, n, k, 1, num_sms, splits, true)).total;
+    return bytes;
+}
+
+// C = alpha op(A) op(B) + beta C with T1 = Ar Br, T2 = Ai Bi,
+// T3 = (Ar + Ai)(Br + Bi) as three emulated real GEMMs in one grouped
+// tensor-core launch (Ar, Ai: the parts of op(A), conjugation applied), then
+// Re = T1 - T2, Im = T3 - T1 - T2.  Statistics and selection are those of A
+// and B (Section 4.1); T3 runs with desc[2] (launch_derive_3m_desc).  Only
+// emulated modes (eff != FP32, k > 0); AUTO's FP32 candidate is the complex
+// SIMT kernel, gated as in run_cgemm.
+int run_cgemm_3m(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n,
+                 int64_t k, float2 alpha, const float2 *A, int64_t lda, const float2 *B,
+                 int64_t ldb, float2 beta, float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out) {
+    if (eff == QCS_MODE_FP32 || k == 0) return QCS_ERR_UNSUPPORTED;
+    cudaStream_t s = h->stream;
+    uint8_t *p = static_cast<uint8_t *>(ws);
+    qcs_gemm_desc_t *desc = reinterpret_cast<qcs_gemm_desc_t *>(p);
+    p += align256(3 * sizeof(qcs_gemm_desc_t));
+    int64_t *partials = reinterpret_cast<int64_t *>(p);
+    p += align256(size_t(2) * h->num_sms * kPartialStride * sizeof(int64_t));
+    float2 *splitk = reinterpret_cast<float2 *>(p);
+    p += align256(kSplitKBytes);
+    cudaError_t e = cudaSuccess;
+    if (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X_SCALED) {
+        const int64_t ra = (opA == QCS_OP_N) ? m : k, ca = (opA == QCS_OP_N) ? k : m;
+        const int64_t rb = (opB == QCS_OP_N) ? k : n, cb = (opB == QCS_OP_N) ? n : k;
+        const int gA = stats2_blocks(ra * ca, h->num_sms), gB = stats2_blocks(rb * cb, h->num_sms);
+        ProfScope ps(h, kProfStats);
+        e = launch_stats_select_2stage(A, ra, ca, lda, gA, B, rb, cb, ldb, gB, h->tol, eff,
+                                       partials, partials + 5 * (gA + gB), desc, h->d_counts,
+                                       8.0 * (double)m * (double)n * (double)k, s);
+    } else {
+        e = launch_set_desc(desc, eff, s);
+    }
+    if (e == cudaSuccess) e = launch_derive_3m_desc(desc, s);
+    if (e != cudaSuccess) return QCS_ERR_CUDA;
+
+    TcWork w;
+    w.G = 3;
+    w.S = tc_split_count(m, n, k, 1, h->num_sms, h->tc_splits, true);
+    const Gauss3Layout L = gauss3_layout(eff, m, n, k, w.S);
+    uint8_t *planesA = p + L.a, *planesB = p + L.b;
+    float *T = reinterpret_cast<float *>(p + L.t);
+    if (w.S > 1) w.P = reinterpret_cast<float2 *>(p + L.partials);
+    w.a_rows = L.mp;
+    w.b_rows = L.np;
+    w.c_stride = m * n;
+    {
+        ProfScope ps(h, kProfSplit);
+        for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+            const int op = which == 0 ? opA : opB;
+            int64_t sr, sc;
+            plane_strides(which, op, which == 0 ? lda : ldb, sr, sc);
+            const float *X = reinterpret_cast<const float *>(which == 0 ? A : B);
+            const int64_t R = which == 0 ? m : n, Rp = which == 0 ? L.mp : L.np;
+            void *planes = which == 0 ? planesA : planesB;
+            const float isign = (op == QCS_OP_C) ? -1.0f : 1.0f;
+            for (int part = 0; part < 3 && e == cudaSuccess; ++part)
+                e = launch_split_real(desc + part, which, X, 2 * sr, 2 * sc, R, k, Rp, L.kp, planes,
+                                      L.kp, 3 * Rp * L.kp, s, part, isign, part * Rp * L.kp);
+        }
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    }
+    const bool need16 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X ||
+                         eff == QCS_MODE_FP16X_SCALED || eff == QCS_MODE_BF16X3);
+    const bool need32 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X);
+    {
+        ProfScope ps_tc(h, kProfGemmTc);
+        for (int esz = 2; esz <= 4; esz += 2) {
+            if ((esz == 2 && !need16) || (esz == 4 && !need32)) continue;
+            CUtensorMap ma, mb;
+            if (encode_planes(h, &ma, planesA, 3 * L.mp, L.kp, esz, 2, kBM) ||
+                encode_planes(h, &mb, planesB, 3 * L.np, L.kp, esz, 2, 2 * kBN))
+                return QCS_ERR_CUDA;
+            const int kind = (esz == 4) ? 1 : (eff == QCS_MODE_BF16X3 ? 2 : 0);
+            e = launch_sgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, L.kp, 1.0f, 0.0f, T, m,
+                                h->d_err, h->num_sms, h->tc_group_m, s, w);
+            if (e != cudaSuccess) return QCS_ERR_CUDA;
+        }
+        e = launch_tc_reduce_real(desc, m, n, 1.0f, 0.0f, T, m, h->num_sms, w, s);
+        if (e == cudaSuccess) e = launch_combine_3m(desc, m, n, T, alpha, beta, C, ldc, h->num_sms, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    }
+    if (eff == QCS_MODE_AUTO) {
+        ProfScope ps(h, kProfGemmSimt);
+        e = launch_cgemm_simt(desc, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, splitk, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    }
+    if (d_desc_out) {
+        e = cudaMemcpyAsync(d_desc_out, desc, sizeof(qcs_gemm_desc_t), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    }
+    return QCS_SUCCESS;
+}
+
 int validate_cgemm(int mode, int opA, int opB, int64_t m, int64_t n, int64_t k, const void *alpha,
                    const void *A, int64_t lda, const void *B, int64_t ldb, const void *beta,
                    const void *C, int64_t ldc) {
@@ -625,6 +753,8 @@ int qcs_create(qcs_handle_t *out, void *cuda_stream) {
     }
     if (const char *g = std::getenv("QCS_TC_GROUP_M")) h->tc_group_m = std::max(1, std::atoi(g));
     if (const char *p = std::getenv("QCS_TC_L2_PROMOTION")) h->tc_l2_promotion = std::atoi(p);
+    if (const char *c = std::getenv("QCS_COMPLEX_PRODUCTS"))
+        h->complex_products = (std::atoi(c) == 3) ? 3 : 4;
     if (const char *k = std::getenv("QCS_TC_SPLITS"))
         h->tc_splits = std::min(kMaxSplits, std::max(0, std::atoi(k)));
     if (const char *d = std::getenv("QCS_DRAIN_STAGES")) {
@@ -683,6 +813,12 @@ int qcs_set_tc_splits(qcs_handle_t h, int splits) {
     return QCS_SUCCESS;
 }
 
+int qcs_set_complex_products(qcs_handle_t h, int products) {
+    if (!h || (products != 3 && products != 4)) return QCS_ERR_INVALID_ARG;
+    h->complex_products = products;
+    return QCS_SUCCESS;
+}
+
 int qcs_set_instance_batch(qcs_handle_t h, int instances) {
     if (!h || instances < 1 || instances > 65535) return QCS_ERR_INVALID_ARG;
     h->instance_batch = instances;
@@ -728,10 +864,19 @@ int qcs_cgemm(qcs_handle_t h, qcs_mode_t mode, qcs_op_t transA, qcs_op_t transB,
     if (m == 0 || n == 0) return QCS_SUCCESS;
     if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX) return QCS_ERR_UNSUPPORTED;
     const int eff = effective_mode(h, mode, transA, transB, m, n, k);
+    const float2 al = make_float2(alpha->x, alpha->y), be = make_float2(beta->x, beta->y);
+    if (h->complex_products == 3 && eff != QCS_MODE_FP32 && k > 0) {
+        if (int r = ensure_workspace(h->ws, cgemm3m_workspace_bytes(eff, m, n, k, h->num_sms,
+                                                                   h->tc_splits)))
+            return r;
+        return run_cgemm_3m(h, h->ws.ptr, eff, transA, transB, m, n, k, al,
+                            reinterpret_cast<const float2 *>(A), lda,
+                            reinterpret_cast<const float2 *>(B), ldb, be,
+                            reinterpret_cast<float2 *>(C), ldc, d_desc_out);
+    }
     if (int r = ensure_workspace(h->ws, gemm_workspace_bytes(eff, m, n, k, h->num_sms,
                                                             gemm_splits(h, transA, transB, m, n, k), 1)))
         return r;
-    const float2 al = make_float2(alpha->x, alpha->y), be = make_float2(beta->x, beta->y);
     return run_cgemm(h, h->ws.ptr, eff, transA, transB, m, n, k, al,
                      reinterpret_cast<const float2 *>(A), lda, reinterpret_cast<const float2 *>(B),
                      ldb, be, reinterpret_cast<float2 *>(C), ldc, d_desc_out, nullptr);

@@ -94,6 +94,7 @@ struct qcs_handle_s {
     int tc_group_m = 8;              // tensor-core raster: tile rows per group
     int tc_l2_promotion = 256;       // L2 promotion of the plane loads (bytes; 0 = none)
     int tc_splits = 0;               // K ranges per tensor-core GEMM (0 = chosen per shape)
+    int complex_products = 4;        // real products per emulated complex product (4, or 3: Gauss)
     int *d_err = nullptr;            // device error word (start of a 64-byte block)
     unsigned long long *d_counts = nullptr;  // in that block: AUTO selections per mode, flops
     qcs::Workspace ws;               // GEMM workspace (planes, partials, descriptor)
@@ -322,9 +323,20 @@ cudaError_t launch_stats_select_2stage_real(const float *X0, int64_t rows0, int6
 // Split a real op(X) (element (r, c) at X[r sr + c sc]) into the planes hi
 // and lo (R_pad x K_pad, pitch elements per row, plane_stride apart), zero
 // beyond R x K; elements of the kind the descriptor selected.
+// ``part`` (a complex source, sr and sc in floats): 0 the real part, 1
+// isign x the imaginary part, 2 their binary32 sum; ``plane_off``: element
+// offset of row 0 in both planes.
 cudaError_t launch_split_real(const qcs_gemm_desc_t *desc, int which, const float *X, int64_t sr,
                               int64_t sc, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
-                              void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s);
+                              void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
+                              int part = 0, float isign = 1.0f, int64_t plane_off = 0);
+// Gauss's three-product CGEMM: desc[1], desc[2] from the selected desc[0]
+// (the T3 operand sums lose one binade of FP16 scaling), and the final
+// combination C = alpha (T1 - T2 + i (T3 - T1 - T2)) + beta C.
+cudaError_t launch_derive_3m_desc(qcs_gemm_desc_t *desc, cudaStream_t s);
+cudaError_t launch_combine_3m(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, const float *T,
+                              float2 alpha, float2 beta, float2 *C, int64_t ldc, int num_sms,
+                              cudaStream_t s);
 // Plain FP32 real GEMM (runs only when desc->mode == FP32, or always when
 // desc is NULL).
 cudaError_t launch_sgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int64_t m,
@@ -342,6 +354,11 @@ cudaError_t launch_sgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
 cudaError_t launch_tc_reduce_real(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, float alpha,
                                   float beta, float *C, int64_t ldc, int num_sms, const TcWork &w,
                                   cudaStream_t s);
+// Gauss's three-product form of one emulated CGEMM (qcs_set_complex_products 3).
+size_t cgemm3m_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits);
+int run_cgemm_3m(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n,
+                 int64_t k, float2 alpha, const float2 *A, int64_t lda, const float2 *B,
+                 int64_t ldb, float2 beta, float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out);
 // Workspace of one real GEMM and its launch sequence (as run_cgemm, G = 1).
 size_t sgemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits);
 int run_sgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n, int64_t k,

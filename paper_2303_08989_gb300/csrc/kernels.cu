@@ -779,14 +779,18 @@ cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X
 
 namespace {
 
-// Eq. 1 for a real operand: op(X) (R x K, element (r, c) at X[r sr + c sc])
-// into two planes, hi and lo, of R_pad x K_pad (row pitch ``pitch``, planes
-// ``plane_stride`` elements apart), zero beyond R x K.  Elements are FP16,
-// BF16 (2 bytes) or TF32 (4 bytes), the kind the descriptor selected.
+// Eq. 1 for a real operand: op(X) (R x K, element (r, c) read at
+// X[r sr + c sc]) into two planes, hi and lo, of R_pad x K_pad (row pitch
+// ``pitch``, planes ``plane_stride`` elements apart, row 0 at element
+// ``plane_off``), zero beyond R x K.  ``part`` picks the value from a
+// complex source (sr, sc in floats): 0 the float itself (the real part),
+// 1 isign x the next float (the imaginary part), 2 their binary32 sum (the
+// real part plus isign x the imaginary part: Gauss's operand sums).  Elements
+// are FP16, BF16 (2 bytes) or TF32 (4 bytes), the kind the descriptor selected.
 __global__ void __launch_bounds__(256) split_real_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int which, const float *__restrict__ X, int64_t sr,
     int64_t sc, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad, void *planes, int64_t pitch,
-    int64_t plane_stride) {
+    int64_t plane_stride, int part, float isign, int64_t plane_off) {
     const int mode = desc->mode;
     if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
     const int s = (mode == QCS_MODE_FP16X_SCALED) ? (which == 0 ? desc->sA : desc->sB) : 0;
@@ -796,7 +800,12 @@ __global__ void __launch_bounds__(256) split_real_kernel(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t r0 = static_cast<int64_t>(blockIdx.y) * kSplitR;
     const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kSplitC;
-    if (sc == 1) {
+    auto value = [&](int64_t i) -> float {
+        if (part == 0) return X[i];
+        if (part == 1) return isign * X[i + 1];
+        return X[i] + isign * X[i + 1];
+    };
+    if (sc <= 2) {  // lanes along c: the source is (nearly) contiguous there
 #pragma unroll
         for (int i = 0; i < kSplitR / 8; ++i) {
             const int rr = warp + 8 * i;
@@ -804,7 +813,7 @@ __global__ void __launch_bounds__(256) split_real_kernel(
             for (int h = 0; h < 2; ++h) {
                 const int cc = lane + 32 * h;
                 float v = 0.f;
-                if (r0 + rr < R && c0 + cc < K) v = X[(r0 + rr) * sr + (c0 + cc)];
+                if (r0 + rr < R && c0 + cc < K) v = value((r0 + rr) * sr + (c0 + cc) * sc);
                 tile[rr][cc] = v;
             }
         }
@@ -814,7 +823,7 @@ __global__ void __launch_bounds__(256) split_real_kernel(
             const int cc = warp + 8 * i;
             const int rr = lane;
             float v = 0.f;
-            if (r0 + rr < R && c0 + cc < K) v = X[(r0 + rr) * sr + (c0 + cc) * sc];
+            if (r0 + rr < R && c0 + cc < K) v = value((r0 + rr) * sr + (c0 + cc) * sc);
             tile[rr][cc] = v;
         }
     }
@@ -834,7 +843,7 @@ __global__ void __launch_bounds__(256) split_real_kernel(
         }
         const bool two = (c + 1 < K_pad);
         if (mode == QCS_MODE_TF32X) {
-            uint32_t *p = static_cast<uint32_t *>(planes) + r * pitch + c;
+            uint32_t *p = static_cast<uint32_t *>(planes) + plane_off + r * pitch + c;
             const bool vec = two && ((reinterpret_cast<uintptr_t>(p) & 7u) == 0);
             if (vec) {
                 *reinterpret_cast<uint2 *>(p) = make_uint2(hib[0], hib[1]);
@@ -848,7 +857,7 @@ __global__ void __launch_bounds__(256) split_real_kernel(
                 }
             }
         } else {
-            uint16_t *p = static_cast<uint16_t *>(planes) + r * pitch + c;
+            uint16_t *p = static_cast<uint16_t *>(planes) + plane_off + r * pitch + c;
             const bool vec = two && ((reinterpret_cast<uintptr_t>(p) & 3u) == 0);
             if (vec) {
                 *reinterpret_cast<uint32_t *>(p) = hib[0] | (hib[1] << 16);
@@ -869,12 +878,78 @@ __global__ void __launch_bounds__(256) split_real_kernel(
 
 cudaError_t launch_split_real(const qcs_gemm_desc_t *desc, int which, const float *X, int64_t sr,
                               int64_t sc, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
-                              void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s) {
+                              void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
+                              int part, float isign, int64_t plane_off) {
     if (R_pad <= 0 || K_pad <= 0) return cudaSuccess;
     dim3 grid((unsigned)((K_pad + kSplitC - 1) / kSplitC), (unsigned)((R_pad + kSplitR - 1) / kSplitR));
     if (grid.y > 65535u) return cudaErrorInvalidValue;
     split_real_kernel<<<grid, 256, 0, s>>>(desc, which, X, sr, sc, R, K, R_pad, K_pad, planes,
-                                           pitch, plane_stride);
+                                           pitch, plane_stride, part, isign, plane_off);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// Descriptors of the three real GEMMs of a Gauss product from the selected
+// one (desc[0]): T1 = Ar Br and T2 = Ai Bi keep it; T3 = (Ar + Ai)(Br + Bi)
+// takes one binade less of scaling for the FP16 kind, whose operand sums can
+// reach twice the largest part (FP16X becomes FP16X_SCALED by 2^-1).
+__global__ void derive_3m_desc_kernel(qcs_gemm_desc_t *desc) {
+    qcs_gemm_desc_t d = desc[0];
+    desc[1] = d;
+    if (d.mode == QCS_MODE_FP16X || d.mode == QCS_MODE_FP16X_SCALED) {
+        if (d.mode == QCS_MODE_FP16X) d.sA = d.sB = 0;
+        d.mode = QCS_MODE_FP16X_SCALED;
+        d.sA -= 1;
+        d.sB -= 1;
+    }
+    desc[2] = d;
+}
+
+// C = alpha (T1 - T2 + i (T3 - T1 - T2)) + beta C from the three real
+// products (consecutive m x n blocks of T, ld m); runs unless FP32 was
+// selected.
+__global__ void __launch_bounds__(256) combine_3m_kernel(const qcs_gemm_desc_t *__restrict__ desc,
+                                                         int64_t m, int64_t n,
+                                                         const float *__restrict__ T, float2 alpha,
+                                                         float2 beta, float2 *__restrict__ C,
+                                                         int64_t ldc) {
+    if (desc->mode == QCS_MODE_FP32) return;
+    const int64_t mn = m * n;
+    const bool use_beta = (beta.x != 0.0f) || (beta.y != 0.0f);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mn;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float t1 = __ldcs(T + i), t2 = __ldcs(T + mn + i), t3 = __ldcs(T + 2 * mn + i);
+        const float pr = t1 - t2;
+        const float pi = (t3 - t1) - t2;
+        const int64_t col = i / m;
+        float2 *dst = C + col * ldc + (i - col * m);
+        float2 o;
+        o.x = alpha.x * pr - alpha.y * pi;
+        o.y = alpha.x * pi + alpha.y * pr;
+        if (use_beta) {
+            const float2 c = *dst;
+            o.x += beta.x * c.x - beta.y * c.y;
+            o.y += beta.x * c.y + beta.y * c.x;
+        }
+        *dst = o;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_derive_3m_desc(qcs_gemm_desc_t *desc, cudaStream_t s) {
+    derive_3m_desc_kernel<<<1, 1, 0, s>>>(desc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine_3m(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, const float *T,
+                              float2 alpha, float2 beta, float2 *C, int64_t ldc, int num_sms,
+                              cudaStream_t s) {
+    if (m == 0 || n == 0) return cudaSuccess;
+    const int64_t need = (m * n + 255) / 256, cap = (int64_t)num_sms * 8;
+    combine_3m_kernel<<<(unsigned)(need < cap ? need : cap), 256, 0, s>>>(desc, m, n, T, alpha, beta,
+                                                                         C, ldc);
     return cudaGetLastError();
 }
 
