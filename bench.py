@@ -71,6 +71,8 @@ def parse():
                         "order of seed 2, 'gather' a random permutation of 2^26 elements, 'gemm' "
                         "ten qcs_cgemm calls of --gemm-shape in --mode, 'sgemm' ten qcs_sgemm "
                         "calls of --gemm-shape in --mode")
+    p.add_argument("--complex-products", type=int, choices=[3, 4], default=4,
+                   help="with --profile gemm: real products per complex product (3: Gauss)")
     p.add_argument("--gemm-shape", type=int, nargs=3, default=[2048, 8192, 32],
                    metavar=("M", "N", "K"), help="the GEMM of --profile gemm")
     p.add_argument("--tuning-file", default=None,
@@ -308,11 +310,13 @@ def profile_run(args):
         B = torch.randn((n, k), dtype=torch.complex64, device=dev, generator=g).t()
         C = q.fortran_empty(m, n, device=dev)
         h = q.Handle(tol=args.tol, size_rule=False)
+        h.set_complex_products(args.complex_products)
 
         def run():
             for _ in range(10):
                 q.cgemm(h, A, B, C, mode=args.mode)
-        what = "10 x qcs_cgemm (%d, %d, %d), mode %s, parts N(0,1)" % (m, n, k, args.mode)
+        what = "10 x qcs_cgemm (%d, %d, %d), mode %s, parts N(0,1), %d real products" % (
+            m, n, k, args.mode, args.complex_products)
     elif args.profile == "sgemm":
         m, n, k = args.gemm_shape
         g = torch.Generator(device=dev).manual_seed(9)
