@@ -3,7 +3,8 @@
 Python face of libqcs (include/qcs.h).  Every numerical step runs in the CUDA
 library; this module only passes device pointers, sizes and the current torch
 stream.  Matrices are column-major: a torch tensor ``X`` of shape (rows, cols)
-with ``X.stride() == (1, ld)`` (``ld >= rows``), complex64, on the GPU.
+with ``X.stride() == (1, ld)`` (``ld >= rows``), complex64 (float32 for
+``sgemm``), on the GPU.
 """
 from __future__ import annotations
 
