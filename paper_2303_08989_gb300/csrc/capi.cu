@@ -645,17 +645,16 @@ int run_cgemm_3m(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m,
     w.c_stride = m * n;
     {
         ProfScope ps(h, kProfSplit);
+        // one pass over each complex operand writes the planes of its three
+        // real operands (parts 0, 1, 2 = instances 0, 1, 2)
         for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
             const int op = which == 0 ? opA : opB;
             int64_t sr, sc;
             plane_strides(which, op, which == 0 ? lda : ldb, sr, sc);
-            const float *X = reinterpret_cast<const float *>(which == 0 ? A : B);
             const int64_t R = which == 0 ? m : n, Rp = which == 0 ? L.mp : L.np;
-            void *planes = which == 0 ? planesA : planesB;
-            const float isign = (op == QCS_OP_C) ? -1.0f : 1.0f;
-            for (int part = 0; part < 3 && e == cudaSuccess; ++part)
-                e = launch_split_real(desc + part, which, X, 2 * sr, 2 * sc, R, k, Rp, L.kp, planes,
-                                      L.kp, 3 * Rp * L.kp, s, part, isign, part * Rp * L.kp);
+            e = launch_split_gauss(desc, which, which == 0 ? A : B, sr, sc, op == QCS_OP_C, R, k, Rp,
+                                   L.kp, which == 0 ? planesA : planesB, L.kp, 3 * Rp * L.kp,
+                                   Rp * L.kp, s);
         }
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     }

@@ -323,17 +323,21 @@ cudaError_t launch_stats_select_2stage_real(const float *X0, int64_t rows0, int6
 // Split a real op(X) (element (r, c) at X[r sr + c sc]) into the planes hi
 // and lo (R_pad x K_pad, pitch elements per row, plane_stride apart), zero
 // beyond R x K; elements of the kind the descriptor selected.
-// ``part`` (a complex source, sr and sc in floats): 0 the real part, 1
-// isign x the imaginary part, 2 their binary32 sum; ``plane_off``: element
-// offset of row 0 in both planes.
 cudaError_t launch_split_real(const qcs_gemm_desc_t *desc, int which, const float *X, int64_t sr,
                               int64_t sc, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
-                              void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
-                              int part = 0, float isign = 1.0f, int64_t plane_off = 0);
+                              void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s);
 // Gauss's three-product CGEMM: desc[1], desc[2] from the selected desc[0]
 // (the T3 operand sums lose one binade of FP16 scaling), and the final
 // combination C = alpha (T1 - T2 + i (T3 - T1 - T2)) + beta C.
 cudaError_t launch_derive_3m_desc(qcs_gemm_desc_t *desc, cudaStream_t s);
+// The three real operands of a Gauss product (real parts, imaginary parts,
+// their binary32 sum) split in one pass over the complex op(X) (complex
+// strides sr, sc; conj negates imaginary parts): part p's planes at element
+// offset p part_off; desc[0]'s scale for parts 0 and 1, desc[2]'s for part 2.
+cudaError_t launch_split_gauss(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
+                               int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad,
+                               int64_t K_pad, void *planes, int64_t pitch, int64_t plane_stride,
+                               int64_t part_off, cudaStream_t s);
 cudaError_t launch_combine_3m(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, const float *T,
                               float2 alpha, float2 beta, float2 *C, int64_t ldc, int num_sms,
                               cudaStream_t s);

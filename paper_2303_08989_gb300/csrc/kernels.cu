@@ -19,6 +19,8 @@
 //                     (Section 5.3.2 irregular shapes).
 //   split_real_kernel, sgemm_simt_kernel, the statistics on float input:
 //                     the same stages for real operands (qcs_sgemm).
+//   split_gauss_kernel, derive_3m_desc_kernel, combine_3m_kernel: the
+//                     three-product (Gauss) form of an emulated CGEMM.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -779,18 +781,14 @@ cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X
 
 namespace {
 
-// Eq. 1 for a real operand: op(X) (R x K, element (r, c) read at
-// X[r sr + c sc]) into two planes, hi and lo, of R_pad x K_pad (row pitch
-// ``pitch``, planes ``plane_stride`` elements apart, row 0 at element
-// ``plane_off``), zero beyond R x K.  ``part`` picks the value from a
-// complex source (sr, sc in floats): 0 the float itself (the real part),
-// 1 isign x the next float (the imaginary part), 2 their binary32 sum (the
-// real part plus isign x the imaginary part: Gauss's operand sums).  Elements
-// are FP16, BF16 (2 bytes) or TF32 (4 bytes), the kind the descriptor selected.
+// Eq. 1 for a real operand: op(X) (R x K, element (r, c) at X[r sr + c sc])
+// into two planes, hi and lo, of R_pad x K_pad (row pitch ``pitch``, planes
+// ``plane_stride`` elements apart), zero beyond R x K.  Elements are FP16,
+// BF16 (2 bytes) or TF32 (4 bytes), the kind the descriptor selected.
 __global__ void __launch_bounds__(256) split_real_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int which, const float *__restrict__ X, int64_t sr,
     int64_t sc, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad, void *planes, int64_t pitch,
-    int64_t plane_stride, int part, float isign, int64_t plane_off) {
+    int64_t plane_stride) {
     const int mode = desc->mode;
     if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
     const int s = (mode == QCS_MODE_FP16X_SCALED) ? (which == 0 ? desc->sA : desc->sB) : 0;
@@ -800,12 +798,7 @@ __global__ void __launch_bounds__(256) split_real_kernel(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t r0 = static_cast<int64_t>(blockIdx.y) * kSplitR;
     const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kSplitC;
-    auto value = [&](int64_t i) -> float {
-        if (part == 0) return X[i];
-        if (part == 1) return isign * X[i + 1];
-        return X[i] + isign * X[i + 1];
-    };
-    if (sc <= 2) {  // lanes along c: the source is (nearly) contiguous there
+    if (sc == 1) {
 #pragma unroll
         for (int i = 0; i < kSplitR / 8; ++i) {
             const int rr = warp + 8 * i;
@@ -813,7 +806,7 @@ __global__ void __launch_bounds__(256) split_real_kernel(
             for (int h = 0; h < 2; ++h) {
                 const int cc = lane + 32 * h;
                 float v = 0.f;
-                if (r0 + rr < R && c0 + cc < K) v = value((r0 + rr) * sr + (c0 + cc) * sc);
+                if (r0 + rr < R && c0 + cc < K) v = X[(r0 + rr) * sr + (c0 + cc)];
                 tile[rr][cc] = v;
             }
         }
@@ -823,7 +816,7 @@ __global__ void __launch_bounds__(256) split_real_kernel(
             const int cc = warp + 8 * i;
             const int rr = lane;
             float v = 0.f;
-            if (r0 + rr < R && c0 + cc < K) v = value((r0 + rr) * sr + (c0 + cc) * sc);
+            if (r0 + rr < R && c0 + cc < K) v = X[(r0 + rr) * sr + (c0 + cc) * sc];
             tile[rr][cc] = v;
         }
     }
@@ -843,7 +836,7 @@ __global__ void __launch_bounds__(256) split_real_kernel(
         }
         const bool two = (c + 1 < K_pad);
         if (mode == QCS_MODE_TF32X) {
-            uint32_t *p = static_cast<uint32_t *>(planes) + plane_off + r * pitch + c;
+            uint32_t *p = static_cast<uint32_t *>(planes) + r * pitch + c;
             const bool vec = two && ((reinterpret_cast<uintptr_t>(p) & 7u) == 0);
             if (vec) {
                 *reinterpret_cast<uint2 *>(p) = make_uint2(hib[0], hib[1]);
@@ -857,7 +850,7 @@ __global__ void __launch_bounds__(256) split_real_kernel(
                 }
             }
         } else {
-            uint16_t *p = static_cast<uint16_t *>(planes) + plane_off + r * pitch + c;
+            uint16_t *p = static_cast<uint16_t *>(planes) + r * pitch + c;
             const bool vec = two && ((reinterpret_cast<uintptr_t>(p) & 3u) == 0);
             if (vec) {
                 *reinterpret_cast<uint32_t *>(p) = hib[0] | (hib[1] << 16);
@@ -878,13 +871,12 @@ __global__ void __launch_bounds__(256) split_real_kernel(
 
 cudaError_t launch_split_real(const qcs_gemm_desc_t *desc, int which, const float *X, int64_t sr,
                               int64_t sc, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
-                              void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
-                              int part, float isign, int64_t plane_off) {
+                              void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s) {
     if (R_pad <= 0 || K_pad <= 0) return cudaSuccess;
     dim3 grid((unsigned)((K_pad + kSplitC - 1) / kSplitC), (unsigned)((R_pad + kSplitR - 1) / kSplitR));
     if (grid.y > 65535u) return cudaErrorInvalidValue;
     split_real_kernel<<<grid, 256, 0, s>>>(desc, which, X, sr, sc, R, K, R_pad, K_pad, planes,
-                                           pitch, plane_stride, part, isign, plane_off);
+                                           pitch, plane_stride);
     return cudaGetLastError();
 }
 
@@ -937,6 +929,120 @@ __global__ void __launch_bounds__(256) combine_3m_kernel(const qcs_gemm_desc_t *
 }
 
 }  // namespace
+
+namespace {
+
+// The three real operands of a Gauss product in one pass over the complex
+// op(X) (R x K, element (r, c) at X[r sr + c sc], conj: negate imaginary
+// parts): part 0 the real parts, 1 the imaginary parts, 2 their binary32
+// sum, each split by Eq. 1 into hi and lo planes at element offset
+// p part_off (planes ``plane_stride`` apart).  Parts 0 and 1 take desc[0]'s
+// scale, part 2 desc[2]'s; all three the kind of desc[0].  X is read once.
+__global__ void __launch_bounds__(256) split_gauss_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int which, const float2 *__restrict__ X, int64_t sr,
+    int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad, void *planes,
+    int64_t pitch, int64_t plane_stride, int64_t part_off) {
+    const int mode = desc[0].mode;
+    if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
+    const int s12 = (mode == QCS_MODE_FP16X_SCALED) ? (which == 0 ? desc[0].sA : desc[0].sB) : 0;
+    const int mode3 = desc[2].mode;
+    const int s3 = (mode3 == QCS_MODE_FP16X_SCALED) ? (which == 0 ? desc[2].sA : desc[2].sB) : 0;
+    const Pow2Scale ps12 = pow2_scale(s12), ps3 = pow2_scale(s3);
+
+    __shared__ float2 tile[kSplitR][kSplitC + 1];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t r0 = static_cast<int64_t>(blockIdx.y) * kSplitR;
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * kSplitC;
+    if (sc == 1) {
+#pragma unroll
+        for (int i = 0; i < kSplitR / 8; ++i) {
+            const int rr = warp + 8 * i;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int cc = lane + 32 * h;
+                float2 v = make_float2(0.f, 0.f);
+                if (r0 + rr < R && c0 + cc < K) v = X[(r0 + rr) * sr + (c0 + cc)];
+                tile[rr][cc] = v;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kSplitC / 8; ++i) {
+            const int cc = warp + 8 * i;
+            const int rr = lane;
+            float2 v = make_float2(0.f, 0.f);
+            if (r0 + rr < R && c0 + cc < K) v = X[(r0 + rr) * sr + (c0 + cc) * sc];
+            tile[rr][cc] = v;
+        }
+    }
+    __syncthreads();
+    const float isign = conj ? -1.0f : 1.0f;
+#pragma unroll
+    for (int i = 0; i < kSplitR / 8; ++i) {
+        const int rr = warp + 8 * i;
+        const int64_t r = r0 + rr;
+        const int cc = 2 * lane;
+        const int64_t c = c0 + cc;
+        if (r >= R_pad || c >= K_pad) continue;
+        const bool two = (c + 1 < K_pad);
+#pragma unroll
+        for (int part = 0; part < 3; ++part) {
+            uint32_t hib[2], lob[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float2 v = tile[rr][cc + e];
+                const float x = part == 0 ? v.x : (part == 1 ? isign * v.y : v.x + isign * v.y);
+                const int s = part == 2 ? s3 : s12;
+                split_value(part == 2 ? mode3 : mode,
+                            (s != 0) ? apply_scale(x, part == 2 ? ps3 : ps12) : x, hib[e], lob[e]);
+            }
+            const int64_t off = part * part_off + r * pitch + c;
+            if (mode == QCS_MODE_TF32X) {
+                uint32_t *p = static_cast<uint32_t *>(planes) + off;
+                const bool vec = two && ((reinterpret_cast<uintptr_t>(p) & 7u) == 0);
+                if (vec) {
+                    *reinterpret_cast<uint2 *>(p) = make_uint2(hib[0], hib[1]);
+                    *reinterpret_cast<uint2 *>(p + plane_stride) = make_uint2(lob[0], lob[1]);
+                } else {
+                    p[0] = hib[0];
+                    p[plane_stride] = lob[0];
+                    if (two) {
+                        p[1] = hib[1];
+                        p[plane_stride + 1] = lob[1];
+                    }
+                }
+            } else {
+                uint16_t *p = static_cast<uint16_t *>(planes) + off;
+                const bool vec = two && ((reinterpret_cast<uintptr_t>(p) & 3u) == 0);
+                if (vec) {
+                    *reinterpret_cast<uint32_t *>(p) = hib[0] | (hib[1] << 16);
+                    *reinterpret_cast<uint32_t *>(p + plane_stride) = lob[0] | (lob[1] << 16);
+                } else {
+                    p[0] = (uint16_t)hib[0];
+                    p[plane_stride] = (uint16_t)lob[0];
+                    if (two) {
+                        p[1] = (uint16_t)hib[1];
+                        p[plane_stride + 1] = (uint16_t)lob[1];
+                    }
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_split_gauss(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
+                               int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad,
+                               int64_t K_pad, void *planes, int64_t pitch, int64_t plane_stride,
+                               int64_t part_off, cudaStream_t s) {
+    if (R_pad <= 0 || K_pad <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((K_pad + kSplitC - 1) / kSplitC), (unsigned)((R_pad + kSplitR - 1) / kSplitR));
+    if (grid.y > 65535u) return cudaErrorInvalidValue;
+    split_gauss_kernel<<<grid, 256, 0, s>>>(desc, which, X, sr, sc, conj, R, K, R_pad, K_pad,
+                                            planes, pitch, plane_stride, part_off);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_derive_3m_desc(qcs_gemm_desc_t *desc, cudaStream_t s) {
     derive_3m_desc_kernel<<<1, 1, 0, s>>>(desc);
