@@ -1,4 +1,4 @@
-// Drop-in interception of cuBLAS complex GEMMs (libqcs_cublas.so).
+// Drop-in interception of cuBLAS single-precision GEMMs (libqcs_cublas.so).
 //
 // The paper's library is used by linking it in front of cuBLAS: calls to the
 // cuBLAS GEMM routines of an unmodified application are redirected to the
@@ -8,16 +8,17 @@
 //   cublasCgemm_v2, cublasCgemmStridedBatched, cublasCgemmBatched,
 //   cublasSgemm_v2, cublasSgemmStridedBatched
 // and runs them through qcs_cgemm / qcs_sgemm on the cuBLAS handle's
-// stream.  Calls it
-// cannot take -- alpha/beta in device memory (CUBLAS_POINTER_MODE_DEVICE),
-// an argument qcs_cgemm rejects, or QCS_CUBLAS_MODE=cublas -- go to the next
-// definition in the link order, the real cuBLAS.
+// stream.  Calls it cannot take -- alpha/beta in device memory
+// (CUBLAS_POINTER_MODE_DEVICE), an argument qcs_cgemm / qcs_sgemm rejects,
+// the batched form with device pointer arrays, or QCS_CUBLAS_MODE=cublas --
+// go to the next definition in the link order, the real cuBLAS.
 //
 // Environment:
 //   QCS_CUBLAS_MODE    auto (default) | fp16x | fp16x_scaled | tf32x | fp32 |
 //                      bf16x3 | cublas (pass every call through)
 //   QCS_UNDERFLOW_TOL  AUTO-t of the qcs handles (read by qcs_create)
 //   QCS_SIZE_RULE      0 off, 1 the paper's cut-offs (default), 2 tuned
+//   QCS_COMPLEX_PRODUCTS  3: complex GEMMs as Gauss's three real products
 //
 // One qcs handle per CUDA stream, created on first use and kept until exit.
 // The calls of one handle are serialised by a lock, as cuBLAS requires of
