@@ -59,8 +59,10 @@ def parse():
     p.add_argument("--no-sweep", action="store_true", help="skip the CGEMM-sweep leg")
     p.add_argument("--no-sgemm", action="store_true", help="skip the real-GEMM leg")
     p.add_argument("--sgemm-sizes", type=int, nargs="+", default=[8192, 16384])
-    p.add_argument("--greedy-trials", type=int, default=256,
+    p.add_argument("--greedy-trials", type=int, default=1024,
                    help="seeded greedy orders tried per network (the cheapest is contracted)")
+    p.add_argument("--greedy-workers", type=int, default=min(16, os.cpu_count() or 1),
+                   help="host processes that cost the seeded orders")
     p.add_argument("--sweep-sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192, 16384])
     p.add_argument("--profile", choices=["slice", "slice_seed2", "gather", "gemm", "sgemm"],
                    default=None,
@@ -282,7 +284,7 @@ def profile_run(args):
         bits = qi.random_bitstrings(30, 1, seed=1)
         if args.profile == "slice":
             plan = tn.plan_circuit(circ, bits, seed=0, n_slices=6, mode=q.MODE_AUTO,
-                                   trials=args.greedy_trials)
+                                   trials=args.greedy_trials, workers=args.greedy_workers)
             ni, what = 16, ("16 slices (one group) of the 5x6 depth-14 network in the cheapest "
                             "of %d greedy orders, AUTO-%g, tuned rule"
                             % (args.greedy_trials, args.tol))
@@ -622,15 +624,28 @@ def main():
                       "serial_ms_per_step": ems_serial}
         del hA, hB, hC, Ad, Bd, Cd, sets
 
+    # The legs after the timed step report beside the headline; one that
+    # raises is recorded as {"error": ...} and the line is still printed.
+    def leg(key, fn):
+        try:
+            res = fn()
+        except Exception as e:  # noqa: BLE001 -- reported in the JSON line
+            import traceback
+
+            traceback.print_exc()
+            out[key or "tree_legs"] = {"error": f"{type(e).__name__}: {e}"[:500]}
+            return
+        out.update(res if key is None else {key: res})
+
     if not args.no_extras:
-        out["hbm_kernels"] = hbm_legs(q, torch, dev, h, stages, n)
+        leg("hbm_kernels", lambda: hbm_legs(q, torch, dev, h, stages, n))
     if not args.no_extras and not args.no_sweep:
-        out["sweep"] = sweep_leg(args, q, torch, dev, rank)
+        leg("sweep", lambda: sweep_leg(args, q, torch, dev, rank))
     if not args.no_extras and not args.no_sgemm:
-        out["sgemm"] = sgemm_leg(args, q, torch, dev, rank)
+        leg("sgemm", lambda: sgemm_leg(args, q, torch, dev, rank))
 
     if not args.no_tree:
-        out.update(tree_legs(args, q, torch, dev, rank))
+        leg(None, lambda: tree_legs(args, q, torch, dev, rank))
 
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -1003,7 +1018,8 @@ def tree_legs(args, q, torch, dev, rank):
     net = tn.circuit_network(circ, bits)
     t0 = time.perf_counter()
     order, sliced, seed_used = tn.best_greedy_order(net, range(args.greedy_trials),
-                                                    skip=[tn.BATCH], n_slices=6)
+                                                    skip=[tn.BATCH], n_slices=6,
+                                                    workers=args.greedy_workers)
     planning_s = time.perf_counter() - t0
     plans = {}
 
@@ -1099,7 +1115,8 @@ def tree_legs(args, q, torch, dev, rank):
     # large enough for the tensor cores) and the cheapest of --greedy-trials orders
     o_s2 = tn.greedy_order(net4, seed=2)
     orders = {"seed2": (o_s2, tn.choose_slices(net4, o_s2, n_labels=2))}
-    o_b, sl_b, _ = tn.best_greedy_order(net4, range(args.greedy_trials), n_slices=2)
+    o_b, sl_b, _ = tn.best_greedy_order(net4, range(args.greedy_trials), n_slices=2,
+                                        workers=args.greedy_workers)
     orders["cheapest"] = (o_b, sl_b)
     for mode, rule, which in (("auto", q.SIZE_RULE_TUNED, "seed2"),
                               ("fp32", q.SIZE_RULE_PAPER, "seed2"),
@@ -1177,7 +1194,8 @@ def scale_leg(args, q, torch, dev, tn, qi, rank):
     bits = qi.random_bitstrings(40, 1, seed=1)
     net = tn.circuit_network(circ, bits)
     order, _, seed_used = tn.best_greedy_order(net, range(args.greedy_trials),
-                                               skip=[tn.BATCH] + labels)
+                                               skip=[tn.BATCH] + labels,
+                                               workers=args.greedy_workers)
     plans = {}
 
     def make_plan(mode):

@@ -235,25 +235,50 @@ def order_cost(net: Network, order, skip: Sequence[int] = ()) -> Tuple[float, fl
     return flops, big
 
 
+def _seeded_order(net: Network, seed: int, skip, n_slices: int, max_log2_size):
+    order = greedy_order(net, seed=seed, skip=skip)
+    sliced = []
+    if n_slices or max_log2_size is not None:
+        sliced = choose_slices(net, order, n_labels=n_slices or None,
+                               max_log2_size=max_log2_size, skip=skip)
+    return order, sliced
+
+
+def _seed_keys(net: Network, seeds: Sequence[int], skip, n_slices: int, max_log2_size):
+    """(flops per instance, largest intermediate, seed) of each seeded order."""
+    keys = []
+    for seed in seeds:
+        order, sliced = _seeded_order(net, seed, skip, n_slices, max_log2_size)
+        flops, big = order_cost(net, order, list(skip) + sliced)
+        keys.append((flops, big, seed))
+    return keys
+
+
 def best_greedy_order(net: Network, seeds: Sequence[int], skip: Sequence[int] = (),
-                      n_slices: int = 0, max_log2_size: Optional[float] = None):
+                      n_slices: int = 0, max_log2_size: Optional[float] = None,
+                      workers: int = 1):
     """The seeded greedy order (and its slicing) with the fewest flops per
     instance over ``seeds``; ties go to the smaller largest intermediate, then
     the smaller seed.  The greedy choice breaks ties between equal scores at
     random, and on grid circuits the seed alone moves the cost of a slice by
-    10x and more.  Returns (order, sliced labels, seed)."""
-    best = None
-    for seed in seeds:
-        order = greedy_order(net, seed=seed, skip=skip)
-        sliced = []
-        if n_slices or max_log2_size is not None:
-            sliced = choose_slices(net, order, n_labels=n_slices or None,
-                                   max_log2_size=max_log2_size, skip=skip)
-        flops, big = order_cost(net, order, list(skip) + sliced)
-        key = (flops, big, seed)
-        if best is None or key < best[0]:
-            best = (key, order, sliced)
-    (_, _, seed), order, sliced = best
+    10x and more.  ``workers`` > 1 costs the seeds in that many worker
+    processes (started with spawn, so a process that already uses CUDA can
+    call it); the result is the same.  Returns (order, sliced labels, seed)."""
+    seeds = list(seeds)
+    skip = list(skip)
+    if workers > 1 and len(seeds) > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        chunks = [seeds[i::workers] for i in range(workers) if seeds[i::workers]]
+        with cf.ProcessPoolExecutor(max_workers=len(chunks),
+                                    mp_context=mp.get_context("spawn")) as ex:
+            futs = [ex.submit(_seed_keys, net, c, skip, n_slices, max_log2_size) for c in chunks]
+            keys = [k for f in futs for k in f.result()]
+    else:
+        keys = _seed_keys(net, seeds, skip, n_slices, max_log2_size)
+    seed = min(keys)[2]
+    order, sliced = _seeded_order(net, seed, skip, n_slices, max_log2_size)
     return order, sliced, seed
 
 
@@ -639,16 +664,18 @@ def contract(cp: CompiledPlan, h, leaves):
 
 
 def plan_circuit(circ, bitstrings=None, seed: int = 2, n_slices: int = 0,
-                 max_log2_size: Optional[float] = None, mode: int = 0, trials: int = 1) -> Plan:
+                 max_log2_size: Optional[float] = None, mode: int = 0, trials: int = 1,
+                 workers: int = 1) -> Plan:
     """circuit -> network -> greedy order (seeded) -> slices -> plan.
     ``n_slices``: number of sliced indices (2**n_slices slices).  ``trials``
     > 1: the cheapest of the greedy orders of seeds seed .. seed + trials - 1
-    (best_greedy_order)."""
+    (best_greedy_order, costed in ``workers`` processes)."""
     net = circuit_network(circ, bitstrings)
     skip = [BATCH] if net.batch else []
     if trials > 1:
         order, sliced, _ = best_greedy_order(net, range(seed, seed + trials), skip=skip,
-                                             n_slices=n_slices, max_log2_size=max_log2_size)
+                                             n_slices=n_slices, max_log2_size=max_log2_size,
+                                             workers=workers)
         return build_plan(net, order, sliced, mode=mode)
     order = greedy_order(net, seed=seed, skip=skip)
     sliced = []

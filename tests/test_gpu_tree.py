@@ -184,8 +184,9 @@ def test_full_size_30_qubit_sliced_amplitudes_vs_fp64_golden(h, golden_dir):
 
 
 def test_full_size_30_qubit_in_the_bench_configuration_vs_fp64_golden(golden_dir):
-    """The contraction as bench.py times it: the cheapest of 256 seeded greedy
-    orders, 6 sliced indices, instances in groups of 16 (grouped tensor-core
+    """The contraction in bench.py's configuration: the cheapest of many
+    seeded greedy orders (256 here), 6 sliced indices, instances in groups
+    of 16 (grouped tensor-core
     launches, batched FP32 steps), AUTO-0.1 under the measured size rule with
     K ranges from the tuner; two bitstrings x 64 slices against the FP64
     amplitudes of tests/golden, eagerly and replayed from a CUDA graph."""

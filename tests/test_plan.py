@@ -127,3 +127,15 @@ def test_best_greedy_order_is_the_cheapest_seed():
     assert plan.flops == pytest.approx(costs[seed][0])
     got = run(plan, _leaves(plan))[:, 0]
     np.testing.assert_allclose(got, oracle.sv_amplitudes(circ, bits), atol=1e-6)
+
+
+def test_best_greedy_order_in_worker_processes_matches_serial():
+    """Costing the seeds in spawned worker processes picks the same order,
+    slicing and seed as the serial search."""
+    circ = qi.random_grid_circuit(4, 4, 10, seed=3)
+    bits = qi.random_bitstrings(16, 1, seed=4)
+    net = tn.circuit_network(circ, bits)
+    skip = [tn.BATCH]
+    serial = tn.best_greedy_order(net, range(5, 29), skip=skip, n_slices=3)
+    parallel = tn.best_greedy_order(net, range(5, 29), skip=skip, n_slices=3, workers=3)
+    assert serial == parallel
