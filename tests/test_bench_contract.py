@@ -13,8 +13,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _run(env_extra):
     env = dict(os.environ)
     env.update(env_extra)
+    # a 2048^3 workload keeps the test short; the contract does not depend on the size
     return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                           "--steps", "1", "--warmup", "3"], cwd=ROOT, env=env,
+                           "--steps", "1", "--warmup", "3", "--size", "2048"], cwd=ROOT, env=env,
                           capture_output=True, text=True, timeout=600)
 
 
@@ -30,7 +31,7 @@ def test_reference_arm_prints_one_contract_line():
         assert key in d, key
     assert d["steps"] == 1 and d["warmup"] == 3 and d["value"] > 0 and d["unit"] == "TFLOP/s"
     assert d["higher_is_better"] is True and d["data"] == "synthetic"
-    assert d["config"]["workload"] and d["config"]["m"] == d["config"]["n"] == d["config"]["k"]
+    assert d["config"]["workload"] and d["config"]["m"] == d["config"]["n"] == d["config"]["k"] == 2048
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     e2e = d["e2e"]
