@@ -28,6 +28,20 @@ def test_library_loads_and_exports_every_declared_symbol():
     assert sorted(_lib.EXPORTED) == names
 
 
+def test_header_is_plain_c_and_cpp():
+    """include/qcs.h is a C ABI: it compiles on its own as C11 and as C++."""
+    import shutil
+    import subprocess
+
+    hdr = os.path.join(ROOT, "include", "qcs.h")
+    for cc, lang, std in (("gcc", "c", "-std=c11"), ("g++", "c++", "-std=c++17")):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not installed")
+        r = subprocess.run([cc, "-fsyntax-only", "-Wall", "-Werror", "-x", lang, std, hdr],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+
+
 def test_cublas_interception_library_exports_its_entry_points():
     """libqcs_cublas.so (the drop-in route) defines the cuBLAS GEMMs it
     intercepts and its counter, and finds libqcs.so next to itself."""
