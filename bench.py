@@ -40,7 +40,7 @@ METRIC = "emulated CGEMM TFLOP/s & contraction s/slice vs plain FP32 at FP32-lev
 UNIT = "TFLOP/s"
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--gpus", type=int, default=1)
@@ -83,7 +83,10 @@ def parse():
                         "would measure distorted times: ncu slows every launch)")
     p.add_argument("--instance-batch", type=int, default=16,
                    help="contraction instances per group (plain-FP32 steps batched)")
-    return p.parse_args()
+    p.add_argument("--legs-file", default=None,
+                   help="also write every leg's full result to this JSON file (each leg is "
+                        "printed to stderr as one JSON line in any case)")
+    return p.parse_args(argv)
 
 
 def log(*a):
@@ -458,6 +461,8 @@ def main():
         "roofline": roofline,
     }
 
+    legs = {}
+
     # ---- error of the GPU result against the FP64 oracle (row sample) + CPU baseline ----
     if rank == 0:
         rows = args.sample_rows
@@ -505,7 +510,7 @@ def main():
             out["fp32"]["rel_fro_vs_fp64"] = oracle.rel_fro_error(C2r, ref)
         # the other emulated paths on the same inputs, forced: TF32X (AUTO's
         # fallback) and BF16X3 (a measured candidate AUTO never selects)
-        out["candidates"] = {}
+        legs["candidates"] = {}
         for mode in ("tf32x", "bf16x3"):
             q.cgemm(h, A, B, C2, mode=mode)
             torch.cuda.synchronize()
@@ -518,7 +523,7 @@ def main():
             if rank == 0:
                 entry["rel_fro_vs_fp64"] = oracle.rel_fro_error(
                     C2[:args.sample_rows].cpu().numpy().astype(np.complex128), ref)
-            out["candidates"][mode] = entry
+            legs["candidates"][mode] = entry
         # Gauss's three-product form (a variant beyond the paper): AUTO-t and
         # forced FP16X on the same inputs, nominal 8 m n k flops
         h3 = q.Handle(tol=args.tol, size_rule=True)
@@ -536,7 +541,7 @@ def main():
             if rank == 0:
                 entry["rel_fro_vs_fp64"] = oracle.rel_fro_error(
                     C2[:args.sample_rows].cpu().numpy().astype(np.complex128), ref)
-            out["candidates"][mode + "_3m"] = entry
+            legs["candidates"][mode + "_3m"] = entry
         h3.close()
         del C2
 
@@ -618,8 +623,7 @@ def main():
         out["e2e"] = {"value": world * flops / (ems * 1e-3) / 1e12, "unit": UNIT,
                       "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8,
                       "ms_per_step": ems, "steps": ek,
-                      "pipelined": "2 buffer sets, 3 streams: copies of neighbouring steps "
-                                   "overlap each step's GEMM",
+                      "pipelined": "2 buffer sets, 3 streams",
                       "serial_value": world * flops / (ems_serial * 1e-3) / 1e12,
                       "serial_ms_per_step": ems_serial}
         del hA, hB, hC, Ad, Bd, Cd, sets
@@ -633,9 +637,9 @@ def main():
             import traceback
 
             traceback.print_exc()
-            out[key or "tree_legs"] = {"error": f"{type(e).__name__}: {e}"[:500]}
+            legs[key or "tree_legs"] = {"error": f"{type(e).__name__}: {e}"[:500]}
             return
-        out.update(res if key is None else {key: res})
+        legs.update(res if key is None else {key: res})
 
     if not args.no_extras:
         leg("hbm_kernels", lambda: hbm_legs(q, torch, dev, h, stages, n))
@@ -648,10 +652,136 @@ def main():
         leg(None, lambda: tree_legs(args, q, torch, dev, rank))
 
     if rank == 0:
-        print(json.dumps(out), flush=True)
+        emit_legs(legs, args.legs_file)
+        print(json.dumps(contract_line(out, legs)), flush=True)
     h.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# output: the legs in full on stderr (and optionally a file), one short line
+# on stdout
+# ---------------------------------------------------------------------------
+
+LINE_LIMIT = 2500  # bytes; the contract line stays well inside what a log tail keeps
+
+
+def _sig(x, digits=4):
+    """``x`` rounded to ``digits`` significant digits (other types unchanged)."""
+    if isinstance(x, float):
+        import math
+
+        if not math.isfinite(x) or x == 0.0:
+            return x if math.isfinite(x) else None
+        return float(f"{x:.{digits}g}")
+    if isinstance(x, dict):
+        return {k: _sig(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_sig(v, digits) for v in x]
+    return x
+
+
+def emit_legs(legs: dict, path=None):
+    """Every leg as one JSON line on stderr, tagged with its name, and all of
+    them in one JSON object at ``path`` when given."""
+    for key, val in legs.items():
+        print(json.dumps({"leg": key, "result": val}, default=str), file=sys.stderr, flush=True)
+    if path:
+        d = os.path.dirname(os.path.abspath(path))
+        os.makedirs(d, exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(legs, f, indent=1, default=str)
+
+
+def legs_summary(legs: dict) -> dict:
+    """A few numbers per leg for the contract line: seconds per slice of the
+    contractions (AUTO against all-FP32) with their errors against FP64, the
+    differentiated workload, the sweep's range of AUTO speed-ups, and the
+    memory-bound kernels' fractions of copy bandwidth; a leg that failed
+    keeps the start of its error message."""
+    s = {}
+
+    def ms(entry):
+        return None if not isinstance(entry, dict) or "s_per_slice" not in entry \
+            else entry["s_per_slice"] * 1e3
+
+    for key, name in (("contraction", "contraction_5x6_d14"),
+                      ("precision_at_scale", "precision_5x8_d12"),
+                      ("contraction_seed2_order", "contraction_5x6_d14_seed2_order")):
+        c = legs.get(key)
+        if not isinstance(c, dict):
+            continue
+        if "error" in c or "skipped" in c:
+            s[name] = {"error": str(c.get("error", c.get("skipped")))[:120]}
+            continue
+        e = {"auto_ms_per_slice": ms(c.get("auto")), "auto_t0.5_ms_per_slice": ms(c.get("auto_t0.5")),
+             "fp32_ms_per_slice": ms(c.get("fp32")), "speedup_vs_fp32": c.get("speedup_vs_fp32")}
+        auto = c.get("auto") or {}
+        if "amplitude_rel_err_vs_fp64" in auto:
+            e["auto_amp_rel_err_vs_fp64"] = auto["amplitude_rel_err_vs_fp64"]
+            e["fp32_amp_rel_err_vs_fp64"] = (c.get("fp32") or {}).get("amplitude_rel_err_vs_fp64")
+        if "sampled_slices_fidelity_vs_fp64" in c:
+            e["auto_infidelity_4_slices_vs_fp64"] = 1.0 - c["sampled_slices_fidelity_vs_fp64"]
+        ff = ((auto.get("routing") or {}).get("flops_fraction"))
+        if ff:
+            e["auto_flops_fraction"] = {k: v for k, v in ff.items() if v}
+        s[name] = e
+    d = legs.get("differentiation")
+    if isinstance(d, dict):
+        if "error" in d:
+            s["differentiation_4x5_d12"] = {"error": str(d["error"])[:120]}
+        else:
+            s["differentiation_4x5_d12"] = {
+                k: d.get(k) for k in ("auto_s", "fp32_s", "speedup_vs_fp32",
+                                      "auto_grad_rel_l2_vs_fp64", "fp32_grad_rel_l2_vs_fp64")}
+            if isinstance(d.get("cheapest_order"), dict):
+                co = d["cheapest_order"]
+                s["differentiation_4x5_d12"]["cheapest_order_auto_s"] = co.get("auto_s")
+                s["differentiation_4x5_d12"]["cheapest_order_fp32_s"] = co.get("fp32_s")
+    p = legs.get("plain_small")
+    if isinstance(p, dict) and "error" not in p:
+        s["plain_3x4_d8"] = {"ms_per_64_bitstrings_graph": (p.get("s_per_batch_grouped_cuda_graph")
+                                                            or 0) * 1e3,
+                             "infidelity_vs_fp64": (None if p.get("fidelity_vs_fp64") is None
+                                                    else 1.0 - p["fidelity_vs_fp64"])}
+    sw = legs.get("sweep")
+    if isinstance(sw, dict):
+        if "error" in sw:
+            s["sweep"] = {"error": str(sw["error"])[:120]}
+        else:
+            sp = [pt["auto_speedup_vs_fp32"] for pt in sw.get("points", [])
+                  if "auto_speedup_vs_fp32" in pt]
+            er = [pt["auto_err_ratio_vs_fp32"] for pt in sw.get("points", [])
+                  if "auto_err_ratio_vs_fp32" in pt]
+            s["sweep"] = {"points": len(sw.get("points", [])),
+                          "auto_speedup_vs_fp32_min_max": [min(sp), max(sp)] if sp else None,
+                          "auto_err_over_fp32_err_min_max": [min(er), max(er)] if er else None}
+    hb = legs.get("hbm_kernels")
+    if isinstance(hb, dict) and "error" not in hb:
+        s["hbm_frac"] = {k: v["frac"] for k, v in hb.items() if isinstance(v, dict) and "frac" in v}
+    for key, val in legs.items():
+        if isinstance(val, dict) and "error" in val and key not in s:
+            s[key] = {"error": str(val["error"])[:120]}
+    return _sig(s)
+
+
+def contract_line(out: dict, legs: dict) -> dict:
+    """The one JSON line of the contract: the headline step's keys from
+    ``out`` and a short summary of the legs, trimmed to ``LINE_LIMIT``
+    bytes (the longest summaries go first)."""
+    line = dict(out)
+    line["legs"] = legs_summary(legs)
+    line["legs_detail"] = "one JSON line per leg on stderr (--legs-file writes them to a file)"
+    keep = ["contraction_5x6_d14", "precision_5x8_d12", "differentiation_4x5_d12", "sweep",
+            "contraction_5x6_d14_seed2_order", "plain_3x4_d8", "hbm_frac"]
+    order = sorted(line["legs"], key=lambda k: -keep.index(k) if k in keep else -len(keep))
+    while len(json.dumps(line)) > LINE_LIMIT and order:
+        line["legs"].pop(order.pop(0))
+    for key in ("stages", "fp32", "error"):
+        if len(json.dumps(line)) > LINE_LIMIT:
+            line.pop(key, None)
+    return line
 
 
 def hbm_legs(q, torch, dev, h, stages, n):
