@@ -168,6 +168,24 @@ int qcs_set_tc_splits(qcs_handle_t h, int splits);
  * Returns QCS_ERR_INVALID_ARG for other values. */
 int qcs_set_complex_products(qcs_handle_t h, int products);
 
+/* Failure detection (not a step of the paper).  Every wait inside the
+ * tensor-core kernels (a TMA stage landing, the MMAs freeing a stage, the
+ * epilogue draining an accumulator) gives up after ``ns`` nanoseconds of the
+ * GPU's global timer; the kernel then records QCS_ERR_TIMEOUT in the
+ * handle's device error word (read by qcs_sync), releases its tensor
+ * memory, waits (bounded) for its copies in flight and returns, leaving C
+ * partly written.  Default 2 s, far above any legitimate wait inside one
+ * launch.  ``ns`` from 1000 to 10^10; QCS_ERR_INVALID_ARG otherwise. */
+int qcs_set_wait_budget(qcs_handle_t h, uint64_t ns);
+
+/* Test hook for failure detection.  While ``enabled`` != 0 the TMA producer
+ * warp of every tensor-core kernel launched on this handle issues no loads,
+ * so the MMA issuer's first wait for a stage never completes and runs out
+ * after the wait budget (qcs_set_wait_budget): the launch takes that path
+ * of a real stall (a lost copy) without any fault.  Results of such calls
+ * are garbage; qcs_sync reports QCS_ERR_TIMEOUT.  Off by default. */
+int qcs_debug_stall_producer(qcs_handle_t h, int enabled);
+
 /* Exponent statistics (Section 4.1, Stage 1 and Stage 2 in one pass) of the
  * rows x cols complex matrix X (device, leading dim ldx >= rows), written
  * to d_stats (device, caller-owned).  rows or cols may be 0. */
@@ -374,33 +392,49 @@ int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
  * Same operation, arguments and semantics as qcs_cgemm, on the stream
  * ``cuda_stream`` (a cudaStream_t; NULL = legacy default stream) of the
  * current device, with underflow tolerance ``underflow_tol`` (as
- * qcs_set_underflow_tol) and the size rule of Section 4.3 disabled (AUTO
- * always selects from the statistics: every problem that fits is below the
- * rule's threshold).  The
+ * qcs_set_underflow_tol) and the size rule that qcs_set_size_rule controls
+ * switched off, so that AUTO always selects from the statistics.  The
  * caller still passes A, B, C (and the optional d_desc_out); the workspace
  * lives in a fixed device array of QCS_NOALLOC_SCRATCH_BYTES (64 MiB) that
  * every GPU which loads this part of the library keeps until the process
- * exits.  A problem whose workspace does not fit -- 256 bytes, the
- * statistics partials, the split-K buffer and the split planes: for op(A)
- * 16 bytes per element of ceil(m/128)*128 x ceil(k/32)*32 and for op(B) 20
- * bytes per element of ceil(n/128)*128 x ceil(k/32)*32 in AUTO and TF32X,
- * half that in the 16-bit modes, none in FP32 --
- * is rejected with QCS_ERR_SCRATCH_TOO_SMALL before anything is launched
- * (m = n = k = 1024 fits in every mode).
+ * exits.  The workspace of a call is 256 bytes, the statistics partials,
+ * the split planes -- for op(A) 16 bytes per element of
+ * ceil(m/128)*128 x ceil(k/32)*32 and for op(B) 20 bytes per element of
+ * ceil(n/128)*128 x ceil(k/32)*32 in AUTO and TF32X, half that in the
+ * 16-bit modes, none in FP32 -- and, when the library splits the
+ * tensor-core GEMM along K (chosen from the shape, up to 16 ranges), 8 bytes
+ * per range per element of m x n for the partial products.  A problem whose
+ * workspace does not fit is rejected with QCS_ERR_SCRATCH_TOO_SMALL before
+ * anything is launched; that return code, not this estimate, is
+ * authoritative (m = n = k = 1024 fits in every mode).
  *
  * Set-up: the first call on a device, with that device current, resolves
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture on the device.  No call allocates or frees
- * memory.  All calls on a device share the one array and it keeps the last
- * call's contents (each call clears what must start at zero): calls that
+ * the array's device address (cudaGetSymbolAddress).  Under CUDA's lazy
+ * module loading that is also the moment the driver commits the 64 MiB on
+ * the device, outside any caller's allocator, and it can fail there with
+ * QCS_ERR_CUDA when the device is full: make that first call at start-up,
+ * and before any stream capture on the device.  Later calls allocate and
+ * free nothing.  All calls on a device share the one array and it keeps the
+ * last call's contents (what must start at zero is cleared): calls that
  * overlap on the GPU, e.g. on two concurrent streams, race and corrupt each
- * other's results; serialise them.  Device-side wait timeouts are recorded
- * in the shared array but not reported (there is no handle to qcs_sync). */
+ * other's results; serialise them.  A device-side wait that times out
+ * (see qcs_set_wait_budget; default 2 s) leaves C partly written and sets
+ * an error word in the array that stays set until qcs_cgemm_noalloc_status
+ * clears it. */
 #define QCS_NOALLOC_SCRATCH_BYTES (64u << 20)
 int qcs_cgemm_noalloc(void *cuda_stream, qcs_mode_t mode, double underflow_tol, qcs_op_t transA,
                       qcs_op_t transB, int64_t m, int64_t n, int64_t k, const qcs_c32 *alpha,
                       const qcs_c32 *A, int64_t lda, const qcs_c32 *B, int64_t ldb,
                       const qcs_c32 *beta, qcs_c32 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out);
+
+/* The device-side status of qcs_cgemm_noalloc on the current device (the
+ * paper has no counterpart; a no-allocation caller has no handle to pass to
+ * qcs_sync).  Waits for ``cuda_stream``, then returns QCS_ERR_TIMEOUT if a
+ * wait inside a tensor-core kernel of any qcs_cgemm_noalloc call on this
+ * device gave up since the word was last cleared, QCS_SUCCESS if none did
+ * (or no call has run on the device yet), QCS_ERR_CUDA on a runtime error.
+ * ``reset`` != 0 clears the word after reading it.  Allocates nothing. */
+int qcs_cgemm_noalloc_status(void *cuda_stream, int reset);
 
 /* ---- autotuning: the size rule re-derived on this GPU ------------------ */
 
@@ -459,6 +493,15 @@ int qcs_get_tuning(qcs_handle_t h, qcs_tune_entry_t *entries, int64_t capacity, 
  * earlier process on the same GPU; each replaces the entry of its key.
  * best must be AUTO, TF32X or FP32. */
 int qcs_set_tuning(qcs_handle_t h, const qcs_tune_entry_t *entries, int64_t count);
+
+/* Measurement aid (not a step of the paper): the FP32 FMA rate of the CUDA
+ * cores, the roofline of the plain FP32 CGEMM (QCS_MODE_FP32 and the
+ * baseline of Section 5).  Runs a kernel of independent FMA chains on every
+ * SM (64 warps each, about 50 ms) on the handle's stream and writes
+ * 2 x FMAs / second / 1e12 to *tflops (host).  Synchronizes the stream; not
+ * during a stream capture.  The rate depends on the clock the GPU runs at
+ * under this load. */
+int qcs_measure_fma_peak(qcs_handle_t h, double *tflops);
 
 /* Stage timing (tracing aid, off by default).  While enabled, every call
  * records a pair of CUDA events on the handle's stream around each stage

@@ -174,6 +174,25 @@ class Handle:
         _lib.check(self.lib.qcs_set_complex_products(self._h, int(products)),
                    "qcs_set_complex_products")
 
+    def set_wait_budget(self, ns: int):
+        """Bound of every device-side wait in the tensor-core kernels
+        (qcs_set_wait_budget), in nanoseconds."""
+        _lib.check(self.lib.qcs_set_wait_budget(self._h, int(ns)), "qcs_set_wait_budget")
+
+    def debug_stall_producer(self, enabled: bool):
+        """Test hook (qcs_debug_stall_producer): the tensor-core kernels'
+        TMA producer issues no loads, so their waits run out."""
+        _lib.check(self.lib.qcs_debug_stall_producer(self._h, int(bool(enabled))),
+                   "qcs_debug_stall_producer")
+
+    def measure_fma_peak(self) -> float:
+        """FP32 FMA rate of the CUDA cores in TFLOP/s (qcs_measure_fma_peak):
+        the roofline of the plain FP32 CGEMM."""
+        out = ctypes.c_double()
+        _lib.check(self.lib.qcs_measure_fma_peak(self._h, ctypes.byref(out)),
+                   "qcs_measure_fma_peak")
+        return out.value
+
     def set_drain_stages(self, stages: int):
         _lib.check(self.lib.qcs_set_drain_stages(self._h, int(stages)), "qcs_set_drain_stages")
         self.drain_stages = int(stages)

@@ -34,7 +34,8 @@ EXPORTED = [
     "qcs_status_string", "qcs_cgemm_noalloc", "qcs_tree_graph_create", "qcs_tree_graph_launch",
     "qcs_tree_graph_destroy", "qcs_get_auto_counts", "qcs_autotune_gemm", "qcs_autotune_tree",
     "qcs_get_tuning", "qcs_set_tuning", "qcs_set_instance_batch", "qcs_set_tc_schedule",
-    "qcs_set_tc_splits", "qcs_sgemm", "qcs_set_complex_products",
+    "qcs_set_tc_splits", "qcs_sgemm", "qcs_set_complex_products", "qcs_set_wait_budget",
+    "qcs_debug_stall_producer", "qcs_cgemm_noalloc_status", "qcs_measure_fma_peak",
 ]
 SIZE_RULE_OFF, SIZE_RULE_PAPER, SIZE_RULE_TUNED = 0, 1, 2
 NUM_MODES = 6
@@ -153,6 +154,10 @@ def load(path: str = LIB_PATH):
         "qcs_set_tc_schedule": [H, I, I],
         "qcs_set_tc_splits": [H, I],
         "qcs_set_complex_products": [H, I],
+        "qcs_set_wait_budget": [H, ctypes.c_uint64],
+        "qcs_debug_stall_producer": [H, I],
+        "qcs_cgemm_noalloc_status": [P, I],
+        "qcs_measure_fma_peak": [H, ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

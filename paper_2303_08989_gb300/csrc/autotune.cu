@@ -39,9 +39,31 @@ __global__ void fill_unit_binade(float2 *__restrict__ x, int64_t n, uint64_t see
     }
 }
 
-constexpr double kFp32BoundFlops = 45e12;  // above the SIMT CGEMM's measured rate
+// Above the SIMT CGEMM's rate: the CUDA cores' FP32 FMA peak at the maximum
+// clock is 152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s.
+constexpr double kFp32BoundFlops = 90e12;
 constexpr float kFp32Prune = 4.0f;
 const int kCandidates[3] = {QCS_MODE_AUTO, QCS_MODE_TF32X, QCS_MODE_FP32};
+
+// FP32 FMA throughput of the CUDA cores: each thread runs 16 independent
+// chains x <- x a + b (a, b are arguments, so nothing folds), 128 FMAs per
+// loop trip.  The sum is stored only if it equals -1, which it never does
+// for a in (0, 1), b > 0, so the chains stay live.
+__global__ void __launch_bounds__(256) fma_peak_kernel(float a, float b, int iters, float *sink) {
+    float x[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = threadIdx.x * 1e-3f + (float)j;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) x[j] = fmaf(x[j], a, b);
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sum += x[j];
+    if (sum == -1.0f) sink[blockIdx.x] = sum;
+}
 
 struct DeviceBuffer {
     void *p = nullptr;
@@ -214,3 +236,39 @@ int qcs_set_tuning(qcs_handle_t h, const qcs_tune_entry_t *entries, int64_t coun
 }
 
 }  // extern "C"
+
+
+int qcs_measure_fma_peak(qcs_handle_t h, double *tflops) {
+    if (!h || !tflops) return QCS_ERR_INVALID_ARG;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return QCS_ERR_UNSUPPORTED;
+    const int blocks = 8 * h->num_sms;  // 64 warps per SM
+    const int iters = 4096;             // 2^19 FMAs per thread: about 50 ms
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return QCS_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return QCS_ERR_CUDA;
+    }
+    float *sink = static_cast<float *>(h->ws.ptr);  // never written (see the kernel)
+    fma_peak_kernel<<<blocks, 256, 0, h->stream>>>(0.999999f, 1e-6f, iters / 8, sink);
+    cudaEventRecord(e0, h->stream);
+    fma_peak_kernel<<<blocks, 256, 0, h->stream>>>(0.999999f, 1e-6f, iters, sink);
+    cudaEventRecord(e1, h->stream);
+    float ms = 0.f;
+    const bool ok = cudaGetLastError() == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                    cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.f;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    const double flops = 2.0 * 128.0 * iters * 256.0 * blocks;
+    *tflops = flops / (ms * 1e-3) / 1e12;
+    return QCS_SUCCESS;
+}

@@ -303,6 +303,8 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                          eff == QCS_MODE_FP16X_SCALED || eff == QCS_MODE_BF16X3);
     const bool need32 = (eff == QCS_MODE_AUTO || eff == QCS_MODE_TF32X);
     TcWork w;
+    w.wait_ns = h->wait_ns;
+    w.stall = h->debug_stall;
     w.G = G;
     w.a_rows = mp;
     w.b_rows = np;
@@ -513,6 +515,8 @@ int run_sgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     } else {
         TcWork w;
+        w.wait_ns = h->wait_ns;
+        w.stall = h->debug_stall;
         w.S = tc_split_count(m, n, k, 1, h->num_sms, h->tc_splits, true);
         const RealLayout L = real_layout(eff, m, n, k, w.S);
         uint8_t *planesA = p + L.a, *planesB = p + L.b;
@@ -634,6 +638,8 @@ int run_cgemm_3m(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m,
     if (e != cudaSuccess) return QCS_ERR_CUDA;
 
     TcWork w;
+    w.wait_ns = h->wait_ns;
+    w.stall = h->debug_stall;
     w.G = 3;
     w.S = tc_split_count(m, n, k, 1, h->num_sms, h->tc_splits, true);
     const Gauss3Layout L = gauss3_layout(eff, m, n, k, w.S);
@@ -815,6 +821,18 @@ int qcs_set_tc_splits(qcs_handle_t h, int splits) {
 int qcs_set_complex_products(qcs_handle_t h, int products) {
     if (!h || (products != 3 && products != 4)) return QCS_ERR_INVALID_ARG;
     h->complex_products = products;
+    return QCS_SUCCESS;
+}
+
+int qcs_set_wait_budget(qcs_handle_t h, uint64_t ns) {
+    if (!h || ns < 1000ull || ns > 10000000000ull) return QCS_ERR_INVALID_ARG;
+    h->wait_ns = ns;
+    return QCS_SUCCESS;
+}
+
+int qcs_debug_stall_producer(qcs_handle_t h, int enabled) {
+    if (!h) return QCS_ERR_INVALID_ARG;
+    h->debug_stall = enabled ? 1 : 0;
     return QCS_SUCCESS;
 }
 

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             uint32_t phase = 0;
             int issued = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+            for (int u = blockIdx.x; u < num_units && ok && !w.stall; u += gridDim.x) {
                 const Unit x = unit_of(u, num_tiles, w.S);
                 if (w.G > 1 && !kind_runs(KIND, desc[x.g].mode)) continue;
                 int tm, tn;
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int rowB = static_cast<int>(x.g * w.b_rows) + tn * Geo::tile_n;
                 const int kb1 = kb_begin(x.r + 1);
                 for (int kb = kb_begin(x.r); kb < kb1; ++kb) {
-                    if (!mbar_wait(&S.empty[stage], phase ^ 1u, globaltimer_ns() + kWaitBudgetNs,
+                    if (!mbar_wait(&S.empty[stage], phase ^ 1u, globaltimer_ns() + w.wait_ns,
                                    abort_flag)) {
                         if (!*abort_flag) raise_abort(S, d_err, kErrTimeoutProducer);
                         ok = false;
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             bool ok = true;
             auto wait_drained = [&]() -> bool {
                 if (!pending) return true;
-                if (!mbar_wait(&S.acc0_empty, e_phase, globaltimer_ns() + kWaitBudgetNs,
+                if (!mbar_wait(&S.acc0_empty, e_phase, globaltimer_ns() + w.wait_ns,
                                abort_flag))
                     return false;
                 e_phase ^= 1u;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (w.G > 1 && !kind_runs(KIND, desc[x.g].mode)) continue;
                 const int kb0 = kb_begin(x.r), kb1 = kb_begin(x.r + 1);
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!mbar_wait(&S.full[stage], phase, globaltimer_ns() + kWaitBudgetNs,
+                    if (!mbar_wait(&S.full[stage], phase, globaltimer_ns() + w.wait_ns,
                                    abort_flag)) {
                         ok = false;
                         break;
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // so tensor memory is idle before it is released.
             tc_commit(&S.drain);
             volatile int never = 0;
-            (void)mbar_wait(&S.drain, 0, globaltimer_ns() + kWaitBudgetNs, &never);
+            (void)mbar_wait(&S.drain, 0, globaltimer_ns() + w.wait_ns, &never);
         }
     } else {
         // ---------------- epilogue (warps 2..9) ----------------
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const bool last = kb >= nkb - 1;  // the group holding the unit's last stage
                 int got = 0;
                 if (lane == 0)
-                    got = mbar_wait(&S.acc0_full, f_phase, globaltimer_ns() + kWaitBudgetNs,
+                    got = mbar_wait(&S.acc0_full, f_phase, globaltimer_ns() + w.wait_ns,
                                     abort_flag)
                               ? 1
                               : 0;

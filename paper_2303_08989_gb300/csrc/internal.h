@@ -95,6 +95,8 @@ struct qcs_handle_s {
     int tc_l2_promotion = 256;       // L2 promotion of the plane loads (bytes; 0 = none)
     int tc_splits = 0;               // K ranges per tensor-core GEMM (0 = chosen per shape)
     int complex_products = 4;        // real products per emulated complex product (4, or 3: Gauss)
+    uint64_t wait_ns = qcs::kWaitBudgetNs;  // bound of the tensor-core kernels' device waits
+    int debug_stall = 0;             // test hook: the TMA producer issues no loads
     int *d_err = nullptr;            // device error word (start of a 64-byte block)
     unsigned long long *d_counts = nullptr;  // in that block: AUTO selections per mode, flops
     qcs::Workspace ws;               // GEMM workspace (planes, partials, descriptor)
@@ -228,6 +230,11 @@ int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k
 size_t gemm_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits,
                             int G = 1);
 // ``bt``: a batch of equal-shape GEMMs (plain FP32 only; UNSUPPORTED otherwise).
+// Host-side argument checks of qcs_cgemm (QCS_SUCCESS or an error code).
+int validate_cgemm(int mode, int opA, int opB, int64_t m, int64_t n, int64_t k, const void *alpha,
+                   const void *A, int64_t lda, const void *B, int64_t ldb, const void *beta,
+                   const void *C, int64_t ldc);
+
 int run_cgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n, int64_t k,
               float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb, float2 beta,
               float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out, const qcs_gemm_desc_t *d_desc_in,
@@ -282,10 +289,15 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
 // desc[g], and writes C + g * c_stride.  S > 1: every range writes its
 // partial into P ([r][g] blocks of m x n complex, column-major, ld m) and
 // launch_tc_reduce then forms C.
+// ``wait_ns`` bounds every device-side wait of the launch; ``stall`` (a test
+// hook, qcs_debug_stall_producer) makes the TMA producer issue no loads, so
+// that the MMA issuer's first wait runs out and the launch records a timeout.
 struct TcWork {
     int G = 1, S = 1;
     int64_t a_rows = 0, b_rows = 0, c_stride = 0;
     float2 *P = nullptr;
+    uint64_t wait_ns = kWaitBudgetNs;
+    int stall = 0;
 };
 constexpr int kMaxSplits = 16;
 // K ranges for a launch over G GEMMs of m x n x k: ``forced`` > 0 is taken

@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "ptx.cuh"
 
 namespace qcs {
 
@@ -1624,8 +1625,23 @@ cudaError_t launch_accumulate_c128(const float2 *src, double *dst, int64_t count
 
 namespace {
 
-constexpr int kSBM = 128, kSBN = 64, kSBK = 8;  // complex tile; 256 threads, 8 x 4 per thread
-constexpr int kSPadA = 2, kSPadB = 2;
+// C = alpha op(A) op(B) + beta C on the CUDA cores, four FP32 FMAs per
+// complex multiply-add.  A block of 256 threads computes a 128 x 64 complex
+// tile of C: warp w owns the 32 x 32 sub-tile at rows 32 (w % 4), columns
+// 32 (w / 4); lane (ty, tx) = (lane / 8, lane % 8) owns rows 4 ty .. 4 ty + 3
+// and 16 + 4 ty .. 16 + 4 ty + 3 of it, columns 2 tx, 2 tx + 1, 16 + 2 tx,
+// 16 + 2 tx + 1 (8 x 4 complex accumulators).  Per k the lane reads its A
+// and B values as six 16-byte shared loads, each one shared-memory wavefront
+// (the A loads are broadcast over tx, the B loads contiguous over tx).
+// Operand tiles of 16 k move from global to shared memory with 8-byte
+// cp.async copies (zero-filled outside the matrix) in a three-stage ring, so
+// the copies of k-tile t + 2 overlap the products of tile t.  op T and op C
+// change the copy addressing; the conjugation of op C is folded into the
+// signs of the FMAs (template flags CA, CB).
+constexpr int kSBM = 128, kSBN = 64, kSBK = 16, kSStages = 3;
+constexpr int kSRowA = kSBM + 2, kSRowB = kSBN + 2;  // padded rows (16-byte multiples)
+constexpr size_t kSimtSmemA = sizeof(float2) * kSStages * kSBK * kSRowA;
+constexpr size_t kSimtSmemBytes = kSimtSmemA + sizeof(float2) * kSStages * kSBK * kSRowB;
 
 __device__ __forceinline__ float2 ld_op(const float2 *X, int op, int64_t r, int64_t c, int64_t ld) {
     float2 v = (op == QCS_OP_N) ? X[r + c * ld] : X[c + r * ld];
@@ -1633,20 +1649,91 @@ __device__ __forceinline__ float2 ld_op(const float2 *X, int op, int64_t r, int6
     return v;
 }
 
-__global__ void __launch_bounds__(256) cgemm_simt_kernel(
-    const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int m, int n, int k, float2 alpha,
+template <int OPA, int OPB>
+__global__ void __launch_bounds__(256, 2) cgemm_simt_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int m, int n, int k, float2 alpha,
     const float2 *__restrict__ A, int64_t lda, const float2 *__restrict__ B, int64_t ldb,
     float2 beta, float2 *__restrict__ C, int64_t ldc, GemmBatch bt) {
+    constexpr bool transA = OPA != QCS_OP_N, transB = OPB != QCS_OP_N;
+    constexpr bool CA = OPA == QCS_OP_C, CB = OPB == QCS_OP_C;
     if (desc && desc->mode != QCS_MODE_FP32) return;
     A += blockIdx.z * bt.sA;
     B += blockIdx.z * bt.sB;
     C += blockIdx.z * bt.sC;
-    __shared__ __align__(16) float2 As[2][kSBK][kSBM + kSPadA];
-    __shared__ __align__(16) float2 Bs[2][kSBK][kSBN + kSPadB];
+    extern __shared__ __align__(16) unsigned char simt_smem[];
+    float2 (*As)[kSBK][kSRowA] = reinterpret_cast<float2 (*)[kSBK][kSRowA]>(simt_smem);
+    float2 (*Bs)[kSBK][kSRowB] = reinterpret_cast<float2 (*)[kSBK][kSRowB]>(simt_smem + kSimtSmemA);
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int ty = lane >> 3, tx = lane & 7;
+    const int wm = (warp & 3) * 32, wn = (warp >> 2) * 32;
     const int64_t bm = static_cast<int64_t>(blockIdx.y) * kSBM;
     const int64_t bn = static_cast<int64_t>(blockIdx.x) * kSBN;
+
+    // Copy assignment (fixed per thread): op(A) tile element (i, l) and op(B)
+    // tile element (l, j).  op N of A: i = tid % 128, l = tid / 128 + 2 q;
+    // op T/C: l = tid % 16, i = tid / 16 + 16 q (q < 8).  op N of B:
+    // l = tid % 16, j = tid / 16 + 16 q; op T/C: j = tid % 64,
+    // l = tid / 64 + 4 q (q < 4).  Consecutive threads read consecutive
+    // addresses.  Copy q of k-tile kt reads base + kt kstep + q qstep; the
+    // rows / columns outside the matrix are fixed per thread (bit q of the
+    // mask), and k is checked only in the last k-tile.
+    const int aI = transA ? (tid >> 4) : (tid & (kSBM - 1));
+    const int aL = transA ? (tid & (kSBK - 1)) : (tid >> 7);
+    const int bL = transB ? (tid >> 6) : (tid & (kSBK - 1));
+    const int bJ = transB ? (tid & (kSBN - 1)) : (tid >> 4);
+    const int64_t a_kstep = transA ? kSBK : kSBK * lda;
+    const int64_t a_qstep = transA ? 16 * lda : 2 * lda;
+    const int64_t b_kstep = transB ? kSBK * ldb : kSBK;
+    const int64_t b_qstep = transB ? 4 * ldb : 16 * ldb;
+    const float2 *a_base = A + (transA ? aL + (bm + aI) * lda : bm + aI + aL * lda);
+    const float2 *b_base = B + (transB ? bn + bJ + bL * ldb : bL + (bn + bJ) * ldb);
+    uint32_t a_mask = 0, b_mask = 0;  // bit q: copy q's row (column) lies inside the matrix
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        a_mask |= uint32_t(bm + aI + (transA ? 16 * q : 0) < m) << q;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        b_mask |= uint32_t(bn + bJ + (transB ? 0 : 16 * q) < n) << q;
+
+    // a tile whose rows and columns all lie inside C copies without checks
+    // except in the last k-tile
+    const bool interior = bm + kSBM <= m && bn + kSBN <= n;
+
+    // k-tile kt of both operands into ring slot st (8 + 4 copies per thread)
+    auto load_tile = [&](int st, int kt) {
+        const int64_t k0 = static_cast<int64_t>(kt) * kSBK;
+        const bool tail = k0 + kSBK > k;
+        const float2 *pa = a_base + kt * a_kstep;
+        const float2 *pb = b_base + kt * b_kstep;
+        if (interior && !tail) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                cp_async8(&As[st][transA ? aL : aL + 2 * q][transA ? aI + 16 * q : aI],
+                          pa + q * a_qstep, 8u);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                cp_async8(&Bs[st][transB ? bL + 4 * q : bL][transB ? bJ : bJ + 16 * q],
+                          pb + q * b_qstep, 8u);
+            return;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int l = transA ? aL : aL + 2 * q;
+            const int i = transA ? aI + 16 * q : aI;
+            bool ok = (a_mask >> q) & 1u;
+            if (tail) ok = ok && k0 + l < k;
+            cp_async8(&As[st][l][i], ok ? pa + q * a_qstep : A, ok ? 8u : 0u);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int l = transB ? bL + 4 * q : bL;
+            const int j = transB ? bJ : bJ + 16 * q;
+            bool ok = (b_mask >> q) & 1u;
+            if (tail) ok = ok && k0 + l < k;
+            cp_async8(&Bs[st][l][j], ok ? pb + q * b_qstep : B, ok ? 8u : 0u);
+        }
+    };
 
     float2 acc[8][4];
 #pragma unroll
@@ -1654,117 +1741,57 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
-    float2 ra[4], rb[2];
-    auto load_global = [&](int kt) {
-        const int64_t k0 = static_cast<int64_t>(kt) * kSBK;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int idx = tid + 256 * q;
-            int i, l;
-            if (opA == QCS_OP_N) {
-                i = idx % kSBM;
-                l = idx / kSBM;
-            } else {
-                l = idx % kSBK;
-                i = idx / kSBK;
-            }
-            const int64_t gi = bm + i, gl = k0 + l;
-            ra[q] = (gi < m && gl < k) ? ld_op(A, opA, gi, gl, lda) : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int idx = tid + 256 * q;
-            int l, j;
-            if (opB == QCS_OP_N) {
-                l = idx % kSBK;
-                j = idx / kSBK;
-            } else {
-                j = idx % kSBN;
-                l = idx / kSBN;
-            }
-            const int64_t gl = k0 + l, gj = bn + j;
-            rb[q] = (gl < k && gj < n) ? ld_op(B, opB, gl, gj, ldb) : make_float2(0.f, 0.f);
-        }
-    };
-    auto store_shared = [&](int buf) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int idx = tid + 256 * q;
-            int i, l;
-            if (opA == QCS_OP_N) {
-                i = idx % kSBM;
-                l = idx / kSBM;
-            } else {
-                l = idx % kSBK;
-                i = idx / kSBK;
-            }
-            As[buf][l][i] = ra[q];
-        }
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int idx = tid + 256 * q;
-            int l, j;
-            if (opB == QCS_OP_N) {
-                l = idx % kSBK;
-                j = idx / kSBK;
-            } else {
-                j = idx % kSBN;
-                l = idx / kSBN;
-            }
-            Bs[buf][l][j] = rb[q];
-        }
-    };
-
     const int ktiles = (k + kSBK - 1) / kSBK;
-    if (ktiles > 0) {
-        load_global(0);
-        store_shared(0);
-        __syncthreads();
-    }
+    if (ktiles > 0) load_tile(0, 0);
+    cp_async_commit();
+    if (ktiles > 1) load_tile(1, 1);
+    cp_async_commit();
     for (int kt = 0; kt < ktiles; ++kt) {
-        const int buf = kt & 1;
-        if (kt + 1 < ktiles) load_global(kt + 1);
+        cp_async_wait<1>();  // every group but the newest has landed: tile kt
+        __syncthreads();     // ... for all threads; and slot (kt + 2) % 3 is free
+        if (kt + 2 < ktiles) load_tile((kt + 2) % kSStages, kt + 2);
+        cp_async_commit();
+        const int st = kt % kSStages;
 #pragma unroll
         for (int l = 0; l < kSBK; ++l) {
             float2 a[8], b[4];
-            const float4 *ap = reinterpret_cast<const float4 *>(&As[buf][l][ty * 8]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float4 v = ap[i];
-                a[2 * i] = make_float2(v.x, v.y);
-                a[2 * i + 1] = make_float2(v.z, v.w);
+            for (int h = 0; h < 4; ++h) {
+                const float4 v = *reinterpret_cast<const float4 *>(
+                    &As[st][l][wm + (h >> 1) * 16 + ty * 4 + (h & 1) * 2]);
+                a[2 * h] = make_float2(v.x, v.y);
+                a[2 * h + 1] = make_float2(v.z, v.w);
             }
-            const float4 *bp = reinterpret_cast<const float4 *>(&Bs[buf][l][tx * 4]);
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const float4 v = bp[j];
-                b[2 * j] = make_float2(v.x, v.y);
-                b[2 * j + 1] = make_float2(v.z, v.w);
+            for (int h = 0; h < 2; ++h) {
+                const float4 v = *reinterpret_cast<const float4 *>(&Bs[st][l][wn + h * 16 + tx * 2]);
+                b[2 * h] = make_float2(v.x, v.y);
+                b[2 * h + 1] = make_float2(v.z, v.w);
             }
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
+                    // op(A) = (ar, sA ai), op(B) = (br, sB bi):
+                    // re += ar br - sA sB ai bi, im += sB ar bi + sA ai br
                     acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
-                    acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
-                    acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
-                    acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
+                    acc[i][j].x = fmaf((CA == CB) ? -a[i].y : a[i].y, b[j].y, acc[i][j].x);
+                    acc[i][j].y = fmaf(CB ? -a[i].x : a[i].x, b[j].y, acc[i][j].y);
+                    acc[i][j].y = fmaf(CA ? -a[i].y : a[i].y, b[j].x, acc[i][j].y);
                 }
         }
-        if (kt + 1 < ktiles) {
-            store_shared(buf ^ 1);
-            __syncthreads();
-        }
     }
+    cp_async_wait<0>();
+
     const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int64_t gi = bm + ty * 8 + i;
-        if (gi >= m) continue;
+    for (int j = 0; j < 4; ++j) {
+        const int64_t gj = bn + wn + (j >> 1) * 16 + tx * 2 + (j & 1);
+        if (gj >= n) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t gj = bn + tx * 4 + j;
-            if (gj >= n) continue;
+        for (int i = 0; i < 8; ++i) {
+            const int64_t gi = bm + wm + (i >> 2) * 16 + ty * 4 + (i & 3);
+            if (gi >= m) continue;
             float2 o;
             o.x = alpha.x * acc[i][j].x - alpha.y * acc[i][j].y;
             o.y = alpha.x * acc[i][j].y + alpha.y * acc[i][j].x;
@@ -1777,6 +1804,39 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(
             *dst = o;
         }
     }
+}
+
+template <int OPA, int OPB>
+cudaError_t launch_simt_tiles(dim3 grid, cudaStream_t s, const qcs_gemm_desc_t *desc, int m,
+                              int n, int k, float2 alpha, const float2 *A, int64_t lda,
+                              const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc,
+                              const GemmBatch &bt) {
+    static bool configured = false;  // the attribute is per function, set once
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(cgemm_simt_kernel<OPA, OPB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSimtSmemBytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    cgemm_simt_kernel<OPA, OPB><<<grid, 256, kSimtSmemBytes, s>>>(desc, m, n, k, alpha, A, lda, B,
+                                                                  ldb, beta, C, ldc, bt);
+    return cudaGetLastError();
+}
+
+template <int OPA>
+cudaError_t launch_simt_tiles_b(int opB, dim3 grid, cudaStream_t s, const qcs_gemm_desc_t *desc,
+                                int m, int n, int k, float2 alpha, const float2 *A, int64_t lda,
+                                const float2 *B, int64_t ldb, float2 beta, float2 *C, int64_t ldc,
+                                const GemmBatch &bt) {
+    if (opB == QCS_OP_N)
+        return launch_simt_tiles<OPA, QCS_OP_N>(grid, s, desc, m, n, k, alpha, A, lda, B, ldb,
+                                                beta, C, ldc, bt);
+    if (opB == QCS_OP_T)
+        return launch_simt_tiles<OPA, QCS_OP_T>(grid, s, desc, m, n, k, alpha, A, lda, B, ldb,
+                                                beta, C, ldc, bt);
+    return launch_simt_tiles<OPA, QCS_OP_C>(grid, s, desc, m, n, k, alpha, A, lda, B, ldb, beta,
+                                            C, ldc, bt);
 }
 
 // Small k with one small output side: the (2, 2^N, 2) and (2^N, 2, 2)
@@ -2191,9 +2251,11 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
     }
     dim3 grid((unsigned)((n + kSBN - 1) / kSBN), (unsigned)((m + kSBM - 1) / kSBM), G);
     if (grid.y > 65535u) return cudaErrorInvalidValue;
-    cgemm_simt_kernel<<<grid, 256, 0, s>>>(desc, opA, opB, (int)m, (int)n, (int)k, alpha, A, lda, B,
-                                           ldb, beta, C, ldc, bt);
-    return cudaGetLastError();
+    auto launch = opA == QCS_OP_N   ? launch_simt_tiles_b<QCS_OP_N>
+                  : opA == QCS_OP_T ? launch_simt_tiles_b<QCS_OP_T>
+                                    : launch_simt_tiles_b<QCS_OP_C>;
+    return launch(opB, grid, s, desc, (int)m, (int)n, (int)k, alpha, A, lda, B, ldb, beta, C, ldc,
+                  bt);
 }
 
 // ===========================================================================

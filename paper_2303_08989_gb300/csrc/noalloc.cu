@@ -25,10 +25,6 @@ constexpr size_t kNoallocBytes = QCS_NOALLOC_SCRATCH_BYTES;
 constexpr size_t kNoallocHeader = 256;  // device error word, then unused bytes
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-int validate_cgemm(int mode, int opA, int opB, int64_t m, int64_t n, int64_t k, const void *alpha,
-                   const void *A, int64_t lda, const void *B, int64_t ldb, const void *beta,
-                   const void *C, int64_t ldc);
-
 namespace {
 
 constexpr int kMaxDevices = 64;
@@ -44,13 +40,19 @@ DeviceSetup g_setup[kMaxDevices];
 EncodeTiledFn g_encode = nullptr;
 
 // Once per device, with that device current: resolve the scratch array's
-// device address and the SM count.  Returns QCS_SUCCESS or an error code.
-int noalloc_setup(int dev, DeviceSetup *&out) {
+// device address and the SM count, and clear the error word on ``s`` (the
+// first caller's stream, ahead of its launches).  Returns QCS_SUCCESS or an
+// error code.
+int noalloc_setup(int dev, cudaStream_t s, DeviceSetup *&out) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     DeviceSetup &d = g_setup[dev];
     if (!d.ready) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
+            cudaGetLastError();
+            return QCS_ERR_CUDA;
+        }
+        if (cudaMemsetAsync(ptr, 0, kNoallocHeader, s) != cudaSuccess) {
             cudaGetLastError();
             return QCS_ERR_CUDA;
         }
@@ -98,12 +100,12 @@ extern "C" int qcs_cgemm_noalloc(void *cuda_stream, qcs_mode_t mode, double unde
     }
     if (dev < 0 || dev >= kMaxDevices) return QCS_ERR_UNSUPPORTED;
     DeviceSetup *d = nullptr;
-    if (int r = noalloc_setup(dev, d)) return r;
+    if (int r = noalloc_setup(dev, static_cast<cudaStream_t>(cuda_stream), d)) return r;
 
     // A stack handle: no workspace of its own, the caller's stream and
-    // tolerance, the size rule off (problems that fit the scratch are below
-    // the rule's 2048 threshold, so AUTO always selects from the
-    // statistics), the scratch's error word.
+    // tolerance, and the size rule off, so that AUTO selects from the
+    // statistics as qcs_cgemm does with the size rule off; the error word is
+    // the scratch's (sticky until qcs_cgemm_noalloc_status clears it).
     qcs_handle_s h;
     h.device = dev;
     h.num_sms = d->num_sms;
@@ -115,14 +117,44 @@ extern "C" int qcs_cgemm_noalloc(void *cuda_stream, qcs_mode_t mode, double unde
     const int eff = mode;
     if (kNoallocHeader + gemm_workspace_bytes(eff, m, n, k, d->num_sms, 0) > kNoallocBytes)
         return QCS_ERR_SCRATCH_TOO_SMALL;
-    // The error word must start at zero; everything else in the scratch is
-    // overwritten by the launches below before it is read.
-    if (cudaMemsetAsync(h.d_err, 0, sizeof(int), h.stream) != cudaSuccess) {
-        cudaGetLastError();
-        return QCS_ERR_CUDA;
-    }
+    // The error word was cleared at set-up and is only ever raised by a
+    // timed-out wait; everything else in the scratch is overwritten by the
+    // launches below before it is read.
     const float2 al = make_float2(alpha->x, alpha->y), be = make_float2(beta->x, beta->y);
     return run_cgemm(&h, d->scratch + kNoallocHeader, eff, transA, transB, m, n, k, al,
                      reinterpret_cast<const float2 *>(A), lda, reinterpret_cast<const float2 *>(B),
                      ldb, be, reinterpret_cast<float2 *>(C), ldc, d_desc_out, nullptr);
+}
+
+extern "C" int qcs_cgemm_noalloc_status(void *cuda_stream, int reset) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) return QCS_ERR_UNSUPPORTED;
+    unsigned char *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (g_setup[dev].ready) scratch = g_setup[dev].scratch;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    if (!scratch) return QCS_SUCCESS;  // no call has run on this device
+    int word = 0;
+    if (cudaMemcpy(&word, scratch, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    if (word != 0 && reset) {
+        if (cudaMemsetAsync(scratch, 0, sizeof(int), s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return QCS_ERR_CUDA;
+        }
+    }
+    return word != 0 ? QCS_ERR_TIMEOUT : QCS_SUCCESS;
 }

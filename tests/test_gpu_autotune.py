@@ -65,11 +65,11 @@ def test_autotune_prunes_and_picks():
         assert set(tiny["ms"]) == {"auto", "tf32x", "fp32"}
         assert all(v > 0 for v in tiny["ms"].values())
         assert tiny["best"] == "fp32"
-        big = hd.autotune_gemm(2048, 2048, 2048, reps=2)
+        big = hd.autotune_gemm(4096, 4096, 4096, reps=2)
         assert "fp32" not in big["ms"]
         assert big["best"] in ("auto", "tf32x")
         keys = [(e["m"], e["n"], e["k"]) for e in hd.tuning()]
-        assert keys == sorted(keys) and (8, 8, 8) in keys and (2048, 2048, 2048) in keys
+        assert keys == sorted(keys) and (8, 8, 8) in keys and (4096, 4096, 4096) in keys
     finally:
         hd.close()
 
