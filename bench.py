@@ -650,7 +650,7 @@ def main():
         leg("sgemm", lambda: sgemm_leg(args, q, torch, dev, rank))
 
     if not args.no_tree:
-        leg(None, lambda: tree_legs(args, q, torch, dev, rank))
+        leg(None, lambda: tree_legs(args, q, torch, dev, rank, world, dist))
 
     if rank == 0:
         emit_legs(legs, args.legs_file)
@@ -740,6 +740,10 @@ def legs_summary(legs: dict) -> dict:
                 co = d["cheapest_order"]
                 s["differentiation_4x5_d12"]["cheapest_order_auto_s"] = co.get("auto_s")
                 s["differentiation_4x5_d12"]["cheapest_order_fp32_s"] = co.get("fp32_s")
+    sh = legs.get("contraction_sharded")
+    if isinstance(sh, dict) and "error" not in sh:
+        s["contraction_5x6_d14_sharded"] = {k: sh.get(k) for k in
+                                            ("ranks", "s_per_slice", "amplitude_rel_err_vs_fp64")}
     p = legs.get("plain_small")
     if isinstance(p, dict) and "error" not in p:
         s["plain_3x4_d8"] = {"ms_per_64_bitstrings_graph": (p.get("s_per_batch_grouped_cuda_graph")
@@ -774,7 +778,8 @@ def contract_line(out: dict, legs: dict) -> dict:
     line = _sig(dict(out), 6)
     line["legs"] = legs_summary(legs)
     line["legs_detail"] = "one JSON line per leg on stderr (--legs-file writes them to a file)"
-    keep = ["contraction_5x6_d14", "precision_5x8_d12", "differentiation_4x5_d12", "sweep",
+    keep = ["contraction_5x6_d14", "contraction_5x6_d14_sharded", "precision_5x8_d12",
+            "differentiation_4x5_d12", "sweep",
             "contraction_5x6_d14_seed2_order", "plain_3x4_d8", "hbm_frac"]
     order = sorted(line["legs"], key=lambda k: -keep.index(k) if k in keep else -len(keep))
     while len(json.dumps(line)) > LINE_LIMIT and order:
@@ -1129,7 +1134,7 @@ def _contract_variants(args, q, tn, torch, dev, make_plan, ns, variants, full=Fa
     return res
 
 
-def tree_legs(args, q, torch, dev, rank):
+def tree_legs(args, q, torch, dev, rank, world=1, dist=None):
     """The contraction half of the metric (s/slice, AUTO vs all-FP32), the
     plain small-grid amplitudes and the differentiated workload."""
     import numpy as np
@@ -1190,6 +1195,8 @@ def tree_legs(args, q, torch, dev, rank):
         "speedup_vs_fp32": per["fp32"]["s_per_slice"] / per["auto"]["s_per_slice"],
         "speedup_vs_fp32_t0.5": per["fp32"]["s_per_slice"] / per["auto_t0.5"]["s_per_slice"],
     }
+    if world > 1:
+        res["contraction_sharded"] = sharded_leg(args, q, tn, torch, dev, p, ref, rank, world, dist)
     # the same network in the order of greedy seed 2 alone: 12x the flops per
     # slice, in larger GEMMs (the regime where one large GEMM dominates)
     order2 = tn.greedy_order(net, seed=2, skip=[tn.BATCH])
@@ -1298,6 +1305,44 @@ def tree_legs(args, q, torch, dev, rank):
             out4[f"{mode}_loss_rel_vs_fp64"] = abs(diff[mode]["loss"] - L_ref) / abs(L_ref)
     res["differentiation"] = out4
     res["precision_at_scale"] = scale_leg(args, q, torch, dev, tn, qi, rank)
+    return res
+
+
+def sharded_leg(args, q, tn, torch, dev, plan, ref, rank, world, dist):
+    """All 64 slices of the 30-qubit network split over the ranks (Section
+    5.3: slices are independent): rank r contracts instances r, r + world, ...
+    (tn.shard_plan) as one CUDA-graph replay, then one all-reduce of the
+    FP64 output slots (NCCL) gives every rank the amplitude.  Timed from a
+    barrier to the end of the all-reduce, max over ranks; seconds per slice
+    over all 64 slices; the amplitude against the FP64 state vector."""
+    sub = tn.shard_plan(plan, rank, world)
+    h = q.Handle(tol=args.tol, size_rule=q.SIZE_RULE_TUNED)
+    h.set_instance_batch(args.instance_batch)
+    cp = tn.CompiledPlan(sub, device=dev)
+    cp.autotune(h, reps=2)
+    g, out = cp.graph(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for timed in (False, True):
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0.record()
+        g.launch()
+        tn.allreduce_slots(out)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    amp = complex(out[0, 0].item())
+    g.close()
+    h.close()
+    res = {"workload": "5x6 grid, depth 14, 64 slices dealt round-robin over %d ranks, AUTO-%g "
+                       "(measured size rule), one graph replay per rank + NCCL all-reduce of the "
+                       "FP64 slots" % (world, args.tol),
+           "ranks": world, "slices_per_rank": int(sub.n_instances),
+           "s_per_slice": float(t.item()) * 1e-3 / plan.n_instances}
+    if ref is not None:
+        res["amplitude_rel_err_vs_fp64"] = abs(amp - ref) / abs(ref)
     return res
 
 

@@ -1282,6 +1282,156 @@ __global__ void __launch_bounds__(256, SPLIT ? 4 : 5) copy_tiled_kernel(CopyPara
     }
 }
 
+// The split through a gather map with quads: the same tiles as
+// copy_tiled_kernel<true>, kept in shared memory as tile[y][x], and each
+// thread writes one run of four consecutive output elements per tile, so
+// that every plane gets one 8-byte (16-bit kinds) or 16-byte (TF32) store
+// per four elements.  Needs the output-contiguous run X to be a multiple of
+// 4 elements long and every other output stride, the operand's plane offset
+// and the plane stride to be multiples of 4 (split_quads_ok).  The kind of
+// the low-precision type is read from the descriptor once per block.
+constexpr int kQuadStages = 4;  // tiles in the cp.async ring: three in flight while one is written
+
+template <int KIND, bool P5>
+__device__ __forceinline__ void split_quads_body(const CopyParams &P, const float2 *__restrict__ in,
+                                                 const SplitOut &so, const Pow2Scale &pscale,
+                                                 float2 (*tile)[32][33], const int64_t *sxi,
+                                                 const int64_t *sxo, const int64_t *syi,
+                                                 const int64_t *syo, const int64_t (*sr)[2],
+                                                 int64_t x0, int64_t y0, int nt) {
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // read: lanes along y
+    const int xq = threadIdx.x & 7, yq = threadIdx.x >> 3;   // write: a quad of x per thread
+    int64_t rin[4];
+    bool okin[4];
+    const bool yok = (y0 + tx) < P.py;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int l = ty + 8 * r;
+        rin[r] = sxi[l] + syi[tx];
+        okin[r] = yok && x0 + l < P.px;
+    }
+    const bool okout = (x0 + 4 * xq < P.px) && (y0 + yq < P.py);
+    const int64_t rout = sxo[4 * xq] + syo[yq];
+    const int64_t ps = so.plane_stride;
+    // tile t -> ring slot t % kQuadStages, transposed on the way in
+    // (tile[slot][y][x]); elements outside the tensor are zero-filled
+    auto load = [&](int t) {
+        const int64_t ri = sr[t][0];
+        const int buf = t % kQuadStages;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            cp_async8(&tile[buf][tx][ty + 8 * r], okin[r] ? in + ri + rin[r] : in, okin[r] ? 8u : 0u);
+    };
+#pragma unroll
+    for (int t = 0; t < kQuadStages - 1; ++t) {
+        if (t < nt) load(t);
+        cp_async_commit();
+    }
+    for (int t = 0; t < nt; ++t) {
+        const int buf = t % kQuadStages;
+        cp_async_wait<kQuadStages - 2>();  // this thread's copies of tile t have landed
+        __syncthreads();  // everyone's have; and slot (t - 1) % kQuadStages is no longer read
+        if (t + kQuadStages - 1 < nt) load(t + kQuadStages - 1);
+        cp_async_commit();
+        if (okout) {
+            uint32_t h[2][4], lo[2][4];  // [re | im][element of the quad]
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 w = tile[buf][yq][4 * xq + e];
+                split_value(KIND == 1 ? QCS_MODE_TF32X : (KIND == 2 ? QCS_MODE_BF16X3 : QCS_MODE_FP16X),
+                            apply_scale(w.x, pscale), h[0][e], lo[0][e]);
+                split_value(KIND == 1 ? QCS_MODE_TF32X : (KIND == 2 ? QCS_MODE_BF16X3 : QCS_MODE_FP16X),
+                            apply_scale(w.y, pscale), h[1][e], lo[1][e]);
+            }
+            const int64_t o = so.off + sr[t][1] + rout;
+            // plane order: P5 -hi.im, hi.re, hi.im, lo.re, lo.im; else hi.re, hi.im, lo.re, lo.im
+            constexpr int NP = P5 ? 5 : 4;
+            if (KIND == 1) {
+                uint4 *p0 = reinterpret_cast<uint4 *>(static_cast<uint32_t *>(
+                                so.planes32 ? so.planes32 : so.planes) + o);
+                const int64_t step = ps / 4;  // plane stride in uint4
+                uint4 q[NP];
+                int k = 0;
+                if (P5)
+                    q[k++] = make_uint4(h[1][0] ^ 0x80000000u, h[1][1] ^ 0x80000000u,
+                                        h[1][2] ^ 0x80000000u, h[1][3] ^ 0x80000000u);
+                q[k++] = make_uint4(h[0][0], h[0][1], h[0][2], h[0][3]);
+                q[k++] = make_uint4(h[1][0], h[1][1], h[1][2], h[1][3]);
+                q[k++] = make_uint4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
+                q[k++] = make_uint4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
+#pragma unroll
+                for (int pl = 0; pl < NP; ++pl) p0[pl * step] = q[pl];
+            } else {
+                uint2 *p0 = reinterpret_cast<uint2 *>(static_cast<uint16_t *>(so.planes) + o);
+                const int64_t step = ps / 4;  // plane stride in uint2 (four 16-bit values)
+                auto pack = [](const uint32_t (&x)[4], uint32_t flip) {
+                    return make_uint2(((x[0] ^ flip) & 0xFFFFu) | ((x[1] ^ flip) << 16),
+                                      ((x[2] ^ flip) & 0xFFFFu) | ((x[3] ^ flip) << 16));
+                };
+                uint2 q[NP];
+                int k = 0;
+                if (P5) q[k++] = pack(h[1], 0x8000u);
+                q[k++] = pack(h[0], 0u);
+                q[k++] = pack(h[1], 0u);
+                q[k++] = pack(lo[0], 0u);
+                q[k++] = pack(lo[1], 0u);
+#pragma unroll
+                for (int pl = 0; pl < NP; ++pl) p0[pl * step] = q[pl];
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
+constexpr int kQuadMaxTiles = 64;  // tiles (rest indices) per block, at most
+
+template <bool P5>
+__global__ void __launch_bounds__(256, 4) split_quads_kernel(CopyParams P,
+                                                             const float2 *__restrict__ in,
+                                                             SplitOut so, int tpb) {
+    const int mode = so.desc->mode;
+    if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
+    const int scale =
+        (mode == QCS_MODE_FP16X_SCALED) ? (so.which == 0 ? so.desc->sA : so.desc->sB) : 0;
+    const Pow2Scale pscale = pow2_scale(scale);
+    __shared__ __align__(16) float2 tile[kQuadStages][32][33];
+    __shared__ int64_t sxi[32], sxo[32], syi[32], syo[32], sr[kQuadMaxTiles][2];
+    in += batch_in(P);
+    int64_t b = blockIdx.x;
+    const int64_t bx = b % P.tiles_x;
+    b /= P.tiles_x;
+    const int64_t by = b % P.tiles_y;
+    const int64_t rb = (b / P.tiles_y) * tpb;  // first rest index of this block
+    const int64_t x0 = bx * 32, y0 = by * 32;
+    if (threadIdx.x < 32) {
+        const int64_t x = x0 + threadIdx.x;
+        int64_t io = 0, oo = 0;
+        if (x < P.px) decompose(P, P.gx, P.nx, x, io, oo);
+        sxi[threadIdx.x] = io;
+        sxo[threadIdx.x] = oo;
+    } else if (threadIdx.x < 64) {
+        const int64_t y = y0 + threadIdx.x - 32;
+        int64_t io = 0, oo = 0;
+        if (y < P.py) decompose(P, P.gy, P.ny, y, io, oo);
+        syi[threadIdx.x - 32] = io;
+        syo[threadIdx.x - 32] = oo;
+    } else if (threadIdx.x < 64 + kQuadMaxTiles) {
+        const int t = threadIdx.x - 64;
+        int64_t io = 0, oo = 0;
+        if (t < tpb && rb + t < P.rest) decompose(P, P.gr, P.nr, rb + t, io, oo);
+        sr[t][0] = io;
+        sr[t][1] = oo;
+    }
+    __syncthreads();
+    const int nt = (int)min((int64_t)tpb, P.rest - rb);
+    if (mode == QCS_MODE_TF32X)
+        split_quads_body<1, P5>(P, in, so, pscale, tile, sxi, sxo, syi, syo, sr, x0, y0, nt);
+    else if (mode == QCS_MODE_BF16X3)
+        split_quads_body<2, P5>(P, in, so, pscale, tile, sxi, sxo, syi, syo, sr, x0, y0, nt);
+    else
+        split_quads_body<0, P5>(P, in, so, pscale, tile, sxi, sxo, syi, syo, sr, x0, y0, nt);
+}
+
 // Shared contiguous prefix (dims 0..nv-1 contiguous from stride 1 in both
 // input and output, product pv): one block per ``per_block`` outer indices,
 // threads copy the contiguous runs.
@@ -1521,7 +1671,35 @@ cudaError_t launch_split_gather(const qcs_gemm_desc_t *desc, int which, int rank
     if (blocks == 0) return cudaSuccess;
     if (blocks > INT32_MAX) return cudaErrorInvalidValue;
     SplitOut so{desc, which, planes, plane_stride, planes6, plane_off, planes32};
-    copy_tiled_kernel<true><<<dim3((unsigned)blocks, 1), 256, 0, s>>>(P, src, nullptr, 0, so);
+    // quads: every output run of four elements lies inside the X run and
+    // starts at a multiple of 4 in every plane
+    bool quads = P.px % 4 == 0 && plane_off % 4 == 0 && plane_stride % 4 == 0;
+    for (int d = 0; d < P.rank && quads; ++d) {
+        bool in_x = false;
+        for (int a = 0; a < P.nx; ++a) in_x |= (P.gx[a] == d);
+        if (!in_x && P.os[d] % 4 != 0) quads = false;
+    }
+    if (quads) {
+        // tiles per block: as many as make the grid a whole number of waves
+        // (4 blocks of 256 threads per SM), at most kQuadMaxTiles
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return cudaGetLastError();
+        const int64_t xy = P.tiles_x * P.tiles_y, wave = 4 * (int64_t)sms;
+        const int64_t min_blocks = xy * ((P.rest + kQuadMaxTiles - 1) / kQuadMaxTiles);
+        const int64_t want = ((min_blocks + wave - 1) / wave) * wave;
+        const int64_t chunks = std::max<int64_t>(1, want / xy);
+        const int tpb = (int)std::min<int64_t>(kQuadMaxTiles, (P.rest + chunks - 1) / chunks);
+        const int64_t qblocks = xy * ((P.rest + tpb - 1) / tpb);
+        if (qblocks > INT32_MAX) return cudaErrorInvalidValue;
+        if (planes6)
+            split_quads_kernel<true><<<dim3((unsigned)qblocks, 1), 256, 0, s>>>(P, src, so, tpb);
+        else
+            split_quads_kernel<false><<<dim3((unsigned)qblocks, 1), 256, 0, s>>>(P, src, so, tpb);
+    } else {
+        copy_tiled_kernel<true><<<dim3((unsigned)blocks, 1), 256, 0, s>>>(P, src, nullptr, 0, so);
+    }
     return cudaGetLastError();
 }
 

@@ -532,7 +532,10 @@ class CompiledPlan:
         import torch
 
         leaves = [t.contiguous() for t in (self.leaves if leaves is None else leaves)]
-        grads = [torch.zeros_like(t) for t in leaves]
+        # every leaf gradient is a slice of one zeroed buffer (one memset)
+        sizes = [t.numel() for t in leaves]
+        grads = list(torch.zeros(sum(sizes), dtype=torch.complex64,
+                                 device=self.device).split(sizes))
         g = grad_out.to(torch.complex128).contiguous()
         info = _lib.qcs_run_info_t()
         _lib.check(h.lib.qcs_contract_tree_backward(
@@ -592,39 +595,47 @@ def info_dict(info) -> dict:
 # differentiation: torch.autograd.Function over qcs_contract_tree
 # ---------------------------------------------------------------------------
 
-def _torch_fsim_leaf(theta, phi):
-    """First-index-fastest flat complex64 fSim(theta, phi) tensor, built with
-    torch ops so that autograd reaches theta and phi."""
+def _torch_fsim_leaves(theta, phi):
+    """First-index-fastest flat complex64 fSim(theta_g, phi_g) tensors, one row
+    per gate (shape (n, 16)), built with a handful of batched torch ops so
+    that autograd reaches theta and phi."""
     import torch
 
     c = torch.cos(theta).to(torch.complex64)
     s = torch.sin(theta).to(torch.complex64)
     e = torch.exp(-1j * phi.to(torch.complex64))
-    one = torch.ones((), dtype=torch.complex64, device=theta.device)
-    zero = torch.zeros((), dtype=torch.complex64, device=theta.device)
-    G = torch.stack([
-        torch.stack([one, zero, zero, zero]),
-        torch.stack([zero, c, -1j * s, zero]),
-        torch.stack([zero, -1j * s, c, zero]),
-        torch.stack([zero, zero, zero, e]),
-    ])
-    return G.reshape(2, 2, 2, 2).permute(3, 2, 1, 0).reshape(-1)
+    one = torch.ones_like(c)
+    zero = torch.zeros_like(c)
+    G = torch.stack([one, zero, zero, zero,
+                     zero, c, -1j * s, zero,
+                     zero, -1j * s, c, zero,
+                     zero, zero, zero, e], dim=-1)  # (n, 16): row-major 4 x 4
+    return G.reshape(-1, 2, 2, 2, 2).permute(0, 4, 3, 2, 1).reshape(-1, 16)
 
 
 def torch_leaves(net: Network, circ, params, device="cuda"):
     """Device leaf tensors of ``net``; the fSim leaves are functions of
     ``params`` ((n_fsim, 2) real tensor: theta, phi per fSim gate in circuit
-    order), every other leaf is constant."""
+    order), every other leaf is constant.  The fSim leaves come from one
+    batched evaluation (rows of one tensor), the constant ones from one
+    host-to-device copy."""
     import torch
 
     fs = {g: i for i, g in enumerate(circ.fsim_indices())}
-    out = []
-    for lf in net.leaves:
-        if lf.kind == "gate" and lf.gate in fs:
-            p = params[fs[lf.gate]]
-            out.append(_torch_fsim_leaf(p[0], p[1]).to(device))
-        else:
-            out.append(torch.from_numpy(lf.data).to(device))
+    var = [i for i, lf in enumerate(net.leaves) if lf.kind == "gate" and lf.gate in fs]
+    const = [i for i in range(len(net.leaves)) if i not in set(var)]
+    out = [None] * len(net.leaves)
+    if var:
+        rows = torch.tensor([fs[net.leaves[i].gate] for i in var], device=params.device)
+        P = params[rows].to(device)
+        for i, t in zip(var, _torch_fsim_leaves(P[:, 0], P[:, 1]).unbind(0)):
+            out[i] = t
+    if const:
+        flat = np.concatenate([net.leaves[i].data.ravel() for i in const]).astype(np.complex64)
+        dev = torch.from_numpy(flat).to(device)
+        sizes = [net.leaves[i].data.size for i in const]
+        for i, t in zip(const, dev.split(sizes)):
+            out[i] = t
     return out
 
 
@@ -708,3 +719,21 @@ def allreduce_slots(out, group=None):
 
     dist.all_reduce(torch.view_as_real(out), op=dist.ReduceOp.SUM, group=group)
     return out
+
+
+def allreduce_leaf_grads(grads, group=None):
+    """Sum leaf gradients (complex tensors, e.g. from CompiledPlan.backward on
+    a shard of the instances) over the ranks of ``group`` in place: every
+    rank then holds the gradient of the whole plan.  One collective over one
+    packed buffer."""
+    import torch
+    import torch.distributed as dist
+
+    flat = torch.cat([torch.view_as_real(g).reshape(-1) for g in grads])
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+    off = 0
+    for g in grads:
+        n = 2 * g.numel()
+        torch.view_as_real(g).reshape(-1).copy_(flat[off:off + n])
+        off += n
+    return grads

@@ -379,7 +379,7 @@ def test_instance_groups_with_direct_and_split_k_steps():
     assert oracle.fidelity(ref, one[:, 0]) >= 1 - 1e-5
 
 
-@pytest.mark.parametrize("mode", ["fp16x", "tf32x", "auto"])
+@pytest.mark.parametrize("mode", ["fp16x", "tf32x", "auto", "bf16x3", "fp16x_scaled"])
 def test_split_through_the_map_equals_gather_then_split(mode):
     """An emulated step whose operand is a permuted intermediate is split
     straight from the intermediate through its gather map (no gather pass;
