@@ -195,11 +195,24 @@ TC_SOURCES = ["paper_2303_08989_gb300/csrc/gemm_tc.cu", "paper_2303_08989_gb300/
 TC_TRAFFIC_PROFILE = "profiles/cgemm_tc_fp16x_16384_dram.md"
 
 
+TC_CONSTANTS = ("kBM", "kBN", "kRowBytes", "kStages", "kPlanes", "kPlanesB", "kTileBytes",
+                "kAStageBytes", "kBStageBytes", "kTcThreads", "kTmemCols")
+
+
 def tc_sources_sha256() -> str:
+    """SHA-256 of what the tensor-core kernel's DRAM traffic depends on: its
+    source, its PTX wrappers and the tile constants it takes from the
+    internal header (the header's other declarations do not count)."""
+    import re
+
     h = hashlib.sha256()
     for rel in TC_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+            data = f.read()
+        if rel.endswith("internal.h"):
+            pat = re.compile(r"^constexpr\s+\w+\s+(%s)\s*=.*$" % "|".join(TC_CONSTANTS))
+            data = "\n".join(ln for ln in data.decode().splitlines() if pat.match(ln)).encode()
+        h.update(data)
     return h.hexdigest()
 
 

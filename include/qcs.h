@@ -168,6 +168,20 @@ int qcs_set_tc_splits(qcs_handle_t h, int splits);
  * Returns QCS_ERR_INVALID_ARG for other values. */
 int qcs_set_complex_products(qcs_handle_t h, int products);
 
+/* Where the Eq. 1 split of a TF32X selection runs (Section 2.1).  0
+ * (default): a separate pass writes the hi / lo TF32 planes of op(A) and
+ * op(B) to the handle's workspace in HBM and the tensor-core kernel reads
+ * them back.  1: the tensor-core kernel reads A and B as stored and its
+ * epilogue warps split each staged tile in shared memory between their
+ * accumulator drains, so the planes never leave the SM; the MMAs and their
+ * order are the same, so the result is bit-identical.  Applies to qcs_cgemm
+ * calls whose mode (after the size rule) is TF32X or AUTO, on matrices (not
+ * gather views of the contraction tree), when the tensor-core GEMM runs as
+ * one K range with the default drain of 4 stages and the TMA limits hold
+ * (lda, ldb even; A, B 16-byte aligned); other calls keep the separate
+ * pass.  Environment override QCS_FUSED_SPLIT. */
+int qcs_set_fused_split(qcs_handle_t h, int enabled);
+
 /* Failure detection (not a step of the paper).  Every wait inside the
  * tensor-core kernels (a TMA stage landing, the MMAs freeing a stage, the
  * epilogue draining an accumulator) gives up after ``ns`` nanoseconds of the

@@ -174,6 +174,12 @@ class Handle:
         _lib.check(self.lib.qcs_set_complex_products(self._h, int(products)),
                    "qcs_set_complex_products")
 
+    def set_fused_split(self, enabled: bool):
+        """TF32X split inside the tensor-core kernel's staging
+        (qcs_set_fused_split) instead of a separate pass."""
+        _lib.check(self.lib.qcs_set_fused_split(self._h, int(bool(enabled))),
+                   "qcs_set_fused_split")
+
     def set_wait_budget(self, ns: int):
         """Bound of every device-side wait in the tensor-core kernels
         (qcs_set_wait_budget), in nanoseconds."""

@@ -36,6 +36,7 @@ EXPORTED = [
     "qcs_get_tuning", "qcs_set_tuning", "qcs_set_instance_batch", "qcs_set_tc_schedule",
     "qcs_set_tc_splits", "qcs_sgemm", "qcs_set_complex_products", "qcs_set_wait_budget",
     "qcs_debug_stall_producer", "qcs_cgemm_noalloc_status", "qcs_measure_fma_peak",
+    "qcs_set_fused_split",
 ]
 SIZE_RULE_OFF, SIZE_RULE_PAPER, SIZE_RULE_TUNED = 0, 1, 2
 NUM_MODES = 6
@@ -158,6 +159,7 @@ def load(path: str = LIB_PATH):
         "qcs_debug_stall_producer": [H, I],
         "qcs_cgemm_noalloc_status": [P, I],
         "qcs_measure_fma_peak": [H, ctypes.POINTER(ctypes.c_double)],
+        "qcs_set_fused_split": [H, I],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

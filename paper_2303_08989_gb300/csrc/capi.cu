@@ -296,6 +296,13 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                         split_gather_supported(0, A0.map->rank, A0.map->dims, A0.map->strides, m, kp);
     const bool fusedB = B0.map && B0.flat > 0 && emulated && np == n && kp == k &&
                         split_gather_supported(1, B0.map->rank, B0.map->dims, B0.map->strides, k, kp);
+    // TF32 selection split inside the tensor-core kernel (qcs_set_fused_split):
+    // one GEMM on matrices as stored, one K range, the default drain
+    const bool tf32_fused =
+        h->fused_split && emulated && G == 1 && bt.count == 1 && !A0.map && !B0.map &&
+        (eff == QCS_MODE_TF32X || eff == QCS_MODE_AUTO) && h->drain_stages == 4 &&
+        tc_split_count(m, n, k, 1, h->num_sms, gemm_splits(h, opA, opB, m, n, k)) == 1 &&
+        tc_fused_supported(opA, opB, m, n, k, A0.X, A0.ld, B0.X, B0.ld);
 
     // The per-instance front of the sequence: gathers, statistics and
     // selection (or the constant descriptor), the split of both operands.
@@ -347,7 +354,7 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
             e = launch_set_desc(dg, eff, s);
             if (e != cudaSuccess) return QCS_ERR_CUDA;
         }
-        if (!emulated) continue;
+        if (!emulated || (tf32_fused && eff == QCS_MODE_TF32X)) continue;
         // The split writes with the selected kind's element size; the pitch
         // is kp elements either way, so both tensor maps below describe it.
         // Instance g owns rows [g R_pad, (g + 1) R_pad) of every plane.
@@ -359,7 +366,7 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
         } else {
             plane_strides(0, opA, A.ld, sr, sc);
             e = launch_split(dg, 0, A.X, sr, sc, opA == QCS_OP_C, m, k, mp, kp, planesA, kp,
-                             G * mp * kp, s, 0, g * mp * kp, sepA32);
+                             G * mp * kp, s, 0, g * mp * kp, sepA32, tf32_fused ? 1 : 0);
         }
         if (e == cudaSuccess) {
             if (fusedB) {
@@ -368,7 +375,7 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
             } else {
                 plane_strides(1, opB, B.ld, sr, sc);
                 e = launch_split(dg, 1, B.X, sr, sc, opB == QCS_OP_C, n, k, np, kp, planesB, kp,
-                                 G * np * kp, s, 1, g * np * kp, sepB32);
+                                 G * np * kp, s, 1, g * np * kp, sepB32, tf32_fused ? 1 : 0);
             }
         }
         if (e != cudaSuccess) return QCS_ERR_CUDA;
@@ -393,7 +400,12 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                                     ldc, h->d_err, h->num_sms, h->tc_group_m, s, w);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             }
-            if (need32) {
+            if (need32 && tf32_fused) {
+                e = launch_cgemm_tc_fused(h->encode, desc, opA, opB, m, n, k, alpha, A0.X, A0.ld,
+                                          B0.X, B0.ld, beta, C, ldc, h->d_err, h->num_sms,
+                                          h->tc_group_m, w, s);
+                if (e != cudaSuccess) return QCS_ERR_CUDA;
+            } else if (need32) {
                 CUtensorMap ma, mb;
                 if (encode_planes(h, &ma, planesA32, G * mp, kp, 4, kPlanes) ||
                     encode_planes(h, &mb, planesB32, G * np, kp, 4, kPlanesB))
@@ -760,6 +772,7 @@ int qcs_create(qcs_handle_t *out, void *cuda_stream) {
     if (const char *p = std::getenv("QCS_TC_L2_PROMOTION")) h->tc_l2_promotion = std::atoi(p);
     if (const char *c = std::getenv("QCS_COMPLEX_PRODUCTS"))
         h->complex_products = (std::atoi(c) == 3) ? 3 : 4;
+    if (const char *f = std::getenv("QCS_FUSED_SPLIT")) h->fused_split = std::atoi(f) != 0;
     if (const char *k = std::getenv("QCS_TC_SPLITS"))
         h->tc_splits = std::min(kMaxSplits, std::max(0, std::atoi(k)));
     if (const char *d = std::getenv("QCS_DRAIN_STAGES")) {
@@ -821,6 +834,12 @@ int qcs_set_tc_splits(qcs_handle_t h, int splits) {
 int qcs_set_complex_products(qcs_handle_t h, int products) {
     if (!h || (products != 3 && products != 4)) return QCS_ERR_INVALID_ARG;
     h->complex_products = products;
+    return QCS_SUCCESS;
+}
+
+int qcs_set_fused_split(qcs_handle_t h, int enabled) {
+    if (!h) return QCS_ERR_INVALID_ARG;
+    h->fused_split = enabled ? 1 : 0;
     return QCS_SUCCESS;
 }
 

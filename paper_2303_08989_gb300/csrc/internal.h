@@ -95,6 +95,7 @@ struct qcs_handle_s {
     int tc_l2_promotion = 256;       // L2 promotion of the plane loads (bytes; 0 = none)
     int tc_splits = 0;               // K ranges per tensor-core GEMM (0 = chosen per shape)
     int complex_products = 4;        // real products per emulated complex product (4, or 3: Gauss)
+    int fused_split = 0;             // TF32X: split inside the tensor-core kernel's staging
     uint64_t wait_ns = qcs::kWaitBudgetNs;  // bound of the tensor-core kernels' device waits
     int debug_stall = 0;             // test hook: the TMA producer issues no loads
     int *d_err = nullptr;            // device error word (start of a 64-byte block)
@@ -183,11 +184,13 @@ cudaError_t launch_set_desc(qcs_gemm_desc_t *desc, int mode, cudaStream_t s);
 // after those of instances 0 .. g-1); elements are those of the kind the
 // descriptor selected.  planes32 (not NULL): where a TF32 selection writes
 // instead of ``planes`` -- a group whose instances may select different
-// kinds keeps the 2-byte and 4-byte planes in separate regions.
+// kinds keeps the 2-byte and 4-byte planes in separate regions.  skip_tf32:
+// write nothing for a TF32 selection (the fused TF32X kernel splits itself).
 cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
                          int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
                          void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
-                         int planes6 = 0, int64_t plane_off = 0, void *planes32 = nullptr);
+                         int planes6 = 0, int64_t plane_off = 0, void *planes32 = nullptr,
+                         int skip_tf32 = 0);
 
 // The split stage reading its operand through a gather map (the reshape of
 // a contraction folded into the split pass): op(X) is the rows x cols
@@ -306,6 +309,18 @@ constexpr int kMaxSplits = 16;
 // ``real``: the real kernel's 128 x 256 tiles and 4-byte outputs.
 int tc_split_count(int64_t m, int64_t n, int64_t k, int64_t G, int num_sms, int forced,
                    bool real = false);
+
+// TF32X CGEMM with the Eq. 1 split in the tensor-core kernel's staging: the
+// kernel reads A and B as stored (op N / T / C), one GEMM, one K range; it
+// runs only if desc->mode is TF32X.  tc_fused_supported: the TMA limits
+// (even lda, ldb; 16-byte aligned A, B; sizes within int).
+bool tc_fused_supported(int opA, int opB, int64_t m, int64_t n, int64_t k, const float2 *A,
+                        int64_t lda, const float2 *B, int64_t ldb);
+cudaError_t launch_cgemm_tc_fused(EncodeTiledFn encode, const qcs_gemm_desc_t *desc, int opA,
+                                  int opB, int64_t m, int64_t n, int64_t k, float2 alpha,
+                                  const float2 *A, int64_t lda, const float2 *B, int64_t ldb,
+                                  float2 beta, float2 *C, int64_t ldc, int *d_err, int num_sms,
+                                  int group_m, const TcWork &w, cudaStream_t s);
 
 // Tensor-core emulated CGEMM over split planes.  ``kind``: 0 FP16 (modes
 // FP16X, FP16X_SCALED), 1 TF32, 2 BF16; the kernel returns at once unless

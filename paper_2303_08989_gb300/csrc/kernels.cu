@@ -614,12 +614,6 @@ namespace {
 
 constexpr int kSplitR = 32, kSplitC = 64;
 
-__device__ __forceinline__ uint32_t tf32_rn(float x) {
-    uint32_t r;
-    asm("cvt.rn.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r & 0xFFFFE000u;
-}
-
 // Eq. 1 for one scaled value xs: hi = toLow(xs), lo = toLow((xs - hi) 2^11),
 // as bit patterns of the mode's low-precision type.
 __device__ __forceinline__ void split_value(int mode, float xs, uint32_t &hi, uint32_t &lo) {
@@ -660,9 +654,11 @@ __device__ __forceinline__ float apply_scale(float x, Pow2Scale p) { return (x *
 __global__ void __launch_bounds__(256, 8) split_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int which, const float2 *__restrict__ X, int64_t sr,
     int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad, void *planes,
-    int64_t pitch, int64_t plane_stride, int planes6, int64_t plane_off, void *planes32) {
+    int64_t pitch, int64_t plane_stride, int planes6, int64_t plane_off, void *planes32,
+    int skip_tf32) {
     const int mode = desc->mode;
-    if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
+    if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO || (skip_tf32 && mode == QCS_MODE_TF32X))
+        return;
     const int s = (mode == QCS_MODE_FP16X_SCALED) ? (which == 0 ? desc->sA : desc->sB) : 0;
     const Pow2Scale ps2 = pow2_scale(s);
 
@@ -771,12 +767,12 @@ __global__ void __launch_bounds__(256, 8) split_kernel(
 cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
                          int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
                          void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
-                         int planes6, int64_t plane_off, void *planes32) {
+                         int planes6, int64_t plane_off, void *planes32, int skip_tf32) {
     if (R_pad <= 0 || K_pad <= 0) return cudaSuccess;
     dim3 grid((unsigned)((K_pad + kSplitC - 1) / kSplitC), (unsigned)((R_pad + kSplitR - 1) / kSplitR));
     if (grid.y > 65535u) return cudaErrorInvalidValue;
     split_kernel<<<grid, 256, 0, s>>>(desc, which, X, sr, sc, conj, R, K, R_pad, K_pad, planes,
-                                      pitch, plane_stride, planes6, plane_off, planes32);
+                                      pitch, plane_stride, planes6, plane_off, planes32, skip_tf32);
     return cudaGetLastError();
 }
 
