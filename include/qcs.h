@@ -168,6 +168,30 @@ int qcs_set_tc_splits(qcs_handle_t h, int splits);
  * Returns QCS_ERR_INVALID_ARG for other values. */
 int qcs_set_complex_products(qcs_handle_t h, int products);
 
+/* The counts of Section 4.1 that AUTO's selection takes for one GEMM, as the
+ * GEMM path computes them (pass 1: e_max, zeros, Inf/NaN, the count below
+ * FP16's least normal 2^-14, i.e. N - N1; pass 2, only when pass 1 does not
+ * decide: the count below the window [e_max - 28, e_max] that scaling by
+ * 2^(14 - e_max) keeps, i.e. N - N2).  Real and imaginary parts count as
+ * separate scalars; zeros are in neither count nor total. */
+typedef struct {
+    int32_t e_max;          /* largest exponent floor(log2|x|) of a finite nonzero scalar; -128 if none */
+    int32_t stage2;         /* 1 if the pass-2 count was taken */
+    int64_t n_nonzero;      /* finite nonzero scalars */
+    int64_t n_nonfinite;    /* Inf / NaN scalars */
+    int64_t n_under_fp16;   /* finite nonzero scalars with exponent < -14 (subnormals included) */
+    int64_t n_under_window; /* finite nonzero scalars below 2^(e_max - 28); 0 unless stage2 */
+} qcs_selection_stats_t;
+
+/* Run the statistics and selection of an AUTO qcs_cgemm of op(A) (m x k) and
+ * op(B) (k x n) -- the same kernels, the handle's tolerance, no size rule --
+ * and return their counts for op(A) in out[0] and op(B) in out[1] (host)
+ * and the descriptor the selection wrote in *desc_out (host, optional).
+ * Arguments as qcs_cgemm (m, n, k >= 1).  Synchronizes the handle's stream. */
+int qcs_selection_stats(qcs_handle_t h, qcs_op_t transA, qcs_op_t transB, int64_t m, int64_t n,
+                        int64_t k, const qcs_c32 *A, int64_t lda, const qcs_c32 *B, int64_t ldb,
+                        qcs_selection_stats_t *out, qcs_gemm_desc_t *desc_out);
+
 /* Where the Eq. 1 split of a TF32X selection runs (Section 2.1).  0
  * (default): a separate pass writes the hi / lo TF32 planes of op(A) and
  * op(B) to the handle's workspace in HBM and the tensor-core kernel reads

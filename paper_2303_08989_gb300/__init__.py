@@ -268,6 +268,30 @@ def cgemm(h: Handle, A, B, C=None, *, m=None, n=None, k=None, alpha=1.0, beta=0.
     return C
 
 
+def selection_stats(h: Handle, A, B, *, opA=OP_N, opB=OP_N):
+    """The Section 4.1 counts AUTO's selection takes for op(A) op(B)
+    (qcs_selection_stats): a list of two dicts (op(A), op(B)) with e_max
+    (None if no finite nonzero scalar), stage2, n_nonzero, n_nonfinite,
+    n_under_fp16, n_under_window, and the descriptor (mode, sA, sB)."""
+    rA, cA = A.shape
+    rB, cB = B.shape
+    m = rA if opA == OP_N else cA
+    k = cA if opA == OP_N else rA
+    n = cB if opB == OP_N else rB
+    out = (_lib.qcs_selection_stats_t * 2)()
+    d = _lib.qcs_gemm_desc_t()
+    _lib.check(h.lib.qcs_selection_stats(h.ptr, int(opA), int(opB), m, n, k,
+                                         ctypes.c_void_p(A.data_ptr()), _ld(A, rA),
+                                         ctypes.c_void_p(B.data_ptr()), _ld(B, rB), out,
+                                         ctypes.byref(d)), "qcs_selection_stats")
+    res = []
+    for o in out:
+        res.append({"e_max": None if o.e_max == -128 else int(o.e_max), "stage2": bool(o.stage2),
+                    "n_nonzero": int(o.n_nonzero), "n_nonfinite": int(o.n_nonfinite),
+                    "n_under_fp16": int(o.n_under_fp16), "n_under_window": int(o.n_under_window)})
+    return res, (int(d.mode), int(d.sA), int(d.sB))
+
+
 def sgemm(h: Handle, A, B, C=None, *, m=None, n=None, k=None, alpha=1.0, beta=0.0,
           opA=OP_N, opB=OP_N, mode="auto", desc_out=None):
     """C = alpha op(A) op(B) + beta C for real matrices with qcs_sgemm;

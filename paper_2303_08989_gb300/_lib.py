@@ -36,7 +36,7 @@ EXPORTED = [
     "qcs_get_tuning", "qcs_set_tuning", "qcs_set_instance_batch", "qcs_set_tc_schedule",
     "qcs_set_tc_splits", "qcs_sgemm", "qcs_set_complex_products", "qcs_set_wait_budget",
     "qcs_debug_stall_producer", "qcs_cgemm_noalloc_status", "qcs_measure_fma_peak",
-    "qcs_set_fused_split",
+    "qcs_set_fused_split", "qcs_selection_stats",
 ]
 SIZE_RULE_OFF, SIZE_RULE_PAPER, SIZE_RULE_TUNED = 0, 1, 2
 NUM_MODES = 6
@@ -63,6 +63,12 @@ class qcs_gemm_desc_t(ctypes.Structure):
 
 
 MAX_RANK = 32
+
+
+class qcs_selection_stats_t(ctypes.Structure):
+    _fields_ = [("e_max", ctypes.c_int32), ("stage2", ctypes.c_int32),
+                ("n_nonzero", ctypes.c_int64), ("n_nonfinite", ctypes.c_int64),
+                ("n_under_fp16", ctypes.c_int64), ("n_under_window", ctypes.c_int64)]
 
 
 class qcs_tune_entry_t(ctypes.Structure):
@@ -160,6 +166,8 @@ def load(path: str = LIB_PATH):
         "qcs_cgemm_noalloc_status": [P, I],
         "qcs_measure_fma_peak": [H, ctypes.POINTER(ctypes.c_double)],
         "qcs_set_fused_split": [H, I],
+        "qcs_selection_stats": [H, I, I, I64, I64, I64, P, I64, P, I64,
+                                ctypes.POINTER(qcs_selection_stats_t), ctypes.POINTER(qcs_gemm_desc_t)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

@@ -87,13 +87,17 @@ int stats_blocks(int64_t nel, int num_sms) {
     return static_cast<int>(g);
 }
 
+}  // namespace
+
 // Blocks of the two-stage statistics for ``nel`` complex values: up to four
 // 256-thread blocks per SM, at least 2048 complex values per block.
-int stats2_blocks(int64_t nel, int num_sms) {
+int qcs::stats2_blocks(int64_t nel, int num_sms) {
     int64_t g = (nel + 2047) / 2048;
     g = std::max<int64_t>(1, std::min<int64_t>(g, 4 * (int64_t)num_sms));
     return static_cast<int>(g);
 }
+
+namespace {
 
 // Tensor map of one operand's planes: {K, R, nplanes}, box = one stage of all
 // planes (kRowBytes of K x 128 rows), 64-byte swizzle (the layout the
@@ -834,6 +838,55 @@ int qcs_set_tc_splits(qcs_handle_t h, int splits) {
 int qcs_set_complex_products(qcs_handle_t h, int products) {
     if (!h || (products != 3 && products != 4)) return QCS_ERR_INVALID_ARG;
     h->complex_products = products;
+    return QCS_SUCCESS;
+}
+
+int qcs_selection_stats(qcs_handle_t h, qcs_op_t transA, qcs_op_t transB, int64_t m, int64_t n,
+                        int64_t k, const qcs_c32 *A, int64_t lda, const qcs_c32 *B, int64_t ldb,
+                        qcs_selection_stats_t *out, qcs_gemm_desc_t *desc_out) {
+    if (!h || !out) return QCS_ERR_INVALID_ARG;
+    const qcs_c32 one{1.f, 0.f}, zero{0.f, 0.f};
+    if (int r = validate_cgemm(QCS_MODE_AUTO, transA, transB, m, n, k, &one, A, lda, B, ldb, &zero,
+                               A, std::max<int64_t>(m, 1)))
+        return r;
+    if (m == 0 || n == 0 || k == 0) return QCS_ERR_INVALID_ARG;
+    const int64_t ra = (transA == QCS_OP_N) ? m : k, ca = (transA == QCS_OP_N) ? k : m;
+    const int64_t rb = (transB == QCS_OP_N) ? k : n, cb = (transB == QCS_OP_N) ? n : k;
+    const int gA = stats2_blocks(ra * ca, h->num_sms), gB = stats2_blocks(rb * cb, h->num_sms);
+    const size_t p1b = align256(sizeof(int64_t) * 5 * (gA + gB));
+    const size_t p2b = align256(sizeof(int64_t) * (gA + gB));
+    const size_t bytes = p1b + p2b + align256(sizeof(qcs_gemm_desc_t)) + align256(10 * sizeof(int64_t));
+    if (int r = ensure_workspace(h->ws, bytes)) return r;
+    uint8_t *p = static_cast<uint8_t *>(h->ws.ptr);
+    int64_t *p1 = reinterpret_cast<int64_t *>(p);
+    int64_t *p2 = reinterpret_cast<int64_t *>(p + p1b);
+    qcs_gemm_desc_t *desc = reinterpret_cast<qcs_gemm_desc_t *>(p + p1b + p2b);
+    int64_t *summary =
+        reinterpret_cast<int64_t *>(p + p1b + p2b + align256(sizeof(qcs_gemm_desc_t)));
+    cudaError_t e = launch_stats_select_2stage(
+        reinterpret_cast<const float2 *>(A), ra, ca, lda, gA, reinterpret_cast<const float2 *>(B),
+        rb, cb, ldb, gB, h->tol, QCS_MODE_AUTO, p1, p2, desc, nullptr, 0.0, h->stream, summary);
+    int64_t hs[10];
+    qcs_gemm_desc_t hd;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hs, summary, sizeof(hs), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&hd, desc, sizeof(hd), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    for (int o = 0; o < 2; ++o) {
+        const int64_t *v = hs + 5 * o;
+        out[o].e_max = v[0] < 0 ? -128 : (int32_t)(v[0] - 127);
+        out[o].stage2 = v[4] >= 0 ? 1 : 0;
+        out[o].n_nonzero = v[1];
+        out[o].n_nonfinite = v[2];
+        out[o].n_under_fp16 = v[3];
+        out[o].n_under_window = v[4] >= 0 ? v[4] : 0;
+    }
+    if (desc_out) *desc_out = hd;
     return QCS_SUCCESS;
 }
 

@@ -162,12 +162,15 @@ cudaError_t launch_select(const int64_t *partials, int gA, int gB, int64_t nA, i
 // the shifted window), final selection.  gA / gB blocks of 256 threads per
 // matrix; p1 holds 5 int64 per block, p2 one.  ``counts`` (optional: 6
 // uint64 indexed by qcs_mode_t, then 6 doubles) gets one increment and
-// ``work`` (the GEMM's 8 m n k) added for the selected mode.
+// ``work`` (the GEMM's 8 m n k) added for the selected mode.  ``summary``
+// (optional, 10 int64): the counts the selection used (qcs_selection_stats).
 cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t cols0, int64_t ld0,
                                        int gA, const float2 *X1, int64_t rows1, int64_t cols1,
                                        int64_t ld1, int gB, double tol, int forced, int64_t *p1,
                                        int64_t *p2, qcs_gemm_desc_t *desc,
-                                       unsigned long long *counts, double work, cudaStream_t s);
+                                       unsigned long long *counts, double work, cudaStream_t s,
+                                       int64_t *summary = nullptr);
+int stats2_blocks(int64_t nel, int num_sms);
 // Select from two finished qcs_stats_t.
 cudaError_t launch_select_from_stats(const qcs_stats_t *a, const qcs_stats_t *b, double tol,
                                      qcs_gemm_desc_t *desc, cudaStream_t s);

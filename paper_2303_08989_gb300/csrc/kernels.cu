@@ -488,7 +488,8 @@ __global__ void __launch_bounds__(kS2Threads) stats_pass2_kernel(
 
 __global__ void select2_kernel(const int64_t *__restrict__ p1, const int64_t *__restrict__ p2,
                                int gA, int gB, int64_t nA, int64_t nB, double tol, int forced,
-                               qcs_gemm_desc_t *desc, unsigned long long *counts, double work) {
+                               qcs_gemm_desc_t *desc, unsigned long long *counts, double work,
+                               int64_t *summary) {
     __shared__ uint64_t shs[kS2Threads / 32];
     __shared__ uint32_t shm[kS2Threads / 32];
     const Sum1 a = reduce_p1(p1, 0, gA, nA, shm, shs);
@@ -518,6 +519,19 @@ __global__ void select2_kernel(const int64_t *__restrict__ p1, const int64_t *__
     sa.under2 = (int64_t)u2a;
     sb.under2 = (int64_t)u2b;
     select_rule(sa, sb, tol, forced, desc);
+    if (summary) {
+        // per operand: biased e_max (-1: none), nonzero, Inf/NaN, below 2^-14,
+        // below the shifted window (-1: Stage 2 not taken)
+        const Sum1 *ss[2] = {&a, &b};
+        const int64_t u2[2] = {(int64_t)u2a, (int64_t)u2b};
+        for (int o = 0; o < 2; ++o) {
+            summary[5 * o + 0] = ss[o]->bmax;
+            summary[5 * o + 1] = ss[o]->nnz;
+            summary[5 * o + 2] = ss[o]->nonfinite;
+            summary[5 * o + 3] = ss[o]->under1;
+            summary[5 * o + 4] = need2 ? u2[o] : -1;
+        }
+    }
     if (counts) {
         // counts[0..5]: GEMMs per selected mode; then 6 doubles of their 8 m n k
         atomicAdd(&counts[desc->mode], 1ULL);
@@ -555,7 +569,8 @@ static cudaError_t stats_select_2stage(const T *X0, int64_t rows0, int64_t cols0
                                        int gA, const T *X1, int64_t rows1, int64_t cols1,
                                        int64_t ld1, int gB, double tol, int forced, int64_t *p1,
                                        int64_t *p2, qcs_gemm_desc_t *desc,
-                                       unsigned long long *counts, double work, cudaStream_t s) {
+                                       unsigned long long *counts, double work, cudaStream_t s,
+                                       int64_t *summary) {
     stats_pass1_kernel<T><<<gA + gB, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1,
                                                          cols1, ld1, gB, p1);
     cudaError_t e = cudaGetLastError();
@@ -566,7 +581,7 @@ static cudaError_t stats_select_2stage(const T *X0, int64_t rows0, int64_t cols0
     if (e != cudaSuccess) return e;
     select2_kernel<<<1, kS2Threads, 0, s>>>(p1, p2, gA, gB, scalars_per<T>() * rows0 * cols0,
                                             scalars_per<T>() * rows1 * cols1, tol, forced, desc,
-                                            counts, work);
+                                            counts, work, summary);
     return cudaGetLastError();
 }
 
@@ -574,9 +589,10 @@ cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t 
                                        int gA, const float2 *X1, int64_t rows1, int64_t cols1,
                                        int64_t ld1, int gB, double tol, int forced, int64_t *p1,
                                        int64_t *p2, qcs_gemm_desc_t *desc,
-                                       unsigned long long *counts, double work, cudaStream_t s) {
+                                       unsigned long long *counts, double work, cudaStream_t s,
+                                       int64_t *summary) {
     return stats_select_2stage(X0, rows0, cols0, ld0, gA, X1, rows1, cols1, ld1, gB, tol, forced,
-                               p1, p2, desc, counts, work, s);
+                               p1, p2, desc, counts, work, s, summary);
 }
 
 cudaError_t launch_stats_select_2stage_real(const float *X0, int64_t rows0, int64_t cols0,
@@ -586,7 +602,7 @@ cudaError_t launch_stats_select_2stage_real(const float *X0, int64_t rows0, int6
                                             qcs_gemm_desc_t *desc, unsigned long long *counts,
                                             double work, cudaStream_t s) {
     return stats_select_2stage(X0, rows0, cols0, ld0, gA, X1, rows1, cols1, ld1, gB, tol, forced,
-                               p1, p2, desc, counts, work, s);
+                               p1, p2, desc, counts, work, s, (int64_t *)nullptr);
 }
 
 cudaError_t launch_select_from_stats(const qcs_stats_t *a, const qcs_stats_t *b, double tol,
