@@ -1290,21 +1290,35 @@ def tree_legs(args, q, torch, dev, rank, world=1, dist=None):
             loss.backward()
             return loss
 
-        fwd_bwd()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        loss = fwd_bwd()
-        torch.cuda.synchronize()
-        diff[mode] = {"s_fwd_bwd": time.perf_counter() - t0, "loss": float(loss.item()),
-                      "grad": params.grad.double().cpu().numpy()}
+        def timed_fwd_bwd():
+            fwd_bwd()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            loss = fwd_bwd()
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0, loss
+
+        t_eager, _ = timed_fwd_bwd()
+        # the same as two CUDA-graph replays, the forward grouped over the slices
+        hd.set_instance_batch(plan.n_instances)
+        cp.use_graphs(hd)
+        t_graph, loss = timed_fwd_bwd()
+        diff[mode] = {"s_fwd_bwd": t_graph, "s_fwd_bwd_eager": t_eager,
+                      "loss": float(loss.item()), "grad": params.grad.double().cpu().numpy()}
+        cp.graphed.close()
         hd.close()
     out4 = {"workload": "4x5 grid, depth 12, fSim(theta, phi) ~ U[0, pi], loss sum log|a|^2 "
                         "over 256 bitstrings; open network, 2 sliced indices (4 slices, "
-                        "recomputed in the backward); AUTO with the measured size rule",
+                        "recomputed in the backward); AUTO with the measured size rule; forward "
+                        "(grouped) and backward as CUDA-graph replays, eager beside",
             "auto_s": diff["auto"]["s_fwd_bwd"], "fp32_s": diff["fp32"]["s_fwd_bwd"],
+            "auto_s_eager": diff["auto"]["s_fwd_bwd_eager"],
+            "fp32_s_eager": diff["fp32"]["s_fwd_bwd_eager"],
             "speedup_vs_fp32": diff["fp32"]["s_fwd_bwd"] / diff["auto"]["s_fwd_bwd"],
             "cheapest_order": {"auto_s": diff["auto_cheapest_order"]["s_fwd_bwd"],
                                "fp32_s": diff["fp32_cheapest_order"]["s_fwd_bwd"],
+                               "auto_s_eager": diff["auto_cheapest_order"]["s_fwd_bwd_eager"],
+                               "fp32_s_eager": diff["fp32_cheapest_order"]["s_fwd_bwd_eager"],
                                "note": "the cheapest of %d seeded greedy orders: 100x and more "
                                        "fewer flops, GEMMs too small for emulation to matter"
                                        % args.greedy_trials}}

@@ -377,7 +377,8 @@ typedef struct {
  * launched gated).  Their outputs hold G instances each (intermediates share
  * memory by liveness).  The later steps -- large enough to fill the GPU
  * alone -- loop over the group.  Results do not depend on G.  The backward
- * always runs one instance at a time. */
+ * runs one instance at a time (its launches can be captured in a graph:
+ * qcs_tree_backward_graph_create). */
 int qcs_set_instance_batch(qcs_handle_t h, int instances);
 
 /* Contract the plan for every instance and accumulate into d_out (device,
@@ -405,6 +406,23 @@ int qcs_tree_graph_create(qcs_handle_t h, const qcs_tree_t *tree, const qcs_c32 
                           double *d_out, qcs_tree_graph_t *out);
 int qcs_tree_graph_launch(qcs_tree_graph_t g);
 int qcs_tree_graph_destroy(qcs_tree_graph_t g);
+
+/* The launches of one qcs_contract_tree_backward call captured into a CUDA
+ * graph, the same way: qcs_tree_backward_graph_create validates the plan,
+ * allocates the graph's own workspace (cudaMalloc; not during a capture) and
+ * records every kernel the call would launch for these leaves, this
+ * d_grad_out and these d_grad_leaves; nothing is computed.  Each
+ * qcs_tree_graph_launch of it then adds the leaf gradients to
+ * d_grad_leaves, from the current contents of the leaf and d_grad_out
+ * buffers, exactly as qcs_contract_tree_backward would (the caller clears
+ * d_grad_leaves between replays if it wants the gradient alone).  The
+ * buffers and the handle must outlive the graph; qcs_tree_graph_destroy
+ * frees it.  Replaying removes the host cost of the backward's launches
+ * (two gathers, two GEMMs and two scatters per step and instance), which
+ * dominates on trees of many small contractions. */
+int qcs_tree_backward_graph_create(qcs_handle_t h, const qcs_tree_t *tree,
+                                   const qcs_c32 *const *leaves, const double *d_grad_out,
+                                   qcs_c32 *const *d_grad_leaves, qcs_tree_graph_t *out);
 
 /* Adjoint of qcs_contract_tree.  Given d_grad_out (device complex128,
  * n_slots * out_size values: dL/dRe + i dL/dIm of each output), adds to

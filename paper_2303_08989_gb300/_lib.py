@@ -36,7 +36,7 @@ EXPORTED = [
     "qcs_get_tuning", "qcs_set_tuning", "qcs_set_instance_batch", "qcs_set_tc_schedule",
     "qcs_set_tc_splits", "qcs_sgemm", "qcs_set_complex_products", "qcs_set_wait_budget",
     "qcs_debug_stall_producer", "qcs_cgemm_noalloc_status", "qcs_measure_fma_peak",
-    "qcs_set_fused_split", "qcs_selection_stats",
+    "qcs_set_fused_split", "qcs_selection_stats", "qcs_tree_backward_graph_create",
 ]
 SIZE_RULE_OFF, SIZE_RULE_PAPER, SIZE_RULE_TUNED = 0, 1, 2
 NUM_MODES = 6
@@ -150,6 +150,8 @@ def load(path: str = LIB_PATH):
                               P, I64, P, I64, ctypes.POINTER(qcs_c32), P, I64, P],
         "qcs_tree_graph_create": [H, ctypes.POINTER(qcs_tree_t), ctypes.POINTER(P), P,
                                   ctypes.POINTER(ctypes.c_void_p)],
+        "qcs_tree_backward_graph_create": [H, ctypes.POINTER(qcs_tree_t), ctypes.POINTER(P), P,
+                                           ctypes.POINTER(P), ctypes.POINTER(ctypes.c_void_p)],
         "qcs_tree_graph_launch": [P],
         "qcs_tree_graph_destroy": [P],
         "qcs_get_auto_counts": [H, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double), I],

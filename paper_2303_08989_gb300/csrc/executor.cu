@@ -581,52 +581,14 @@ int forward_all(const Ctx &c, double *d_out) {
     return QCS_SUCCESS;
 }
 
-}  // namespace
-}  // namespace qcs
-
-struct qcs_tree_graph_s {
-    qcs_handle_t h = nullptr;
-    qcs::Workspace ws;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-};
-
-using namespace qcs;
-
-extern "C" {
-
-int qcs_contract_tree(qcs_handle_t h, const qcs_tree_t *tree, const qcs_c32 *const *leaves,
-                      double *d_out, qcs_run_info_t *info) {
-    if (!h || !tree || !leaves || !d_out) return QCS_ERR_INVALID_ARG;
-    const auto t0 = std::chrono::steady_clock::now();
-    if (info) *info = qcs_run_info_t{};
-    for (int i = 0; i < tree->n_leaves; ++i)
-        if (!leaves[i] || (reinterpret_cast<uintptr_t>(leaves[i]) & 7u)) return QCS_ERR_INVALID_ARG;
-    Ctx c;
-    c.leaves = leaves;
-    c.info = info;
-    if (int r = begin(h, tree, false, c)) return r;
-    if (int r = forward_all(c, d_out)) return r;
-    if (info)
-        info->seconds =
-            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    return QCS_SUCCESS;
-}
-
-int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
-                               const qcs_c32 *const *leaves, const double *d_grad_out,
-                               qcs_c32 *const *d_grad_leaves, qcs_run_info_t *info) {
-    if (!h || !tree || !leaves || !d_grad_out || !d_grad_leaves) return QCS_ERR_INVALID_ARG;
-    const auto t0 = std::chrono::steady_clock::now();
-    if (info) *info = qcs_run_info_t{};
-    for (int i = 0; i < tree->n_leaves; ++i)
-        if (!leaves[i] || !d_grad_leaves[i] || (reinterpret_cast<uintptr_t>(leaves[i]) & 7u) ||
-            (reinterpret_cast<uintptr_t>(d_grad_leaves[i]) & 7u))
-            return QCS_ERR_INVALID_ARG;
-    Ctx c;
-    c.leaves = leaves;
-    c.info = info;
-    if (int r = begin(h, tree, true, c)) return r;
+// Every launch of a backward call after begin(): per instance the forward
+// recomputed, the root's gradient seeded from its slot, then per step (last
+// to first) the two adjoint GEMMs and the scatters of the operand gradients
+// through the maps that gathered the operands.
+int backward_all(Ctx &c, const double *d_grad_out, qcs_c32 *const *d_grad_leaves) {
+    const qcs_tree_t *tree = c.t;
+    qcs_handle_t h = c.h;
+    qcs_run_info_t *info = c.info;
     const std::vector<int64_t> &size_of = c.size_of;
     const int nl = tree->n_leaves, ns = tree->n_steps;
     cudaStream_t s = h->stream;
@@ -678,9 +640,112 @@ int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
             if (int r = scatter_into(st.b, inst, st.map_b, gB)) return r;
         }
     }
+    return QCS_SUCCESS;
+}
+
+bool backward_args_ok(const qcs_tree_t *tree, const qcs_c32 *const *leaves,
+                      qcs_c32 *const *d_grad_leaves) {
+    for (int i = 0; i < tree->n_leaves; ++i)
+        if (!leaves[i] || !d_grad_leaves[i] || (reinterpret_cast<uintptr_t>(leaves[i]) & 7u) ||
+            (reinterpret_cast<uintptr_t>(d_grad_leaves[i]) & 7u))
+            return false;
+    return true;
+}
+
+}  // namespace
+}  // namespace qcs
+
+struct qcs_tree_graph_s {
+    qcs_handle_t h = nullptr;
+    qcs::Workspace ws;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+using namespace qcs;
+
+extern "C" {
+
+int qcs_contract_tree(qcs_handle_t h, const qcs_tree_t *tree, const qcs_c32 *const *leaves,
+                      double *d_out, qcs_run_info_t *info) {
+    if (!h || !tree || !leaves || !d_out) return QCS_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (info) *info = qcs_run_info_t{};
+    for (int i = 0; i < tree->n_leaves; ++i)
+        if (!leaves[i] || (reinterpret_cast<uintptr_t>(leaves[i]) & 7u)) return QCS_ERR_INVALID_ARG;
+    Ctx c;
+    c.leaves = leaves;
+    c.info = info;
+    if (int r = begin(h, tree, false, c)) return r;
+    if (int r = forward_all(c, d_out)) return r;
     if (info)
         info->seconds =
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return QCS_SUCCESS;
+}
+
+int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
+                               const qcs_c32 *const *leaves, const double *d_grad_out,
+                               qcs_c32 *const *d_grad_leaves, qcs_run_info_t *info) {
+    if (!h || !tree || !leaves || !d_grad_out || !d_grad_leaves) return QCS_ERR_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (info) *info = qcs_run_info_t{};
+    if (tree->n_leaves >= 1 && !backward_args_ok(tree, leaves, d_grad_leaves))
+        return QCS_ERR_INVALID_ARG;
+    Ctx c;
+    c.leaves = leaves;
+    c.info = info;
+    if (int r = begin(h, tree, true, c)) return r;
+    if (int r = backward_all(c, d_grad_out, d_grad_leaves)) return r;
+    if (info)
+        info->seconds =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return QCS_SUCCESS;
+}
+
+int qcs_tree_backward_graph_create(qcs_handle_t h, const qcs_tree_t *tree,
+                                   const qcs_c32 *const *leaves, const double *d_grad_out,
+                                   qcs_c32 *const *d_grad_leaves, qcs_tree_graph_t *out) {
+    if (!h || !tree || !leaves || !d_grad_out || !d_grad_leaves || !out) return QCS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (tree->n_leaves >= 1 && !backward_args_ok(tree, leaves, d_grad_leaves))
+        return QCS_ERR_INVALID_ARG;
+    qcs_tree_graph_s *g = new (std::nothrow) qcs_tree_graph_s;
+    if (!g) return QCS_ERR_ALLOC;
+    g->h = h;
+    Ctx c;
+    c.leaves = leaves;
+    c.info = nullptr;
+    int r = begin(h, tree, true, c, &g->ws);
+    if (r == QCS_SUCCESS && cudaStreamSynchronize(h->stream) != cudaSuccess) r = QCS_ERR_CUDA;
+    const int profiling = h->profiling;
+    cudaStream_t user = h->stream, cap = nullptr;
+    h->profiling = 0;
+    if (r == QCS_SUCCESS && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+        r = QCS_ERR_CUDA;
+    if (r == QCS_SUCCESS) {
+        h->stream = cap;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            r = QCS_ERR_CUDA;
+        } else {
+            const int rb = backward_all(c, d_grad_out, d_grad_leaves);
+            const cudaError_t e = cudaStreamEndCapture(cap, &g->graph);
+            r = rb ? rb : (e == cudaSuccess ? QCS_SUCCESS : QCS_ERR_CUDA);
+        }
+    }
+    h->stream = user;
+    h->profiling = profiling;
+    if (cap) cudaStreamDestroy(cap);
+    if (r == QCS_SUCCESS && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess)
+        r = QCS_ERR_CUDA;
+    if (r != QCS_SUCCESS) {
+        cudaGetLastError();
+        if (g->graph) cudaGraphDestroy(g->graph);
+        if (g->ws.ptr) cudaFree(g->ws.ptr);
+        delete g;
+        return r;
+    }
+    *out = g;
     return QCS_SUCCESS;
 }
 

@@ -544,6 +544,14 @@ class CompiledPlan:
         self.last_info = info
         return grads
 
+    def use_graphs(self, h):
+        """From now on, contract() runs this plan's forward and backward as two
+        CUDA-graph replays on ``h`` (GraphedPlan) instead of launching every
+        kernel from the host.  Call after any autotuning and with the
+        instance batch already set; returns the GraphedPlan."""
+        self.graphed = GraphedPlan(self, h)
+        return self.graphed
+
     def autotune(self, h, backward: bool = False, reps: int = 3) -> int:
         """Time the candidate modes of every AUTO GEMM shape this plan issues
         (qcs_autotune_tree) and record them in ``h``'s table; returns the
@@ -576,6 +584,67 @@ class TreeGraph:
         if self._g:
             self.h.lib.qcs_tree_graph_destroy(self._g)
             self._g = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GraphedPlan:
+    """A plan's forward and backward captured as two CUDA graphs over
+    persistent device buffers: the leaves packed into one buffer, the output,
+    the output gradient and the packed leaf gradients.  ``forward(leaves)``
+    copies the leaves in (one kernel) and replays the forward graph;
+    ``backward(leaves, grad_out)`` copies the leaves and the output gradient
+    in, clears the gradients and replays the backward graph.  Both return
+    fresh tensors, so the buffers may be reused by the next call."""
+
+    def __init__(self, cp: "CompiledPlan", h):
+        import torch
+
+        self.cp, self.h = cp, h
+        plan, dev = cp.plan, cp.device
+        self.sizes = [lf.data.size for lf in plan.net.leaves]
+        self.leaf_buf = torch.zeros(sum(self.sizes), dtype=torch.complex64, device=dev)
+        self.grad_buf = torch.zeros_like(self.leaf_buf)
+        self.leaves = list(self.leaf_buf.split(self.sizes))
+        self.grads = list(self.grad_buf.split(self.sizes))
+        self.out = torch.zeros((plan.n_slots, plan.out_size), dtype=torch.complex128, device=dev)
+        self.gout = torch.zeros_like(self.out)
+        lp, gp = cp._ptrs(self.leaves), cp._ptrs(self.grads)
+        self._keep = (lp, gp)
+        self._fwd, self._bwd = ctypes.c_void_p(), ctypes.c_void_p()
+        _lib.check(h.lib.qcs_tree_graph_create(h.ptr, ctypes.byref(cp.tree), lp,
+                                               ctypes.c_void_p(self.out.data_ptr()),
+                                               ctypes.byref(self._fwd)), "qcs_tree_graph_create")
+        _lib.check(h.lib.qcs_tree_backward_graph_create(
+            h.ptr, ctypes.byref(cp.tree), lp, ctypes.c_void_p(self.gout.data_ptr()), gp,
+            ctypes.byref(self._bwd)), "qcs_tree_backward_graph_create")
+
+    def _load(self, leaves):
+        import torch
+
+        torch.cat([t.reshape(-1) for t in leaves], out=self.leaf_buf)
+
+    def forward(self, leaves):
+        self._load(leaves)
+        _lib.check(self.h.lib.qcs_tree_graph_launch(self._fwd), "qcs_tree_graph_launch")
+        return self.out.clone()
+
+    def backward(self, leaves, grad_out):
+        self._load(leaves)
+        self.gout.copy_(grad_out)
+        self.grad_buf.zero_()
+        _lib.check(self.h.lib.qcs_tree_graph_launch(self._bwd), "qcs_tree_graph_launch")
+        return list(self.grad_buf.clone().split(self.sizes))
+
+    def close(self):
+        for g in ("_fwd", "_bwd"):
+            if getattr(self, g, None):
+                self.h.lib.qcs_tree_graph_destroy(getattr(self, g))
+                setattr(self, g, ctypes.c_void_p())
 
     def __del__(self):
         try:
@@ -652,12 +721,19 @@ def _make_function():
             ctx.cp = cp
             ctx.h = h
             ctx.save_for_backward(*leaves)
+            gp = getattr(cp, "graphed", None)
+            if gp is not None and gp.h is h:
+                return gp.forward(list(leaves))
             return cp.forward(h, list(leaves))
 
         @staticmethod
         def backward(ctx, grad_out):
             leaves = ctx.saved_tensors
-            grads = ctx.cp.backward(ctx.h, grad_out, list(leaves))
+            gp = getattr(ctx.cp, "graphed", None)
+            if gp is not None and gp.h is ctx.h:
+                grads = gp.backward(list(leaves), grad_out)
+            else:
+                grads = ctx.cp.backward(ctx.h, grad_out, list(leaves))
             return (None, None, *[g if t.requires_grad else None for g, t in zip(grads, leaves)])
 
     return ContractTree
