@@ -1295,8 +1295,9 @@ __global__ void __launch_bounds__(256, SPLIT ? 4 : 5) copy_tiled_kernel(CopyPara
 }
 
 // The split through a gather map with quads: the same tiles as
-// copy_tiled_kernel<true>, kept in shared memory as tile[y][x], and each
-// thread writes one run of four consecutive output elements per tile, so
+// copy_tiled_kernel<true>, and each thread writes one run of four
+// consecutive output elements per tile (reading them from a column of the
+// shared tile, 33 elements per row so that the reads spread over banks), so
 // that every plane gets one 8-byte (16-bit kinds) or 16-byte (TF32) store
 // per four elements.  Needs the output-contiguous run X to be a multiple of
 // 4 elements long and every other output stride, the operand's plane offset
@@ -1325,14 +1326,15 @@ __device__ __forceinline__ void split_quads_body(const CopyParams &P, const floa
     const bool okout = (x0 + 4 * xq < P.px) && (y0 + yq < P.py);
     const int64_t rout = sxo[4 * xq] + syo[yq];
     const int64_t ps = so.plane_stride;
-    // tile t -> ring slot t % kQuadStages, transposed on the way in
-    // (tile[slot][y][x]); elements outside the tensor are zero-filled
+    // tile t -> ring slot t % kQuadStages as tile[slot][x][y]: a warp's copies
+    // land in one contiguous 256-byte row (lanes along y); elements outside
+    // the tensor are zero-filled
     auto load = [&](int t) {
         const int64_t ri = sr[t][0];
         const int buf = t % kQuadStages;
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-            cp_async8(&tile[buf][tx][ty + 8 * r], okin[r] ? in + ri + rin[r] : in, okin[r] ? 8u : 0u);
+            cp_async8(&tile[buf][ty + 8 * r][tx], okin[r] ? in + ri + rin[r] : in, okin[r] ? 8u : 0u);
     };
 #pragma unroll
     for (int t = 0; t < kQuadStages - 1; ++t) {
@@ -1349,7 +1351,7 @@ __device__ __forceinline__ void split_quads_body(const CopyParams &P, const floa
             uint32_t h[2][4], lo[2][4];  // [re | im][element of the quad]
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const float2 w = tile[buf][yq][4 * xq + e];
+                const float2 w = tile[buf][4 * xq + e][yq];
                 split_value(KIND == 1 ? QCS_MODE_TF32X : (KIND == 2 ? QCS_MODE_BF16X3 : QCS_MODE_FP16X),
                             apply_scale(w.x, pscale), h[0][e], lo[0][e]);
                 split_value(KIND == 1 ? QCS_MODE_TF32X : (KIND == 2 ? QCS_MODE_BF16X3 : QCS_MODE_FP16X),
@@ -2455,55 +2457,74 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
 namespace {
 
 constexpr int kRT = 128;    // output rows and columns of a tile
-constexpr int kRK = 8;      // k per shared-memory step
-constexpr int kRPad = 132;  // row length of a shared tile (transposed stores spread over banks)
+constexpr int kRK = 16;     // k per shared-memory stage
+constexpr int kRStages = 3;
+constexpr int kRPad = 132;  // row length of a shared tile (16-byte rows; transposed copies spread over banks)
+constexpr size_t kRSmemBytes = sizeof(float) * 2 * kRStages * kRK * kRPad;
 
 // C = alpha op(A) op(B) + beta C on the CUDA cores: 128 x 128 tiles, 256
 // threads with 8 x 8 outputs each (rows 4t..4t+3 and 64+4t..64+4t+3 of the
-// tile, likewise columns), the next k step loaded into registers while the
-// current one is multiplied.  Runs only when the descriptor selected FP32
-// (always when desc is NULL).  Tiles in y are walked in a grid-stride loop.
+// tile, likewise columns).  Operand tiles of 16 k move to shared memory with
+// 4-byte cp.async copies (zero-filled outside the matrix) in a three-stage
+// ring, unchecked for tiles inside the matrix except in the last k-tile;
+// TA / TB: op(A) / op(B) is op T (op C acts as op T on real matrices).
+// Runs only when the descriptor selected FP32 (always when desc is NULL).
+// Tiles in y are walked in a grid-stride loop.
+template <bool TA, bool TB>
 __global__ void __launch_bounds__(256, 2) sgemm_simt_kernel(
-    const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int64_t k,
-    float alpha, const float *__restrict__ A, int64_t lda, const float *__restrict__ B,
-    int64_t ldb, float beta, float *__restrict__ C, int64_t ldc) {
+    const qcs_gemm_desc_t *__restrict__ desc, int64_t m, int64_t n, int64_t k, float alpha,
+    const float *__restrict__ A, int64_t lda, const float *__restrict__ B, int64_t ldb, float beta,
+    float *__restrict__ C, int64_t ldc) {
     if (desc && desc->mode != QCS_MODE_FP32) return;
-    __shared__ __align__(16) float As[2][kRK][kRPad];
-    __shared__ __align__(16) float Bs[2][kRK][kRPad];
+    extern __shared__ __align__(16) unsigned char sgemm_smem[];
+    float (*As)[kRK][kRPad] = reinterpret_cast<float (*)[kRK][kRPad]>(sgemm_smem);
+    float (*Bs)[kRK][kRPad] =
+        reinterpret_cast<float (*)[kRK][kRPad]>(sgemm_smem + sizeof(float) * kRStages * kRK * kRPad);
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    // element (i, l) of op(A) is A[i sAi + l sAl]; (l, j) of op(B) is B[l sBl + j sBj]
-    const int64_t sAi = (opA == QCS_OP_N) ? 1 : lda, sAl = (opA == QCS_OP_N) ? lda : 1;
-    const int64_t sBl = (opB == QCS_OP_N) ? 1 : ldb, sBj = (opB == QCS_OP_N) ? ldb : 1;
+    // copy assignment: op N of A: i = tid % 128, l = tid / 128 + 2 q; op T:
+    // l = tid % 16, i = tid / 16 + 16 q (q < 8); op N of B: l = tid % 16,
+    // j = tid / 16 + 16 q; op T: j = tid % 128, l = tid / 128 + 2 q
+    const int aI = TA ? (tid >> 4) : (tid & (kRT - 1));
+    const int aL = TA ? (tid & (kRK - 1)) : (tid >> 7);
+    const int bJ = TB ? (tid & (kRT - 1)) : (tid >> 4);
+    const int bL = TB ? (tid >> 7) : (tid & (kRK - 1));
+    const int64_t a_kstep = TA ? kRK : kRK * lda, a_qstep = TA ? 16 * lda : 2 * lda;
+    const int64_t b_kstep = TB ? kRK * ldb : kRK, b_qstep = TB ? 2 * ldb : 16 * ldb;
     const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kRT;
     const int64_t tiles_n = (n + kRT - 1) / kRT;
+    const int ktiles = (int)((k + kRK - 1) / kRK);
     for (int64_t tj = blockIdx.y; tj < tiles_n; tj += gridDim.y) {
         const int64_t j0 = tj * kRT;
-        float ra[4], rb[4];
-        // loads of a k step: 1024 elements of each operand, 4 per thread,
-        // consecutive threads along the operand's contiguous index
-        auto load = [&](int64_t l0) {
+        const float *a_base = A + (TA ? aL + (i0 + aI) * lda : i0 + aI + aL * lda);
+        const float *b_base = B + (TB ? j0 + bJ + bL * ldb : bL + (j0 + bJ) * ldb);
+        uint32_t a_mask = 0, b_mask = 0;  // bit q: copy q's row (column) lies inside the matrix
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int idx = tid + 256 * q;
-                int i, l;
-                if (sAi == 1) { i = idx & 127; l = idx >> 7; } else { l = idx & 7; i = idx >> 3; }
-                const int64_t gi = i0 + i, gl = l0 + l;
-                ra[q] = (gi < m && gl < k) ? A[gi * sAi + gl * sAl] : 0.f;
-                int j, lb;
-                if (sBj == 1) { j = idx & 127; lb = idx >> 7; } else { lb = idx & 7; j = idx >> 3; }
-                const int64_t gj = j0 + j, glb = l0 + lb;
-                rb[q] = (gj < n && glb < k) ? B[glb * sBl + gj * sBj] : 0.f;
+        for (int q = 0; q < 8; ++q) {
+            a_mask |= uint32_t(i0 + aI + (TA ? 16 * q : 0) < m) << q;
+            b_mask |= uint32_t(j0 + bJ + (TB ? 0 : 16 * q) < n) << q;
+        }
+        const bool interior = i0 + kRT <= m && j0 + kRT <= n;
+        auto load_tile = [&](int st, int kt) {
+            const int64_t k0 = static_cast<int64_t>(kt) * kRK;
+            const bool tail = k0 + kRK > k;
+            const float *pa = a_base + kt * a_kstep;
+            const float *pb = b_base + kt * b_kstep;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int l = TA ? aL : aL + 2 * q;
+                const int i = TA ? aI + 16 * q : aI;
+                bool ok = true;
+                if (!interior || tail) ok = ((a_mask >> q) & 1u) && k0 + l < k;
+                cp_async4(&As[st][l][i], ok ? pa + q * a_qstep : A, ok ? 4u : 0u);
             }
-        };
-        auto store = [&](int buf) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int idx = tid + 256 * q;
-                if (sAi == 1) As[buf][idx >> 7][idx & 127] = ra[q];
-                else As[buf][idx & 7][idx >> 3] = ra[q];
-                if (sBj == 1) Bs[buf][idx >> 7][idx & 127] = rb[q];
-                else Bs[buf][idx & 7][idx >> 3] = rb[q];
+            for (int q = 0; q < 8; ++q) {
+                const int l = TB ? bL + 2 * q : bL;
+                const int j = TB ? bJ : bJ + 16 * q;
+                bool ok = true;
+                if (!interior || tail) ok = ((b_mask >> q) & 1u) && k0 + l < k;
+                cp_async4(&Bs[st][l][j], ok ? pb + q * b_qstep : B, ok ? 4u : 0u);
             }
         };
         float acc[8][8];
@@ -2511,20 +2532,23 @@ __global__ void __launch_bounds__(256, 2) sgemm_simt_kernel(
         for (int r = 0; r < 8; ++r)
 #pragma unroll
             for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
-        __syncthreads();  // the previous tile's readers are done with both buffers
-        load(0);
-        store(0);
-        __syncthreads();
-        int buf = 0;
-        for (int64_t l0 = 0; l0 < k; l0 += kRK) {
-            const bool more = l0 + kRK < k;
-            if (more) load(l0 + kRK);
+        __syncthreads();  // the previous tile's readers are done with the ring
+        if (ktiles > 0) load_tile(0, 0);
+        cp_async_commit();
+        if (ktiles > 1) load_tile(1, 1);
+        cp_async_commit();
+        for (int kt = 0; kt < ktiles; ++kt) {
+            cp_async_wait<1>();  // every group but the newest has landed: k-tile kt
+            __syncthreads();     // ... for all threads; and slot (kt + 2) % 3 is free
+            if (kt + 2 < ktiles) load_tile((kt + 2) % kRStages, kt + 2);
+            cp_async_commit();
+            const int st = kt % kRStages;
 #pragma unroll
             for (int kk = 0; kk < kRK; ++kk) {
-                const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][tx * 4]);
-                const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + tx * 4]);
-                const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][ty * 4]);
-                const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + ty * 4]);
+                const float4 a0 = *reinterpret_cast<const float4 *>(&As[st][kk][tx * 4]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&As[st][kk][64 + tx * 4]);
+                const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[st][kk][ty * 4]);
+                const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[st][kk][64 + ty * 4]);
                 const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
                 const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -2532,12 +2556,8 @@ __global__ void __launch_bounds__(256, 2) sgemm_simt_kernel(
 #pragma unroll
                     for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
             }
-            if (more) {
-                store(buf ^ 1);
-                __syncthreads();
-                buf ^= 1;
-            }
         }
+        cp_async_wait<0>();
         const bool vec = ((reinterpret_cast<uintptr_t>(C) & 15u) == 0) && (ldc % 4 == 0);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -2574,6 +2594,23 @@ __global__ void __launch_bounds__(256, 2) sgemm_simt_kernel(
     }
 }
 
+template <bool TA, bool TB>
+cudaError_t launch_sgemm_tiles(dim3 grid, cudaStream_t s, const qcs_gemm_desc_t *desc, int64_t m,
+                               int64_t n, int64_t k, float alpha, const float *A, int64_t lda,
+                               const float *B, int64_t ldb, float beta, float *C, int64_t ldc) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(sgemm_simt_kernel<TA, TB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kRSmemBytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    sgemm_simt_kernel<TA, TB><<<grid, 256, kRSmemBytes, s>>>(desc, m, n, k, alpha, A, lda, B, ldb,
+                                                             beta, C, ldc);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_sgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int64_t m,
@@ -2584,9 +2621,10 @@ cudaError_t launch_sgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
     const int64_t gx = (m + kRT - 1) / kRT, gy = (n + kRT - 1) / kRT;
     if (gx > INT32_MAX) return cudaErrorInvalidValue;
     dim3 grid((unsigned)gx, (unsigned)(gy < 65535 ? gy : 65535));
-    sgemm_simt_kernel<<<grid, 256, 0, s>>>(desc, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C,
-                                           ldc);
-    return cudaGetLastError();
+    const bool ta = opA != QCS_OP_N, tb = opB != QCS_OP_N;
+    auto launch = ta ? (tb ? launch_sgemm_tiles<true, true> : launch_sgemm_tiles<true, false>)
+                     : (tb ? launch_sgemm_tiles<false, true> : launch_sgemm_tiles<false, false>);
+    return launch(grid, s, desc, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
 }  // namespace qcs

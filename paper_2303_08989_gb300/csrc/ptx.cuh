@@ -76,6 +76,12 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src, uint32_t s
                  "l"(reinterpret_cast<uint64_t>(src)), "r"(src_bytes)
                  : "memory");
 }
+// The same for 4 bytes.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(src_bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
