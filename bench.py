@@ -64,7 +64,8 @@ def parse(argv=None):
     p.add_argument("--greedy-workers", type=int, default=min(16, os.cpu_count() or 1),
                    help="host processes that cost the seeded orders")
     p.add_argument("--sweep-sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192, 16384])
-    p.add_argument("--profile", choices=["slice", "slice_seed2", "gather", "gemm", "sgemm"],
+    p.add_argument("--profile", choices=["slice", "slice_seed2", "gather", "gemm", "sgemm",
+                                         "scaling"],
                    default=None,
                    help="run one workload for an ncu capture (NVTX range 'measure') and exit: "
                         "'slice' one group of 16 slices of the 30-qubit network in the cheapest "
@@ -72,7 +73,9 @@ def parse(argv=None):
                         "slice in the "
                         "order of seed 2, 'gather' a random permutation of 2^26 elements, 'gemm' "
                         "ten qcs_cgemm calls of --gemm-shape in --mode, 'sgemm' ten qcs_sgemm "
-                        "calls of --gemm-shape in --mode")
+                        "calls of --gemm-shape in --mode, 'scaling' the exponent spread of the "
+                        "large GEMM operands of the 5x6 depth-14 network (order of seed 2) under "
+                        "one scale per matrix, per row of op(A) and per column of op(B)")
     p.add_argument("--complex-products", type=int, choices=[3, 4], default=4,
                    help="with --profile gemm: real products per complex product (3: Gauss)")
     p.add_argument("--gemm-shape", type=int, nargs=3, default=[2048, 8192, 32],
@@ -282,6 +285,69 @@ def run_reference(args, rank: int):
 # our arm
 # ---------------------------------------------------------------------------
 
+def scaling_probe(args):
+    """Per-row / per-column power-of-two scaling (a variant beyond Section
+    4.1's one scale per matrix) on the operands a contraction feeds its large
+    GEMMs.  Instance 0 of the 5x6 depth-14 network in the greedy order of
+    seed 2 is contracted step by step with qcs_cgemm in plain FP32 (the
+    intermediates carry FP32 rounding, as on the emulated path); for every
+    step with m n k >= 2^33 it prints the fraction of op(A)'s and op(B)'s
+    nonzero scalars below the window [e_max - 28, e_max] that scaling keeps,
+    with e_max taken over the whole matrix (the paper), over each row of
+    op(A) and over each column of op(B) (scales that the epilogue can undo
+    exactly, 2^-(r_i + c_j))."""
+    import torch
+
+    import paper_2303_08989_gb300 as q
+    import paper_2303_08989_gb300.tn as tn
+    import qcs_inputs as qi
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+
+    def fractions(X, per_row):
+        v = torch.view_as_real(X).abs()
+        nz = v > 0
+        e = torch.frexp(v)[1].to(torch.int32) - 1  # floor(log2 |x|) of the nonzero scalars
+        e = torch.where(nz, e, torch.full_like(e, -1000))
+        n = max(int(nz.sum()), 1)
+        emax = int(e.max())
+        local = e.amax(dim=(1, 2) if per_row else (0, 2), keepdim=True)
+        return (emax, int(((e < emax - 28) & nz).sum()) / n,
+                int(((e < local - 28) & nz).sum()) / n)
+
+    circ = qi.random_grid_circuit(5, 6, 14, seed=0)
+    bits = qi.random_bitstrings(30, 1, seed=1)
+    net = tn.circuit_network(circ, bits)
+    order = tn.greedy_order(net, seed=2, skip=[tn.BATCH])
+    plan = tn.build_plan(net, order, tn.choose_slices(net, order, n_labels=6, skip=[tn.BATCH]))
+    h = q.Handle(size_rule=False)
+    nl = len(plan.net.leaves)
+    leaves = [torch.from_numpy(lf.data).to(dev) for lf in plan.net.leaves]
+    tens = []
+
+    def src(i):
+        return leaves[i][int(plan.instance_offset[0, i]):] if i < nl else tens[i - nl]
+
+    rows = []
+    for s, st in enumerate(plan.steps):
+        A = torch.as_strided(src(st.a), tuple(st.map_a[0][::-1]), tuple(st.map_a[1][::-1]))
+        B = torch.as_strided(src(st.b), tuple(st.map_b[0][::-1]), tuple(st.map_b[1][::-1]))
+        A = q.to_fortran(A.reshape(st.k, st.m).t(), device=dev)
+        B = q.to_fortran(B.reshape(st.n, st.k).t(), device=dev)
+        C = q.cgemm(h, A, B, mode="fp32")
+        if st.m * st.n * st.k >= 2 ** 33:
+            ea, ga, la = fractions(A, True)
+            eb, gb, lb = fractions(B, False)
+            rows.append({"step": s, "m": st.m, "n": st.n, "k": st.k,
+                         "A": {"e_max": ea, "below_window_per_matrix": ga, "per_row": la},
+                         "B": {"e_max": eb, "below_window_per_matrix": gb, "per_column": lb}})
+        tens.append(C.t().reshape(-1))
+        del A, B
+    h.close()
+    print(json.dumps({"profile": "scaling", "steps": rows}), flush=True)
+
+
 def profile_run(args):
     """One workload between torch.cuda.nvtx range 'measure' (after one
     untimed run), for ``ncu --nvtx --nvtx-include "measure/"``; prints a
@@ -377,6 +443,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.profile == "scaling":
+        scaling_probe(args)
         return
     if args.profile:
         profile_run(args)
