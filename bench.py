@@ -84,6 +84,9 @@ def parse(argv=None):
                    help="with --profile slice*: load the size-rule tuning table from this JSON "
                         "file if it exists, else measure it and write it there (a run under ncu "
                         "would measure distorted times: ncu slows every launch)")
+    p.add_argument("--no-absorb", action="store_true",
+                   help="contract the networks with their single-qubit gates as separate leaves "
+                        "(default: absorbed into their neighbours on the host first)")
     p.add_argument("--instance-batch", type=int, default=16,
                    help="contraction instances per group (plain-FP32 steps batched)")
     p.add_argument("--legs-file", default=None,
@@ -1233,11 +1236,12 @@ def tree_legs(args, q, torch, dev, rank, world=1, dist=None):
     # contracted in the cheapest of --greedy-trials seeded greedy orders
     circ = qi.random_grid_circuit(5, 6, 14, seed=0)
     bits = qi.random_bitstrings(30, 1, seed=1)
-    net = tn.circuit_network(circ, bits)
+    net_full = tn.circuit_network(circ, bits)
+    nets = [net_full] + ([] if args.no_absorb else [tn.absorb_single_qubit_gates(net_full)])
     t0 = time.perf_counter()
-    order, sliced, seed_used = tn.best_greedy_order(net, range(args.greedy_trials),
-                                                    skip=[tn.BATCH], n_slices=6,
-                                                    workers=args.greedy_workers)
+    which, order, sliced, seed_used = tn.cheapest_network_order(
+        nets, range(args.greedy_trials), skip=[tn.BATCH], n_slices=6, workers=args.greedy_workers)
+    net = nets[which]
     planning_s = time.perf_counter() - t0
     plans = {}
 
@@ -1270,6 +1274,7 @@ def tree_legs(args, q, torch, dev, rank, world=1, dist=None):
                     "64 slices vs the FP64 state vector"
                     % (args.greedy_trials, args.greedy_trials - 1, args.tol, ns),
         "greedy_seed": seed_used, "planning_s": planning_s,
+        "single_qubit_gates_absorbed": which == 1, "steps": len(p.steps),
         "slices_total": p.n_instances, "flops_per_slice": p.flops,
         "max_intermediate_log2": p.max_log2_size,
         "auto": per["auto"], "auto_t0.5": per["auto_t0.5"],
@@ -1281,12 +1286,12 @@ def tree_legs(args, q, torch, dev, rank, world=1, dist=None):
         res["contraction_sharded"] = sharded_leg(args, q, tn, torch, dev, p, ref, rank, world, dist)
     # the same network in the order of greedy seed 2 alone: 12x the flops per
     # slice, in larger GEMMs (the regime where one large GEMM dominates)
-    order2 = tn.greedy_order(net, seed=2, skip=[tn.BATCH])
-    sliced2 = tn.choose_slices(net, order2, n_labels=6, skip=[tn.BATCH])
+    order2 = tn.greedy_order(net_full, seed=2, skip=[tn.BATCH])
+    sliced2 = tn.choose_slices(net_full, order2, n_labels=6, skip=[tn.BATCH])
     plans2 = {}
 
     def make_plan2(mode):
-        plans2[mode] = tn.build_plan(net, order2, sliced2, mode=mode)
+        plans2[mode] = tn.build_plan(net_full, order2, sliced2, mode=mode)
         return plans2[mode]
 
     per2 = _contract_variants(args, q, tn, torch, dev, make_plan2, 4,
@@ -1306,7 +1311,7 @@ def tree_legs(args, q, torch, dev, rank, world=1, dist=None):
     # plain method, smallest size: 3x4 grid, depth 8, 64 bitstrings (FP32 path by the size rule)
     c0 = qi.random_grid_circuit(3, 4, 8, seed=0)
     b0 = qi.random_bitstrings(12, 64, seed=1)
-    p0 = tn.plan_circuit(c0, b0, seed=2)
+    p0 = tn.plan_circuit(c0, b0, seed=2, absorb=not args.no_absorb)
     cp0 = tn.CompiledPlan(p0, device=dev)
     secs0, out0 = _time_plan(torch, cp0, h, reps=3)
     secs_g, _ = _time_graph(torch, cp0, h, reps=3)
@@ -1330,20 +1335,23 @@ def tree_legs(args, q, torch, dev, rank, world=1, dist=None):
     b4 = qi.random_bitstrings(20, 256, seed=1)
     p0s = np.array([g.params for g in c4.gates if g.name == "fsim"])
     diff = {}
-    net4 = tn.circuit_network(c4, None)
+    net4_full = tn.circuit_network(c4, None)
+    # the parametric fSim leaves stay as they are
+    nets4 = [net4_full] + ([] if args.no_absorb else
+                           [tn.absorb_single_qubit_gates(net4_full, frozen_gates=c4.fsim_indices())])
     # the greedy order of seed 2 (4.2e11 flops per slice: the adjoint GEMMs are
     # large enough for the tensor cores) and the cheapest of --greedy-trials orders
-    o_s2 = tn.greedy_order(net4, seed=2)
-    orders = {"seed2": (o_s2, tn.choose_slices(net4, o_s2, n_labels=2))}
-    o_b, sl_b, _ = tn.best_greedy_order(net4, range(args.greedy_trials), n_slices=2,
-                                        workers=args.greedy_workers)
-    orders["cheapest"] = (o_b, sl_b)
+    o_s2 = tn.greedy_order(net4_full, seed=2)
+    orders = {"seed2": (net4_full, o_s2, tn.choose_slices(net4_full, o_s2, n_labels=2))}
+    w4, o_b, sl_b, _ = tn.cheapest_network_order(nets4, range(args.greedy_trials), n_slices=2,
+                                                 workers=args.greedy_workers)
+    orders["cheapest"] = (nets4[w4], o_b, sl_b)
     for mode, rule, which in (("auto", q.SIZE_RULE_TUNED, "seed2"),
                               ("fp32", q.SIZE_RULE_PAPER, "seed2"),
                               ("auto_cheapest_order", q.SIZE_RULE_TUNED, "cheapest"),
                               ("fp32_cheapest_order", q.SIZE_RULE_PAPER, "cheapest")):
         hd = q.Handle(tol=args.tol, size_rule=rule)
-        order, sliced = orders[which]
+        net4, order, sliced = orders[which]
         plan = tn.build_plan(net4, order, sliced, mode=q.MODE_BY_NAME[mode.split("_")[0]],
                              outputs=b4)
         cp = tn.CompiledPlan(plan, device=dev, leaf_data=[])
@@ -1390,7 +1398,8 @@ def tree_legs(args, q, torch, dev, rank, world=1, dist=None):
                                "fp32_s_eager": diff["fp32_cheapest_order"]["s_fwd_bwd_eager"],
                                "note": "the cheapest of %d seeded greedy orders: 100x and more "
                                        "fewer flops, GEMMs too small for emulation to matter"
-                                       % args.greedy_trials}}
+                                       % args.greedy_trials,
+                               "single_qubit_gates_absorbed": w4 == 1}}
     if rank == 0:
         import oracle
 
@@ -1464,10 +1473,13 @@ def scale_leg(args, q, torch, dev, tn, qi, rank):
                 rows.append((v, float(re) + 1j * float(im)))
     circ = qi.random_grid_circuit(5, 8, 12, seed=0)
     bits = qi.random_bitstrings(40, 1, seed=1)
-    net = tn.circuit_network(circ, bits)
-    order, _, seed_used = tn.best_greedy_order(net, range(args.greedy_trials),
-                                               skip=[tn.BATCH] + labels,
-                                               workers=args.greedy_workers)
+    net_full = tn.circuit_network(circ, bits)
+    # absorbed or not, the oracle's sliced labels survive
+    nets = [net_full] + ([] if args.no_absorb else
+                         [tn.absorb_single_qubit_gates(net_full, keep_labels=labels)])
+    which, order, _, seed_used = tn.cheapest_network_order(
+        nets, range(args.greedy_trials), skip=[tn.BATCH] + labels, workers=args.greedy_workers)
+    net = nets[which]
     plans = {}
 
     def make_plan(mode):
@@ -1483,7 +1495,8 @@ def scale_leg(args, q, torch, dev, tn, qi, rank):
                        "cheapest of %d seeded greedy orders of the sliced network, 1 bitstring; "
                        "AUTO-%g (measured size rule) vs all-FP32, CUDA-graph replays of 16 "
                        "slices" % (args.greedy_trials, args.tol),
-           "greedy_seed": seed_used,
+           "greedy_seed": seed_used, "single_qubit_gates_absorbed": which == 1,
+           "steps": len(plan.steps),
            "flops_per_slice": plan.flops, "max_intermediate_log2": plan.max_log2_size}
     idx = [int(v, 2) for v, _ in rows]
     sub = copy.copy(plan)

@@ -92,6 +92,78 @@ def circuit_network(circ, bitstrings: Optional[np.ndarray] = None) -> Network:
     return Network(leaves, [], dims, batch=B)
 
 
+def _merge_gate(T: Leaf, g: Leaf, elim: int) -> Leaf:
+    """T contracted with the single-qubit gate leaf g (labels [out, in]) over
+    label ``elim`` of T: elim = in (T produces the gate's input) gives
+    T'[..., out, ...] = sum_in g[out, in] T[..., in, ...]; elim = out (T
+    consumes its output) gives T'[..., in, ...] = sum_out T[..., out, ...]
+    g[out, in].  The label keeps its position; arithmetic in complex128."""
+    out_l, in_l = g.labels
+    G = g.data.astype(np.complex128).reshape((2, 2), order="F")  # G[out, in]
+    t = T.data.astype(np.complex128).reshape(T.dims, order="F")
+    ax = T.labels.index(elim)
+    if elim == in_l:
+        t = np.moveaxis(np.tensordot(G, t, axes=([1], [ax])), 0, ax)
+        new = out_l
+    else:
+        t = np.moveaxis(np.tensordot(G, t, axes=([0], [ax])), 0, ax)
+        new = in_l
+    labels = list(T.labels)
+    labels[ax] = new
+    return Leaf(_fortran_flat(t), labels, list(T.dims), T.kind, T.gate)
+
+
+def absorb_single_qubit_gates(net: Network, frozen_gates: Sequence[int] = (),
+                              keep_labels: Sequence[int] = ()) -> Network:
+    """The same network with every single-qubit gate contracted, on the host,
+    into the tensor that produces its input wire (or, when that is not
+    allowed, the tensor that consumes its output): chains of single-qubit
+    gates between two multi-qubit gates become part of the multi-qubit gate's
+    tensor, and those at the start of a wire part of its |0> leaf.  The tree
+    then has none of the (2, 2^N, 2)-shaped steps that contract a 2 x 2 gate
+    into a large intermediate.  ``frozen_gates``: circuit gate indices whose
+    leaves must stay as they are (parametric gates of a differentiated
+    circuit); ``keep_labels``: labels that must survive (e.g. sliced
+    indices; output and bitstring labels always do).  Exact up to complex64
+    rounding of the merged tensors."""
+    leaves = [Leaf(lf.data.copy(), list(lf.labels), list(lf.dims), lf.kind, lf.gate)
+              for lf in net.leaves]
+    frozen = set(frozen_gates)
+    keep = set(keep_labels) | set(net.output) | {BATCH}
+    alive = [True] * len(leaves)
+    holders: Dict[int, set] = {}
+    for i, lf in enumerate(leaves):
+        for l in lf.labels:
+            holders.setdefault(l, set()).add(i)
+
+    def other(label, i):
+        h = [j for j in holders.get(label, ()) if j != i and alive[j]]
+        return h[0] if h else None
+
+    def mutable(j):
+        return not (leaves[j].kind == "gate" and leaves[j].gate in frozen)
+
+    for i, lf in enumerate(leaves):
+        if not (lf.kind == "gate" and len(lf.labels) == 2 and lf.gate not in frozen):
+            continue
+        out_l, in_l = lf.labels
+        p, c = other(in_l, i), other(out_l, i)
+        if p is not None and in_l not in keep and mutable(p):
+            tgt, elim, new = p, in_l, out_l
+        elif c is not None and out_l not in keep and mutable(c):
+            tgt, elim, new = c, out_l, in_l
+        else:
+            continue
+        leaves[tgt] = _merge_gate(leaves[tgt], lf, elim)
+        holders[elim].discard(tgt)
+        holders[elim].discard(i)
+        holders[new].discard(i)
+        holders[new].add(tgt)
+        alive[i] = False
+    return Network([lf for lf, a in zip(leaves, alive) if a], list(net.output), dict(net.dims),
+                   net.batch)
+
+
 # ---------------------------------------------------------------------------
 # contraction order
 # ---------------------------------------------------------------------------
@@ -750,14 +822,35 @@ def contract(cp: CompiledPlan, h, leaves):
     return _FN.apply(cp, h, *leaves)
 
 
+def cheapest_network_order(nets: Sequence[Network], seeds: Sequence[int],
+                           skip: Sequence[int] = (), n_slices: int = 0,
+                           max_log2_size: Optional[float] = None, workers: int = 1):
+    """best_greedy_order over each of several equivalent networks (e.g. a
+    circuit's network with and without absorb_single_qubit_gates); returns
+    (index of the network, order, sliced labels, seed) of the one whose best
+    order has the fewest flops per instance (ties: the earlier network)."""
+    best = None
+    for i, nw in enumerate(nets):
+        order, sliced, seed = best_greedy_order(nw, seeds, skip=skip, n_slices=n_slices,
+                                                max_log2_size=max_log2_size, workers=workers)
+        flops, _ = order_cost(nw, order, skip=list(skip) + list(sliced))
+        if best is None or flops < best[0]:
+            best = (flops, i, order, sliced, seed)
+    return best[1:]
+
+
 def plan_circuit(circ, bitstrings=None, seed: int = 2, n_slices: int = 0,
                  max_log2_size: Optional[float] = None, mode: int = 0, trials: int = 1,
-                 workers: int = 1) -> Plan:
+                 workers: int = 1, absorb: bool = False) -> Plan:
     """circuit -> network -> greedy order (seeded) -> slices -> plan.
     ``n_slices``: number of sliced indices (2**n_slices slices).  ``trials``
     > 1: the cheapest of the greedy orders of seeds seed .. seed + trials - 1
-    (best_greedy_order, costed in ``workers`` processes)."""
+    (best_greedy_order, costed in ``workers`` processes).  ``absorb``: the
+    single-qubit gates contracted into their neighbours first
+    (absorb_single_qubit_gates)."""
     net = circuit_network(circ, bitstrings)
+    if absorb:
+        net = absorb_single_qubit_gates(net)
     skip = [BATCH] if net.batch else []
     if trials > 1:
         order, sliced, _ = best_greedy_order(net, range(seed, seed + trials), skip=skip,

@@ -51,6 +51,21 @@ def test_plain_method_small_grid_fp32(h):
     assert info.mode_count[4] == info.gemm_count  # all plain FP32 under the size rule
 
 
+def test_plain_method_small_grid_with_absorbed_gates(h):
+    """The same 12-qubit workload with the single-qubit gates contracted into
+    their neighbours on the host (a third of the steps), against the FP64
+    state vector."""
+    tn = _tn()
+    circ = qi.random_grid_circuit(3, 4, 8, seed=0)
+    bits = qi.random_bitstrings(12, 64, seed=1)
+    plan = tn.plan_circuit(circ, bits, seed=2, absorb=True)
+    assert len(plan.steps) < len(tn.plan_circuit(circ, bits, seed=2).steps) // 2
+    got, _ = _run(h, plan)
+    ref = oracle.sv_amplitudes(circ, bits)
+    assert oracle.fidelity(ref, got[:, 0]) >= 1 - 1e-5
+    assert np.max(np.abs(got[:, 0] - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
 @pytest.mark.parametrize("mode", ["fp16x", "tf32x", "fp16x_scaled", "auto"])
 def test_emulated_modes_on_every_step(h, mode):
     tn = _tn()
@@ -183,7 +198,8 @@ def test_full_size_30_qubit_sliced_amplitudes_vs_fp64_golden(h, golden_dir):
     assert info.mode_count[0] > 0  # some GEMMs took the statistics-based selection
 
 
-def test_full_size_30_qubit_in_the_bench_configuration_vs_fp64_golden(golden_dir):
+@pytest.mark.parametrize("absorb", [False, True])
+def test_full_size_30_qubit_in_the_bench_configuration_vs_fp64_golden(golden_dir, absorb):
     """The contraction in bench.py's configuration: the cheapest of many
     seeded greedy orders (256 here), 6 sliced indices, instances in groups
     of 16 (grouped tensor-core
@@ -197,8 +213,11 @@ def test_full_size_30_qubit_in_the_bench_configuration_vs_fp64_golden(golden_dir
     q = lib()
     bits_all, ref_all = _golden_amplitudes(os.path.join(golden_dir, "grid5x6_d14_amplitudes.txt"))
     circ = qi.random_grid_circuit(5, 6, 14, seed=0)
-    bits, ref = bits_all[2:4], ref_all[2:4]
-    plan = tn.plan_circuit(circ, bits, seed=0, n_slices=6, mode=q.MODE_AUTO, trials=256)
+    bits, ref = (bits_all[4:6], ref_all[4:6]) if absorb else (bits_all[2:4], ref_all[2:4])
+    plan = tn.plan_circuit(circ, bits, seed=0, n_slices=6, mode=q.MODE_AUTO, trials=256,
+                           absorb=absorb, workers=8)
+    if absorb:  # the single-qubit gates are part of their neighbours' tensors
+        assert len(plan.steps) < len(tn.circuit_network(circ, bits).leaves) // 2
     assert plan.n_instances == 2 * 64 and plan.max_log2_size <= 25
     hd = q.Handle(tol=0.1, size_rule=q.SIZE_RULE_TUNED)
     try:

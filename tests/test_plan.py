@@ -139,3 +139,51 @@ def test_best_greedy_order_in_worker_processes_matches_serial():
     serial = tn.best_greedy_order(net, range(5, 29), skip=skip, n_slices=3)
     parallel = tn.best_greedy_order(net, range(5, 29), skip=skip, n_slices=3, workers=3)
     assert serial == parallel
+
+
+def test_absorbing_single_qubit_gates_keeps_the_amplitudes():
+    """Single-qubit gates contracted into their neighbours on the host: a
+    third of the leaves remain, and the plan interpreter's amplitudes equal
+    those of the full network and the oracle's state vector (up to the
+    complex64 rounding of the merged tensors)."""
+    import oracle
+
+    circ = qi.random_grid_circuit(3, 3, 8, seed=4)
+    bits = qi.random_bitstrings(9, 6, seed=5)
+    net = tn.circuit_network(circ, bits)
+    small = tn.absorb_single_qubit_gates(net)
+    n1 = sum(1 for g in circ.gates if len(g.qubits) == 1)
+    assert len(small.leaves) == len(net.leaves) - n1
+    assert not [lf for lf in small.leaves if lf.kind == "gate" and len(lf.labels) == 2]
+    ref = oracle.sv_amplitudes(circ, bits)
+    for nw in (net, small):
+        order = tn.greedy_order(nw, seed=1, skip=[tn.BATCH])
+        plan = tn.build_plan(nw, order, tn.choose_slices(nw, order, n_labels=2, skip=[tn.BATCH]))
+        got = run(plan, [lf.data for lf in plan.net.leaves])[:, 0]
+        np.testing.assert_allclose(got, ref, atol=2e-6)
+
+
+def test_absorption_respects_frozen_gates_and_kept_labels():
+    circ = qi.random_grid_circuit(2, 3, 6, seed=4, theta=None, phi=None, param_seed=5)
+    net = tn.circuit_network(circ, None)
+    fs = set(circ.fsim_indices())
+    small = tn.absorb_single_qubit_gates(net, frozen_gates=fs)
+    before = {lf.gate: lf for lf in net.leaves if lf.kind == "gate" and lf.gate in fs}
+    after = {lf.gate: lf for lf in small.leaves if lf.kind == "gate" and lf.gate in fs}
+    assert before.keys() == after.keys()
+    for g, lf in after.items():  # parametric leaves untouched
+        assert lf.labels == before[g].labels and np.array_equal(lf.data, before[g].data)
+    assert len(small.leaves) < len(net.leaves)
+    # the same network, frozen or not, gives the same state
+    import oracle
+
+    ref = oracle.statevector(circ).ravel()
+    order = tn.greedy_order(small, seed=1)
+    plan = tn.build_plan(small, order, [])
+    got = run(plan, [lf.data for lf in plan.net.leaves])[0]
+    np.testing.assert_allclose(got, ref, atol=2e-6)
+    # kept labels survive
+    lab = [lf.labels[1] for lf in net.leaves if lf.kind == "gate" and len(lf.labels) == 2][:3]
+    kept = tn.absorb_single_qubit_gates(net, keep_labels=lab)
+    present = {l for lf in kept.leaves for l in lf.labels}
+    assert set(lab) <= present
