@@ -505,7 +505,13 @@ int qcs_cgemm_noalloc_status(void *cuda_stream, int reset);
  * qcs_set_tc_splits) that ran the faster emulated candidate fastest; under
  * QCS_SIZE_RULE_TUNED the tensor-core GEMMs of this shape use it unless
  * qcs_set_tc_splits forces a count.  0: not measured (the per-shape rule
- * applies); ms[] of the emulated candidate is its time at that count. */
+ * applies); ms[] of the emulated candidate is its time at that count.
+ * group_m is the tensor-core raster measured for the shape (tile rows per
+ * raster group, see qcs_set_tc_schedule) for shapes with at least twice as
+ * many 128 x 128 output tiles as SMs; under QCS_SIZE_RULE_TUNED the
+ * tensor-core GEMMs of this shape use it.  0: not measured (the handle's
+ * schedule applies).  The raster only orders the tiles: results do not
+ * depend on it. */
 typedef struct {
     int64_t m, n, k;
     int32_t opA, opB;
@@ -513,7 +519,7 @@ typedef struct {
     int32_t best;
     int32_t reps;
     int32_t splits;
-    int32_t reserved;
+    int32_t group_m;
 } qcs_tune_entry_t;
 
 /* Time the candidates for one shape on the handle's stream and record the
@@ -527,7 +533,9 @@ typedef struct {
  * shape with fewer 128 x 128 output tiles than twice the SM count, the
  * faster emulated candidate is also timed at 1, 2, 4, 8 and 16 K ranges
  * (at most one per 32 k; not when qcs_set_tc_splits forces a count) and the
- * fastest count is recorded in ``splits``.
+ * fastest count is recorded in ``splits``; for a shape with more tiles, it
+ * is timed with raster groups of 2, 4, 8 and 16 tile rows and the fastest is
+ * recorded in ``group_m``.
  * Synchronizes the stream; not during a stream capture.  out (host,
  * optional) receives the entry.  m, n, k >= 1. */
 int qcs_autotune_gemm(qcs_handle_t h, qcs_op_t transA, qcs_op_t transB, int64_t m, int64_t n,

@@ -149,6 +149,7 @@ class Handle:
             e.best = MODE_BY_NAME[d["best"]]
             e.reps = d.get("reps", 0)
             e.splits = d.get("splits", 0)
+            e.group_m = d.get("group_m", 0)
         _lib.check(self.lib.qcs_set_tuning(self._h, arr, len(entries)), "qcs_set_tuning")
 
     def set_instance_batch(self, instances: int):
@@ -232,7 +233,7 @@ class Handle:
 def _tune_dict(e) -> dict:
     return {"m": e.m, "n": e.n, "k": e.k, "opA": e.opA, "opB": e.opB,
             "ms": {MODE_NAME[j]: e.ms[j] for j in range(_lib.NUM_MODES) if e.ms[j] >= 0},
-            "best": MODE_NAME[e.best], "reps": e.reps, "splits": e.splits}
+            "best": MODE_NAME[e.best], "reps": e.reps, "splits": e.splits, "group_m": e.group_m}
 
 
 def cgemm(h: Handle, A, B, C=None, *, m=None, n=None, k=None, alpha=1.0, beta=0.0,

@@ -75,7 +75,7 @@ class qcs_tune_entry_t(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
                 ("opA", ctypes.c_int32), ("opB", ctypes.c_int32),
                 ("ms", ctypes.c_float * 6), ("best", ctypes.c_int32), ("reps", ctypes.c_int32),
-                ("splits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("splits", ctypes.c_int32), ("group_m", ctypes.c_int32)]
 
 
 class qcs_gather_t(ctypes.Structure):

@@ -103,6 +103,8 @@ int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k
     fill_unit_binade<<<grid, 256, 0, h->stream>>>(dB, rb * cb, 0xA2A2ull);
     if (cudaGetLastError() != cudaSuccess) return QCS_ERR_CUDA;
 
+    // a new measurement replaces the table's entry, which must not steer it
+    h->tuned.erase(std::make_tuple(m, n, k, opA, opB));
     qcs_tune_entry_t e{};
     e.m = m;
     e.n = n;
@@ -166,6 +168,26 @@ int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k
         e.ms[emu] = best_ms;
         e.splits = best_s;
     }
+    // The raster: with many output tiles, time the faster emulated candidate
+    // with groups of 2, 4, 8 and 16 tile rows and keep the fastest.
+    if (rc == QCS_SUCCESS && tiles >= 2 * (int64_t)h->num_sms) {
+        const int emu = e.ms[QCS_MODE_TF32X] < e.ms[QCS_MODE_AUTO] ? QCS_MODE_TF32X : QCS_MODE_AUTO;
+        const int handle_gm = h->tc_group_m;
+        int best_g = handle_gm;
+        float best_ms = e.ms[emu];
+        for (int g : {2, 4, 8, 16}) {
+            if (g == handle_gm) continue;
+            h->tc_group_m = g;
+            if ((rc = time_mode(emu)) != QCS_SUCCESS) break;
+            if (e.ms[emu] < best_ms) {
+                best_ms = e.ms[emu];
+                best_g = g;
+            }
+        }
+        h->tc_group_m = handle_gm;
+        e.ms[emu] = best_ms;
+        e.group_m = best_g;
+    }
     h->tc_splits = forced_splits;
     if (rc == QCS_SUCCESS) {
         const float emulated = std::min(e.ms[QCS_MODE_AUTO], e.ms[QCS_MODE_TF32X]);
@@ -225,7 +247,7 @@ int qcs_set_tuning(qcs_handle_t h, const qcs_tune_entry_t *entries, int64_t coun
         const qcs_tune_entry_t &e = entries[i];
         if (e.m < 1 || e.n < 1 || e.k < 1 || !valid_tune_op(e.opA) || !valid_tune_op(e.opB) ||
             (e.best != QCS_MODE_AUTO && e.best != QCS_MODE_TF32X && e.best != QCS_MODE_FP32) ||
-            e.splits < 0 || e.splits > kMaxSplits)
+            e.splits < 0 || e.splits > kMaxSplits || e.group_m < 0 || e.group_m > 64)
             return QCS_ERR_INVALID_ARG;
     }
     for (int64_t i = 0; i < count; ++i) {

@@ -163,6 +163,16 @@ int qcs::gemm_splits(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int
     return 0;
 }
 
+// Raster of a tensor-core GEMM of this shape: the group the tuner measured
+// for it (under the tuned size rule), else the handle's schedule.
+int qcs::gemm_group_m(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k) {
+    if (h->size_rule == QCS_SIZE_RULE_TUNED) {
+        const auto it = h->tuned.find(std::make_tuple(m, n, k, opA, opB));
+        if (it != h->tuned.end() && it->second.group_m > 0) return it->second.group_m;
+    }
+    return h->tc_group_m;
+}
+
 // The whole emulated CGEMM on the handle's stream.  desc_ws/partials/planes
 // come from ``ws`` (a device buffer of at least gemm_workspace_bytes()).
 namespace qcs {
@@ -267,6 +277,7 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                     const GemmBatch &bt) {
     cudaStream_t s = h->stream;
     if (G < 1) return QCS_ERR_INVALID_ARG;
+    const int gm = gemm_group_m(h, opA, opB, m, n, k);
     if (bt.count != 1 && (eff != QCS_MODE_FP32 || k == 0 || d_desc_out || d_desc_in || G != 1 ||
                           A_in[0].map || B_in[0].map))
         return QCS_ERR_UNSUPPORTED;
@@ -401,13 +412,13 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                     return QCS_ERR_CUDA;
                 const int kind = (eff == QCS_MODE_BF16X3) ? 2 : 0;
                 e = launch_cgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
-                                    ldc, h->d_err, h->num_sms, h->tc_group_m, s, w);
+                                    ldc, h->d_err, h->num_sms, gm, s, w);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             }
             if (need32 && tf32_fused) {
                 e = launch_cgemm_tc_fused(h->encode, desc, opA, opB, m, n, k, alpha, A0.X, A0.ld,
                                           B0.X, B0.ld, beta, C, ldc, h->d_err, h->num_sms,
-                                          h->tc_group_m, w, s);
+                                          gm, w, s);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             } else if (need32) {
                 CUtensorMap ma, mb;
@@ -415,7 +426,7 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                     encode_planes(h, &mb, planesB32, G * np, kp, 4, kPlanesB))
                     return QCS_ERR_CUDA;
                 e = launch_cgemm_tc(1, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
-                                    ldc, h->d_err, h->num_sms, h->tc_group_m, s, w);
+                                    ldc, h->d_err, h->num_sms, gm, s, w);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             }
             e = launch_tc_reduce(desc, m, n, alpha, beta, C, ldc, h->num_sms, w, s);

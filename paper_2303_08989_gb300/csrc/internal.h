@@ -228,6 +228,8 @@ cudaError_t launch_seed_grad(const double *g, const int64_t *index, float2 *grad
 int effective_mode(qcs_handle_t h, int mode, int opA, int opB, int64_t m, int64_t n, int64_t k);
 // K-range setting for a GEMM of this shape: forced, tuned, or 0 (per-shape rule).
 int gemm_splits(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k);
+// Raster group of the tensor-core GEMMs of this shape (tuned, else the handle's).
+int gemm_group_m(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k);
 // Time the candidate modes of one shape (qcs_autotune_gemm without validation).
 int tune_shape(qcs_handle_t h, int opA, int opB, int64_t m, int64_t n, int64_t k, int reps,
                qcs_tune_entry_t *out);

@@ -165,3 +165,37 @@ def test_autotune_measures_the_k_range_count():
             hd.set_tuning([dict(e, splits=17)])
     finally:
         hd.close()
+
+
+def test_tuner_measures_the_raster_and_results_do_not_depend_on_it():
+    """Shapes with at least twice as many output tiles as SMs get a raster
+    group measured by the tuner; under the tuned rule the table's raster is
+    used, and changing it only reorders tiles (the same bits)."""
+    need_gpu()
+    q = lib()
+    hd = q.Handle(tol=0.1, size_rule=False)
+    try:
+        e = hd.autotune_gemm(4096, 4096, 1024, reps=1)  # 1024 tiles of 128 x 128
+        assert e["group_m"] in (2, 4, 8, 16), e
+        small = hd.autotune_gemm(1024, 1024, 1024, reps=1)  # 64 tiles: K ranges instead
+        assert small["group_m"] == 0
+        m, n, k = 2048, 2304, 256
+        A = dev(qi.cgemm_operand(m, k, 0, seed=(61, 1)))
+        B = dev(qi.cgemm_operand(k, n, 0, seed=(61, 2)))
+        outs = []
+        hd.set_size_rule(q.SIZE_RULE_TUNED)
+        for gm in (1, 3, 16):
+            hd.set_tuning([{"m": m, "n": n, "k": k, "opA": 0, "opB": 0, "ms": {}, "best": "auto",
+                            "splits": 1, "group_m": gm}])
+            assert [t["group_m"] for t in hd.tuning() if (t["m"], t["n"], t["k"]) == (m, n, k)] == [gm]
+            outs.append(q.cgemm(hd, A, B, mode="auto"))
+            torch.cuda.synchronize()
+            hd.sync()
+        assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+        from paper_2303_08989_gb300 import _lib as L
+
+        with pytest.raises(L.QcsError):
+            hd.set_tuning([{"m": m, "n": n, "k": k, "opA": 0, "opB": 0, "ms": {}, "best": "auto",
+                            "group_m": 65}])
+    finally:
+        hd.close()
