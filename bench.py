@@ -87,6 +87,9 @@ def parse(argv=None):
     p.add_argument("--no-absorb", action="store_true",
                    help="contract the networks with their single-qubit gates as separate leaves "
                         "(default: absorbed into their neighbours on the host first)")
+    p.add_argument("--no-levels", action="store_true",
+                   help="run contraction trees step by step in plan order (default: level "
+                        "launches of the small plain-FP32 steps, qcs_set_tree_levels)")
     p.add_argument("--instance-batch", type=int, default=16,
                    help="contraction instances per group (plain-FP32 steps batched)")
     p.add_argument("--legs-file", default=None,
@@ -441,6 +444,8 @@ def profile_run(args):
 
 def main():
     args = parse()
+    if args.no_levels:
+        os.environ["QCS_TREE_LEVELS"] = "0"  # read by every handle at creation
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -1207,7 +1212,14 @@ def _contract_variants(args, q, tn, torch, dev, make_plan, ns, variants, full=Fa
                   "instance_batch": args.instance_batch,
                   "workspace_gb": info["workspace_bytes"] / 1e9,
                   "tflops": info["flops"] / gsecs / 1e12, "gemms_per_slice": info["gemm_count"] / ns,
+                  "level_launches_per_slice": info["level_launches"] / ns,
+                  "level_gemm_fraction": round(info["level_gemms"] / max(info["gemm_count"], 1), 4),
                   "routing": _routing(info, counts, cflops)})
+        if name == variants[0][0] and not args.no_levels:
+            # the same variant step by step (one launch sequence per step, plan order)
+            h.set_tree_levels(False)
+            e["s_per_slice_step_by_step"] = _time_graph(torch, cp, h)[0] / ns
+            h.set_tree_levels(True)
         e["_out"] = out.cpu().numpy()
         if full:
             cp.tree.n_instances = n_all

@@ -362,6 +362,8 @@ typedef struct {
     int64_t workspace_bytes;  /* bytes of the tree workspace */
     double flops;             /* nominal 8 m n k summed over the GEMMs */
     double mode_flops[6];     /* the same per effective mode (as mode_count) */
+    int64_t level_launches;   /* level launches issued (qcs_set_tree_levels) */
+    int64_t level_gemms;      /* GEMMs they covered (all instances; part of gemm_count) */
 } qcs_run_info_t;
 
 /* Instances per group of qcs_contract_tree and qcs_tree_graph_create (1 to
@@ -380,6 +382,20 @@ typedef struct {
  * runs one instance at a time (its launches can be captured in a graph:
  * qcs_tree_backward_graph_create). */
 int qcs_set_instance_batch(qcs_handle_t h, int instances);
+
+/* Level launches of the tree executor (Section 2.2: the steps of one level
+ * of the contraction tree are independent).  While ``enabled`` is 1 (the
+ * default; environment override QCS_TREE_LEVELS) the executor runs the
+ * steps of a group level by level (a step's level: one more than its
+ * operands' highest), and the steps of a level whose GEMM runs in plain FP32
+ * (after the size rule) with op(A) and op(B) of at most 1024 elements and C
+ * of at most 4096 -- the gate-sized contractions that make up most of a
+ * circuit's tree -- run as ONE launch for all of them and all instances of
+ * the group, their gathers folded into the operand loads.  Each output
+ * element is the same FP32 sum, term order l = 0 .. k-1 with one FMA per
+ * real product, as the plain-FP32 per-element kernels form.  0: one step
+ * after another in plan order.  QCS_ERR_INVALID_ARG for other values. */
+int qcs_set_tree_levels(qcs_handle_t h, int enabled);
 
 /* Contract the plan for every instance and accumulate into d_out (device,
  * complex128 as interleaved doubles, n_slots * out_size values, slot-major;

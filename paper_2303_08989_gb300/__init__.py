@@ -175,6 +175,12 @@ class Handle:
         _lib.check(self.lib.qcs_set_complex_products(self._h, int(products)),
                    "qcs_set_complex_products")
 
+    def set_tree_levels(self, enabled: bool):
+        """Run a contraction tree level by level, the small plain-FP32 steps
+        of each level as one launch (qcs_set_tree_levels; on by default)."""
+        _lib.check(self.lib.qcs_set_tree_levels(self._h, int(bool(enabled))),
+                   "qcs_set_tree_levels")
+
     def set_fused_split(self, enabled: bool):
         """TF32X split inside the tensor-core kernel's staging
         (qcs_set_fused_split) instead of a separate pass."""

@@ -36,7 +36,7 @@ EXPORTED = [
     "qcs_get_tuning", "qcs_set_tuning", "qcs_set_instance_batch", "qcs_set_tc_schedule",
     "qcs_set_tc_splits", "qcs_sgemm", "qcs_set_complex_products", "qcs_set_wait_budget",
     "qcs_debug_stall_producer", "qcs_cgemm_noalloc_status", "qcs_measure_fma_peak",
-    "qcs_set_fused_split", "qcs_selection_stats", "qcs_tree_backward_graph_create",
+    "qcs_set_fused_split", "qcs_set_tree_levels", "qcs_selection_stats", "qcs_tree_backward_graph_create",
 ]
 SIZE_RULE_OFF, SIZE_RULE_PAPER, SIZE_RULE_TUNED = 0, 1, 2
 NUM_MODES = 6
@@ -104,7 +104,8 @@ class qcs_run_info_t(ctypes.Structure):
     _fields_ = [("seconds", ctypes.c_double), ("gemm_count", ctypes.c_int64),
                 ("gather_count", ctypes.c_int64), ("mode_count", ctypes.c_int64 * 6),
                 ("workspace_bytes", ctypes.c_int64), ("flops", ctypes.c_double),
-                ("mode_flops", ctypes.c_double * 6)]
+                ("mode_flops", ctypes.c_double * 6), ("level_launches", ctypes.c_int64),
+                ("level_gemms", ctypes.c_int64)]
 
 
 _lib = None
@@ -168,6 +169,7 @@ def load(path: str = LIB_PATH):
         "qcs_cgemm_noalloc_status": [P, I],
         "qcs_measure_fma_peak": [H, ctypes.POINTER(ctypes.c_double)],
         "qcs_set_fused_split": [H, I],
+        "qcs_set_tree_levels": [H, I],
         "qcs_selection_stats": [H, I, I, I64, I64, I64, P, I64, P, I64,
                                 ctypes.POINTER(qcs_selection_stats_t), ctypes.POINTER(qcs_gemm_desc_t)],
     }

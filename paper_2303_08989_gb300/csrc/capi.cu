@@ -788,6 +788,7 @@ int qcs_create(qcs_handle_t *out, void *cuda_stream) {
     if (const char *c = std::getenv("QCS_COMPLEX_PRODUCTS"))
         h->complex_products = (std::atoi(c) == 3) ? 3 : 4;
     if (const char *f = std::getenv("QCS_FUSED_SPLIT")) h->fused_split = std::atoi(f) != 0;
+    if (const char *l = std::getenv("QCS_TREE_LEVELS")) h->tree_levels = std::atoi(l) != 0;
     if (const char *k = std::getenv("QCS_TC_SPLITS"))
         h->tc_splits = std::min(kMaxSplits, std::max(0, std::atoi(k)));
     if (const char *d = std::getenv("QCS_DRAIN_STAGES")) {
@@ -898,6 +899,12 @@ int qcs_selection_stats(qcs_handle_t h, qcs_op_t transA, qcs_op_t transB, int64_
         out[o].n_under_window = v[4] >= 0 ? v[4] : 0;
     }
     if (desc_out) *desc_out = hd;
+    return QCS_SUCCESS;
+}
+
+int qcs_set_tree_levels(qcs_handle_t h, int enabled) {
+    if (!h || (enabled != 0 && enabled != 1)) return QCS_ERR_INVALID_ARG;
+    h->tree_levels = enabled;
     return QCS_SUCCESS;
 }
 

@@ -34,6 +34,14 @@ namespace {
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// One entry of a step sequence: a single step, or (step < 0) the level
+// launch of small steps small_order[first .. first + count).
+struct Item {
+    int step = -1;
+    int first = 0, count = 0;
+    int smem_elems = 0;  // level launch: shared memory per warp (complex values)
+};
+
 struct Layout {
     int G = 1;                      // instances per group
     std::vector<size_t> inter_off;  // byte offset of each step's output ([G][m n])
@@ -41,7 +49,13 @@ struct Layout {
     std::vector<char> batched;      // step runs as one batched launch per group
     int P = 0;                      // steps [0, P): batched; [P, ns): one instance at a time
     std::vector<int> eff;           // effective mode of each step's forward GEMM
+    std::vector<char> small;        // step runs inside its level's launch
+    std::vector<Item> seq_b, seq_i; // order of the steps before P (once per group), from P on
+    std::vector<int> small_order;   // the small steps, grouped by launch
+    std::vector<int32_t> tab;       // element-offset tables of the small steps' operands
+    std::vector<int32_t> tab_a, tab_b;  // start of each small step's tables in ``tab``
     size_t out_index = 0, offsets = 0, bufA = 0, bufB = 0, tmpA = 0, tmpB = 0, gemm = 0, total = 0;
+    size_t small_desc = 0, small_tab = 0;
     size_t gemm_bytes = 0, inter_bytes = 0;
 };
 
@@ -135,19 +149,26 @@ inline int fwd_op(int direct) { return direct == QCS_OP_T ? QCS_OP_T : QCS_OP_N;
 // step's output never overlaps its operands, which are still live then.
 // Steps from P on run once per instance of the group, so an output of an
 // earlier step that one of them reads stays live to the end.
+// time[s] orders the steps as they run: steps of equal time may run at once
+// (one level launch, or steps of a level issued back to back), so an output
+// is live from its step's time to its last reader's time, inclusive.
 size_t place_by_liveness(const qcs_tree_t *t, const std::vector<size_t> &bytes, int P,
-                         std::vector<size_t> &off) {
+                         const std::vector<int> &time, std::vector<size_t> &off) {
     const int nl = t->n_leaves, ns = t->n_steps;
-    std::vector<int> last(ns, ns);  // last reading step of each output; the root: the end
-    for (int s = 0; s < ns; ++s) last[s] = (s == ns - 1) ? ns : -1;
+    constexpr int kEnd = INT32_MAX;
+    std::vector<int> last(ns);  // time of the last reader of each output; the root: the end
+    for (int s = 0; s < ns; ++s) last[s] = (s == ns - 1) ? kEnd : -1;
     for (int s = 0; s < ns; ++s) {
         const qcs_step_t &st = t->steps[s];
         for (const int id : {st.a, st.b}) {
             if (id < nl) continue;
             const int p = id - nl;
-            last[p] = std::max(last[p], (s >= P && p < P) ? ns : s);
+            last[p] = std::max(last[p], (s >= P && p < P) ? kEnd : time[s]);
         }
     }
+    std::vector<int> order(ns);
+    for (int s = 0; s < ns; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return time[x] < time[y]; });
     struct Block {
         size_t off, size;
         int id;
@@ -155,9 +176,9 @@ size_t place_by_liveness(const qcs_tree_t *t, const std::vector<size_t> &bytes, 
     std::vector<Block> live;  // sorted by offset
     size_t peak = 0;
     off.assign(ns, 0);
-    for (int s = 0; s < ns; ++s) {
+    for (const int s : order) {
         live.erase(std::remove_if(live.begin(), live.end(),
-                                  [&](const Block &b) { return last[b.id] < s; }),
+                                  [&](const Block &b) { return last[b.id] < time[s]; }),
                    live.end());
         size_t at = 0;
         for (const Block &b : live) {
@@ -171,6 +192,81 @@ size_t place_by_liveness(const qcs_tree_t *t, const std::vector<size_t> &bytes, 
         peak = std::max(peak, at + bytes[s]);
     }
     return peak;
+}
+
+// Element offsets of op(X) (rows x cols, element e = i + l rows) inside its
+// tensor: through the gather map (e split by the map's dims, first fastest),
+// or the tensor itself in N or T layout.  False if an offset exceeds int32.
+bool operand_table(int direct, const qcs_gather_t &g, int64_t rows, int64_t cols,
+                   std::vector<int32_t> &tab) {
+    const int64_t count = rows * cols;
+    for (int64_t e = 0; e < count; ++e) {
+        int64_t o;
+        if (direct == QCS_OP_N) {
+            o = e;
+        } else if (direct == QCS_OP_T) {
+            o = (e / rows) + (e % rows) * cols;
+        } else {
+            o = 0;
+            int64_t rest = e;
+            for (int d = 0; d < g.rank; ++d) {
+                o += (rest % g.dims[d]) * g.strides[d];
+                rest /= g.dims[d];
+            }
+        }
+        if (o > INT32_MAX) return false;
+        tab.push_back((int32_t)o);
+    }
+    return true;
+}
+
+// The steps [lo, hi) in the order they run, into ``items``.  Level
+// launches on: level by level (a step's level is one more than the highest
+// level of its operands produced in [lo, hi)), the small steps of a level
+// first as one launch, then its other steps in plan order; every step of a
+// level gets the time base + level - 1.  Off: plan order, time = step.
+// Returns the next free time.
+int schedule(const qcs_tree_t *t, Layout &L, int lo, int hi, int base, bool levels,
+             std::vector<Item> &items, std::vector<int> &time) {
+    const int nl = t->n_leaves;
+    if (!levels) {
+        for (int s = lo; s < hi; ++s) {
+            Item it;
+            it.step = s;
+            items.push_back(it);
+            time[s] = s;
+        }
+        return hi;
+    }
+    std::vector<int> level(hi > lo ? hi - lo : 0, 1);
+    int top = 0;
+    for (int s = lo; s < hi; ++s) {
+        const qcs_step_t &st = t->steps[s];
+        for (const int id : {st.a, st.b})
+            if (id >= nl + lo) level[s - lo] = std::max(level[s - lo], level[id - nl - lo] + 1);
+        top = std::max(top, level[s - lo]);
+    }
+    for (int d = 1; d <= top; ++d) {
+        Item lv;
+        lv.first = (int)L.small_order.size();
+        for (int s = lo; s < hi; ++s) {
+            if (level[s - lo] != d || !L.small[s]) continue;
+            const qcs_step_t &st = t->steps[s];
+            L.small_order.push_back(s);
+            lv.smem_elems = std::max<int>(lv.smem_elems, (int)(st.m * st.k + st.k * st.n));
+        }
+        lv.count = (int)L.small_order.size() - lv.first;
+        if (lv.count > 0) items.push_back(lv);
+        for (int s = lo; s < hi; ++s) {
+            if (level[s - lo] != d) continue;
+            time[s] = base + d - 1;
+            if (L.small[s]) continue;
+            Item it;
+            it.step = s;
+            items.push_back(it);
+        }
+    }
+    return base + top;
 }
 
 // Workspace of one call.  Forward: the instances run in groups of G that
@@ -211,6 +307,30 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
     L.P = 0;
     while (L.P < ns && L.batched[L.P]) ++L.P;
     for (int s = L.P; s < ns; ++s) L.batched[s] = 0;
+    // small plain-FP32 steps: run inside their level's launch, operands read
+    // through element-offset tables
+    L.small.assign(ns, 0);
+    L.tab_a.assign(ns, 0);
+    L.tab_b.assign(ns, 0);
+    for (int s = 0; s < ns && h->tree_levels; ++s) {
+        const qcs_step_t &st = t->steps[s];
+        if (L.eff[s] != QCS_MODE_FP32 || st.m * st.k > kTreeSmallOperand ||
+            st.k * st.n > kTreeSmallOperand || st.m * st.n > kTreeSmallOutput)
+            continue;
+        const size_t at = L.tab.size();
+        L.tab_a[s] = (int32_t)at;
+        bool ok = operand_table(st.direct_a, st.map_a, st.m, st.k, L.tab);
+        L.tab_b[s] = (int32_t)L.tab.size();
+        ok = ok && operand_table(st.direct_b, st.map_b, st.k, st.n, L.tab);
+        if (ok && L.tab.size() <= (size_t)INT32_MAX) {
+            L.small[s] = 1;
+        } else {
+            L.tab.resize(at);
+        }
+    }
+    std::vector<int> time(ns, 0);
+    const int tb = schedule(t, L, 0, L.P, 0, h->tree_levels != 0, L.seq_b, time);
+    schedule(t, L, L.P, ns, tb, h->tree_levels != 0, L.seq_i, time);
     for (int s = 0; s < ns; ++s) {
         const qcs_step_t &st = t->steps[s];
         const int64_t gb = L.batched[s] ? G : 1;
@@ -256,7 +376,7 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
         }
     } else {
         std::vector<size_t> rel;
-        const size_t inter = place_by_liveness(t, bytes, L.P, rel);
+        const size_t inter = place_by_liveness(t, bytes, L.P, time, rel);
         for (int s = 0; s < ns; ++s) L.inter_off[s] = p + rel[s];
         p += align256(inter);
     }
@@ -279,6 +399,10 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
     L.gemm = p;
     L.gemm_bytes = gemm;
     p += align256(gemm);
+    L.small_desc = p;
+    p += align256(sizeof(TreeSmallStep) * L.small_order.size());
+    L.small_tab = p;
+    p += align256(sizeof(int32_t) * L.tab.size());
     L.total = p;
     return L;
 }
@@ -513,12 +637,37 @@ int accumulate_root(const Ctx &c, int inst, int g, double *d_out) {
                : QCS_ERR_CUDA;
 }
 
+// One level launch: the small steps of ``it`` for G instances (instances
+// inst0 .. inst0 + G - 1 at group positions g0 .. g0 + G - 1).
+int level_small(const Ctx &c, const Item &it, int inst0, int g0, int G) {
+    for (int q = it.first; q < it.first + it.count; ++q) {
+        const qcs_step_t &st = c.t->steps[c.L.small_order[q]];
+        count_gemm(c, QCS_MODE_FP32, st.m, st.n, st.k, G);
+    }
+    if (c.info) {
+        c.info->level_launches++;
+        c.info->level_gemms += (int64_t)it.count * G;
+    }
+    ProfScope ps(c.h, kProfGemmSimt);
+    const auto *desc = reinterpret_cast<const TreeSmallStep *>(c.ws + c.L.small_desc) + it.first;
+    return launch_tree_small(desc, it.count, G, inst0, g0,
+                             reinterpret_cast<const int64_t *>(c.ws + c.L.offsets),
+                             c.t->n_leaves, reinterpret_cast<const int32_t *>(c.ws + c.L.small_tab),
+                             it.smem_elems, c.h->stream) == cudaSuccess
+               ? QCS_SUCCESS
+               : QCS_ERR_CUDA;
+}
+
 // Forward pass of the G instances inst0 .. inst0 + G - 1: the batched steps
 // once for the group, then the remaining steps instance by instance, each
 // root added into its output slot (when d_out is not NULL).
 int forward_group(const Ctx &c, int inst0, int G, double *d_out) {
-    const int ns = c.t->n_steps;
-    for (int s = 0; s < c.L.P; ++s) {
+    for (const Item &it : c.L.seq_b) {
+        if (it.step < 0) {
+            if (int r = level_small(c, it, inst0, 0, G)) return r;
+            continue;
+        }
+        const int s = it.step;
         if (G > 1) {
             if (int r = (c.L.eff[s] == QCS_MODE_FP32 ? step_batched(c, s, inst0, G)
                                                      : step_grouped(c, s, inst0, G)))
@@ -528,10 +677,60 @@ int forward_group(const Ctx &c, int inst0, int G, double *d_out) {
         }
     }
     for (int g = 0; g < G; ++g) {
-        for (int s = c.L.P; s < ns; ++s)
-            if (int r = step_instance(c, s, inst0 + g, g)) return r;
+        for (const Item &it : c.L.seq_i) {
+            if (int r = (it.step < 0 ? level_small(c, it, inst0 + g, g, 1)
+                                     : step_instance(c, it.step, inst0 + g, g)))
+                return r;
+        }
         if (d_out)
             if (int r = accumulate_root(c, inst0 + g, g, d_out)) return r;
+    }
+    return QCS_SUCCESS;
+}
+
+// The level launches' step table (device pointers of this call's workspace
+// and leaves) and offset tables, uploaded once per call.
+int upload_small(const Ctx &c) {
+    const Layout &L = c.L;
+    if (L.small_order.empty()) return QCS_SUCCESS;
+    const int nl = c.t->n_leaves;
+    std::vector<TreeSmallStep> desc(L.small_order.size());
+    for (size_t q = 0; q < desc.size(); ++q) {
+        const int s = L.small_order[q];
+        const qcs_step_t &st = c.t->steps[s];
+        TreeSmallStep &d = desc[q];
+        const int ids[2] = {st.a, st.b};
+        const float2 **base[2] = {&d.a, &d.b};
+        int64_t *istride[2] = {&d.a_istride, &d.b_istride};
+        int32_t *leaf[2] = {&d.a_leaf, &d.b_leaf};
+        for (int o = 0; o < 2; ++o) {
+            const int id = ids[o];
+            if (id < nl) {
+                *base[o] = reinterpret_cast<const float2 *>(c.leaves[id]);
+                *leaf[o] = id;
+                *istride[o] = 0;
+            } else {
+                *base[o] = inter_ptr(c, id - nl);
+                *leaf[o] = -1;
+                *istride[o] = L.batched[id - nl] ? c.size_of[id] : 0;
+            }
+        }
+        d.c = inter_ptr(c, s);
+        d.c_istride = L.batched[s] ? st.m * st.n : 0;
+        d.m = (int32_t)st.m;
+        d.n = (int32_t)st.n;
+        d.k = (int32_t)st.k;
+        d.a_tab = L.tab_a[s];
+        d.b_tab = L.tab_b[s];
+        d.pad = 0;
+    }
+    cudaStream_t st = c.h->stream;
+    if (cudaMemcpyAsync(c.ws + L.small_desc, desc.data(), sizeof(TreeSmallStep) * desc.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(c.ws + L.small_tab, L.tab.data(), sizeof(int32_t) * L.tab.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
     }
     return QCS_SUCCESS;
 }
@@ -554,12 +753,14 @@ int begin(qcs_handle_t h, const qcs_tree_t *t, bool backward, Ctx &c, Workspace 
             return QCS_ERR_CUDA;
         }
     }
-    if (G > 1 && cudaMemcpyAsync(c.ws + c.L.offsets, t->instance_offset,
-                                 sizeof(int64_t) * (size_t)t->n_instances * t->n_leaves,
-                                 cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
+    if ((G > 1 || !c.L.small_order.empty()) &&
+        cudaMemcpyAsync(c.ws + c.L.offsets, t->instance_offset,
+                        sizeof(int64_t) * (size_t)t->n_instances * t->n_leaves,
+                        cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
         cudaGetLastError();
         return QCS_ERR_CUDA;
     }
+    if (int r = upload_small(c)) return r;
     if (c.info) c.info->workspace_bytes = (int64_t)c.L.total;
     return QCS_SUCCESS;
 }

@@ -96,6 +96,7 @@ struct qcs_handle_s {
     int tc_splits = 0;               // K ranges per tensor-core GEMM (0 = chosen per shape)
     int complex_products = 4;        // real products per emulated complex product (4, or 3: Gauss)
     int fused_split = 0;             // TF32X: split inside the tensor-core kernel's staging
+    int tree_levels = 1;             // tree executor: small FP32 steps of a level in one launch
     uint64_t wait_ns = qcs::kWaitBudgetNs;  // bound of the tensor-core kernels' device waits
     int debug_stall = 0;             // test hook: the TMA producer issues no loads
     int *d_err = nullptr;            // device error word (start of a 64-byte block)
@@ -223,6 +224,31 @@ cudaError_t launch_accumulate_gather_c128(const float2 *src, const int64_t *inde
                                           int64_t count, cudaStream_t s);
 cudaError_t launch_seed_grad(const double *g, const int64_t *index, float2 *grad_root,
                              int64_t count, cudaStream_t s);
+
+// One small plain-FP32 contraction step of a tree level, as the level launch
+// reads it.  op(A) (m x k) and op(B) (k x n) are read element by element
+// through offset tables (element e = i + l m of op(A) lies at
+// a[tab[a_tab + e]], likewise op(B) with e = l + j k), which fold the step's
+// gather map (or its direct N / T layout) into the load; C (m x n) is written
+// dense.  Instance r of the launch (position g0 + r of its group, instance
+// inst0 + r of the plan) reads a leaf operand at its per-instance offset
+// off[inst nl + leaf] and an intermediate at g istride.
+struct TreeSmallStep {
+    const float2 *a, *b;
+    float2 *c;
+    int64_t a_istride, b_istride, c_istride;
+    int32_t a_leaf, b_leaf;  // leaf index, or -1 for an intermediate
+    int32_t m, n, k;
+    int32_t a_tab, b_tab;
+    int32_t pad;
+};
+constexpr int64_t kTreeSmallOperand = 1024;  // max elements of op(A) and of op(B)
+constexpr int64_t kTreeSmallOutput = 4096;   // max elements of C
+// steps[0 .. n_steps) for G instances each: one warp per (step, instance),
+// smem_elems complex values of shared memory per warp (>= m k + k n).
+cudaError_t launch_tree_small(const TreeSmallStep *steps, int n_steps, int G, int inst0, int g0,
+                              const int64_t *off, int nl, const int32_t *tab, int smem_elems,
+                              cudaStream_t s);
 
 // ---- shared with the executor (capi.cu) ------------------------------------
 int effective_mode(qcs_handle_t h, int mode, int opA, int opB, int64_t m, int64_t n, int64_t k);

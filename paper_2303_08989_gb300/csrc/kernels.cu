@@ -1812,6 +1812,82 @@ cudaError_t launch_accumulate_c128(const float2 *src, double *dst, int64_t count
 }
 
 // ===========================================================================
+// Small plain-FP32 contraction steps of one tree level, all in one launch
+// ===========================================================================
+
+namespace {
+
+constexpr int kTreeSmallWarps = 4;
+
+// One warp per (step, instance): the warp gathers op(A) and op(B) through
+// the step's offset tables into its slice of shared memory, then each lane
+// forms output elements e = lane, lane + 32, ... (i = e mod m, j = e div m)
+// as the same FP32 FMA chain over l = 0 .. k-1 as the per-element FP32
+// kernels (re: + ar br - ai bi, im: + ar bi + ai br), scaled by alpha the
+// same way, and writes C contiguously.
+__global__ void __launch_bounds__(32 * kTreeSmallWarps) tree_small_kernel(
+    const TreeSmallStep *__restrict__ steps, int n_steps, int G, int inst0, int g0,
+    const int64_t *__restrict__ off, int nl, const int32_t *__restrict__ tab, int smem_elems,
+    float2 alpha) {
+    extern __shared__ float2 tree_small_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)blockIdx.x * kTreeSmallWarps + warp;
+    if (p >= (int64_t)n_steps * G) return;  // the whole warp; no block barrier follows
+    const int r = (int)(p % G);
+    const TreeSmallStep &st = steps[p / G];
+    const int m = st.m, n = st.n, k = st.k;
+    const int64_t inst = (int64_t)inst0 + r, g = (int64_t)g0 + r;
+    const float2 *A = st.a + (st.a_leaf >= 0 ? off[inst * nl + st.a_leaf] : g * st.a_istride);
+    const float2 *B = st.b + (st.b_leaf >= 0 ? off[inst * nl + st.b_leaf] : g * st.b_istride);
+    float2 *C = st.c + g * st.c_istride;
+    float2 *As = tree_small_smem + (size_t)warp * smem_elems;
+    float2 *Bs = As + m * k;
+    const int32_t *ta = tab + st.a_tab, *tb = tab + st.b_tab;
+    for (int e = lane; e < m * k; e += 32) As[e] = A[ta[e]];
+    for (int e = lane; e < k * n; e += 32) Bs[e] = B[tb[e]];
+    __syncwarp();
+    for (int e = lane; e < m * n; e += 32) {
+        const int i = e % m, j = e / m;
+        float sr = 0.f, si = 0.f;
+        for (int l = 0; l < k; ++l) {
+            const float2 a = As[i + l * m], b = Bs[l + j * k];
+            sr = fmaf(a.x, b.x, sr);
+            sr = fmaf(-a.y, b.y, sr);
+            si = fmaf(a.x, b.y, si);
+            si = fmaf(a.y, b.x, si);
+        }
+        float2 o;
+        o.x = alpha.x * sr - alpha.y * si;
+        o.y = alpha.x * si + alpha.y * sr;
+        C[e] = o;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_tree_small(const TreeSmallStep *steps, int n_steps, int G, int inst0, int g0,
+                              const int64_t *off, int nl, const int32_t *tab, int smem_elems,
+                              cudaStream_t s) {
+    if (n_steps <= 0 || G <= 0) return cudaSuccess;
+    if (smem_elems < 1 || smem_elems > 2 * kTreeSmallOperand) return cudaErrorInvalidValue;
+    static bool configured = false;  // the attribute is per function, set once
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(
+            tree_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)(sizeof(float2) * 2 * kTreeSmallOperand * kTreeSmallWarps));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int64_t warps = (int64_t)n_steps * G;
+    const int64_t blocks = (warps + kTreeSmallWarps - 1) / kTreeSmallWarps;
+    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float2) * (size_t)smem_elems * kTreeSmallWarps;
+    tree_small_kernel<<<(unsigned)blocks, 32 * kTreeSmallWarps, smem, s>>>(
+        steps, n_steps, G, inst0, g0, off, nl, tab, smem_elems, make_float2(1.f, 0.f));
+    return cudaGetLastError();
+}
+
+// ===========================================================================
 // Plain FP32 CGEMM on the CUDA cores
 // ===========================================================================
 

@@ -729,7 +729,8 @@ def info_dict(info) -> dict:
     return {"seconds": info.seconds, "gemm_count": info.gemm_count,
             "gather_count": info.gather_count, "mode_count": list(info.mode_count),
             "workspace_bytes": info.workspace_bytes, "flops": info.flops,
-            "mode_flops": list(info.mode_flops)}
+            "mode_flops": list(info.mode_flops), "level_launches": info.level_launches,
+            "level_gemms": info.level_gemms}
 
 
 # ---------------------------------------------------------------------------
