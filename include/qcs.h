@@ -369,19 +369,30 @@ typedef struct {
 /* Instances per group of qcs_contract_tree and qcs_tree_graph_create (1 to
  * 65535; default 1).  With G > 1 the forward pass runs the instances in
  * groups of G (Section 5.3: slices and bitstrings are independent instances
- * of one step sequence).  Each step up to the first emulated step with at
- * least one 128 x 128 output tile per SM runs once per group: a step whose
+ * of one step sequence).  Each step up to the first emulated step that
+ * fills the GPU alone (at least one 128 x 128 output tile per SM) AND whose
+ * split planes and output for the G instances exceed the group budget
+ * (qcs_set_group_budget) runs once per group: a step whose
  * GEMM runs in plain FP32 (after the size rule) as one batched gather and
  * one batched GEMM launch; an emulated step as per-instance statistics,
  * selection and split followed by one persistent tensor-core launch per
  * kind over the output tiles of all G instances (each instance keeps its
  * own selected mode; for AUTO the FP32 candidate of each instance is
  * launched gated).  Their outputs hold G instances each (intermediates share
- * memory by liveness).  The later steps -- large enough to fill the GPU
- * alone -- loop over the group.  Results do not depend on G.  The backward
+ * memory by liveness).  The later steps loop over the group.  Results do
+ * not depend on G.  The backward
  * runs one instance at a time (its launches can be captured in a graph:
  * qcs_tree_backward_graph_create). */
 int qcs_set_instance_batch(qcs_handle_t h, int instances);
+
+/* Memory a grouped step of the tree executor may hold (bytes; default
+ * 32 GiB; environment override QCS_GROUP_BUDGET_MB): an emulated step that
+ * fills the GPU alone still runs once for its group of G instances -- full
+ * tile waves and one pipeline ramp for all of them -- unless its split planes
+ * and output for the G instances exceed this; then it and every later step
+ * run per instance (qcs_set_instance_batch).  0: every step that fills the
+ * GPU alone runs per instance.  Results do not depend on it. */
+int qcs_set_group_budget(qcs_handle_t h, uint64_t bytes);
 
 /* Level launches of the tree executor (Section 2.2: the steps of one level
  * of the contraction tree are independent).  While ``enabled`` is 1 (the

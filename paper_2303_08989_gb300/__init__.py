@@ -175,6 +175,11 @@ class Handle:
         _lib.check(self.lib.qcs_set_complex_products(self._h, int(products)),
                    "qcs_set_complex_products")
 
+    def set_group_budget(self, nbytes: int):
+        """Bytes a grouped GPU-filling tree step may hold for its instances
+        (qcs_set_group_budget; default 32 GiB, 0 = such steps per instance)."""
+        _lib.check(self.lib.qcs_set_group_budget(self._h, int(nbytes)), "qcs_set_group_budget")
+
     def set_tree_levels(self, enabled: bool):
         """Run a contraction tree level by level, the small plain-FP32 steps
         of each level as one launch (qcs_set_tree_levels; on by default)."""

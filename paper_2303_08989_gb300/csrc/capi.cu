@@ -789,6 +789,8 @@ int qcs_create(qcs_handle_t *out, void *cuda_stream) {
         h->complex_products = (std::atoi(c) == 3) ? 3 : 4;
     if (const char *f = std::getenv("QCS_FUSED_SPLIT")) h->fused_split = std::atoi(f) != 0;
     if (const char *l = std::getenv("QCS_TREE_LEVELS")) h->tree_levels = std::atoi(l) != 0;
+    if (const char *b = std::getenv("QCS_GROUP_BUDGET_MB"))
+        h->group_budget = (size_t)std::max(0LL, std::atoll(b)) << 20;
     if (const char *k = std::getenv("QCS_TC_SPLITS"))
         h->tc_splits = std::min(kMaxSplits, std::max(0, std::atoi(k)));
     if (const char *d = std::getenv("QCS_DRAIN_STAGES")) {
@@ -899,6 +901,12 @@ int qcs_selection_stats(qcs_handle_t h, qcs_op_t transA, qcs_op_t transB, int64_
         out[o].n_under_window = v[4] >= 0 ? v[4] : 0;
     }
     if (desc_out) *desc_out = hd;
+    return QCS_SUCCESS;
+}
+
+int qcs_set_group_budget(qcs_handle_t h, uint64_t bytes) {
+    if (!h) return QCS_ERR_INVALID_ARG;
+    h->group_budget = (size_t)bytes;
     return QCS_SUCCESS;
 }
 

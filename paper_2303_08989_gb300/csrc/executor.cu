@@ -274,11 +274,12 @@ int schedule(const qcs_tree_t *t, Layout &L, int lo, int hi, int base, bool leve
 // step as one batched gather and one batched GEMM launch, an emulated step as
 // one grouped sequence (run_cgemm_group: one tensor-core launch per kind over
 // the tiles of all G instances), outputs holding G instances.  P is the first
-// emulated step with at least one output tile per SM: it fills the GPU alone,
-// so from there on (in a tree from a greedy order, the few large
-// contractions at the end) the steps run one instance after another, outputs
-// holding one instance.  Outputs reuse memory by liveness.  Backward (G = 1):
-// every output is kept.
+// emulated step with at least one output tile per SM whose planes and output
+// for G instances exceed the handle's group budget: from there on (in a tree
+// from a greedy order, the few largest contractions at the end) the steps run
+// one instance after another, outputs holding one instance.  Steps run level
+// by level when level launches are on (schedule()).  Outputs reuse memory by
+// liveness.  Backward (G = 1): every output is kept.
 Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
     Layout L;
     L.G = G;
@@ -297,11 +298,22 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
         const qcs_step_t &st = t->steps[s];
         L.eff[s] = effective_mode(h, st.mode, fwd_op(st.direct_a), fwd_op(st.direct_b), st.m, st.n,
                                   st.k);
-        // An emulated step whose output tiles fill the GPU alone gains nothing
-        // from running its instances in one launch, and a group would hold G
-        // copies of its planes: it and every later step run per instance.
+        // An emulated step whose output tiles fill the GPU alone still gains
+        // from one launch over its instances (full tile waves, one pipeline
+        // ramp), but a group holds G copies of its planes and output: when
+        // those exceed the handle's budget it and every later step run per
+        // instance.
         const int64_t tiles = ((st.m + kBM - 1) / kBM) * ((st.n + kBN - 1) / kBN);
-        const bool fills = L.eff[s] != QCS_MODE_FP32 && tiles >= h->num_sms;
+        bool fills = L.eff[s] != QCS_MODE_FP32 && tiles >= h->num_sms;
+        if (fills) {
+            const size_t grouped =
+                gemm_workspace_bytes(L.eff[s], st.m, st.n, st.k, h->num_sms,
+                                     gemm_splits(h, fwd_op(st.direct_a), fwd_op(st.direct_b), st.m,
+                                                 st.n, st.k),
+                                     G) +
+                sizeof(float2) * (size_t)(st.m * st.n) * G;
+            fills = grouped > h->group_budget;
+        }
         L.batched[s] = (G > 1 && !fills) ? 1 : 0;
     }
     L.P = 0;

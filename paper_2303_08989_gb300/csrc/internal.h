@@ -97,6 +97,7 @@ struct qcs_handle_s {
     int complex_products = 4;        // real products per emulated complex product (4, or 3: Gauss)
     int fused_split = 0;             // TF32X: split inside the tensor-core kernel's staging
     int tree_levels = 1;             // tree executor: small FP32 steps of a level in one launch
+    size_t group_budget = size_t(32) << 30;  // tree executor: bytes a grouped GPU-filling step may hold
     uint64_t wait_ns = qcs::kWaitBudgetNs;  // bound of the tensor-core kernels' device waits
     int debug_stall = 0;             // test hook: the TMA producer issues no loads
     int *d_err = nullptr;            // device error word (start of a 64-byte block)

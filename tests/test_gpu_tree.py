@@ -202,10 +202,11 @@ def test_full_size_30_qubit_sliced_amplitudes_vs_fp64_golden(h, golden_dir):
 def test_full_size_30_qubit_in_the_bench_configuration_vs_fp64_golden(golden_dir, absorb):
     """The contraction in bench.py's configuration: the cheapest of many
     seeded greedy orders (256 here), 6 sliced indices, instances in groups
-    of 16 (grouped tensor-core
-    launches, batched FP32 steps), AUTO-0.1 under the measured size rule with
+    of 16 (grouped tensor-core launches, also for the steps that fill the
+    GPU alone; batched FP32 steps), AUTO-0.1 under the measured size rule with
     K ranges from the tuner; two bitstrings x 64 slices against the FP64
-    amplitudes of tests/golden, eagerly and replayed from a CUDA graph."""
+    amplitudes of tests/golden, eagerly, replayed from a CUDA graph, and with
+    the GPU-filling steps one instance at a time (bit-identical)."""
     import os
 
     need_gpu()
@@ -235,10 +236,17 @@ def test_full_size_30_qubit_in_the_bench_configuration_vs_fp64_golden(golden_dir
         hd.sync()
         replay = out.cpu().numpy()
         g.close()
+        # the steps that fill the GPU alone one instance at a time (group budget 0)
+        hd.set_group_budget(0)
+        per_instance = cp.forward(hd).cpu().numpy()
+        hd.sync()
+        info0 = cp.last_info
     finally:
         hd.close()
     a = eager.cpu().numpy()[:, 0]
     assert np.array_equal(replay[:, 0], a)
+    assert np.array_equal(per_instance[:, 0], a)
+    assert info0.workspace_bytes < info.workspace_bytes  # the default grouped those steps
     assert oracle.fidelity(ref, a) >= 1 - 1e-5
     assert np.all(np.abs(a - ref) <= 1e-4 * np.abs(ref)), (a, ref)
     assert info.mode_count[q.MODE_FP32] > 0 and info.mode_count[q.MODE_FP32] < info.gemm_count
