@@ -460,7 +460,10 @@ int qcs_tree_backward_graph_create(qcs_handle_t h, const qcs_tree_t *tree,
  * grad_B = A_mat^H grad_out, run as emulated CGEMMs in the step's mode
  * (op C flags); the forward intermediates are recomputed per instance
  * (slice) rather than kept across instances.  Every tensor of the plan must
- * be used by exactly one step (a tree). */
+ * be used by exactly one step (a tree), and the gradients of different leaves
+ * must not overlap in memory (QCS_ERR_INVALID_ARG otherwise): with level
+ * launches (qcs_set_tree_levels) the adjoints of a level's small steps run
+ * at once and add into them concurrently. */
 int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
                                const qcs_c32 *const *leaves, const double *d_grad_out,
                                qcs_c32 *const *d_grad_leaves, qcs_run_info_t *info);

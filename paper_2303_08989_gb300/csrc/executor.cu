@@ -40,6 +40,7 @@ struct Item {
     int step = -1;
     int first = 0, count = 0;
     int smem_elems = 0;  // level launch: shared memory per warp (complex values)
+    int smem_bwd = 0;    // ... of its adjoint launch
 };
 
 struct Layout {
@@ -55,7 +56,7 @@ struct Layout {
     std::vector<int32_t> tab;       // element-offset tables of the small steps' operands
     std::vector<int32_t> tab_a, tab_b;  // start of each small step's tables in ``tab``
     size_t out_index = 0, offsets = 0, bufA = 0, bufB = 0, tmpA = 0, tmpB = 0, gemm = 0, total = 0;
-    size_t small_desc = 0, small_tab = 0;
+    size_t small_desc = 0, small_tab = 0, small_bwd = 0;
     size_t gemm_bytes = 0, inter_bytes = 0;
 };
 
@@ -254,6 +255,8 @@ int schedule(const qcs_tree_t *t, Layout &L, int lo, int hi, int base, bool leve
             const qcs_step_t &st = t->steps[s];
             L.small_order.push_back(s);
             lv.smem_elems = std::max<int>(lv.smem_elems, (int)(st.m * st.k + st.k * st.n));
+            lv.smem_bwd =
+                std::max<int>(lv.smem_bwd, (int)(st.m * st.n + st.m * st.k + st.k * st.n));
         }
         lv.count = (int)L.small_order.size() - lv.first;
         if (lv.count > 0) items.push_back(lv);
@@ -328,6 +331,14 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
         const qcs_step_t &st = t->steps[s];
         if (L.eff[s] != QCS_MODE_FP32 || st.m * st.k > kTreeSmallOperand ||
             st.k * st.n > kTreeSmallOperand || st.m * st.n > kTreeSmallOutput)
+            continue;
+        // the adjoint's level launch too: both adjoint GEMMs plain FP32, and
+        // grad_out with both operands in one warp's shared memory
+        if (backward && (st.m * st.n + st.m * st.k + st.k * st.n > kTreeSmallBwdElems ||
+                         effective_mode(h, st.mode, QCS_OP_N, QCS_OP_C, st.m, st.k, st.n) !=
+                             QCS_MODE_FP32 ||
+                         effective_mode(h, st.mode, QCS_OP_C, QCS_OP_N, st.k, st.n, st.m) !=
+                             QCS_MODE_FP32))
             continue;
         const size_t at = L.tab.size();
         L.tab_a[s] = (int32_t)at;
@@ -415,6 +426,10 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
     p += align256(sizeof(TreeSmallStep) * L.small_order.size());
     L.small_tab = p;
     p += align256(sizeof(int32_t) * L.tab.size());
+    if (backward) {
+        L.small_bwd = p;
+        p += align256(sizeof(TreeSmallBwd) * L.small_order.size());
+    }
     L.total = p;
     return L;
 }
@@ -427,6 +442,7 @@ struct Ctx {
     Layout L;
     std::vector<int64_t> size_of;  // elements of every tensor (leaves, then step outputs)
     qcs_run_info_t *info;
+    qcs_c32 *const *grad_leaves = nullptr;  // backward: the caller's leaf gradients
 };
 
 float2 *inter_ptr(const Ctx &c, int s) { return reinterpret_cast<float2 *>(c.ws + c.L.inter_off[s]); }
@@ -744,6 +760,43 @@ int upload_small(const Ctx &c) {
         cudaGetLastError();
         return QCS_ERR_CUDA;
     }
+    if (!c.grad_leaves) return QCS_SUCCESS;
+    // the adjoint's table: operands and their gradients (leaf gradients at
+    // offset 0 here; the kernel adds the instance offset to both)
+    std::vector<TreeSmallBwd> bwd(L.small_order.size());
+    for (size_t q = 0; q < bwd.size(); ++q) {
+        const int s = L.small_order[q];
+        const qcs_step_t &sp = c.t->steps[s];
+        TreeSmallBwd &d = bwd[q];
+        const int ids[2] = {sp.a, sp.b};
+        const float2 **x[2] = {&d.a, &d.b};
+        float2 **gx[2] = {&d.ga, &d.gb};
+        int32_t *leaf[2] = {&d.a_leaf, &d.b_leaf};
+        for (int o = 0; o < 2; ++o) {
+            const int id = ids[o];
+            if (id < nl) {
+                *x[o] = reinterpret_cast<const float2 *>(c.leaves[id]);
+                *gx[o] = reinterpret_cast<float2 *>(c.grad_leaves[id]);
+                *leaf[o] = id;
+            } else {
+                *x[o] = inter_ptr(c, id - nl);
+                *gx[o] = grad_ptr(c, id - nl);
+                *leaf[o] = -1;
+            }
+        }
+        d.gc = grad_ptr(c, s);
+        d.m = (int32_t)sp.m;
+        d.n = (int32_t)sp.n;
+        d.k = (int32_t)sp.k;
+        d.a_tab = L.tab_a[s];
+        d.b_tab = L.tab_b[s];
+        d.pad = 0;
+    }
+    if (cudaMemcpyAsync(c.ws + L.small_bwd, bwd.data(), sizeof(TreeSmallBwd) * bwd.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
     return QCS_SUCCESS;
 }
 
@@ -835,7 +888,31 @@ int backward_all(Ctx &c, const double *d_grad_out, qcs_c32 *const *d_grad_leaves
         }
         if (launch_seed_grad(g, dev_index(c), groot, tree->out_size, s) != cudaSuccess)
             return QCS_ERR_CUDA;
-        for (int st_i = ns - 1; st_i >= 0; --st_i) {
+        // the steps in the reverse of the order the forward ran them: a
+        // step's output gradient is complete once its consumer (a later step,
+        // at a higher level) has run
+        for (auto it = c.L.seq_i.rbegin(); it != c.L.seq_i.rend(); ++it) {
+            if (it->step < 0) {
+                if (info) {
+                    info->level_launches++;
+                    for (int q = it->first; q < it->first + it->count; ++q) {
+                        const qcs_step_t &sp = tree->steps[c.L.small_order[q]];
+                        count_gemm(c, QCS_MODE_FP32, sp.m, sp.k, sp.n);
+                        count_gemm(c, QCS_MODE_FP32, sp.k, sp.n, sp.m);
+                        info->level_gemms += 2;
+                    }
+                }
+                ProfScope ps(h, kProfGemmSimt);
+                const auto *desc =
+                    reinterpret_cast<const TreeSmallBwd *>(c.ws + c.L.small_bwd) + it->first;
+                if (launch_tree_small_bwd(desc, it->count, inst,
+                                          reinterpret_cast<const int64_t *>(c.ws + c.L.offsets),
+                                          nl, reinterpret_cast<const int32_t *>(c.ws + c.L.small_tab),
+                                          it->smem_bwd, s) != cudaSuccess)
+                    return QCS_ERR_CUDA;
+                continue;
+            }
+            const int st_i = it->step;
             const qcs_step_t &st = tree->steps[st_i];
             const float2 *gC = grad_ptr(c, st_i);
             float2 *Am = reinterpret_cast<float2 *>(c.ws + c.L.bufA);
@@ -856,12 +933,22 @@ int backward_all(Ctx &c, const double *d_grad_out, qcs_c32 *const *d_grad_leaves
     return QCS_SUCCESS;
 }
 
+// Pointers present and 8-byte aligned, and the leaf gradients pairwise
+// disjoint (the adjoints of independent steps add into them at once).
 bool backward_args_ok(const qcs_tree_t *tree, const qcs_c32 *const *leaves,
                       qcs_c32 *const *d_grad_leaves) {
-    for (int i = 0; i < tree->n_leaves; ++i)
+    if (!tree->leaf_size) return false;
+    std::vector<std::pair<uintptr_t, uintptr_t>> spans;
+    for (int i = 0; i < tree->n_leaves; ++i) {
         if (!leaves[i] || !d_grad_leaves[i] || (reinterpret_cast<uintptr_t>(leaves[i]) & 7u) ||
-            (reinterpret_cast<uintptr_t>(d_grad_leaves[i]) & 7u))
+            (reinterpret_cast<uintptr_t>(d_grad_leaves[i]) & 7u) || tree->leaf_size[i] < 1)
             return false;
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(d_grad_leaves[i]);
+        spans.emplace_back(lo, lo + sizeof(qcs_c32) * (uintptr_t)tree->leaf_size[i]);
+    }
+    std::sort(spans.begin(), spans.end());
+    for (size_t i = 1; i < spans.size(); ++i)
+        if (spans[i].first < spans[i - 1].second) return false;
     return true;
 }
 
@@ -907,6 +994,7 @@ int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
         return QCS_ERR_INVALID_ARG;
     Ctx c;
     c.leaves = leaves;
+    c.grad_leaves = d_grad_leaves;
     c.info = info;
     if (int r = begin(h, tree, true, c)) return r;
     if (int r = backward_all(c, d_grad_out, d_grad_leaves)) return r;
@@ -928,6 +1016,7 @@ int qcs_tree_backward_graph_create(qcs_handle_t h, const qcs_tree_t *tree,
     g->h = h;
     Ctx c;
     c.leaves = leaves;
+    c.grad_leaves = d_grad_leaves;
     c.info = nullptr;
     int r = begin(h, tree, true, c, &g->ws);
     if (r == QCS_SUCCESS && cudaStreamSynchronize(h->stream) != cudaSuccess) r = QCS_ERR_CUDA;

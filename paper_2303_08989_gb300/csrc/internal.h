@@ -251,6 +251,24 @@ cudaError_t launch_tree_small(const TreeSmallStep *steps, int n_steps, int G, in
                               const int64_t *off, int nl, const int32_t *tab, int smem_elems,
                               cudaStream_t s);
 
+// The adjoint of one small step for one instance: from the output gradient
+// gc (m x n, dense) grad_A = gc op(B)^H and grad_B = op(A)^H gc, written
+// through the operands' offset tables into their gradients: ga[tab[a_tab + e]]
+// (added for a leaf, at its instance offset; stored for an intermediate,
+// whose map covers it once), likewise gb.
+struct TreeSmallBwd {
+    const float2 *a, *b, *gc;
+    float2 *ga, *gb;
+    int32_t a_leaf, b_leaf;  // leaf index, or -1 for an intermediate
+    int32_t m, n, k;
+    int32_t a_tab, b_tab;
+    int32_t pad;
+};
+constexpr int64_t kTreeSmallBwdElems = 2048;  // max m n + m k + k n of a step's adjoint
+cudaError_t launch_tree_small_bwd(const TreeSmallBwd *steps, int n_steps, int inst,
+                                  const int64_t *off, int nl, const int32_t *tab, int smem_elems,
+                                  cudaStream_t s);
+
 // ---- shared with the executor (capi.cu) ------------------------------------
 int effective_mode(qcs_handle_t h, int mode, int opA, int opB, int64_t m, int64_t n, int64_t k);
 // K-range setting for a GEMM of this shape: forced, tuned, or 0 (per-shape rule).

@@ -1863,6 +1863,74 @@ __global__ void __launch_bounds__(32 * kTreeSmallWarps) tree_small_kernel(
     }
 }
 
+// One warp per step of the level: gc, op(A) and op(B) into shared memory,
+// then grad_A (m x k) and grad_B (k x n) element by element as FP32 FMA
+// chains in the order of the per-element kernels with op C on the
+// conjugated operand (the conjugation applied on load), and the writes
+// through the offset tables.
+__global__ void __launch_bounds__(32 * kTreeSmallWarps) tree_small_bwd_kernel(
+    const TreeSmallBwd *__restrict__ steps, int n_steps, int inst,
+    const int64_t *__restrict__ off, int nl, const int32_t *__restrict__ tab, int smem_elems) {
+    extern __shared__ float2 tree_small_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * kTreeSmallWarps + warp;
+    if (p >= n_steps) return;  // the whole warp; no block barrier follows
+    const TreeSmallBwd &st = steps[p];
+    const int m = st.m, n = st.n, k = st.k;
+    const int64_t oa = st.a_leaf >= 0 ? off[(int64_t)inst * nl + st.a_leaf] : 0;
+    const int64_t ob = st.b_leaf >= 0 ? off[(int64_t)inst * nl + st.b_leaf] : 0;
+    float2 *Gs = tree_small_smem + (size_t)warp * smem_elems;
+    float2 *As = Gs + m * n;
+    float2 *Bs = As + m * k;
+    const int32_t *ta = tab + st.a_tab, *tb = tab + st.b_tab;
+    for (int e = lane; e < m * n; e += 32) Gs[e] = st.gc[e];
+    for (int e = lane; e < m * k; e += 32) As[e] = st.a[oa + ta[e]];
+    for (int e = lane; e < k * n; e += 32) Bs[e] = st.b[ob + tb[e]];
+    __syncwarp();
+    // grad_A[i, l] = sum_j gc[i, j] conj(B[l, j])
+    for (int e = lane; e < m * k; e += 32) {
+        const int i = e % m, l = e / m;
+        float sr = 0.f, si = 0.f;
+        for (int j = 0; j < n; ++j) {
+            const float2 a = Gs[i + j * m];
+            float2 b = Bs[l + j * k];
+            b.y = -b.y;
+            sr = fmaf(a.x, b.x, sr);
+            sr = fmaf(-a.y, b.y, sr);
+            si = fmaf(a.x, b.y, si);
+            si = fmaf(a.y, b.x, si);
+        }
+        float2 *dst = st.ga + oa + ta[e];
+        if (st.a_leaf >= 0) {
+            const float2 u = *dst;
+            sr += u.x;
+            si += u.y;
+        }
+        *dst = make_float2(sr, si);
+    }
+    // grad_B[l, j] = sum_i conj(A[i, l]) gc[i, j]
+    for (int e = lane; e < k * n; e += 32) {
+        const int l = e % k, j = e / k;
+        float sr = 0.f, si = 0.f;
+        for (int i = 0; i < m; ++i) {
+            float2 a = As[i + l * m];
+            a.y = -a.y;
+            const float2 b = Gs[i + j * m];
+            sr = fmaf(a.x, b.x, sr);
+            sr = fmaf(-a.y, b.y, sr);
+            si = fmaf(a.x, b.y, si);
+            si = fmaf(a.y, b.x, si);
+        }
+        float2 *dst = st.gb + ob + tb[e];
+        if (st.b_leaf >= 0) {
+            const float2 u = *dst;
+            sr += u.x;
+            si += u.y;
+        }
+        *dst = make_float2(sr, si);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_tree_small(const TreeSmallStep *steps, int n_steps, int G, int inst0, int g0,
@@ -1884,6 +1952,26 @@ cudaError_t launch_tree_small(const TreeSmallStep *steps, int n_steps, int G, in
     const size_t smem = sizeof(float2) * (size_t)smem_elems * kTreeSmallWarps;
     tree_small_kernel<<<(unsigned)blocks, 32 * kTreeSmallWarps, smem, s>>>(
         steps, n_steps, G, inst0, g0, off, nl, tab, smem_elems, make_float2(1.f, 0.f));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_small_bwd(const TreeSmallBwd *steps, int n_steps, int inst,
+                                  const int64_t *off, int nl, const int32_t *tab, int smem_elems,
+                                  cudaStream_t s) {
+    if (n_steps <= 0) return cudaSuccess;
+    if (smem_elems < 1 || smem_elems > kTreeSmallBwdElems) return cudaErrorInvalidValue;
+    static bool configured = false;  // the attribute is per function, set once
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(
+            tree_small_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)(sizeof(float2) * kTreeSmallBwdElems * kTreeSmallWarps));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int blocks = (n_steps + kTreeSmallWarps - 1) / kTreeSmallWarps;
+    const size_t smem = sizeof(float2) * (size_t)smem_elems * kTreeSmallWarps;
+    tree_small_bwd_kernel<<<(unsigned)blocks, 32 * kTreeSmallWarps, smem, s>>>(
+        steps, n_steps, inst, off, nl, tab, smem_elems);
     return cudaGetLastError();
 }
 

@@ -161,6 +161,13 @@ def test_adjoint_with_level_launches(n_slices):
             torch.cuda.synchronize()
             hd.sync()
             grads.append(params.grad.double().cpu().numpy())
+            info = cp.last_info  # the backward call's
+            if levels:
+                # forward recompute and adjoint: most GEMMs inside level launches
+                assert info.level_launches > 0
+                assert info.level_gemms >= info.gemm_count // 2
+            else:
+                assert info.level_launches == 0
     finally:
         hd.close()
     _, g_ref = oracle.loss_and_grad(circ, bits)
@@ -178,5 +185,41 @@ def test_level_setter_rejects_bad_values():
         assert rc == -1
         hd.set_tree_levels(False)
         hd.set_tree_levels(True)
+    finally:
+        hd.close()
+
+
+def test_adjoint_rejects_overlapping_leaf_gradients():
+    """The adjoints of a level's steps add into their leaves' gradients at
+    the same time, so gradient buffers that overlap are an argument error,
+    found on the host before any launch."""
+    import ctypes
+
+    need_gpu()
+    tn = _tn()
+    q = lib()
+    circ = qi.random_grid_circuit(2, 3, 4, seed=4)
+    bits = qi.random_bitstrings(6, 2, seed=6)
+    plan = tn.plan_circuit(circ, bits, seed=2, mode=q.MODE_FP32)
+    cp = tn.CompiledPlan(plan)
+    hd = q.Handle(tol=0.0, size_rule=True)
+    try:
+        sizes = [t.numel() for t in cp.leaves]
+        g_out = torch.zeros((plan.n_slots, plan.out_size), dtype=torch.complex128, device="cuda")
+        buf = torch.zeros(sum(sizes), dtype=torch.complex64, device="cuda")
+        ok = list(buf.split(sizes))
+        bad = list(ok)
+        bad[1] = buf[: sizes[1]]  # overlaps leaf 0's gradient
+        info = q._lib.qcs_run_info_t()
+        rc = hd.lib.qcs_contract_tree_backward(
+            hd.ptr, ctypes.byref(cp.tree), cp._ptrs(cp.leaves), ctypes.c_void_p(g_out.data_ptr()),
+            cp._ptrs(bad), ctypes.byref(info))
+        assert rc == -1
+        rc = hd.lib.qcs_contract_tree_backward(
+            hd.ptr, ctypes.byref(cp.tree), cp._ptrs(cp.leaves), ctypes.c_void_p(g_out.data_ptr()),
+            cp._ptrs(ok), ctypes.byref(info))
+        assert rc == 0
+        torch.cuda.synchronize()
+        hd.sync()
     finally:
         hd.close()
