@@ -260,6 +260,31 @@ int gather_view(qcs_handle_t h, OperandView &v, int64_t rows, const qcs_gemm_des
     return QCS_SUCCESS;
 }
 
+// The split of one operand (which 0: op(A), R = m; 1: op(B), R = n) into
+// its planes: through its map (fused), or from the matrix.  The split
+// writes with the selected kind's element size; the pitch is kp elements
+// either way, so both tensor maps of the GEMM describe it.  Instance g of a
+// group owns rows [g R_pad, (g + 1) R_pad) of every plane.
+int split_operand(qcs_handle_t h, int which, const qcs_gemm_desc_t *dg, const OperandView &X,
+                  int op, int64_t R, int64_t k, int64_t R_pad, int64_t kp, void *planes,
+                  int64_t plane_stride, int64_t plane_off, void *planes32, bool fused,
+                  bool tf32_fused, const SplitBatch &sb) {
+    ProfScope ps(h, kProfSplit);
+    cudaError_t e;
+    if (fused) {
+        e = launch_split_gather(dg, which, X.map->rank, X.map->dims, X.map->strides, X.X,
+                                which == 0 ? R : k, planes, kp, plane_stride, h->stream, which,
+                                plane_off, planes32, sb);
+    } else {
+        int64_t sr, sc;
+        plane_strides(which, op, X.ld, sr, sc);
+        e = launch_split(dg, which, X.X, sr, sc, op == QCS_OP_C, R, k, R_pad, kp, planes, kp,
+                         plane_stride, h->stream, which, plane_off, planes32, tf32_fused ? 1 : 0,
+                         sb);
+    }
+    return e == cudaSuccess ? QCS_SUCCESS : QCS_ERR_CUDA;
+}
+
 }  // namespace
 
 int run_cgemm_views(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n,
@@ -340,6 +365,31 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
     void *sepA32 = (PL.a32 != PL.a16) ? planesA32 : nullptr;
     void *sepB32 = (PL.b32 != PL.b16) ? planesB32 : nullptr;
     if (w.S > 1) w.P = reinterpret_cast<float2 *>(p + PL.partials);
+    // One split launch for an operand of the whole group when the instances'
+    // operands lie one stride apart and are read the same way (a matrix, or
+    // the same whole-tensor map): the intermediates of a grouped step.
+    auto one_stride = [&](const std::vector<OperandView> &V, bool mapped_ok, int64_t &stride) {
+        if (G < 2 || !emulated || (V[0].map && !mapped_ok)) return false;
+        const intptr_t d = reinterpret_cast<intptr_t>(V[1].X) - reinterpret_cast<intptr_t>(V[0].X);
+        if (d % (intptr_t)sizeof(float2) != 0) return false;
+        for (int g = 1; g < G; ++g)
+            if (reinterpret_cast<intptr_t>(V[g].X) - reinterpret_cast<intptr_t>(V[0].X) !=
+                    (intptr_t)g * d ||
+                V[g].map != V[0].map || V[g].ld != V[0].ld || V[g].flat != V[0].flat)
+                return false;
+        stride = (int64_t)(d / (intptr_t)sizeof(float2));
+        return true;
+    };
+    int64_t dxA = 0, dxB = 0;
+    const bool batchA = !(tf32_fused && eff == QCS_MODE_TF32X) && one_stride(Av, fusedA, dxA);
+    const bool batchB = !(tf32_fused && eff == QCS_MODE_TF32X) && one_stride(Bv, fusedB, dxB);
+    // constant descriptors of the whole group in one launch
+    const bool const_desc = !d_desc_in && eff != QCS_MODE_AUTO && eff != QCS_MODE_FP16X_SCALED &&
+                            (eff != QCS_MODE_FP32 || d_desc_out);
+    if (const_desc) {
+        e = launch_set_desc(desc, eff, s, G);
+        if (e != cudaSuccess) return QCS_ERR_CUDA;
+    }
     for (int g = 0; g < G; ++g) {
         OperandView &A = Av[g], &B = Bv[g];
         qcs_gemm_desc_t *dg = desc + g;
@@ -364,37 +414,26 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                                            partials, partials + 5 * (gA + gB), dg, h->d_counts,
                                            8.0 * (double)m * (double)n * (double)k, s);
             if (e != cudaSuccess) return QCS_ERR_CUDA;
-        } else if (eff != QCS_MODE_FP32 || d_desc_out) {
-            // A plain FP32 GEMM runs ungated; it needs a descriptor only to report it.
-            e = launch_set_desc(dg, eff, s);
-            if (e != cudaSuccess) return QCS_ERR_CUDA;
         }
+        // (a plain FP32 GEMM runs ungated; it needs a descriptor only to report it)
         if (!emulated || (tf32_fused && eff == QCS_MODE_TF32X)) continue;
-        // The split writes with the selected kind's element size; the pitch
-        // is kp elements either way, so both tensor maps below describe it.
-        // Instance g owns rows [g R_pad, (g + 1) R_pad) of every plane.
-        int64_t sr, sc;
-        ProfScope ps(h, kProfSplit);
-        if (fusedA) {
-            e = launch_split_gather(dg, 0, A.map->rank, A.map->dims, A.map->strides, A.X, m,
-                                    planesA, kp, G * mp * kp, s, 0, g * mp * kp, sepA32);
-        } else {
-            plane_strides(0, opA, A.ld, sr, sc);
-            e = launch_split(dg, 0, A.X, sr, sc, opA == QCS_OP_C, m, k, mp, kp, planesA, kp,
-                             G * mp * kp, s, 0, g * mp * kp, sepA32, tf32_fused ? 1 : 0);
-        }
-        if (e == cudaSuccess) {
-            if (fusedB) {
-                e = launch_split_gather(dg, 1, B.map->rank, B.map->dims, B.map->strides, B.X, k,
-                                        planesB, kp, G * np * kp, s, 1, g * np * kp, sepB32);
-            } else {
-                plane_strides(1, opB, B.ld, sr, sc);
-                e = launch_split(dg, 1, B.X, sr, sc, opB == QCS_OP_C, n, k, np, kp, planesB, kp,
-                                 G * np * kp, s, 1, g * np * kp, sepB32, tf32_fused ? 1 : 0);
-            }
-        }
-        if (e != cudaSuccess) return QCS_ERR_CUDA;
+        if (!batchA)
+            if (int r = split_operand(h, 0, dg, A, opA, m, k, mp, kp, planesA, G * mp * kp,
+                                      g * mp * kp, sepA32, fusedA, tf32_fused, SplitBatch{}))
+                return r;
+        if (!batchB)
+            if (int r = split_operand(h, 1, dg, B, opB, n, k, np, kp, planesB, G * np * kp,
+                                      g * np * kp, sepB32, fusedB, tf32_fused, SplitBatch{}))
+                return r;
     }
+    if (batchA)
+        if (int r = split_operand(h, 0, desc, Av[0], opA, m, k, mp, kp, planesA, G * mp * kp, 0,
+                                  sepA32, fusedA, tf32_fused, SplitBatch{G, dxA, mp * kp}))
+            return r;
+    if (batchB)
+        if (int r = split_operand(h, 1, desc, Bv[0], opB, n, k, np, kp, planesB, G * np * kp, 0,
+                                  sepB32, fusedB, tf32_fused, SplitBatch{G, dxB, np * kp}))
+            return r;
 
     if (k == 0) {
         // C = beta C: the SIMT kernel with k = 0 does exactly that (no desc gate).

@@ -176,8 +176,18 @@ int stats2_blocks(int64_t nel, int num_sms);
 // Select from two finished qcs_stats_t.
 cudaError_t launch_select_from_stats(const qcs_stats_t *a, const qcs_stats_t *b, double tol,
                                      qcs_gemm_desc_t *desc, cudaStream_t s);
-// Write a constant descriptor (forced mode).
-cudaError_t launch_set_desc(qcs_gemm_desc_t *desc, int mode, cudaStream_t s);
+// Write ``count`` constant descriptors (forced mode).
+cudaError_t launch_set_desc(qcs_gemm_desc_t *desc, int mode, cudaStream_t s, int count = 1);
+
+// The splits of the same operand of ``count`` equal-shape GEMMs in one
+// launch: instance g reads its operand in_stride elements after that of
+// instance g - 1, takes descriptor desc + g, and writes its rows
+// off_stride elements after those of instance g - 1 in every plane.
+struct SplitBatch {
+    int count = 1;
+    int64_t in_stride = 0;
+    int64_t off_stride = 0;
+};
 
 // Split op(X) into 4 planes (R x K, row pitch ``pitch`` elements, planes
 // ``plane_stride`` elements apart); rows >= R or columns >= K up to
@@ -195,7 +205,7 @@ cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X
                          int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
                          void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
                          int planes6 = 0, int64_t plane_off = 0, void *planes32 = nullptr,
-                         int skip_tf32 = 0);
+                         int skip_tf32 = 0, const SplitBatch &sb = SplitBatch{});
 
 // The split stage reading its operand through a gather map (the reshape of
 // a contraction folded into the split pass): op(X) is the rows x cols
@@ -211,7 +221,7 @@ cudaError_t launch_split_gather(const qcs_gemm_desc_t *desc, int which, int rank
                                 const int64_t *dims, const int64_t *strides, const float2 *src,
                                 int64_t rows, void *planes, int64_t pitch, int64_t plane_stride,
                                 cudaStream_t s, int planes6 = 0, int64_t plane_off = 0,
-                                void *planes32 = nullptr);
+                                void *planes32 = nullptr, const SplitBatch &sb = SplitBatch{});
 cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
                            const float2 *in, float2 *out, int64_t *stats_partials, int gstats,
                            cudaStream_t s, const CopyBatch &cb = CopyBatch{});

@@ -230,11 +230,13 @@ __global__ void select_from_stats_kernel(const qcs_stats_t *a, const qcs_stats_t
     if (threadIdx.x == 0) select_rule(summarize(hA), summarize(hB), tol, QCS_MODE_AUTO, desc);
 }
 
-__global__ void set_desc_kernel(qcs_gemm_desc_t *desc, int mode) {
-    desc->mode = mode;
-    desc->sA = 0;
-    desc->sB = 0;
-    desc->reserved = 0;
+__global__ void set_desc_kernel(qcs_gemm_desc_t *desc, int mode, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        desc[i].mode = mode;
+        desc[i].sA = 0;
+        desc[i].sB = 0;
+        desc[i].reserved = 0;
+    }
 }
 
 __global__ void stats_finalize_kernel(const int64_t *__restrict__ partials, int g, int64_t n,
@@ -611,8 +613,9 @@ cudaError_t launch_select_from_stats(const qcs_stats_t *a, const qcs_stats_t *b,
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_desc(qcs_gemm_desc_t *desc, int mode, cudaStream_t s) {
-    set_desc_kernel<<<1, 1, 0, s>>>(desc, mode);
+cudaError_t launch_set_desc(qcs_gemm_desc_t *desc, int mode, cudaStream_t s, int count) {
+    if (count < 1) return cudaSuccess;
+    set_desc_kernel<<<(count + 255) / 256, 256, 0, s>>>(desc, mode, count);
     return cudaGetLastError();
 }
 
@@ -671,7 +674,10 @@ __global__ void __launch_bounds__(256, 8) split_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int which, const float2 *__restrict__ X, int64_t sr,
     int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad, void *planes,
     int64_t pitch, int64_t plane_stride, int planes6, int64_t plane_off, void *planes32,
-    int skip_tf32) {
+    int skip_tf32, int64_t x_bstride, int64_t off_bstride) {
+    desc += blockIdx.z;  // instance z of a batch (SplitBatch)
+    X += blockIdx.z * x_bstride;
+    plane_off += blockIdx.z * off_bstride;
     const int mode = desc->mode;
     if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO || (skip_tf32 && mode == QCS_MODE_TF32X))
         return;
@@ -783,12 +789,15 @@ __global__ void __launch_bounds__(256, 8) split_kernel(
 cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
                          int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
                          void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
-                         int planes6, int64_t plane_off, void *planes32, int skip_tf32) {
-    if (R_pad <= 0 || K_pad <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((K_pad + kSplitC - 1) / kSplitC), (unsigned)((R_pad + kSplitR - 1) / kSplitR));
-    if (grid.y > 65535u) return cudaErrorInvalidValue;
+                         int planes6, int64_t plane_off, void *planes32, int skip_tf32,
+                         const SplitBatch &sb) {
+    if (R_pad <= 0 || K_pad <= 0 || sb.count < 1) return cudaSuccess;
+    dim3 grid((unsigned)((K_pad + kSplitC - 1) / kSplitC), (unsigned)((R_pad + kSplitR - 1) / kSplitR),
+              (unsigned)sb.count);
+    if (grid.y > 65535u || sb.count > 65535) return cudaErrorInvalidValue;
     split_kernel<<<grid, 256, 0, s>>>(desc, which, X, sr, sc, conj, R, K, R_pad, K_pad, planes,
-                                      pitch, plane_stride, planes6, plane_off, planes32, skip_tf32);
+                                      pitch, plane_stride, planes6, plane_off, planes32, skip_tf32,
+                                      sb.in_stride, sb.off_stride);
     return cudaGetLastError();
 }
 
@@ -1119,7 +1128,16 @@ struct SplitOut {
     int planes6;  // the five-plane op(B) layout of the GEMM path
     int64_t off;  // element offset of this operand's rows in every plane
     void *planes32;  // not NULL: the planes of a TF32 selection (else ``planes``)
+    int64_t off_bstride;  // batch (blockIdx.y = g): desc + g, rows g off_bstride further
 };
+
+// The SplitOut of instance blockIdx.y of a batched split.
+__device__ __forceinline__ SplitOut batch_split_out(const SplitOut &so) {
+    SplitOut r = so;
+    r.desc = so.desc + blockIdx.y;
+    r.off = so.off + blockIdx.y * so.off_bstride;
+    return r;
+}
 
 __device__ __forceinline__ int64_t batch_in(const CopyParams &P) {
     const int64_t g = blockIdx.y;
@@ -1162,9 +1180,10 @@ template <bool SPLIT>
 __global__ void __launch_bounds__(256, SPLIT ? 4 : 5) copy_tiled_kernel(CopyParams P,
                                                             const float2 *__restrict__ in,
                                                             float2 *__restrict__ out,
-                                                            int accumulate, SplitOut so) {
+                                                            int accumulate, SplitOut so_batch) {
     int mode = 0, scale = 0;
     Pow2Scale pscale;
+    const SplitOut so = SPLIT ? batch_split_out(so_batch) : so_batch;
     if (SPLIT) {
         mode = so.desc->mode;
         if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
@@ -1402,7 +1421,8 @@ constexpr int kQuadMaxTiles = 64;  // tiles (rest indices) per block, at most
 template <bool P5>
 __global__ void __launch_bounds__(256, 4) split_quads_kernel(CopyParams P,
                                                              const float2 *__restrict__ in,
-                                                             SplitOut so, int tpb) {
+                                                             SplitOut so_batch, int tpb) {
+    const SplitOut so = batch_split_out(so_batch);
     const int mode = so.desc->mode;
     if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO) return;
     const int scale =
@@ -1677,14 +1697,16 @@ bool split_gather_supported(int which, int rank, const int64_t *dims, const int6
 cudaError_t launch_split_gather(const qcs_gemm_desc_t *desc, int which, int rank,
                                 const int64_t *dims, const int64_t *strides, const float2 *src,
                                 int64_t rows, void *planes, int64_t pitch, int64_t plane_stride,
-                                cudaStream_t s, int planes6, int64_t plane_off, void *planes32) {
+                                cudaStream_t s, int planes6, int64_t plane_off, void *planes32,
+                                const SplitBatch &sb) {
     CopyParams P;
     if (!split_gather_params(which, rank, dims, strides, rows, pitch, P))
         return cudaErrorNotSupported;
     const int64_t blocks = finish_tiled(P);
-    if (blocks == 0) return cudaSuccess;
-    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
-    SplitOut so{desc, which, planes, plane_stride, planes6, plane_off, planes32};
+    if (blocks == 0 || sb.count < 1) return cudaSuccess;
+    if (blocks > INT32_MAX || sb.count > 65535) return cudaErrorInvalidValue;
+    P.bin = sb.in_stride;  // instance blockIdx.y reads from src + y in_stride
+    SplitOut so{desc, which, planes, plane_stride, planes6, plane_off, planes32, sb.off_stride};
     // quads: every output run of four elements lies inside the X run and
     // starts at a multiple of 4 in every plane
     bool quads = P.px % 4 == 0 && plane_off % 4 == 0 && plane_stride % 4 == 0;
@@ -1700,19 +1722,21 @@ cudaError_t launch_split_gather(const qcs_gemm_desc_t *desc, int which, int rank
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return cudaGetLastError();
-        const int64_t xy = P.tiles_x * P.tiles_y, wave = 4 * (int64_t)sms;
+        const int64_t xy = P.tiles_x * P.tiles_y * sb.count, wave = 4 * (int64_t)sms;
         const int64_t min_blocks = xy * ((P.rest + kQuadMaxTiles - 1) / kQuadMaxTiles);
         const int64_t want = ((min_blocks + wave - 1) / wave) * wave;
         const int64_t chunks = std::max<int64_t>(1, want / xy);
         const int tpb = (int)std::min<int64_t>(kQuadMaxTiles, (P.rest + chunks - 1) / chunks);
-        const int64_t qblocks = xy * ((P.rest + tpb - 1) / tpb);
+        const int64_t qblocks = P.tiles_x * P.tiles_y * ((P.rest + tpb - 1) / tpb);
         if (qblocks > INT32_MAX) return cudaErrorInvalidValue;
+        const dim3 grid((unsigned)qblocks, (unsigned)sb.count);
         if (planes6)
-            split_quads_kernel<true><<<dim3((unsigned)qblocks, 1), 256, 0, s>>>(P, src, so, tpb);
+            split_quads_kernel<true><<<grid, 256, 0, s>>>(P, src, so, tpb);
         else
-            split_quads_kernel<false><<<dim3((unsigned)qblocks, 1), 256, 0, s>>>(P, src, so, tpb);
+            split_quads_kernel<false><<<grid, 256, 0, s>>>(P, src, so, tpb);
     } else {
-        copy_tiled_kernel<true><<<dim3((unsigned)blocks, 1), 256, 0, s>>>(P, src, nullptr, 0, so);
+        copy_tiled_kernel<true><<<dim3((unsigned)blocks, (unsigned)sb.count), 256, 0, s>>>(
+            P, src, nullptr, 0, so);
     }
     return cudaGetLastError();
 }
