@@ -90,6 +90,9 @@ def parse(argv=None):
     p.add_argument("--no-levels", action="store_true",
                    help="run contraction trees step by step in plan order (default: level "
                         "launches of the small plain-FP32 steps, qcs_set_tree_levels)")
+    p.add_argument("--group-budget-mb", type=int, default=None,
+                   help="bytes (MiB) a grouped GPU-filling tree step may hold (qcs_set_group_budget; "
+                        "default: the library's 32 GiB; 0: such steps one instance at a time)")
     p.add_argument("--instance-batch", type=int, default=16,
                    help="contraction instances per group (plain-FP32 steps batched)")
     p.add_argument("--legs-file", default=None,
@@ -446,6 +449,8 @@ def main():
     args = parse()
     if args.no_levels:
         os.environ["QCS_TREE_LEVELS"] = "0"  # read by every handle at creation
+    if args.group_budget_mb is not None:
+        os.environ["QCS_GROUP_BUDGET_MB"] = str(args.group_budget_mb)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
