@@ -468,6 +468,25 @@ int qcs_contract_tree_backward(qcs_handle_t h, const qcs_tree_t *tree,
                                const qcs_c32 *const *leaves, const double *d_grad_out,
                                qcs_c32 *const *d_grad_leaves, qcs_run_info_t *info);
 
+/* FP64 reductions of a result against a reference (Section 5.3 measures
+ * amplitudes by their fidelity and error against an exact reference; these
+ * are the only FP64 arithmetic on the GPU besides the slice sums).  a
+ * (device, n complex: complex128 as interleaved doubles, or complex64 when
+ * a_c64 is 1) and ref (device, n complex128, or NULL: then only the norm of
+ * a) give, in d_out (device, 6 doubles):
+ *   [0] sum |a_j|^2        [1] sum |ref_j|^2
+ *   [2] Re sum conj(ref_j) a_j   [3] Im of the same
+ *   [4] sum |a_j - ref_j|^2     [5] max_j |a_j - ref_j|
+ * so that the fidelity is (d[2]^2 + d[3]^2) / (d[0] d[1]) and the relative
+ * L2 error sqrt(d[4] / d[1]); entries that need ref are 0 without it.  Every
+ * sum is formed in FP64 in a fixed order (per-block partials, then one block
+ * in a fixed tree), so the result does not depend on scheduling.
+ * Asynchronous on the handle's stream; n >= 0; QCS_ERR_INVALID_ARG for NULL
+ * a or d_out, or misaligned pointers (8-byte for complex64, 16 for
+ * complex128). */
+int qcs_fidelity_stats(qcs_handle_t h, const void *a, int a_c64, const double *ref, int64_t n,
+                       double *d_out);
+
 /* qcs_cgemm without a handle and without allocating device memory.  (The
  * paper has no counterpart: this serves callers that must not allocate at
  * call time -- their device memory is owned by another allocator with a

@@ -304,6 +304,39 @@ def selection_stats(h: Handle, A, B, *, opA=OP_N, opB=OP_N):
     return res, (int(d.mode), int(d.sA), int(d.sB))
 
 
+def fidelity_stats(h: Handle, a, ref=None) -> dict:
+    """FP64 sums on the GPU (qcs_fidelity_stats) of a (complex128 or
+    complex64 CUDA tensor) against ref (complex128 CUDA tensor of the same
+    number of elements, or None): norms, overlap, error; with ref also the
+    fidelity |<ref|a>|^2 / (<a|a><ref|ref>) and the relative L2 error.
+    Synchronises to return host floats."""
+    import torch
+
+    a = a.contiguous()
+    if a.dtype not in (torch.complex128, torch.complex64):
+        raise TypeError("a must be complex128 or complex64")
+    n = a.numel()
+    r = None
+    if ref is not None:
+        r = ref.contiguous()
+        if r.dtype != torch.complex128 or r.numel() != n:
+            raise ValueError("ref must be complex128 with as many elements as a")
+    out = torch.zeros(6, dtype=torch.float64, device=a.device)
+    _lib.check(h.lib.qcs_fidelity_stats(h.ptr, ctypes.c_void_p(a.data_ptr()),
+                                        1 if a.dtype == torch.complex64 else 0,
+                                        ctypes.c_void_p(r.data_ptr()) if r is not None else None,
+                                        n, ctypes.c_void_p(out.data_ptr())),
+               "qcs_fidelity_stats")
+    v = out.cpu().tolist()
+    res = {"norm2": v[0]}
+    if r is not None:
+        res.update({"ref_norm2": v[1], "overlap": complex(v[2], v[3]), "err2": v[4],
+                    "max_abs_err": v[5],
+                    "fidelity": (v[2] ** 2 + v[3] ** 2) / (v[0] * v[1]) if v[0] * v[1] > 0 else 0.0,
+                    "rel_l2_err": (v[4] / v[1]) ** 0.5 if v[1] > 0 else float("inf")})
+    return res
+
+
 def sgemm(h: Handle, A, B, C=None, *, m=None, n=None, k=None, alpha=1.0, beta=0.0,
           opA=OP_N, opB=OP_N, mode="auto", desc_out=None):
     """C = alpha op(A) op(B) + beta C for real matrices with qcs_sgemm;

@@ -36,7 +36,7 @@ EXPORTED = [
     "qcs_get_tuning", "qcs_set_tuning", "qcs_set_instance_batch", "qcs_set_tc_schedule",
     "qcs_set_tc_splits", "qcs_sgemm", "qcs_set_complex_products", "qcs_set_wait_budget",
     "qcs_debug_stall_producer", "qcs_cgemm_noalloc_status", "qcs_measure_fma_peak",
-    "qcs_set_fused_split", "qcs_set_tree_levels", "qcs_set_group_budget",
+    "qcs_set_fused_split", "qcs_set_tree_levels", "qcs_set_group_budget", "qcs_fidelity_stats",
     "qcs_selection_stats", "qcs_tree_backward_graph_create",
 ]
 SIZE_RULE_OFF, SIZE_RULE_PAPER, SIZE_RULE_TUNED = 0, 1, 2
@@ -172,6 +172,7 @@ def load(path: str = LIB_PATH):
         "qcs_set_fused_split": [H, I],
         "qcs_set_tree_levels": [H, I],
         "qcs_set_group_budget": [H, ctypes.c_uint64],
+        "qcs_fidelity_stats": [H, P, I, P, I64, P],
         "qcs_selection_stats": [H, I, I, I64, I64, I64, P, I64, P, I64,
                                 ctypes.POINTER(qcs_selection_stats_t), ctypes.POINTER(qcs_gemm_desc_t)],
     }

@@ -949,6 +949,23 @@ int qcs_set_group_budget(qcs_handle_t h, uint64_t bytes) {
     return QCS_SUCCESS;
 }
 
+int qcs_fidelity_stats(qcs_handle_t h, const void *a, int a_c64, const double *ref, int64_t n,
+                       double *d_out) {
+    if (!h || !a || !d_out || n < 0 || (a_c64 != 0 && a_c64 != 1)) return QCS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(a) & (a_c64 ? 7u : 15u)) ||
+        (ref && (reinterpret_cast<uintptr_t>(ref) & 15u)) ||
+        (reinterpret_cast<uintptr_t>(d_out) & 7u))
+        return QCS_ERR_INVALID_ARG;
+    // a fixed block count for a given n, so the summation order depends on n alone
+    const int blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>((n + 255) / 256, std::min(kFidBlocksMax, 4 * h->num_sms)));
+    if (int r = ensure_workspace(h->ws, sizeof(double) * 6 * (size_t)blocks)) return r;
+    return launch_fidelity_stats(a, a_c64, ref, n, static_cast<double *>(h->ws.ptr), blocks,
+                                 d_out, h->stream) == cudaSuccess
+               ? QCS_SUCCESS
+               : QCS_ERR_CUDA;
+}
+
 int qcs_set_tree_levels(qcs_handle_t h, int enabled) {
     if (!h || (enabled != 0 && enabled != 1)) return QCS_ERR_INVALID_ARG;
     h->tree_levels = enabled;

@@ -176,7 +176,13 @@ int stats2_blocks(int64_t nel, int num_sms);
 // Select from two finished qcs_stats_t.
 cudaError_t launch_select_from_stats(const qcs_stats_t *a, const qcs_stats_t *b, double tol,
                                      qcs_gemm_desc_t *desc, cudaStream_t s);
-// Write ``count`` constant descriptors (forced mode).
+// FP64 sums of a result against a reference (qcs_fidelity_stats): per-block
+// partials (6 doubles per block, ``blocks`` blocks) then one block.
+constexpr int kFidBlocksMax = 1024;
+cudaError_t launch_fidelity_stats(const void *a, int a_c64, const double *ref, int64_t n,
+                                  double *partials, int blocks, double *out, cudaStream_t s);
+
+// Write a constant descriptor (forced mode).
 cudaError_t launch_set_desc(qcs_gemm_desc_t *desc, int mode, cudaStream_t s, int count = 1);
 
 // The splits of the same operand of ``count`` equal-shape GEMMs in one

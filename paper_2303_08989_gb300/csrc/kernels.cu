@@ -2000,6 +2000,89 @@ cudaError_t launch_tree_small_bwd(const TreeSmallBwd *steps, int n_steps, int in
 }
 
 // ===========================================================================
+// FP64 fidelity and error sums (qcs_fidelity_stats)
+// ===========================================================================
+
+namespace {
+
+constexpr int kFidThreads = 256;
+
+// The six quantities of one block in shared memory, summed (max for [5])
+// over the block in a fixed tree.
+__device__ void fid_block_reduce(double (&v)[6], double (*sh)[kFidThreads]) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] = v[q];
+    __syncthreads();
+    for (int w = kFidThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+            sh[5][threadIdx.x] = fmax(sh[5][threadIdx.x], sh[5][threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+}
+
+// Block b sums the elements j = b, b + G, ... in one thread each, thread t
+// of the block taking every kFidThreads-th of them, then the block's tree.
+__global__ void __launch_bounds__(kFidThreads) fidelity_partials_kernel(
+    const void *__restrict__ a, int a_c64, const double2 *__restrict__ ref, int64_t n,
+    double *__restrict__ partials) {
+    __shared__ double sh[6][kFidThreads];
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t j = blockIdx.x * (int64_t)kFidThreads + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * kFidThreads) {
+        double2 x;
+        if (a_c64) {
+            const float2 f = reinterpret_cast<const float2 *>(a)[j];
+            x = make_double2((double)f.x, (double)f.y);
+        } else {
+            x = reinterpret_cast<const double2 *>(a)[j];
+        }
+        v[0] = fma(x.x, x.x, fma(x.y, x.y, v[0]));
+        if (ref) {
+            const double2 r = ref[j];
+            v[1] = fma(r.x, r.x, fma(r.y, r.y, v[1]));
+            v[2] = fma(r.x, x.x, fma(r.y, x.y, v[2]));   // Re conj(r) x
+            v[3] = fma(r.x, x.y, fma(-r.y, x.x, v[3]));  // Im conj(r) x
+            const double dx = x.x - r.x, dy = x.y - r.y;
+            const double d2 = fma(dx, dx, dy * dy);
+            v[4] += d2;
+            v[5] = fmax(v[5], sqrt(d2));
+        }
+    }
+    fid_block_reduce(v, sh);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 6; ++q) partials[(int64_t)blockIdx.x * 6 + q] = sh[q][0];
+}
+
+__global__ void __launch_bounds__(kFidThreads) fidelity_final_kernel(
+    const double *__restrict__ partials, int blocks, double *__restrict__ out) {
+    __shared__ double sh[6][kFidThreads];
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < blocks; b += kFidThreads) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) v[q] += partials[(int64_t)b * 6 + q];
+        v[5] = fmax(v[5], partials[(int64_t)b * 6 + 5]);
+    }
+    fid_block_reduce(v, sh);
+    if (threadIdx.x < 6) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+}  // namespace
+
+cudaError_t launch_fidelity_stats(const void *a, int a_c64, const double *ref, int64_t n,
+                                  double *partials, int blocks, double *out, cudaStream_t s) {
+    if (blocks < 1 || blocks > kFidBlocksMax) return cudaErrorInvalidValue;
+    fidelity_partials_kernel<<<blocks, kFidThreads, 0, s>>>(
+        a, a_c64, reinterpret_cast<const double2 *>(ref), n, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    fidelity_final_kernel<<<1, kFidThreads, 0, s>>>(partials, blocks, out);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
 // Plain FP32 CGEMM on the CUDA cores
 // ===========================================================================
 
