@@ -57,6 +57,12 @@ struct Layout {
     std::vector<int32_t> tab_a, tab_b;  // start of each small step's tables in ``tab``
     size_t out_index = 0, offsets = 0, bufA = 0, bufB = 0, tmpA = 0, tmpB = 0, gemm = 0, total = 0;
     size_t small_desc = 0, small_tab = 0, small_bwd = 0;
+    // backward in groups (G > 1): each instance's leaf gradients in its own
+    // zeroed buffer of lgrad_stride elements (leaf i at lgrad_off[i]), added
+    // into the caller's in instance order after the group (leaf_tab)
+    size_t lgrad = 0, leaf_tab = 0;
+    int64_t lgrad_stride = 0, max_leaf = 0;
+    std::vector<int64_t> lgrad_off;
     size_t gemm_bytes = 0, inter_bytes = 0;
 };
 
@@ -379,16 +385,23 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
                                       (int)gb));
         }
         if (backward) {
+            // the two adjoint GEMMs, for the whole group (batched FP32 with a
+            // split-K buffer per instance, or grouped emulated)
+            const int eA = effective_mode(h, st.mode, QCS_OP_N, QCS_OP_C, st.m, st.k, st.n);
+            const int eB = effective_mode(h, st.mode, QCS_OP_C, QCS_OP_N, st.k, st.n, st.m);
             gemm = std::max(gemm, gemm_workspace_bytes(
-                                      effective_mode(h, st.mode, QCS_OP_N, QCS_OP_C, st.m, st.k,
-                                                     st.n),
-                                      st.m, st.k, st.n, h->num_sms,
-                                      gemm_splits(h, QCS_OP_N, QCS_OP_C, st.m, st.k, st.n)));
+                                      eA, st.m, st.k, st.n, h->num_sms,
+                                      gemm_splits(h, QCS_OP_N, QCS_OP_C, st.m, st.k, st.n),
+                                      (int)gb) +
+                                      (eA == QCS_MODE_FP32 ? (size_t)(gb - 1) * kSplitKBytes : 0));
             gemm = std::max(gemm, gemm_workspace_bytes(
-                                      effective_mode(h, st.mode, QCS_OP_C, QCS_OP_N, st.k, st.n,
-                                                     st.m),
-                                      st.k, st.n, st.m, h->num_sms,
-                                      gemm_splits(h, QCS_OP_C, QCS_OP_N, st.k, st.n, st.m)));
+                                      eB, st.k, st.n, st.m, h->num_sms,
+                                      gemm_splits(h, QCS_OP_C, QCS_OP_N, st.k, st.n, st.m),
+                                      (int)gb) +
+                                      (eB == QCS_MODE_FP32 ? (size_t)(gb - 1) * kSplitKBytes : 0));
+            // its gathers and scatters handle the whole group at once
+            maxA = std::max(maxA, st.m * st.k * gb);
+            maxB = std::max(maxB, st.k * st.n * gb);
         }
     }
     L.inter_off.resize(ns);
@@ -412,12 +425,26 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
         L.grad_off.resize(ns);
         for (int s = 0; s < ns; ++s) {
             L.grad_off[s] = p;
-            p += align256(sizeof(float2) * t->steps[s].m * t->steps[s].n);
+            p += align256(sizeof(float2) * t->steps[s].m * t->steps[s].n * (L.batched[s] ? G : 1));
         }
         L.tmpA = p;
         p += align256(sizeof(float2) * maxA);
         L.tmpB = p;
         p += align256(sizeof(float2) * maxB);
+        if (G > 1) {
+            L.lgrad_off.resize(t->n_leaves);
+            int64_t q = 0;
+            for (int i = 0; i < t->n_leaves; ++i) {
+                L.lgrad_off[i] = q;
+                q += (t->leaf_size[i] + 31) / 32 * 32;  // 256-byte aligned per leaf
+                L.max_leaf = std::max(L.max_leaf, t->leaf_size[i]);
+            }
+            L.lgrad_stride = q;
+            L.lgrad = p;
+            p += align256(sizeof(float2) * (size_t)q * G);
+            L.leaf_tab = p;
+            p += align256(sizeof(LeafGradRef) * t->n_leaves);
+        }
     }
     L.gemm = p;
     L.gemm_bytes = gemm;
@@ -718,9 +745,11 @@ int forward_group(const Ctx &c, int inst0, int G, double *d_out) {
 
 // The level launches' step table (device pointers of this call's workspace
 // and leaves) and offset tables, uploaded once per call.
+int upload_leaf_tab(const Ctx &c);
+
 int upload_small(const Ctx &c) {
     const Layout &L = c.L;
-    if (L.small_order.empty()) return QCS_SUCCESS;
+    if (L.small_order.empty()) return upload_leaf_tab(c);
     const int nl = c.t->n_leaves;
     std::vector<TreeSmallStep> desc(L.small_order.size());
     for (size_t q = 0; q < desc.size(); ++q) {
@@ -762,7 +791,10 @@ int upload_small(const Ctx &c) {
     }
     if (!c.grad_leaves) return QCS_SUCCESS;
     // the adjoint's table: operands and their gradients (leaf gradients at
-    // offset 0 here; the kernel adds the instance offset to both)
+    // offset 0 here; the kernel adds the instance offset to both).  In groups
+    // a leaf's gradient goes to the instance's own buffer of the group.
+    const bool grp = L.G > 1;
+    float2 *lgrad = reinterpret_cast<float2 *>(c.ws + L.lgrad);
     std::vector<TreeSmallBwd> bwd(L.small_order.size());
     for (size_t q = 0; q < bwd.size(); ++q) {
         const int s = L.small_order[q];
@@ -771,20 +803,26 @@ int upload_small(const Ctx &c) {
         const int ids[2] = {sp.a, sp.b};
         const float2 **x[2] = {&d.a, &d.b};
         float2 **gx[2] = {&d.ga, &d.gb};
+        int64_t *xs[2] = {&d.a_istride, &d.b_istride};
+        int64_t *gxs[2] = {&d.ga_istride, &d.gb_istride};
         int32_t *leaf[2] = {&d.a_leaf, &d.b_leaf};
         for (int o = 0; o < 2; ++o) {
             const int id = ids[o];
             if (id < nl) {
                 *x[o] = reinterpret_cast<const float2 *>(c.leaves[id]);
-                *gx[o] = reinterpret_cast<float2 *>(c.grad_leaves[id]);
+                *gx[o] = grp ? lgrad + L.lgrad_off[id] : reinterpret_cast<float2 *>(c.grad_leaves[id]);
+                *xs[o] = 0;
+                *gxs[o] = grp ? L.lgrad_stride : 0;
                 *leaf[o] = id;
             } else {
                 *x[o] = inter_ptr(c, id - nl);
                 *gx[o] = grad_ptr(c, id - nl);
+                *xs[o] = *gxs[o] = L.batched[id - nl] ? c.size_of[id] : 0;
                 *leaf[o] = -1;
             }
         }
         d.gc = grad_ptr(c, s);
+        d.gc_istride = L.batched[s] ? sp.m * sp.n : 0;
         d.m = (int32_t)sp.m;
         d.n = (int32_t)sp.n;
         d.k = (int32_t)sp.k;
@@ -797,17 +835,35 @@ int upload_small(const Ctx &c) {
         cudaGetLastError();
         return QCS_ERR_CUDA;
     }
-    return QCS_SUCCESS;
+    return upload_leaf_tab(c);
 }
 
-int forward_instance(const Ctx &c, int inst) { return forward_group(c, inst, 1, nullptr); }
+// The caller's leaf gradients and where each instance's buffer of a group
+// holds them (backward in groups).
+int upload_leaf_tab(const Ctx &c) {
+    const Layout &L = c.L;
+    if (L.G <= 1 || !c.grad_leaves) return QCS_SUCCESS;
+    std::vector<LeafGradRef> tab(c.t->n_leaves);
+    for (int i = 0; i < c.t->n_leaves; ++i)
+        tab[i] = LeafGradRef{reinterpret_cast<float2 *>(c.grad_leaves[i]), c.t->leaf_size[i],
+                             L.lgrad_off[i]};
+    if (cudaMemcpyAsync(c.ws + L.leaf_tab, tab.data(), sizeof(LeafGradRef) * tab.size(),
+                        cudaMemcpyHostToDevice, c.h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return QCS_ERR_CUDA;
+    }
+    return QCS_SUCCESS;
+}
 
 int begin(qcs_handle_t h, const qcs_tree_t *t, bool backward, Ctx &c, Workspace *own = nullptr) {
     if (int r = validate(t, c.size_of, backward)) return r;
     c.h = h;
     c.t = t;
-    const int G = backward ? 1 : std::max(1, std::min(h->instance_batch, t->n_instances));
+    // the backward runs in groups too when every step can hold the group
+    const int G = std::max(1, std::min(h->instance_batch, t->n_instances));
     c.L = plan_layout(h, t, backward, G);
+    if (backward && G > 1 && (t->n_steps == 0 || c.L.P < t->n_steps))
+        c.L = plan_layout(h, t, backward, 1);
     Workspace &w = own ? *own : h->tree_ws;
     if (int r = ensure_workspace(w, c.L.total)) return r;
     c.ws = static_cast<uint8_t *>(w.ptr);
@@ -818,7 +874,7 @@ int begin(qcs_handle_t h, const qcs_tree_t *t, bool backward, Ctx &c, Workspace 
             return QCS_ERR_CUDA;
         }
     }
-    if ((G > 1 || !c.L.small_order.empty()) &&
+    if ((c.L.G > 1 || !c.L.small_order.empty()) &&
         cudaMemcpyAsync(c.ws + c.L.offsets, t->instance_offset,
                         sizeof(int64_t) * (size_t)t->n_instances * t->n_leaves,
                         cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
@@ -855,80 +911,166 @@ int backward_all(Ctx &c, const double *d_grad_out, qcs_c32 *const *d_grad_leaves
     const qcs_tree_t *tree = c.t;
     qcs_handle_t h = c.h;
     qcs_run_info_t *info = c.info;
+    const Layout &L = c.L;
     const std::vector<int64_t> &size_of = c.size_of;
     const int nl = tree->n_leaves, ns = tree->n_steps;
     cudaStream_t s = h->stream;
-    auto scatter_into = [&](int id, int inst, const qcs_gather_t &g, const float2 *src) -> int {
-        if (info) info->gather_count++;
+    // G > 1: a group's instances at once; their intermediates and gradients
+    // at one stride, each one's leaf gradients in its own buffer (lgrad)
+    const int G = L.G;
+    const bool grp = G > 1;
+    const std::vector<Item> &seq = grp ? L.seq_b : L.seq_i;
+    const int64_t *offs = reinterpret_cast<const int64_t *>(c.ws + L.offsets);
+    float2 *lgrad = reinterpret_cast<float2 *>(c.ws + L.lgrad);
+    float2 *Am = reinterpret_cast<float2 *>(c.ws + L.bufA);
+    float2 *Bm = reinterpret_cast<float2 *>(c.ws + L.bufB);
+    float2 *gA = reinterpret_cast<float2 *>(c.ws + L.tmpA);
+    float2 *gB = reinterpret_cast<float2 *>(c.ws + L.tmpB);
+    // operand ``id`` of the instances inst0 .. inst0 + Gc - 1 gathered into
+    // buf, elems complex apart
+    auto gather_op = [&](int id, const qcs_gather_t &map, int inst0, int Gc, int64_t elems,
+                         float2 *buf) -> int {
+        if (!grp) return gather(c, map, tensor_ptr(c, id, inst0), buf);
+        CopyBatch cb;
+        cb.count = Gc;
+        cb.out_stride = elems;
+        const float2 *src;
+        if (id < nl) {
+            src = reinterpret_cast<const float2 *>(c.leaves[id]);
+            cb.off = offs + (int64_t)inst0 * nl + id;
+            cb.off_stride = nl;
+        } else {
+            src = inter_ptr(c, id - nl);
+            cb.in_stride = size_of[id];
+        }
+        return gather(c, map, src, buf, cb);
+    };
+    // an operand gradient scattered back through the map that gathered the
+    // operand: added into a leaf's gradient (alone) or stored into the
+    // instance's own leaf buffer (groups); stored into an intermediate's
+    auto scatter_op = [&](int id, const qcs_gather_t &g, int inst0, int Gc, const float2 *src,
+                          int64_t elems) -> int {
+        if (info) info->gather_count += Gc;
         ProfScope ps(h, kProfPermute);
         cudaError_t e;
-        if (id < nl) {
+        CopyBatch cb;
+        cb.count = Gc;
+        cb.in_stride = elems;
+        if (!grp && id < nl) {
             float2 *dst = reinterpret_cast<float2 *>(d_grad_leaves[id]) +
-                          tree->instance_offset[(int64_t)inst * nl + id];
+                          tree->instance_offset[(int64_t)inst0 * nl + id];
             e = launch_scatter(g.rank, g.dims, g.strides, 0, src, dst, 1, s);
+        } else if (id < nl) {
+            cb.out_stride = L.lgrad_stride;
+            cb.out_off = offs + (int64_t)inst0 * nl + id;
+            cb.out_off_stride = nl;
+            e = launch_scatter(g.rank, g.dims, g.strides, 0, src, lgrad + L.lgrad_off[id], 0, s, cb);
         } else {
-            e = launch_scatter(g.rank, g.dims, g.strides, 0, src, grad_ptr(c, id - nl), 0, s);
+            cb.out_stride = size_of[id];
+            e = launch_scatter(g.rank, g.dims, g.strides, 0, src, grad_ptr(c, id - nl), 0, s, cb);
         }
         return e == cudaSuccess ? QCS_SUCCESS : QCS_ERR_CUDA;
     };
-    for (int inst = 0; inst < tree->n_instances; ++inst) {
-        if (int r = forward_instance(c, inst)) return r;
-        const int64_t slot = tree->instance_slot[inst];
-        const double *g = d_grad_out + 2 * slot * tree->out_size;
-        // seed the root's gradient
-        float2 *groot;
+    // one adjoint GEMM for the group: a batched plain-FP32 launch, or one
+    // grouped emulated sequence; operands and results sA, sB, sC apart
+    auto adj_gemm = [&](int mode, int opA, int opB, int64_t m, int64_t n, int64_t k,
+                        const float2 *A, int64_t lda, int64_t sA, const float2 *B, int64_t ldb,
+                        int64_t sB, float2 *C, int64_t sC, int Gc) -> int {
+        if (!grp) return gemm(c, mode, opA, opB, m, n, k, A, lda, B, ldb, C);
+        const int eff = effective_mode(h, mode, opA, opB, m, n, k);
+        count_gemm(c, eff, m, n, k, Gc);
+        if (eff == QCS_MODE_FP32) {
+            GemmBatch bt;
+            bt.count = Gc;
+            bt.sA = sA;
+            bt.sB = sB;
+            bt.sC = sC;
+            return run_cgemm(h, c.ws + L.gemm, eff, opA, opB, m, n, k, make_float2(1.f, 0.f), A,
+                             lda, B, ldb, make_float2(0.f, 0.f), C, m, nullptr, nullptr, bt);
+        }
+        std::vector<OperandView> va(Gc), vb(Gc);
+        for (int g = 0; g < Gc; ++g) {
+            va[g].X = A + g * sA;
+            va[g].ld = lda;
+            vb[g].X = B + g * sB;
+            vb[g].ld = ldb;
+        }
+        return run_cgemm_group(h, c.ws + L.gemm, eff, opA, opB, m, n, k, make_float2(1.f, 0.f),
+                               va.data(), vb.data(), Gc, make_float2(0.f, 0.f), C, m, sC, nullptr,
+                               nullptr);
+    };
+    for (int inst0 = 0; inst0 < tree->n_instances; inst0 += G) {
+        const int Gc = std::min(G, tree->n_instances - inst0);
+        if (grp && cudaMemsetAsync(lgrad, 0, sizeof(float2) * (size_t)L.lgrad_stride * Gc, s) !=
+                       cudaSuccess) {
+            cudaGetLastError();
+            return QCS_ERR_CUDA;
+        }
+        if (int r = forward_group(c, inst0, Gc, nullptr)) return r;
+        // seed the roots' gradients
         if (ns > 0) {
-            groot = grad_ptr(c, ns - 1);
-            if (cudaMemsetAsync(groot, 0, sizeof(float2) * size_of[nl + ns - 1], s) != cudaSuccess) {
+            const int64_t rs = size_of[nl + ns - 1];
+            float2 *groot = grad_ptr(c, ns - 1);
+            if (cudaMemsetAsync(groot, 0, sizeof(float2) * rs * Gc, s) != cudaSuccess) {
                 cudaGetLastError();
                 return QCS_ERR_CUDA;
             }
-        } else {
-            groot = reinterpret_cast<float2 *>(d_grad_leaves[0]) + tree->instance_offset[(int64_t)inst * nl];
+            for (int r = 0; r < Gc; ++r) {
+                const int64_t slot = tree->instance_slot[inst0 + r];
+                if (launch_seed_grad(d_grad_out + 2 * slot * tree->out_size, dev_index(c),
+                                     groot + r * rs, tree->out_size, s) != cudaSuccess)
+                    return QCS_ERR_CUDA;
+            }
+        } else {  // a lone leaf (groups need a step)
+            float2 *groot = reinterpret_cast<float2 *>(d_grad_leaves[0]) +
+                            tree->instance_offset[(int64_t)inst0 * nl];
+            const int64_t slot = tree->instance_slot[inst0];
+            if (launch_seed_grad(d_grad_out + 2 * slot * tree->out_size, dev_index(c), groot,
+                                 tree->out_size, s) != cudaSuccess)
+                return QCS_ERR_CUDA;
         }
-        if (launch_seed_grad(g, dev_index(c), groot, tree->out_size, s) != cudaSuccess)
-            return QCS_ERR_CUDA;
         // the steps in the reverse of the order the forward ran them: a
         // step's output gradient is complete once its consumer (a later step,
         // at a higher level) has run
-        for (auto it = c.L.seq_i.rbegin(); it != c.L.seq_i.rend(); ++it) {
+        for (auto it = seq.rbegin(); it != seq.rend(); ++it) {
             if (it->step < 0) {
                 if (info) {
                     info->level_launches++;
                     for (int q = it->first; q < it->first + it->count; ++q) {
-                        const qcs_step_t &sp = tree->steps[c.L.small_order[q]];
-                        count_gemm(c, QCS_MODE_FP32, sp.m, sp.k, sp.n);
-                        count_gemm(c, QCS_MODE_FP32, sp.k, sp.n, sp.m);
-                        info->level_gemms += 2;
+                        const qcs_step_t &sp = tree->steps[L.small_order[q]];
+                        count_gemm(c, QCS_MODE_FP32, sp.m, sp.k, sp.n, Gc);
+                        count_gemm(c, QCS_MODE_FP32, sp.k, sp.n, sp.m, Gc);
+                        info->level_gemms += 2 * Gc;
                     }
                 }
                 ProfScope ps(h, kProfGemmSimt);
-                const auto *desc =
-                    reinterpret_cast<const TreeSmallBwd *>(c.ws + c.L.small_bwd) + it->first;
-                if (launch_tree_small_bwd(desc, it->count, inst,
-                                          reinterpret_cast<const int64_t *>(c.ws + c.L.offsets),
-                                          nl, reinterpret_cast<const int32_t *>(c.ws + c.L.small_tab),
+                const auto *desc = reinterpret_cast<const TreeSmallBwd *>(c.ws + L.small_bwd) + it->first;
+                if (launch_tree_small_bwd(desc, it->count, Gc, inst0, offs, nl,
+                                          reinterpret_cast<const int32_t *>(c.ws + L.small_tab),
                                           it->smem_bwd, s) != cudaSuccess)
                     return QCS_ERR_CUDA;
                 continue;
             }
-            const int st_i = it->step;
-            const qcs_step_t &st = tree->steps[st_i];
-            const float2 *gC = grad_ptr(c, st_i);
-            float2 *Am = reinterpret_cast<float2 *>(c.ws + c.L.bufA);
-            float2 *Bm = reinterpret_cast<float2 *>(c.ws + c.L.bufB);
-            float2 *gA = reinterpret_cast<float2 *>(c.ws + c.L.tmpA);
-            float2 *gB = reinterpret_cast<float2 *>(c.ws + c.L.tmpB);
-            if (int r = gather(c, st.map_a, tensor_ptr(c, st.a, inst), Am)) return r;
-            if (int r = gather(c, st.map_b, tensor_ptr(c, st.b, inst), Bm)) return r;
+            const qcs_step_t &st = tree->steps[it->step];
+            const float2 *gC = grad_ptr(c, it->step);
+            const int64_t mk = st.m * st.k, kn = st.k * st.n, mn = st.m * st.n;
+            if (int r = gather_op(st.a, st.map_a, inst0, Gc, mk, Am)) return r;
+            if (int r = gather_op(st.b, st.map_b, inst0, Gc, kn, Bm)) return r;
             // grad_A (m x k) = grad_out (m x n) B_mat^H ; grad_B (k x n) = A_mat^H grad_out
-            if (int r = gemm(c, st.mode, QCS_OP_N, QCS_OP_C, st.m, st.k, st.n, gC, st.m, Bm, st.k, gA))
+            if (int r = adj_gemm(st.mode, QCS_OP_N, QCS_OP_C, st.m, st.k, st.n, gC, st.m, mn, Bm,
+                                 st.k, kn, gA, mk, Gc))
                 return r;
-            if (int r = gemm(c, st.mode, QCS_OP_C, QCS_OP_N, st.k, st.n, st.m, Am, st.m, gC, st.m, gB))
+            if (int r = adj_gemm(st.mode, QCS_OP_C, QCS_OP_N, st.k, st.n, st.m, Am, st.m, mk, gC,
+                                 st.m, mn, gB, kn, Gc))
                 return r;
-            if (int r = scatter_into(st.a, inst, st.map_a, gA)) return r;
-            if (int r = scatter_into(st.b, inst, st.map_b, gB)) return r;
+            if (int r = scatter_op(st.a, st.map_a, inst0, Gc, gA, mk)) return r;
+            if (int r = scatter_op(st.b, st.map_b, inst0, Gc, gB, kn)) return r;
         }
+        // the group's leaf gradients into the caller's, in instance order
+        if (grp && launch_leaf_grad_reduce(reinterpret_cast<const LeafGradRef *>(c.ws + L.leaf_tab),
+                                           nl, L.max_leaf, lgrad, L.lgrad_stride, Gc, s) !=
+                       cudaSuccess)
+            return QCS_ERR_CUDA;
     }
     return QCS_SUCCESS;
 }

@@ -145,6 +145,9 @@ struct CopyBatch {
     const int64_t *off = nullptr;
     int64_t off_stride = 0;
     int64_t in_stride = 0, out_stride = 0;
+    // not NULL: copy g also writes out_off[g * out_off_stride] elements further
+    const int64_t *out_off = nullptr;
+    int64_t out_off_stride = 0;
     const qcs_gemm_desc_t *gate = nullptr;  // not NULL: copy only if that GEMM selected FP32
 };
 
@@ -236,7 +239,8 @@ cudaError_t launch_stats_finalize(const int64_t *partials, int g, int64_t n, qcs
 cudaError_t launch_accumulate_c128(const float2 *src, double *dst, int64_t count, int overwrite,
                                    cudaStream_t s);
 cudaError_t launch_scatter(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
-                           const float2 *src, float2 *dst, int accumulate, cudaStream_t s);
+                           const float2 *src, float2 *dst, int accumulate, cudaStream_t s,
+                           const CopyBatch &cb = CopyBatch{});
 cudaError_t launch_accumulate_gather_c128(const float2 *src, const int64_t *index, double *dst,
                                           int64_t count, cudaStream_t s);
 cudaError_t launch_seed_grad(const double *g, const int64_t *index, float2 *grad_root,
@@ -267,23 +271,37 @@ cudaError_t launch_tree_small(const TreeSmallStep *steps, int n_steps, int G, in
                               const int64_t *off, int nl, const int32_t *tab, int smem_elems,
                               cudaStream_t s);
 
-// The adjoint of one small step for one instance: from the output gradient
-// gc (m x n, dense) grad_A = gc op(B)^H and grad_B = op(A)^H gc, written
-// through the operands' offset tables into their gradients: ga[tab[a_tab + e]]
-// (added for a leaf, at its instance offset; stored for an intermediate,
-// whose map covers it once), likewise gb.
+// The adjoint of one small step: from the output gradient gc (m x n, dense)
+// grad_A = gc op(B)^H and grad_B = op(A)^H gc, written through the operands'
+// offset tables into their gradients: ga[tab[a_tab + e]] (added for a leaf,
+// at its instance offset; stored for an intermediate, whose map covers it
+// once), likewise gb.  Instance r of the launch (position r of its group,
+// instance inst0 + r) reads an intermediate operand r a_istride further,
+// writes its gradients r ga_istride further (for a leaf too: its own
+// gradient buffer of the group), and takes gc r gc_istride further.
 struct TreeSmallBwd {
     const float2 *a, *b, *gc;
     float2 *ga, *gb;
+    int64_t a_istride, b_istride, ga_istride, gb_istride, gc_istride;
     int32_t a_leaf, b_leaf;  // leaf index, or -1 for an intermediate
     int32_t m, n, k;
     int32_t a_tab, b_tab;
     int32_t pad;
 };
 constexpr int64_t kTreeSmallBwdElems = 2048;  // max m n + m k + k n of a step's adjoint
-cudaError_t launch_tree_small_bwd(const TreeSmallBwd *steps, int n_steps, int inst,
+cudaError_t launch_tree_small_bwd(const TreeSmallBwd *steps, int n_steps, int G, int inst0,
                                   const int64_t *off, int nl, const int32_t *tab, int smem_elems,
                                   cudaStream_t s);
+
+// grad[i][e] += scratch[g stride + leaf_off[i] + e] for g = 0 .. G-1 in
+// order, for every leaf i (the leaf gradients of a group of instances of
+// the adjoint, each instance's in its own buffer, added in instance order).
+struct LeafGradRef {
+    float2 *grad;
+    int64_t size, scratch_off;
+};
+cudaError_t launch_leaf_grad_reduce(const LeafGradRef *leaves, int nl, int64_t max_size,
+                                    const float2 *scratch, int64_t stride, int G, cudaStream_t s);
 
 // ---- shared with the executor (capi.cu) ------------------------------------
 int effective_mode(qcs_handle_t h, int mode, int opA, int opB, int64_t m, int64_t n, int64_t k);

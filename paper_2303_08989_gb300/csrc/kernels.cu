@@ -1115,6 +1115,8 @@ struct CopyParams {
     // elements in (or g * bin when boff is NULL), its output g * bout.
     const int64_t *boff;
     int64_t boff_stride, bin, bout;
+    const int64_t *oboff;  // not NULL: copy g writes oboff[g * oboff_stride] further too
+    int64_t oboff_stride;
     const qcs_gemm_desc_t *gate;  // not NULL: copy only if the GEMM selected plain FP32
 };
 
@@ -1142,6 +1144,11 @@ __device__ __forceinline__ SplitOut batch_split_out(const SplitOut &so) {
 __device__ __forceinline__ int64_t batch_in(const CopyParams &P) {
     const int64_t g = blockIdx.y;
     return P.boff ? P.boff[g * P.boff_stride] : g * P.bin;
+}
+
+__device__ __forceinline__ int64_t batch_out(const CopyParams &P) {
+    const int64_t g = blockIdx.y;
+    return g * P.bout + (P.oboff ? P.oboff[g * P.oboff_stride] : 0);
 }
 
 __device__ __forceinline__ void decompose(const CopyParams &P, const int8_t *g, int ng, int64_t v,
@@ -1195,7 +1202,7 @@ __global__ void __launch_bounds__(256, SPLIT ? 4 : 5) copy_tiled_kernel(CopyPara
     __shared__ float2 tile[2][32][33];
     __shared__ int64_t sxi[32], sxo[32], syi[32], syo[32], sr[kTilesPerBlock][2];
     in += batch_in(P);
-    out += blockIdx.y * P.bout;
+    out += batch_out(P);
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     int64_t b = blockIdx.x;
     const int64_t bx = b % P.tiles_x;
@@ -1475,7 +1482,7 @@ __global__ void __launch_bounds__(256) copy_vector_kernel(CopyParams P, int nv, 
     if (P.gate && P.gate->mode != QCS_MODE_FP32) return;
     __shared__ int64_t so[2];
     in += batch_in(P);
-    out += blockIdx.y * P.bout;
+    out += batch_out(P);
     for (int64_t q = blockIdx.x; q < outer; q += gridDim.x) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1510,7 +1517,7 @@ __global__ void copy_simple_kernel(CopyParams P, int64_t total, const float2 *__
                                    float2 *__restrict__ out, int accumulate) {
     if (P.gate && P.gate->mode != QCS_MODE_FP32) return;
     in += batch_in(P);
-    out += blockIdx.y * P.bout;
+    out += batch_out(P);
     for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
          o += (int64_t)gridDim.x * blockDim.x) {
         int64_t rem = o, io = 0, oo = 0;
@@ -1618,6 +1625,8 @@ cudaError_t launch_copy(int rank, const int64_t *dims, const int64_t *is, const 
     P.boff_stride = cb.off_stride;
     P.bin = cb.in_stride;
     P.bout = cb.out_stride;
+    P.oboff = cb.out_off;
+    P.oboff_stride = cb.out_off_stride;
     P.gate = cb.gate;
     const unsigned G = (unsigned)cb.count;
     int64_t total = 1;
@@ -1800,14 +1809,15 @@ cudaError_t launch_permute(int rank, const int64_t *dims, const int64_t *strides
 }
 
 cudaError_t launch_scatter(int rank, const int64_t *dims, const int64_t *strides, int64_t offset,
-                           const float2 *src, float2 *dst, int accumulate, cudaStream_t s) {
+                           const float2 *src, float2 *dst, int accumulate, cudaStream_t s,
+                           const CopyBatch &cb) {
     int64_t dense[QCS_MAX_RANK];
     int64_t acc = 1;
     for (int d = 0; d < rank; ++d) {
         dense[d] = acc;
         acc *= dims[d];
     }
-    return launch_copy(rank, dims, dense, strides, src, dst + offset, accumulate, s);
+    return launch_copy(rank, dims, dense, strides, src, dst + offset, accumulate, s, cb);
 }
 
 cudaError_t launch_accumulate_gather_c128(const float2 *src, const int64_t *index, double *dst,
@@ -1893,21 +1903,27 @@ __global__ void __launch_bounds__(32 * kTreeSmallWarps) tree_small_kernel(
 // conjugated operand (the conjugation applied on load), and the writes
 // through the offset tables.
 __global__ void __launch_bounds__(32 * kTreeSmallWarps) tree_small_bwd_kernel(
-    const TreeSmallBwd *__restrict__ steps, int n_steps, int inst,
+    const TreeSmallBwd *__restrict__ steps, int n_steps, int G, int inst0,
     const int64_t *__restrict__ off, int nl, const int32_t *__restrict__ tab, int smem_elems) {
     extern __shared__ float2 tree_small_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = blockIdx.x * kTreeSmallWarps + warp;
-    if (p >= n_steps) return;  // the whole warp; no block barrier follows
-    const TreeSmallBwd &st = steps[p];
+    const int64_t p = (int64_t)blockIdx.x * kTreeSmallWarps + warp;
+    if (p >= (int64_t)n_steps * G) return;  // the whole warp; no block barrier follows
+    const int r = (int)(p % G);
+    const TreeSmallBwd &st = steps[p / G];
     const int m = st.m, n = st.n, k = st.k;
-    const int64_t oa = st.a_leaf >= 0 ? off[(int64_t)inst * nl + st.a_leaf] : 0;
-    const int64_t ob = st.b_leaf >= 0 ? off[(int64_t)inst * nl + st.b_leaf] : 0;
+    const int64_t inst = (int64_t)inst0 + r;
+    // element offsets of this instance's operands and their gradients
+    const int64_t oa = st.a_leaf >= 0 ? off[inst * nl + st.a_leaf] : r * st.a_istride;
+    const int64_t ob = st.b_leaf >= 0 ? off[inst * nl + st.b_leaf] : r * st.b_istride;
+    const int64_t oga = (st.a_leaf >= 0 ? off[inst * nl + st.a_leaf] : 0) + r * st.ga_istride;
+    const int64_t ogb = (st.b_leaf >= 0 ? off[inst * nl + st.b_leaf] : 0) + r * st.gb_istride;
+    const float2 *gc = st.gc + r * st.gc_istride;
     float2 *Gs = tree_small_smem + (size_t)warp * smem_elems;
     float2 *As = Gs + m * n;
     float2 *Bs = As + m * k;
     const int32_t *ta = tab + st.a_tab, *tb = tab + st.b_tab;
-    for (int e = lane; e < m * n; e += 32) Gs[e] = st.gc[e];
+    for (int e = lane; e < m * n; e += 32) Gs[e] = gc[e];
     for (int e = lane; e < m * k; e += 32) As[e] = st.a[oa + ta[e]];
     for (int e = lane; e < k * n; e += 32) Bs[e] = st.b[ob + tb[e]];
     __syncwarp();
@@ -1924,7 +1940,7 @@ __global__ void __launch_bounds__(32 * kTreeSmallWarps) tree_small_bwd_kernel(
             si = fmaf(a.x, b.y, si);
             si = fmaf(a.y, b.x, si);
         }
-        float2 *dst = st.ga + oa + ta[e];
+        float2 *dst = st.ga + oga + ta[e];
         if (st.a_leaf >= 0) {
             const float2 u = *dst;
             sr += u.x;
@@ -1945,7 +1961,7 @@ __global__ void __launch_bounds__(32 * kTreeSmallWarps) tree_small_bwd_kernel(
             si = fmaf(a.x, b.y, si);
             si = fmaf(a.y, b.x, si);
         }
-        float2 *dst = st.gb + ob + tb[e];
+        float2 *dst = st.gb + ogb + tb[e];
         if (st.b_leaf >= 0) {
             const float2 u = *dst;
             sr += u.x;
@@ -1979,10 +1995,10 @@ cudaError_t launch_tree_small(const TreeSmallStep *steps, int n_steps, int G, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_tree_small_bwd(const TreeSmallBwd *steps, int n_steps, int inst,
+cudaError_t launch_tree_small_bwd(const TreeSmallBwd *steps, int n_steps, int G, int inst0,
                                   const int64_t *off, int nl, const int32_t *tab, int smem_elems,
                                   cudaStream_t s) {
-    if (n_steps <= 0) return cudaSuccess;
+    if (n_steps <= 0 || G <= 0) return cudaSuccess;
     if (smem_elems < 1 || smem_elems > kTreeSmallBwdElems) return cudaErrorInvalidValue;
     static bool configured = false;  // the attribute is per function, set once
     if (!configured) {
@@ -1992,10 +2008,40 @@ cudaError_t launch_tree_small_bwd(const TreeSmallBwd *steps, int n_steps, int in
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int blocks = (n_steps + kTreeSmallWarps - 1) / kTreeSmallWarps;
+    const int64_t blocks = ((int64_t)n_steps * G + kTreeSmallWarps - 1) / kTreeSmallWarps;
+    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
     const size_t smem = sizeof(float2) * (size_t)smem_elems * kTreeSmallWarps;
     tree_small_bwd_kernel<<<(unsigned)blocks, 32 * kTreeSmallWarps, smem, s>>>(
-        steps, n_steps, inst, off, nl, tab, smem_elems);
+        steps, n_steps, G, inst0, off, nl, tab, smem_elems);
+    return cudaGetLastError();
+}
+
+namespace {
+
+__global__ void leaf_grad_reduce_kernel(const LeafGradRef *__restrict__ leaves,
+                                        const float2 *__restrict__ scratch, int64_t stride, int G) {
+    const LeafGradRef &L = leaves[blockIdx.y];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L.size;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float2 acc = L.grad[e];
+        for (int g = 0; g < G; ++g) {
+            const float2 v = scratch[g * stride + L.scratch_off + e];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        L.grad[e] = acc;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_leaf_grad_reduce(const LeafGradRef *leaves, int nl, int64_t max_size,
+                                    const float2 *scratch, int64_t stride, int G, cudaStream_t s) {
+    if (nl <= 0 || max_size <= 0) return cudaSuccess;
+    if (nl > 65535) return cudaErrorInvalidValue;
+    const int64_t bx = std::min<int64_t>((max_size + 255) / 256, 1024);
+    leaf_grad_reduce_kernel<<<dim3((unsigned)bx, (unsigned)nl), 256, 0, s>>>(leaves, scratch,
+                                                                           stride, G);
     return cudaGetLastError();
 }
 

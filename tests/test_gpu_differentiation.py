@@ -79,9 +79,11 @@ def test_gradient_at_the_differentiation_workload(workload):
 
 
 def test_graphed_forward_and_backward_equal_eager(workload):
-    """The same forward + backward replayed as two CUDA graphs (the forward
-    grouped over the 4 slices): loss and gradient bit-identical to the eager
-    calls, on two replays in a row."""
+    """The same forward + backward replayed as two CUDA graphs (both grouped
+    over the 4 slices: the adjoint's steps for all slices at once, each
+    slice's leaf gradients in its own buffer, added in slice order): loss and
+    gradient bit-identical to the eager one-slice-at-a-time calls, on two
+    replays in a row."""
     import time
 
     tn, q, circ, bits, plan, p0, L_ref, g_ref = workload
