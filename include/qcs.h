@@ -380,9 +380,13 @@ typedef struct {
  * own selected mode; for AUTO the FP32 candidate of each instance is
  * launched gated).  Their outputs hold G instances each (intermediates share
  * memory by liveness).  The later steps loop over the group.  Results do
- * not depend on G.  The backward
- * runs one instance at a time (its launches can be captured in a graph:
- * qcs_tree_backward_graph_create). */
+ * not depend on G.  The backward runs in groups of G as well when every
+ * step can hold the group (else one instance at a time): the recomputed
+ * forward, then per step the gathers, the two adjoint GEMMs and the
+ * scatters of all G instances, each instance's leaf gradients in a buffer
+ * of its own that is added into d_grad_leaves in instance order -- the same
+ * sums in the same order as one instance at a time.  Its launches can be
+ * captured in a graph (qcs_tree_backward_graph_create). */
 int qcs_set_instance_batch(qcs_handle_t h, int instances);
 
 /* Memory a grouped step of the tree executor may hold (bytes; default
