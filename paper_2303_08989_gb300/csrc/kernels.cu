@@ -2730,6 +2730,18 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
         }
         return cudaGetLastError();
     }
+    // 16 < k <= 32 with m too small for the 128-row SIMT tile (half of it or
+    // more would stay empty): the small-k kernel below with 32 registers of k
+    if (k > 16 && k <= 32 && m <= 64 && mn > 4096) {
+        const int rows = m <= 32 ? 32 : 64;
+        const int64_t gy = (n + kSmallKCols - 1) / kSmallKCols;
+        if (gy <= 65535) {
+            dim3 grid(1u, (unsigned)gy, G);
+            cgemm_smallk_kernel<32><<<grid, 256, 0, s>>>(desc, opA, opB, m, n, (int)k, rows, alpha,
+                                                         A, lda, B, ldb, beta, C, ldc, bt);
+            return cudaGetLastError();
+        }
+    }
     if (k <= 16 && mn > 4096 && m <= INT32_MAX) {
         // rows per block: all of m up to 256, at least a warp
         const int rows = m >= 256 ? 256 : (m <= 32 ? 32 : (m <= 64 ? 64 : (m <= 128 ? 128 : 256)));

@@ -271,7 +271,10 @@ def test_cgemm_fp32_split_k_small_outputs(h, m, n, k, opA, opB):
 @pytest.mark.parametrize("m,n,k,opA,opB", [(2, 5000, 2, 0, 0), (5000, 2, 2, 0, 0), (3, 1000, 16, 1, 2),
                                            (1000, 16, 7, 2, 1), (16, 16, 16, 0, 1), (2048, 300, 8, 0, 0),
                                            (50, 60, 40, 1, 0), (300, 5000, 3, 1, 2), (40, 2000, 16, 2, 1),
-                                           (100, 130, 12, 0, 1), (517, 4099, 5, 0, 0), (17, 700, 9, 1, 0)])
+                                           (100, 130, 12, 0, 1), (517, 4099, 5, 0, 0), (17, 700, 9, 1, 0),
+                                           # 16 < k <= 32 with m <= 64: the small-k kernel's 32-register form
+                                           (64, 4096, 32, 0, 0), (40, 5003, 17, 1, 2), (33, 2000, 24, 2, 1),
+                                           (20, 9000, 31, 0, 1)])
 def test_cgemm_fp32_skinny_and_per_element_shapes(h, m, n, k, opA, opB):
     """The bandwidth-bound FP32 kernels of Section 5.1.2's irregular shapes."""
     A, B = _operands(m, n, k, opA, opB, 3, seed=(m, n, k, 9), ldpad=2)
