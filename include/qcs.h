@@ -389,6 +389,32 @@ typedef struct {
  * captured in a graph (qcs_tree_backward_graph_create). */
 int qcs_set_instance_batch(qcs_handle_t h, int instances);
 
+/* The tree executor's plan for a call, computed on the host only (no device
+ * is touched; for inspection and tests): with ``instance_batch`` instances
+ * per group, level launches on or off, ``num_sms`` SMs, the given group
+ * budget, the paper's size rule and no tuning table.  Per step (host arrays
+ * of n_steps, each optional): the byte offset of its output in the tree
+ * workspace (step_offset) and its size (step_bytes, all instances of a
+ * group), the time it runs at (step_time: steps of equal time may run at
+ * once, so their outputs must not overlap; an output is live from its
+ * step's time to its last reader's), whether it runs inside a level
+ * launch (step_small), and the order the steps are issued in (step_order,
+ * a permutation; a level launch's steps consecutive).  *out gets the
+ * workspace size, the group size used, the steps that run once per group
+ * and the level launches per group.  QCS_ERR_INVALID_ARG as
+ * qcs_contract_tree for a bad plan. */
+typedef struct {
+    int64_t total_bytes;
+    int32_t group;
+    int32_t batched_steps;
+    int32_t level_launches;
+    int32_t reserved;
+} qcs_tree_layout_t;
+int qcs_tree_layout_info(const qcs_tree_t *tree, int backward, int instance_batch, int levels,
+                         int num_sms, uint64_t group_budget, int64_t *step_offset,
+                         int64_t *step_bytes, int32_t *step_time, int32_t *step_small,
+                         int32_t *step_order, qcs_tree_layout_t *out);
+
 /* Memory a grouped step of the tree executor may hold (bytes; default
  * 32 GiB; environment override QCS_GROUP_BUDGET_MB): an emulated step that
  * fills the GPU alone still runs once for its group of G instances -- full

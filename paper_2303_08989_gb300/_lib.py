@@ -37,6 +37,7 @@ EXPORTED = [
     "qcs_set_tc_splits", "qcs_sgemm", "qcs_set_complex_products", "qcs_set_wait_budget",
     "qcs_debug_stall_producer", "qcs_cgemm_noalloc_status", "qcs_measure_fma_peak",
     "qcs_set_fused_split", "qcs_set_tree_levels", "qcs_set_group_budget", "qcs_fidelity_stats",
+    "qcs_tree_layout_info",
     "qcs_selection_stats", "qcs_tree_backward_graph_create",
 ]
 SIZE_RULE_OFF, SIZE_RULE_PAPER, SIZE_RULE_TUNED = 0, 1, 2
@@ -109,6 +110,12 @@ class qcs_run_info_t(ctypes.Structure):
                 ("level_gemms", ctypes.c_int64)]
 
 
+class qcs_tree_layout_t(ctypes.Structure):
+    _fields_ = [("total_bytes", ctypes.c_int64), ("group", ctypes.c_int32),
+                ("batched_steps", ctypes.c_int32), ("level_launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -173,6 +180,8 @@ def load(path: str = LIB_PATH):
         "qcs_set_tree_levels": [H, I],
         "qcs_set_group_budget": [H, ctypes.c_uint64],
         "qcs_fidelity_stats": [H, P, I, P, I64, P],
+        "qcs_tree_layout_info": [ctypes.POINTER(qcs_tree_t), I, I, I, I, ctypes.c_uint64, P, P,
+                                 P, P, P, ctypes.POINTER(qcs_tree_layout_t)],
         "qcs_selection_stats": [H, I, I, I64, I64, I64, P, I64, P, I64,
                                 ctypes.POINTER(qcs_selection_stats_t), ctypes.POINTER(qcs_gemm_desc_t)],
     }

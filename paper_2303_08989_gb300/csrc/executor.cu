@@ -53,6 +53,7 @@ struct Layout {
     std::vector<char> small;        // step runs inside its level's launch
     std::vector<Item> seq_b, seq_i; // order of the steps before P (once per group), from P on
     std::vector<int> small_order;   // the small steps, grouped by launch
+    std::vector<int> time;          // when each step runs (equal times may overlap)
     std::vector<int32_t> tab;       // element-offset tables of the small steps' operands
     std::vector<int32_t> tab_a, tab_b;  // start of each small step's tables in ``tab``
     size_t out_index = 0, offsets = 0, bufA = 0, bufB = 0, tmpA = 0, tmpB = 0, gemm = 0, total = 0;
@@ -357,7 +358,8 @@ Layout plan_layout(qcs_handle_t h, const qcs_tree_t *t, bool backward, int G) {
             L.tab.resize(at);
         }
     }
-    std::vector<int> time(ns, 0);
+    L.time.assign(ns, 0);
+    std::vector<int> &time = L.time;
     const int tb = schedule(t, L, 0, L.P, 0, h->tree_levels != 0, L.seq_b, time);
     schedule(t, L, L.P, ns, tb, h->tree_levels != 0, L.seq_i, time);
     for (int s = 0; s < ns; ++s) {
@@ -1190,6 +1192,54 @@ int qcs_tree_backward_graph_create(qcs_handle_t h, const qcs_tree_t *tree,
         return r;
     }
     *out = g;
+    return QCS_SUCCESS;
+}
+
+int qcs_tree_layout_info(const qcs_tree_t *tree, int backward, int instance_batch, int levels,
+                         int num_sms, uint64_t group_budget, int64_t *step_offset,
+                         int64_t *step_bytes, int32_t *step_time, int32_t *step_small,
+                         int32_t *step_order, qcs_tree_layout_t *out) {
+    if (!tree || !out || instance_batch < 1 || num_sms < 1 || (levels != 0 && levels != 1))
+        return QCS_ERR_INVALID_ARG;
+    std::vector<int64_t> size_of;
+    if (int r = validate(tree, size_of, backward != 0)) return r;
+    // a handle that never touches a device: the paper's size rule, no tuning
+    qcs_handle_s h;
+    h.num_sms = num_sms;
+    h.tree_levels = levels;
+    h.group_budget = (size_t)group_budget;
+    const int ns = tree->n_steps;
+    const int G = std::max(1, std::min(instance_batch, tree->n_instances));
+    Layout L = plan_layout(&h, tree, backward != 0, G);
+    if (backward && G > 1 && (ns == 0 || L.P < ns)) L = plan_layout(&h, tree, true, 1);
+    for (int s = 0; s < ns; ++s) {
+        if (step_offset) step_offset[s] = (int64_t)L.inter_off[s];
+        if (step_bytes)
+            step_bytes[s] = (int64_t)(sizeof(float2) * tree->steps[s].m * tree->steps[s].n *
+                                      (L.batched[s] ? L.G : 1));
+        if (step_time) step_time[s] = L.time[s];
+        if (step_small) step_small[s] = L.small[s];
+    }
+    if (step_order) {
+        int q = 0;
+        for (const std::vector<Item> *seq : {&L.seq_b, &L.seq_i})
+            for (const Item &it : *seq) {
+                if (it.step >= 0) {
+                    step_order[q++] = it.step;
+                } else {
+                    for (int i = it.first; i < it.first + it.count; ++i)
+                        step_order[q++] = L.small_order[i];
+                }
+            }
+    }
+    *out = qcs_tree_layout_t{};
+    out->total_bytes = (int64_t)L.total;
+    out->group = L.G;
+    out->batched_steps = L.P;
+    int launches = 0;
+    for (const std::vector<Item> *seq : {&L.seq_b, &L.seq_i})
+        for (const Item &it : *seq) launches += it.step < 0 ? 1 : 0;
+    out->level_launches = launches;
     return QCS_SUCCESS;
 }
 
