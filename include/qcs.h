@@ -138,6 +138,17 @@ int qcs_set_drain_stages(qcs_handle_t h, int stages);
  * QCS_TC_L2_PROMOTION. */
 int qcs_set_tc_schedule(qcs_handle_t h, int group_m, int l2_promotion);
 
+/* Clusters of the complex tensor-core kernel (a schedule; results do not
+ * depend on it).  While ``enabled`` is 1 the kernel runs as clusters of two
+ * CTAs on pairs of tile rows of the same tile column, in lockstep: each
+ * loads part of the shared op(B) box of a stage and multicasts it to both
+ * (TMA multicast within the cluster), so each CTA reads half as much of B
+ * from L2; a stage is released when the MMAs of both CTAs have read it.
+ * Used when the output has an even number of 128-row tile rows.  Default 0;
+ * environment override QCS_TC_MULTICAST.  QCS_ERR_INVALID_ARG for other
+ * values. */
+int qcs_set_tc_multicast(qcs_handle_t h, int enabled);
+
 /* K ranges of the tensor-core kernels.  A GEMM with few 128 x 128 output
  * tiles for its K (for example m = n = 1024: 64 tiles on 152 SMs) leaves
  * SMs idle; its K loop can be cut into ``splits`` equal ranges that run as

@@ -180,6 +180,12 @@ class Handle:
         (qcs_set_group_budget; default 32 GiB, 0 = such steps per instance)."""
         _lib.check(self.lib.qcs_set_group_budget(self._h, int(nbytes)), "qcs_set_group_budget")
 
+    def set_tc_multicast(self, enabled: bool):
+        """Run the complex tensor-core kernel in clusters of two CTAs that share
+        each op(B) box by TMA multicast (qcs_set_tc_multicast; off by default)."""
+        _lib.check(self.lib.qcs_set_tc_multicast(self._h, int(bool(enabled))),
+                   "qcs_set_tc_multicast")
+
     def set_tree_levels(self, enabled: bool):
         """Run a contraction tree level by level, the small plain-FP32 steps
         of each level as one launch (qcs_set_tree_levels; on by default)."""

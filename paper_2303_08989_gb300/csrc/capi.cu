@@ -103,12 +103,13 @@ namespace {
 // planes (kRowBytes of K x 128 rows), 64-byte swizzle (the layout the
 // kernel's shared-memory descriptors describe).
 int encode_planes(qcs_handle_t h, CUtensorMap *map, void *base, int64_t R_pad, int64_t K_pad,
-                  int esz, int nplanes, int box_rows = kBM) {
+                  int esz, int nplanes, int box_rows = kBM, int box_planes = 0) {
     const CUtensorMapDataType dt =
         esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     cuuint64_t gdim[3] = {(cuuint64_t)K_pad, (cuuint64_t)R_pad, (cuuint64_t)nplanes};
     cuuint64_t gstride[2] = {(cuuint64_t)(K_pad * esz), (cuuint64_t)(K_pad * R_pad * esz)};
-    cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)box_rows, (cuuint32_t)nplanes};
+    cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)box_rows,
+                         (cuuint32_t)(box_planes > 0 ? box_planes : nplanes)};
     cuuint32_t estride[3] = {1, 1, 1};
     const CUtensorMapL2promotion promo =
         h->tc_l2_promotion >= 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
@@ -445,13 +446,17 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
             // One launch per kind over the tiles of all G instances.
             ProfScope ps_tc(h, kProfGemmTc);
             if (need16) {
-                CUtensorMap ma, mb;
+                CUtensorMap ma, mb, mc[2];
                 if (encode_planes(h, &ma, planesA, G * mp, kp, 2, kPlanes) ||
-                    encode_planes(h, &mb, planesB, G * np, kp, 2, kPlanesB))
+                    encode_planes(h, &mb, planesB, G * np, kp, 2, kPlanesB) ||
+                    (h->tc_multicast &&
+                     (encode_planes(h, &mc[0], planesB, G * np, kp, 2, kPlanesB, kBM, 3) ||
+                      encode_planes(h, &mc[1], planesB, G * np, kp, 2, kPlanesB, kBM, 2))))
                     return QCS_ERR_CUDA;
                 const int kind = (eff == QCS_MODE_BF16X3) ? 2 : 0;
                 e = launch_cgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
-                                    ldc, h->d_err, h->num_sms, gm, s, w);
+                                    ldc, h->d_err, h->num_sms, gm, s, w,
+                                    h->tc_multicast ? mc : nullptr);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             }
             if (need32 && tf32_fused) {
@@ -460,12 +465,16 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                                           gm, w, s);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             } else if (need32) {
-                CUtensorMap ma, mb;
+                CUtensorMap ma, mb, mc[2];
                 if (encode_planes(h, &ma, planesA32, G * mp, kp, 4, kPlanes) ||
-                    encode_planes(h, &mb, planesB32, G * np, kp, 4, kPlanesB))
+                    encode_planes(h, &mb, planesB32, G * np, kp, 4, kPlanesB) ||
+                    (h->tc_multicast &&
+                     (encode_planes(h, &mc[0], planesB32, G * np, kp, 4, kPlanesB, kBM, 3) ||
+                      encode_planes(h, &mc[1], planesB32, G * np, kp, 4, kPlanesB, kBM, 2))))
                     return QCS_ERR_CUDA;
                 e = launch_cgemm_tc(1, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
-                                    ldc, h->d_err, h->num_sms, gm, s, w);
+                                    ldc, h->d_err, h->num_sms, gm, s, w,
+                                    h->tc_multicast ? mc : nullptr);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             }
             e = launch_tc_reduce(desc, m, n, alpha, beta, C, ldc, h->num_sms, w, s);
@@ -828,6 +837,7 @@ int qcs_create(qcs_handle_t *out, void *cuda_stream) {
         h->complex_products = (std::atoi(c) == 3) ? 3 : 4;
     if (const char *f = std::getenv("QCS_FUSED_SPLIT")) h->fused_split = std::atoi(f) != 0;
     if (const char *l = std::getenv("QCS_TREE_LEVELS")) h->tree_levels = std::atoi(l) != 0;
+    if (const char *c = std::getenv("QCS_TC_MULTICAST")) h->tc_multicast = std::atoi(c) != 0;
     if (const char *b = std::getenv("QCS_GROUP_BUDGET_MB"))
         h->group_budget = (size_t)std::max(0LL, std::atoll(b)) << 20;
     if (const char *k = std::getenv("QCS_TC_SPLITS"))
@@ -964,6 +974,12 @@ int qcs_fidelity_stats(qcs_handle_t h, const void *a, int a_c64, const double *r
                                  d_out, h->stream) == cudaSuccess
                ? QCS_SUCCESS
                : QCS_ERR_CUDA;
+}
+
+int qcs_set_tc_multicast(qcs_handle_t h, int enabled) {
+    if (!h || (enabled != 0 && enabled != 1)) return QCS_ERR_INVALID_ARG;
+    h->tc_multicast = enabled;
+    return QCS_SUCCESS;
 }
 
 int qcs_set_tree_levels(qcs_handle_t h, int enabled) {

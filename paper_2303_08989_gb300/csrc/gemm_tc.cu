@@ -68,6 +68,13 @@
 // two of lo*hi and hi*lo into acc1, the same tensor-memory layout (the
 // "re" and "im" halves of an accumulator are output columns 0-127 and
 // 128-255 of the tile) and the same drain.  A stage is 48 KB, so four fit.
+//
+// Clusters (MC = true, complex kernel, qcs_set_tc_multicast): two CTAs along
+// M work on tile rows 2p and 2p + 1 of the same tile column in lockstep and
+// share its B box: rank 0 loads planes 0-2 of it, rank 1 planes 3-4, each
+// with one TMA multicast into the shared memory of both.  A stage is freed
+// once the MMAs of both CTAs have read it (each commit arrives on both CTAs'
+// "empty" barriers), so the B traffic from L2 per CTA halves.
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -149,14 +156,17 @@ __device__ __forceinline__ Unit unit_of(int u, int tiles, int S) {
     return x;
 }
 
-template <int KIND, int DRAIN, bool REAL>
+template <int KIND, int DRAIN, bool REAL, bool MC>
 __global__ void __launch_bounds__(kTcThreads, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                     const __grid_constant__ CUtensorMap mapB,
+                    const __grid_constant__ CUtensorMap mapB2,
                     const qcs_gemm_desc_t *__restrict__ desc, int m, int n, int k_pad,
                     float2 alpha, float2 beta, float2 *__restrict__ C, int64_t ldc, int *d_err,
                     int group_m, const TcWork w) {
+    static_assert(!(MC && REAL), "clusters are built for the complex kernel");
     // a single GEMM that did not select this kind exits before touching anything
+    // (both CTAs of a cluster read the same descriptor)
     if (w.G == 1 && !kind_runs(KIND, desc->mode)) return;
 
     using Geo = TcGeom<REAL>;
@@ -172,7 +182,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&S.full[s], 1);
-            mbar_init(&S.empty[s], 1);
+            mbar_init(&S.empty[s], MC ? 2 : 1);  // MC: the MMAs of both CTAs of the cluster
         }
         mbar_init(&S.acc0_full, 1);
         mbar_init(&S.acc0_empty, kEpiWarps);
@@ -181,6 +191,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         fence_barrier_init();
         tma_prefetch_desc(&mapA);
         tma_prefetch_desc(&mapB);
+        if (MC) tma_prefetch_desc(&mapB2);
     }
     if (warp == 1) {
         tmem_alloc(&S.tmem_base, kTmemCols);
@@ -190,11 +201,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem_base;
+    // MC: the peer's barriers are initialised before anything reaches them
+    if constexpr (MC) cluster_sync();
 
     const int tiles_m = (m + kBM - 1) / kBM;
     const int tiles_n = (n + Geo::tile_n - 1) / Geo::tile_n;
-    const int num_tiles = tiles_m * tiles_n;
+    // MC: units over pairs of tile rows (the host makes tiles_m even), one
+    // per cluster at a time; a cluster's rank-r CTA takes row 2 p + r
+    const int num_tiles = (MC ? tiles_m / 2 : tiles_m) * tiles_n;
     const int num_units = w.G * w.S * num_tiles;
+    auto first_unit = [] { return MC ? (int)(blockIdx.x >> 1) : (int)blockIdx.x; };
+    auto unit_step = [] { return MC ? (int)(gridDim.x >> 1) : (int)gridDim.x; };
+    auto coords = [&](int t, int &tm, int &tn) {
+        if constexpr (MC) {
+            tile_coords(t, tiles_m / 2, tiles_n, group_m / 2 > 0 ? group_m / 2 : 1, tm, tn);
+            tm = 2 * tm + (int)cluster_ctarank();
+        } else {
+            tile_coords(t, tiles_m, tiles_n, group_m, tm, tn);
+        }
+    };
     constexpr int kElemBytes = (KIND == 1) ? 4 : 2;
     constexpr int kKPerStage = kRowBytes / kElemBytes;  // two MMA K steps: 32 (16-bit) or 16 (TF32)
     const int num_kb = k_pad / kKPerStage;
@@ -208,11 +233,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             uint32_t phase = 0;
             int issued = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < num_units && ok && !w.stall; u += gridDim.x) {
+            for (int u = first_unit(); u < num_units && ok && !w.stall; u += unit_step()) {
                 const Unit x = unit_of(u, num_tiles, w.S);
                 if (w.G > 1 && !kind_runs(KIND, desc[x.g].mode)) continue;
                 int tm, tn;
-                tile_coords(x.t, tiles_m, tiles_n, group_m, tm, tn);
+                coords(x.t, tm, tn);
                 const int rowA = static_cast<int>(x.g * w.a_rows) + tm * kBM;
                 const int rowB = static_cast<int>(x.g * w.b_rows) + tn * Geo::tile_n;
                 const int kb1 = kb_begin(x.r + 1);
@@ -225,8 +250,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     mbar_arrive_expect_tx(&S.full[stage], Geo::stage_bytes);
                     tma_load_3d(S.stage[stage], &mapA, &S.full[stage], kb * kKPerStage, rowA, 0);
-                    tma_load_3d(S.stage[stage] + Geo::a_bytes, &mapB, &S.full[stage],
-                                kb * kKPerStage, rowB, 0);
+                    if constexpr (MC) {
+                        // this CTA's share of the B box, to both CTAs of the cluster
+                        if (cluster_ctarank() == 0)
+                            tma_load_3d_mc(S.stage[stage] + Geo::a_bytes, &mapB, &S.full[stage],
+                                           kb * kKPerStage, rowB, 0, (uint16_t)0x3);
+                        else
+                            tma_load_3d_mc(S.stage[stage] + Geo::a_bytes + 3 * kTileBytes, &mapB2,
+                                           &S.full[stage], kb * kKPerStage, rowB, 3, (uint16_t)0x3);
+                    } else {
+                        tma_load_3d(S.stage[stage] + Geo::a_bytes, &mapB, &S.full[stage],
+                                    kb * kKPerStage, rowB, 0);
+                    }
                     ++issued;
                     if (++stage == NST) {
                         stage = 0;
@@ -270,7 +305,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc_fence_after();
                 return true;
             };
-            for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+            for (int u = first_unit(); u < num_units && ok; u += unit_step()) {
                 const Unit x = unit_of(u, num_tiles, w.S);
                 if (w.G > 1 && !kind_runs(KIND, desc[x.g].mode)) continue;
                 const int kb0 = kb_begin(x.r), kb1 = kb_begin(x.r + 1);
@@ -335,7 +370,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
 #undef A_
 #undef B_
-                    tc_commit(&S.empty[stage]);  // frees the smem stage when these MMAs finish
+                    // frees the smem stage when these MMAs finish (MC: in both CTAs)
+                    if constexpr (MC)
+                        tc_commit_mc(&S.empty[stage], (uint16_t)0x3);
+                    else
+                        tc_commit(&S.empty[stage]);
                     if (group_end) {
                         tc_commit(&S.acc0_full);  // acc0 (and, on a tile's last stage, acc1) ready
                         pending = true;
@@ -361,7 +400,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const bool use_beta = (beta.x != 0.0f) || (beta.y != 0.0f);
         uint32_t f_phase = 0;
         bool ok = true;
-        for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+        for (int u = first_unit(); u < num_units && ok; u += unit_step()) {
             const Unit x = unit_of(u, num_tiles, w.S);
             const qcs_gemm_desc_t dg = desc[x.g];
             if (w.G > 1 && !kind_runs(KIND, dg.mode)) continue;
@@ -369,7 +408,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const float unB = ldexpf(1.0f, -dg.sB);
             const int nkb = kb_begin(x.r + 1) - kb_begin(x.r);
             int tm, tn;
-            tile_coords(x.t, tiles_m, tiles_n, group_m, tm, tn);
+            coords(x.t, tm, tn);
             float racc[kEpiCols], iacc[kEpiCols];
 #pragma unroll
             for (int j = 0; j < kEpiCols; ++j) racc[j] = iacc[j] = 0.0f;
@@ -498,6 +537,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     tc_fence_before();
     __syncthreads();
+    // MC: neither CTA leaves while the other may still write into its shared
+    // memory or arrive on its barriers
+    if constexpr (MC) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
         __syncwarp();
@@ -561,26 +603,71 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// mcB not NULL (complex kernel, an even number of tile rows): clusters of
+// two CTAs sharing each B box, mcB[0] covering B planes 0-2 and mcB[1]
+// planes 3-4 of every box (mapB, all five planes, otherwise).
 template <int KIND, int DRAIN, bool REAL>
 cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
-                        const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad, float2 alpha,
-                        float2 beta, float2 *C, int64_t ldc, int *d_err, int num_sms,
-                        int group_m, const TcWork &w, cudaStream_t s) {
+                        const CUtensorMap *mapB, const CUtensorMap *mcB, int64_t m, int64_t n,
+                        int64_t k_pad, float2 alpha, float2 beta, float2 *C, int64_t ldc,
+                        int *d_err, int num_sms, int group_m, const TcWork &w, cudaStream_t s) {
     const size_t smem = sizeof(TcSmem<REAL>) + 1024;
+    constexpr int tn = TcGeom<REAL>::tile_n;
+    const int64_t tiles_m = (m + kBM - 1) / kBM;
+    const int64_t units = tiles_m * ((n + tn - 1) / tn) * w.G * w.S;
+    if (units == 0 || k_pad == 0) return cudaSuccess;
+    const int gm = group_m < 1 ? 1 : group_m;
+    if (!REAL && mcB && tiles_m % 2 == 0) {
+        auto kern = cgemm_tc_kernel<KIND, DRAIN, REAL, !REAL>;
+        static int max_clusters = 0;  // clusters of two that fit at once, measured once
+        if (max_clusters == 0) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            cudaLaunchConfig_t q = {};
+            cudaLaunchAttribute qa[1];
+            qa[0].id = cudaLaunchAttributeClusterDimension;
+            qa[0].val.clusterDim.x = 2;
+            qa[0].val.clusterDim.y = 1;
+            qa[0].val.clusterDim.z = 1;
+            q.gridDim = dim3((unsigned)(num_sms & ~1));
+            q.blockDim = dim3(kTcThreads);
+            q.dynamicSmemBytes = smem;
+            q.attrs = qa;
+            q.numAttrs = 1;
+            e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &q);
+            if (e != cudaSuccess || max_clusters < 1) {
+                cudaGetLastError();
+                return cudaErrorNotSupported;
+            }
+        }
+        const int64_t pair_units = units / 2;
+        const int clusters = (int)std::min<int64_t>(pair_units, max_clusters);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(2 * clusters));
+        cfg.blockDim = dim3(kTcThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kern, *mapA, mcB[0], mcB[1], desc, (int)m, (int)n,
+                                  (int)k_pad, alpha, beta, C, ldc, d_err, gm, w);
+    }
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel<KIND, DRAIN, REAL>,
+        cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel<KIND, DRAIN, REAL, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    constexpr int tn = TcGeom<REAL>::tile_n;
-    const int64_t units = ((m + kBM - 1) / kBM) * ((n + tn - 1) / tn) * w.G * w.S;
-    if (units == 0 || k_pad == 0) return cudaSuccess;
     const int grid = static_cast<int>(units < num_sms ? units : num_sms);
-    cgemm_tc_kernel<KIND, DRAIN, REAL><<<grid, kTcThreads, smem, s>>>(
-        *mapA, *mapB, desc, (int)m, (int)n, (int)k_pad, alpha, beta, C, ldc, d_err,
-        group_m < 1 ? 1 : group_m, w);
+    cgemm_tc_kernel<KIND, DRAIN, REAL, false><<<grid, kTcThreads, smem, s>>>(
+        *mapA, *mapB, *mapB, desc, (int)m, (int)n, (int)k_pad, alpha, beta, C, ldc, d_err, gm, w);
     return cudaGetLastError();
 }
 
@@ -588,35 +675,35 @@ cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
 // 16-bit kinds, 16 for TF32).
 template <int KIND, bool REAL>
 cudaError_t launch_drain(int drain, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
-                         const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad,
-                         float2 alpha, float2 beta, float2 *C, int64_t ldc, int *d_err,
-                         int num_sms, int group_m, const TcWork &w, cudaStream_t s) {
+                         const CUtensorMap *mapB, const CUtensorMap *mcB, int64_t m, int64_t n,
+                         int64_t k_pad, float2 alpha, float2 beta, float2 *C, int64_t ldc,
+                         int *d_err, int num_sms, int group_m, const TcWork &w, cudaStream_t s) {
     if (drain >= 4)
-        return launch_kind<KIND, 4, REAL>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                          d_err, num_sms, group_m, w, s);
+        return launch_kind<KIND, 4, REAL>(desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta, C,
+                                          ldc, d_err, num_sms, group_m, w, s);
     if (drain == 2)
-        return launch_kind<KIND, 2, REAL>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                          d_err, num_sms, group_m, w, s);
-    return launch_kind<KIND, 1, REAL>(desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc, d_err,
-                                      num_sms, group_m, w, s);
+        return launch_kind<KIND, 2, REAL>(desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta, C,
+                                          ldc, d_err, num_sms, group_m, w, s);
+    return launch_kind<KIND, 1, REAL>(desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta, C, ldc,
+                                      d_err, num_sms, group_m, w, s);
 }
 
 template <bool REAL>
 cudaError_t launch_any(int kind, int drain, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
-                       const CUtensorMap *mapB, int64_t m, int64_t n, int64_t k_pad, float2 alpha,
-                       float2 beta, float2 *C, int64_t ldc, int *d_err, int num_sms, int group_m,
-                       cudaStream_t s, const TcWork &w) {
+                       const CUtensorMap *mapB, const CUtensorMap *mcB, int64_t m, int64_t n,
+                       int64_t k_pad, float2 alpha, float2 beta, float2 *C, int64_t ldc,
+                       int *d_err, int num_sms, int group_m, cudaStream_t s, const TcWork &w) {
     if (w.G < 1 || w.S < 1 || (w.S > 1 && !w.P)) return cudaErrorInvalidValue;
     switch (kind) {
         case 0:
-            return launch_drain<0, REAL>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                         d_err, num_sms, group_m, w, s);
+            return launch_drain<0, REAL>(drain, desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta,
+                                         C, ldc, d_err, num_sms, group_m, w, s);
         case 1:
-            return launch_drain<1, REAL>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                         d_err, num_sms, group_m, w, s);
+            return launch_drain<1, REAL>(drain, desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta,
+                                         C, ldc, d_err, num_sms, group_m, w, s);
         default:
-            return launch_drain<2, REAL>(drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                                         d_err, num_sms, group_m, w, s);
+            return launch_drain<2, REAL>(drain, desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta,
+                                         C, ldc, d_err, num_sms, group_m, w, s);
     }
 }
 
@@ -626,9 +713,9 @@ cudaError_t launch_cgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
                             const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
                             int64_t n, int64_t k_pad, float2 alpha, float2 beta, float2 *C,
                             int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s,
-                            const TcWork &w) {
-    return launch_any<false>(kind, drain, desc, mapA, mapB, m, n, k_pad, alpha, beta, C, ldc,
-                             d_err, num_sms, group_m, s, w);
+                            const TcWork &w, const CUtensorMap *mcB) {
+    return launch_any<false>(kind, drain, desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta, C,
+                             ldc, d_err, num_sms, group_m, s, w);
 }
 
 cudaError_t launch_sgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
@@ -636,7 +723,8 @@ cudaError_t launch_sgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
                             int64_t n, int64_t k_pad, float alpha, float beta, float *C,
                             int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s,
                             const TcWork &w) {
-    return launch_any<true>(kind, drain, desc, mapA, mapB, m, n, k_pad, make_float2(alpha, 0.f),
+    return launch_any<true>(kind, drain, desc, mapA, mapB, nullptr, m, n, k_pad,
+                            make_float2(alpha, 0.f),
                             make_float2(beta, 0.f), reinterpret_cast<float2 *>(C), ldc, d_err,
                             num_sms, group_m, s, w);
 }

@@ -97,6 +97,7 @@ struct qcs_handle_s {
     int complex_products = 4;        // real products per emulated complex product (4, or 3: Gauss)
     int fused_split = 0;             // TF32X: split inside the tensor-core kernel's staging
     int tree_levels = 1;             // tree executor: small FP32 steps of a level in one launch
+    int tc_multicast = 0;            // complex tensor-core kernel in clusters of two sharing B
     size_t group_budget = size_t(32) << 30;  // tree executor: bytes a grouped GPU-filling step may hold
     uint64_t wait_ns = qcs::kWaitBudgetNs;  // bound of the tensor-core kernels' device waits
     int debug_stall = 0;             // test hook: the TMA producer issues no loads
@@ -410,12 +411,14 @@ cudaError_t launch_cgemm_tc_fused(EncodeTiledFn encode, const qcs_gemm_desc_t *d
 // FP16X, FP16X_SCALED), 1 TF32, 2 BF16; the kernel returns at once unless
 // desc->mode belongs to its kind (per instance when w.G > 1).
 // ``drain``: pipeline stages per round-to-nearest drain of the hi*hi
-// accumulator (1, 2 or 4).
+// accumulator (1, 2 or 4).  mcB not NULL: clusters of two CTAs share the
+// B boxes (mcB[0]: planes 0-2 of each box, mcB[1]: planes 3-4) when the
+// output has an even number of tile rows; otherwise mapB (all five planes).
 cudaError_t launch_cgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
                             const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
                             int64_t n, int64_t k_pad, float2 alpha, float2 beta, float2 *C,
                             int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s,
-                            const TcWork &w = TcWork{});
+                            const TcWork &w = TcWork{}, const CUtensorMap *mcB = nullptr);
 // C = alpha sum_r P_r + beta C after a split-K launch (nothing when w.S == 1),
 // for the instances whose descriptor did not select FP32.
 cudaError_t launch_tc_reduce(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, float2 alpha,
