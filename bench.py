@@ -65,7 +65,7 @@ def parse(argv=None):
                    help="host processes that cost the seeded orders")
     p.add_argument("--sweep-sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192, 16384])
     p.add_argument("--profile", choices=["slice", "slice_seed2", "gather", "gemm", "sgemm",
-                                         "scaling"],
+                                         "scaling", "contraction", "precision"],
                    default=None,
                    help="run one workload for an ncu capture (NVTX range 'measure') and exit: "
                         "'slice' one group of 16 slices of the 30-qubit network in the cheapest "
@@ -357,6 +357,47 @@ def scaling_probe(args):
     print(json.dumps({"profile": "scaling", "steps": rows}), flush=True)
 
 
+def contraction_network(args, tn, qi):
+    """The 30-qubit network of the contraction leg: 5x6 grid, depth 14, one
+    bitstring, in the cheapest of --greedy-trials seeded greedy orders over
+    the network with and without its single-qubit gates absorbed, 6 sliced
+    indices.  Returns (circuit, bits, networks, index used, order, sliced, seed)."""
+    circ = qi.random_grid_circuit(5, 6, 14, seed=0)
+    bits = qi.random_bitstrings(30, 1, seed=1)
+    net_full = tn.circuit_network(circ, bits)
+    nets = [net_full] + ([] if args.no_absorb else [tn.absorb_single_qubit_gates(net_full)])
+    which, order, sliced, seed_used = tn.cheapest_network_order(
+        nets, range(args.greedy_trials), skip=[tn.BATCH], n_slices=6, workers=args.greedy_workers)
+    return circ, bits, nets, which, order, sliced, seed_used
+
+
+def precision_network(args, tn, qi):
+    """The 40-qubit network of the precision leg: 5x8 grid, depth 12, one
+    bitstring, sliced on the 8 indices of tests/golden/slices5x8_d12.txt, in
+    the cheapest of --greedy-trials orders.  Returns (labels, golden rows,
+    circuit, bits, networks, index used, order, seed), or None without the file."""
+    path = os.path.join(ROOT, "tests", "golden", "slices5x8_d12.txt")
+    if not os.path.exists(path):
+        return None
+    labels, rows = None, []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("sliced"):
+                labels = [int(v) for v in line.split()[1:]]
+            elif line.strip() and not line.startswith("#"):
+                v, re, im = line.split()
+                rows.append((v, float(re) + 1j * float(im)))
+    circ = qi.random_grid_circuit(5, 8, 12, seed=0)
+    bits = qi.random_bitstrings(40, 1, seed=1)
+    net_full = tn.circuit_network(circ, bits)
+    # absorbed or not, the oracle's sliced labels survive
+    nets = [net_full] + ([] if args.no_absorb else
+                         [tn.absorb_single_qubit_gates(net_full, keep_labels=labels)])
+    which, order, _, seed_used = tn.cheapest_network_order(
+        nets, range(args.greedy_trials), skip=[tn.BATCH] + labels, workers=args.greedy_workers)
+    return labels, rows, circ, bits, nets, which, order, seed_used
+
+
 def profile_run(args):
     """One workload between torch.cuda.nvtx range 'measure' (after one
     untimed run), for ``ncu --nvtx --nvtx-include "measure/"``; prints a
@@ -370,10 +411,23 @@ def profile_run(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if args.profile in ("slice", "slice_seed2"):
+    if args.profile in ("slice", "slice_seed2", "contraction", "precision"):
         circ = qi.random_grid_circuit(5, 6, 14, seed=0)
         bits = qi.random_bitstrings(30, 1, seed=1)
-        if args.profile == "slice":
+        if args.profile == "contraction":
+            _, _, nets, which, order, sliced, seed_used = contraction_network(args, tn, qi)
+            plan = tn.build_plan(nets[which], order, sliced, mode=q.MODE_AUTO)
+            ni, what = 16, ("16 slices (one group) of the contraction leg's 30-qubit network "
+                            "(seed %d of %d, single-qubit gates %s), AUTO-%g, tuned rule"
+                            % (seed_used, args.greedy_trials,
+                               "absorbed" if which == 1 else "apart", args.tol))
+        elif args.profile == "precision":
+            labels, _, _, _, nets, which, order, seed_used = precision_network(args, tn, qi)
+            plan = tn.build_plan(nets[which], order, labels, mode=q.MODE_AUTO)
+            ni, what = 16, ("16 slices (one group) of the precision leg's 40-qubit network "
+                            "(seed %d of %d), AUTO-%g, tuned rule"
+                            % (seed_used, args.greedy_trials, args.tol))
+        elif args.profile == "slice":
             plan = tn.plan_circuit(circ, bits, seed=0, n_slices=6, mode=q.MODE_AUTO,
                                    trials=args.greedy_trials, workers=args.greedy_workers)
             ni, what = 16, ("16 slices (one group) of the 5x6 depth-14 network in the cheapest "
@@ -1266,14 +1320,9 @@ def tree_legs(args, q, torch, dev, rank, world=1, dist=None):
                 ("fp32", "fp32", q.SIZE_RULE_PAPER, 0.0)]
     # 30-qubit 5x6 grid, depth 14, sliced on 6 indices (64 slices), one bitstring,
     # contracted in the cheapest of --greedy-trials seeded greedy orders
-    circ = qi.random_grid_circuit(5, 6, 14, seed=0)
-    bits = qi.random_bitstrings(30, 1, seed=1)
-    net_full = tn.circuit_network(circ, bits)
-    nets = [net_full] + ([] if args.no_absorb else [tn.absorb_single_qubit_gates(net_full)])
     t0 = time.perf_counter()
-    which, order, sliced, seed_used = tn.cheapest_network_order(
-        nets, range(args.greedy_trials), skip=[tn.BATCH], n_slices=6, workers=args.greedy_workers)
-    net = nets[which]
+    circ, bits, nets, which, order, sliced, seed_used = contraction_network(args, tn, qi)
+    net, net_full = nets[which], nets[0]
     planning_s = time.perf_counter() - t0
     plans = {}
 
@@ -1494,25 +1543,10 @@ def scale_leg(args, q, torch, dev, tn, qi, rank):
 
     import numpy as np
 
-    path = os.path.join(ROOT, "tests", "golden", "slices5x8_d12.txt")
-    if not os.path.exists(path):
+    found = precision_network(args, tn, qi)
+    if found is None:
         return {"skipped": "tests/golden/slices5x8_d12.txt missing"}
-    labels, rows = None, []
-    with open(path) as f:
-        for line in f:
-            if line.startswith("sliced"):
-                labels = [int(v) for v in line.split()[1:]]
-            elif line.strip() and not line.startswith("#"):
-                v, re, im = line.split()
-                rows.append((v, float(re) + 1j * float(im)))
-    circ = qi.random_grid_circuit(5, 8, 12, seed=0)
-    bits = qi.random_bitstrings(40, 1, seed=1)
-    net_full = tn.circuit_network(circ, bits)
-    # absorbed or not, the oracle's sliced labels survive
-    nets = [net_full] + ([] if args.no_absorb else
-                         [tn.absorb_single_qubit_gates(net_full, keep_labels=labels)])
-    which, order, _, seed_used = tn.cheapest_network_order(
-        nets, range(args.greedy_trials), skip=[tn.BATCH] + labels, workers=args.greedy_workers)
+    labels, rows, circ, bits, nets, which, order, seed_used = found
     net = nets[which]
     plans = {}
 
