@@ -85,3 +85,50 @@ def test_grouped_adjoint_with_sliced_leaves_and_levels_off():
     assert np.array_equal(gg, g1)
     L_ref, g_ref = oracle.loss_and_grad(circ, bits)
     assert np.linalg.norm(gg - g_ref) / np.linalg.norm(g_ref) < 1e-4
+
+
+def test_a_lone_leaf_forward_and_backward_in_groups():
+    """A plan without steps (the root is the leaf itself, read at each
+    instance's offset): the forward copies, the backward seeds the leaf's
+    gradient at each instance's offset; a group size above 1 falls back to
+    one instance at a time and gives the same result."""
+    import ctypes
+
+    need_gpu()
+    q = lib()
+    L = q._lib
+    n_inst, out_size = 3, 4
+    leaf = torch.arange(12, dtype=torch.float32, device="cuda").to(torch.complex64) * (1 + 2j)
+    t = L.qcs_tree_t()
+    sizes = (ctypes.c_int64 * 1)(12)
+    offs = (ctypes.c_int64 * 3)(0, 4, 8)
+    slots = (ctypes.c_int32 * 3)(0, 1, 2)
+    t.n_leaves, t.n_steps, t.n_instances, t.n_slots = 1, 0, n_inst, n_inst
+    t.leaf_size, t.instance_offset, t.instance_slot = sizes, offs, slots
+    t.steps, t.out_size, t.out_index = None, out_size, None
+    leaves = (ctypes.c_void_p * 1)(leaf.data_ptr())
+    g_out = torch.zeros((n_inst, out_size), dtype=torch.complex128, device="cuda")
+    g_out += torch.arange(n_inst * out_size, dtype=torch.float64, device="cuda").reshape(
+        n_inst, out_size).to(torch.complex128) * (0.5 - 1j)
+    grads = []
+    for G in (1, 3):
+        hd = q.Handle()
+        try:
+            hd.set_instance_batch(G)
+            out = torch.zeros((n_inst, out_size), dtype=torch.complex128, device="cuda")
+            info = L.qcs_run_info_t()
+            assert hd.lib.qcs_contract_tree(hd.ptr, ctypes.byref(t), leaves,
+                                            ctypes.c_void_p(out.data_ptr()), ctypes.byref(info)) == 0
+            gl = torch.zeros(12, dtype=torch.complex64, device="cuda")
+            gp = (ctypes.c_void_p * 1)(gl.data_ptr())
+            assert hd.lib.qcs_contract_tree_backward(hd.ptr, ctypes.byref(t), leaves,
+                                                     ctypes.c_void_p(g_out.data_ptr()), gp,
+                                                     ctypes.byref(info)) == 0
+            torch.cuda.synchronize()
+            hd.sync()
+            assert torch.equal(out.cpu(), leaf.cpu().to(torch.complex128).reshape(n_inst, out_size))
+            grads.append(gl.cpu())
+        finally:
+            hd.close()
+    assert torch.equal(grads[0], grads[1])
+    assert torch.equal(grads[0], g_out.reshape(-1).cpu().to(torch.complex64))
