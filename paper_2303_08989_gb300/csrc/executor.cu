@@ -133,14 +133,15 @@ int validate(const qcs_tree_t *t, std::vector<int64_t> &size_of, bool need_tree)
         }
         size_of[self] = st.m * st.n;
     }
-    const int64_t rs = root_size(t, size_of);
+    // The root as every instance sees it: the last step's output, or (no
+    // steps) leaf 0 from the instance's offset on.
+    const int64_t rs = ns > 0 ? root_size(t, size_of) : size_of[0] - max_off[0];
     if (t->out_index) {
         for (int64_t j = 0; j < t->out_size; ++j)
             if (t->out_index[j] < 0 || t->out_index[j] >= rs) return QCS_ERR_INVALID_ARG;
-    } else if (rs != t->out_size) {
+    } else if (ns > 0 ? rs != t->out_size : rs < t->out_size) {
         return QCS_ERR_INVALID_ARG;
     }
-    if (ns == 0 && max_off[0] + t->out_size > size_of[0] && !t->out_index) return QCS_ERR_INVALID_ARG;
     if (need_tree) {
         for (int i = 0; i < nl + ns - 1; ++i)
             if (uses[i] != 1) return QCS_ERR_INVALID_ARG;

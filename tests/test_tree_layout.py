@@ -163,3 +163,33 @@ def test_invalid_plan_rejected():
     cp.tree.steps[0].a = cp.tree.steps[0].b  # a step reading the same tensor twice
     assert lib.qcs_tree_layout_info(ctypes.byref(cp.tree), 0, 1, 1, 152, 0, None, None, None,
                                     None, None, ctypes.byref(out)) == -1
+
+
+@pytest.mark.parametrize("offsets,index,ok", [
+    ((0, 4, 8), None, True),          # each instance reads its own 4 elements
+    ((0, 4, 9), None, False),         # the last window runs past the leaf
+    ((0, 4, 8), (0, 1, 2, 3), True),
+    ((0, 4, 9), (0, 1, 2, 3), False),  # index 3 at offset 9 is element 12 of 12
+    ((0, 0, 0), (11, 0, 5, 5), True),
+    ((0, 0, 1), (11, 0, 5, 5), False),
+])
+def test_a_lone_leaf_is_read_at_every_instance_offset(offsets, index, ok):
+    """A plan without steps: the root of an instance is leaf 0 from that
+    instance's offset on, so the output (the first out_size elements, or the
+    out_index entries) must lie inside the leaf at every offset."""
+    L, _ = _mods()
+    lib = L.load()
+    t = L.qcs_tree_t()
+    sizes = (ctypes.c_int64 * 1)(12)
+    offs = (ctypes.c_int64 * 3)(*offsets)
+    slots = (ctypes.c_int32 * 3)(0, 1, 2)
+    t.n_leaves, t.n_steps, t.n_instances, t.n_slots = 1, 0, 3, 3
+    t.leaf_size, t.instance_offset, t.instance_slot = sizes, offs, slots
+    t.steps, t.out_size = None, 4
+    idx = (ctypes.c_int64 * 4)(*index) if index is not None else None
+    t.out_index = idx
+    out = L.qcs_tree_layout_t()
+    for backward in (0, 1):
+        rc = lib.qcs_tree_layout_info(ctypes.byref(t), backward, 1, 1, 152, 32 << 30, None, None,
+                                      None, None, None, ctypes.byref(out))
+        assert rc == (0 if ok else L.QCS_ERR_INVALID_ARG), backward
