@@ -149,6 +149,19 @@ int qcs_set_tc_schedule(qcs_handle_t h, int group_m, int l2_promotion);
  * values. */
 int qcs_set_tc_multicast(qcs_handle_t h, int enabled);
 
+/* CTA pairs for the tensor-core kernels (a schedule; each output element is
+ * the same sequence of tensor-core products in the same order either way).
+ * While ``enabled`` is 1 the complex and real kernels run in clusters of two
+ * CTAs, each cluster on one 256-row tile (two 128-row tile rows of the same
+ * tile column) with tcgen05 MMAs of cta_group::2: each CTA holds its 128
+ * rows of op(A) and half of every op(B) operand of a stage, and one thread
+ * of the even CTA issues the MMAs of both, so each tensor core reads half as
+ * many op(B) bytes per MMA from shared memory.  Used when the output has an
+ * even number of 128-row tile rows and the drain is 4 stages (the default);
+ * takes precedence over qcs_set_tc_multicast.  Default 0; environment
+ * override QCS_TC_PAIRS.  QCS_ERR_INVALID_ARG for other values. */
+int qcs_set_tc_pairs(qcs_handle_t h, int enabled);
+
 /* K ranges of the tensor-core kernels.  A GEMM with few 128 x 128 output
  * tiles for its K (for example m = n = 1024: 64 tiles on 152 SMs) leaves
  * SMs idle; its K loop can be cut into ``splits`` equal ranges that run as
@@ -362,7 +375,9 @@ typedef struct {
     const qcs_step_t *steps;         /* host, n_steps */
     int64_t out_size;                /* results per slot */
     const int64_t *out_index;        /* host, out_size indices into the root, or NULL:
-                                        the root itself (then root size == out_size) */
+                                        the root itself (then root size == out_size;
+                                        n_steps == 0: the out_size elements of leaf 0
+                                        from the instance's offset on) */
 } qcs_tree_t;
 
 typedef struct {

@@ -186,6 +186,12 @@ class Handle:
         _lib.check(self.lib.qcs_set_tc_multicast(self._h, int(bool(enabled))),
                    "qcs_set_tc_multicast")
 
+    def set_tc_pairs(self, enabled: bool):
+        """Run the tensor-core kernels as CTA pairs on 256-row tiles, each CTA
+        holding half of every op(B) operand (tcgen05 cta_group::2;
+        qcs_set_tc_pairs; off by default)."""
+        _lib.check(self.lib.qcs_set_tc_pairs(self._h, int(bool(enabled))), "qcs_set_tc_pairs")
+
     def set_tree_levels(self, enabled: bool):
         """Run a contraction tree level by level, the small plain-FP32 steps
         of each level as one launch (qcs_set_tree_levels; on by default)."""

@@ -37,7 +37,7 @@ EXPORTED = [
     "qcs_set_tc_splits", "qcs_sgemm", "qcs_set_complex_products", "qcs_set_wait_budget",
     "qcs_debug_stall_producer", "qcs_cgemm_noalloc_status", "qcs_measure_fma_peak",
     "qcs_set_fused_split", "qcs_set_tree_levels", "qcs_set_group_budget", "qcs_fidelity_stats",
-    "qcs_tree_layout_info", "qcs_set_tc_multicast",
+    "qcs_tree_layout_info", "qcs_set_tc_multicast", "qcs_set_tc_pairs",
     "qcs_selection_stats", "qcs_tree_backward_graph_create",
 ]
 SIZE_RULE_OFF, SIZE_RULE_PAPER, SIZE_RULE_TUNED = 0, 1, 2
@@ -179,6 +179,7 @@ def load(path: str = LIB_PATH):
         "qcs_set_fused_split": [H, I],
         "qcs_set_tree_levels": [H, I],
         "qcs_set_tc_multicast": [H, I],
+        "qcs_set_tc_pairs": [H, I],
         "qcs_set_group_budget": [H, ctypes.c_uint64],
         "qcs_fidelity_stats": [H, P, I, P, I64, P],
         "qcs_tree_layout_info": [ctypes.POINTER(qcs_tree_t), I, I, I, I, ctypes.c_uint64, P, P,

@@ -446,17 +446,20 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
             // One launch per kind over the tiles of all G instances.
             ProfScope ps_tc(h, kProfGemmTc);
             if (need16) {
-                CUtensorMap ma, mb, mc[2];
+                CUtensorMap ma, mb, mc[2], pc[2];
                 if (encode_planes(h, &ma, planesA, G * mp, kp, 2, kPlanes) ||
                     encode_planes(h, &mb, planesB, G * np, kp, 2, kPlanesB) ||
                     (h->tc_multicast &&
                      (encode_planes(h, &mc[0], planesB, G * np, kp, 2, kPlanesB, kBM, 3) ||
-                      encode_planes(h, &mc[1], planesB, G * np, kp, 2, kPlanesB, kBM, 2))))
+                      encode_planes(h, &mc[1], planesB, G * np, kp, 2, kPlanesB, kBM, 2))) ||
+                    (h->tc_pairs &&
+                     (encode_planes(h, &pc[0], planesB, G * np, kp, 2, kPlanesB, kBM, 2) ||
+                      encode_planes(h, &pc[1], planesB, G * np, kp, 2, kPlanesB, kBN / 2, 2))))
                     return QCS_ERR_CUDA;
                 const int kind = (eff == QCS_MODE_BF16X3) ? 2 : 0;
                 e = launch_cgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
                                     ldc, h->d_err, h->num_sms, gm, s, w,
-                                    h->tc_multicast ? mc : nullptr);
+                                    h->tc_multicast ? mc : nullptr, h->tc_pairs ? pc : nullptr);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             }
             if (need32 && tf32_fused) {
@@ -465,16 +468,19 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
                                           gm, w, s);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             } else if (need32) {
-                CUtensorMap ma, mb, mc[2];
+                CUtensorMap ma, mb, mc[2], pc[2];
                 if (encode_planes(h, &ma, planesA32, G * mp, kp, 4, kPlanes) ||
                     encode_planes(h, &mb, planesB32, G * np, kp, 4, kPlanesB) ||
                     (h->tc_multicast &&
                      (encode_planes(h, &mc[0], planesB32, G * np, kp, 4, kPlanesB, kBM, 3) ||
-                      encode_planes(h, &mc[1], planesB32, G * np, kp, 4, kPlanesB, kBM, 2))))
+                      encode_planes(h, &mc[1], planesB32, G * np, kp, 4, kPlanesB, kBM, 2))) ||
+                    (h->tc_pairs &&
+                     (encode_planes(h, &pc[0], planesB32, G * np, kp, 4, kPlanesB, kBM, 2) ||
+                      encode_planes(h, &pc[1], planesB32, G * np, kp, 4, kPlanesB, kBN / 2, 2))))
                     return QCS_ERR_CUDA;
                 e = launch_cgemm_tc(1, h->drain_stages, desc, &ma, &mb, m, n, kp, alpha, beta, C,
                                     ldc, h->d_err, h->num_sms, gm, s, w,
-                                    h->tc_multicast ? mc : nullptr);
+                                    h->tc_multicast ? mc : nullptr, h->tc_pairs ? pc : nullptr);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             }
             e = launch_tc_reduce(desc, m, n, alpha, beta, C, ldc, h->num_sms, w, s);
@@ -617,13 +623,15 @@ int run_sgemm(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, in
             ProfScope ps_tc(h, kProfGemmTc);
             for (int esz = 2; esz <= 4; esz += 2) {
                 if ((esz == 2 && !need16) || (esz == 4 && !need32)) continue;
-                CUtensorMap ma, mb;
+                CUtensorMap ma, mb, pb;
                 if (encode_planes(h, &ma, planesA, L.mp, L.kp, esz, 2, kBM) ||
-                    encode_planes(h, &mb, planesB, L.np, L.kp, esz, 2, 2 * kBN))
+                    encode_planes(h, &mb, planesB, L.np, L.kp, esz, 2, 2 * kBN) ||
+                    (h->tc_pairs && encode_planes(h, &pb, planesB, L.np, L.kp, esz, 2, kBM)))
                     return QCS_ERR_CUDA;
                 const int kind = (esz == 4) ? 1 : (eff == QCS_MODE_BF16X3 ? 2 : 0);
                 e = launch_sgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, L.kp, alpha, beta,
-                                    C, ldc, h->d_err, h->num_sms, h->tc_group_m, s, w);
+                                    C, ldc, h->d_err, h->num_sms, h->tc_group_m, s, w,
+                                    h->tc_pairs ? &pb : nullptr);
                 if (e != cudaSuccess) return QCS_ERR_CUDA;
             }
             e = launch_tc_reduce_real(desc, m, n, alpha, beta, C, ldc, h->num_sms, w, s);
@@ -746,13 +754,15 @@ int run_cgemm_3m(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m,
         ProfScope ps_tc(h, kProfGemmTc);
         for (int esz = 2; esz <= 4; esz += 2) {
             if ((esz == 2 && !need16) || (esz == 4 && !need32)) continue;
-            CUtensorMap ma, mb;
+            CUtensorMap ma, mb, pb;
             if (encode_planes(h, &ma, planesA, 3 * L.mp, L.kp, esz, 2, kBM) ||
-                encode_planes(h, &mb, planesB, 3 * L.np, L.kp, esz, 2, 2 * kBN))
+                encode_planes(h, &mb, planesB, 3 * L.np, L.kp, esz, 2, 2 * kBN) ||
+                (h->tc_pairs && encode_planes(h, &pb, planesB, 3 * L.np, L.kp, esz, 2, kBM)))
                 return QCS_ERR_CUDA;
             const int kind = (esz == 4) ? 1 : (eff == QCS_MODE_BF16X3 ? 2 : 0);
             e = launch_sgemm_tc(kind, h->drain_stages, desc, &ma, &mb, m, n, L.kp, 1.0f, 0.0f, T, m,
-                                h->d_err, h->num_sms, h->tc_group_m, s, w);
+                                h->d_err, h->num_sms, h->tc_group_m, s, w,
+                                h->tc_pairs ? &pb : nullptr);
             if (e != cudaSuccess) return QCS_ERR_CUDA;
         }
         e = launch_tc_reduce_real(desc, m, n, 1.0f, 0.0f, T, m, h->num_sms, w, s);
@@ -838,6 +848,7 @@ int qcs_create(qcs_handle_t *out, void *cuda_stream) {
     if (const char *f = std::getenv("QCS_FUSED_SPLIT")) h->fused_split = std::atoi(f) != 0;
     if (const char *l = std::getenv("QCS_TREE_LEVELS")) h->tree_levels = std::atoi(l) != 0;
     if (const char *c = std::getenv("QCS_TC_MULTICAST")) h->tc_multicast = std::atoi(c) != 0;
+    if (const char *c = std::getenv("QCS_TC_PAIRS")) h->tc_pairs = std::atoi(c) != 0;
     if (const char *b = std::getenv("QCS_GROUP_BUDGET_MB"))
         h->group_budget = (size_t)std::max(0LL, std::atoll(b)) << 20;
     if (const char *k = std::getenv("QCS_TC_SPLITS"))
@@ -979,6 +990,12 @@ int qcs_fidelity_stats(qcs_handle_t h, const void *a, int a_c64, const double *r
 int qcs_set_tc_multicast(qcs_handle_t h, int enabled) {
     if (!h || (enabled != 0 && enabled != 1)) return QCS_ERR_INVALID_ARG;
     h->tc_multicast = enabled;
+    return QCS_SUCCESS;
+}
+
+int qcs_set_tc_pairs(qcs_handle_t h, int enabled) {
+    if (!h || (enabled != 0 && enabled != 1)) return QCS_ERR_INVALID_ARG;
+    h->tc_pairs = enabled;
     return QCS_SUCCESS;
 }
 

@@ -75,6 +75,26 @@
 // with one TMA multicast into the shared memory of both.  A stage is freed
 // once the MMAs of both CTAs have read it (each commit arrives on both CTAs'
 // "empty" barriers), so the B traffic from L2 per CTA halves.
+//
+// CTA pairs (CL = kClPair, qcs_set_tc_pairs): the two CTAs of a cluster run
+// one M = 256 tile (tile rows 2p and 2p + 1) with tcgen05 MMAs of
+// cta_group::2, issued by one thread of the even CTA.  Each CTA keeps its own
+// 128 rows of A and HALF of every B operand: a pair MMA takes the first N/2
+// rows of its K-major B from the even CTA and the rest from the odd one, at
+// the same shared-memory offset, so each tensor core reads half the B bytes
+// per MMA it did alone (complex: 56 KB of shared-memory reads per K step
+// instead of 80).  Per complex stage the even CTA holds B planes 0, 1
+// (-Bi_hi, Br_hi) and the odd one planes 1, 2 (Br_hi, Bi_hi), so that the
+// same slot is [-Bi; Br] or [Br; Bi] across the pair; and each holds its 64
+// of the 128 rows of the lo planes 3, 4 for the N = 128 MMAs.  A stage is
+// 32 + 24 KB and four fit.  Real pairs: each CTA holds 128 of the 256 B rows
+// of both planes (32 KB stages, six of them).  Each CTA loads its own
+// operands (TMA, its own "full" barriers); the odd CTA's MMA warp forwards
+// each completed stage to the even CTA's "full" barrier (a remote arrive),
+// the even CTA's commits arrive on both CTAs' "empty" and "acc0_full"
+// barriers, and the odd CTA's epilogue warps arrive remotely on the even
+// CTA's "acc0_empty".  Every tensor-core result of a tile is the same MMA
+// sequence as in one CTA.
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -87,21 +107,36 @@ namespace {
 constexpr int kEpiWarps = 8;
 constexpr int kEpiCols = kBN / 2;  // columns per epilogue warp
 
+// Cluster forms of a launch: one CTA per tile, two CTAs sharing each B box
+// by TMA multicast, or a CTA pair running M = 256 tiles.
+constexpr int kClNone = 0, kClMulticast = 1, kClPair = 2;
+
 // Stage geometry of the complex (REAL = false) and real kernels.
-template <bool REAL>
+template <bool REAL, int CL = kClNone>
 struct TcGeom {
-    static constexpr int stages = REAL ? 4 : kStages;
+    static constexpr bool pair = CL == kClPair;
+    static constexpr int stages = pair ? (REAL ? 6 : 4) : (REAL ? 4 : kStages);
     static constexpr int a_bytes = REAL ? 2 * kTileBytes : kAStageBytes;  // 16 | 32 KB
-    static constexpr int b_bytes = REAL ? 4 * kTileBytes : kBStageBytes;  // 32 | 40 KB
-    static constexpr int stage_bytes = a_bytes + b_bytes;                 // 48 | 72 KB
+    // B bytes per CTA and stage: alone 32 | 40 KB; pairs 16 | 24 KB
+    static constexpr int b_bytes =
+        pair ? (REAL ? 2 * kTileBytes : 3 * kTileBytes) : (REAL ? 4 * kTileBytes : kBStageBytes);
+    static constexpr int stage_bytes = a_bytes + b_bytes;  // 48 | 72 KB; pairs 32 | 56 KB
     static constexpr int tile_n = REAL ? 2 * kBN : kBN;  // output columns of a tile
+    // Byte offset, in the B part of a stage, of the operand the MMAs call B
+    // plane p (complex: 0 -Bi_hi, 1 Br_hi, 3 Br_lo, 4 Bi_lo, the 256-row
+    // operands at 0 and 1; real: 0 hi, 2 lo).  Pairs: this CTA's half of it.
+    __host__ __device__ static constexpr int b_off(int p) {
+        return !pair ? p * kTileBytes
+               : REAL ? (p / 2) * kTileBytes
+                      : (p <= 1 ? p * kTileBytes : 2 * kTileBytes + (p - 3) * (kTileBytes / 2));
+    }
 };
 
-template <bool REAL>
+template <bool REAL, int CL = kClNone>
 struct TcSmem {
-    uint8_t stage[TcGeom<REAL>::stages][TcGeom<REAL>::stage_bytes];
-    uint64_t full[TcGeom<REAL>::stages];
-    uint64_t empty[TcGeom<REAL>::stages];
+    uint8_t stage[TcGeom<REAL, CL>::stages][TcGeom<REAL, CL>::stage_bytes];
+    uint64_t full[TcGeom<REAL, CL>::stages];
+    uint64_t empty[TcGeom<REAL, CL>::stages];
     uint64_t acc0_full;
     uint64_t acc0_empty;
     uint64_t drain;
@@ -134,13 +169,20 @@ __device__ __forceinline__ bool kind_runs(int kind, int mode) {
     return mode == QCS_MODE_BF16X3;
 }
 
-template <int KIND>
+template <int KIND, bool PAIR = false>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                     uint32_t acc) {
-    if (KIND == 1)
-        mma_tf32(d, a, b, idesc, acc);
-    else
-        mma_f16(d, a, b, idesc, acc);
+    if constexpr (PAIR) {
+        if (KIND == 1)
+            mma_tf32_pair(d, a, b, idesc, acc);
+        else
+            mma_f16_pair(d, a, b, idesc, acc);
+    } else {
+        if (KIND == 1)
+            mma_tf32(d, a, b, idesc, acc);
+        else
+            mma_f16(d, a, b, idesc, acc);
+    }
 }
 
 // Unit u of a launch: instance g, K range r (of S), tile t (of tiles).
@@ -156,7 +198,7 @@ __device__ __forceinline__ Unit unit_of(int u, int tiles, int S) {
     return x;
 }
 
-template <int KIND, int DRAIN, bool REAL, bool MC>
+template <int KIND, int DRAIN, bool REAL, int CL>
 __global__ void __launch_bounds__(kTcThreads, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap mapA,
                     const __grid_constant__ CUtensorMap mapB,
@@ -164,56 +206,68 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const qcs_gemm_desc_t *__restrict__ desc, int m, int n, int k_pad,
                     float2 alpha, float2 beta, float2 *__restrict__ C, int64_t ldc, int *d_err,
                     int group_m, const TcWork w) {
-    static_assert(!(MC && REAL), "clusters are built for the complex kernel");
+    constexpr bool MC = CL == kClMulticast;
+    constexpr bool PAIR = CL == kClPair;
+    constexpr bool CLU = CL != kClNone;  // clusters of two CTAs
+    static_assert(!(MC && REAL), "multicast clusters are built for the complex kernel");
     // a single GEMM that did not select this kind exits before touching anything
     // (both CTAs of a cluster read the same descriptor)
     if (w.G == 1 && !kind_runs(KIND, desc->mode)) return;
 
-    using Geo = TcGeom<REAL>;
+    using Geo = TcGeom<REAL, CL>;
     constexpr int NST = Geo::stages;
     extern __shared__ uint8_t smem_raw[];
-    TcSmem<REAL> &S = *reinterpret_cast<TcSmem<REAL> *>(
+    TcSmem<REAL, CL> &S = *reinterpret_cast<TcSmem<REAL, CL> *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     volatile int *abort_flag = &S.abort;
+    // PAIR: the even CTA (rank 0) issues the MMAs of the pair
+    const bool leader = !PAIR || cluster_ctarank() == 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
-            mbar_init(&S.full[s], 1);
+            // PAIR: the leader's stage is full once its own bytes landed and
+            // the peer forwarded its own stage's completion
+            mbar_init(&S.full[s], (PAIR && leader) ? 2 : 1);
             mbar_init(&S.empty[s], MC ? 2 : 1);  // MC: the MMAs of both CTAs of the cluster
         }
         mbar_init(&S.acc0_full, 1);
-        mbar_init(&S.acc0_empty, kEpiWarps);
+        mbar_init(&S.acc0_empty, PAIR ? 2 * kEpiWarps : kEpiWarps);  // PAIR: both epilogues
         mbar_init(&S.drain, 1);
         S.abort = 0;
         fence_barrier_init();
         tma_prefetch_desc(&mapA);
         tma_prefetch_desc(&mapB);
-        if (MC) tma_prefetch_desc(&mapB2);
+        if (CLU) tma_prefetch_desc(&mapB2);
     }
     if (warp == 1) {
-        tmem_alloc(&S.tmem_base, kTmemCols);
-        tmem_relinquish();
+        if constexpr (PAIR) {
+            tmem_alloc_pair(&S.tmem_base, kTmemCols);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(&S.tmem_base, kTmemCols);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem_base;
-    // MC: the peer's barriers are initialised before anything reaches them
-    if constexpr (MC) cluster_sync();
+    // clusters: the peer's barriers are initialised before anything reaches them
+    if constexpr (CLU) cluster_sync();
 
     const int tiles_m = (m + kBM - 1) / kBM;
     const int tiles_n = (n + Geo::tile_n - 1) / Geo::tile_n;
-    // MC: units over pairs of tile rows (the host makes tiles_m even), one
-    // per cluster at a time; a cluster's rank-r CTA takes row 2 p + r
-    const int num_tiles = (MC ? tiles_m / 2 : tiles_m) * tiles_n;
+    // clusters: units over pairs of tile rows (the host makes tiles_m even),
+    // one per cluster at a time; a cluster's rank-r CTA takes row 2 p + r
+    const int num_tiles = (CLU ? tiles_m / 2 : tiles_m) * tiles_n;
     const int num_units = w.G * w.S * num_tiles;
-    auto first_unit = [] { return MC ? (int)(blockIdx.x >> 1) : (int)blockIdx.x; };
-    auto unit_step = [] { return MC ? (int)(gridDim.x >> 1) : (int)gridDim.x; };
+    auto first_unit = [] { return CLU ? (int)(blockIdx.x >> 1) : (int)blockIdx.x; };
+    auto unit_step = [] { return CLU ? (int)(gridDim.x >> 1) : (int)gridDim.x; };
     auto coords = [&](int t, int &tm, int &tn) {
-        if constexpr (MC) {
+        if constexpr (CLU) {
             tile_coords(t, tiles_m / 2, tiles_n, group_m / 2 > 0 ? group_m / 2 : 1, tm, tn);
             tm = 2 * tm + (int)cluster_ctarank();
         } else {
@@ -250,7 +304,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     mbar_arrive_expect_tx(&S.full[stage], Geo::stage_bytes);
                     tma_load_3d(S.stage[stage], &mapA, &S.full[stage], kb * kKPerStage, rowA, 0);
-                    if constexpr (MC) {
+                    if constexpr (PAIR) {
+                        // this CTA's half of the B operands (box of mapB: 128 rows x 2
+                        // planes; of mapB2: 64 rows x 2 planes)
+                        const int rk = (int)cluster_ctarank();
+                        uint8_t *bst = S.stage[stage] + Geo::a_bytes;
+                        if constexpr (REAL) {
+                            tma_load_3d(bst, &mapB, &S.full[stage], kb * kKPerStage,
+                                        rowB + rk * kBM, 0);
+                        } else {
+                            tma_load_3d(bst, &mapB, &S.full[stage], kb * kKPerStage, rowB, rk);
+                            tma_load_3d(bst + Geo::b_off(3), &mapB2, &S.full[stage],
+                                        kb * kKPerStage, rowB + rk * (kBN / 2), 3);
+                        }
+                    } else if constexpr (MC) {
                         // this CTA's share of the B box, to both CTAs of the cluster
                         if (cluster_ctarank() == 0)
                             tma_load_3d_mc(S.stage[stage] + Geo::a_bytes, &mapB, &S.full[stage],
@@ -282,24 +349,63 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
             }
         }
+    } else if (warp == 1 && !leader) {
+        // ---------------- PAIR, odd CTA: forward its stages to the leader ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int u = first_unit(); u < num_units && ok; u += unit_step()) {
+                const Unit x = unit_of(u, num_tiles, w.S);
+                if (w.G > 1 && !kind_runs(KIND, desc[x.g].mode)) continue;
+                const int kb1 = kb_begin(x.r + 1);
+                for (int kb = kb_begin(x.r); kb < kb1; ++kb) {
+                    if (!mbar_wait(&S.full[stage], phase, globaltimer_ns() + w.wait_ns,
+                                   abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_cluster(&S.full[stage], 0);
+                    if (++stage == NST) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok && !*abort_flag) raise_abort(S, d_err, kErrTimeoutMma);
+        }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             constexpr uint32_t fmt = (KIND == 0) ? 0u : (KIND == 1 ? 2u : 1u);
-            constexpr uint32_t id = idesc_make(fmt, kBM, 2 * kBN, 0);   // M 128, N 256
-            constexpr uint32_t idh = idesc_make(fmt, kBM, kBN, 0);      // M 128, N 128
-            constexpr uint32_t idhn = idesc_make(fmt, kBM, kBN, 1);     // ... negated A
+            constexpr uint32_t MM = PAIR ? 2 * kBM : kBM;                // M 128 (PAIR: 256)
+            constexpr uint32_t id = idesc_make(fmt, MM, 2 * kBN, 0);     // N 256
+            constexpr uint32_t idh = idesc_make(fmt, MM, kBN, 0);        // N 128
+            constexpr uint32_t idhn = idesc_make(fmt, MM, kBN, 1);       // ... negated A
             const uint32_t a0 = tmem, a1 = tmem + 256;  // [re | im] each
             const uint32_t a1r = a1, a1i = a1 + 128;
             int stage = 0;
             uint32_t phase = 0, e_phase = 0;
             bool pending = false;  // an acc0 drain the epilogue has not yet confirmed
             bool ok = true;
+            // PAIR: the peer's threads arrive on these barriers too
+            auto wait_bar = [&](uint64_t *bar, uint32_t par) -> bool {
+                if constexpr (PAIR)
+                    return mbar_wait_cluster(bar, par, globaltimer_ns() + w.wait_ns, abort_flag);
+                else
+                    return mbar_wait(bar, par, globaltimer_ns() + w.wait_ns, abort_flag);
+            };
+            auto commit = [&](uint64_t *bar) {
+                if constexpr (PAIR)
+                    tc_commit_pair_mc(bar, (uint16_t)0x3);  // on both CTAs' barrier
+                else if constexpr (MC)
+                    tc_commit_mc(bar, (uint16_t)0x3);
+                else
+                    tc_commit(bar);
+            };
             auto wait_drained = [&]() -> bool {
                 if (!pending) return true;
-                if (!mbar_wait(&S.acc0_empty, e_phase, globaltimer_ns() + w.wait_ns,
-                               abort_flag))
-                    return false;
+                if (!wait_bar(&S.acc0_empty, e_phase)) return false;
                 e_phase ^= 1u;
                 pending = false;
                 tc_fence_after();
@@ -310,8 +416,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (w.G > 1 && !kind_runs(KIND, desc[x.g].mode)) continue;
                 const int kb0 = kb_begin(x.r), kb1 = kb_begin(x.r + 1);
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!mbar_wait(&S.full[stage], phase, globaltimer_ns() + w.wait_ns,
-                                   abort_flag)) {
+                    if (!wait_bar(&S.full[stage], phase)) {
                         ok = false;
                         break;
                     }
@@ -326,28 +431,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     // address >> 4), which never carries out for shared memory.
                     // A planes: 0 Ar_hi, 1 Ai_hi, 2 Ar_lo, 3 Ai_lo.  B planes:
                     // 0 -Bi_hi, 1 Br_hi, 2 Bi_hi, 3 Br_lo, 4 Bi_lo; the 256-row
-                    // operand at plane p covers planes p and p + 1.  K step ks
-                    // starts 32 bytes into each 64-byte row.
+                    // operand at plane p covers planes p and p + 1 (PAIR: slot p
+                    // of both CTAs).  K step ks starts 32 bytes into each 64-byte row.
                     // Real kernel: A planes 0 hi, 1 lo; B planes of 256 rows, hi at
-                    // tile offset 0, lo at 2.
+                    // tile offset 0, lo at 2 (PAIR: 128 rows each).
                     const uint64_t dA = sdesc_kmajor_sw64(smem_u32(S.stage[stage]));
                     const uint64_t dB = dA + (Geo::a_bytes >> 4);
 #define A_(ks, p) (dA + (uint64_t)(((p) * kTileBytes + (ks) * 32) >> 4))
-#define B_(ks, p) (dB + (uint64_t)(((p) * kTileBytes + (ks) * 32) >> 4))
+#define B_(ks, p) (dB + (uint64_t)((Geo::b_off(p) + (ks) * 32) >> 4))
                     // correction products: acc1 += lo*hi + hi*lo
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
                         const uint32_t first = (kb == kb0 && ks == 0) ? 0u : 1u;
                         if constexpr (REAL) {
-                            mma<KIND>(a1, A_(ks, 1), B_(ks, 0), id, first);   // A_lo B_hi
-                            mma<KIND>(a1, A_(ks, 0), B_(ks, 2), id, 1u);      // A_hi B_lo
+                            mma<KIND, PAIR>(a1, A_(ks, 1), B_(ks, 0), id, first);   // A_lo B_hi
+                            mma<KIND, PAIR>(a1, A_(ks, 0), B_(ks, 2), id, 1u);      // A_hi B_lo
                         } else {
-                            mma<KIND>(a1, A_(ks, 2), B_(ks, 1), id, first);   // Ar_lo [Br_hi; Bi_hi]
-                            mma<KIND>(a1, A_(ks, 3), B_(ks, 0), id, 1u);      // Ai_lo [-Bi_hi; Br_hi]
-                            mma<KIND>(a1r, A_(ks, 0), B_(ks, 3), idh, 1u);    //  Ar_hi Br_lo
-                            mma<KIND>(a1i, A_(ks, 0), B_(ks, 4), idh, 1u);    //  Ar_hi Bi_lo
-                            mma<KIND>(a1r, A_(ks, 1), B_(ks, 4), idhn, 1u);   // -Ai_hi Bi_lo
-                            mma<KIND>(a1i, A_(ks, 1), B_(ks, 3), idh, 1u);    //  Ai_hi Br_lo
+                            mma<KIND, PAIR>(a1, A_(ks, 2), B_(ks, 1), id, first);   // Ar_lo [Br_hi; Bi_hi]
+                            mma<KIND, PAIR>(a1, A_(ks, 3), B_(ks, 0), id, 1u);      // Ai_lo [-Bi_hi; Br_hi]
+                            mma<KIND, PAIR>(a1r, A_(ks, 0), B_(ks, 3), idh, 1u);    //  Ar_hi Br_lo
+                            mma<KIND, PAIR>(a1i, A_(ks, 0), B_(ks, 4), idh, 1u);    //  Ar_hi Bi_lo
+                            mma<KIND, PAIR>(a1r, A_(ks, 1), B_(ks, 4), idhn, 1u);   // -Ai_hi Bi_lo
+                            mma<KIND, PAIR>(a1i, A_(ks, 1), B_(ks, 3), idh, 1u);    //  Ai_hi Br_lo
                         }
                     }
                     // hi*hi products: a fresh acc0 every DRAIN stages, once the
@@ -362,21 +467,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     for (int ks = 0; ks < 2; ++ks) {
                         const uint32_t first = (ks == 0 && group_start) ? 0u : 1u;
                         if constexpr (REAL) {
-                            mma<KIND>(a0, A_(ks, 0), B_(ks, 0), id, first);   // A_hi B_hi
+                            mma<KIND, PAIR>(a0, A_(ks, 0), B_(ks, 0), id, first);   // A_hi B_hi
                         } else {
-                            mma<KIND>(a0, A_(ks, 0), B_(ks, 1), id, first);   // Ar_hi [Br_hi; Bi_hi]
-                            mma<KIND>(a0, A_(ks, 1), B_(ks, 0), id, 1u);      // Ai_hi [-Bi_hi; Br_hi]
+                            mma<KIND, PAIR>(a0, A_(ks, 0), B_(ks, 1), id, first);   // Ar_hi [Br_hi; Bi_hi]
+                            mma<KIND, PAIR>(a0, A_(ks, 1), B_(ks, 0), id, 1u);      // Ai_hi [-Bi_hi; Br_hi]
                         }
                     }
 #undef A_
 #undef B_
-                    // frees the smem stage when these MMAs finish (MC: in both CTAs)
-                    if constexpr (MC)
-                        tc_commit_mc(&S.empty[stage], (uint16_t)0x3);
-                    else
-                        tc_commit(&S.empty[stage]);
+                    // frees the smem stage when these MMAs finish (clusters: in both CTAs)
+                    commit(&S.empty[stage]);
                     if (group_end) {
-                        tc_commit(&S.acc0_full);  // acc0 (and, on a tile's last stage, acc1) ready
+                        // acc0 (and, on a tile's last stage, acc1) ready (MC: this
+                        // CTA's only; PAIR: in both CTAs)
+                        if constexpr (PAIR)
+                            commit(&S.acc0_full);
+                        else
+                            tc_commit(&S.acc0_full);
                         pending = true;
                     }
                     if (++stage == NST) {
@@ -388,7 +495,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (!ok && !*abort_flag) raise_abort(S, d_err, kErrTimeoutMma);
             // Wait (bounded) until every MMA this thread issued has finished,
             // so tensor memory is idle before it is released.
-            tc_commit(&S.drain);
+            if constexpr (PAIR)
+                tc_commit_pair(&S.drain);
+            else
+                tc_commit(&S.drain);
             volatile int never = 0;
             (void)mbar_wait(&S.drain, 0, globaltimer_ns() + w.wait_ns, &never);
         }
@@ -458,7 +568,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&S.acc0_empty);
+                if (lane == 0) {
+                    if (leader)
+                        mbar_arrive(&S.acc0_empty);
+                    else
+                        mbar_arrive_cluster(&S.acc0_empty, 0);  // PAIR: the leader's barrier
+                }
             }
             if (!ok) break;
             const int row = tm * kBM + q * 32 + lane;
@@ -537,13 +652,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     tc_fence_before();
     __syncthreads();
-    // MC: neither CTA leaves while the other may still write into its shared
-    // memory or arrive on its barriers
-    if constexpr (MC) cluster_sync();
+    // clusters: neither CTA leaves while the other may still write into its
+    // shared memory or tensor memory, or arrive on its barriers
+    if constexpr (CLU) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
         __syncwarp();
-        tmem_dealloc(tmem, kTmemCols);
+        if constexpr (PAIR)
+            tmem_dealloc_pair(tmem, kTmemCols);
+        else
+            tmem_dealloc(tmem, kTmemCols);
     }
 }
 
@@ -603,70 +721,96 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// mcB not NULL (complex kernel, an even number of tile rows): clusters of
-// two CTAs sharing each B box, mcB[0] covering B planes 0-2 and mcB[1]
-// planes 3-4 of every box (mapB, all five planes, otherwise).
+// A launch in clusters of two CTAs (CL = kClMulticast or kClPair): one
+// cluster per pair of tile rows at a time, as many clusters as fit at once.
+template <int KIND, int DRAIN, bool REAL, int CL>
+cudaError_t launch_clusters(const CUtensorMap &mapA, const CUtensorMap &mapB,
+                            const CUtensorMap &mapB2, const qcs_gemm_desc_t *desc, int64_t m,
+                            int64_t n, int64_t k_pad, float2 alpha, float2 beta, float2 *C,
+                            int64_t ldc, int *d_err, int num_sms, int gm, int64_t units,
+                            const TcWork &w, cudaStream_t s) {
+    auto kern = cgemm_tc_kernel<KIND, DRAIN, REAL, CL>;
+    const size_t smem = sizeof(TcSmem<REAL, CL>) + 1024;
+    static int max_clusters = 0;  // clusters of two that fit at once, measured once
+    if (max_clusters == 0) {
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t q = {};
+        cudaLaunchAttribute qa[1];
+        qa[0].id = cudaLaunchAttributeClusterDimension;
+        qa[0].val.clusterDim.x = 2;
+        qa[0].val.clusterDim.y = 1;
+        qa[0].val.clusterDim.z = 1;
+        q.gridDim = dim3((unsigned)(num_sms & ~1));
+        q.blockDim = dim3(kTcThreads);
+        q.dynamicSmemBytes = smem;
+        q.attrs = qa;
+        q.numAttrs = 1;
+        e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &q);
+        if (e != cudaSuccess || max_clusters < 1) {
+            max_clusters = 0;
+            cudaGetLastError();
+            return cudaErrorNotSupported;
+        }
+    }
+    const int64_t pair_units = units / 2;
+    const int clusters = (int)std::min<int64_t>(pair_units, max_clusters);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(2 * clusters));
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, mapA, mapB, mapB2, desc, (int)m, (int)n, (int)k_pad,
+                              alpha, beta, C, ldc, d_err, gm, w);
+}
+
+// With an even number of tile rows: pairB not NULL runs CTA pairs (complex:
+// pairB[0] boxes of 128 rows x 2 planes, pairB[1] 64 rows x 2 planes; real:
+// pairB[0] 128 rows x 2 planes; the default drain only), else mcB not NULL
+// (complex kernel) clusters of two CTAs sharing each B box, mcB[0] covering
+// B planes 0-2 and mcB[1] planes 3-4 of every box.  Otherwise one CTA per
+// tile with mapB (all planes of a box).
 template <int KIND, int DRAIN, bool REAL>
 cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
-                        const CUtensorMap *mapB, const CUtensorMap *mcB, int64_t m, int64_t n,
-                        int64_t k_pad, float2 alpha, float2 beta, float2 *C, int64_t ldc,
-                        int *d_err, int num_sms, int group_m, const TcWork &w, cudaStream_t s) {
+                        const CUtensorMap *mapB, const CUtensorMap *mcB,
+                        const CUtensorMap *pairB, int64_t m, int64_t n, int64_t k_pad,
+                        float2 alpha, float2 beta, float2 *C, int64_t ldc, int *d_err,
+                        int num_sms, int group_m, const TcWork &w, cudaStream_t s) {
     const size_t smem = sizeof(TcSmem<REAL>) + 1024;
     constexpr int tn = TcGeom<REAL>::tile_n;
     const int64_t tiles_m = (m + kBM - 1) / kBM;
     const int64_t units = tiles_m * ((n + tn - 1) / tn) * w.G * w.S;
     if (units == 0 || k_pad == 0) return cudaSuccess;
     const int gm = group_m < 1 ? 1 : group_m;
-    if (!REAL && mcB && tiles_m % 2 == 0) {
-        auto kern = cgemm_tc_kernel<KIND, DRAIN, REAL, !REAL>;
-        static int max_clusters = 0;  // clusters of two that fit at once, measured once
-        if (max_clusters == 0) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e != cudaSuccess) return e;
-            cudaLaunchConfig_t q = {};
-            cudaLaunchAttribute qa[1];
-            qa[0].id = cudaLaunchAttributeClusterDimension;
-            qa[0].val.clusterDim.x = 2;
-            qa[0].val.clusterDim.y = 1;
-            qa[0].val.clusterDim.z = 1;
-            q.gridDim = dim3((unsigned)(num_sms & ~1));
-            q.blockDim = dim3(kTcThreads);
-            q.dynamicSmemBytes = smem;
-            q.attrs = qa;
-            q.numAttrs = 1;
-            e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &q);
-            if (e != cudaSuccess || max_clusters < 1) {
-                cudaGetLastError();
-                return cudaErrorNotSupported;
-            }
-        }
-        const int64_t pair_units = units / 2;
-        const int clusters = (int)std::min<int64_t>(pair_units, max_clusters);
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3((unsigned)(2 * clusters));
-        cfg.blockDim = dim3(kTcThreads);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = s;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, kern, *mapA, mcB[0], mcB[1], desc, (int)m, (int)n,
-                                  (int)k_pad, alpha, beta, C, ldc, d_err, gm, w);
+    if constexpr (DRAIN == 4) {
+        if (pairB && tiles_m % 2 == 0)
+            return launch_clusters<KIND, DRAIN, REAL, kClPair>(
+                *mapA, pairB[0], REAL ? pairB[0] : pairB[1], desc, m, n, k_pad, alpha, beta, C,
+                ldc, d_err, num_sms, gm, units, w, s);
+    }
+    if constexpr (!REAL) {
+        if (mcB && tiles_m % 2 == 0)
+            return launch_clusters<KIND, DRAIN, REAL, kClMulticast>(
+                *mapA, mcB[0], mcB[1], desc, m, n, k_pad, alpha, beta, C, ldc, d_err, num_sms,
+                gm, units, w, s);
     }
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel<KIND, DRAIN, REAL, false>,
+        cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel<KIND, DRAIN, REAL, kClNone>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     const int grid = static_cast<int>(units < num_sms ? units : num_sms);
-    cgemm_tc_kernel<KIND, DRAIN, REAL, false><<<grid, kTcThreads, smem, s>>>(
+    cgemm_tc_kernel<KIND, DRAIN, REAL, kClNone><<<grid, kTcThreads, smem, s>>>(
         *mapA, *mapB, *mapB, desc, (int)m, (int)n, (int)k_pad, alpha, beta, C, ldc, d_err, gm, w);
     return cudaGetLastError();
 }
@@ -675,34 +819,36 @@ cudaError_t launch_kind(const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
 // 16-bit kinds, 16 for TF32).
 template <int KIND, bool REAL>
 cudaError_t launch_drain(int drain, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
-                         const CUtensorMap *mapB, const CUtensorMap *mcB, int64_t m, int64_t n,
+                         const CUtensorMap *mapB, const CUtensorMap *mcB,
+                         const CUtensorMap *pairB, int64_t m, int64_t n,
                          int64_t k_pad, float2 alpha, float2 beta, float2 *C, int64_t ldc,
                          int *d_err, int num_sms, int group_m, const TcWork &w, cudaStream_t s) {
     if (drain >= 4)
-        return launch_kind<KIND, 4, REAL>(desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta, C,
+        return launch_kind<KIND, 4, REAL>(desc, mapA, mapB, mcB, pairB, m, n, k_pad, alpha, beta, C,
                                           ldc, d_err, num_sms, group_m, w, s);
     if (drain == 2)
-        return launch_kind<KIND, 2, REAL>(desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta, C,
+        return launch_kind<KIND, 2, REAL>(desc, mapA, mapB, mcB, pairB, m, n, k_pad, alpha, beta, C,
                                           ldc, d_err, num_sms, group_m, w, s);
-    return launch_kind<KIND, 1, REAL>(desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta, C, ldc,
+    return launch_kind<KIND, 1, REAL>(desc, mapA, mapB, mcB, pairB, m, n, k_pad, alpha, beta, C, ldc,
                                       d_err, num_sms, group_m, w, s);
 }
 
 template <bool REAL>
 cudaError_t launch_any(int kind, int drain, const qcs_gemm_desc_t *desc, const CUtensorMap *mapA,
-                       const CUtensorMap *mapB, const CUtensorMap *mcB, int64_t m, int64_t n,
+                       const CUtensorMap *mapB, const CUtensorMap *mcB,
+                       const CUtensorMap *pairB, int64_t m, int64_t n,
                        int64_t k_pad, float2 alpha, float2 beta, float2 *C, int64_t ldc,
                        int *d_err, int num_sms, int group_m, cudaStream_t s, const TcWork &w) {
     if (w.G < 1 || w.S < 1 || (w.S > 1 && !w.P)) return cudaErrorInvalidValue;
     switch (kind) {
         case 0:
-            return launch_drain<0, REAL>(drain, desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta,
+            return launch_drain<0, REAL>(drain, desc, mapA, mapB, mcB, pairB, m, n, k_pad, alpha, beta,
                                          C, ldc, d_err, num_sms, group_m, w, s);
         case 1:
-            return launch_drain<1, REAL>(drain, desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta,
+            return launch_drain<1, REAL>(drain, desc, mapA, mapB, mcB, pairB, m, n, k_pad, alpha, beta,
                                          C, ldc, d_err, num_sms, group_m, w, s);
         default:
-            return launch_drain<2, REAL>(drain, desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta,
+            return launch_drain<2, REAL>(drain, desc, mapA, mapB, mcB, pairB, m, n, k_pad, alpha, beta,
                                          C, ldc, d_err, num_sms, group_m, w, s);
     }
 }
@@ -713,8 +859,9 @@ cudaError_t launch_cgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
                             const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
                             int64_t n, int64_t k_pad, float2 alpha, float2 beta, float2 *C,
                             int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s,
-                            const TcWork &w, const CUtensorMap *mcB) {
-    return launch_any<false>(kind, drain, desc, mapA, mapB, mcB, m, n, k_pad, alpha, beta, C,
+                            const TcWork &w, const CUtensorMap *mcB,
+                            const CUtensorMap *pairB) {
+    return launch_any<false>(kind, drain, desc, mapA, mapB, mcB, pairB, m, n, k_pad, alpha, beta, C,
                              ldc, d_err, num_sms, group_m, s, w);
 }
 
@@ -722,8 +869,8 @@ cudaError_t launch_sgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
                             const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
                             int64_t n, int64_t k_pad, float alpha, float beta, float *C,
                             int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s,
-                            const TcWork &w) {
-    return launch_any<true>(kind, drain, desc, mapA, mapB, nullptr, m, n, k_pad,
+                            const TcWork &w, const CUtensorMap *pairB) {
+    return launch_any<true>(kind, drain, desc, mapA, mapB, nullptr, pairB, m, n, k_pad,
                             make_float2(alpha, 0.f),
                             make_float2(beta, 0.f), reinterpret_cast<float2 *>(C), ldc, d_err,
                             num_sms, group_m, s, w);

@@ -98,6 +98,7 @@ struct qcs_handle_s {
     int fused_split = 0;             // TF32X: split inside the tensor-core kernel's staging
     int tree_levels = 1;             // tree executor: small FP32 steps of a level in one launch
     int tc_multicast = 0;            // complex tensor-core kernel in clusters of two sharing B
+    int tc_pairs = 0;                // tensor-core kernels as CTA pairs (cta_group::2)
     size_t group_budget = size_t(32) << 30;  // tree executor: bytes a grouped GPU-filling step may hold
     uint64_t wait_ns = qcs::kWaitBudgetNs;  // bound of the tensor-core kernels' device waits
     int debug_stall = 0;             // test hook: the TMA producer issues no loads
@@ -411,14 +412,18 @@ cudaError_t launch_cgemm_tc_fused(EncodeTiledFn encode, const qcs_gemm_desc_t *d
 // FP16X, FP16X_SCALED), 1 TF32, 2 BF16; the kernel returns at once unless
 // desc->mode belongs to its kind (per instance when w.G > 1).
 // ``drain``: pipeline stages per round-to-nearest drain of the hi*hi
-// accumulator (1, 2 or 4).  mcB not NULL: clusters of two CTAs share the
-// B boxes (mcB[0]: planes 0-2 of each box, mcB[1]: planes 3-4) when the
-// output has an even number of tile rows; otherwise mapB (all five planes).
+// accumulator (1, 2 or 4).  When the output has an even number of tile
+// rows: pairB not NULL (and drain 4) runs CTA pairs on M = 256 tiles
+// (pairB[0]: the B planes in boxes of 128 rows x 2 planes, pairB[1]: 64 rows
+// x 2 planes); else mcB not NULL runs clusters of two CTAs sharing the B
+// boxes (mcB[0]: planes 0-2 of each box, mcB[1]: planes 3-4).  Otherwise
+// mapB (all five planes of a box).
 cudaError_t launch_cgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
                             const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
                             int64_t n, int64_t k_pad, float2 alpha, float2 beta, float2 *C,
                             int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s,
-                            const TcWork &w = TcWork{}, const CUtensorMap *mcB = nullptr);
+                            const TcWork &w = TcWork{}, const CUtensorMap *mcB = nullptr,
+                            const CUtensorMap *pairB = nullptr);
 // C = alpha sum_r P_r + beta C after a split-K launch (nothing when w.S == 1),
 // for the instances whose descriptor did not select FP32.
 cudaError_t launch_tc_reduce(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, float2 alpha,
@@ -463,12 +468,14 @@ cudaError_t launch_sgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
                               cudaStream_t s);
 // The tensor-core kernel on real planes: A two planes (hi, lo) read in
 // 128-row boxes, B two planes in 256-row boxes, tiles of 128 x 256 floats of
-// C; w.P (when w.S > 1) holds S G m n floats.
+// C; w.P (when w.S > 1) holds S G m n floats.  pairB not NULL (the B planes
+// in 128-row boxes; drain 4, an even number of tile rows): CTA pairs on
+// 256 x 256 tiles.
 cudaError_t launch_sgemm_tc(int kind, int drain, const qcs_gemm_desc_t *desc,
                             const CUtensorMap *mapA, const CUtensorMap *mapB, int64_t m,
                             int64_t n, int64_t k_pad, float alpha, float beta, float *C,
                             int64_t ldc, int *d_err, int num_sms, int group_m, cudaStream_t s,
-                            const TcWork &w = TcWork{});
+                            const TcWork &w = TcWork{}, const CUtensorMap *pairB = nullptr);
 cudaError_t launch_tc_reduce_real(const qcs_gemm_desc_t *desc, int64_t m, int64_t n, float alpha,
                                   float beta, float *C, int64_t ldc, int num_sms, const TcWork &w,
                                   cudaStream_t s);
