@@ -2452,6 +2452,94 @@ __global__ void __launch_bounds__(256) cgemm_2x2_cols_kernel(
     }
 }
 
+// (m, 2, 2) with op(A) = A stored m x 2 and C m x 2, both with an even
+// leading dimension and 16-byte aligned (the (2^N, 2, 2) shape of Section
+// 5.1.2): a thread per pair of rows, one 16-byte load per column of A and
+// one 16-byte store per column of C, four pairs in flight.  The arithmetic
+// per output element is that of cgemm_skinny_rows_kernel (same FMA chain).
+// An odd last row is done by the first thread of the grid.
+__global__ void __launch_bounds__(256) cgemm_nx2x2_rows_kernel(
+    const qcs_gemm_desc_t *__restrict__ desc, int opB, const float4 *__restrict__ A, int64_t lda2,
+    const float2 *__restrict__ B, int64_t ldb, float4 *__restrict__ C, int64_t ldc2, int64_t m,
+    float2 alpha, float2 beta, GemmBatch bt) {
+    if (desc && desc->mode != QCS_MODE_FP32) return;
+    A += blockIdx.y * (bt.sA >> 1);
+    B += blockIdx.y * bt.sB;
+    C += blockIdx.y * (bt.sC >> 1);
+    float2 b[2][2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) b[l][j] = ld_op(B, opB, l, j, ldb);
+    const bool use_beta = (beta.x != 0.f) || (beta.y != 0.f);
+    auto dot2 = [&](float2 a0, float2 a1, int j) {
+        float sr = 0.f, si = 0.f;
+        sr = fmaf(a0.x, b[0][j].x, sr);
+        sr = fmaf(-a0.y, b[0][j].y, sr);
+        si = fmaf(a0.x, b[0][j].y, si);
+        si = fmaf(a0.y, b[0][j].x, si);
+        sr = fmaf(a1.x, b[1][j].x, sr);
+        sr = fmaf(-a1.y, b[1][j].y, sr);
+        si = fmaf(a1.x, b[1][j].y, si);
+        si = fmaf(a1.y, b[1][j].x, si);
+        return make_float2(alpha.x * sr - alpha.y * si, alpha.x * si + alpha.y * sr);
+    };
+    auto add_beta = [&](float2 o, float2 c) {
+        o.x += beta.x * c.x - beta.y * c.y;
+        o.y += beta.x * c.y + beta.y * c.x;
+        return o;
+    };
+    const int64_t pairs = m >> 1;
+    constexpr int U = 4;
+    const int64_t S = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p0 < pairs; p0 += U * S) {
+        float4 a0[U], a1[U], c0[U], c1[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t p = p0 + u * S;
+            if (p < pairs) {
+                a0[u] = __ldcs(A + p);
+                a1[u] = __ldcs(A + lda2 + p);
+                if (use_beta) {
+                    c0[u] = C[p];
+                    c1[u] = C[ldc2 + p];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t p = p0 + u * S;
+            if (p >= pairs) continue;
+            // rows 2p (x, y of each float4) and 2p + 1 (z, w)
+            const float2 r0a0 = make_float2(a0[u].x, a0[u].y), r0a1 = make_float2(a1[u].x, a1[u].y);
+            const float2 r1a0 = make_float2(a0[u].z, a0[u].w), r1a1 = make_float2(a1[u].z, a1[u].w);
+            float2 o00 = dot2(r0a0, r0a1, 0), o10 = dot2(r1a0, r1a1, 0);
+            float2 o01 = dot2(r0a0, r0a1, 1), o11 = dot2(r1a0, r1a1, 1);
+            if (use_beta) {
+                o00 = add_beta(o00, make_float2(c0[u].x, c0[u].y));
+                o10 = add_beta(o10, make_float2(c0[u].z, c0[u].w));
+                o01 = add_beta(o01, make_float2(c1[u].x, c1[u].y));
+                o11 = add_beta(o11, make_float2(c1[u].z, c1[u].w));
+            }
+            __stcs(C + p, make_float4(o00.x, o00.y, o10.x, o10.y));
+            __stcs(C + ldc2 + p, make_float4(o01.x, o01.y, o11.x, o11.y));
+        }
+    }
+    if ((m & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const float2 *Af = reinterpret_cast<const float2 *>(A);
+        float2 *Cf = reinterpret_cast<float2 *>(C);
+        const int64_t i = m - 1;
+        const float2 ra0 = Af[i], ra1 = Af[2 * lda2 + i];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            float2 o = dot2(ra0, ra1, j);
+            float2 *dst = Cf + i + j * (2 * ldc2);
+            if (use_beta) o = add_beta(o, *dst);
+            *dst = o;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) cgemm_skinny_cols_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int opA, int opB, int64_t m, int64_t n, int k,
     int lg_m2, float2 alpha, const float2 *__restrict__ A, int64_t lda, const float2 *__restrict__ B,
@@ -2695,7 +2783,15 @@ cudaError_t launch_cgemm_simt(const qcs_gemm_desc_t *desc, int opA, int opB, int
         return cudaGetLastError();
     }
     if (k <= 16 && (m <= 16 || n <= 16)) {
-        if (m >= n) {  // then n <= 16: a thread per row
+        if (m >= n && n == 2 && k == 2 && opA == QCS_OP_N && lda % 2 == 0 && ldc % 2 == 0 &&
+            ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(C)) & 15u) == 0 &&
+            (bt.sA % 2) == 0 && (bt.sC % 2) == 0) {
+            const int64_t blocks = (m / 2 + 4 * 256 - 1) / (4 * 256);
+            const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, 65535)), G);
+            cgemm_nx2x2_rows_kernel<<<grid, 256, 0, s>>>(
+                desc, opB, reinterpret_cast<const float4 *>(A), lda / 2, B, ldb,
+                reinterpret_cast<float4 *>(C), ldc / 2, m, alpha, beta, bt);
+        } else if (m >= n) {  // then n <= 16: a thread per row
             const int64_t blocks = (m + 255) / 256;
             const dim3 grid((unsigned)(blocks < 65536 ? blocks : 65536), G);
             const int kk = (int)k;

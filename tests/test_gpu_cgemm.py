@@ -311,6 +311,27 @@ def test_cgemm_fp32_two_by_n_columns(h, n, opA):
     assert np.all(np.abs(got - ref) <= bound + 1e-30)
 
 
+@pytest.mark.parametrize("m", [2, 3, 7, 5000, 65539])
+@pytest.mark.parametrize("opB", [0, 1, 2])
+@pytest.mark.parametrize("pad", [0, 1])
+def test_cgemm_fp32_n_by_two_rows(h, m, opB, pad):
+    """The (2^N, 2, 2) shape of Section 5.1.2: A and C stored m x 2 with an
+    even leading dimension (the paired-row kernel, odd m included: its last
+    row is done alone) or an odd one (the per-row kernel), beta != 0."""
+    n = k = 2
+    ld = m + (m & 1)                       # even
+    lda = m + 1 - (m & 1) if pad else ld   # odd with pad
+    A = qi.cgemm_operand(m, k, 3, seed=(m, opB, 1), ld=lda)
+    B = _operands(m, n, k, 0, opB, 3, seed=(m, opB, 2))[1]
+    C0 = qi.cgemm_operand(m, n, 0, seed=(m, 6), ld=ld)
+    alpha, beta = 0.5 + 0.25j, -1.0 + 0.5j
+    got, _ = _run(h, "fp32", m, n, k, 0, opB, A, B, alpha, beta, C0)
+    ref = oracle.cgemm(0, opB, m, n, k, alpha, A, B, beta, C0)
+    bound = (2 * k + 8) * 2.0 ** -24 * (abs(alpha) * 2 * abs_bound(A, B, 0, opB, m, k, n)
+                                        + abs(beta) * 2 * np.abs(C0[:m, :n]))
+    assert np.all(np.abs(got - ref) <= bound + 1e-30)
+
+
 # ---------------------------------------------------------------------------
 # K ranges as separate work units (qcs_set_tc_splits)
 # ---------------------------------------------------------------------------
