@@ -65,7 +65,8 @@ def parse(argv=None):
                    help="host processes that cost the seeded orders")
     p.add_argument("--sweep-sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192, 16384])
     p.add_argument("--profile", choices=["slice", "slice_seed2", "gather", "gemm", "sgemm",
-                                         "scaling", "contraction", "precision"],
+                                         "scaling", "contraction", "precision",
+                                         "differentiation"],
                    default=None,
                    help="run one workload for an ncu capture (NVTX range 'measure') and exit: "
                         "'slice' one group of 16 slices of the 30-qubit network in the cheapest "
@@ -75,13 +76,16 @@ def parse(argv=None):
                         "ten qcs_cgemm calls of --gemm-shape in --mode, 'sgemm' ten qcs_sgemm "
                         "calls of --gemm-shape in --mode, 'scaling' the exponent spread of the "
                         "large GEMM operands of the 5x6 depth-14 network (order of seed 2) under "
-                        "one scale per matrix, per row of op(A) and per column of op(B)")
+                        "one scale per matrix, per row of op(A) and per column of op(B); "
+                        "'differentiation' one forward + backward of the differentiated "
+                        "workload in its cheapest order (--mode auto or fp32)")
     p.add_argument("--complex-products", type=int, choices=[3, 4], default=4,
                    help="with --profile gemm: real products per complex product (3: Gauss)")
     p.add_argument("--gemm-shape", type=int, nargs=3, default=[2048, 8192, 32],
                    metavar=("M", "N", "K"), help="the GEMM of --profile gemm")
     p.add_argument("--tuning-file", default=None,
-                   help="with --profile slice*: load the size-rule tuning table from this JSON "
+                   help="with --profile slice*|contraction|precision|differentiation: load the "
+                        "size-rule tuning table from this JSON "
                         "file if it exists, else measure it and write it there (a run under ncu "
                         "would measure distorted times: ncu slows every launch)")
     p.add_argument("--no-absorb", action="store_true",
@@ -398,6 +402,60 @@ def precision_network(args, tn, qi):
     return labels, rows, circ, bits, nets, which, order, seed_used
 
 
+def differentiation_network(args, tn, qi):
+    """The differentiated workload (4x5 grid, depth 12, free fSim parameters,
+    256 bitstrings) and its two contraction orders: the greedy order of seed 2
+    (4.2e11 flops per slice: the adjoint GEMMs are large enough for the tensor
+    cores) and the cheapest of --greedy-trials orders over the network with and
+    without its frozen single-qubit gates absorbed."""
+    import numpy as np
+
+    c4 = qi.random_grid_circuit(4, 5, 12, seed=0, theta=None, phi=None, param_seed=3)
+    b4 = qi.random_bitstrings(20, 256, seed=1)
+    p0s = np.array([g.params for g in c4.gates if g.name == "fsim"])
+    net4_full = tn.circuit_network(c4, None)
+    # the parametric fSim leaves stay as they are
+    nets4 = [net4_full] + ([] if args.no_absorb else
+                           [tn.absorb_single_qubit_gates(net4_full, frozen_gates=c4.fsim_indices())])
+    o_s2 = tn.greedy_order(net4_full, seed=2)
+    orders = {"seed2": (net4_full, o_s2, tn.choose_slices(net4_full, o_s2, n_labels=2))}
+    w4, o_b, sl_b, _ = tn.cheapest_network_order(nets4, range(args.greedy_trials), n_slices=2,
+                                                 workers=args.greedy_workers)
+    orders["cheapest"] = (nets4[w4], o_b, sl_b)
+    return c4, b4, p0s, orders, w4
+
+
+def differentiation_setup(q, tn, torch, dev, hd, c4, b4, p0s, net_order, mode, rule,
+                          tuning_file=None):
+    """Plan, compiled plan, parameters and the forward + backward closure of
+    the differentiated workload in one order (the loss is the sum of
+    log|a|^2 over the bitstrings).  Under the tuned rule the size-rule table
+    is measured, or loaded from ``tuning_file`` when that file exists (and
+    written there otherwise)."""
+    net4, order, sliced = net_order
+    plan = tn.build_plan(net4, order, sliced, mode=q.MODE_BY_NAME[mode], outputs=b4)
+    cp = tn.CompiledPlan(plan, device=dev, leaf_data=[])
+    if rule == q.SIZE_RULE_TUNED:
+        if tuning_file and os.path.exists(tuning_file):
+            with open(tuning_file) as f:
+                hd.set_tuning(json.load(f))
+        else:
+            cp.autotune(hd, backward=True, reps=2)
+            if tuning_file:
+                with open(tuning_file, "w") as f:
+                    json.dump(hd.tuning(), f)
+    params = torch.tensor(p0s, dtype=torch.float32, device=dev, requires_grad=True)
+
+    def fwd_bwd():
+        params.grad = None
+        leaves = tn.torch_leaves(plan.net, c4, params, device=dev)
+        amps = tn.contract(cp, hd, leaves)
+        loss = torch.log(amps.abs() ** 2).sum()
+        loss.backward()
+        return loss
+    return plan, cp, params, fwd_bwd
+
+
 def profile_run(args):
     """One workload between torch.cuda.nvtx range 'measure' (after one
     untimed run), for ``ncu --nvtx --nvtx-include "measure/"``; prints a
@@ -411,7 +469,19 @@ def profile_run(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if args.profile in ("slice", "slice_seed2", "contraction", "precision"):
+    if args.profile == "differentiation":
+        c4, b4, p0s, orders, w4 = differentiation_network(args, tn, qi)
+        rule = q.SIZE_RULE_PAPER if args.mode == "fp32" else q.SIZE_RULE_TUNED
+        h = q.Handle(tol=args.tol, size_rule=rule)
+        plan, cp, params, run = differentiation_setup(q, tn, torch, dev, h, c4, b4, p0s,
+                                                      orders["cheapest"], args.mode, rule,
+                                                      args.tuning_file)
+        h.set_instance_batch(plan.n_instances)
+        cp.use_graphs(h)
+        what = ("forward + backward of the differentiated 4x5 depth-12 workload (256 "
+                "bitstrings, 4 slices) in the cheapest of %d orders, %s, two CUDA-graph "
+                "replays" % (args.greedy_trials, args.mode))
+    elif args.profile in ("slice", "slice_seed2", "contraction", "precision"):
         circ = qi.random_grid_circuit(5, 6, 14, seed=0)
         bits = qi.random_bitstrings(30, 1, seed=1)
         if args.profile == "contraction":
@@ -489,13 +559,17 @@ def profile_run(args):
     run()
     torch.cuda.synchronize()
     with torch.cuda.nvtx.range("measure"):
+        t0 = time.perf_counter()
         e0.record()
         run()
         e1.record()
         torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
     h.sync()
-    print(json.dumps({"profile": args.profile, "workload": what, "ms": e0.elapsed_time(e1)}),
-          flush=True)
+    print(json.dumps({"profile": args.profile, "workload": what, "ms": e0.elapsed_time(e1),
+                      "wall_ms": wall * 1e3}), flush=True)
+    if args.profile == "differentiation":
+        cp.graphed.close()
     h.close()
 
 
@@ -1414,41 +1488,16 @@ def tree_legs(args, q, torch, dev, rank, world=1, dist=None):
             q, torch, dev, out0.cpu().numpy()[:, 0], ref)["fidelity"]
     h.close()
     # differentiation: 4x5 grid, depth 12, free fSim parameters, 256 bitstrings
-    c4 = qi.random_grid_circuit(4, 5, 12, seed=0, theta=None, phi=None, param_seed=3)
-    b4 = qi.random_bitstrings(20, 256, seed=1)
-    p0s = np.array([g.params for g in c4.gates if g.name == "fsim"])
+    c4, b4, p0s, orders, w4 = differentiation_network(args, tn, qi)
     diff = {}
-    net4_full = tn.circuit_network(c4, None)
-    # the parametric fSim leaves stay as they are
-    nets4 = [net4_full] + ([] if args.no_absorb else
-                           [tn.absorb_single_qubit_gates(net4_full, frozen_gates=c4.fsim_indices())])
-    # the greedy order of seed 2 (4.2e11 flops per slice: the adjoint GEMMs are
-    # large enough for the tensor cores) and the cheapest of --greedy-trials orders
-    o_s2 = tn.greedy_order(net4_full, seed=2)
-    orders = {"seed2": (net4_full, o_s2, tn.choose_slices(net4_full, o_s2, n_labels=2))}
-    w4, o_b, sl_b, _ = tn.cheapest_network_order(nets4, range(args.greedy_trials), n_slices=2,
-                                                 workers=args.greedy_workers)
-    orders["cheapest"] = (nets4[w4], o_b, sl_b)
     for mode, rule, which in (("auto", q.SIZE_RULE_TUNED, "seed2"),
                               ("fp32", q.SIZE_RULE_PAPER, "seed2"),
                               ("auto_cheapest_order", q.SIZE_RULE_TUNED, "cheapest"),
                               ("fp32_cheapest_order", q.SIZE_RULE_PAPER, "cheapest")):
         hd = q.Handle(tol=args.tol, size_rule=rule)
-        net4, order, sliced = orders[which]
-        plan = tn.build_plan(net4, order, sliced, mode=q.MODE_BY_NAME[mode.split("_")[0]],
-                             outputs=b4)
-        cp = tn.CompiledPlan(plan, device=dev, leaf_data=[])
-        if rule == q.SIZE_RULE_TUNED:
-            cp.autotune(hd, backward=True, reps=2)
-        params = torch.tensor(p0s, dtype=torch.float32, device=dev, requires_grad=True)
-
-        def fwd_bwd():
-            params.grad = None
-            leaves = tn.torch_leaves(plan.net, c4, params, device=dev)
-            amps = tn.contract(cp, hd, leaves)
-            loss = torch.log(amps.abs() ** 2).sum()
-            loss.backward()
-            return loss
+        plan, cp, params, fwd_bwd = differentiation_setup(q, tn, torch, dev, hd, c4, b4, p0s,
+                                                          orders[which], mode.split("_")[0],
+                                                          rule)
 
         def timed_fwd_bwd():
             fwd_bwd()
