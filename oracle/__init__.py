@@ -20,6 +20,10 @@ What it computes, each following a passage of the paper (Ootomo et al. 2023):
 * ``tcec_cgemm``: the emulated product of Eq. 1 with the complex expansion of
   Section 3, evaluated exactly in FP64; ``tcec_cgemm_3m`` the same with
   Gauss's three real products (a variant beyond the paper).
+* ``rowcol_stats`` / ``select_rowcol`` / ``tcec_cgemm_rowcol``: Section 4.1's
+  per-matrix scaling applied to every row of op(A) and column of op(B) (a
+  variant beyond the paper), built from ``exp_stats`` / ``stats_summary`` per
+  line and ``tcec_cgemm`` of the scaled operands.
 * ``statevector`` / ``circuit_tn`` / ``amplitude``: the state-vector method and
   the tensor-network representation of a circuit (Section 2.2), the amplitude
   <x|U|0> of Eq. prob_dist (Section 5.3), with slicing (Section 5.3).
@@ -58,6 +62,10 @@ MODE_NAMES = {
     MODE_FP32: "fp32",
     MODE_BF16X3: "bf16x3",
 }
+# FP16 emulation with one power-of-two scale per row of op(A) and per column
+# of op(B) (a variant beyond the paper; the value the C ABI reports for it)
+MODE_FP16X_ROWCOL = 6
+MODE_NAMES[MODE_FP16X_ROWCOL] = "fp16x_rowcol"
 OP_N, OP_T, OP_C = 0, 1, 2
 
 
@@ -396,6 +404,100 @@ def select_mode(sa: Dict[str, int], sb: Dict[str, int], t: float = 0.0):
         scl = lambda s: 0 if s["e_max"] is None else FP16_ETOP - s["e_max"]
         return MODE_FP16X_SCALED, scl(sa), scl(sb)
     return MODE_FP16X, 0, 0
+
+
+# ---------------------------------------------------------------------------
+# Per-row / per-column scaling (a variant beyond the paper: Section 4.1's
+# per-matrix scaling basis applied to each row of op(A) and column of op(B))
+# ---------------------------------------------------------------------------
+
+def _lines(X: np.ndarray, op: int, count: int, k: int, rows_of_op: bool):
+    """The lines of op(X) as Fortran column vectors: rows of op(A)
+    (rows_of_op) or columns of op(B).  Conjugation is left out: it does not
+    change an exponent."""
+    X, _ = _mat_view(X)
+    out = []
+    for i in range(count):
+        if rows_of_op:   # row i of op(A): a stored row of A (N) or a stored column
+            v = X[i, :k] if op == OP_N else X[:k, i]
+        else:            # column j of op(B): a stored column of B (N) or a stored row
+            v = X[:k, i] if op == OP_N else X[i, :k]
+        out.append(np.asfortranarray(np.asarray(v, dtype=np.complex64).reshape(-1, 1)))
+    return out
+
+
+def rowcol_stats(A: np.ndarray, B: np.ndarray, opA: int, opB: int, m: int, n: int, k: int):
+    """Per-line statistics of per-row / per-column scaling, each line taken as
+    a matrix of its own through exp_stats and stats_summary (Section 4.1):
+    the biased largest exponent of every row of op(A) (m) and column of
+    op(B) (n), -1 for a line without a nonzero finite scalar, and the counts
+    [under A, nonzero A, under B, nonzero B], "under" being the Stage 2 count
+    of each line (below its window [e_max - 28, e_max]) summed over the lines."""
+    res = []
+    for X, op, cnt, rows_of_op in ((A, opA, m, True), (B, opB, n, False)):
+        emax, under, nnz = [], 0, 0
+        for v in _lines(X, op, cnt, k, rows_of_op):
+            st = stats_summary(*exp_stats(v))
+            emax.append(-1 if st["e_max"] is None else st["e_max"] + 127)
+            under += st["under2"]
+            nnz += st["nnz"]
+        res.append((np.array(emax, dtype=np.int64), under, nnz))
+    (ea, ua, na), (eb, ub, nb) = res
+    return ea, eb, np.array([ua, na, ub, nb], dtype=np.int64)
+
+
+def line_scale(emax_biased: int) -> int:
+    """Scale exponent of a line: 14 - e_max moves its largest magnitude to
+    [2^14, 2^15) as for a whole matrix in Section 4.1; 0 for a line without
+    a nonzero finite scalar."""
+    return 0 if emax_biased < 0 else FP16_ETOP - (int(emax_biased) - 127)
+
+
+def select_rowcol(sa: Dict[str, int], sb: Dict[str, int], counts, t: float = 0.0):
+    """Section 4.1's rule, then per-row / per-column scaling where the rule
+    gives up on FP16 (TF32X): FP16 emulation with line scales when each
+    operand's summed Stage 2 count over its lines is at most t times its
+    nonzero count.  Returns (mode, sA, sB)."""
+    mode = select_mode(sa, sb, t)
+    if mode[0] == MODE_TF32X and counts[0] <= t * counts[1] and counts[2] <= t * counts[3]:
+        return MODE_FP16X_ROWCOL, 0, 0
+    return mode
+
+
+def tcec_cgemm_rowcol(emaxA, emaxB, opA: int, opB: int, m: int, n: int, k: int, alpha, A, B,
+                      beta=0.0, C=None) -> np.ndarray:
+    """Exact (FP64) value of FP16 emulation with line scales: row i of op(A)
+    multiplied by 2^sA_i and column j of op(B) by 2^sB_j in binary32 (the
+    scaled matrices as stored), the Eq. 1 / Section 3 product of those
+    (tcec_cgemm, FP16, no further scaling), element (i, j) multiplied back by
+    2^-(sA_i + sB_j), then alpha and beta."""
+    A32, _ = _mat_view(A)
+    B32, _ = _mat_view(B)
+    sa = [line_scale(e) for e in emaxA]
+    sb = [line_scale(e) for e in emaxB]
+
+    def scaled(X, op, scales, rows_of_op):
+        Y = np.array(X, dtype=np.complex64, order="F", copy=True)
+        for i, s in enumerate(scales):
+            if rows_of_op:
+                sl = (i, slice(0, k)) if op == OP_N else (slice(0, k), i)
+            else:
+                sl = (slice(0, k), i) if op == OP_N else (i, slice(0, k))
+            v = Y[sl]
+            re = np.ldexp(v.real.astype(np.float32), np.int32(s)).astype(np.float32)
+            im = np.ldexp(v.imag.astype(np.float32), np.int32(s)).astype(np.float32)
+            Y[sl] = re + 1j * im
+        return Y
+
+    As = scaled(A32, opA, sa, True)
+    Bs = scaled(B32, opB, sb, False)
+    prod = tcec_cgemm(0, 0, 0, opA, opB, m, n, k, 1.0, As, Bs)
+    unscale = np.ldexp(1.0, -(np.array(sa)[:, None] + np.array(sb)[None, :]))
+    out = complex(alpha) * (prod * unscale)
+    if C is not None:
+        C64, _ = _mat_view(C)
+        out = out + complex(beta) * C64[:m, :n].astype(np.complex128)
+    return np.asfortranarray(out)
 
 
 def size_rule(m: int, n: int, k: int) -> Optional[int]:

@@ -96,6 +96,24 @@ def uniform_operand(rows: int, cols: int, seed) -> np.ndarray:
     return np.asfortranarray((re + 1j * im).astype(np.complex64))
 
 
+def line_scaled_operand(rows: int, cols: int, s: int, axis: int, seed,
+                        ld: int | None = None) -> np.ndarray:
+    """Column-major complex64 matrix whose rows (axis 0) or columns (axis 1)
+    each carry one random binade: parts ~ N(0, 1) * 2**e_line with
+    e_line ~ Uniform int [-s, s] per line, drawn once for the line's real and
+    imaginary parts alike.  Padding rows (ld > rows) hold NaN."""
+    ld = rows if ld is None else ld
+    assert ld >= rows
+    g = _rng(seed)
+    re = g.standard_normal((rows, cols), dtype=np.float64)
+    im = g.standard_normal((rows, cols), dtype=np.float64)
+    e = g.integers(-s, s + 1, size=rows if axis == 0 else cols)
+    f = np.exp2(e)[:, None] if axis == 0 else np.exp2(e)[None, :]
+    out = np.full((ld, cols), np.nan + 1j * np.nan, dtype=np.complex64, order="F")
+    out[:rows, :] = ((re + 1j * im) * f).astype(np.complex64)
+    return out
+
+
 def typed_matrix(rows: int, cols: int, kind: int, seed) -> np.ndarray:
     """Type-1/2/3 element initialisation of Section 5.2 (complex64, column-major).
 

@@ -614,3 +614,144 @@ def test_random_greedy_order_and_slice_chooser_preserve_the_amplitude():
     total = sum(complex(oracle.contract_network(oracle.slice_network(tn, dict(zip(labels, v))), outl))
                 for v in np.ndindex(2, 2, 2))
     assert abs(total - ref) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Per-row / per-column scaling (a variant beyond the paper, on Section 4.1's
+# scaling basis): line statistics, selection, emulation model
+# ---------------------------------------------------------------------------
+
+def _op_lines(X, op, rows_of_op, r, c):
+    """Lines of op(X) by numpy indexing: rows of op(A) / columns of op(B)."""
+    M = np.asarray(X)[:r, :c]
+    M = M if op == OP_N else M.T
+    return [M[i, :] for i in range(M.shape[0])] if rows_of_op else [M[:, j] for j in range(M.shape[1])]
+
+
+def _biased_exp_frexp(x: float) -> int:
+    """floor(log2|x|) + 127 through frexp for normal binary32 numbers, 0 for
+    subnormals, -1 for zero and Inf/NaN."""
+    if x == 0 or not math.isfinite(x):
+        return -1
+    if abs(x) < 2.0 ** -126:
+        return 0
+    return math.frexp(x)[1] - 1 + 127
+
+
+def _brute_rowcol(A, B, opA, opB, m, n, k):
+    res = []
+    for X, op, rows_of_op, r, c in ((A, opA, True, *((m, k) if opA == OP_N else (k, m))),
+                                    (B, opB, False, *((k, n) if opB == OP_N else (n, k)))):
+        emax, under, nnz = [], 0, 0
+        for line in _op_lines(X, op, rows_of_op, r, c):
+            bs = [_biased_exp_frexp(float(np.float32(v))) for z in line for v in (z.real, z.imag)]
+            bs = [b for b in bs if b >= 0]
+            E = max(bs) if bs else -1
+            emax.append(E)
+            nnz += len(bs)
+            under += sum(1 for b in bs if b == 0 or b < E - 28)
+        res.append((emax, under, nnz))
+    return res
+
+
+@pytest.mark.parametrize("opA,opB", [(OP_N, OP_N), (OP_T, OP_C), (OP_C, OP_T)])
+def test_rowcol_stats_brute_force(opA, opB):
+    m, n, k = 9, 7, 11
+    ra, ca = (m, k) if opA == OP_N else (k, m)
+    rb, cb = (k, n) if opB == OP_N else (n, k)
+    A = qi.line_scaled_operand(ra, ca, 40, 0 if opA == OP_N else 1, seed=(opA, 1), ld=ra + 2)
+    B = qi.line_scaled_operand(rb, cb, 40, 1 if opB == OP_N else 0, seed=(opB, 2))
+    # a zero line, a subnormal-only line, a scalar 29 binades under its line
+    if opA == OP_N:
+        A[3, :k] = 0
+        A[5, :k] = np.float32(3e-41)
+        A[6, 2] = complex(A[6, 2].real * np.float32(2.0 ** -29), 0)
+    else:
+        A[:k, 3] = 0
+        A[:k, 5] = np.float32(3e-41)
+    ea, eb, cnt = oracle.rowcol_stats(A, B, opA, opB, m, n, k)
+    (ba, ua, na), (bb, ub, nb) = _brute_rowcol(A, B, opA, opB, m, n, k)
+    assert list(ea) == ba and list(eb) == bb
+    assert list(cnt) == [ua, na, ub, nb]
+    assert ea[3] == -1 and ea[5] == 0
+
+
+def test_rowcol_stats_hand_window_edges():
+    # each row: 2^a, 2^(a-28) (on the window's lower edge), 2^(a-29) (below), 0
+    a = [-100, -3, 0, 17, 90]
+    A = F([[2.0 ** e, 2.0 ** (e - 28), 2.0 ** (e - 29) * 1j, 0] for e in a])
+    B = F(np.ones((4, 2)))
+    ea, eb, cnt = oracle.rowcol_stats(A, B, OP_N, OP_N, 5, 2, 4)
+    assert list(ea) == [e + 127 for e in a]
+    assert list(eb) == [127, 127]
+    # under: 2^(a-29) of every row, and 2^-128 of the first (a binary32 subnormal)
+    assert list(cnt) == [6, 15, 0, 8]
+    assert [oracle.line_scale(E) for E in ea] == [14 - e for e in a]
+    assert oracle.line_scale(-1) == 0
+
+
+def test_select_rowcol_cases():
+    m = n = k = 48
+    summ = lambda X: oracle.stats_summary(*oracle.exp_stats(X))
+    # lines two to forty binades apart: the whole-matrix window fails, every line fits
+    A = qi.line_scaled_operand(m, k, 20, 0, seed=5)
+    B = qi.line_scaled_operand(k, n, 20, 1, seed=6)
+    cnt = oracle.rowcol_stats(A, B, OP_N, OP_N, m, n, k)[2]
+    assert oracle.select_mode(summ(A), summ(B), 0.1)[0] == oracle.MODE_TF32X
+    assert oracle.select_rowcol(summ(A), summ(B), cnt, 0.1) == (oracle.MODE_FP16X_ROWCOL, 0, 0)
+    # per-element spread: every line spans the whole range, TF32X stays
+    A2 = qi.cgemm_operand(m, k, 20, seed=7)
+    cnt2 = oracle.rowcol_stats(A2, B, OP_N, OP_N, m, n, k)[2]
+    assert oracle.select_rowcol(summ(A2), summ(B), cnt2, 0.1)[0] == oracle.MODE_TF32X
+    # what Section 4.1 already accepts is left as it is
+    A3, B3 = qi.cgemm_operand(m, k, 0, seed=8), qi.cgemm_operand(k, n, 0, seed=9)
+    cnt3 = oracle.rowcol_stats(A3, B3, OP_N, OP_N, m, n, k)[2]
+    assert oracle.select_rowcol(summ(A3), summ(B3), cnt3, 0.1) == oracle.select_mode(summ(A3), summ(B3), 0.1)
+    # Inf: plain FP32
+    A4 = A.copy(order="F")
+    A4[0, 0] = np.inf
+    cnt4 = oracle.rowcol_stats(A4, B, OP_N, OP_N, m, n, k)[2]
+    assert oracle.select_rowcol(summ(A4), summ(B), cnt4, 0.1)[0] == oracle.MODE_FP32
+
+
+@pytest.mark.parametrize("opA,opB", [(OP_N, OP_N), (OP_T, OP_C), (OP_C, OP_N)])
+def test_tcec_rowcol_model_exact_on_line_scaled_integers(opA, opB):
+    g = np.random.default_rng(11)
+    m, n, k = 6, 5, 7
+    ra, ca = (m, k) if opA == OP_N else (k, m)
+    rb, cb = (k, n) if opB == OP_N else (n, k)
+    ints = lambda r, c: g.integers(-8, 9, (r, c)) + 1j * g.integers(-8, 9, (r, c))
+    # op(A)'s rows and op(B)'s columns 2^-40 .. 2^40 apart
+    fa = np.exp2(g.integers(-40, 41, m))
+    fb = np.exp2(g.integers(-40, 41, n))
+    A = ints(ra, ca) * (fa[:, None] if opA == OP_N else fa[None, :])
+    B = ints(rb, cb) * (fb[None, :] if opB == OP_N else fb[:, None])
+    A, B = F(A), F(B)
+    opm = lambda X, op: X if op == OP_N else (X.T if op == OP_T else X.conj().T)
+    ref = opm(A.astype(np.complex128), opA) @ opm(B.astype(np.complex128), opB)
+    ea, eb, _ = oracle.rowcol_stats(A, B, opA, opB, m, n, k)
+    got = oracle.tcec_cgemm_rowcol(ea, eb, opA, opB, m, n, k, 1.0, A, B)
+    assert np.array_equal(got, ref)
+    # one scale per matrix loses the rows far below the largest
+    sa = oracle.stats_summary(*oracle.exp_stats(A))
+    sb = oracle.stats_summary(*oracle.exp_stats(B))
+    whole = oracle.tcec_cgemm(0, 14 - sa["e_max"], 14 - sb["e_max"], opA, opB, m, n, k, 1.0, A, B)
+    assert not np.array_equal(whole, ref)
+    # alpha and beta after the unscaling
+    C0 = F(ints(m, n))
+    got = oracle.tcec_cgemm_rowcol(ea, eb, opA, opB, m, n, k, 0.5 - 1j, A, B, 2.0, C0)
+    assert np.array_equal(got, (0.5 - 1j) * ref + 2.0 * C0.astype(np.complex128))
+
+
+def test_tcec_rowcol_model_accuracy_line_scaled_gaussian():
+    m, n, k = 40, 36, 256
+    A = qi.line_scaled_operand(m, k, 30, 0, seed=12)
+    B = qi.line_scaled_operand(k, n, 30, 1, seed=13)
+    exact = oracle.cgemm(OP_N, OP_N, m, n, k, 1.0, A, B)
+    ea, eb, _ = oracle.rowcol_stats(A, B, OP_N, OP_N, m, n, k)
+    err = oracle.rel_fro_error(oracle.tcec_cgemm_rowcol(ea, eb, OP_N, OP_N, m, n, k, 1.0, A, B), exact)
+    # per element against the magnitudes: FP32-level, as Eq. 1 promises per line
+    got = oracle.tcec_cgemm_rowcol(ea, eb, OP_N, OP_N, m, n, k, 1.0, A, B)
+    mag = np.abs(A[:m, :k]).astype(np.float64) @ np.abs(B[:k, :n]).astype(np.float64)
+    assert np.all(np.abs(got - exact) <= 2.0 ** -20 * mag)
+    assert err < 1e-6
