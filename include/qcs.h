@@ -56,6 +56,10 @@ typedef enum {
     QCS_MODE_BF16X3 = 5
 } qcs_mode_t;
 #define QCS_NUM_MODES 6
+/* Reported only (in a qcs_cgemm call's d_desc_out, never accepted as an
+ * argument): FP16 emulation with every row of op(A) and every column of
+ * op(B) scaled by its own power of two (qcs_set_rowcol_scaling). */
+#define QCS_MODE_FP16X_ROWCOL 6
 
 typedef enum { QCS_OP_N = 0, QCS_OP_T = 1, QCS_OP_C = 2 } qcs_op_t;
 
@@ -175,6 +179,39 @@ int qcs_set_tc_pairs(qcs_handle_t h, int enabled);
  * This is a schedule of Section 2.1's emulation, not a step of the paper.
  * Returns QCS_ERR_INVALID_ARG for other values. */
 int qcs_set_tc_splits(qcs_handle_t h, int splits);
+
+/* Per-row / per-column power-of-two scaling for AUTO (a variant beyond the
+ * paper: the scaling basis of Section 4.1, where one power of two per
+ * matrix moves its largest exponent to 14, applied to each row of op(A) and
+ * each column of op(B) instead).  While ``enabled`` is 1, a qcs_cgemm call
+ * whose mode after the size rule is AUTO (k > 0, four real products) first
+ * selects as Section 4.1 does.  If that selection is TF32X, row i of op(A)
+ * is scaled by 2^(14 - e_max(i)) and column j of op(B) by 2^(14 - e_max(j))
+ * (e_max over the nonzero finite real and imaginary scalars of the line; a
+ * line without any keeps scale 1), and the GEMM runs as FP16 emulation when
+ * each operand's count of nonzero scalars below its lines' shifted windows
+ * [e_max - 28, e_max] (binary32 subnormals included) is at most t times its
+ * nonzero count, t the underflow tolerance; the product is multiplied back
+ * by 2^-(sA_i + sB_j), then alpha and beta are applied.  d_desc_out then
+ * reports QCS_MODE_FP16X_ROWCOL with sA = sB = 0; otherwise the call gives
+ * what it gives with the option off.  The call takes a further m x n complex
+ * product and the line statistics (two passes over A and B) from the
+ * handle's workspace.  Default 0; QCS_ERR_INVALID_ARG for other values. */
+int qcs_set_rowcol_scaling(qcs_handle_t h, int enabled);
+
+/* The per-line statistics of qcs_set_rowcol_scaling for op(A) (m x k) and
+ * op(B) (k x n) as stored (A: lda, B: ldb, column-major, device): the
+ * largest biased binary32 exponent of every row of op(A) into d_emaxA[m] and
+ * of every column of op(B) into d_emaxB[n] (-1 for a line without a nonzero
+ * finite scalar; real and imaginary parts count separately), and into
+ * d_counts[4]: op(A)'s nonzero scalars below their row's shifted window
+ * (biased exponent 0, or below e_max - 28), op(A)'s nonzero finite scalars,
+ * and the same two for op(B)'s columns.  Device buffers, caller-owned;
+ * asynchronous on the handle's stream.  QCS_ERR_INVALID_ARG on bad
+ * arguments. */
+int qcs_rowcol_stats(qcs_handle_t h, qcs_op_t transA, qcs_op_t transB, int64_t m, int64_t n,
+                     int64_t k, const qcs_c32 *A, int64_t lda, const qcs_c32 *B, int64_t ldb,
+                     int32_t *d_emaxA, int32_t *d_emaxB, int64_t *d_counts);
 
 /* Real products per emulated complex product of qcs_cgemm: 4 (default; the
  * complex expansion of Section 3, Re = ArBr - AiBi, Im = ArBi + AiBr) or 3

@@ -12,13 +12,15 @@ import ctypes
 from typing import Optional
 
 from . import _lib
-from ._lib import (MODE_AUTO, MODE_BF16X3, MODE_BY_NAME, MODE_FP16X, MODE_FP16X_SCALED, MODE_FP32,
-                   MODE_NAME, MODE_TF32X, OP_C, OP_N, OP_T, SIZE_RULE_OFF, SIZE_RULE_PAPER,
+from ._lib import (MODE_AUTO, MODE_BF16X3, MODE_BY_NAME, MODE_FP16X, MODE_FP16X_ROWCOL,
+                   MODE_FP16X_SCALED, MODE_FP32, MODE_NAME, MODE_TF32X, OP_C, OP_N, OP_T,
+                   SIZE_RULE_OFF, SIZE_RULE_PAPER,
                    SIZE_RULE_TUNED, QcsError)
 
 __all__ = [
     "Handle", "cgemm", "sgemm", "fortran_empty_real", "exp_stats", "select", "split", "permute", "fortran_empty", "to_fortran",
     "MODE_AUTO", "MODE_FP16X", "MODE_FP16X_SCALED", "MODE_TF32X", "MODE_FP32", "MODE_BF16X3",
+    "MODE_FP16X_ROWCOL", "rowcol_stats",
     "MODE_BY_NAME", "MODE_NAME", "OP_N", "OP_T", "OP_C", "QcsError",
     "SIZE_RULE_OFF", "SIZE_RULE_PAPER", "SIZE_RULE_TUNED",
 ]
@@ -186,6 +188,13 @@ class Handle:
         _lib.check(self.lib.qcs_set_tc_multicast(self._h, int(bool(enabled))),
                    "qcs_set_tc_multicast")
 
+    def set_rowcol_scaling(self, enabled: bool):
+        """AUTO falls back to FP16 emulation with per-row (op(A)) and
+        per-column (op(B)) power-of-two scaling before TF32X
+        (qcs_set_rowcol_scaling; off by default)."""
+        _lib.check(self.lib.qcs_set_rowcol_scaling(self._h, int(bool(enabled))),
+                   "qcs_set_rowcol_scaling")
+
     def set_tc_pairs(self, enabled: bool):
         """Run the tensor-core kernels as CTA pairs on 256-row tiles, each CTA
         holding half of every op(B) operand (tcgen05 cta_group::2;
@@ -314,6 +323,28 @@ def selection_stats(h: Handle, A, B, *, opA=OP_N, opB=OP_N):
                     "n_nonzero": int(o.n_nonzero), "n_nonfinite": int(o.n_nonfinite),
                     "n_under_fp16": int(o.n_under_fp16), "n_under_window": int(o.n_under_window)})
     return res, (int(d.mode), int(d.sA), int(d.sB))
+
+
+def rowcol_stats(h: Handle, A, B, *, opA=OP_N, opB=OP_N):
+    """The per-line statistics of per-row / per-column scaling
+    (qcs_rowcol_stats): (emaxA, emaxB, counts) as CUDA int32 tensors of m
+    and n biased exponents (-1: no nonzero finite scalar) and an int64
+    tensor [under A, nonzero A, under B, nonzero B]."""
+    torch = _torch()
+    rA, cA = A.shape
+    rB, cB = B.shape
+    m = rA if opA == OP_N else cA
+    k = cA if opA == OP_N else rA
+    n = cB if opB == OP_N else rB
+    ea = torch.empty(m, dtype=torch.int32, device=A.device)
+    eb = torch.empty(n, dtype=torch.int32, device=A.device)
+    cnt = torch.empty(4, dtype=torch.int64, device=A.device)
+    _lib.check(h.lib.qcs_rowcol_stats(h.ptr, int(opA), int(opB), m, n, k,
+                                      ctypes.c_void_p(A.data_ptr()), _ld(A, rA),
+                                      ctypes.c_void_p(B.data_ptr()), _ld(B, rB),
+                                      ctypes.c_void_p(ea.data_ptr()), ctypes.c_void_p(eb.data_ptr()),
+                                      ctypes.c_void_p(cnt.data_ptr())), "qcs_rowcol_stats")
+    return ea, eb, cnt
 
 
 def fidelity_stats(h: Handle, a, ref=None) -> dict:

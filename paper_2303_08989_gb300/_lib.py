@@ -23,6 +23,8 @@ QCS_ERR_SCRATCH_TOO_SMALL = -6
 MODE_AUTO, MODE_FP16X, MODE_FP16X_SCALED, MODE_TF32X, MODE_FP32, MODE_BF16X3 = range(6)
 MODE_BY_NAME = {"auto": 0, "fp16x": 1, "fp16x_scaled": 2, "tf32x": 3, "fp32": 4, "bf16x3": 5}
 MODE_NAME = {v: k for k, v in MODE_BY_NAME.items()}
+MODE_FP16X_ROWCOL = 6  # reported only, never an argument (qcs_set_rowcol_scaling)
+MODE_NAME[MODE_FP16X_ROWCOL] = "fp16x_rowcol"
 OP_N, OP_T, OP_C = 0, 1, 2
 
 #: every entry point include/qcs.h declares
@@ -38,7 +40,8 @@ EXPORTED = [
     "qcs_debug_stall_producer", "qcs_cgemm_noalloc_status", "qcs_measure_fma_peak",
     "qcs_set_fused_split", "qcs_set_tree_levels", "qcs_set_group_budget", "qcs_fidelity_stats",
     "qcs_tree_layout_info", "qcs_set_tc_multicast", "qcs_set_tc_pairs",
-    "qcs_selection_stats", "qcs_tree_backward_graph_create",
+    "qcs_selection_stats", "qcs_tree_backward_graph_create", "qcs_set_rowcol_scaling",
+    "qcs_rowcol_stats",
 ]
 SIZE_RULE_OFF, SIZE_RULE_PAPER, SIZE_RULE_TUNED = 0, 1, 2
 NUM_MODES = 6
@@ -180,6 +183,8 @@ def load(path: str = LIB_PATH):
         "qcs_set_tree_levels": [H, I],
         "qcs_set_tc_multicast": [H, I],
         "qcs_set_tc_pairs": [H, I],
+        "qcs_set_rowcol_scaling": [H, I],
+        "qcs_rowcol_stats": [H, I, I, I64, I64, I64, P, I64, P, I64, P, P, P],
         "qcs_set_group_budget": [H, ctypes.c_uint64],
         "qcs_fidelity_stats": [H, P, I, P, I64, P],
         "qcs_tree_layout_info": [ctypes.POINTER(qcs_tree_t), I, I, I, I, ctypes.c_uint64, P, P,

@@ -281,7 +281,7 @@ int split_operand(qcs_handle_t h, int which, const qcs_gemm_desc_t *dg, const Op
         plane_strides(which, op, X.ld, sr, sc);
         e = launch_split(dg, which, X.X, sr, sc, op == QCS_OP_C, R, k, R_pad, kp, planes, kp,
                          plane_stride, h->stream, which, plane_off, planes32, tf32_fused ? 1 : 0,
-                         sb);
+                         sb, h->line_emax[which]);
     }
     return e == cudaSuccess ? QCS_SUCCESS : QCS_ERR_CUDA;
 }
@@ -678,6 +678,104 @@ Gauss3Layout gauss3_layout(int eff, int64_t m, int64_t n, int64_t k, int S) {
 
 }  // namespace
 
+// The per-line statistics of op(A)'s rows and op(B)'s columns: each line's
+// largest biased exponent (emaxA: m, emaxB: n) and counts[4] = {below the
+// shifted windows in op(A), nonzero in op(A), the same for op(B)}.
+cudaError_t rowcol_line_stats(cudaStream_t s, int opA, int opB, int64_t m, int64_t n, int64_t k,
+                              const float2 *A, int64_t lda, const float2 *B, int64_t ldb,
+                              int *emaxA, int *emaxB, unsigned long long *counts) {
+    // a row of op(A) is a stored row of A (N) or a stored column (T, C); a
+    // column of op(B) is a stored column of B (N) or a stored row (T, C)
+    const int64_t ra = (opA == QCS_OP_N) ? m : k, ca = (opA == QCS_OP_N) ? k : m;
+    const int64_t rb = (opB == QCS_OP_N) ? k : n, cb = (opB == QCS_OP_N) ? n : k;
+    const int rowsA = (opA == QCS_OP_N) ? 1 : 0, rowsB = (opB == QCS_OP_N) ? 0 : 1;
+    cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = launch_line_emax(A, ra, ca, lda, rowsA, emaxA, s);
+    if (e == cudaSuccess) e = launch_line_emax(B, rb, cb, ldb, rowsB, emaxB, s);
+    if (e == cudaSuccess) e = launch_line_under(A, ra, ca, lda, rowsA, emaxA, counts, s);
+    if (e == cudaSuccess) e = launch_line_under(B, rb, cb, ldb, rowsB, emaxB, counts + 2, s);
+    return e;
+}
+
+namespace {
+
+struct RowcolLayout {
+    size_t desc, partials, counts, emaxA, emaxB, P, total;
+};
+
+RowcolLayout rowcol_layout(int64_t m, int64_t n, int num_sms) {
+    RowcolLayout L;
+    size_t off = 0;
+    L.desc = off;  // desc0, descK, descOut
+    off += align256(3 * sizeof(qcs_gemm_desc_t));
+    L.partials = off;
+    off += align256(size_t(2) * num_sms * kPartialStride * sizeof(int64_t));
+    L.counts = off;
+    off += align256(4 * sizeof(unsigned long long));
+    L.emaxA = off;
+    off += align256(sizeof(int) * (size_t)m);
+    L.emaxB = off;
+    off += align256(sizeof(int) * (size_t)n);
+    L.P = off;
+    off += align256(sizeof(float2) * (size_t)m * (size_t)n);
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+size_t rowcol_workspace_bytes(int64_t m, int64_t n, int64_t k, int num_sms, int splits) {
+    return rowcol_layout(m, n, num_sms).total +
+           gemm_workspace_bytes(QCS_MODE_AUTO, m, n, k, num_sms, splits, 1);
+}
+
+int run_cgemm_rowcol(qcs_handle_t h, void *ws, int opA, int opB, int64_t m, int64_t n, int64_t k,
+                     float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb,
+                     float2 beta, float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out) {
+    if (k == 0 || m == 0 || n == 0) return QCS_ERR_UNSUPPORTED;
+    cudaStream_t s = h->stream;
+    uint8_t *p = static_cast<uint8_t *>(ws);
+    const RowcolLayout L = rowcol_layout(m, n, h->num_sms);
+    qcs_gemm_desc_t *desc0 = reinterpret_cast<qcs_gemm_desc_t *>(p + L.desc);
+    qcs_gemm_desc_t *descK = desc0 + 1, *descOut = desc0 + 2;
+    int64_t *partials = reinterpret_cast<int64_t *>(p + L.partials);
+    unsigned long long *counts = reinterpret_cast<unsigned long long *>(p + L.counts);
+    int *emaxA = reinterpret_cast<int *>(p + L.emaxA);
+    int *emaxB = reinterpret_cast<int *>(p + L.emaxB);
+    float2 *P = reinterpret_cast<float2 *>(p + L.P);
+    {
+        // Section 4.1 on the whole matrices, as qcs_cgemm's AUTO
+        const int64_t ra = (opA == QCS_OP_N) ? m : k, ca = (opA == QCS_OP_N) ? k : m;
+        const int64_t rb = (opB == QCS_OP_N) ? k : n, cb = (opB == QCS_OP_N) ? n : k;
+        const int gA = stats2_blocks(ra * ca, h->num_sms), gB = stats2_blocks(rb * cb, h->num_sms);
+        ProfScope ps(h, kProfStats);
+        if (launch_stats_select_2stage(A, ra, ca, lda, gA, B, rb, cb, ldb, gB, h->tol,
+                                       QCS_MODE_AUTO, partials, partials + 5 * (gA + gB), desc0,
+                                       h->d_counts, 8.0 * (double)m * (double)n * (double)k,
+                                       s) != cudaSuccess ||
+            rowcol_line_stats(s, opA, opB, m, n, k, A, lda, B, ldb, emaxA, emaxB, counts) !=
+                cudaSuccess ||
+            launch_rowcol_select(desc0, counts, h->tol, descK, descOut, s) != cudaSuccess)
+            return QCS_ERR_CUDA;
+    }
+    // the GEMM on the selected descriptor into P (alpha 1, beta 0); the
+    // split reads the line exponents when descK says so
+    h->line_emax[0] = emaxA;
+    h->line_emax[1] = emaxB;
+    const int r = run_cgemm(h, p + L.total, QCS_MODE_AUTO, opA, opB, m, n, k, make_float2(1.f, 0.f),
+                            A, lda, B, ldb, make_float2(0.f, 0.f), P, m, nullptr, descK);
+    h->line_emax[0] = h->line_emax[1] = nullptr;
+    if (r != QCS_SUCCESS) return r;
+    if (launch_rowcol_combine(descK, emaxA, emaxB, P, m, n, alpha, beta, C, ldc, h->num_sms, s) !=
+        cudaSuccess)
+        return QCS_ERR_CUDA;
+    if (d_desc_out &&
+        cudaMemcpyAsync(d_desc_out, descOut, sizeof(qcs_gemm_desc_t), cudaMemcpyDeviceToDevice,
+                        s) != cudaSuccess)
+        return QCS_ERR_CUDA;
+    return QCS_SUCCESS;
+}
+
 size_t cgemm3m_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits) {
     size_t bytes = align256(3 * sizeof(qcs_gemm_desc_t));
     bytes += align256(size_t(2) * num_sms * kPartialStride * sizeof(int64_t));
@@ -999,6 +1097,28 @@ int qcs_set_tc_pairs(qcs_handle_t h, int enabled) {
     return QCS_SUCCESS;
 }
 
+int qcs_set_rowcol_scaling(qcs_handle_t h, int enabled) {
+    if (!h || (enabled != 0 && enabled != 1)) return QCS_ERR_INVALID_ARG;
+    h->rowcol = enabled;
+    return QCS_SUCCESS;
+}
+
+int qcs_rowcol_stats(qcs_handle_t h, qcs_op_t transA, qcs_op_t transB, int64_t m, int64_t n,
+                     int64_t k, const qcs_c32 *A, int64_t lda, const qcs_c32 *B, int64_t ldb,
+                     int32_t *d_emaxA, int32_t *d_emaxB, int64_t *d_counts) {
+    if (!h || !valid_op(transA) || !valid_op(transB) || m < 0 || n < 0 || k < 0 || !d_counts)
+        return QCS_ERR_INVALID_ARG;
+    if ((m > 0 && !d_emaxA) || (n > 0 && !d_emaxB)) return QCS_ERR_INVALID_ARG;
+    const int64_t ra = (transA == QCS_OP_N) ? m : k, rb = (transB == QCS_OP_N) ? k : n;
+    if ((m * k > 0 && !A) || (n * k > 0 && !B) || lda < std::max<int64_t>(1, ra) ||
+        ldb < std::max<int64_t>(1, rb))
+        return QCS_ERR_INVALID_ARG;
+    return cuda_status(rowcol_line_stats(
+        h->stream, transA, transB, m, n, k, reinterpret_cast<const float2 *>(A), lda,
+        reinterpret_cast<const float2 *>(B), ldb, reinterpret_cast<int *>(d_emaxA),
+        reinterpret_cast<int *>(d_emaxB), reinterpret_cast<unsigned long long *>(d_counts)));
+}
+
 int qcs_set_tree_levels(qcs_handle_t h, int enabled) {
     if (!h || (enabled != 0 && enabled != 1)) return QCS_ERR_INVALID_ARG;
     h->tree_levels = enabled;
@@ -1077,6 +1197,16 @@ int qcs_cgemm(qcs_handle_t h, qcs_mode_t mode, qcs_op_t transA, qcs_op_t transB,
                             reinterpret_cast<const float2 *>(A), lda,
                             reinterpret_cast<const float2 *>(B), ldb, be,
                             reinterpret_cast<float2 *>(C), ldc, d_desc_out);
+    }
+    if (h->rowcol && eff == QCS_MODE_AUTO && k > 0) {
+        if (int r = ensure_workspace(h->ws, rowcol_workspace_bytes(
+                                                m, n, k, h->num_sms,
+                                                gemm_splits(h, transA, transB, m, n, k))))
+            return r;
+        return run_cgemm_rowcol(h, h->ws.ptr, transA, transB, m, n, k, al,
+                                reinterpret_cast<const float2 *>(A), lda,
+                                reinterpret_cast<const float2 *>(B), ldb, be,
+                                reinterpret_cast<float2 *>(C), ldc, d_desc_out);
     }
     if (int r = ensure_workspace(h->ws, gemm_workspace_bytes(eff, m, n, k, h->num_sms,
                                                             gemm_splits(h, transA, transB, m, n, k), 1)))

@@ -99,6 +99,8 @@ struct qcs_handle_s {
     int tree_levels = 1;             // tree executor: small FP32 steps of a level in one launch
     int tc_multicast = 0;            // complex tensor-core kernel in clusters of two sharing B
     int tc_pairs = 0;                // tensor-core kernels as CTA pairs (cta_group::2)
+    int rowcol = 0;                  // AUTO: per-row / per-column scaling before TF32X
+    const int *line_emax[2] = {nullptr, nullptr};  // set only inside run_cgemm_rowcol
     size_t group_budget = size_t(32) << 30;  // tree executor: bytes a grouped GPU-filling step may hold
     uint64_t wait_ns = qcs::kWaitBudgetNs;  // bound of the tensor-core kernels' device waits
     int debug_stall = 0;             // test hook: the TMA producer issues no loads
@@ -212,11 +214,41 @@ struct SplitBatch {
 // instead of ``planes`` -- a group whose instances may select different
 // kinds keeps the 2-byte and 4-byte planes in separate regions.  skip_tf32:
 // write nothing for a TF32 selection (the fused TF32X kernel splits itself).
+// qcs_gemm_desc_t::reserved value of a descriptor whose FP16 split scales
+// every row of op(A) and every column of op(B) by its own power of two (the
+// per-line exponents passed to launch_split / launch_rowcol_combine).
+constexpr int kDescLineScales = 1;
+
+// Per-row / per-column power-of-two scaling (qcs_set_rowcol_scaling).
+// launch_line_emax: for each row (per_row = 1) or column (0) of the stored
+// rows x cols matrix X (column-major, ld), the largest biased binary32
+// exponent over its nonzero finite real and imaginary scalars, -1 if none
+// (emax is cleared first).  launch_line_under: counts[0] += scalars below the
+// line's shifted window (biased exponent 0, or below emax - 28), counts[1] +=
+// nonzero finite scalars (counts must be cleared by the caller).
+cudaError_t launch_line_emax(const float2 *X, int64_t rows, int64_t cols, int64_t ld, int per_row,
+                             int *emax, cudaStream_t s);
+cudaError_t launch_line_under(const float2 *X, int64_t rows, int64_t cols, int64_t ld,
+                              int per_row, const int *emax, unsigned long long *counts,
+                              cudaStream_t s);
+// descK (for the kernels) and descOut (reported) from the Section 4.1
+// selection desc0 and counts[4] = {under A, nonzero A, under B, nonzero B}.
+cudaError_t launch_rowcol_select(const qcs_gemm_desc_t *desc0, const unsigned long long *counts,
+                                 double tol, qcs_gemm_desc_t *descK, qcs_gemm_desc_t *descOut,
+                                 cudaStream_t s);
+// C = alpha D_A^-1 P D_B^-1 + beta C (D: the per-line scales when descK
+// carries kDescLineScales, else the identity); P is m x n with ld m.
+cudaError_t launch_rowcol_combine(const qcs_gemm_desc_t *descK, const int *emaxA,
+                                  const int *emaxB, const float2 *P, int64_t m, int64_t n,
+                                  float2 alpha, float2 beta, float2 *C, int64_t ldc, int num_sms,
+                                  cudaStream_t s);
+
 cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X, int64_t sr,
                          int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
                          void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
                          int planes6 = 0, int64_t plane_off = 0, void *planes32 = nullptr,
-                         int skip_tf32 = 0, const SplitBatch &sb = SplitBatch{});
+                         int skip_tf32 = 0, const SplitBatch &sb = SplitBatch{},
+                         const int *line_emax = nullptr);
 
 // The split stage reading its operand through a gather map (the reshape of
 // a contraction folded into the split pass): op(X) is the rows x cols
@@ -480,6 +512,17 @@ cudaError_t launch_tc_reduce_real(const qcs_gemm_desc_t *desc, int64_t m, int64_
                                   float beta, float *C, int64_t ldc, int num_sms, const TcWork &w,
                                   cudaStream_t s);
 // Gauss's three-product form of one emulated CGEMM (qcs_set_complex_products 3).
+// AUTO with per-row / per-column scaling (qcs_set_rowcol_scaling): the
+// Section 4.1 selection, the per-line statistics and the decision, then
+// run_cgemm on the selected descriptor into a scratch product, then the
+// combine with the line scales, alpha and beta.
+size_t rowcol_workspace_bytes(int64_t m, int64_t n, int64_t k, int num_sms, int splits);
+cudaError_t rowcol_line_stats(cudaStream_t s, int opA, int opB, int64_t m, int64_t n, int64_t k,
+                              const float2 *A, int64_t lda, const float2 *B, int64_t ldb,
+                              int *emaxA, int *emaxB, unsigned long long *counts);
+int run_cgemm_rowcol(qcs_handle_t h, void *ws, int opA, int opB, int64_t m, int64_t n, int64_t k,
+                     float2 alpha, const float2 *A, int64_t lda, const float2 *B, int64_t ldb,
+                     float2 beta, float2 *C, int64_t ldc, qcs_gemm_desc_t *d_desc_out);
 size_t cgemm3m_workspace_bytes(int eff, int64_t m, int64_t n, int64_t k, int num_sms, int splits);
 int run_cgemm_3m(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t m, int64_t n,
                  int64_t k, float2 alpha, const float2 *A, int64_t lda, const float2 *B,

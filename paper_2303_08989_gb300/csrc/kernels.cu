@@ -668,19 +668,28 @@ __device__ __forceinline__ Pow2Scale pow2_scale(int s) {
 }
 __device__ __forceinline__ float apply_scale(float x, Pow2Scale p) { return (x * p.m1) * p.m2; }
 
+// The scale exponent of a row of op(A) or a column of op(B) from its largest
+// biased binary32 exponent E (-1: no nonzero finite scalar): the line is
+// multiplied by 2^(14 - e_max), e_max = E - 127, so that its largest
+// magnitude lands in [2^14, 2^15) as for a whole matrix in Section 4.1.
+__device__ __forceinline__ int line_scale(int E) { return E < 0 ? 0 : 141 - E; }
+
 // planes6: write op(B) as the five planes of the GEMM path (-hi.im, hi.re,
 // hi.im, lo.re, lo.im) instead of hi.re, hi.im, lo.re, lo.im.
 __global__ void __launch_bounds__(256, 8) split_kernel(
     const qcs_gemm_desc_t *__restrict__ desc, int which, const float2 *__restrict__ X, int64_t sr,
     int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad, void *planes,
     int64_t pitch, int64_t plane_stride, int planes6, int64_t plane_off, void *planes32,
-    int skip_tf32, int64_t x_bstride, int64_t off_bstride) {
+    int skip_tf32, int64_t x_bstride, int64_t off_bstride, const int *__restrict__ line_emax) {
     desc += blockIdx.z;  // instance z of a batch (SplitBatch)
     X += blockIdx.z * x_bstride;
     plane_off += blockIdx.z * off_bstride;
     const int mode = desc->mode;
     if (mode == QCS_MODE_FP32 || mode == QCS_MODE_AUTO || (skip_tf32 && mode == QCS_MODE_TF32X))
         return;
+    // per-row (op(A)) / per-column (op(B)) scales: only when the descriptor
+    // says so (reserved == kDescLineScales, written by rowcol_select_kernel)
+    const bool lines = line_emax != nullptr && desc->reserved == kDescLineScales;
     const int s = (mode == QCS_MODE_FP16X_SCALED) ? (which == 0 ? desc->sA : desc->sB) : 0;
     const Pow2Scale ps2 = pow2_scale(s);
 
@@ -723,10 +732,16 @@ __global__ void __launch_bounds__(256, 8) split_kernel(
         x[1] = conj ? -tile[rr][cc].y : tile[rr][cc].y;
         x[2] = tile[rr][cc + 1].x;
         x[3] = conj ? -tile[rr][cc + 1].y : tile[rr][cc + 1].y;
+        int sr_ = s;
+        Pow2Scale pr_ = ps2;
+        if (lines) {
+            sr_ = (r < R) ? line_scale(line_emax[r]) : 0;
+            pr_ = pow2_scale(sr_);
+        }
         // hi/lo of re and im for columns c and c+1
         uint32_t hib[4], lob[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) split_value(mode, (s != 0) ? apply_scale(x[e], ps2) : x[e], hib[e], lob[e]);
+        for (int e = 0; e < 4; ++e) split_value(mode, (sr_ != 0) ? apply_scale(x[e], pr_) : x[e], hib[e], lob[e]);
         const bool two = (c + 1 < K_pad);
         // x[0]/x[2] real, x[1]/x[3] imaginary parts of columns c, c+1; the
         // planes in the order written, two consecutive values each
@@ -790,16 +805,227 @@ cudaError_t launch_split(const qcs_gemm_desc_t *desc, int which, const float2 *X
                          int64_t sc, int conj, int64_t R, int64_t K, int64_t R_pad, int64_t K_pad,
                          void *planes, int64_t pitch, int64_t plane_stride, cudaStream_t s,
                          int planes6, int64_t plane_off, void *planes32, int skip_tf32,
-                         const SplitBatch &sb) {
+                         const SplitBatch &sb, const int *line_emax) {
     if (R_pad <= 0 || K_pad <= 0 || sb.count < 1) return cudaSuccess;
+    if (line_emax && sb.count != 1) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((K_pad + kSplitC - 1) / kSplitC), (unsigned)((R_pad + kSplitR - 1) / kSplitR),
               (unsigned)sb.count);
     if (grid.y > 65535u || sb.count > 65535) return cudaErrorInvalidValue;
     split_kernel<<<grid, 256, 0, s>>>(desc, which, X, sr, sc, conj, R, K, R_pad, K_pad, planes,
                                       pitch, plane_stride, planes6, plane_off, planes32, skip_tf32,
-                                      sb.in_stride, sb.off_stride);
+                                      sb.in_stride, sb.off_stride, line_emax);
     return cudaGetLastError();
 }
+
+// ===========================================================================
+// Per-row / per-column power-of-two scaling (a variant beyond the paper: the
+// per-matrix scaling of Section 4.1 applied to each row of op(A) and each
+// column of op(B)).
+// ===========================================================================
+
+namespace {
+
+constexpr int kLineTile = 32;  // 32 x 32 tiles of the stored matrix, 256 threads
+
+// biased binary32 exponent of a nonzero finite x (0: subnormal), -1 otherwise
+__device__ __forceinline__ int biased_exp_nz(float x) {
+    const uint32_t b = __float_as_uint(x) & 0x7FFFFFFFu;
+    if (b == 0u) return -1;
+    const int e = (int)(b >> 23);
+    return e == 255 ? -1 : e;
+}
+
+__global__ void __launch_bounds__(256) line_emax_kernel(const float2 *__restrict__ X, int64_t rows,
+                                                        int64_t cols, int64_t ld, int per_row,
+                                                        int *__restrict__ emax) {
+    __shared__ int red[8][kLineTile + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * kLineTile + lane;
+    const int64_t ctiles = (cols + kLineTile - 1) / kLineTile;
+    for (int64_t ct = blockIdx.y; ct < ctiles; ct += gridDim.y) {
+        const int64_t c0 = ct * kLineTile;
+        int mine = -1;
+#pragma unroll
+        for (int i = 0; i < kLineTile / 8; ++i) {
+            const int64_t c = c0 + warp + 8 * i;
+            int e = -1;
+            if (r < rows && c < cols) {
+                const float2 v = X[r + c * ld];
+                e = max(biased_exp_nz(v.x), biased_exp_nz(v.y));
+            }
+            if (per_row) {
+                mine = max(mine, e);
+            } else {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+                if (lane == 0 && c < cols && e >= 0) atomicMax(emax + c, e);
+            }
+        }
+        if (per_row) {
+            red[warp][lane] = mine;
+            __syncthreads();
+            if (warp == 0) {
+                int v = red[0][lane];
+#pragma unroll
+                for (int w = 1; w < 8; ++w) v = max(v, red[w][lane]);
+                if (r < rows && v >= 0) atomicMax(emax + r, v);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) line_under_kernel(const float2 *__restrict__ X, int64_t rows,
+                                                         int64_t cols, int64_t ld, int per_row,
+                                                         const int *__restrict__ emax,
+                                                         unsigned long long *__restrict__ counts) {
+    __shared__ unsigned long long su[8], sn[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * kLineTile + lane;
+    const int64_t ctiles = (cols + kLineTile - 1) / kLineTile;
+    unsigned long long under = 0, nnz = 0;
+    const int er = (per_row && r < rows) ? emax[r] : -1;
+    for (int64_t ct = blockIdx.y; ct < ctiles; ct += gridDim.y) {
+        const int64_t c0 = ct * kLineTile;
+#pragma unroll
+        for (int i = 0; i < kLineTile / 8; ++i) {
+            const int64_t c = c0 + warp + 8 * i;
+            if (r < rows && c < cols) {
+                const float2 v = X[r + c * ld];
+                const int E = per_row ? er : emax[c];
+                const float parts[2] = {v.x, v.y};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int b = biased_exp_nz(parts[h]);
+                    if (b < 0) continue;
+                    ++nnz;
+                    if (b == 0 || b < E - 28) ++under;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        under += __shfl_xor_sync(0xffffffffu, under, o);
+        nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
+    }
+    if (lane == 0) {
+        su[warp] = under;
+        sn[warp] = nnz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tu = 0, tn = 0;
+        for (int w = 0; w < 8; ++w) {
+            tu += su[w];
+            tn += sn[w];
+        }
+        if (tu) atomicAdd(counts, tu);
+        if (tn) atomicAdd(counts + 1, tn);
+    }
+}
+
+__global__ void rowcol_select_kernel(const qcs_gemm_desc_t *__restrict__ desc0,
+                                     const unsigned long long *__restrict__ counts, double tol,
+                                     qcs_gemm_desc_t *descK, qcs_gemm_desc_t *descOut) {
+    qcs_gemm_desc_t d = *desc0;
+    qcs_gemm_desc_t out = d;
+    d.reserved = 0;
+    // only where Section 4.1 gives up on FP16 (TF32X): every line scaled to
+    // its own maximum, each operand's count below the shifted windows
+    // tolerated as the whole-matrix count is
+    if (d.mode == QCS_MODE_TF32X && (double)counts[0] <= tol * (double)counts[1] &&
+        (double)counts[2] <= tol * (double)counts[3]) {
+        d.mode = QCS_MODE_FP16X_SCALED;
+        d.sA = d.sB = 0;
+        d.reserved = kDescLineScales;
+        out.mode = QCS_MODE_FP16X_ROWCOL;
+        out.sA = out.sB = 0;
+        out.reserved = 0;
+    }
+    *descK = d;
+    *descOut = out;
+}
+
+__global__ void __launch_bounds__(256) rowcol_combine_kernel(
+    const qcs_gemm_desc_t *__restrict__ descK, const int *__restrict__ emaxA,
+    const int *__restrict__ emaxB, const float2 *__restrict__ P, int64_t m, int64_t n,
+    float2 alpha, float2 beta, float2 *__restrict__ C, int64_t ldc) {
+    const bool lines = descK->reserved == kDescLineScales;
+    const bool use_beta = (beta.x != 0.0f) || (beta.y != 0.0f);
+    const int64_t mn = m * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < mn;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / m, i = t - j * m;
+        float pr = P[t].x, pi = P[t].y;
+        if (lines) {
+            // 2^-(sA_i + sB_j) in one correctly rounded step
+            const int sh = -(line_scale(emaxA[i]) + line_scale(emaxB[j]));
+            pr = ldexpf(pr, sh);
+            pi = ldexpf(pi, sh);
+        }
+        float2 o;
+        o.x = alpha.x * pr - alpha.y * pi;
+        o.y = alpha.x * pi + alpha.y * pr;
+        float2 *dst = C + i + j * ldc;
+        if (use_beta) {
+            const float2 c = *dst;
+            o.x += beta.x * c.x - beta.y * c.y;
+            o.y += beta.x * c.y + beta.y * c.x;
+        }
+        *dst = o;
+    }
+}
+
+dim3 line_grid(int64_t rows, int64_t cols) {
+    const int64_t gx = (rows + kLineTile - 1) / kLineTile;
+    const int64_t gy = (cols + kLineTile - 1) / kLineTile;
+    return dim3((unsigned)gx, (unsigned)std::min<int64_t>(gy, 65535));
+}
+
+}  // namespace
+
+cudaError_t launch_line_emax(const float2 *X, int64_t rows, int64_t cols, int64_t ld, int per_row,
+                             int *emax, cudaStream_t s) {
+    const int64_t lines = per_row ? rows : cols;
+    if (lines > 0) {
+        cudaError_t e = cudaMemsetAsync(emax, 0xFF, sizeof(int) * (size_t)lines, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if ((rows + kLineTile - 1) / kLineTile > INT32_MAX) return cudaErrorInvalidValue;
+    line_emax_kernel<<<line_grid(rows, cols), 256, 0, s>>>(X, rows, cols, ld, per_row, emax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_line_under(const float2 *X, int64_t rows, int64_t cols, int64_t ld,
+                              int per_row, const int *emax, unsigned long long *counts,
+                              cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if ((rows + kLineTile - 1) / kLineTile > INT32_MAX) return cudaErrorInvalidValue;
+    line_under_kernel<<<line_grid(rows, cols), 256, 0, s>>>(X, rows, cols, ld, per_row, emax,
+                                                            counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowcol_select(const qcs_gemm_desc_t *desc0, const unsigned long long *counts,
+                                 double tol, qcs_gemm_desc_t *descK, qcs_gemm_desc_t *descOut,
+                                 cudaStream_t s) {
+    rowcol_select_kernel<<<1, 1, 0, s>>>(desc0, counts, tol, descK, descOut);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowcol_combine(const qcs_gemm_desc_t *descK, const int *emaxA,
+                                  const int *emaxB, const float2 *P, int64_t m, int64_t n,
+                                  float2 alpha, float2 beta, float2 *C, int64_t ldc, int num_sms,
+                                  cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    const int64_t need = (m * n + 255) / 256, cap = (int64_t)num_sms * 16;
+    rowcol_combine_kernel<<<(unsigned)std::min(need, cap), 256, 0, s>>>(descK, emaxA, emaxB, P, m,
+                                                                       n, alpha, beta, C, ldc);
+    return cudaGetLastError();
+}
+
 
 namespace {
 
