@@ -759,25 +759,35 @@ def torch_leaves(net: Network, circ, params, device="cuda"):
     """Device leaf tensors of ``net``; the fSim leaves are functions of
     ``params`` ((n_fsim, 2) real tensor: theta, phi per fSim gate in circuit
     order), every other leaf is constant.  The fSim leaves come from one
-    batched evaluation (rows of one tensor), the constant ones from one
-    host-to-device copy."""
+    batched evaluation (rows of one tensor).  The constant ones come from one
+    host-to-device copy, made on the first call for a (network, circuit,
+    device) and kept on the network for later calls, with the index rows of
+    the fSim gates; replacing ``net.leaves`` drops the kept copy."""
     import torch
 
-    fs = {g: i for i, g in enumerate(circ.fsim_indices())}
-    var = [i for i, lf in enumerate(net.leaves) if lf.kind == "gate" and lf.gate in fs]
-    const = [i for i in range(len(net.leaves)) if i not in set(var)]
+    key = (id(circ), str(torch.device(device)), str(params.device))
+    kept = net.__dict__.get("_torch_leaf_cache")
+    if kept is None or kept[0] != key or kept[1] is not net.leaves:
+        fs = {g: i for i, g in enumerate(circ.fsim_indices())}
+        var = [i for i, lf in enumerate(net.leaves) if lf.kind == "gate" and lf.gate in fs]
+        const = [i for i in range(len(net.leaves)) if i not in set(var)]
+        rows = (torch.tensor([fs[net.leaves[i].gate] for i in var], device=params.device)
+                if var else None)
+        consts = []
+        if const:
+            flat = np.concatenate([net.leaves[i].data.ravel() for i in const]).astype(np.complex64)
+            dev = torch.from_numpy(flat).to(device)
+            consts = list(dev.split([net.leaves[i].data.size for i in const]))
+        kept = (key, net.leaves, var, rows, const, consts)
+        net.__dict__["_torch_leaf_cache"] = kept
+    _, _, var, rows, const, consts = kept
     out = [None] * len(net.leaves)
     if var:
-        rows = torch.tensor([fs[net.leaves[i].gate] for i in var], device=params.device)
         P = params[rows].to(device)
         for i, t in zip(var, _torch_fsim_leaves(P[:, 0], P[:, 1]).unbind(0)):
             out[i] = t
-    if const:
-        flat = np.concatenate([net.leaves[i].data.ravel() for i in const]).astype(np.complex64)
-        dev = torch.from_numpy(flat).to(device)
-        sizes = [net.leaves[i].data.size for i in const]
-        for i, t in zip(const, dev.split(sizes)):
-            out[i] = t
+    for i, t in zip(const, consts):
+        out[i] = t
     return out
 
 

@@ -187,3 +187,30 @@ def test_absorption_respects_frozen_gates_and_kept_labels():
     kept = tn.absorb_single_qubit_gates(net, keep_labels=lab)
     present = {l for lf in kept.leaves for l in lf.labels}
     assert set(lab) <= present
+
+
+def test_torch_leaves_keep_constant_copies_and_follow_params():
+    """The leaf tensors of a differentiated network (CPU tensors here): fSim
+    leaves are the gate's matrix at the given parameters in first-index-
+    fastest order; the constant leaves are copied once and reused, and a new
+    leaf list is copied again."""
+    torch = pytest.importorskip("torch")
+    circ = qi.random_grid_circuit(2, 2, 4, seed=0, theta=None, phi=None, param_seed=3)
+    net = tn.circuit_network(circ, None)
+    p0 = np.array([g.params for g in circ.gates if g.name == "fsim"])
+    params = torch.tensor(p0, dtype=torch.float64)
+    first = tn.torch_leaves(net, circ, params, device="cpu")
+    second = tn.torch_leaves(net, circ, params * 0.5, device="cpu")
+    fs = {g: i for i, g in enumerate(circ.fsim_indices())}
+    for i, lf in enumerate(net.leaves):
+        if lf.kind == "gate" and lf.gate in fs:
+            th, ph = (p0[fs[lf.gate]] * 0.5)
+            want = qi.fsim(th, ph).reshape(2, 2, 2, 2).transpose(3, 2, 1, 0).ravel()
+            np.testing.assert_allclose(second[i].numpy(), want, atol=1e-6)
+        else:
+            assert second[i] is first[i]
+            assert np.array_equal(second[i].numpy(), lf.data)
+    net.leaves = list(net.leaves)
+    third = tn.torch_leaves(net, circ, params, device="cpu")
+    assert all(third[i] is not first[i] for i, lf in enumerate(net.leaves)
+               if not (lf.kind == "gate" and lf.gate in fs))
