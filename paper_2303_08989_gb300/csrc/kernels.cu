@@ -738,11 +738,50 @@ __global__ void __launch_bounds__(256, 8) split_kernel(
             sr_ = (r < R) ? line_scale(line_emax[r]) : 0;
             pr_ = pow2_scale(sr_);
         }
+        const bool two = (c + 1 < K_pad);
+        if (mode == QCS_MODE_FP16X || mode == QCS_MODE_FP16X_SCALED) {
+            // Eq. 1 on the pairs (column c, column c + 1) of the real and of
+            // the imaginary parts with packed conversions: per value the same
+            // round-to-nearest steps as split_value, half the instructions
+            float2 re = make_float2(x[0], x[2]), im = make_float2(x[1], x[3]);
+            if (sr_ != 0) {
+                re = make_float2(apply_scale(re.x, pr_), apply_scale(re.y, pr_));
+                im = make_float2(apply_scale(im.x, pr_), apply_scale(im.y, pr_));
+            }
+            const __half2 hr = __float22half2_rn(re), hm = __float22half2_rn(im);
+            const float2 fr = __half22float2(hr), fm = __half22float2(hm);
+            const __half2 lr = __float22half2_rn(
+                make_float2((re.x - fr.x) * 2048.0f, (re.y - fr.y) * 2048.0f));
+            const __half2 lm = __float22half2_rn(
+                make_float2((im.x - fm.x) * 2048.0f, (im.y - fm.y) * 2048.0f));
+            auto bits = [](__half2 v) { return *reinterpret_cast<const uint32_t *>(&v); };
+            uint32_t w[5];
+            int nw = 0;
+            if (planes6) w[nw++] = bits(hm) ^ 0x80008000u;  // -hi.im
+            w[nw++] = bits(hr);
+            w[nw++] = bits(hm);
+            w[nw++] = bits(lr);
+            w[nw++] = bits(lm);
+            uint16_t *p = static_cast<uint16_t *>(planes) + plane_off + r * pitch + c;
+            const bool vec = two && ((reinterpret_cast<uintptr_t>(p) & 3u) == 0);
+#pragma unroll
+            for (int pl = 0; pl < 5; ++pl) {
+                if (pl < nw) {
+                    if (vec) {
+                        *reinterpret_cast<uint32_t *>(p) = w[pl];
+                    } else {
+                        p[0] = (uint16_t)(w[pl] & 0xFFFFu);
+                        if (two) p[1] = (uint16_t)(w[pl] >> 16);
+                    }
+                }
+                p += plane_stride;
+            }
+            continue;
+        }
         // hi/lo of re and im for columns c and c+1
         uint32_t hib[4], lob[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) split_value(mode, (sr_ != 0) ? apply_scale(x[e], pr_) : x[e], hib[e], lob[e]);
-        const bool two = (c + 1 < K_pad);
         // x[0]/x[2] real, x[1]/x[3] imaginary parts of columns c, c+1; the
         // planes in the order written, two consecutive values each
         uint32_t v0[5], v1[5];
