@@ -81,6 +81,8 @@ def parse(argv=None):
                         "one scale per matrix, per row of op(A) and per column of op(B); "
                         "'differentiation' one forward + backward of the differentiated "
                         "workload in its cheapest order (--mode auto or fp32)")
+    p.add_argument("--rowcol", action="store_true",
+                   help="with --profile gemm: line-scaled operands and per-row/column scaling on")
     p.add_argument("--complex-products", type=int, choices=[3, 4], default=4,
                    help="with --profile gemm: real products per complex product (3: Gauss)")
     p.add_argument("--gemm-shape", type=int, nargs=3, default=[2048, 8192, 32],
@@ -555,18 +557,27 @@ def profile_run(args):
         run = lambda: cp.forward(h)
     elif args.profile == "gemm":
         m, n, k = args.gemm_shape
-        g = torch.Generator(device=dev).manual_seed(9)
-        A = torch.randn((k, m), dtype=torch.complex64, device=dev, generator=g).t()
-        B = torch.randn((n, k), dtype=torch.complex64, device=dev, generator=g).t()
-        C = q.fortran_empty(m, n, device=dev)
         h = q.Handle(tol=args.tol, size_rule=False)
         h.set_complex_products(args.complex_products)
+        if args.rowcol:
+            if not (m == n == k):
+                raise SystemExit("--rowcol takes a square --gemm-shape")
+            A = make_line_operand(torch, m, 30, 0, 41 * m, dev)
+            B = make_line_operand(torch, m, 30, 1, 43 * m, dev)
+            h.set_rowcol_scaling(True)
+        else:
+            g = torch.Generator(device=dev).manual_seed(9)
+            A = torch.randn((k, m), dtype=torch.complex64, device=dev, generator=g).t()
+            B = torch.randn((n, k), dtype=torch.complex64, device=dev, generator=g).t()
+        C = q.fortran_empty(m, n, device=dev)
 
         def run():
             for _ in range(10):
                 q.cgemm(h, A, B, C, mode=args.mode)
-        what = "10 x qcs_cgemm (%d, %d, %d), mode %s, parts N(0,1), %d real products" % (
-            m, n, k, args.mode, args.complex_products)
+        what = "10 x qcs_cgemm (%d, %d, %d), mode %s, %s, %d real products" % (
+            m, n, k, args.mode,
+            "lines N(0,1)*2^e, e~U_int[-30,30], per-row/column scaling on" if args.rowcol
+            else "parts N(0,1)", args.complex_products)
     elif args.profile == "sgemm":
         m, n, k = args.gemm_shape
         g = torch.Generator(device=dev).manual_seed(9)

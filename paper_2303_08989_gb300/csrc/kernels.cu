@@ -881,17 +881,21 @@ __global__ void __launch_bounds__(256) line_emax_kernel(const float2 *__restrict
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t r = (int64_t)blockIdx.x * kLineTile + lane;
     const int64_t ctiles = (cols + kLineTile - 1) / kLineTile;
+    // a block walks several column tiles of its 32 rows; a row's maximum is
+    // kept in registers across them and reduced once at the end
+    int mine = -1;
     for (int64_t ct = blockIdx.y; ct < ctiles; ct += gridDim.y) {
         const int64_t c0 = ct * kLineTile;
-        int mine = -1;
+        float2 v[kLineTile / 8];
 #pragma unroll
         for (int i = 0; i < kLineTile / 8; ++i) {
             const int64_t c = c0 + warp + 8 * i;
-            int e = -1;
-            if (r < rows && c < cols) {
-                const float2 v = X[r + c * ld];
-                e = max(biased_exp_nz(v.x), biased_exp_nz(v.y));
-            }
+            v[i] = (r < rows && c < cols) ? X[r + c * ld] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < kLineTile / 8; ++i) {
+            const int64_t c = c0 + warp + 8 * i;
+            int e = max(biased_exp_nz(v[i].x), biased_exp_nz(v[i].y));
             if (per_row) {
                 mine = max(mine, e);
             } else {
@@ -900,16 +904,15 @@ __global__ void __launch_bounds__(256) line_emax_kernel(const float2 *__restrict
                 if (lane == 0 && c < cols && e >= 0) atomicMax(emax + c, e);
             }
         }
-        if (per_row) {
-            red[warp][lane] = mine;
-            __syncthreads();
-            if (warp == 0) {
-                int v = red[0][lane];
+    }
+    if (per_row) {
+        red[warp][lane] = mine;
+        __syncthreads();
+        if (warp == 0) {
+            int m = red[0][lane];
 #pragma unroll
-                for (int w = 1; w < 8; ++w) v = max(v, red[w][lane]);
-                if (r < rows && v >= 0) atomicMax(emax + r, v);
-            }
-            __syncthreads();
+            for (int w = 1; w < 8; ++w) m = max(m, red[w][lane]);
+            if (r < rows && m >= 0) atomicMax(emax + r, m);
         }
     }
 }
@@ -926,20 +929,24 @@ __global__ void __launch_bounds__(256) line_under_kernel(const float2 *__restric
     const int er = (per_row && r < rows) ? emax[r] : -1;
     for (int64_t ct = blockIdx.y; ct < ctiles; ct += gridDim.y) {
         const int64_t c0 = ct * kLineTile;
+        float2 v[kLineTile / 8];
+        int E[kLineTile / 8];
 #pragma unroll
         for (int i = 0; i < kLineTile / 8; ++i) {
             const int64_t c = c0 + warp + 8 * i;
-            if (r < rows && c < cols) {
-                const float2 v = X[r + c * ld];
-                const int E = per_row ? er : emax[c];
-                const float parts[2] = {v.x, v.y};
+            const bool in = r < rows && c < cols;
+            v[i] = in ? X[r + c * ld] : make_float2(0.f, 0.f);  // zeros count nowhere
+            E[i] = per_row ? er : (c < cols ? emax[c] : -1);
+        }
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int b = biased_exp_nz(parts[h]);
-                    if (b < 0) continue;
-                    ++nnz;
-                    if (b == 0 || b < E - 28) ++under;
-                }
+        for (int i = 0; i < kLineTile / 8; ++i) {
+            const float parts[2] = {v[i].x, v[i].y};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int b = biased_exp_nz(parts[h]);
+                if (b < 0) continue;
+                ++nnz;
+                if (b == 0 || b < E[i] - 28) ++under;
             }
         }
     }
@@ -1016,9 +1023,13 @@ __global__ void __launch_bounds__(256) rowcol_combine_kernel(
     }
 }
 
+// 32-row block columns, each block walking up to kLineTilesPerBlock column
+// tiles (fewer blocks, more bytes in flight per thread)
+constexpr int kLineTilesPerBlock = 16;
 dim3 line_grid(int64_t rows, int64_t cols) {
     const int64_t gx = (rows + kLineTile - 1) / kLineTile;
-    const int64_t gy = (cols + kLineTile - 1) / kLineTile;
+    const int64_t ct = (cols + kLineTile - 1) / kLineTile;
+    const int64_t gy = (ct + kLineTilesPerBlock - 1) / kLineTilesPerBlock;
     return dim3((unsigned)gx, (unsigned)std::min<int64_t>(gy, 65535));
 }
 
