@@ -391,6 +391,46 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
         e = launch_set_desc(desc, eff, s, G);
         if (e != cudaSuccess) return QCS_ERR_CUDA;
     }
+    // The statistics and selection of all instances in one launch each, when
+    // every operand is read as stored (a matrix, or a whole-tensor map) with
+    // the instances' operands one stride apart
+    bool stats_done = false;
+    if (!d_desc_in && G > 1 && (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X_SCALED) &&
+        (!A0.map || fusedA) && (!B0.map || fusedB)) {
+        auto stride_of = [&](const std::vector<OperandView> &V, int64_t &stride) {
+            const intptr_t d = reinterpret_cast<intptr_t>(V[1].X) - reinterpret_cast<intptr_t>(V[0].X);
+            if (d % (intptr_t)sizeof(float2) != 0) return false;
+            for (int g = 1; g < G; ++g)
+                if (reinterpret_cast<intptr_t>(V[g].X) - reinterpret_cast<intptr_t>(V[0].X) !=
+                        (intptr_t)g * d ||
+                    V[g].map != V[0].map || V[g].ld != V[0].ld || V[g].flat != V[0].flat)
+                    return false;
+            stride = (int64_t)(d / (intptr_t)sizeof(float2));
+            return true;
+        };
+        int64_t sxA = 0, sxB = 0;
+        const int64_t ra = fusedA ? A0.flat : ((opA == QCS_OP_N) ? m : k);
+        const int64_t ca = fusedA ? 1 : ((opA == QCS_OP_N) ? k : m);
+        const int64_t rb = fusedB ? B0.flat : ((opB == QCS_OP_N) ? k : n);
+        const int64_t cb = fusedB ? 1 : ((opB == QCS_OP_N) ? n : k);
+        // per-instance blocks so that the whole batch fills the GPU about as
+        // one instance does; the partials of all instances fit the buffer
+        const int share = std::max(1, (4 * h->num_sms + G - 1) / G);
+        const int gA = std::min(stats2_blocks(ra * ca, h->num_sms), share);
+        const int gB = std::min(stats2_blocks(rb * cb, h->num_sms), share);
+        const int64_t need = (int64_t)6 * G * (gA + gB);
+        if (G <= 65535 && need <= (int64_t)2 * h->num_sms * kPartialStride &&
+            stride_of(Av, sxA) && stride_of(Bv, sxB)) {
+            ProfScope ps(h, kProfStats);
+            e = launch_stats_select_2stage_batch(
+                A0.X, ra, ca, fusedA ? A0.flat : A0.ld, gA, sxA, B0.X, rb, cb,
+                fusedB ? B0.flat : B0.ld, gB, sxB, G, h->tol, eff, partials,
+                partials + (int64_t)5 * G * (gA + gB), desc, h->d_counts,
+                8.0 * (double)m * (double)n * (double)k, s);
+            if (e != cudaSuccess) return QCS_ERR_CUDA;
+            stats_done = true;
+        }
+    }
     for (int g = 0; g < G; ++g) {
         OperandView &A = Av[g], &B = Bv[g];
         qcs_gemm_desc_t *dg = desc + g;
@@ -401,7 +441,7 @@ int run_cgemm_group(qcs_handle_t h, void *ws, int eff, int opA, int opB, int64_t
         if (d_desc_in) {
             dg = const_cast<qcs_gemm_desc_t *>(d_desc_in);
             desc = dg;
-        } else if (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X_SCALED) {
+        } else if (!stats_done && (eff == QCS_MODE_AUTO || eff == QCS_MODE_FP16X_SCALED)) {
             // Statistics of both operands as stored (a transpose or a
             // whole-tensor permutation does not change the multiset).
             const int64_t ra = fusedA ? A.flat : ((opA == QCS_OP_N) ? m : k);

@@ -179,6 +179,17 @@ cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t 
                                        int64_t *p2, qcs_gemm_desc_t *desc,
                                        unsigned long long *counts, double work, cudaStream_t s,
                                        int64_t *summary = nullptr);
+// The same for G instances in one launch each: instance g reads X0 + g dx0
+// and X1 + g dx1, uses partials p1 + 5 g (gA + gB), p2 + g (gA + gB) and
+// writes desc[g]; the counts are integers, so a decision does not depend on
+// the batch or the block counts.
+cudaError_t launch_stats_select_2stage_batch(const float2 *X0, int64_t rows0, int64_t cols0,
+                                             int64_t ld0, int gA, int64_t dx0, const float2 *X1,
+                                             int64_t rows1, int64_t cols1, int64_t ld1, int gB,
+                                             int64_t dx1, int G, double tol, int forced,
+                                             int64_t *p1, int64_t *p2, qcs_gemm_desc_t *desc,
+                                             unsigned long long *counts, double work,
+                                             cudaStream_t s);
 int stats2_blocks(int64_t nel, int num_sms);
 // Select from two finished qcs_stats_t.
 cudaError_t launch_select_from_stats(const qcs_stats_t *a, const qcs_stats_t *b, double tol,

@@ -399,9 +399,13 @@ template <class T>
 __global__ void __launch_bounds__(kS2Threads) stats_pass1_kernel(
     const T *__restrict__ X0, int64_t rows0, int64_t cols0, int64_t ld0, int gA,
     const T *__restrict__ X1, int64_t rows1, int64_t cols1, int64_t ld1, int gB,
-    int64_t *__restrict__ p1) {
+    int64_t *__restrict__ p1, int64_t dx0, int64_t dx1) {
     __shared__ uint32_t shm[kS2Threads / 32];
     __shared__ uint64_t shs[kS2Threads / 32];
+    // instance blockIdx.y of a batch: operands dx0 / dx1 elements apart
+    X0 += blockIdx.y * dx0;
+    X1 += blockIdx.y * dx1;
+    p1 += (int64_t)blockIdx.y * 5 * (gA + gB);
     const bool first = blockIdx.x < gA;
     const T *X = first ? X0 : X1;
     const int64_t blk = first ? blockIdx.x : blockIdx.x - gA;
@@ -466,9 +470,14 @@ template <class T>
 __global__ void __launch_bounds__(kS2Threads) stats_pass2_kernel(
     const T *__restrict__ X0, int64_t rows0, int64_t cols0, int64_t ld0, int gA,
     const T *__restrict__ X1, int64_t rows1, int64_t cols1, int64_t ld1, int gB,
-    const int64_t *__restrict__ p1, double tol, int forced, int64_t *__restrict__ p2) {
+    const int64_t *__restrict__ p1, double tol, int forced, int64_t *__restrict__ p2,
+    int64_t dx0, int64_t dx1) {
     __shared__ uint64_t shs[kS2Threads / 32];
     __shared__ uint32_t shm[kS2Threads / 32];
+    X0 += blockIdx.y * dx0;
+    X1 += blockIdx.y * dx1;
+    p1 += (int64_t)blockIdx.y * 5 * (gA + gB);
+    p2 += (int64_t)blockIdx.y * (gA + gB);
     const Sum1 a = reduce_p1(p1, 0, gA, scalars_per<T>() * rows0 * cols0, shm, shs);
     const Sum1 b = reduce_p1(p1, gA, gA + gB, scalars_per<T>() * rows1 * cols1, shm, shs);
     if (!needs_stage2(a, b, tol, forced)) return;  // uniform across the block
@@ -494,6 +503,10 @@ __global__ void select2_kernel(const int64_t *__restrict__ p1, const int64_t *__
                                int64_t *summary) {
     __shared__ uint64_t shs[kS2Threads / 32];
     __shared__ uint32_t shm[kS2Threads / 32];
+    // instance blockIdx.x of a batch: its partials and its descriptor
+    p1 += (int64_t)blockIdx.x * 5 * (gA + gB);
+    p2 += (int64_t)blockIdx.x * (gA + gB);
+    desc += blockIdx.x;
     const Sum1 a = reduce_p1(p1, 0, gA, nA, shm, shs);
     const Sum1 b = reduce_p1(p1, gA, gA + gB, nB, shm, shs);
     uint64_t u2a = 0, u2b = 0;
@@ -572,19 +585,34 @@ static cudaError_t stats_select_2stage(const T *X0, int64_t rows0, int64_t cols0
                                        int64_t ld1, int gB, double tol, int forced, int64_t *p1,
                                        int64_t *p2, qcs_gemm_desc_t *desc,
                                        unsigned long long *counts, double work, cudaStream_t s,
-                                       int64_t *summary) {
-    stats_pass1_kernel<T><<<gA + gB, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1,
-                                                         cols1, ld1, gB, p1);
+                                       int64_t *summary, int G = 1, int64_t dx0 = 0,
+                                       int64_t dx1 = 0) {
+    if (G < 1 || G > 65535 || (G > 1 && summary)) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)(gA + gB), (unsigned)G);
+    stats_pass1_kernel<T><<<grid, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1,
+                                                      cols1, ld1, gB, p1, dx0, dx1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    stats_pass2_kernel<T><<<gA + gB, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1,
-                                                         cols1, ld1, gB, p1, tol, forced, p2);
+    stats_pass2_kernel<T><<<grid, kS2Threads, 0, s>>>(X0, rows0, cols0, ld0, gA, X1, rows1,
+                                                      cols1, ld1, gB, p1, tol, forced,
+                                                      p2, dx0, dx1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    select2_kernel<<<1, kS2Threads, 0, s>>>(p1, p2, gA, gB, scalars_per<T>() * rows0 * cols0,
+    select2_kernel<<<G, kS2Threads, 0, s>>>(p1, p2, gA, gB, scalars_per<T>() * rows0 * cols0,
                                             scalars_per<T>() * rows1 * cols1, tol, forced, desc,
                                             counts, work, summary);
     return cudaGetLastError();
+}
+
+cudaError_t launch_stats_select_2stage_batch(const float2 *X0, int64_t rows0, int64_t cols0,
+                                             int64_t ld0, int gA, int64_t dx0, const float2 *X1,
+                                             int64_t rows1, int64_t cols1, int64_t ld1, int gB,
+                                             int64_t dx1, int G, double tol, int forced,
+                                             int64_t *p1, int64_t *p2, qcs_gemm_desc_t *desc,
+                                             unsigned long long *counts, double work,
+                                             cudaStream_t s) {
+    return stats_select_2stage(X0, rows0, cols0, ld0, gA, X1, rows1, cols1, ld1, gB, tol, forced,
+                               p1, p2, desc, counts, work, s, (int64_t *)nullptr, G, dx0, dx1);
 }
 
 cudaError_t launch_stats_select_2stage(const float2 *X0, int64_t rows0, int64_t cols0, int64_t ld0,
