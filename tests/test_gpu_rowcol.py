@@ -3,6 +3,8 @@ variant beyond the paper on Section 4.1's scaling basis) against the FP64
 oracle: the per-line statistics bit for bit, the selection, the product
 element by element against the oracle's exact model of the emulation, and
 every other outcome bit-identical to the call with the option off."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -146,3 +148,26 @@ def test_rowcol_error_bar_and_against_tf32x(handles):
     err_f32 = oracle.rel_fro_error(f32.astype(np.complex128), exact)
     err_tf = oracle.rel_fro_error(got_tf[rows].astype(np.complex128), exact)
     assert err <= 1e-6 and err <= 2 * err_f32, (err, err_f32, err_tf)
+
+
+def test_invalid_arguments_are_rejected(handles):
+    on, _ = handles
+    q = lib()
+    L = q._lib
+    f = on.lib.qcs_rowcol_stats
+    buf = torch.zeros(64, dtype=torch.int64, device="cuda")
+    P = buf.data_ptr()
+    E = L.QCS_ERR_INVALID_ARG
+    assert on.lib.qcs_set_rowcol_scaling(on.ptr, 2) == E
+    assert on.lib.qcs_set_rowcol_scaling(None, 1) == E
+    assert f(None, 0, 0, 2, 2, 2, P, 2, P, 2, P, P, P) == E
+    assert f(on.ptr, 3, 0, 2, 2, 2, P, 2, P, 2, P, P, P) == E      # bad op
+    assert f(on.ptr, 0, 0, 4, 2, 2, P, 3, P, 2, P, P, P) == E      # lda < m
+    assert f(on.ptr, 0, 1, 2, 4, 2, P, 2, P, 3, P, P, P) == E      # ldb < n for op T
+    assert f(on.ptr, 0, 0, 2, 2, 2, P, 2, P, 2, None, P, P) == E   # no emaxA
+    assert f(on.ptr, 0, 0, 2, 2, 2, P, 2, P, 2, P, P, None) == E   # no counts
+    assert f(on.ptr, 0, 0, -1, 2, 2, P, 2, P, 2, P, P, P) == E
+    # a GEMM that reports the per-line mode takes no such mode as an argument
+    one, zero = L.qcs_c32(1.0, 0.0), L.qcs_c32(0.0, 0.0)
+    assert on.lib.qcs_cgemm(on.ptr, q.MODE_FP16X_ROWCOL, 0, 0, 2, 2, 2, ctypes.byref(one), P, 2,
+                            P, 2, ctypes.byref(zero), P, 2, None) == E
