@@ -3191,6 +3191,13 @@ constexpr int kRStages = 3;
 constexpr int kRPad = 132;  // row length of a shared tile (16-byte rows; transposed copies spread over banks)
 constexpr size_t kRSmemBytes = sizeof(float) * 2 * kRStages * kRK * kRPad;
 
+// 16-byte asynchronous copy to shared memory (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src))
+                 : "memory");
+}
+
 // C = alpha op(A) op(B) + beta C on the CUDA cores: 128 x 128 tiles, 256
 // threads with 8 x 8 outputs each (rows 4t..4t+3 and 64+4t..64+4t+3 of the
 // tile, likewise columns).  Operand tiles of 16 k move to shared memory with
@@ -3234,26 +3241,48 @@ __global__ void __launch_bounds__(256, 2) sgemm_simt_kernel(
             b_mask |= uint32_t(j0 + bJ + (TB ? 0 : 16 * q) < n) << q;
         }
         const bool interior = i0 + kRT <= m && j0 + kRT <= n;
+        // operands contiguous along the shared tile's rows (op(A) N, op(B) T)
+        // with 16-byte aligned columns move in 16-byte copies inside the matrix
+        const bool a16 = !TA && interior && lda % 4 == 0 &&
+                         (reinterpret_cast<uintptr_t>(A) & 15u) == 0;
+        const bool b16 = TB && interior && ldb % 4 == 0 &&
+                         (reinterpret_cast<uintptr_t>(B) & 15u) == 0;
         auto load_tile = [&](int st, int kt) {
             const int64_t k0 = static_cast<int64_t>(kt) * kRK;
             const bool tail = k0 + kRK > k;
-            const float *pa = a_base + kt * a_kstep;
-            const float *pb = b_base + kt * b_kstep;
+            if (a16 && !tail) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int l = TA ? aL : aL + 2 * q;
-                const int i = TA ? aI + 16 * q : aI;
-                bool ok = true;
-                if (!interior || tail) ok = ((a_mask >> q) & 1u) && k0 + l < k;
-                cp_async4(&As[st][l][i], ok ? pa + q * a_qstep : A, ok ? 4u : 0u);
+                for (int q = 0; q < 2; ++q) {
+                    const int c = tid + 256 * q, i = 4 * (c & 31), l = c >> 5;
+                    cp_async16(&As[st][l][i], A + (i0 + i) + (k0 + l) * lda);
+                }
+            } else {
+                const float *pa = a_base + kt * a_kstep;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int l = TA ? aL : aL + 2 * q;
+                    const int i = TA ? aI + 16 * q : aI;
+                    bool ok = true;
+                    if (!interior || tail) ok = ((a_mask >> q) & 1u) && k0 + l < k;
+                    cp_async4(&As[st][l][i], ok ? pa + q * a_qstep : A, ok ? 4u : 0u);
+                }
             }
+            if (b16 && !tail) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int l = TB ? bL + 2 * q : bL;
-                const int j = TB ? bJ : bJ + 16 * q;
-                bool ok = true;
-                if (!interior || tail) ok = ((b_mask >> q) & 1u) && k0 + l < k;
-                cp_async4(&Bs[st][l][j], ok ? pb + q * b_qstep : B, ok ? 4u : 0u);
+                for (int q = 0; q < 2; ++q) {
+                    const int c = tid + 256 * q, j = 4 * (c & 31), l = c >> 5;
+                    cp_async16(&Bs[st][l][j], B + (j0 + j) + (k0 + l) * ldb);
+                }
+            } else {
+                const float *pb = b_base + kt * b_kstep;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int l = TB ? bL + 2 * q : bL;
+                    const int j = TB ? bJ : bJ + 16 * q;
+                    bool ok = true;
+                    if (!interior || tail) ok = ((b_mask >> q) & 1u) && k0 + l < k;
+                    cp_async4(&Bs[st][l][j], ok ? pb + q * b_qstep : B, ok ? 4u : 0u);
+                }
             }
         };
         float acc[8][8];
